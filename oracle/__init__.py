@@ -1,0 +1,186 @@
+"""TEST INFRASTRUCTURE ONLY: ctypes wrapper around the C oracle (``oracle.c``).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The product library never loads it.
+
+``run(workload)`` evaluates a :class:`datagen.workloads.Workload` and returns an
+:class:`OracleResult` with the groups sorted ascending by packed key.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ORC_I32, ORC_I64, ORC_U8 = 0, 1, 2
+ORC_SUM, ORC_SUM_MUL_SUB, ORC_COUNT, ORC_AVG = 0, 1, 2, 3
+STATUS = {0: "ok", 1: "invalid", 4: "dup_key", 8: "range", 9: "nomem"}
+_TYPES = {np.dtype(np.int32): ORC_I32, np.dtype(np.int64): ORC_I64, np.dtype(np.uint8): ORC_U8}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code):
+        super().__init__(f"oracle status {code} ({STATUS.get(code, '?')})")
+        self.code = code
+        self.status = STATUS.get(code, "?")
+
+
+class _Column(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("data", ctypes.c_void_p)]
+
+
+class _Agg(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("col_a", ctypes.c_int32), ("col_b", ctypes.c_int32),
+                ("k", ctypes.c_int64)]
+
+
+class _Query(ctypes.Structure):
+    _fields_ = [
+        ("n_fact", ctypes.c_uint64), ("n_fact_cols", ctypes.c_int32),
+        ("fact", ctypes.POINTER(_Column)),
+        ("n_dim", ctypes.c_uint64), ("n_dim_cols", ctypes.c_int32),
+        ("dim", ctypes.POINTER(_Column)),
+        ("filter_col", ctypes.c_int32), ("filter_lo", ctypes.c_int64), ("filter_hi", ctypes.c_int64),
+        ("join_fact_col", ctypes.c_int32), ("join_dim_col", ctypes.c_int32),
+        ("n_group", ctypes.c_int32), ("group_side", ctypes.c_int32 * 4),
+        ("group_col", ctypes.c_int32 * 4), ("group_bits", ctypes.c_int32 * 4),
+        ("n_agg", ctypes.c_int32), ("aggs", _Agg * 8),
+    ]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("n_groups", ctypes.c_uint64), ("keys", ctypes.POINTER(ctypes.c_uint64)),
+                ("counts", ctypes.POINTER(ctypes.c_int64)), ("sums", ctypes.POINTER(ctypes.c_uint64)),
+                ("avgs", ctypes.POINTER(ctypes.c_double))]
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(_HERE, "oracle.c")
+    hdr = os.path.join(_HERE, "oracle.h")
+    newest = max(os.path.getmtime(src), os.path.getmtime(hdr))
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, src])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            lib.orc_run.restype = ctypes.c_int32
+            lib.orc_run.argtypes = [ctypes.POINTER(_Query), ctypes.POINTER(_Result)]
+            lib.orc_free.restype = None
+            lib.orc_free.argtypes = [ctypes.POINTER(_Result)]
+            lib.orc_i128_to_double.restype = ctypes.c_double
+            lib.orc_i128_to_double.argtypes = [ctypes.c_uint64, ctypes.c_int64]
+            _lib = lib
+    return _lib
+
+
+@dataclass
+class OracleResult:
+    keys: np.ndarray        # uint64 [G], ascending
+    counts: np.ndarray      # int64 [G]
+    sums: np.ndarray        # uint64 [G, A, 2]: int128 as (lo, hi) words
+    avgs: np.ndarray        # float64 [G, A]
+    aggs: list
+
+    @property
+    def n_groups(self) -> int:
+        return int(self.keys.size)
+
+    def sum_int(self, g: int, a: int) -> int:
+        lo, hi = int(self.sums[g, a, 0]), int(self.sums[g, a, 1])
+        v = (hi << 64) | lo
+        return v - (1 << 128) if v >= 1 << 127 else v
+
+
+def _columns(table: dict):
+    names = list(table.keys())
+    arrs = [np.ascontiguousarray(table[n]) for n in names]
+    cols = (_Column * max(1, len(arrs)))()
+    for i, a in enumerate(arrs):
+        cols[i].type = _TYPES[a.dtype]
+        cols[i].data = a.ctypes.data
+    return names, arrs, cols
+
+
+def run(wl) -> OracleResult:
+    """Evaluate a workload's query over its tables; raises OracleError."""
+    return run_query(wl.fact, wl.dim, wl.query)
+
+
+def run_query(fact: dict, dim: dict | None, query: dict) -> OracleResult:
+    lib = _load()
+    fnames, farrs, fcols = _columns(fact)
+    dnames, darrs, dcols = _columns(dim if dim is not None else {})
+    n_fact = len(farrs[0]) if farrs else 0
+    n_dim = len(darrs[0]) if darrs else 0
+    q = _Query()
+    q.n_fact, q.n_fact_cols, q.fact = n_fact, len(farrs), fcols
+    q.n_dim, q.n_dim_cols, q.dim = n_dim, len(darrs), dcols
+    f = query.get("filter")
+    if f is None:
+        q.filter_col, q.filter_lo, q.filter_hi = -1, 0, 0
+    else:
+        q.filter_col, q.filter_lo, q.filter_hi = fnames.index(f["col"]), f["lo"], f["hi"]
+    j = query.get("join")
+    if j is None:
+        q.join_fact_col, q.join_dim_col = -1, -1
+    else:
+        q.join_fact_col, q.join_dim_col = fnames.index(j["fact_col"]), dnames.index(j["dim_col"])
+    q.n_group = len(query["group"])
+    for i, (side, col, bits) in enumerate(query["group"]):
+        q.group_side[i] = 0 if side == "fact" else 1
+        q.group_col[i] = (fnames if side == "fact" else dnames).index(col)
+        q.group_bits[i] = bits
+    q.n_agg = len(query["aggs"])
+    for i, ag in enumerate(query["aggs"]):
+        kind = ag[0]
+        if kind == "sum":
+            q.aggs[i].kind, q.aggs[i].col_a = ORC_SUM, fnames.index(ag[1])
+        elif kind == "avg":
+            q.aggs[i].kind, q.aggs[i].col_a = ORC_AVG, fnames.index(ag[1])
+        elif kind == "count":
+            q.aggs[i].kind = ORC_COUNT
+        elif kind == "sum_mul_sub":
+            q.aggs[i].kind = ORC_SUM_MUL_SUB
+            q.aggs[i].col_a, q.aggs[i].k, q.aggs[i].col_b = fnames.index(ag[1]), ag[2], fnames.index(ag[3])
+        else:
+            raise ValueError(kind)
+    res = _Result()
+    rc = lib.orc_run(ctypes.byref(q), ctypes.byref(res))
+    if rc != 0:
+        raise OracleError(rc)
+    try:
+        g, a = int(res.n_groups), q.n_agg
+        keys = np.ctypeslib.as_array(res.keys, shape=(max(g, 1),))[:g].copy()
+        counts = np.ctypeslib.as_array(res.counts, shape=(max(g, 1),))[:g].copy()
+        sums = np.ctypeslib.as_array(res.sums, shape=(max(g, 1) * max(a, 1) * 2,))
+        sums = sums[: g * a * 2].copy().reshape(g, a, 2)
+        avgs = np.ctypeslib.as_array(res.avgs, shape=(max(g, 1) * max(a, 1),))[: g * a].copy()
+        avgs = avgs.reshape(g, a)
+    finally:
+        lib.orc_free(ctypes.byref(res))
+    return OracleResult(keys, counts, sums, avgs, list(query["aggs"]))
+
+
+def i128_to_double(v: int) -> float:
+    """(double) of a 128-bit integer, by the C conversion the oracle uses."""
+    v &= (1 << 128) - 1
+    hi = v >> 64
+    hi = hi - (1 << 64) if hi >= 1 << 63 else hi
+    return _load().orc_i128_to_double(v & ((1 << 64) - 1), hi)

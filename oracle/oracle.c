@@ -1,0 +1,211 @@
+/*
+ * TEST INFRASTRUCTURE ONLY -- the oracle.  Plain, slow, single-threaded C.
+ * Only tests, the smoke check and the benchmark's CPU-baseline leg use it.
+ *
+ * It writes out the relational definition of the query directly:
+ *   1. Filter (Section 3.1, the Filter operator): keep fact row f when
+ *      lo <= f.filter_col <= hi.
+ *   2. Join (Section 3.2, the Adaptive Join; here a PK-FK inner equi-join):
+ *      pair f with the unique dimension row d whose key equals f's foreign
+ *      key; rows without a partner drop out.  The dimension keys are sorted
+ *      and searched by bisection; duplicate keys are an error.
+ *   3. Group and aggregate: the group key concatenates the group fields, the
+ *      first field in the highest bits.  Surviving (key, row) pairs are sorted
+ *      and each run of equal keys is reduced with exact 128-bit integer sums
+ *      (Section 4: decimals held as 128-bit integers).  AVG is one IEEE
+ *      double division of the exact sum, converted to double, by the count.
+ * No step is blocked, fused or reordered beyond that definition.
+ */
+#include "oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+static int64_t col_at(const orc_column* c, uint64_t i) {
+    switch (c->type) {
+    case ORC_I32: return ((const int32_t*)c->data)[i];
+    case ORC_I64: return ((const int64_t*)c->data)[i];
+    default: return ((const uint8_t*)c->data)[i];
+    }
+}
+
+typedef struct { int64_t key; uint64_t row; } key_row;
+
+static int cmp_key_row_signed(const void* a, const void* b) {
+    const key_row* x = (const key_row*)a;
+    const key_row* y = (const key_row*)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->row < y->row ? -1 : (x->row > y->row);
+}
+
+static int cmp_key_row_unsigned(const void* a, const void* b) {
+    const key_row* x = (const key_row*)a;
+    const key_row* y = (const key_row*)b;
+    uint64_t kx = (uint64_t)x->key, ky = (uint64_t)y->key;
+    if (kx != ky) return kx < ky ? -1 : 1;
+    return x->row < y->row ? -1 : (x->row > y->row);
+}
+
+/* dimension row holding key k, or -1 */
+static int64_t find_dim_row(const key_row* sorted, uint64_t n, int64_t k) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (sorted[mid].key < k) lo = mid + 1; else hi = mid;
+    }
+    return (lo < n && sorted[lo].key == k) ? (int64_t)sorted[lo].row : -1;
+}
+
+static int valid_col(int32_t c, int32_t n) { return c >= 0 && c < n; }
+
+static int32_t validate(const orc_query* q) {
+    int total = 0;
+    if (q->n_group < 0 || q->n_group > 4 || q->n_agg < 0 || q->n_agg > 8) return ORC_INVALID;
+    if (q->filter_col >= 0 && !valid_col(q->filter_col, q->n_fact_cols)) return ORC_INVALID;
+    if (q->join_fact_col >= 0 &&
+        (!valid_col(q->join_fact_col, q->n_fact_cols) || !valid_col(q->join_dim_col, q->n_dim_cols)))
+        return ORC_INVALID;
+    for (int g = 0; g < q->n_group; ++g) {
+        int bits = q->group_bits[g];
+        if (bits < 1 || bits > 64) return ORC_INVALID;
+        total += bits;
+        if (q->group_side[g] == 0) {
+            if (!valid_col(q->group_col[g], q->n_fact_cols)) return ORC_INVALID;
+        } else {
+            if (q->join_fact_col < 0 || !valid_col(q->group_col[g], q->n_dim_cols)) return ORC_INVALID;
+        }
+    }
+    if (total > 64) return ORC_INVALID;
+    for (int a = 0; a < q->n_agg; ++a) {
+        const orc_agg* ag = &q->aggs[a];
+        if (ag->kind == ORC_SUM || ag->kind == ORC_AVG) {
+            if (!valid_col(ag->col_a, q->n_fact_cols)) return ORC_INVALID;
+        } else if (ag->kind == ORC_SUM_MUL_SUB) {
+            if (!valid_col(ag->col_a, q->n_fact_cols) || !valid_col(ag->col_b, q->n_fact_cols))
+                return ORC_INVALID;
+        } else if (ag->kind != ORC_COUNT) {
+            return ORC_INVALID;
+        }
+    }
+    return ORC_OK;
+}
+
+double orc_i128_to_double(uint64_t lo, int64_t hi) {
+    i128 v = (i128)(((u128)(uint64_t)hi << 64) | (u128)lo);
+    return (double)v;
+}
+
+int32_t orc_run(const orc_query* q, orc_result* out) {
+    int32_t rc = validate(q);
+    memset(out, 0, sizeof(*out));
+    if (rc != ORC_OK) return rc;
+
+    /* Join side: sort (pk, row) and reject duplicate keys. */
+    key_row* dim = NULL;
+    if (q->join_fact_col >= 0 && q->n_dim > 0) {
+        dim = (key_row*)malloc(q->n_dim * sizeof(key_row));
+        if (!dim) return ORC_NOMEM;
+        for (uint64_t i = 0; i < q->n_dim; ++i) {
+            dim[i].key = col_at(&q->dim[q->join_dim_col], i);
+            dim[i].row = i;
+        }
+        qsort(dim, q->n_dim, sizeof(key_row), cmp_key_row_signed);
+        for (uint64_t i = 1; i < q->n_dim; ++i)
+            if (dim[i].key == dim[i - 1].key) { free(dim); return ORC_DUP_KEY; }
+    }
+
+    /* Filter, join and key every fact row; keep (group key, fact row). */
+    key_row* kept = (key_row*)malloc((q->n_fact ? q->n_fact : 1) * sizeof(key_row));
+    if (!kept) { free(dim); return ORC_NOMEM; }
+    uint64_t n_kept = 0;
+    for (uint64_t i = 0; i < q->n_fact; ++i) {
+        if (q->filter_col >= 0) {
+            int64_t v = col_at(&q->fact[q->filter_col], i);
+            if (v < q->filter_lo || v > q->filter_hi) continue;
+        }
+        int64_t d = -1;
+        if (q->join_fact_col >= 0) {
+            if (dim == NULL) continue;
+            d = find_dim_row(dim, q->n_dim, col_at(&q->fact[q->join_fact_col], i));
+            if (d < 0) continue;
+        }
+        uint64_t key = 0;
+        for (int g = 0; g < q->n_group; ++g) {
+            int bits = q->group_bits[g];
+            int64_t v = q->group_side[g] == 0 ? col_at(&q->fact[q->group_col[g]], i)
+                                              : col_at(&q->dim[q->group_col[g]], (uint64_t)d);
+            if (bits < 64) {
+                if (v < 0 || (uint64_t)v >= (1ull << bits)) {
+                    free(dim); free(kept);
+                    return ORC_RANGE;
+                }
+                key = (key << bits) | (uint64_t)v;
+            } else {
+                key = (uint64_t)v;
+            }
+        }
+        kept[n_kept].key = (int64_t)key;
+        kept[n_kept].row = i;
+        ++n_kept;
+    }
+    free(dim);
+    qsort(kept, n_kept, sizeof(key_row), cmp_key_row_unsigned);
+
+    /* Count groups, then reduce each run of equal keys. */
+    uint64_t n_groups = 0;
+    for (uint64_t i = 0; i < n_kept; ++i)
+        if (i == 0 || kept[i].key != kept[i - 1].key) ++n_groups;
+    int na = q->n_agg;
+    out->n_groups = n_groups;
+    out->keys = (uint64_t*)malloc((n_groups ? n_groups : 1) * sizeof(uint64_t));
+    out->counts = (int64_t*)malloc((n_groups ? n_groups : 1) * sizeof(int64_t));
+    out->sums = (uint64_t*)calloc((n_groups ? n_groups : 1) * (na ? na : 1) * 2, sizeof(uint64_t));
+    out->avgs = (double*)calloc((n_groups ? n_groups : 1) * (na ? na : 1), sizeof(double));
+    if (!out->keys || !out->counts || !out->sums || !out->avgs) {
+        free(kept); orc_free(out);
+        return ORC_NOMEM;
+    }
+    uint64_t g = 0, start = 0;
+    while (start < n_kept) {
+        uint64_t end = start;
+        while (end < n_kept && kept[end].key == kept[start].key) ++end;
+        int64_t count = (int64_t)(end - start);
+        out->keys[g] = (uint64_t)kept[start].key;
+        out->counts[g] = count;
+        for (int a = 0; a < na; ++a) {
+            const orc_agg* ag = &q->aggs[a];
+            u128 s = 0; /* wraps modulo 2^128, like any fixed-width sum */
+            for (uint64_t r = start; r < end; ++r) {
+                uint64_t i = kept[r].row;
+                if (ag->kind == ORC_SUM || ag->kind == ORC_AVG) {
+                    s += (u128)(i128)col_at(&q->fact[ag->col_a], i);
+                } else if (ag->kind == ORC_SUM_MUL_SUB) {
+                    i128 av = col_at(&q->fact[ag->col_a], i);
+                    i128 bv = col_at(&q->fact[ag->col_b], i);
+                    s += (u128)(av * ((i128)ag->k - bv)); /* |product| < 2^127 */
+                } else {
+                    s += 1;
+                }
+            }
+            out->sums[(g * na + a) * 2] = (uint64_t)s;
+            out->sums[(g * na + a) * 2 + 1] = (uint64_t)(s >> 64);
+            if (ag->kind == ORC_AVG)
+                out->avgs[g * na + a] = (double)(i128)s / (double)count;
+        }
+        ++g;
+        start = end;
+    }
+    free(kept);
+    return ORC_OK;
+}
+
+void orc_free(orc_result* r) {
+    free(r->keys);
+    free(r->counts);
+    free(r->sums);
+    free(r->avgs);
+    memset(r, 0, sizeof(*r));
+}

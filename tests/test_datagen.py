@@ -1,0 +1,51 @@
+"""The seeded input generator: determinism, row-indexability, ranges."""
+import numpy as np
+
+import datagen
+from datagen import workloads as W
+
+
+def test_row_ranges_regenerate_independently():
+    full = datagen.uniform(11, 3, np.int64, 10_000, -7, 1_000)
+    part = datagen.uniform(11, 3, np.int64, 1_000, -7, 1_000, row0=4_321)
+    assert np.array_equal(full[4_321:5_321], part)
+    assert full.min() >= -7 and full.max() <= 1_000
+    assert np.array_equal(full, datagen.uniform(11, 3, np.int64, 10_000, -7, 1_000))
+    assert not np.array_equal(full, datagen.uniform(12, 3, np.int64, 10_000, -7, 1_000))
+
+
+def test_permutations_are_bijections():
+    for n in (1, 2, 3, 1000, 4097, 65_536, 1_000_003):
+        p = datagen.fill(5, 9, datagen.PERM, np.int64, n, b=n)
+        assert np.array_equal(np.sort(p), np.arange(n))
+    p = datagen.fill(5, 9, datagen.PERM, np.int64, 1000, b=1000)
+    assert (p != np.arange(1000)).mean() > 0.9
+
+
+def test_raw64_unique_and_zipf_skew():
+    raw = datagen.fill(1, 1, datagen.RAW64, np.int64, 1_000_000)
+    assert np.unique(raw).size == raw.size
+    assert np.array_equal(datagen.raw_at(1, 1, np.array([5, 999_999, 0])), raw[[5, 999_999, 0]])
+    cdf = datagen.zipf_cdf(0.8, 100_000)
+    idx = datagen.index(3, 3, 100_000, 500_000, cdf=cdf)
+    counts = np.bincount(idx, minlength=100_000)
+    top = np.sort(counts)[::-1]
+    assert top[0] / idx.size > 0.01             # hottest rank ~1/H(0.8) of the mass
+    assert top[0] > 20 * np.median(counts)
+
+
+def test_config_shapes():
+    wl = W.config1(n_fact=100_000, n_dim=10_000)
+    f = wl.fact
+    assert f["fk"].dtype == np.int32 and f["qty"].dtype == np.int64 and f["flag"].dtype == np.uint8
+    assert f["qty"].min() >= 100 and f["qty"].max() <= 5000 and (f["qty"] % 100 == 0).all()
+    assert f["price"].min() >= 90_000 and f["price"].max() <= 10_500_000
+    assert f["disc"].min() >= 0 and f["disc"].max() <= 10
+    assert 0.975 < (f["date"] <= W.CUTOFF_98).mean() < 0.985
+    fact, dim = W.config2_tables(n_fact=400_000, n_dim=100_000)
+    assert np.unique(dim["pk"]).size == 100_000
+    assert np.isin(fact["fk"], dim["pk"]).all()
+    assert np.unique(fact["okey"]).size == 100_000
+    sizes = W.config4_sizes()
+    assert sizes["fact"].min() >= 10_000 and sizes["fact"].max() <= 50_000_000
+    assert 1e8 < sizes["fact"].sum() < 1e9
