@@ -1,0 +1,305 @@
+/*
+ * theseus_gb.h -- C ABI of the GB300 relational hot path.
+ *
+ * One GPU, one process.  The library evaluates
+ *
+ *     SELECT g, SUM(..), SUM(a*(K-b)), COUNT(*), AVG(..)
+ *     FROM fact [JOIN dim ON fact.fk = dim.pk]
+ *     WHERE lo <= fact.c <= hi
+ *     GROUP BY g
+ *
+ * over columnar tables (paper, Section 3.1: a batch is a slice of all columns
+ * of a table with the same number of rows).  Decimals are scaled 64-bit
+ * integers; every SUM is an exact 128-bit integer (Section 4 holds
+ * decimal(11,2) values in 128 bits).  AVG is the exact sum, rounded to double,
+ * divided by the count in one IEEE double division.
+ *
+ * Conventions for every call:
+ *   - Returns tp_status: TP_OK (0) or a TP_E_* code.  No C++ exception ever
+ *     crosses this boundary.  After an error, tp_last_error() returns a
+ *     human-readable message for the calling thread.
+ *   - Objects (engine, tables, plans, results) are opaque and owned by the
+ *     library until the matching *_destroy / *_free / tp_shutdown.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     device memory of the engine's GPU.  Caller buffers passed in are only
+ *     read during the call unless stated otherwise.
+ *   - One engine may be used from several host threads; calls on one engine
+ *     serialise internally where they touch shared state.
+ */
+#ifndef THESEUS_GB_H
+#define THESEUS_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+
+typedef int32_t tp_status;
+enum {
+    TP_OK = 0,
+    TP_E_INVALID = 1,     /* bad argument, plan or call order                 */
+    TP_E_POOL_EMPTY = 2,  /* the pinned page pool has no free page            */
+    TP_E_BUDGET = 3,      /* the device-memory reservation does not fit       */
+    TP_E_DUP_KEY = 4,     /* the join's build side holds a key twice          */
+    TP_E_TIMEOUT = 5,     /* a bounded wait expired (host or device side)     */
+    TP_E_CUDA = 6,        /* a CUDA runtime call failed                       */
+    TP_E_INTERNAL = 7,    /* a device-side consistency check failed           */
+    TP_E_RANGE = 8,       /* a group field value does not fit its bit width   */
+    TP_E_NOMEM = 9        /* host allocation failed                           */
+};
+
+/* ----------------------------------------------------------------- engine */
+
+typedef struct tp_engine tp_engine;
+typedef struct tp_table tp_table;
+typedef struct tp_plan tp_plan;
+typedef struct tp_result tp_result;
+
+enum { TP_AGG_AUTO = 0, TP_AGG_SHARED = 1, TP_AGG_GLOBAL = 2 };
+
+/*
+ * Engine configuration.  Start from tp_config_default() and change fields.
+ *
+ *   page_bytes, n_pages   the pinned host page pool, allocated once in
+ *                         tp_init (Section 3.4: a pool of pre-allocated
+ *                         fixed-size page-locked buffers, allocated during
+ *                         engine initialisation).  page_bytes is rounded up
+ *                         to a multiple of 4096.  n_pages may be 0.
+ *   device_budget_bytes   cap on device bytes the engine may reserve
+ *                         (Section 3.3.2: tasks reserve memory before they
+ *                         run).  0 = 90% of the GPU's free memory at init.
+ *   prefetch_depth        batches copied ahead of compute on the copy stream
+ *                         (Section 3.3.3, compute-task pre-loading).  0 =
+ *                         no prefetch: the compute stream copies each batch
+ *                         itself before using it.
+ *   batch_rows            default rows per batch for host-page tables.
+ *   cuda_device           CUDA device ordinal.
+ *   load_factor           target fill of the hash tables, in (0.05, 0.9].
+ *   agg_strategy          TP_AGG_AUTO, TP_AGG_SHARED (per-CTA shared-memory
+ *                         tables, few groups) or TP_AGG_GLOBAL (one device
+ *                         hash table).
+ *   compute_stream        optional cudaStream_t (as void*) on which all
+ *                         compute work is issued; NULL = engine-owned stream.
+ *   flags                 TP_FLAG_TIME_KERNELS: bracket every fused
+ *                         filter/probe/aggregate launch with CUDA events on
+ *                         the compute stream and accumulate its device time
+ *                         in tp_stats (agg_kernel_ms, agg_kernel_launches).
+ */
+enum { TP_FLAG_TIME_KERNELS = 1 };
+typedef struct {
+    uint64_t page_bytes;
+    uint32_t n_pages;
+    uint32_t flags;
+    uint64_t device_budget_bytes;
+    int32_t prefetch_depth;
+    int32_t cuda_device;
+    uint64_t batch_rows;
+    float load_factor;
+    int32_t agg_strategy;
+    void* compute_stream;
+} tp_config;
+
+/* Fills *cfg with defaults: 64 MiB pages, 0 pages, budget 0 (auto),
+ * prefetch_depth 2, batch_rows 4M, device 0, load_factor 0.5, AUTO. */
+void tp_config_default(tp_config* cfg);
+
+/* Creates an engine on cfg->cuda_device: pins the page pool, creates the
+ * copy and compute streams.  *out receives the engine.
+ * Errors: TP_E_INVALID (bad config), TP_E_CUDA, TP_E_NOMEM. */
+tp_status tp_init(const tp_config* cfg, tp_engine** out);
+
+/* Waits for outstanding work, frees every table, plan, result, page and
+ * stream of the engine.  NULL is ignored. */
+void tp_shutdown(tp_engine* eng);
+
+/* ---------------------------------------------------------------- page pool */
+
+/* A page is an index into the engine's pool (Section 3.4). */
+typedef uint32_t tp_page;
+
+/* Takes one free page.  O(1); never allocates.  TP_E_POOL_EMPTY if none. */
+tp_status tp_page_alloc(tp_engine* eng, tp_page* out);
+/* Returns a page to the pool.  TP_E_INVALID if it is not currently lent out. */
+tp_status tp_page_free(tp_engine* eng, tp_page page);
+/* Host address of a page (page-locked, page_bytes long), or NULL. */
+void* tp_page_ptr(tp_engine* eng, tp_page page);
+/* Size of every page in bytes. */
+uint64_t tp_page_bytes(const tp_engine* eng);
+/* Pages currently free in the pool. */
+uint32_t tp_pages_free(const tp_engine* eng);
+
+/* ------------------------------------------------------------------ budget */
+
+/* Changes the device-memory cap; a lower cap applies to later reservations. */
+tp_status tp_set_device_budget(tp_engine* eng, uint64_t bytes);
+/* Bytes currently reserved and the cap. Either pointer may be NULL. */
+tp_status tp_budget_query(tp_engine* eng, uint64_t* reserved, uint64_t* cap);
+
+/* ------------------------------------------------------------------ tables */
+
+enum { TP_I32 = 0, TP_I64 = 1, TP_U8 = 2 };
+enum { TP_HOST_PAGES = 1, TP_DEVICE = 2 };
+
+typedef struct {
+    const char* name;     /* copied; may be NULL */
+    int32_t type;         /* TP_I32, TP_I64 or TP_U8 */
+    int32_t scale;        /* decimal scale (digits after the point); metadata only */
+} tp_column_desc;
+
+typedef struct {
+    int32_t n_cols;                 /* 1..32 */
+    const tp_column_desc* cols;     /* n_cols entries */
+    uint64_t batch_rows;            /* rows per batch; 0 = engine default */
+} tp_table_desc;
+
+/* Creates an empty table whose rows will live in pool pages. */
+tp_status tp_table_create(tp_engine* eng, const tp_table_desc* desc, tp_table** out);
+
+/* Copies nrows rows from host arrays cols[0..n_cols) (one contiguous array
+ * per column, element type as declared) into pool pages.  Rows are cut into
+ * batches of batch_rows; within a batch the columns lie back to back across
+ * as many pages as they need, so one column may span pages, and the tail of
+ * the batch's last page stays unused (Section 3.4).  The caller keeps its
+ * arrays.  Errors: TP_E_POOL_EMPTY (pool exhausted: the append is undone),
+ * TP_E_INVALID (table already on the device). */
+tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows);
+
+/* Moves the table: TP_DEVICE copies every column into one contiguous device
+ * array (reserving its bytes in the budget) and returns the pages;
+ * TP_HOST_PAGES is a no-op for a paged table.  Errors: TP_E_BUDGET,
+ * TP_E_CUDA, TP_E_INVALID. */
+tp_status tp_table_place(tp_table* t, int32_t placement);
+
+/* Registers caller-owned device columns without copying (for example tensors
+ * held by PyTorch).  dev_cols[i] must hold nrows elements, be 16-byte aligned
+ * and outlive the table.  Not counted against the budget. */
+tp_status tp_table_wrap_device(tp_engine* eng, const tp_table_desc* desc,
+                               const void* const* dev_cols, uint64_t nrows, tp_table** out);
+
+uint64_t tp_table_rows(const tp_table* t);
+/* Number of batches (paged tables) or 1 (device tables). */
+uint64_t tp_table_batches(const tp_table* t);
+/* Frees the table's pages or device memory (not wrapped caller memory). */
+void tp_table_destroy(tp_table* t);
+
+/* ------------------------------------------------------------------- plans */
+
+enum { TP_SIDE_FACT = 0, TP_SIDE_DIM = 1 };
+enum { TP_AGG_SUM = 0, TP_AGG_SUM_MUL_SUB = 1, TP_AGG_COUNT = 2, TP_AGG_AVG = 3 };
+
+typedef struct {
+    int32_t col;          /* fact column, -1 = no filter */
+    int64_t lo, hi;       /* keep rows with lo <= value <= hi (inclusive) */
+} tp_filter;
+
+typedef struct {
+    int32_t fact_col;     /* fact foreign-key column, -1 = no join */
+    int32_t dim_col;      /* dimension key column; keys must be unique */
+} tp_join;
+
+typedef struct {
+    int32_t side;         /* TP_SIDE_FACT or TP_SIDE_DIM */
+    int32_t col;
+    int32_t bits;         /* 1..64; the value must lie in [0, 2^bits) unless bits == 64 */
+} tp_group_field;
+
+typedef struct {
+    int32_t kind;         /* TP_AGG_* */
+    int32_t col_a;        /* fact column summed (SUM, AVG) or factor a (SUM_MUL_SUB) */
+    int32_t col_b;        /* fact column b of SUM_MUL_SUB */
+    int64_t k;            /* constant K of SUM_MUL_SUB: SUM(a * (K - b)) */
+} tp_agg;
+
+/*
+ * A query over one fact table and an optional dimension table.  The group key
+ * packs the fields first-field-highest into at most 64 bits; dimension-side
+ * fields may use at most 32 bits in total.  Aggregates read fact columns.
+ */
+typedef struct {
+    tp_table* fact;
+    tp_table* dim;                  /* NULL when join.fact_col < 0 */
+    tp_filter filter;
+    tp_join join;
+    int32_t n_group;                /* 0..4 (0: one group, key 0) */
+    tp_group_field group[4];
+    int32_t n_agg;                  /* 1..8 */
+    tp_agg aggs[8];
+    int32_t agg_strategy;           /* TP_AGG_*; AUTO = engine choice */
+    float load_factor;              /* 0 = engine default */
+    uint64_t expected_groups;       /* sizing hint for TP_AGG_GLOBAL; 0 = estimate */
+} tp_plan_desc;
+
+/* Validates and stores a plan.  TP_E_INVALID on any inconsistency. */
+tp_status tp_plan_create(tp_engine* eng, const tp_plan_desc* desc, tp_plan** out);
+void tp_plan_destroy(tp_plan* p);
+
+/* ----------------------------------------------------------------- execute */
+
+/*
+ * Runs the plan and waits for it:
+ *   1. reserve device memory for hash tables, accumulators and staging
+ *      (TP_E_BUDGET if the estimate exceeds the cap);
+ *   2. build the dimension hash table (TP_E_DUP_KEY on a repeated key);
+ *   3. for each fact batch: filter, probe and aggregate in one kernel; a
+ *      paged fact table streams through device staging slots, copied ahead on
+ *      the copy stream while the previous batch computes;
+ *   4. merge, compute AVG, compact and sort the groups by key.
+ * *out receives a result that stays on the device until read.
+ */
+tp_status tp_execute(tp_plan* p, tp_result** out);
+
+/* ----------------------------------------------------------------- results */
+
+typedef struct {
+    uint64_t lo;          /* low 64 bits */
+    int64_t hi;           /* high 64 bits (two's complement) */
+} tp_i128;
+
+uint64_t tp_result_groups(const tp_result* r);
+/* Host arrays of tp_result_groups() entries, ascending by key; copied from
+ * the device on first use and owned by the result.  NULL on error or when
+ * the aggregate has no such output. */
+const uint64_t* tp_result_keys(tp_result* r);
+const int64_t* tp_result_count(tp_result* r);
+/* Exact sum of aggregate `agg` (SUM, SUM_MUL_SUB or AVG). */
+const tp_i128* tp_result_sum(tp_result* r, int32_t agg);
+/* AVG of aggregate `agg` (AVG only). */
+const double* tp_result_avg(tp_result* r, int32_t agg);
+/* Device addresses of the same arrays (no copy); NULL where absent. */
+const void* tp_result_device_keys(const tp_result* r);
+const void* tp_result_device_count(const tp_result* r);
+const void* tp_result_device_sum(const tp_result* r, int32_t agg);
+const void* tp_result_device_avg(const tp_result* r, int32_t agg);
+void tp_result_free(tp_result* r);
+
+/* ------------------------------------------------------------- diagnostics */
+
+typedef struct {
+    uint64_t h2d_bytes;          /* bytes copied host -> device */
+    uint64_t d2h_bytes;          /* bytes copied device -> host */
+    uint64_t batches;            /* fact batches processed */
+    uint64_t kernel_launches;    /* kernels launched by the library */
+    uint64_t peak_reserved;      /* highest reservation seen */
+    uint64_t retries;            /* executions repeated with a larger table */
+    uint32_t pages_in_use;
+    uint32_t pages_total;
+    double agg_kernel_ms;        /* device time of fused aggregate kernels (TP_FLAG_TIME_KERNELS) */
+    uint64_t agg_kernel_launches;
+    uint64_t agg_kernel_rows;    /* fact rows those launches processed */
+} tp_stats;
+
+/* Message for the last error on this thread ("" if none). */
+const char* tp_last_error(void);
+tp_status tp_stats_get(tp_engine* eng, tp_stats* out);
+/* Fault injection for tests: the next n host page allocations and device
+ * reservations fail as if exhausted. */
+tp_status tp_debug_fail_next_alloc(tp_engine* eng, int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,444 @@
+// Engine lifetime, pinned page pool, device-memory budget and table
+// registration behind the C ABI.
+//
+// Paper basis: Section 3.4 (a pool of fixed-size page-locked buffers
+// allocated at engine initialisation; columns laid across buffers so one
+// column may span several; a small unused tail per batch), Section 3.3.2
+// (tasks reserve memory before executing), Section 3.1 (batches are row
+// slices of all columns).
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+
+#include "tp_internal.h"
+
+namespace tp {
+
+static thread_local char g_err[512] = "";
+
+tp_status fail(tp_status code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int type_size(int32_t type) {
+    switch (type) {
+    case TP_I32: return 4;
+    case TP_I64: return 8;
+    case TP_U8: return 1;
+    default: return 0;
+    }
+}
+
+tp_status reserve(tp_engine* e, uint64_t bytes) {
+    std::lock_guard<std::mutex> lk(e->budget.mu);
+    if (e->budget.fail_next > 0) {
+        --e->budget.fail_next;
+        return fail(TP_E_BUDGET, "device reservation of %llu bytes refused (injected)",
+                    (unsigned long long)bytes);
+    }
+    if (e->budget.reserved + bytes > e->budget.cap)
+        return fail(TP_E_BUDGET, "device reservation of %llu bytes exceeds budget (%llu of %llu reserved)",
+                    (unsigned long long)bytes, (unsigned long long)e->budget.reserved,
+                    (unsigned long long)e->budget.cap);
+    e->budget.reserved += bytes;
+    if (e->budget.reserved > e->budget.peak) e->budget.peak = e->budget.reserved;
+    return TP_OK;
+}
+
+void release(tp_engine* e, uint64_t bytes) {
+    {
+        std::lock_guard<std::mutex> lk(e->budget.mu);
+        e->budget.reserved = bytes > e->budget.reserved ? 0 : e->budget.reserved - bytes;
+    }
+    e->budget.cv.notify_all();
+}
+
+tp_status dev_alloc(tp_engine* e, void** p, uint64_t bytes, cudaStream_t st) {
+    (void)e;
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    cudaError_t err = cudaMallocAsync(p, bytes, st);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(TP_E_CUDA, "device allocation of %llu bytes failed: %s", (unsigned long long)bytes,
+                    cudaGetErrorString(err));
+    }
+    return TP_OK;
+}
+
+void dev_free(tp_engine* e, void* p, cudaStream_t st) {
+    (void)e;
+    if (p) cudaFreeAsync(p, st);
+}
+
+}  // namespace tp
+
+using namespace tp;
+
+extern "C" {
+
+const char* tp_last_error(void) { return tp::g_err; }
+
+void tp_config_default(tp_config* c) {
+    if (!c) return;
+    memset(c, 0, sizeof(*c));
+    c->page_bytes = 64ull << 20;
+    c->n_pages = 0;
+    c->device_budget_bytes = 0;
+    c->prefetch_depth = 2;
+    c->cuda_device = 0;
+    c->batch_rows = 4ull << 20;
+    c->load_factor = 0.5f;
+    c->agg_strategy = TP_AGG_AUTO;
+    c->compute_stream = nullptr;
+}
+
+tp_status tp_init(const tp_config* cfg, tp_engine** out) {
+    clear_error();
+    if (!cfg || !out) return fail(TP_E_INVALID, "tp_init: NULL argument");
+    *out = nullptr;
+    if (cfg->page_bytes == 0 || cfg->batch_rows == 0 || cfg->prefetch_depth < 0 ||
+        cfg->prefetch_depth > 64 || !(cfg->load_factor > 0.05f && cfg->load_factor <= 0.9f) ||
+        cfg->agg_strategy < TP_AGG_AUTO || cfg->agg_strategy > TP_AGG_GLOBAL)
+        return fail(TP_E_INVALID, "tp_init: invalid configuration");
+    std::unique_ptr<tp_engine> e(new (std::nothrow) tp_engine());
+    if (!e) return fail(TP_E_NOMEM, "tp_init: out of host memory");
+    e->cfg = *cfg;
+    e->cfg.page_bytes = (cfg->page_bytes + 4095) & ~4095ull;
+    e->device = cfg->cuda_device;
+    TP_TRY_CUDA(cudaSetDevice(e->device));
+    TP_TRY_CUDA(cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device));
+    size_t free_b = 0, total_b = 0;
+    TP_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    e->budget.cap = cfg->device_budget_bytes ? cfg->device_budget_bytes : (uint64_t)(free_b * 0.9);
+    // keep freed stream-ordered allocations cached in the device pool
+    cudaMemPool_t pool;
+    TP_TRY_CUDA(cudaDeviceGetDefaultMemPool(&pool, e->device));
+    uint64_t threshold = ~0ull;
+    TP_TRY_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold));
+    TP_TRY_CUDA(cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking));
+    if (cfg->compute_stream) {
+        e->compute = (cudaStream_t)cfg->compute_stream;
+    } else {
+        TP_TRY_CUDA(cudaStreamCreateWithFlags(&e->compute, cudaStreamNonBlocking));
+        e->own_compute = true;
+    }
+    TP_TRY_CUDA(cudaHostAlloc((void**)&e->host_words, 4096, cudaHostAllocDefault));
+    // the page pool: one page-locked allocation cut into equal pages
+    PagePool& pp = e->pool;
+    pp.page_bytes = e->cfg.page_bytes;
+    pp.n_pages = cfg->n_pages;
+    if (pp.n_pages) {
+        cudaError_t err = cudaHostAlloc((void**)&pp.base, pp.page_bytes * pp.n_pages, cudaHostAllocDefault);
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(e->host_words);
+            cudaStreamDestroy(e->copy);
+            if (e->own_compute) cudaStreamDestroy(e->compute);
+            return fail(TP_E_NOMEM, "page pool of %u x %llu bytes could not be pinned: %s", pp.n_pages,
+                        (unsigned long long)pp.page_bytes, cudaGetErrorString(err));
+        }
+        pp.free_stack.resize(pp.n_pages);
+        for (uint32_t i = 0; i < pp.n_pages; ++i) pp.free_stack[i] = pp.n_pages - 1 - i;
+        pp.lent.assign(pp.n_pages, 0);
+    }
+    *out = e.release();
+    return TP_OK;
+}
+
+void tp_shutdown(tp_engine* e) {
+    if (!e) return;
+    cudaSetDevice(e->device);
+    cudaStreamSynchronize(e->compute);
+    cudaStreamSynchronize(e->copy);
+    if (e->pool.base) cudaFreeHost(e->pool.base);
+    if (e->host_words) cudaFreeHost(e->host_words);
+    cudaStreamDestroy(e->copy);
+    if (e->own_compute) cudaStreamDestroy(e->compute);
+    delete e;
+}
+
+// ---------------------------------------------------------------- page pool
+
+tp_status tp_page_alloc(tp_engine* e, tp_page* out) {
+    if (!e || !out) return fail(TP_E_INVALID, "tp_page_alloc: NULL argument");
+    std::lock_guard<std::mutex> lk(e->pool.mu);
+    if (e->pool.fail_next > 0) {
+        --e->pool.fail_next;
+        return fail(TP_E_POOL_EMPTY, "page pool exhausted (injected)");
+    }
+    if (e->pool.free_stack.empty()) return fail(TP_E_POOL_EMPTY, "page pool exhausted (%u pages)", e->pool.n_pages);
+    *out = e->pool.free_stack.back();
+    e->pool.free_stack.pop_back();
+    e->pool.lent[*out] = 1;
+    return TP_OK;
+}
+
+tp_status tp_page_free(tp_engine* e, tp_page p) {
+    if (!e) return fail(TP_E_INVALID, "tp_page_free: NULL engine");
+    std::lock_guard<std::mutex> lk(e->pool.mu);
+    if (p >= e->pool.n_pages || !e->pool.lent[p]) return fail(TP_E_INVALID, "tp_page_free: page %u not lent", p);
+    e->pool.lent[p] = 0;
+    e->pool.free_stack.push_back(p);
+    return TP_OK;
+}
+
+void* tp_page_ptr(tp_engine* e, tp_page p) {
+    if (!e || p >= e->pool.n_pages) return nullptr;
+    return e->pool.base + (uint64_t)p * e->pool.page_bytes;
+}
+
+uint64_t tp_page_bytes(const tp_engine* e) { return e ? e->pool.page_bytes : 0; }
+
+uint32_t tp_pages_free(const tp_engine* e) {
+    if (!e) return 0;
+    std::lock_guard<std::mutex> lk(const_cast<tp_engine*>(e)->pool.mu);
+    return (uint32_t)e->pool.free_stack.size();
+}
+
+// ------------------------------------------------------------------- budget
+
+tp_status tp_set_device_budget(tp_engine* e, uint64_t bytes) {
+    if (!e) return fail(TP_E_INVALID, "tp_set_device_budget: NULL engine");
+    {
+        std::lock_guard<std::mutex> lk(e->budget.mu);
+        e->budget.cap = bytes;
+    }
+    e->budget.cv.notify_all();
+    return TP_OK;
+}
+
+tp_status tp_budget_query(tp_engine* e, uint64_t* reserved, uint64_t* cap) {
+    if (!e) return fail(TP_E_INVALID, "tp_budget_query: NULL engine");
+    std::lock_guard<std::mutex> lk(e->budget.mu);
+    if (reserved) *reserved = e->budget.reserved;
+    if (cap) *cap = e->budget.cap;
+    return TP_OK;
+}
+
+// ------------------------------------------------------------------- tables
+
+static tp_status check_desc(const tp_table_desc* d) {
+    if (!d || d->n_cols < 1 || d->n_cols > 32 || !d->cols) return fail(TP_E_INVALID, "table: bad descriptor");
+    for (int i = 0; i < d->n_cols; ++i)
+        if (type_size(d->cols[i].type) == 0) return fail(TP_E_INVALID, "table: column %d has a bad type", i);
+    return TP_OK;
+}
+
+static tp_table* new_table(tp_engine* e, const tp_table_desc* d) {
+    tp_table* t = new (std::nothrow) tp_table();
+    if (!t) return nullptr;
+    t->eng = e;
+    t->batch_rows = d->batch_rows ? d->batch_rows : e->cfg.batch_rows;
+    for (int i = 0; i < d->n_cols; ++i) {
+        t->types.push_back(d->cols[i].type);
+        t->scales.push_back(d->cols[i].scale);
+        t->names.push_back(d->cols[i].name ? d->cols[i].name : "");
+    }
+    return t;
+}
+
+tp_status tp_table_create(tp_engine* e, const tp_table_desc* d, tp_table** out) {
+    clear_error();
+    if (!e || !out) return fail(TP_E_INVALID, "tp_table_create: NULL argument");
+    tp_status s = check_desc(d);
+    if (s) return s;
+    *out = new_table(e, d);
+    return *out ? TP_OK : fail(TP_E_NOMEM, "tp_table_create: out of host memory");
+}
+
+static void free_batch_pages(tp_engine* e, Batch& b) {
+    for (uint32_t p : b.pages) tp_page_free(e, p);
+    b.pages.clear();
+}
+
+tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) {
+    clear_error();
+    if (!t || (!cols && nrows)) return fail(TP_E_INVALID, "tp_table_append: NULL argument");
+    if (t->placement != PL_PAGES) return fail(TP_E_INVALID, "tp_table_append: table is not in host pages");
+    tp_engine* e = t->eng;
+    const uint64_t pb = e->pool.page_bytes;
+    const size_t first_new = t->batches.size();
+    const int nc = (int)t->types.size();
+    for (uint64_t r0 = 0; r0 < nrows; r0 += t->batch_rows) {
+        const uint64_t rows = std::min<uint64_t>(t->batch_rows, nrows - r0);
+        // columns back to back, each starting on a 256-byte boundary
+        std::vector<uint64_t> off(nc);
+        uint64_t total = 0;
+        for (int c = 0; c < nc; ++c) {
+            total = (total + 255) & ~255ull;
+            off[c] = total;
+            total += rows * type_size(t->types[c]);
+        }
+        const uint64_t n_pages = (total + pb - 1) / pb;
+        Batch b;
+        b.row0 = t->rows + r0;
+        b.rows = rows;
+        for (uint64_t i = 0; i < n_pages; ++i) {
+            tp_page p;
+            tp_status s = tp_page_alloc(e, &p);
+            if (s) {
+                free_batch_pages(e, b);
+                for (size_t k = first_new; k < t->batches.size(); ++k) free_batch_pages(e, t->batches[k]);
+                t->batches.resize(first_new);
+                return s;
+            }
+            b.pages.push_back(p);
+        }
+        b.cols.resize(nc);
+        for (int c = 0; c < nc; ++c) {
+            const int sz = type_size(t->types[c]);
+            const uint8_t* src = (const uint8_t*)cols[c] + r0 * sz;
+            uint64_t pos = off[c], left = rows * sz;
+            while (left) {
+                const uint64_t pi = pos / pb, po = pos % pb;
+                const uint64_t take = std::min<uint64_t>(left, pb - po);
+                memcpy((uint8_t*)tp_page_ptr(e, b.pages[pi]) + po, src, take);
+                b.cols[c].push_back(Extent{b.pages[pi], 0, po, take});
+                src += take;
+                pos += take;
+                left -= take;
+            }
+        }
+        t->batches.push_back(std::move(b));
+    }
+    t->rows += nrows;
+    return TP_OK;
+}
+
+tp_status tp_table_place(tp_table* t, int32_t placement) {
+    clear_error();
+    if (!t) return fail(TP_E_INVALID, "tp_table_place: NULL table");
+    if (placement == TP_HOST_PAGES) {
+        return t->placement == PL_PAGES ? TP_OK
+                                        : fail(TP_E_INVALID, "tp_table_place: device tables stay on the device");
+    }
+    if (placement != TP_DEVICE) return fail(TP_E_INVALID, "tp_table_place: bad placement");
+    if (t->placement != PL_PAGES) return TP_OK;
+    tp_engine* e = t->eng;
+    std::lock_guard<std::mutex> lk(e->exec_mu);
+    const int nc = (int)t->types.size();
+    uint64_t bytes = 0;
+    for (int c = 0; c < nc; ++c) bytes += ((t->rows * type_size(t->types[c]) + 255) & ~255ull);
+    tp_status s = reserve(e, bytes);
+    if (s) return s;
+    std::vector<void*> cols(nc, nullptr);
+    for (int c = 0; c < nc; ++c) {
+        s = dev_alloc(e, &cols[c], t->rows * type_size(t->types[c]), e->compute);
+        if (s) {
+            for (void* p : cols) dev_free(e, p, e->compute);
+            release(e, bytes);
+            return s;
+        }
+    }
+    cudaStreamSynchronize(e->compute);
+    for (auto& b : t->batches) {
+        for (int c = 0; c < nc; ++c) {
+            uint8_t* dst = (uint8_t*)cols[c] + b.row0 * type_size(t->types[c]);
+            for (const Extent& x : b.cols[c]) {
+                cudaError_t err = cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes,
+                                                  cudaMemcpyHostToDevice, e->copy);
+                if (err != cudaSuccess) {
+                    cudaStreamSynchronize(e->copy);
+                    for (void* p : cols) dev_free(e, p, e->compute);
+                    release(e, bytes);
+                    return fail(TP_E_CUDA, "tp_table_place: copy failed: %s", cudaGetErrorString(err));
+                }
+                dst += x.bytes;
+                e->h2d_bytes += x.bytes;
+            }
+        }
+    }
+    TP_TRY_CUDA(cudaStreamSynchronize(e->copy));
+    for (auto& b : t->batches) free_batch_pages(e, b);
+    t->batches.clear();
+    t->dev_cols = cols;
+    t->dev_reserved = bytes;
+    t->placement = PL_DEVICE;
+    return TP_OK;
+}
+
+tp_status tp_table_wrap_device(tp_engine* e, const tp_table_desc* d, const void* const* dev_cols,
+                               uint64_t nrows, tp_table** out) {
+    clear_error();
+    if (!e || !out || !dev_cols) return fail(TP_E_INVALID, "tp_table_wrap_device: NULL argument");
+    tp_status s = check_desc(d);
+    if (s) return s;
+    for (int c = 0; c < d->n_cols; ++c)
+        if (nrows && (!dev_cols[c] || ((uintptr_t)dev_cols[c] & 15u)))
+            return fail(TP_E_INVALID, "tp_table_wrap_device: column %d is NULL or not 16-byte aligned", c);
+    tp_table* t = new_table(e, d);
+    if (!t) return fail(TP_E_NOMEM, "tp_table_wrap_device: out of host memory");
+    t->rows = nrows;
+    t->placement = PL_WRAPPED;
+    for (int c = 0; c < d->n_cols; ++c) t->dev_cols.push_back(const_cast<void*>(dev_cols[c]));
+    *out = t;
+    return TP_OK;
+}
+
+uint64_t tp_table_rows(const tp_table* t) { return t ? t->rows : 0; }
+
+uint64_t tp_table_batches(const tp_table* t) {
+    if (!t) return 0;
+    return t->placement == PL_PAGES ? t->batches.size() : 1;
+}
+
+void tp_table_destroy(tp_table* t) {
+    if (!t) return;
+    tp_engine* e = t->eng;
+    if (t->placement == PL_PAGES) {
+        for (auto& b : t->batches) free_batch_pages(e, b);
+    } else if (t->placement == PL_DEVICE) {
+        cudaSetDevice(e->device);
+        cudaStreamSynchronize(e->compute);
+        for (void* p : t->dev_cols) dev_free(e, p, e->compute);
+        release(e, t->dev_reserved);
+    }
+    delete t;
+}
+
+// -------------------------------------------------------------- diagnostics
+
+tp_status tp_stats_get(tp_engine* e, tp_stats* s) {
+    if (!e || !s) return fail(TP_E_INVALID, "tp_stats_get: NULL argument");
+    memset(s, 0, sizeof(*s));
+    s->h2d_bytes = e->h2d_bytes;
+    s->d2h_bytes = e->d2h_bytes;
+    s->batches = e->batches;
+    s->kernel_launches = e->launches;
+    s->retries = e->retries;
+    {
+        std::lock_guard<std::mutex> lk(e->time_mu);
+        s->agg_kernel_ms = e->agg_ms;
+        s->agg_kernel_launches = e->agg_launches;
+        s->agg_kernel_rows = e->agg_rows;
+    }
+    {
+        std::lock_guard<std::mutex> lk(e->budget.mu);
+        s->peak_reserved = e->budget.peak;
+    }
+    std::lock_guard<std::mutex> lk(e->pool.mu);
+    s->pages_total = e->pool.n_pages;
+    s->pages_in_use = e->pool.n_pages - (uint32_t)e->pool.free_stack.size();
+    return TP_OK;
+}
+
+tp_status tp_debug_fail_next_alloc(tp_engine* e, int32_t n) {
+    if (!e || n < 0) return fail(TP_E_INVALID, "tp_debug_fail_next_alloc: bad argument");
+    {
+        std::lock_guard<std::mutex> lk(e->pool.mu);
+        e->pool.fail_next = n;
+    }
+    std::lock_guard<std::mutex> lk(e->budget.mu);
+    e->budget.fail_next = n;
+    return TP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,779 @@
+// Plans, execution and results behind the C ABI.
+//
+// One execution (Section 3.3.1: a compute task reserves memory, loads its
+// input batches into GPU memory, then computes):
+//   reserve -> build the join table -> per fact batch: [copy stream: H2D of
+//   the batch's pages into a free staging slot] -> [compute stream: fused
+//   filter/probe/aggregate] -> finalise -> release.
+// Batches of a paged fact table are copied ahead of the kernel that consumes
+// them (Section 3.3.3, compute-task pre-loading); with prefetch_depth 0 the
+// compute stream copies each batch itself.
+#include <algorithm>
+#include <cmath>
+
+#include "tp_internal.h"
+
+using namespace tp;
+
+namespace {
+
+uint64_t pow2_at_least(uint64_t x) {
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+bool valid_col(const tp_table* t, int32_t c) { return t && c >= 0 && c < (int32_t)t->types.size(); }
+
+// Value of one column at one row of a paged table (host read of the pages).
+int64_t paged_value(const tp_table* t, int c, uint64_t row) {
+    auto it = std::upper_bound(t->batches.begin(), t->batches.end(), row,
+                               [](uint64_t r, const Batch& b) { return r < b.row0; });
+    const Batch& b = *(it - 1);
+    const int sz = type_size(t->types[c]);
+    uint64_t off = (row - b.row0) * sz;
+    for (const Extent& x : b.cols[c]) {
+        if (off < x.bytes) {
+            const uint8_t* p = (const uint8_t*)tp_page_ptr(t->eng, x.page) + x.offset + off;
+            switch (t->types[c]) {
+            case TP_I32: { int32_t v; memcpy(&v, p, 4); return v; }
+            case TP_I64: { int64_t v; memcpy(&v, p, 8); return v; }
+            default: return *p;
+            }
+        }
+        off -= x.bytes;
+    }
+    return 0;
+}
+
+// Device memory of one execution, released together at the end.
+struct Scratch {
+    tp_engine* e;
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    uint64_t reserved = 0;
+    explicit Scratch(tp_engine* eng, cudaStream_t s) : e(eng), st(s) {}
+    tp_status alloc(void** p, uint64_t bytes) {
+        tp_status s = dev_alloc(e, p, bytes, st);
+        if (s == TP_OK) ptrs.push_back(*p);
+        return s;
+    }
+    void free_all() {
+        for (void* p : ptrs) dev_free(e, p, st);
+        ptrs.clear();
+        if (reserved) release(e, reserved);
+        reserved = 0;
+    }
+    ~Scratch() { free_all(); }
+};
+
+struct ExecState {
+    tp_plan* p;
+    tp_engine* e;
+    tp_table* fact;
+    tp_table* dim;
+    std::vector<int> used;          // fact columns the query reads
+    bool key64 = false;
+    uint64_t join_cap = 0;
+    tpk::JoinTable jt{};
+    uint32_t* err = nullptr;        // device error word
+    unsigned long long* counters = nullptr;   // [0] agg used, [1] compact count, [2] max key, [3] sample
+    bool eager = true;
+};
+
+void mark_launch(tp_engine* e) { e->launches++; }
+
+// Brackets fused-kernel launches with events on the compute stream when the
+// engine was created with TP_FLAG_TIME_KERNELS; totals are folded into the
+// engine statistics once the execution has synchronised.
+struct KernelTimer {
+    tp_engine* e;
+    bool on;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    uint64_t rows = 0;
+    explicit KernelTimer(tp_engine* eng) : e(eng), on((eng->cfg.flags & TP_FLAG_TIME_KERNELS) != 0) {}
+    template <class F>
+    cudaError_t run(cudaStream_t st, uint64_t n, F&& launch) {
+        if (!on) return launch();
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
+        cudaError_t r = launch();
+        cudaEventRecord(b, st);
+        ev.emplace_back(a, b);
+        rows += n;
+        return r;
+    }
+    void collect() {  // after a stream synchronisation
+        if (!on) return;
+        double ms = 0;
+        for (auto& p : ev) {
+            float t = 0;
+            if (cudaEventElapsedTime(&t, p.first, p.second) == cudaSuccess) ms += t;
+            cudaEventDestroy(p.first);
+            cudaEventDestroy(p.second);
+        }
+        std::lock_guard<std::mutex> lk(e->time_mu);
+        e->agg_ms += ms;
+        e->agg_launches += ev.size();
+        e->agg_rows += rows;
+        ev.clear();
+        rows = 0;
+    }
+    ~KernelTimer() {
+        for (auto& p : ev) {
+            cudaEventDestroy(p.first);
+            cudaEventDestroy(p.second);
+        }
+    }
+};
+
+tpk::DevCol devcol(const tp_table* t, int c, const void* ptr) {
+    tpk::DevCol d{};
+    d.ptr = ptr;
+    d.type = t->types[c];
+    return d;
+}
+
+// QueryDev for one batch: colptr[c] is the device address of fact column c's
+// first row in this batch (nullptr for columns the query does not read).
+tpk::QueryDev make_query(const ExecState& S, const std::vector<const void*>& colptr) {
+    const tp_plan_desc& d = S.p->d;
+    tpk::QueryDev q{};
+    q.has_filter = d.filter.col >= 0;
+    if (q.has_filter) {
+        q.fcol = devcol(S.fact, d.filter.col, colptr[d.filter.col]);
+        q.flo = d.filter.lo;
+        q.fhi = d.filter.hi;
+    }
+    q.has_join = d.join.fact_col >= 0;
+    if (q.has_join) {
+        q.fk = devcol(S.fact, d.join.fact_col, colptr[d.join.fact_col]);
+        q.jt = S.jt;
+    }
+    q.n_group = d.n_group;
+    for (int g = 0; g < d.n_group; ++g) {
+        q.gside[g] = d.group[g].side;
+        q.gbits[g] = d.group[g].bits;
+        q.gdpos[g] = S.p->gdpos[g];
+        if (d.group[g].side == TP_SIDE_FACT) q.gcol[g] = devcol(S.fact, d.group[g].col, colptr[d.group[g].col]);
+    }
+    q.n_sum = S.p->n_sum;
+    for (int a = 0; a < d.n_agg; ++a) {
+        const int s = S.p->sum_of_agg[a];
+        if (s < 0) continue;
+        const tp_agg& ag = d.aggs[a];
+        q.sa[s] = devcol(S.fact, ag.col_a, colptr[ag.col_a]);
+        if (ag.kind == TP_AGG_SUM_MUL_SUB) {
+            q.skind[s] = tpk::S_MUL_SUB;
+            q.sb[s] = devcol(S.fact, ag.col_b, colptr[ag.col_b]);
+            q.sk[s] = ag.k;
+        } else {
+            q.skind[s] = tpk::S_SUM;
+        }
+    }
+    q.eager = S.eager ? 1 : 0;
+    q.err = S.err;
+    return q;
+}
+
+tp_status cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return TP_OK;
+    cudaGetLastError();
+    return fail(TP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ----------------------------------------------------------------- build
+
+tp_status build_join(ExecState& S, Scratch& sc) {
+    tp_engine* e = S.e;
+    const tp_plan_desc& d = S.p->d;
+    cudaStream_t st = e->compute;
+    tpk::BuildDev b{};
+    b.jt = S.jt;
+    b.err = S.err;
+    int nf = 0;
+    std::vector<int> bcols = {d.join.dim_col};
+    for (int g = 0; g < d.n_group; ++g) {
+        if (d.group[g].side != TP_SIDE_DIM) continue;
+        b.dbits[nf] = d.group[g].bits;
+        b.dpos[nf] = S.p->gdpos[g];
+        bcols.push_back(d.group[g].col);
+        ++nf;
+    }
+    b.n_dfield = nf;
+    tp_table* t = S.dim;
+    if (t->placement != PL_PAGES) {
+        b.key = devcol(t, d.join.dim_col, t->dev_cols[d.join.dim_col]);
+        int k = 0;
+        for (int g = 0; g < d.n_group; ++g)
+            if (d.group[g].side == TP_SIDE_DIM) { b.dcol[k] = devcol(t, d.group[g].col, t->dev_cols[d.group[g].col]); ++k; }
+        tp_status s = cuda_check(tpk::launch_build(b, t->rows, e->num_sms, st), "build");
+        mark_launch(e);
+        return s;
+    }
+    // paged dimension: copy each batch's key and field columns, then insert
+    uint64_t max_rows = 0;
+    for (auto& bt : t->batches) max_rows = std::max(max_rows, bt.rows);
+    std::vector<void*> stage(bcols.size(), nullptr);
+    for (size_t i = 0; i < bcols.size(); ++i) {
+        tp_status s = sc.alloc(&stage[i], align256(max_rows * type_size(t->types[bcols[i]])));
+        if (s) return s;
+    }
+    for (auto& bt : t->batches) {
+        for (size_t i = 0; i < bcols.size(); ++i) {
+            uint8_t* dst = (uint8_t*)stage[i];
+            for (const Extent& x : bt.cols[bcols[i]]) {
+                tp_status s = cuda_check(cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes,
+                                                         cudaMemcpyHostToDevice, st), "dim copy");
+                if (s) return s;
+                dst += x.bytes;
+                e->h2d_bytes += x.bytes;
+            }
+        }
+        b.key = devcol(t, bcols[0], stage[0]);
+        for (int k = 0; k < nf; ++k) b.dcol[k] = devcol(t, bcols[1 + k], stage[1 + k]);
+        tp_status s = cuda_check(tpk::launch_build(b, bt.rows, e->num_sms, st), "build");
+        mark_launch(e);
+        if (s) return s;
+    }
+    return TP_OK;
+}
+
+// ------------------------------------------------------- fact batch driver
+
+// Runs `kernel(q, rows)` over every batch of the fact table.
+template <class F>
+tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
+    tp_engine* e = S.e;
+    tp_table* t = S.fact;
+    const int nc = (int)t->types.size();
+    std::vector<const void*> colptr(nc, nullptr);
+    if (t->placement != PL_PAGES) {
+        for (int c : S.used) colptr[c] = t->dev_cols[c];
+        if (t->rows == 0) return TP_OK;
+        tpk::QueryDev q = make_query(S, colptr);
+        e->batches++;
+        return kernel(q, t->rows);
+    }
+    if (t->batches.empty()) return TP_OK;
+    uint64_t max_rows = 0;
+    for (auto& b : t->batches) max_rows = std::max(max_rows, b.rows);
+    const bool prefetch = e->cfg.prefetch_depth > 0;
+    const int n_slots = prefetch ? e->cfg.prefetch_depth + 1 : 1;
+    // staging slots: every used column of one batch
+    std::vector<std::vector<void*>> slot(n_slots, std::vector<void*>(nc, nullptr));
+    for (int s = 0; s < n_slots; ++s)
+        for (int c : S.used) {
+            tp_status st = sc.alloc(&slot[s][c], align256(max_rows * type_size(t->types[c])));
+            if (st) return st;
+        }
+    std::vector<cudaEvent_t> loaded(n_slots), freed(n_slots);
+    for (int s = 0; s < n_slots; ++s) {
+        cudaEventCreateWithFlags(&loaded[s], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&freed[s], cudaEventDisableTiming);
+    }
+    tp_status rc = TP_OK;
+    if (prefetch) {  // the copy stream may touch the slots only after they exist
+        cudaEventRecord(freed[0], e->compute);
+        cudaStreamWaitEvent(e->copy, freed[0], 0);
+    }
+    cudaStream_t cs = prefetch ? e->copy : e->compute;
+    for (size_t bi = 0; bi < t->batches.size() && rc == TP_OK; ++bi) {
+        const Batch& b = t->batches[bi];
+        const int s = (int)(bi % n_slots);
+        if (prefetch && bi >= (size_t)n_slots) cudaStreamWaitEvent(e->copy, freed[s], 0);
+        for (int c : S.used) {
+            uint8_t* dst = (uint8_t*)slot[s][c];
+            for (const Extent& x : b.cols[c]) {
+                rc = cuda_check(cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes,
+                                                cudaMemcpyHostToDevice, cs), "batch copy");
+                if (rc) break;
+                dst += x.bytes;
+                e->h2d_bytes += x.bytes;
+            }
+            if (rc) break;
+            colptr[c] = slot[s][c];
+        }
+        if (rc) break;
+        if (prefetch) {
+            cudaEventRecord(loaded[s], e->copy);
+            cudaStreamWaitEvent(e->compute, loaded[s], 0);
+        }
+        tpk::QueryDev q = make_query(S, colptr);
+        rc = kernel(q, b.rows);
+        e->batches++;
+        if (prefetch) cudaEventRecord(freed[s], e->compute);
+    }
+    if (prefetch) {  // the slots are freed on the compute stream after the last copy
+        cudaEventRecord(loaded[0], e->copy);
+        cudaStreamWaitEvent(e->compute, loaded[0], 0);
+    }
+    for (int s = 0; s < n_slots; ++s) {
+        cudaEventDestroy(loaded[s]);
+        cudaEventDestroy(freed[s]);
+    }
+    return rc;
+}
+
+tp_status sample_selectivity(ExecState& S) {
+    tp_plan* p = S.p;
+    const tp_plan_desc& d = p->d;
+    if (d.filter.col < 0) { p->selectivity = 1.0; return TP_OK; }
+    tp_table* t = S.fact;
+    const uint32_t samples = 4096;
+    if (t->rows == 0) { p->selectivity = 1.0; return TP_OK; }
+    if (t->placement == PL_PAGES) {
+        uint64_t pass = 0;
+        for (uint32_t j = 0; j < samples; ++j) {
+            uint64_t row = (uint64_t)(((unsigned __int128)j * t->rows) / samples);
+            int64_t v = paged_value(t, d.filter.col, row);
+            pass += (v >= d.filter.lo && v <= d.filter.hi);
+        }
+        p->selectivity = (double)pass / samples;
+        return TP_OK;
+    }
+    std::vector<const void*> colptr(t->types.size(), nullptr);
+    for (int c : S.used) colptr[c] = t->dev_cols[c];
+    tpk::QueryDev q = make_query(S, colptr);
+    tp_engine* e = S.e;
+    TP_TRY_CUDA(cudaMemsetAsync(S.counters + 3, 0, sizeof(unsigned long long), e->compute));
+    TP_TRY_CUDA(tpk::launch_sample_filter(q, t->rows, samples, S.counters + 3, e->compute));
+    mark_launch(e);
+    TP_TRY_CUDA(cudaMemcpyAsync(e->host_words, S.counters + 3, 8, cudaMemcpyDeviceToHost, e->compute));
+    TP_TRY_CUDA(cudaStreamSynchronize(e->compute));
+    p->selectivity = (double)e->host_words[0] / samples;
+    return TP_OK;
+}
+
+tp_status map_err(uint32_t err) {
+    if (err & tpk::ERR_DUP) return fail(TP_E_DUP_KEY, "join build side holds a duplicate key");
+    if (err & tpk::ERR_RANGE) return fail(TP_E_RANGE, "a group field value does not fit its bit width");
+    if (err & tpk::ERR_TIMEOUT) return fail(TP_E_TIMEOUT, "a bounded device wait expired");
+    if (err & tpk::ERR_INTERNAL) return fail(TP_E_INTERNAL, "device consistency check failed");
+    return TP_OK;
+}
+
+// Output arrays for `cap` groups carved from one allocation.
+tp_status alloc_result(tp_engine* e, tp_plan* p, uint64_t cap, tp_result** out, tpk::OutDev* od,
+                       unsigned long long* n_groups_dev) {
+    const tp_plan_desc& d = p->d;
+    int n_avg = 0;
+    for (int a = 0; a < d.n_agg; ++a) n_avg += d.aggs[a].kind == TP_AGG_AVG;
+    const uint64_t c = cap ? cap : 1;
+    uint64_t bytes = align256(c * 8) * 2 + align256(c * 16) * p->n_sum + align256(c * 8) * n_avg;
+    tp_status s = reserve(e, bytes);
+    if (s) return s;
+    tp_result* r = new (std::nothrow) tp_result();
+    if (!r) { release(e, bytes); return fail(TP_E_NOMEM, "result: out of host memory"); }
+    r->eng = e;
+    r->reserved = bytes;
+    s = dev_alloc(e, &r->dev, bytes, e->compute);
+    if (s) { release(e, bytes); delete r; return s; }
+    uint8_t* base = (uint8_t*)r->dev;
+    r->d_keys = (uint64_t*)base; base += align256(c * 8);
+    r->d_counts = (int64_t*)base; base += align256(c * 8);
+    memset(od, 0, sizeof(*od));
+    od->keys = r->d_keys;
+    od->counts = r->d_counts;
+    for (int a = 0; a < d.n_agg; ++a) {
+        const int si = p->sum_of_agg[a];
+        r->sum_of_agg[a] = si;
+        r->is_avg[a] = d.aggs[a].kind == TP_AGG_AVG;
+    }
+    for (int si = 0; si < p->n_sum; ++si) {
+        r->d_sums[si] = (uint64_t*)base;
+        od->sums[si] = r->d_sums[si];
+        base += align256(c * 16);
+    }
+    for (int a = 0; a < d.n_agg; ++a) {
+        if (!r->is_avg[a]) continue;
+        const int si = p->sum_of_agg[a];
+        r->d_avgs[si] = (double*)base;
+        od->avgs[si] = r->d_avgs[si];
+        od->has_avg[si] = 1;
+        base += align256(c * 8);
+    }
+    od->n_groups = n_groups_dev;
+    r->n_agg = d.n_agg;
+    r->n_sum = p->n_sum;
+    r->have_sum.assign(8, false);
+    r->have_avg.assign(8, false);
+    r->h_sums.resize(8);
+    r->h_avgs.resize(8);
+    *out = r;
+    return TP_OK;
+}
+
+// ------------------------------------------------------------- execution
+
+tp_status execute_locked(tp_plan* p, tp_result** out) {
+    tp_engine* e = p->eng;
+    const tp_plan_desc& d = p->d;
+    cudaStream_t st = e->compute;
+    TP_TRY_CUDA(cudaSetDevice(e->device));
+    ExecState S;
+    S.p = p;
+    S.e = e;
+    S.fact = d.fact;
+    S.dim = d.join.fact_col >= 0 ? d.dim : nullptr;
+    {
+        std::vector<bool> u(d.fact->types.size(), false);
+        if (d.filter.col >= 0) u[d.filter.col] = true;
+        if (d.join.fact_col >= 0) u[d.join.fact_col] = true;
+        for (int g = 0; g < d.n_group; ++g)
+            if (d.group[g].side == TP_SIDE_FACT) u[d.group[g].col] = true;
+        for (int a = 0; a < d.n_agg; ++a) {
+            if (d.aggs[a].kind == TP_AGG_COUNT) continue;
+            u[d.aggs[a].col_a] = true;
+            if (d.aggs[a].kind == TP_AGG_SUM_MUL_SUB) u[d.aggs[a].col_b] = true;
+        }
+        for (size_t c = 0; c < u.size(); ++c)
+            if (u[c]) S.used.push_back((int)c);
+    }
+    const int ns = p->n_sum;
+    const float lf = p->load_factor;
+    Scratch sc(e, st);
+    // ---- misc words: error word, counters, join side cell
+    tp_status s = reserve(e, 4096);
+    if (s) return s;
+    sc.reserved = 4096;
+    void* misc = nullptr;
+    if ((s = sc.alloc(&misc, 4096))) return s;
+    TP_TRY_CUDA(cudaMemsetAsync(misc, 0, 4096, st));
+    S.err = (uint32_t*)misc;
+    S.counters = (unsigned long long*)((uint8_t*)misc + 256);
+    // ---- filter selectivity from a sample, once per plan (decides eager loads
+    // and the first size estimate of a global aggregation table)
+    if (p->selectivity < 0 && (s = sample_selectivity(S))) return s;
+    S.eager = p->selectivity >= 0.25;
+    // ---- reservation estimate (Section 3.3.2)
+    uint64_t est = 0;
+    if (S.dim) {
+        S.key64 = S.dim->types[d.join.dim_col] == TP_I64;
+        S.join_cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(S.dim->rows / lf)));
+        est += align256(S.join_cap * (S.key64 ? 16 : 8));
+        if (S.dim->placement == PL_PAGES) est += 4 * align256(S.dim->batch_rows * 8);
+    }
+    if (S.fact->placement == PL_PAGES) {
+        const int n_slots = e->cfg.prefetch_depth > 0 ? e->cfg.prefetch_depth + 1 : 1;
+        uint64_t max_rows = 0;
+        for (auto& b : S.fact->batches) max_rows = std::max(max_rows, b.rows);
+        for (int c : S.used) est += n_slots * align256(max_rows * type_size(S.fact->types[c]));
+    }
+    const bool shared = p->strategy == TP_AGG_SHARED;
+    const uint32_t G = shared ? (1u << p->key_bits) : 0;
+    uint64_t agg_cap = 0;
+    const uint32_t words = 2 + 2 * ns;
+    if (shared) {
+        est += align256((uint64_t)G * (1 + 2 * ns) * 8);
+    } else {
+        uint64_t groups = d.expected_groups ? d.expected_groups : p->history_groups;
+        if (groups == 0) {
+            groups = (uint64_t)std::ceil(S.fact->rows * std::min(1.0, p->selectivity * 1.25)) + 16;
+            if (p->key_bits < 40) groups = std::min<uint64_t>(groups, 1ull << p->key_bits);
+        }
+        agg_cap = pow2_at_least(std::max<uint64_t>(1024, (uint64_t)std::ceil(groups / lf)));
+        // table + compaction/sort arrays
+        est += align256((agg_cap + 1) * words * 8) + 2 * align256((agg_cap + 1) * 12) +
+               align256(tpk::radix_sort_hist_words(agg_cap + 1) * 4);
+    }
+    if ((s = reserve(e, est))) return s;
+    sc.reserved += est;
+    // ---- join table
+    if (S.dim) {
+        void* slots = nullptr;
+        const uint64_t jbytes = S.join_cap * (S.key64 ? 16 : 8);
+        if ((s = sc.alloc(&slots, jbytes))) return s;
+        TP_TRY_CUDA(cudaMemsetAsync(slots, 0xFF, jbytes, st));
+        S.jt.slots = (uint64_t*)slots;
+        S.jt.mask = S.join_cap - 1;
+        S.jt.side = (uint32_t*)((uint8_t*)misc + 128);
+        S.jt.key64 = S.key64 ? 1 : 0;
+        if ((s = build_join(S, sc))) return s;
+    }
+    // ---- aggregate
+    tp_result* res = nullptr;
+    KernelTimer timer(e);
+    if (shared) {
+        void* gacc = nullptr;
+        const uint64_t gbytes = (uint64_t)G * (1 + 2 * ns) * 8;
+        if ((s = sc.alloc(&gacc, gbytes))) return s;
+        TP_TRY_CUDA(cudaMemsetAsync(gacc, 0, gbytes, st));
+        const int grid = tpk::agg_shared_grid(p->key_bits, ns, e->num_sms);
+        s = for_each_batch(S, sc, [&](const tpk::QueryDev& q, uint64_t rows) {
+            mark_launch(e);
+            return cuda_check(timer.run(st, rows, [&] {
+                return tpk::launch_agg_shared(q, rows, (uint64_t*)gacc, p->key_bits, grid, st);
+            }), "aggregate");
+        });
+        if (s) return s;
+        tpk::OutDev od;
+        if ((s = alloc_result(e, p, G, &res, &od, S.counters + 1))) return s;
+        std::unique_ptr<tp_result, void (*)(tp_result*)> guard(res, tp_result_free);
+        TP_TRY_CUDA(tpk::launch_final_dense((const uint64_t*)gacc, p->key_bits, ns, od, st));
+        mark_launch(e);
+        TP_TRY_CUDA(cudaMemcpyAsync(e->host_words, misc, 8, cudaMemcpyDeviceToHost, st));
+        TP_TRY_CUDA(cudaMemcpyAsync(e->host_words + 1, S.counters + 1, 8, cudaMemcpyDeviceToHost, st));
+        TP_TRY_CUDA(cudaStreamSynchronize(st));
+        e->d2h_bytes += 16;
+        if ((s = map_err((uint32_t)e->host_words[0]))) return s;
+        res->n_groups = e->host_words[1];
+        timer.collect();
+        guard.release();
+    } else {
+        for (int attempt = 0;; ++attempt) {
+            void* tab = nullptr;
+            const uint64_t tbytes = (agg_cap + 1) * words * 8;
+            if ((s = sc.alloc(&tab, tbytes))) return s;
+            TP_TRY_CUDA(tpk::launch_init_agg((uint64_t*)tab, agg_cap + 1, words, st));
+            mark_launch(e);
+            TP_TRY_CUDA(cudaMemsetAsync(S.counters, 0, 3 * sizeof(unsigned long long), st));
+            tpk::AggTable at{};
+            at.slots = (uint64_t*)tab;
+            at.mask = agg_cap - 1;
+            at.words = words;
+            at.used = S.counters;
+            at.max_used = (uint64_t)(agg_cap * 0.9);
+            s = for_each_batch(S, sc, [&](const tpk::QueryDev& q, uint64_t rows) {
+                mark_launch(e);
+                return cuda_check(timer.run(st, rows, [&] {
+                    return tpk::launch_agg_global(q, rows, at, e->num_sms, st);
+                }), "aggregate");
+            });
+            if (s) return s;
+            TP_TRY_CUDA(cudaMemcpyAsync(e->host_words, misc, 8, cudaMemcpyDeviceToHost, st));
+            TP_TRY_CUDA(cudaMemcpyAsync(e->host_words + 1, S.counters, 8, cudaMemcpyDeviceToHost, st));
+            TP_TRY_CUDA(cudaStreamSynchronize(st));
+            const uint32_t err = (uint32_t)e->host_words[0];
+            if ((s = map_err(err))) return s;
+            if (err & tpk::ERR_OVERFLOW) {
+                timer.ev.clear();  // a discarded attempt is not counted
+                if (attempt >= 6) return fail(TP_E_INTERNAL, "aggregation table overflow after retries");
+                // retry with a table sized from what was seen so far (Section 3.3.2:
+                // a task that ran out of memory is retried with a better estimate)
+                const uint64_t seen = std::max<uint64_t>(e->host_words[1], agg_cap);
+                const uint64_t ncap = pow2_at_least((uint64_t)std::ceil(4.0 * seen / lf));
+                dev_free(e, tab, st);
+                sc.ptrs.erase(std::find(sc.ptrs.begin(), sc.ptrs.end(), tab));
+                const uint64_t extra = align256((ncap + 1) * words * 8) - align256((agg_cap + 1) * words * 8) +
+                                       2 * (align256((ncap + 1) * 12) - align256((agg_cap + 1) * 12)) +
+                                       align256(tpk::radix_sort_hist_words(ncap + 1) * 4);
+                if ((s = reserve(e, extra))) return s;
+                sc.reserved += extra;
+                agg_cap = ncap;
+                TP_TRY_CUDA(cudaMemsetAsync(misc, 0, 4, st));
+                e->retries++;
+                continue;
+            }
+            // compact occupied slots, sort them by key, gather the rows
+            void *k0 = nullptr, *k1 = nullptr, *v0 = nullptr, *v1 = nullptr, *hist = nullptr;
+            if ((s = sc.alloc(&k0, (agg_cap + 1) * 8)) || (s = sc.alloc(&k1, (agg_cap + 1) * 8)) ||
+                (s = sc.alloc(&v0, (agg_cap + 1) * 4)) || (s = sc.alloc(&v1, (agg_cap + 1) * 4)) ||
+                (s = sc.alloc(&hist, tpk::radix_sort_hist_words(agg_cap + 1) * 4)))
+                return s;
+            TP_TRY_CUDA(tpk::launch_compact_global(at, agg_cap + 1, (uint64_t*)k0, (uint32_t*)v0, S.counters + 1,
+                                                   S.counters + 2, e->num_sms, st));
+            mark_launch(e);
+            TP_TRY_CUDA(cudaMemcpyAsync(e->host_words, S.counters + 1, 16, cudaMemcpyDeviceToHost, st));
+            TP_TRY_CUDA(cudaStreamSynchronize(st));
+            e->d2h_bytes += 32;
+            const uint64_t n = e->host_words[0];
+            const uint64_t maxkey = e->host_words[1];
+            int bits = 0;
+            while (bits < 64 && (maxkey >> bits) != 0) ++bits;
+            uint64_t *kk = (uint64_t*)k0, *tk = (uint64_t*)k1;
+            uint32_t *vv = (uint32_t*)v0, *tv = (uint32_t*)v1;
+            TP_TRY_CUDA(tpk::radix_sort_pairs(&kk, &vv, &tk, &tv, (uint32_t*)hist, n, bits, st));
+            e->launches += 3 * ((bits + 7) / 8);
+            tpk::OutDev od;
+            if ((s = alloc_result(e, p, n, &res, &od, S.counters + 1))) return s;
+            TP_TRY_CUDA(tpk::launch_gather_global(at, kk, vv, n, ns, od, e->num_sms, st));
+            mark_launch(e);
+            TP_TRY_CUDA(cudaStreamSynchronize(st));
+            res->n_groups = n;
+            p->history_groups = n;
+            timer.collect();
+            break;
+        }
+    }
+    sc.free_all();
+    *out = res;
+    return TP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tp_status tp_plan_create(tp_engine* e, const tp_plan_desc* d, tp_plan** out) {
+    clear_error();
+    if (!e || !d || !out) return fail(TP_E_INVALID, "tp_plan_create: NULL argument");
+    *out = nullptr;
+    const tp_table* f = d->fact;
+    if (!f || f->eng != e) return fail(TP_E_INVALID, "plan: fact table missing or from another engine");
+    if (d->filter.col != -1 && !valid_col(f, d->filter.col)) return fail(TP_E_INVALID, "plan: bad filter column");
+    const bool join = d->join.fact_col >= 0;
+    if (join) {
+        if (!valid_col(f, d->join.fact_col)) return fail(TP_E_INVALID, "plan: bad join fact column");
+        if (!d->dim || d->dim->eng != e || !valid_col(d->dim, d->join.dim_col))
+            return fail(TP_E_INVALID, "plan: bad dimension table or key column");
+    } else if (d->join.fact_col != -1) {
+        return fail(TP_E_INVALID, "plan: bad join fact column");
+    }
+    if (d->n_group < 0 || d->n_group > 4) return fail(TP_E_INVALID, "plan: 0..4 group fields");
+    if (d->n_agg < 1 || d->n_agg > 8) return fail(TP_E_INVALID, "plan: 1..8 aggregates");
+    std::unique_ptr<tp_plan> p(new (std::nothrow) tp_plan());
+    if (!p) return fail(TP_E_NOMEM, "plan: out of host memory");
+    p->eng = e;
+    p->d = *d;
+    int key_bits = 0, dim_bits = 0;
+    for (int g = 0; g < d->n_group; ++g) {
+        const tp_group_field& gf = d->group[g];
+        if (gf.bits < 1 || gf.bits > 64) return fail(TP_E_INVALID, "plan: group field %d needs 1..64 bits", g);
+        key_bits += gf.bits;
+        p->gdpos[g] = 0;
+        if (gf.side == TP_SIDE_FACT) {
+            if (!valid_col(f, gf.col)) return fail(TP_E_INVALID, "plan: bad group column %d", g);
+        } else if (gf.side == TP_SIDE_DIM) {
+            if (!join || !valid_col(d->dim, gf.col)) return fail(TP_E_INVALID, "plan: bad dimension group column %d", g);
+            p->gdpos[g] = dim_bits;
+            dim_bits += gf.bits;
+        } else {
+            return fail(TP_E_INVALID, "plan: bad group side %d", g);
+        }
+    }
+    if (key_bits > 64) return fail(TP_E_INVALID, "plan: group key wider than 64 bits");
+    if (dim_bits > tpk::MAX_DIM_BITS) return fail(TP_E_INVALID, "plan: dimension group fields wider than 31 bits");
+    int ns = 0;
+    for (int a = 0; a < d->n_agg; ++a) {
+        const tp_agg& ag = d->aggs[a];
+        p->sum_of_agg[a] = -1;
+        switch (ag.kind) {
+        case TP_AGG_COUNT: break;
+        case TP_AGG_SUM_MUL_SUB:
+            if (!valid_col(f, ag.col_b)) return fail(TP_E_INVALID, "plan: bad aggregate column");
+            /* fallthrough */
+        case TP_AGG_SUM:
+        case TP_AGG_AVG:
+            if (!valid_col(f, ag.col_a)) return fail(TP_E_INVALID, "plan: bad aggregate column");
+            p->sum_of_agg[a] = ns++;
+            break;
+        default: return fail(TP_E_INVALID, "plan: bad aggregate kind");
+        }
+    }
+    p->n_sum = ns;
+    p->key_bits = key_bits;
+    p->dim_bits = dim_bits;
+    p->load_factor = d->load_factor > 0 ? d->load_factor : e->cfg.load_factor;
+    if (!(p->load_factor > 0.05f && p->load_factor <= 0.9f)) return fail(TP_E_INVALID, "plan: bad load factor");
+    const int want = d->agg_strategy ? d->agg_strategy : e->cfg.agg_strategy;
+    const bool fits_shared = key_bits <= 12 && tpk::agg_shared_smem_bytes(key_bits, ns) <= 160 * 1024;
+    if (want == TP_AGG_SHARED && !fits_shared)
+        return fail(TP_E_INVALID, "plan: shared-memory aggregation needs a key of at most 12 bits");
+    if (want < TP_AGG_AUTO || want > TP_AGG_GLOBAL) return fail(TP_E_INVALID, "plan: bad strategy");
+    p->strategy = (want == TP_AGG_GLOBAL || !fits_shared) ? TP_AGG_GLOBAL : TP_AGG_SHARED;
+    *out = p.release();
+    return TP_OK;
+}
+
+void tp_plan_destroy(tp_plan* p) { delete p; }
+
+tp_status tp_execute(tp_plan* p, tp_result** out) {
+    clear_error();
+    if (!p || !out) return fail(TP_E_INVALID, "tp_execute: NULL argument");
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(p->eng->exec_mu);
+    return execute_locked(p, out);
+}
+
+// ----------------------------------------------------------------- results
+
+uint64_t tp_result_groups(const tp_result* r) { return r ? r->n_groups : 0; }
+
+static bool fetch(tp_result* r, void* dst, const void* src, uint64_t bytes) {
+    if (bytes == 0) return true;
+    if (cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        fail(TP_E_CUDA, "result copy failed");
+        return false;
+    }
+    r->eng->d2h_bytes += bytes;
+    return true;
+}
+
+const uint64_t* tp_result_keys(tp_result* r) {
+    if (!r) return nullptr;
+    std::lock_guard<std::mutex> lk(r->mu);
+    if (!r->have_keys) {
+        r->h_keys.resize(r->n_groups ? r->n_groups : 1);
+        if (!fetch(r, r->h_keys.data(), r->d_keys, r->n_groups * 8)) return nullptr;
+        r->have_keys = true;
+    }
+    return r->h_keys.data();
+}
+
+const int64_t* tp_result_count(tp_result* r) {
+    if (!r) return nullptr;
+    std::lock_guard<std::mutex> lk(r->mu);
+    if (!r->have_counts) {
+        r->h_counts.resize(r->n_groups ? r->n_groups : 1);
+        if (!fetch(r, r->h_counts.data(), r->d_counts, r->n_groups * 8)) return nullptr;
+        r->have_counts = true;
+    }
+    return r->h_counts.data();
+}
+
+const tp_i128* tp_result_sum(tp_result* r, int32_t agg) {
+    if (!r || agg < 0 || agg >= r->n_agg || r->sum_of_agg[agg] < 0) return nullptr;
+    const int si = r->sum_of_agg[agg];
+    std::lock_guard<std::mutex> lk(r->mu);
+    if (!r->have_sum[si]) {
+        r->h_sums[si].resize(r->n_groups ? r->n_groups : 1);
+        if (!fetch(r, r->h_sums[si].data(), r->d_sums[si], r->n_groups * 16)) return nullptr;
+        r->have_sum[si] = true;
+    }
+    return r->h_sums[si].data();
+}
+
+const double* tp_result_avg(tp_result* r, int32_t agg) {
+    if (!r || agg < 0 || agg >= r->n_agg || !r->is_avg[agg]) return nullptr;
+    const int si = r->sum_of_agg[agg];
+    std::lock_guard<std::mutex> lk(r->mu);
+    if (!r->have_avg[si]) {
+        r->h_avgs[si].resize(r->n_groups ? r->n_groups : 1);
+        if (!fetch(r, r->h_avgs[si].data(), r->d_avgs[si], r->n_groups * 8)) return nullptr;
+        r->have_avg[si] = true;
+    }
+    return r->h_avgs[si].data();
+}
+
+const void* tp_result_device_keys(const tp_result* r) { return r ? r->d_keys : nullptr; }
+const void* tp_result_device_count(const tp_result* r) { return r ? r->d_counts : nullptr; }
+
+const void* tp_result_device_sum(const tp_result* r, int32_t agg) {
+    if (!r || agg < 0 || agg >= r->n_agg || r->sum_of_agg[agg] < 0) return nullptr;
+    return r->d_sums[r->sum_of_agg[agg]];
+}
+
+const void* tp_result_device_avg(const tp_result* r, int32_t agg) {
+    if (!r || agg < 0 || agg >= r->n_agg || !r->is_avg[agg]) return nullptr;
+    return r->d_avgs[r->sum_of_agg[agg]];
+}
+
+void tp_result_free(tp_result* r) {
+    if (!r) return;
+    tp_engine* e = r->eng;
+    if (r->dev) {
+        cudaSetDevice(e->device);
+        cudaStreamSynchronize(e->compute);
+        dev_free(e, r->dev, e->compute);
+    }
+    if (r->reserved) release(e, r->reserved);
+    delete r;
+}
+
+}  // extern "C"

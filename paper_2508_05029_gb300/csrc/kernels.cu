@@ -1,0 +1,734 @@
+// Operator kernels of the per-batch pipeline: hash build, fused
+// filter -> probe -> aggregate (shared-memory or global table), and the
+// finalisation that turns accumulators into sorted result rows.
+//
+// Paper basis: Section 3.1 (operators run GPU kernels over batches of
+// equal-length columns; Filter and Join), Section 4 (decimal values held as
+// 128-bit integers).  The kernel designs are this library's own.
+//
+// Row layout inside a warp tile: a warp owns 128 consecutive rows.  Lane l
+// holds rows {2l, 2l+1, 64+2l, 64+2l+1}, so every column is read with two
+// fully coalesced vector loads per lane whatever its width (8-bit: 2 bytes,
+// 32-bit: 8 bytes, 64-bit: 16 bytes per load).
+#include "kernels.cuh"
+
+namespace tpk {
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+// ------------------------------------------------------------------ loads
+
+__device__ __forceinline__ int64_t ld1(const DevCol& c, uint64_t i) {
+    switch (c.type) {
+    case T_I32: return __ldcs((const int*)c.ptr + i);
+    case T_I64: return __ldcs((const long long*)c.ptr + i);
+    default: return (int64_t)__ldcs((const unsigned char*)c.ptr + i);
+    }
+}
+
+// rows r, r+1, r+64, r+65 of a full tile (r even)
+__device__ __forceinline__ void ld4(const DevCol& c, uint64_t r, int64_t v[4]) {
+    switch (c.type) {
+    case T_I32: {
+        const int2* p = reinterpret_cast<const int2*>((const int32_t*)c.ptr + r);
+        int2 a = __ldcs(p), b = __ldcs(p + 32);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        break;
+    }
+    case T_I64: {
+        const longlong2* p = reinterpret_cast<const longlong2*>((const int64_t*)c.ptr + r);
+        longlong2 a = __ldcs(p), b = __ldcs(p + 32);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        break;
+    }
+    default: {
+        const uchar2* p = reinterpret_cast<const uchar2*>((const uint8_t*)c.ptr + r);
+        uchar2 a = __ldcs(p), b = __ldcs(p + 32);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        break;
+    }
+    }
+}
+
+template <bool FULL>
+__device__ __forceinline__ void load_rows(const DevCol& c, uint64_t r, uint64_t n, const bool want[4],
+                                          int64_t v[4]) {
+    if (FULL) {
+        ld4(c, r, v);
+    } else {
+        const uint64_t rows[4] = {r, r + 1, r + 64, r + 65};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = (want[i] && rows[i] < n) ? ld1(c, rows[i]) : 0;
+    }
+}
+
+// ------------------------------------------------------------- 128-bit sums
+
+struct I128 {
+    uint64_t lo;
+    uint64_t hi;
+};
+
+__device__ __forceinline__ I128 i128_from_i64(int64_t v) {
+    return I128{(uint64_t)v, (uint64_t)(v >> 63)};
+}
+
+__device__ __forceinline__ I128 i128_add(I128 a, I128 b) {
+    I128 r;
+    r.lo = a.lo + b.lo;
+    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+    return r;
+}
+
+// a * (k - b) for 64-bit a, b, k: exact, since |a| < 2^63 and |k - b| < 2^64
+// keep the product below 2^127 in magnitude.
+__device__ __forceinline__ I128 mul_sub(int64_t a, int64_t k, int64_t b) {
+    __int128 d = (__int128)k - (__int128)b;
+    __int128 p = (__int128)a * d;
+    return I128{(uint64_t)p, (uint64_t)((unsigned __int128)p >> 64)};
+}
+
+// Adds t to the 128-bit value (lo, hi) with two 64-bit atomics: the carry out
+// of each low-word addition follows from the value the atomic returned, so the
+// high word receives exactly the sum of all carries plus all high words.
+__device__ __forceinline__ void atomic_add_i128(uint64_t* lo, uint64_t* hi, I128 t) {
+    unsigned long long old = atomicAdd((unsigned long long*)lo, (unsigned long long)t.lo);
+    uint64_t h = t.hi + ((old + t.lo) < old ? 1ull : 0ull);
+    if (h != 0) atomicAdd((unsigned long long*)hi, (unsigned long long)h);
+}
+
+// ------------------------------------------------------------------ probing
+
+// Looks up four keys at once so their table loads overlap.  pass[i] is
+// cleared for rows whose key is absent.
+__device__ __forceinline__ void probe4(const JoinTable& jt, const int64_t key[4], bool pass[4],
+                                       uint32_t payload[4], uint32_t* err) {
+    uint64_t slot[4];
+    bool act[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        act[i] = pass[i];
+        payload[i] = 0;
+        if (!act[i]) continue;
+        bool special;
+        if (jt.key64) {
+            special = (uint64_t)key[i] == EMPTY64;
+        } else {
+            if (key[i] < INT32_MIN || key[i] > INT32_MAX) {  // cannot match a 32-bit key
+                pass[i] = false;
+                act[i] = false;
+                continue;
+            }
+            special = (uint32_t)key[i] == EMPTY32;
+        }
+        if (special) {
+            pass[i] = __ldg(jt.side) != 0;
+            payload[i] = __ldg(jt.side + 1);
+            act[i] = false;
+            continue;
+        }
+        slot[i] = fmix64((uint64_t)key[i]) & jt.mask;
+    }
+    for (uint64_t it = 0; it <= jt.mask; ++it) {
+        bool any = false;
+        if (!jt.key64) {
+            uint64_t w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (act[i]) w[i] = __ldg((const unsigned long long*)jt.slots + slot[i]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (!act[i]) continue;
+                uint32_t wk = (uint32_t)w[i];
+                if (wk == (uint32_t)key[i]) {
+                    payload[i] = (uint32_t)(w[i] >> 32);
+                    act[i] = false;
+                } else if (wk == EMPTY32) {
+                    pass[i] = false;
+                    act[i] = false;
+                } else {
+                    slot[i] = (slot[i] + 1) & jt.mask;
+                    any = true;
+                }
+            }
+        } else {
+            ulonglong2 w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (act[i]) w[i] = __ldg((const ulonglong2*)jt.slots + slot[i]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (!act[i]) continue;
+                if (w[i].x == (uint64_t)key[i]) {
+                    payload[i] = (uint32_t)w[i].y;
+                    act[i] = false;
+                } else if (w[i].x == EMPTY64) {
+                    pass[i] = false;
+                    act[i] = false;
+                } else {
+                    slot[i] = (slot[i] + 1) & jt.mask;
+                    any = true;
+                }
+            }
+        }
+        if (!any) return;
+    }
+    atomicOr(err, ERR_INTERNAL);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (act[i]) pass[i] = false;
+}
+
+// ------------------------------------------------------------ tile pipeline
+//
+// A lane evaluates its four rows in phases so that only the row state (pass
+// bits and packed keys) stays live across phases: filter, then join probe,
+// then the group key, then each aggregate column in turn, fed straight into
+// the accumulators.
+
+__device__ __forceinline__ bool any4(const bool p[4]) { return p[0] || p[1] || p[2] || p[3]; }
+
+// Filter, join and key packing of the lane's four rows in warp tile t0.
+// Returns false when no row of the lane survives.
+template <bool FULL>
+__device__ __forceinline__ bool eval_keys(const QueryDev& q, uint64_t t0, uint64_t n, int lane,
+                                          bool pass[4], uint64_t key[4]) {
+    const uint64_t r = t0 + 2ull * (uint64_t)lane;
+    const uint64_t rows[4] = {r, r + 1, r + 64, r + 65};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) pass[i] = FULL || rows[i] < n;
+    int64_t v[4];
+    if (q.has_filter) {
+        load_rows<FULL>(q.fcol, r, n, pass, v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pass[i] = pass[i] && v[i] >= q.flo && v[i] <= q.fhi;
+        if (!any4(pass)) return false;
+    }
+    uint32_t payload[4] = {0, 0, 0, 0};
+    if (q.has_join) {
+        load_rows<FULL>(q.fk, r, n, pass, v);
+        probe4(q.jt, v, pass, payload, q.err);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (pass[i] && (payload[i] & PAYLOAD_BAD)) {
+                atomicOr(q.err, ERR_RANGE);
+                pass[i] = false;
+            }
+        }
+        if (!any4(pass)) return false;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) key[i] = 0;
+#pragma unroll
+    for (int g = 0; g < MAX_GROUP; ++g) {
+        if (g >= q.n_group) break;
+        const int bits = q.gbits[g];
+        const bool fact_side = q.gside[g] == 0;
+        if (fact_side) load_rows<FULL>(q.gcol[g], r, n, pass, v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint64_t f = fact_side ? (uint64_t)v[i]
+                                         : (uint64_t)(payload[i] >> q.gdpos[g]) & ((1ull << bits) - 1ull);
+            if (bits < 64) {
+                if (pass[i] && (f >> bits) != 0) {
+                    atomicOr(q.err, ERR_RANGE);
+                    pass[i] = false;
+                }
+                key[i] = (key[i] << bits) | f;
+            } else {
+                key[i] = f;
+            }
+        }
+    }
+    return any4(pass);
+}
+
+// The four terms of aggregate s for the lane's rows.
+template <bool FULL>
+__device__ __forceinline__ void eval_terms(const QueryDev& q, int s, uint64_t t0, uint64_t n, int lane,
+                                           const bool pass[4], I128 t[4]) {
+    const uint64_t r = t0 + 2ull * (uint64_t)lane;
+    int64_t a[4];
+    load_rows<FULL>(q.sa[s], r, n, pass, a);
+    if (q.skind[s] == S_MUL_SUB) {
+        int64_t b[4];
+        load_rows<FULL>(q.sb[s], r, n, pass, b);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) t[i] = mul_sub(a[i], q.sk[s], b[i]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) t[i] = i128_from_i64(a[i]);
+    }
+}
+
+// --------------------------------------------------------------------- fill
+
+__global__ void k_fill_u64(uint64_t* p, uint64_t n, uint64_t v) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+cudaError_t launch_fill_u64(uint64_t* p, uint64_t n, uint64_t v, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_fill_u64<<<(unsigned)blocks, 256, 0, st>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+__global__ void k_init_agg(uint64_t* slots, uint64_t n_words, uint32_t words) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_words;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        slots[i] = (i % words == 0) ? EMPTY64 : 0ull;
+}
+
+cudaError_t launch_init_agg(uint64_t* slots, uint64_t n_slots, uint32_t words, cudaStream_t st) {
+    const uint64_t n = n_slots * words;
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_init_agg<<<(unsigned)blocks, 256, 0, st>>>(slots, n, words);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------- build
+
+__global__ void __launch_bounds__(256) k_build(const __grid_constant__ BuildDev b, uint64_t n) {
+    const JoinTable& jt = b.jt;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        int64_t key = ld1(b.key, i);
+        // Dimension group fields packed into bits 0..30 of the payload; bit 31
+        // marks a row with a field outside its width.  That is an error only
+        // if a surviving fact row joins to it, which the probe side reports.
+        uint32_t payload = 0;
+        for (int f = 0; f < b.n_dfield; ++f) {
+            int64_t v = ld1(b.dcol[f], i);
+            if (v < 0 || ((uint64_t)v >> b.dbits[f]) != 0) payload |= PAYLOAD_BAD;
+            else payload |= (uint32_t)((uint64_t)v << b.dpos[f]);
+        }
+        bool special = jt.key64 ? (uint64_t)key == EMPTY64 : (uint32_t)key == EMPTY32;
+        if (special) {
+            if (atomicCAS(jt.side, 0u, 1u) != 0u) atomicOr(b.err, ERR_DUP);
+            else jt.side[1] = payload;
+            continue;
+        }
+        uint64_t s = fmix64((uint64_t)key) & jt.mask;
+        bool placed = false;
+        for (uint64_t it = 0; it <= jt.mask; ++it) {
+            if (!jt.key64) {
+                unsigned long long want = ((unsigned long long)payload << 32) | (uint32_t)key;
+                unsigned long long prev =
+                    atomicCAS((unsigned long long*)jt.slots + s, (unsigned long long)EMPTY64, want);
+                if (prev == EMPTY64) { placed = true; break; }
+                if ((uint32_t)prev == (uint32_t)key) { atomicOr(b.err, ERR_DUP); placed = true; break; }
+            } else {
+                unsigned long long prev = atomicCAS((unsigned long long*)jt.slots + 2 * s,
+                                                    (unsigned long long)EMPTY64, (unsigned long long)key);
+                if (prev == EMPTY64) {
+                    jt.slots[2 * s + 1] = payload;
+                    placed = true;
+                    break;
+                }
+                if (prev == (unsigned long long)key) { atomicOr(b.err, ERR_DUP); placed = true; break; }
+            }
+            s = (s + 1) & jt.mask;
+        }
+        if (!placed) atomicOr(b.err, ERR_INTERNAL);
+    }
+}
+
+cudaError_t launch_build(const BuildDev& b, uint64_t n, int num_sms, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    uint64_t cap = (uint64_t)num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    k_build<<<(unsigned)blocks, 256, 0, st>>>(b, n);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- shared-memory aggregation
+//
+// Few groups (packed key of at most 12 bits): every CTA keeps a private dense
+// table in shared memory indexed by the key itself -- count[G], then lo[G],
+// hi[G] per sum -- updated with shared-memory atomics, and merges it into the
+// global dense table (same layout) once at the end.
+
+constexpr int AGG_THREADS = 512;
+
+template <int NS>
+__global__ void __launch_bounds__(AGG_THREADS) k_agg_shared(const __grid_constant__ QueryDev q,
+                                                           uint64_t n, uint64_t* __restrict__ gacc,
+                                                           uint32_t G) {
+    extern __shared__ uint64_t sm[];
+    const uint32_t words = G * (1 + 2 * NS);
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) sm[i] = 0;
+    __syncthreads();
+    uint64_t* cnt = sm;
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = blockDim.x >> 5;
+    const uint64_t ntiles = (n + 127) / 128;
+    const uint64_t nfull = n / 128;
+    for (uint64_t t = blockIdx.x * nwarps + (threadIdx.x >> 5); t < ntiles; t += gridDim.x * nwarps) {
+        const bool full = t < nfull;
+        bool pass[4];
+        uint64_t key[4];
+        const bool any = full ? eval_keys<true>(q, t * 128, n, lane, pass, key)
+                              : eval_keys<false>(q, t * 128, n, lane, pass, key);
+        if (!any) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (pass[i]) atomicAdd((unsigned long long*)&cnt[(uint32_t)key[i]], 1ull);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            I128 tm[4];
+            if (full) eval_terms<true>(q, s, t * 128, n, lane, pass, tm);
+            else eval_terms<false>(q, s, t * 128, n, lane, pass, tm);
+            uint64_t* lo = sm + G * (1 + 2 * s);
+            uint64_t* hi = sm + G * (2 + 2 * s);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (pass[i]) atomic_add_i128(lo + (uint32_t)key[i], hi + (uint32_t)key[i], tm[i]);
+        }
+    }
+    __syncthreads();
+    for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) {
+        const uint64_t c = cnt[g];
+        if (c == 0) continue;
+        atomicAdd((unsigned long long*)&gacc[g], (unsigned long long)c);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            I128 v{sm[G * (1 + 2 * s) + g], sm[G * (2 + 2 * s) + g]};
+            atomic_add_i128(&gacc[G * (1 + 2 * s) + g], &gacc[G * (2 + 2 * s) + g], v);
+        }
+    }
+}
+
+size_t agg_shared_smem_bytes(uint32_t key_bits, int n_sum) {
+    return (size_t)(1u << key_bits) * (1 + 2 * (size_t)n_sum) * sizeof(uint64_t);
+}
+
+template <int NS>
+static void* agg_shared_fn() { return (void*)k_agg_shared<NS>; }
+
+static void* agg_shared_kernel(int n_sum) {
+    switch (n_sum) {
+    case 0: return agg_shared_fn<0>();
+    case 1: return agg_shared_fn<1>();
+    case 2: return agg_shared_fn<2>();
+    case 3: return agg_shared_fn<3>();
+    case 4: return agg_shared_fn<4>();
+    case 5: return agg_shared_fn<5>();
+    case 6: return agg_shared_fn<6>();
+    case 7: return agg_shared_fn<7>();
+    default: return agg_shared_fn<8>();
+    }
+}
+
+int agg_shared_grid(uint32_t key_bits, int n_sum, int num_sms) {
+    size_t smem = agg_shared_smem_bytes(key_bits, n_sum);
+    void* fn = agg_shared_kernel(n_sum);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, AGG_THREADS, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    return per_sm * num_sms;
+}
+
+cudaError_t launch_agg_shared(const QueryDev& q, uint64_t n, uint64_t* gacc, uint32_t key_bits,
+                              int grid, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t G = 1u << key_bits;
+    const size_t smem = agg_shared_smem_bytes(key_bits, q.n_sum);
+    uint64_t tiles = (n + 127) / 128;
+    uint64_t need = (tiles + (AGG_THREADS / 32) - 1) / (AGG_THREADS / 32);
+    unsigned blocks = (unsigned)(need < (uint64_t)grid ? need : (uint64_t)grid);
+    switch (q.n_sum) {
+#define TPK_CASE(K) \
+    case K: k_agg_shared<K><<<blocks, AGG_THREADS, smem, st>>>(q, n, gacc, G); break;
+    TPK_CASE(0) TPK_CASE(1) TPK_CASE(2) TPK_CASE(3) TPK_CASE(4) TPK_CASE(5) TPK_CASE(6) TPK_CASE(7) TPK_CASE(8)
+#undef TPK_CASE
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- global aggregation
+//
+// Many groups: one open-addressing table in device memory.  A lane merges its
+// two pairs of adjacent rows first when their keys agree (clustered keys such
+// as an order key repeated over consecutive line items), then claims or finds
+// the slot and adds count and sums with 64-bit atomics.
+
+__device__ __forceinline__ uint64_t* agg_slot(const AggTable& t, uint64_t key, uint32_t* err) {
+    if (key == EMPTY64) return t.slots + (t.mask + 1) * t.words;   // side slot
+    uint64_t s = fmix64(key) & t.mask;
+    for (uint64_t it = 0; it <= t.mask; ++it) {
+        uint64_t* p = t.slots + s * t.words;
+        uint64_t k = __ldcg((const unsigned long long*)p);
+        if (k == key) return p;
+        if (k == EMPTY64) {
+            unsigned long long prev =
+                atomicCAS((unsigned long long*)p, (unsigned long long)EMPTY64, (unsigned long long)key);
+            if (prev == EMPTY64) {
+                unsigned long long u = atomicAdd(t.used, 1ull);
+                if (u >= t.max_used) atomicOr(err, ERR_OVERFLOW);
+                return p;
+            }
+            if (prev == key) return p;
+        }
+        s = (s + 1) & t.mask;
+    }
+    atomicOr(err, ERR_OVERFLOW);
+    return nullptr;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(256) k_agg_global(const __grid_constant__ QueryDev q, uint64_t n,
+                                                   const __grid_constant__ AggTable t) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwarps = blockDim.x >> 5;
+    const uint64_t ntiles = (n + 127) / 128;
+    const uint64_t nfull = n / 128;
+    for (uint64_t tt = blockIdx.x * nwarps + (threadIdx.x >> 5); tt < ntiles; tt += gridDim.x * nwarps) {
+        const bool full = tt < nfull;
+        bool pass[4];
+        uint64_t key[4];
+        const bool any = full ? eval_keys<true>(q, tt * 128, n, lane, pass, key)
+                              : eval_keys<false>(q, tt * 128, n, lane, pass, key);
+        if (!any) continue;
+        // rows (0,1) and (2,3) are adjacent: fold the second into the first
+        // when their keys agree
+        bool fold[2];
+        uint64_t* slot[4];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            fold[j] = pass[2 * j] && pass[2 * j + 1] && key[2 * j] == key[2 * j + 1];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            slot[i] = nullptr;
+            if (!pass[i] || ((i & 1) && fold[i >> 1])) continue;
+            slot[i] = agg_slot(t, key[i], q.err);
+            if (slot[i])
+                atomicAdd((unsigned long long*)(slot[i] + 1), (i & 1) == 0 && fold[i >> 1] ? 2ull : 1ull);
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            I128 tm[4];
+            if (full) eval_terms<true>(q, s, tt * 128, n, lane, pass, tm);
+            else eval_terms<false>(q, s, tt * 128, n, lane, pass, tm);
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (fold[j]) tm[2 * j] = i128_add(tm[2 * j], tm[2 * j + 1]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (slot[i]) atomic_add_i128(slot[i] + 2 + 2 * s, slot[i] + 3 + 2 * s, tm[i]);
+        }
+    }
+}
+
+cudaError_t launch_agg_global(const QueryDev& q, uint64_t n, const AggTable& t, int num_sms,
+                              cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint64_t tiles = (n + 127) / 128;
+    uint64_t need = (tiles + 7) / 8;
+    uint64_t cap = (uint64_t)num_sms * 8;
+    unsigned blocks = (unsigned)(need < cap ? need : cap);
+    switch (q.n_sum) {
+#define TPK_CASE(K) \
+    case K: k_agg_global<K><<<blocks, 256, 0, st>>>(q, n, t); break;
+    TPK_CASE(0) TPK_CASE(1) TPK_CASE(2) TPK_CASE(3) TPK_CASE(4) TPK_CASE(5) TPK_CASE(6) TPK_CASE(7) TPK_CASE(8)
+#undef TPK_CASE
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- finalise
+
+// Correctly rounded conversion of a 128-bit integer to double.  Values that
+// fit in 64 bits use the hardware conversion directly.  Wider magnitudes keep
+// their top 64 bits and fold every discarded bit into the lowest kept bit
+// (a "sticky" bit): with 64 kept bits and 53 significand bits the rounding
+// decision (round bit plus "anything below it") is unchanged, so one
+// round-to-nearest conversion of the 64-bit value, scaled by an exact power
+// of two, is the correctly rounded result.
+__device__ __forceinline__ double i128_to_double(uint64_t lo, uint64_t hi) {
+    if (hi == (uint64_t)((int64_t)lo >> 63)) return __ll2double_rn((long long)lo);
+    const bool neg = (int64_t)hi < 0;
+    uint64_t mlo = lo, mhi = hi;
+    if (neg) {  // two's complement negate; -2^127 maps to 2^127 as unsigned
+        mlo = ~lo + 1ull;
+        mhi = ~hi + (mlo == 0 ? 1ull : 0ull);
+    }
+    double d;
+    if (mhi == 0) {
+        d = __ull2double_rn(mlo);
+    } else {
+        const int lz = __clzll((long long)mhi);
+        const int s = 64 - lz;  // 1..64
+        uint64_t top, sticky;
+        if (s == 64) {
+            top = mhi;
+            sticky = mlo != 0;
+        } else {
+            top = (mhi << (64 - s)) | (mlo >> s);
+            sticky = (mlo & ((1ull << s) - 1ull)) != 0;
+        }
+        d = ldexp(__ull2double_rn(top | sticky), s);
+    }
+    return neg ? -d : d;
+}
+
+__device__ __forceinline__ void write_row(const OutDev& o, uint64_t pos, uint64_t key, uint64_t c,
+                                          const uint64_t* lo_hi, int n_sum) {
+    o.keys[pos] = key;
+    o.counts[pos] = (int64_t)c;
+    for (int s = 0; s < n_sum; ++s) {
+        o.sums[s][2 * pos] = lo_hi[2 * s];
+        o.sums[s][2 * pos + 1] = lo_hi[2 * s + 1];
+        if (o.has_avg[s])
+            o.avgs[s][pos] = __ddiv_rn(i128_to_double(lo_hi[2 * s], lo_hi[2 * s + 1]),
+                                       __ll2double_rn((long long)c));
+    }
+}
+
+// One CTA walks the dense table in key order, so the output is sorted.
+__global__ void __launch_bounds__(1024) k_final_dense(const uint64_t* __restrict__ gacc, uint32_t G,
+                                                     int n_sum, const __grid_constant__ OutDev o) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint64_t base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t c0 = 0; c0 < G; c0 += blockDim.x) {
+        const uint32_t g = c0 + threadIdx.x;
+        const bool has = g < G && gacc[g] != 0;
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        if (lane == 0) warp_tot[warp] = __popc(m);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < warp) before += warp_tot[w];
+            total += warp_tot[w];
+        }
+        if (has) {
+            const uint64_t pos = base + before + __popc(m & ((1u << lane) - 1u));
+            uint64_t lh[2 * MAX_SUM];
+            for (int s = 0; s < n_sum; ++s) {
+                lh[2 * s] = gacc[(uint64_t)G * (1 + 2 * s) + g];
+                lh[2 * s + 1] = gacc[(uint64_t)G * (2 + 2 * s) + g];
+            }
+            write_row(o, pos, g, gacc[g], lh, n_sum);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *o.n_groups = base;
+}
+
+cudaError_t launch_final_dense(const uint64_t* gacc, uint32_t key_bits, int n_sum, const OutDev& o,
+                               cudaStream_t st) {
+    k_final_dense<<<1, 1024, 0, st>>>(gacc, 1u << key_bits, n_sum, o);
+    return cudaGetLastError();
+}
+
+// Occupied slots of the global table -> (key, slot index); also the max key.
+__global__ void k_compact_global(const __grid_constant__ AggTable t, uint64_t cap_with_side,
+                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ idx,
+                                 unsigned long long* count, unsigned long long* maxkey) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long local_max = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n_iter = (cap_with_side + stride - 1) / stride;
+    for (uint64_t it = 0; it < n_iter; ++it) {
+        const uint64_t s = it * stride + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+        bool has = false;
+        uint64_t key = 0;
+        if (s < cap_with_side) {
+            const uint64_t* p = t.slots + s * t.words;
+            has = p[1] != 0;
+            key = (s == cap_with_side - 1) ? EMPTY64 : p[0];
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        unsigned long long base = 0;
+        if (lane == 0 && m) base = atomicAdd(count, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (has) {
+            const uint64_t pos = base + __popc(m & ((1u << lane) - 1u));
+            keys[pos] = key;
+            idx[pos] = (uint32_t)s;
+            if (key > local_max) local_max = key;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long o = __shfl_xor_sync(0xffffffffu, local_max, off);
+        if (o > local_max) local_max = o;
+    }
+    if (lane == 0 && local_max) atomicMax(maxkey, local_max);
+}
+
+cudaError_t launch_compact_global(const AggTable& t, uint64_t cap_with_side, uint64_t* keys,
+                                  uint32_t* idx, unsigned long long* count,
+                                  unsigned long long* maxkey, int num_sms, cudaStream_t st) {
+    uint64_t blocks = (cap_with_side + 255) / 256;
+    uint64_t cap = (uint64_t)num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    k_compact_global<<<(unsigned)blocks, 256, 0, st>>>(t, cap_with_side, keys, idx, count, maxkey);
+    return cudaGetLastError();
+}
+
+__global__ void k_gather_global(const __grid_constant__ AggTable t, const uint64_t* __restrict__ skeys,
+                                const uint32_t* __restrict__ sidx, uint64_t n, int n_sum,
+                                const __grid_constant__ OutDev o) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t* p = t.slots + (uint64_t)sidx[i] * t.words;
+        write_row(o, i, skeys[i], p[1], p + 2, n_sum);
+    }
+}
+
+cudaError_t launch_gather_global(const AggTable& t, const uint64_t* sorted_keys,
+                                 const uint32_t* sorted_idx, uint64_t n, int n_sum, const OutDev& o,
+                                 int num_sms, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    uint64_t cap = (uint64_t)num_sms * 8;
+    if (blocks > cap) blocks = cap;
+    k_gather_global<<<(unsigned)blocks, 256, 0, st>>>(t, sorted_keys, sorted_idx, n, n_sum, o);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------- selectivity sampling
+
+__global__ void k_sample_filter(const __grid_constant__ QueryDev q, uint64_t n, uint32_t samples,
+                                unsigned long long* out) {
+    unsigned local = 0;
+    for (uint32_t j = threadIdx.x; j < samples; j += blockDim.x) {
+        const uint64_t row = (uint64_t)(((unsigned __int128)j * n) / samples);
+        const int64_t v = ld1(q.fcol, row);
+        local += (v >= q.flo && v <= q.fhi) ? 1u : 0u;
+    }
+    for (int off = 16; off > 0; off >>= 1) local += __shfl_xor_sync(0xffffffffu, local, off);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(out, (unsigned long long)local);
+}
+
+cudaError_t launch_sample_filter(const QueryDev& q, uint64_t n, uint32_t samples,
+                                 unsigned long long* out, cudaStream_t st) {
+    if (n == 0 || samples == 0) return cudaSuccess;
+    k_sample_filter<<<1, 256, 0, st>>>(q, n, samples, out);
+    return cudaGetLastError();
+}
+
+}  // namespace tpk

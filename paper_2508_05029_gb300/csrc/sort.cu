@@ -1,0 +1,210 @@
+// Device LSD radix sort of (64-bit key, 32-bit value) pairs, used to emit
+// high-cardinality group-by results in ascending key order.
+//
+// Each pass sorts stably by one 8-bit digit:
+//   1. k_digit_hist: per tile of 4096 pairs, a digit histogram, stored
+//      digit-major (hist[d * tiles + tile]) so that one exclusive scan over the
+//      whole array yields every (digit, tile) output offset;
+//   2. an exclusive scan of that array (k_scan_*);
+//   3. k_digit_scatter: every warp ranks its 512 pairs in input order with
+//      __match_any_sync on the digit, so equal digits keep their order and the
+//      pass is stable.
+#include "kernels.cuh"
+
+namespace tpk {
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_ROUNDS = 16;                                // pairs per lane
+constexpr int SORT_TILE = SORT_THREADS * SORT_ROUNDS;          // 4096
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;           // 4096
+
+// ---------------------------------------------------------- exclusive scan
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* warp_buf, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_buf[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t w = lane < nw ? warp_buf[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        if (lane < nw) warp_buf[lane] = w;   // inclusive warp prefix
+    }
+    __syncthreads();
+    const uint32_t before = warp ? warp_buf[warp - 1] : 0;
+    if (total) *total = warp_buf[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* in, uint64_t n,
+                                                             uint32_t* block_sums) {
+    __shared__ uint32_t buf[32];
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t s = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < n) s += in[base + k];
+    uint32_t total;
+    block_excl_scan(s, buf, &total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// exclusive scan of up to SCAN_TILE values in one block
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(uint32_t* v, uint64_t n) {
+    __shared__ uint32_t buf[32];
+    const uint64_t base = (uint64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t x[SCAN_ITEMS], s = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        x[k] = base + k < n ? v[base + k] : 0;
+        s += x[k];
+    }
+    uint32_t run = block_excl_scan(s, buf, nullptr);
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) v[base + k] = run;
+        run += x[k];
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(uint32_t* v, uint64_t n,
+                                                            const uint32_t* block_prefix) {
+    __shared__ uint32_t buf[32];
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t x[SCAN_ITEMS], s = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        x[k] = base + k < n ? v[base + k] : 0;
+        s += x[k];
+    }
+    uint32_t run = block_excl_scan(s, buf, nullptr) + block_prefix[blockIdx.x];
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) v[base + k] = run;
+        run += x[k];
+    }
+}
+
+// in-place exclusive scan of n <= SCAN_TILE^2 values; scratch holds SCAN_TILE words
+static cudaError_t excl_scan(uint32_t* v, uint64_t n, uint32_t* scratch, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (blocks > SCAN_TILE) return cudaErrorInvalidValue;
+    if (blocks == 1) {
+        k_scan_single<<<1, SCAN_THREADS, 0, st>>>(v, n);
+        return cudaGetLastError();
+    }
+    k_scan_reduce<<<(unsigned)blocks, SCAN_THREADS, 0, st>>>(v, n, scratch);
+    k_scan_single<<<1, SCAN_THREADS, 0, st>>>(scratch, blocks);
+    k_scan_apply<<<(unsigned)blocks, SCAN_THREADS, 0, st>>>(v, n, scratch);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- radix pass
+
+__global__ void __launch_bounds__(SORT_THREADS) k_digit_hist(const uint64_t* __restrict__ keys,
+                                                            uint64_t n, int shift,
+                                                            uint32_t* __restrict__ hist,
+                                                            uint64_t tiles) {
+    __shared__ uint32_t cnt[256];
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) cnt[d] = 0;
+    __syncthreads();
+    const uint64_t base = (uint64_t)blockIdx.x * SORT_TILE;
+    for (int k = threadIdx.x; k < SORT_TILE; k += blockDim.x) {
+        const uint64_t i = base + k;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(uint64_t)d * tiles + blockIdx.x] = cnt[d];
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_digit_scatter(
+    const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+    uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint64_t n, int shift,
+    const uint32_t* __restrict__ offsets, uint64_t tiles) {
+    __shared__ uint32_t wpos[SORT_WARPS][257];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < SORT_WARPS * 257; i += blockDim.x) (&wpos[0][0])[i] = 0;
+    __syncthreads();
+    // this warp's 512 pairs, in input order: round r, lane l -> chunk + 32 r + l
+    const uint64_t chunk = (uint64_t)blockIdx.x * SORT_TILE + (uint64_t)warp * (SORT_ROUNDS * 32);
+    uint64_t k[SORT_ROUNDS];
+    uint32_t v[SORT_ROUNDS];
+    uint32_t d[SORT_ROUNDS];
+#pragma unroll
+    for (int r = 0; r < SORT_ROUNDS; ++r) {
+        const uint64_t i = chunk + 32 * r + lane;
+        if (i < n) {
+            k[r] = keys_in[i];
+            v[r] = vals_in[i];
+            d[r] = (uint32_t)((k[r] >> shift) & 255u);
+        } else {
+            d[r] = 256;  // past the end: counted nowhere
+        }
+    }
+    // per-warp digit counts
+#pragma unroll
+    for (int r = 0; r < SORT_ROUNDS; ++r) {
+        const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
+        if (d[r] < 256 && lane == __ffs(peers) - 1) wpos[warp][d[r]] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // turn counts into this warp's first output position per digit
+    for (int dg = threadIdx.x; dg < 256; dg += blockDim.x) {
+        uint32_t run = offsets[(uint64_t)dg * tiles + blockIdx.x];
+        for (int w = 0; w < SORT_WARPS; ++w) {
+            const uint32_t c = wpos[w][dg];
+            wpos[w][dg] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < SORT_ROUNDS; ++r) {
+        const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
+        uint32_t pos = 0;
+        if (d[r] < 256) {
+            pos = wpos[warp][d[r]] + __popc(peers & below);
+            keys_out[pos] = k[r];
+            vals_out[pos] = v[r];
+        }
+        __syncwarp();
+        if (d[r] < 256 && lane == __ffs(peers) - 1) wpos[warp][d[r]] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+uint64_t radix_sort_hist_words(uint64_t n) {
+    const uint64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    return 256 * (tiles ? tiles : 1) + SCAN_TILE;
+}
+
+cudaError_t radix_sort_pairs(uint64_t** keys, uint32_t** vals, uint64_t** tmp_keys,
+                             uint32_t** tmp_vals, uint32_t* hist, uint64_t n, int bits,
+                             cudaStream_t st) {
+    if (n <= 1 || bits <= 0) return cudaSuccess;
+    const uint64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    if (256 * tiles > (uint64_t)SCAN_TILE * SCAN_TILE) return cudaErrorInvalidValue;
+    uint32_t* scan_scratch = hist + 256 * tiles;
+    for (int shift = 0; shift < bits && shift < 64; shift += 8) {
+        k_digit_hist<<<(unsigned)tiles, SORT_THREADS, 0, st>>>(*keys, n, shift, hist, tiles);
+        cudaError_t e = excl_scan(hist, 256 * tiles, scan_scratch, st);
+        if (e != cudaSuccess) return e;
+        k_digit_scatter<<<(unsigned)tiles, SORT_THREADS, 0, st>>>(*keys, *vals, *tmp_keys, *tmp_vals, n,
+                                                                  shift, hist, tiles);
+        uint64_t* tk = *keys; *keys = *tmp_keys; *tmp_keys = tk;
+        uint32_t* tv = *vals; *vals = *tmp_vals; *tmp_vals = tv;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace tpk

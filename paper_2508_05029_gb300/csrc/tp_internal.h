@@ -1,0 +1,164 @@
+// Host-side state behind the C ABI: engine, page pool, budget, tables, plans
+// and results.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/theseus_gb.h"
+#include "kernels.cuh"
+
+namespace tp {
+
+// thread-local error message; returns code for tail calls
+tp_status fail(tp_status code, const char* fmt, ...);
+void clear_error();
+
+#define TP_TRY_CUDA(call)                                                             \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return ::tp::fail(TP_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+int type_size(int32_t type);
+
+// ------------------------------------------------------------- page pool
+// One page-locked allocation of n_pages * page_bytes made at engine init and
+// cut into equal pages; a free stack gives O(1) alloc/free (Section 3.4).
+struct PagePool {
+    uint8_t* base = nullptr;
+    uint64_t page_bytes = 0;
+    uint32_t n_pages = 0;
+    std::vector<uint32_t> free_stack;
+    std::vector<uint8_t> lent;
+    std::mutex mu;
+    int fail_next = 0;
+};
+
+// ----------------------------------------------------------------- budget
+// Reservations before execution (Section 3.3.2): a task states its device
+// bytes up front; a reservation that does not fit under the cap fails instead
+// of running into out-of-memory mid-way.
+struct Budget {
+    std::mutex mu;
+    std::condition_variable cv;
+    uint64_t cap = 0;
+    uint64_t reserved = 0;
+    uint64_t peak = 0;
+    int fail_next = 0;
+};
+
+// A contiguous piece of one column inside one page.
+struct Extent {
+    uint32_t page;
+    uint32_t pad;
+    uint64_t offset;   // bytes into the page
+    uint64_t bytes;
+};
+
+// One batch of a paged table: a row range whose columns lie back to back
+// across a run of pages.
+struct Batch {
+    uint64_t row0 = 0;
+    uint64_t rows = 0;
+    std::vector<std::vector<Extent>> cols;   // per column
+    std::vector<uint32_t> pages;
+};
+
+enum Placement : int32_t { PL_PAGES = TP_HOST_PAGES, PL_DEVICE = TP_DEVICE, PL_WRAPPED = 3 };
+
+}  // namespace tp
+
+struct tp_engine {
+    tp_config cfg{};
+    int device = 0;
+    int num_sms = 0;
+    tp::PagePool pool;
+    tp::Budget budget;
+    cudaStream_t compute = nullptr;
+    cudaStream_t copy = nullptr;
+    bool own_compute = false;
+    std::mutex exec_mu;          // one execution at a time on the engine streams
+    std::mutex obj_mu;
+    // statistics
+    std::atomic<uint64_t> h2d_bytes{0}, d2h_bytes{0}, batches{0}, launches{0}, retries{0};
+    // small pinned scratch for status words read back after an execution
+    uint64_t* host_words = nullptr;
+    // fused-kernel timing (TP_FLAG_TIME_KERNELS)
+    std::mutex time_mu;
+    double agg_ms = 0;
+    uint64_t agg_launches = 0, agg_rows = 0;
+};
+
+struct tp_table {
+    tp_engine* eng = nullptr;
+    std::vector<int32_t> types;
+    std::vector<int32_t> scales;
+    std::vector<std::string> names;
+    uint64_t batch_rows = 0;
+    uint64_t rows = 0;
+    int32_t placement = tp::PL_PAGES;
+    std::vector<tp::Batch> batches;
+    std::vector<void*> dev_cols;       // device / wrapped placement
+    uint64_t dev_reserved = 0;
+};
+
+struct tp_plan {
+    tp_engine* eng = nullptr;
+    tp_plan_desc d{};
+    int n_sum = 0;
+    int sum_of_agg[8];      // sum slot of each aggregate, -1 for COUNT
+    int key_bits = 0;       // total packed key width
+    int dim_bits = 0;
+    int gdpos[4];
+    int strategy = TP_AGG_SHARED;
+    float load_factor = 0.5f;
+    // execution history (Section 3.3.2: observed consumption refines later
+    // reservations)
+    uint64_t history_groups = 0;
+    double selectivity = -1.0;   // sampled filter pass rate, < 0 until measured
+};
+
+struct tp_result {
+    tp_engine* eng = nullptr;
+    uint64_t n_groups = 0;
+    int n_agg = 0;
+    int n_sum = 0;
+    int sum_of_agg[8];
+    bool is_avg[8];
+    void* dev = nullptr;            // one device allocation holding every array
+    uint64_t reserved = 0;
+    uint64_t* d_keys = nullptr;
+    int64_t* d_counts = nullptr;
+    uint64_t* d_sums[8] = {};
+    double* d_avgs[8] = {};
+    // host copies, filled on first access
+    std::mutex mu;
+    std::vector<uint64_t> h_keys;
+    std::vector<int64_t> h_counts;
+    std::vector<std::vector<tp_i128>> h_sums;
+    std::vector<std::vector<double>> h_avgs;
+    bool have_keys = false, have_counts = false;
+    std::vector<bool> have_sum, have_avg;
+};
+
+namespace tp {
+
+// budget helpers
+tp_status reserve(tp_engine* e, uint64_t bytes);
+void release(tp_engine* e, uint64_t bytes);
+// device memory (stream-ordered allocator on the compute stream)
+tp_status dev_alloc(tp_engine* e, void** p, uint64_t bytes, cudaStream_t st);
+void dev_free(tp_engine* e, void* p, cudaStream_t st);
+
+}  // namespace tp

@@ -1,0 +1,205 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Sizes span several tiles and a ragged tail; the full-size star workload
+(60M fact rows, 2M-row dimension) is checked against the oracle too."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+from datagen import workloads as W
+from paper_2508_05029_gb300 import theseus as T
+from tests.helpers import assert_matches_oracle
+from tests.test_oracle_pins import _tiny
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_2508_05029_gb300 import build
+    build.build()
+    e = T.Engine(page_bytes=4 << 20, n_pages=512, batch_rows=1 << 20)
+    yield e
+    e.close()
+
+
+def run_gpu(eng, fact, dim, query, placement=T.TP_DEVICE, batch_rows=0, **plan_kw):
+    ft = eng.table_from_numpy(fact, placement=placement, batch_rows=batch_rows)
+    dt = eng.table_from_numpy(dim, placement=placement, batch_rows=batch_rows) if dim is not None else None
+    try:
+        p = eng.plan(ft, dt, query, **plan_kw)
+        try:
+            return p.execute()
+        finally:
+            p.destroy()
+    finally:
+        ft.destroy()
+        if dt is not None:
+            dt.destroy()
+
+
+def check(eng, fact, dim, query, **kw):
+    ref = oracle.run_query(fact, dim, query)
+    with run_gpu(eng, fact, dim, query, **kw) as res:
+        assert_matches_oracle(res, ref, query["aggs"])
+    return ref
+
+
+def test_config1_full_size(eng):
+    wl = W.config1()
+    ref = check(eng, wl.fact, wl.dim, wl.query)
+    assert ref.n_groups == 150
+
+
+@pytest.mark.parametrize("n_fact,n_dim", [(1, 1), (127, 10), (128, 100), (129, 100), (1000, 1),
+                                          (65_537, 10_000), (300_001, 777)])
+def test_config1_ragged(eng, n_fact, n_dim):
+    wl = W.config1(n_fact=n_fact, n_dim=n_dim)
+    check(eng, wl.fact, wl.dim, wl.query)
+
+
+@pytest.mark.parametrize("which,strategy", [("a", T.TP_AGG_AUTO), ("a", T.TP_AGG_GLOBAL),
+                                            ("b", T.TP_AGG_AUTO), ("b2", T.TP_AGG_AUTO)])
+def test_config2_small(eng, which, strategy):
+    wl = W.config2(which, n_fact=3_000_017, n_dim=300_000)
+    check(eng, wl.fact, wl.dim, wl.query, agg_strategy=strategy)
+
+
+def test_torch_wrapped_columns(eng):
+    import torch
+    wl = W.config1(n_fact=500_003)
+    ref = oracle.run(wl)
+    ft = eng.table_from_torch({k: torch.from_numpy(v).cuda() for k, v in wl.fact.items()})
+    dt = eng.table_from_torch({k: torch.from_numpy(v).cuda() for k, v in wl.dim.items()})
+    p = eng.plan(ft, dt, wl.query)
+    for _ in range(2):   # second run reuses the plan's sampled selectivity
+        with p.execute() as res:
+            assert_matches_oracle(res, ref, wl.query["aggs"])
+    p.destroy()
+    ft.destroy()
+    dt.destroy()
+
+
+@pytest.mark.parametrize("batch_rows", [65_536, 99_991, 1_000_000])
+def test_paged_streaming(eng, batch_rows):
+    wl = W.config1(n_fact=2_000_003, n_dim=10_000)
+    check(eng, wl.fact, wl.dim, wl.query, placement=T.TP_HOST_PAGES, batch_rows=batch_rows)
+
+
+@pytest.mark.parametrize("depth", [0, 1, 4])
+def test_prefetch_depths_agree(depth):
+    wl = W.config1(n_fact=700_001, n_dim=5_000)
+    ref = oracle.run(wl)
+    e = T.Engine(page_bytes=1 << 20, n_pages=256, batch_rows=50_000, prefetch_depth=depth)
+    try:
+        with run_gpu(e, wl.fact, wl.dim, wl.query, placement=T.TP_HOST_PAGES) as res:
+            assert_matches_oracle(res, ref, wl.query["aggs"])
+        st = e.stats()
+        assert st["batches"] == 15 and st["h2d_bytes"] > 0
+    finally:
+        e.close()
+
+
+def test_int64_keys_and_sparse_pk(eng):
+    dim = W.config3_dim(n_dim=100_000)
+    fact = W.config3_fact(0, 1_000_003, n_dim=100_000)
+    q = W.q_lowcard()
+    check(eng, fact, dim, q)
+    check(eng, fact, dim, q, placement=T.TP_HOST_PAGES, batch_rows=300_000)
+
+
+@pytest.mark.parametrize("seed,n_fact,n_dim,span,cutoff", [
+    (0, 2000, 200, 250, W.CUTOFF_98), (1, 1500, 150, 150, W.N_DAYS - 1), (2, 1000, 100, 400, 1000),
+    (3, 777, 1, 2, 2000), (4, 500, 120, 120, -1), (5, 0, 50, 50, W.CUTOFF_98), (6, 300, 0, 10, W.CUTOFF_98)])
+def test_tiny_cases(eng, seed, n_fact, n_dim, span, cutoff):
+    fact, dim = _tiny(seed, n_fact, n_dim, span)
+    q = W.q_lowcard(cutoff)
+    check(eng, fact, dim, q)
+    check(eng, fact, dim, q, agg_strategy=T.TP_AGG_GLOBAL)
+
+
+def test_other_query_shapes(eng):
+    fact, dim = _tiny(8, 50_000, 600, 800, signed=True)
+    queries = [
+        dict(filter=None, join=dict(fact_col="fk", dim_col="pk"), group=[("dim", "attr", 5)],
+             aggs=[("sum", "price"), ("avg", "qty"), ("sum_mul_sub", "qty", -7, "price")]),
+        dict(filter=dict(col="date", lo=300, hi=2000), join=None,
+             group=[("fact", "flag", 2), ("fact", "status", 1)],
+             aggs=[("sum_mul_sub", "price", 100, "disc"), ("count",), ("avg", "price")]),
+        dict(filter=None, join=None, group=[], aggs=[("sum", "qty"), ("count",)]),
+        dict(filter=None, join=dict(fact_col="fk", dim_col="pk"), group=[("fact", "qty", 64)],
+             aggs=[("count",)]),
+        dict(filter=dict(col="qty", lo=-100, hi=2500), join=dict(fact_col="fk", dim_col="pk"),
+             group=[("dim", "attr", 5), ("fact", "flag", 2)], aggs=[("count",), ("avg", "disc")]),
+    ]
+    for q in queries:
+        check(eng, fact, dim, q)
+        check(eng, fact, dim, q, agg_strategy=T.TP_AGG_GLOBAL)
+
+
+def test_sentinel_keys(eng):
+    """Keys equal to the all-ones empty-slot pattern: join key -1 (32- and
+    64-bit tables) and a packed group key of 2^64-1."""
+    n = 10_000
+    for kt in (np.int32, np.int64):
+        dim = dict(pk=np.array([-1, 0, 5, 7], kt), attr=np.array([3, 1, 2, 4], np.int32))
+        fk = datagen.uniform(3, 1, np.int64, n, -2, 8).astype(kt)
+        fact = dict(fk=fk, qty=datagen.uniform(3, 2, np.int64, n, -1000, 1000),
+                    g=datagen.uniform(3, 3, np.int64, n, -2, 1))
+        q = dict(filter=None, join=dict(fact_col="fk", dim_col="pk"),
+                 group=[("fact", "g", 64)], aggs=[("sum", "qty"), ("count",)])
+        check(eng, fact, dim, q)
+        q2 = dict(q, group=[("dim", "attr", 3)])
+        check(eng, fact, dim, q2)
+
+
+def test_errors(eng):
+    fact, dim = _tiny(9, 5_000, 200, 200)
+    bad = dict(dim)
+    bad["pk"] = dim["pk"].copy()
+    bad["pk"][5] = bad["pk"][6]
+    with pytest.raises(T.TPError) as e:
+        run_gpu(eng, fact, bad, W.q_lowcard())
+    assert e.value.status == "dup_key"
+    with pytest.raises(T.TPError) as e:
+        run_gpu(eng, fact, dim, W.q_lowcard(cutoff=W.N_DAYS - 1, attr_bits=4))
+    assert e.value.status == "range"
+    # an out-of-range attribute on a dimension row no fact row reaches is fine
+    dim2 = {k: v.copy() for k, v in dim.items()}
+    fact2 = {k: v.copy() for k, v in fact.items()}
+    fact2["fk"][fact2["fk"] == dim2["pk"][0]] = dim2["pk"][1]
+    dim2["attr"][0] = 99
+    check(eng, fact2, dim2, W.q_lowcard())
+
+
+def test_repeat_is_deterministic(eng):
+    wl = W.config2("b2", n_fact=1_000_000, n_dim=100_000)
+    ft = eng.table_from_numpy(wl.fact, placement=T.TP_DEVICE)
+    dt = eng.table_from_numpy(wl.dim, placement=T.TP_DEVICE)
+    p = eng.plan(ft, dt, wl.query)
+    outs = []
+    for _ in range(3):
+        with p.execute() as r:
+            outs.append((r.keys(), r.counts(), r.sum_words(0)))
+    for o in outs[1:]:
+        for x, y in zip(outs[0], o):
+            assert np.array_equal(x, y)
+    p.destroy()
+    ft.destroy()
+    dt.destroy()
+
+
+def test_budget_refusal_and_release(eng):
+    wl = W.config1(n_fact=100_000)
+    used0, cap0 = eng.budget()
+    eng.set_budget(used0 + 1000)
+    try:
+        with pytest.raises(T.TPError) as e:
+            run_gpu(eng, wl.fact, wl.dim, wl.query, placement=T.TP_HOST_PAGES)
+        assert e.value.status == "budget"
+    finally:
+        eng.set_budget(cap0)
+    assert eng.budget()[0] == used0
+    check(eng, wl.fact, wl.dim, wl.query)
+    assert eng.budget()[0] == used0
