@@ -299,6 +299,55 @@ tp_status tp_stats_get(tp_engine* eng, tp_stats* out);
  * reservations fail as if exhausted. */
 tp_status tp_debug_fail_next_alloc(tp_engine* eng, int32_t n);
 
+/* ------------------------------------------------------ allocation-free call */
+
+/*
+ * tp_execute_noalloc -- the paper has no counterpart to this call; it exists
+ * for callers that cannot allocate device memory while they run a query:
+ * applications that have given all GPU memory to their own allocator (a
+ * database buffer pool, PyTorch's caching allocator) and forbid side
+ * allocations, or latency-bound code that cannot afford a cudaMalloc or
+ * cudaFree, which may synchronise the device or fail under fragmentation.
+ *
+ * It runs the same filter -> join -> low-cardinality group-by as tp_execute,
+ * on caller-owned device columns and into caller-owned device outputs, and
+ * allocates nothing: no engine, no cudaMalloc/cudaFree, no host heap.  Its
+ * scratch (join hash table, per-group accumulators, status words) is one
+ * fixed device array of 8,945,920 bytes inside this library, which every GPU
+ * that loads the library holds until the process exits.
+ *
+ *   d            query; d->fact and d->dim are ignored, column indices refer
+ *                to fact_cols / dim_cols.  join.fact_col < 0 means no join.
+ *   fact_cols    n_fact_cols device pointers (16-byte aligned), n_fact rows,
+ *                types TP_I32 / TP_I64 / TP_U8 in fact_types (host array).
+ *   dim_cols     n_dim_cols device pointers, n_dim rows (join only).
+ *   keys, counts device arrays of 2^(total group bits) entries (the most
+ *                groups there can be); groups are written ascending by key.
+ *   sums[a]      device tp_i128 array of the same length for every SUM,
+ *                SUM_MUL_SUB and AVG aggregate a (other entries ignored).
+ *   avgs[a]      device double array for every AVG aggregate a.
+ *   n_groups     host; receives the number of groups written.
+ *   stream       cudaStream_t (as void*) of the current device; the call
+ *                synchronises it before returning.
+ *
+ * Limits (TP_E_INVALID with a message beyond them): a group key of at most
+ * 12 bits; a join table of at most 2^20 slots for 32-bit keys (2^19 for
+ * 64-bit keys), i.e. at most ceil(0.5 * 2^20) = 524,288 dimension rows at the
+ * default load factor 0.5.  Other errors as tp_execute (TP_E_DUP_KEY,
+ * TP_E_RANGE, TP_E_CUDA).
+ *
+ * The first call on a device looks up the scratch array's device address
+ * with that device current; make that first call before any stream capture.
+ * Every call reuses the array and clears what must start at zero; calls
+ * whose GPU work overlaps (other streams or host threads) race on it, so the
+ * caller must serialise them.
+ */
+tp_status tp_execute_noalloc(const tp_plan_desc* d, const void* const* fact_cols, const int32_t* fact_types,
+                             int32_t n_fact_cols, uint64_t n_fact, const void* const* dim_cols,
+                             const int32_t* dim_types, int32_t n_dim_cols, uint64_t n_dim, uint64_t* keys,
+                             int64_t* counts, tp_i128* const* sums, double* const* avgs, uint64_t* n_groups,
+                             void* stream);
+
 #ifdef __cplusplus
 }
 #endif

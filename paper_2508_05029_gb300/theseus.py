@@ -134,6 +134,9 @@ SIGNATURES = {
     "tp_last_error": (ctypes.c_char_p, []),
     "tp_stats_get": (_i32, [_vp, ctypes.POINTER(tp_stats)]),
     "tp_debug_fail_next_alloc": (_i32, [_vp, _i32]),
+    "tp_execute_noalloc": (_i32, [ctypes.POINTER(tp_plan_desc), _PP, ctypes.POINTER(_i32), _i32, _u64, _PP,
+                                  ctypes.POINTER(_i32), _i32, _u64, _vp, _vp, _PP, _PP, ctypes.POINTER(_u64),
+                                  _vp]),
 }
 
 
