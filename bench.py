@@ -45,7 +45,7 @@ METRIC = "fact rows/s & HBM GB/s (join+agg); served p50/p99 latency vs plain"
 WORKLOAD = "star-60M-lowcard"
 BYTES_PER_FACT_ROW = 4 + 4 + 8 + 8 + 8 + 1 + 1      # date, fk, qty, price, disc, flag, status
 BYTES_PER_DIM_ROW = 4 + 4                            # pk, attr
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "agg_shared_star60M.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_agg_shared_star12M.md")
 
 
 def parse_args():
