@@ -88,8 +88,12 @@ enum { TP_AGG_AUTO = 0, TP_AGG_SHARED = 1, TP_AGG_GLOBAL = 2 };
  *                         filter/probe/aggregate launch with CUDA events on
  *                         the compute stream and accumulate its device time
  *                         in tp_stats (agg_kernel_ms, agg_kernel_launches).
+ *                         TP_FLAG_NO_STAGED: never use the bulk-copy staged
+ *                         kernels (plain-load kernels only).
+ *                         TP_FLAG_EXACT_ONLY: never use 64-bit accumulation,
+ *                         even where column bounds prove it cannot overflow.
  */
-enum { TP_FLAG_TIME_KERNELS = 1 };
+enum { TP_FLAG_TIME_KERNELS = 1, TP_FLAG_NO_STAGED = 2, TP_FLAG_EXACT_ONLY = 4 };
 typedef struct {
     uint64_t page_bytes;
     uint32_t n_pages;

@@ -6,7 +6,9 @@
 // column may span several; a small unused tail per batch), Section 3.3.2
 // (tasks reserve memory before executing), Section 3.1 (batches are row
 // slices of all columns).
+#include <algorithm>
 #include <cstdarg>
+#include <climits>
 #include <cstdio>
 #include <cstdlib>
 
@@ -242,6 +244,8 @@ static tp_table* new_table(tp_engine* e, const tp_table_desc* d) {
         t->scales.push_back(d->cols[i].scale);
         t->names.push_back(d->cols[i].name ? d->cols[i].name : "");
     }
+    t->cmin.assign(d->n_cols, INT64_MAX);
+    t->cmax.assign(d->n_cols, INT64_MIN);
     return t;
 }
 
@@ -309,6 +313,29 @@ tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) 
         }
         t->batches.push_back(std::move(b));
     }
+    // column bounds of the appended rows
+    for (int c = 0; c < nc && nrows; ++c) {
+        int64_t lo = t->cmin[c], hi = t->cmax[c];
+        switch (t->types[c]) {
+        case TP_I32: {
+            const int32_t* v = (const int32_t*)cols[c];
+            for (uint64_t i = 0; i < nrows; ++i) { lo = std::min<int64_t>(lo, v[i]); hi = std::max<int64_t>(hi, v[i]); }
+            break;
+        }
+        case TP_I64: {
+            const int64_t* v = (const int64_t*)cols[c];
+            for (uint64_t i = 0; i < nrows; ++i) { lo = std::min(lo, v[i]); hi = std::max(hi, v[i]); }
+            break;
+        }
+        default: {
+            const uint8_t* v = (const uint8_t*)cols[c];
+            for (uint64_t i = 0; i < nrows; ++i) { lo = std::min<int64_t>(lo, v[i]); hi = std::max<int64_t>(hi, v[i]); }
+            break;
+        }
+        }
+        t->cmin[c] = lo;
+        t->cmax[c] = hi;
+    }
     t->rows += nrows;
     return TP_OK;
 }
@@ -374,12 +401,39 @@ tp_status tp_table_wrap_device(tp_engine* e, const tp_table_desc* d, const void*
     for (int c = 0; c < d->n_cols; ++c)
         if (nrows && (!dev_cols[c] || ((uintptr_t)dev_cols[c] & 15u)))
             return fail(TP_E_INVALID, "tp_table_wrap_device: column %d is NULL or not 16-byte aligned", c);
-    tp_table* t = new_table(e, d);
+    std::unique_ptr<tp_table> t(new_table(e, d));
     if (!t) return fail(TP_E_NOMEM, "tp_table_wrap_device: out of host memory");
     t->rows = nrows;
     t->placement = PL_WRAPPED;
     for (int c = 0; c < d->n_cols; ++c) t->dev_cols.push_back(const_cast<void*>(dev_cols[c]));
-    *out = t;
+    if (nrows) {  // column bounds, one reduction per column
+        std::lock_guard<std::mutex> lk(e->exec_mu);
+        TP_TRY_CUDA(cudaSetDevice(e->device));
+        long long* h = (long long*)e->host_words;
+        for (int c = 0; c < d->n_cols; ++c) {
+            h[2 * c] = LLONG_MAX;
+            h[2 * c + 1] = LLONG_MIN;
+        }
+        void* dmm = nullptr;
+        tp_status s2 = dev_alloc(e, &dmm, 16 * d->n_cols, e->compute);
+        if (s2) return s2;
+        TP_TRY_CUDA(cudaMemcpyAsync(dmm, h, 16 * d->n_cols, cudaMemcpyHostToDevice, e->compute));
+        for (int c = 0; c < d->n_cols; ++c) {
+            tpk::DevCol col{};
+            col.ptr = dev_cols[c];
+            col.type = d->cols[c].type;
+            TP_TRY_CUDA(tpk::launch_minmax(col, nrows, (long long*)dmm + 2 * c, e->num_sms, e->compute));
+            e->launches++;
+        }
+        TP_TRY_CUDA(cudaMemcpyAsync(h, dmm, 16 * d->n_cols, cudaMemcpyDeviceToHost, e->compute));
+        dev_free(e, dmm, e->compute);
+        TP_TRY_CUDA(cudaStreamSynchronize(e->compute));
+        for (int c = 0; c < d->n_cols; ++c) {
+            t->cmin[c] = h[2 * c];
+            t->cmax[c] = h[2 * c + 1];
+        }
+    }
+    *out = t.release();
     return TP_OK;
 }
 

@@ -349,6 +349,56 @@ tp_status sample_selectivity(ExecState& S) {
     return TP_OK;
 }
 
+// True when column bounds prove that every sum of the query stays inside
+// int64 over all n fact rows, so kernels may accumulate 64-bit values without
+// carry handling.  |a| <= A and |K - b| <= D give |term| <= A * D < 2^127.
+bool sums_fit_int64(const tp_plan* p, const tp_table* fact) {
+    const uint64_t n = fact->rows;
+    if (n == 0) return true;
+    if (n >= (1ull << 32)) return false;   // per-CTA 32-bit counts
+    const tp_plan_desc& d = p->d;
+    typedef __int128 i128;
+    auto mag = [](i128 v) { return v < 0 ? -v : v; };
+    const i128 limit = ((i128)1 << 63) - 1;
+    for (int a = 0; a < d.n_agg; ++a) {
+        const tp_agg& ag = d.aggs[a];
+        if (ag.kind == TP_AGG_COUNT) continue;
+        const i128 A = std::max(mag(fact->cmin[ag.col_a]), mag(fact->cmax[ag.col_a]));
+        i128 B = A;
+        if (ag.kind == TP_AGG_SUM_MUL_SUB) {
+            const i128 D = std::max(mag((i128)ag.k - fact->cmin[ag.col_b]), mag((i128)ag.k - fact->cmax[ag.col_b]));
+            if (D > limit) return false;
+            B = A * D;
+        }
+        if (B > limit / (i128)n) return false;
+    }
+    return true;
+}
+
+// Per-row term range of every sum slot, from column statistics.
+void term_bounds(const tp_plan* p, const tp_table* fact, tpk::TermBounds* out) {
+    const tp_plan_desc& d = p->d;
+    typedef __int128 i128;
+    for (int a = 0; a < d.n_agg; ++a) {
+        const int s = p->sum_of_agg[a];
+        if (s < 0) continue;
+        const tp_agg& ag = d.aggs[a];
+        i128 lo = fact->cmin[ag.col_a], hi = fact->cmax[ag.col_a];
+        if (ag.kind == TP_AGG_SUM_MUL_SUB) {
+            const i128 d0 = (i128)ag.k - fact->cmax[ag.col_b], d1 = (i128)ag.k - fact->cmin[ag.col_b];
+            const i128 c[4] = {lo * d0, lo * d1, hi * d0, hi * d1};
+            lo = hi = c[0];
+            for (int i = 1; i < 4; ++i) {
+                lo = c[i] < lo ? c[i] : lo;
+                hi = c[i] > hi ? c[i] : hi;
+            }
+        }
+        // only used when sums_fit_int64 holds, so both ends fit in int64
+        out[s].lo = (int64_t)lo;
+        out[s].span = (uint64_t)(hi - lo);
+    }
+}
+
 tp_status map_err(uint32_t err) {
     if (err & tpk::ERR_DUP) return fail(TP_E_DUP_KEY, "join build side holds a duplicate key");
     if (err & tpk::ERR_RANGE) return fail(TP_E_RANGE, "a group field value does not fit its bit width");
@@ -504,8 +554,34 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
         if ((s = sc.alloc(&gacc, gbytes))) return s;
         TP_TRY_CUDA(cudaMemsetAsync(gacc, 0, gbytes, st));
         const int grid = tpk::agg_shared_grid(p->key_bits, ns, e->num_sms);
+        const bool want_staged = !(e->cfg.flags & TP_FLAG_NO_STAGED);
+        bool fast = want_staged && !(e->cfg.flags & TP_FLAG_EXACT_ONLY) && sums_fit_int64(p, S.fact);
+        tpk::TermBounds bounds[tpk::MAX_SUM] = {};
+        if (fast) term_bounds(p, S.fact, bounds);
+        int mode = -1;  // 0 plain exact, 1 staged exact, 2 staged 64-bit
         s = for_each_batch(S, sc, [&](const tpk::QueryDev& q, uint64_t rows) {
+            tpk::StageLayout L;
+            bool can = want_staged && tpk::staged_layout_shared(q, p->key_bits, mode != 1 && fast, bounds, rows,
+                                                                e->num_sms, &L);
+            if (mode < 0 && !can && fast) {  // no 32-bit table fits: exact staged table instead
+                fast = false;
+                can = want_staged && tpk::staged_layout_shared(q, p->key_bits, false, bounds, rows, e->num_sms, &L);
+            }
+            if (mode < 0) mode = can ? (fast ? 2 : 1) : 0;
+            if (mode == 2 && !can) return fail(TP_E_INTERNAL, "staged layout changed between batches");
             mark_launch(e);
+            if (mode > 0 && can) {
+                const uint64_t whole = rows / tpk::ST_TILE * tpk::ST_TILE;
+                tp_status r = cuda_check(timer.run(st, whole, [&] {
+                    return tpk::launch_agg_shared_staged(q, L, rows, (uint64_t*)gacc, p->key_bits, mode == 2,
+                                                         e->num_sms, st);
+                }), "aggregate");
+                if (r || whole == rows) return r;
+                mark_launch(e);  // rows after the last whole tile
+                const tpk::QueryDev qt = tpk::offset_rows(q, whole);
+                return cuda_check(tpk::launch_agg_shared(qt, rows - whole, (uint64_t*)gacc, p->key_bits, grid, st),
+                                  "aggregate tail");
+            }
             return cuda_check(timer.run(st, rows, [&] {
                 return tpk::launch_agg_shared(q, rows, (uint64_t*)gacc, p->key_bits, grid, st);
             }), "aggregate");
@@ -514,7 +590,7 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
         tpk::OutDev od;
         if ((s = alloc_result(e, p, G, &res, &od, S.counters + 1))) return s;
         std::unique_ptr<tp_result, void (*)(tp_result*)> guard(res, tp_result_free);
-        TP_TRY_CUDA(tpk::launch_final_dense((const uint64_t*)gacc, p->key_bits, ns, od, st));
+        TP_TRY_CUDA(tpk::launch_final_dense((const uint64_t*)gacc, p->key_bits, ns, od, st, mode == 2));
         mark_launch(e);
         TP_TRY_CUDA(cudaMemcpyAsync(e->host_words, misc, 8, cudaMemcpyDeviceToHost, st));
         TP_TRY_CUDA(cudaMemcpyAsync(e->host_words + 1, S.counters + 1, 8, cudaMemcpyDeviceToHost, st));
@@ -525,6 +601,15 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
         timer.collect();
         guard.release();
     } else {
+        // staged kernel unless disabled; all columns staged unless the filter is
+        // selective; runs folded when the key comes from fact columns only; 64-bit
+        // low-word updates when column bounds rule out overflow (any mix of the
+        // staged and plain kernels then agrees on the low words)
+        const bool g_staged = !(e->cfg.flags & TP_FLAG_NO_STAGED);
+        const bool gfast = g_staged && !(e->cfg.flags & TP_FLAG_EXACT_ONLY) && sums_fit_int64(p, S.fact);
+        const bool stage_all = p->selectivity >= 0.25;
+        bool fold = d.n_group > 0;
+        for (int g = 0; g < d.n_group; ++g) fold = fold && d.group[g].side == TP_SIDE_FACT;
         for (int attempt = 0;; ++attempt) {
             void* tab = nullptr;
             const uint64_t tbytes = (agg_cap + 1) * words * 8;
@@ -540,6 +625,17 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
             at.max_used = (uint64_t)(agg_cap * 0.9);
             s = for_each_batch(S, sc, [&](const tpk::QueryDev& q, uint64_t rows) {
                 mark_launch(e);
+                tpk::StageLayout L;
+                if (g_staged && tpk::staged_layout_global(q, stage_all, &L)) {
+                    const uint64_t whole = rows / tpk::ST_TILE * tpk::ST_TILE;
+                    tp_status r = cuda_check(timer.run(st, whole, [&] {
+                        return tpk::launch_agg_global_staged(q, L, rows, at, gfast, fold, e->num_sms, st);
+                    }), "aggregate");
+                    if (r || whole == rows) return r;
+                    mark_launch(e);  // rows after the last whole tile
+                    return cuda_check(tpk::launch_agg_global(tpk::offset_rows(q, whole), rows - whole, at,
+                                                             e->num_sms, st), "aggregate tail");
+                }
                 return cuda_check(timer.run(st, rows, [&] {
                     return tpk::launch_agg_global(q, rows, at, e->num_sms, st);
                 }), "aggregate");
@@ -591,7 +687,7 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
             e->launches += 3 * ((bits + 7) / 8);
             tpk::OutDev od;
             if ((s = alloc_result(e, p, n, &res, &od, S.counters + 1))) return s;
-            TP_TRY_CUDA(tpk::launch_gather_global(at, kk, vv, n, ns, od, e->num_sms, st));
+            TP_TRY_CUDA(tpk::launch_gather_global(at, kk, vv, n, ns, od, e->num_sms, st, gfast));
             mark_launch(e);
             TP_TRY_CUDA(cudaStreamSynchronize(st));
             res->n_groups = n;

@@ -10,263 +10,9 @@
 // holds rows {2l, 2l+1, 64+2l, 64+2l+1}, so every column is read with two
 // fully coalesced vector loads per lane whatever its width (8-bit: 2 bytes,
 // 32-bit: 8 bytes, 64-bit: 16 bytes per load).
-#include "kernels.cuh"
+#include "device.cuh"
 
 namespace tpk {
-
-__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
-    k ^= k >> 33;
-    k *= 0xff51afd7ed558ccdull;
-    k ^= k >> 33;
-    k *= 0xc4ceb9fe1a85ec53ull;
-    k ^= k >> 33;
-    return k;
-}
-
-// ------------------------------------------------------------------ loads
-
-__device__ __forceinline__ int64_t ld1(const DevCol& c, uint64_t i) {
-    switch (c.type) {
-    case T_I32: return __ldcs((const int*)c.ptr + i);
-    case T_I64: return __ldcs((const long long*)c.ptr + i);
-    default: return (int64_t)__ldcs((const unsigned char*)c.ptr + i);
-    }
-}
-
-// rows r, r+1, r+64, r+65 of a full tile (r even)
-__device__ __forceinline__ void ld4(const DevCol& c, uint64_t r, int64_t v[4]) {
-    switch (c.type) {
-    case T_I32: {
-        const int2* p = reinterpret_cast<const int2*>((const int32_t*)c.ptr + r);
-        int2 a = __ldcs(p), b = __ldcs(p + 32);
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-        break;
-    }
-    case T_I64: {
-        const longlong2* p = reinterpret_cast<const longlong2*>((const int64_t*)c.ptr + r);
-        longlong2 a = __ldcs(p), b = __ldcs(p + 32);
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-        break;
-    }
-    default: {
-        const uchar2* p = reinterpret_cast<const uchar2*>((const uint8_t*)c.ptr + r);
-        uchar2 a = __ldcs(p), b = __ldcs(p + 32);
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-        break;
-    }
-    }
-}
-
-template <bool FULL>
-__device__ __forceinline__ void load_rows(const DevCol& c, uint64_t r, uint64_t n, const bool want[4],
-                                          int64_t v[4]) {
-    if (FULL) {
-        ld4(c, r, v);
-    } else {
-        const uint64_t rows[4] = {r, r + 1, r + 64, r + 65};
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = (want[i] && rows[i] < n) ? ld1(c, rows[i]) : 0;
-    }
-}
-
-// ------------------------------------------------------------- 128-bit sums
-
-struct I128 {
-    uint64_t lo;
-    uint64_t hi;
-};
-
-__device__ __forceinline__ I128 i128_from_i64(int64_t v) {
-    return I128{(uint64_t)v, (uint64_t)(v >> 63)};
-}
-
-__device__ __forceinline__ I128 i128_add(I128 a, I128 b) {
-    I128 r;
-    r.lo = a.lo + b.lo;
-    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
-    return r;
-}
-
-// a * (k - b) for 64-bit a, b, k: exact, since |a| < 2^63 and |k - b| < 2^64
-// keep the product below 2^127 in magnitude.
-__device__ __forceinline__ I128 mul_sub(int64_t a, int64_t k, int64_t b) {
-    __int128 d = (__int128)k - (__int128)b;
-    __int128 p = (__int128)a * d;
-    return I128{(uint64_t)p, (uint64_t)((unsigned __int128)p >> 64)};
-}
-
-// Adds t to the 128-bit value (lo, hi) with two 64-bit atomics: the carry out
-// of each low-word addition follows from the value the atomic returned, so the
-// high word receives exactly the sum of all carries plus all high words.
-__device__ __forceinline__ void atomic_add_i128(uint64_t* lo, uint64_t* hi, I128 t) {
-    unsigned long long old = atomicAdd((unsigned long long*)lo, (unsigned long long)t.lo);
-    uint64_t h = t.hi + ((old + t.lo) < old ? 1ull : 0ull);
-    if (h != 0) atomicAdd((unsigned long long*)hi, (unsigned long long)h);
-}
-
-// ------------------------------------------------------------------ probing
-
-// Looks up four keys at once so their table loads overlap.  pass[i] is
-// cleared for rows whose key is absent.
-__device__ __forceinline__ void probe4(const JoinTable& jt, const int64_t key[4], bool pass[4],
-                                       uint32_t payload[4], uint32_t* err) {
-    uint64_t slot[4];
-    bool act[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        act[i] = pass[i];
-        payload[i] = 0;
-        if (!act[i]) continue;
-        bool special;
-        if (jt.key64) {
-            special = (uint64_t)key[i] == EMPTY64;
-        } else {
-            if (key[i] < INT32_MIN || key[i] > INT32_MAX) {  // cannot match a 32-bit key
-                pass[i] = false;
-                act[i] = false;
-                continue;
-            }
-            special = (uint32_t)key[i] == EMPTY32;
-        }
-        if (special) {
-            pass[i] = __ldg(jt.side) != 0;
-            payload[i] = __ldg(jt.side + 1);
-            act[i] = false;
-            continue;
-        }
-        slot[i] = fmix64((uint64_t)key[i]) & jt.mask;
-    }
-    for (uint64_t it = 0; it <= jt.mask; ++it) {
-        bool any = false;
-        if (!jt.key64) {
-            uint64_t w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (act[i]) w[i] = __ldg((const unsigned long long*)jt.slots + slot[i]);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (!act[i]) continue;
-                uint32_t wk = (uint32_t)w[i];
-                if (wk == (uint32_t)key[i]) {
-                    payload[i] = (uint32_t)(w[i] >> 32);
-                    act[i] = false;
-                } else if (wk == EMPTY32) {
-                    pass[i] = false;
-                    act[i] = false;
-                } else {
-                    slot[i] = (slot[i] + 1) & jt.mask;
-                    any = true;
-                }
-            }
-        } else {
-            ulonglong2 w[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (act[i]) w[i] = __ldg((const ulonglong2*)jt.slots + slot[i]);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (!act[i]) continue;
-                if (w[i].x == (uint64_t)key[i]) {
-                    payload[i] = (uint32_t)w[i].y;
-                    act[i] = false;
-                } else if (w[i].x == EMPTY64) {
-                    pass[i] = false;
-                    act[i] = false;
-                } else {
-                    slot[i] = (slot[i] + 1) & jt.mask;
-                    any = true;
-                }
-            }
-        }
-        if (!any) return;
-    }
-    atomicOr(err, ERR_INTERNAL);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        if (act[i]) pass[i] = false;
-}
-
-// ------------------------------------------------------------ tile pipeline
-//
-// A lane evaluates its four rows in phases so that only the row state (pass
-// bits and packed keys) stays live across phases: filter, then join probe,
-// then the group key, then each aggregate column in turn, fed straight into
-// the accumulators.
-
-__device__ __forceinline__ bool any4(const bool p[4]) { return p[0] || p[1] || p[2] || p[3]; }
-
-// Filter, join and key packing of the lane's four rows in warp tile t0.
-// Returns false when no row of the lane survives.
-template <bool FULL>
-__device__ __forceinline__ bool eval_keys(const QueryDev& q, uint64_t t0, uint64_t n, int lane,
-                                          bool pass[4], uint64_t key[4]) {
-    const uint64_t r = t0 + 2ull * (uint64_t)lane;
-    const uint64_t rows[4] = {r, r + 1, r + 64, r + 65};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) pass[i] = FULL || rows[i] < n;
-    int64_t v[4];
-    if (q.has_filter) {
-        load_rows<FULL>(q.fcol, r, n, pass, v);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) pass[i] = pass[i] && v[i] >= q.flo && v[i] <= q.fhi;
-        if (!any4(pass)) return false;
-    }
-    uint32_t payload[4] = {0, 0, 0, 0};
-    if (q.has_join) {
-        load_rows<FULL>(q.fk, r, n, pass, v);
-        probe4(q.jt, v, pass, payload, q.err);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (pass[i] && (payload[i] & PAYLOAD_BAD)) {
-                atomicOr(q.err, ERR_RANGE);
-                pass[i] = false;
-            }
-        }
-        if (!any4(pass)) return false;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) key[i] = 0;
-#pragma unroll
-    for (int g = 0; g < MAX_GROUP; ++g) {
-        if (g >= q.n_group) break;
-        const int bits = q.gbits[g];
-        const bool fact_side = q.gside[g] == 0;
-        if (fact_side) load_rows<FULL>(q.gcol[g], r, n, pass, v);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint64_t f = fact_side ? (uint64_t)v[i]
-                                         : (uint64_t)(payload[i] >> q.gdpos[g]) & ((1ull << bits) - 1ull);
-            if (bits < 64) {
-                if (pass[i] && (f >> bits) != 0) {
-                    atomicOr(q.err, ERR_RANGE);
-                    pass[i] = false;
-                }
-                key[i] = (key[i] << bits) | f;
-            } else {
-                key[i] = f;
-            }
-        }
-    }
-    return any4(pass);
-}
-
-// The four terms of aggregate s for the lane's rows.
-template <bool FULL>
-__device__ __forceinline__ void eval_terms(const QueryDev& q, int s, uint64_t t0, uint64_t n, int lane,
-                                           const bool pass[4], I128 t[4]) {
-    const uint64_t r = t0 + 2ull * (uint64_t)lane;
-    int64_t a[4];
-    load_rows<FULL>(q.sa[s], r, n, pass, a);
-    if (q.skind[s] == S_MUL_SUB) {
-        int64_t b[4];
-        load_rows<FULL>(q.sb[s], r, n, pass, b);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) t[i] = mul_sub(a[i], q.sk[s], b[i]);
-    } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) t[i] = i128_from_i64(a[i]);
-    }
-}
 
 // --------------------------------------------------------------------- fill
 
@@ -321,7 +67,7 @@ __global__ void __launch_bounds__(256) k_build(const __grid_constant__ BuildDev 
             else jt.side[1] = payload;
             continue;
         }
-        uint64_t s = fmix64((uint64_t)key) & jt.mask;
+        uint64_t s = join_hash(jt, key) & jt.mask;
         bool placed = false;
         for (uint64_t it = 0; it <= jt.mask; ++it) {
             if (!jt.key64) {
@@ -469,29 +215,6 @@ cudaError_t launch_agg_shared(const QueryDev& q, uint64_t n, uint64_t* gacc, uin
 // as an order key repeated over consecutive line items), then claims or finds
 // the slot and adds count and sums with 64-bit atomics.
 
-__device__ __forceinline__ uint64_t* agg_slot(const AggTable& t, uint64_t key, uint32_t* err) {
-    if (key == EMPTY64) return t.slots + (t.mask + 1) * t.words;   // side slot
-    uint64_t s = fmix64(key) & t.mask;
-    for (uint64_t it = 0; it <= t.mask; ++it) {
-        uint64_t* p = t.slots + s * t.words;
-        uint64_t k = __ldcg((const unsigned long long*)p);
-        if (k == key) return p;
-        if (k == EMPTY64) {
-            unsigned long long prev =
-                atomicCAS((unsigned long long*)p, (unsigned long long)EMPTY64, (unsigned long long)key);
-            if (prev == EMPTY64) {
-                unsigned long long u = atomicAdd(t.used, 1ull);
-                if (u >= t.max_used) atomicOr(err, ERR_OVERFLOW);
-                return p;
-            }
-            if (prev == key) return p;
-        }
-        s = (s + 1) & t.mask;
-    }
-    atomicOr(err, ERR_OVERFLOW);
-    return nullptr;
-}
-
 template <int NS>
 __global__ void __launch_bounds__(256) k_agg_global(const __grid_constant__ QueryDev q, uint64_t n,
                                                    const __grid_constant__ AggTable t) {
@@ -605,7 +328,7 @@ __device__ __forceinline__ void write_row(const OutDev& o, uint64_t pos, uint64_
 
 // One CTA walks the dense table in key order, so the output is sorted.
 __global__ void __launch_bounds__(1024) k_final_dense(const uint64_t* __restrict__ gacc, uint32_t G,
-                                                     int n_sum, const __grid_constant__ OutDev o) {
+                                                     int n_sum, const __grid_constant__ OutDev o, int lo_only) {
     __shared__ uint32_t warp_tot[32];
     __shared__ uint64_t base;
     if (threadIdx.x == 0) base = 0;
@@ -627,7 +350,7 @@ __global__ void __launch_bounds__(1024) k_final_dense(const uint64_t* __restrict
             uint64_t lh[2 * MAX_SUM];
             for (int s = 0; s < n_sum; ++s) {
                 lh[2 * s] = gacc[(uint64_t)G * (1 + 2 * s) + g];
-                lh[2 * s + 1] = gacc[(uint64_t)G * (2 + 2 * s) + g];
+                lh[2 * s + 1] = lo_only ? (uint64_t)((int64_t)lh[2 * s] >> 63) : gacc[(uint64_t)G * (2 + 2 * s) + g];
             }
             write_row(o, pos, g, gacc[g], lh, n_sum);
         }
@@ -639,8 +362,8 @@ __global__ void __launch_bounds__(1024) k_final_dense(const uint64_t* __restrict
 }
 
 cudaError_t launch_final_dense(const uint64_t* gacc, uint32_t key_bits, int n_sum, const OutDev& o,
-                               cudaStream_t st) {
-    k_final_dense<<<1, 1024, 0, st>>>(gacc, 1u << key_bits, n_sum, o);
+                               cudaStream_t st, bool lo_only) {
+    k_final_dense<<<1, 1024, 0, st>>>(gacc, 1u << key_bits, n_sum, o, lo_only ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -691,22 +414,27 @@ cudaError_t launch_compact_global(const AggTable& t, uint64_t cap_with_side, uin
 
 __global__ void k_gather_global(const __grid_constant__ AggTable t, const uint64_t* __restrict__ skeys,
                                 const uint32_t* __restrict__ sidx, uint64_t n, int n_sum,
-                                const __grid_constant__ OutDev o) {
+                                const __grid_constant__ OutDev o, int lo_only) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t* p = t.slots + (uint64_t)sidx[i] * t.words;
-        write_row(o, i, skeys[i], p[1], p + 2, n_sum);
+        uint64_t lh[2 * MAX_SUM];
+        for (int s = 0; s < n_sum; ++s) {
+            lh[2 * s] = p[2 + 2 * s];
+            lh[2 * s + 1] = lo_only ? (uint64_t)((int64_t)lh[2 * s] >> 63) : p[3 + 2 * s];
+        }
+        write_row(o, i, skeys[i], p[1], lh, n_sum);
     }
 }
 
 cudaError_t launch_gather_global(const AggTable& t, const uint64_t* sorted_keys,
                                  const uint32_t* sorted_idx, uint64_t n, int n_sum, const OutDev& o,
-                                 int num_sms, cudaStream_t st) {
+                                 int num_sms, cudaStream_t st, bool lo_only) {
     if (n == 0) return cudaSuccess;
     uint64_t blocks = (n + 255) / 256;
     uint64_t cap = (uint64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;
-    k_gather_global<<<(unsigned)blocks, 256, 0, st>>>(t, sorted_keys, sorted_idx, n, n_sum, o);
+    k_gather_global<<<(unsigned)blocks, 256, 0, st>>>(t, sorted_keys, sorted_idx, n, n_sum, o, lo_only ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -728,6 +456,37 @@ cudaError_t launch_sample_filter(const QueryDev& q, uint64_t n, uint32_t samples
                                  unsigned long long* out, cudaStream_t st) {
     if (n == 0 || samples == 0) return cudaSuccess;
     k_sample_filter<<<1, 256, 0, st>>>(q, n, samples, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- column statistics
+
+__global__ void k_minmax(const __grid_constant__ DevCol c, uint64_t n, long long* out) {
+    long long lo = LLONG_MAX, hi = LLONG_MIN;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const long long v = ld1(c, i);
+        lo = v < lo ? v : lo;
+        hi = v > hi ? v : hi;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const long long a = __shfl_xor_sync(0xffffffffu, lo, off);
+        const long long b = __shfl_xor_sync(0xffffffffu, hi, off);
+        lo = a < lo ? a : lo;
+        hi = b > hi ? b : hi;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(out, lo);
+        atomicMax(out + 1, hi);
+    }
+}
+
+cudaError_t launch_minmax(const DevCol& c, uint64_t n, long long* out, int num_sms, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    const uint64_t cap = (uint64_t)num_sms * 4;
+    if (blocks > cap) blocks = cap;
+    k_minmax<<<(unsigned)blocks, 256, 0, st>>>(c, n, out);
     return cudaGetLastError();
 }
 

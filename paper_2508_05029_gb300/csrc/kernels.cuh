@@ -1,10 +1,9 @@
 // Device-side parameter blocks and launchers of the relational hot path.
 //
 // Hash tables use open addressing with linear probing.  The slot of a key is
-// fmix64(key) & mask, where fmix64 is the 64-bit finaliser of MurmurHash3
-// (Appleby, public domain).  The top 6 bits of the same hash pick the radix
-// partition, so partition bits and slot bits never overlap for tables below
-// 2^58 slots.
+// hash(key) & mask, where hash is the 64-bit finaliser of MurmurHash3
+// (Appleby, public domain) for 64-bit keys and its 32-bit finaliser for join
+// tables with 32-bit keys.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -107,6 +106,79 @@ struct OutDev {
     unsigned long long* n_groups;
 };
 
+// --------------------------------------------------------- staged pipeline
+//
+// A staged launch runs one producer warp that copies whole tiles of every
+// column the query reads into a ring of shared-memory stages with 1-D bulk
+// copies (cp.async.bulk, completion on an mbarrier), and ST_CONSUMERS warps
+// that evaluate the rows from shared memory, 8 rows per lane.
+
+#ifndef TP_ST_CONSUMERS
+#define TP_ST_CONSUMERS 16     // consumer warps per CTA
+#endif
+#ifndef TP_ST_RPL
+#define TP_ST_RPL 2            // rows per lane per stage
+#endif
+#ifndef TP_ST_CTAS
+#define TP_ST_CTAS 2           // resident CTAs per SM (shared memory is split between them)
+#endif
+constexpr int ST_CONSUMERS = TP_ST_CONSUMERS;
+constexpr int ST_RPL = TP_ST_RPL;
+constexpr int ST_CTAS = TP_ST_CTAS;
+constexpr int ST_SUB = 32 * ST_RPL;                // rows per consumer warp per stage
+constexpr int ST_TILE = ST_CONSUMERS * ST_SUB;     // rows per stage
+constexpr int ST_THREADS = 32 * (1 + ST_CONSUMERS);
+constexpr int ST_MAX_COLS = 22;
+constexpr int ST_MAX_STAGES = 8;
+// column slots of a QueryDev: filter, fk, 4 group columns, 8 + 8 sum columns
+enum : int { SL_FILTER = 0, SL_FK = 1, SL_GROUP = 2, SL_SA = 6, SL_SB = 14, SL_COUNT = 22 };
+
+struct StageLayout {
+    const void* src[ST_MAX_COLS];      // global base of each staged column
+    uint32_t off[ST_MAX_COLS];         // byte offset of its tile inside a stage
+    int32_t esize[ST_MAX_COLS];
+    int8_t col_of_slot[SL_COUNT];      // staged column feeding each slot, -1 if none
+    int16_t pad;
+    int32_t n_cols;
+    uint32_t stage_bytes;              // bytes between consecutive stages
+    uint32_t tile_bytes;               // bytes one full tile brings in (expect_tx)
+    int32_t n_stages;
+    uint32_t table_bytes;              // shared-memory aggregation table in front of the stages
+    uint32_t smem_bytes;               // total dynamic shared memory
+    uint64_t wait_ns;                  // limit of every mbarrier wait
+    // narrow (32-bit) shared-memory table, used with 64-bit accumulation:
+    // count[G] in word 0, then per sum its low words and, for mode 2, a carry
+    // word block.  Terms are offset by sum_off so they are non-negative.
+    int8_t sum_mode[MAX_SUM];          // 1: low word only, 2: low word + carry word
+    uint32_t sum_word[MAX_SUM];        // index (in blocks of G words) of sum s's low words
+    int64_t sum_off[MAX_SUM];
+};
+
+// Proven range of one aggregate's per-row term, from column statistics.
+struct TermBounds {
+    int64_t lo;      // minimum term
+    uint64_t span;   // maximum term - minimum term
+};
+
+// The same query over the rows from `row` on: every fact column pointer
+// advanced by `row` elements.
+inline QueryDev offset_rows(const QueryDev& q, uint64_t row) {
+    QueryDev r = q;
+    auto adv = [row](DevCol& c) {
+        if (!c.ptr) return;
+        const uint64_t sz = c.type == T_I64 ? 8 : (c.type == T_I32 ? 4 : 1);
+        c.ptr = (const unsigned char*)c.ptr + row * sz;
+    };
+    adv(r.fcol);
+    adv(r.fk);
+    for (int g = 0; g < MAX_GROUP; ++g) adv(r.gcol[g]);
+    for (int s = 0; s < MAX_SUM; ++s) {
+        adv(r.sa[s]);
+        adv(r.sb[s]);
+    }
+    return r;
+}
+
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return cudaGetLastError().
 
@@ -120,15 +192,44 @@ size_t agg_shared_smem_bytes(uint32_t key_bits, int n_sum);
 int agg_shared_grid(uint32_t key_bits, int n_sum, int num_sms);
 cudaError_t launch_agg_global(const QueryDev& q, uint64_t n, const AggTable& t, int num_sms,
                               cudaStream_t st);
+// lo_only: the table's sums were accumulated as 64-bit values (overflow ruled
+// out by column bounds); their high words are the sign extension of the low.
 cudaError_t launch_final_dense(const uint64_t* gacc, uint32_t key_bits, int n_sum, const OutDev& o,
-                               cudaStream_t st);
+                               cudaStream_t st, bool lo_only = false);
+
+// Staged shared-memory aggregation.  staged_layout_shared() fills *L for the
+// query (false when the staged kernel cannot run it: misaligned columns,
+// too little shared memory); fast selects 64-bit accumulation.  The launch
+// covers the first floor(n / ST_TILE) * ST_TILE rows; the caller runs the
+// remaining rows through launch_agg_shared (64-bit accumulation stays exact
+// there: both keep the same low words, and the high words are ignored).
+// With fast, bounds[s] must give every sum's term range; the layout fails
+// when a 32-bit table cannot hold `rows` rows' worth of sums.
+bool staged_layout_shared(const QueryDev& q, uint32_t key_bits, bool fast, const TermBounds* bounds,
+                          uint64_t rows, int num_sms, StageLayout* L);
+cudaError_t launch_agg_shared_staged(const QueryDev& q, const StageLayout& L, uint64_t n, uint64_t* gacc,
+                                     uint32_t key_bits, bool fast, int num_sms, cudaStream_t st);
+
+// Staged global-table aggregation.  stage_all = false stages only the filter
+// column (selective filters: the other columns are read for surviving rows
+// only).  fast: 64-bit reductions on low words (bounds proved); fold: fold
+// runs of equal keys in consecutive rows.  Whole tiles only, as above; the
+// caller runs the remaining rows through launch_agg_global.
+bool staged_layout_global(const QueryDev& q, bool stage_all, StageLayout* L);
+cudaError_t launch_agg_global_staged(const QueryDev& q, const StageLayout& L, uint64_t n, const AggTable& t,
+                                     bool fast, bool fold, int num_sms, cudaStream_t st);
+
+// Minimum and maximum of a column (out[0] = min, out[1] = max, initialised by
+// the caller to INT64_MAX / INT64_MIN).
+cudaError_t launch_minmax(const DevCol& c, uint64_t n, long long* out, int num_sms, cudaStream_t st);
 // compaction of the global table into (key, slot) pairs + max key
 cudaError_t launch_compact_global(const AggTable& t, uint64_t cap_with_side, uint64_t* keys,
                                   uint32_t* idx, unsigned long long* count,
                                   unsigned long long* maxkey, int num_sms, cudaStream_t st);
+// lo_only: sums were accumulated as 64-bit low words (high words by sign extension)
 cudaError_t launch_gather_global(const AggTable& t, const uint64_t* sorted_keys,
                                  const uint32_t* sorted_idx, uint64_t n, int n_sum, const OutDev& o,
-                                 int num_sms, cudaStream_t st);
+                                 int num_sms, cudaStream_t st, bool lo_only = false);
 
 // Rows of the filter column that pass, among `samples` evenly spaced rows.
 cudaError_t launch_sample_filter(const QueryDev& q, uint64_t n, uint32_t samples,

@@ -1,0 +1,316 @@
+// Pieces of the staged (bulk-copy) pipeline shared by its kernels: mbarrier
+// and bulk-copy PTX wrappers, bounded waits, shared-memory row loads, and
+// batched join probes.  sm_90+ PTX, built for sm_103a.
+#pragma once
+#include "device.cuh"
+
+namespace tpk {
+
+// ------------------------------------------------------------- PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for completion of the phase with the given parity; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// global -> shared bulk copy; both addresses 16-byte aligned, bytes % 16 == 0
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                          uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
+}
+
+// ------------------------------------------------------------ row passes
+
+// Eight probes at once; clears the bits of rows whose key is absent.  Join
+// tables of the staged path have fewer than 2^32 slots.
+__device__ __forceinline__ void probe8(const JoinTable& jt, const int64_t key[ST_RPL], uint32_t& pm,
+                                       uint32_t pay[ST_RPL], uint32_t* err) {
+    uint32_t slot[ST_RPL];
+    const uint32_t mask = (uint32_t)jt.mask;
+    uint32_t act = 0;
+#pragma unroll
+    for (int j = 0; j < ST_RPL; ++j) {
+        pay[j] = 0;
+        if (!(pm & (1u << j))) continue;
+        bool special;
+        if (jt.key64) {
+            special = (uint64_t)key[j] == EMPTY64;
+        } else {
+            if (key[j] < INT32_MIN || key[j] > INT32_MAX) {
+                pm &= ~(1u << j);
+                continue;
+            }
+            special = (uint32_t)key[j] == EMPTY32;
+        }
+        if (special) {
+            if (__ldg(jt.side) != 0) pay[j] = __ldg(jt.side + 1);
+            else pm &= ~(1u << j);
+            continue;
+        }
+        slot[j] = (uint32_t)join_hash(jt, key[j]) & mask;
+        act |= 1u << j;
+    }
+    for (uint32_t it = 0; act && it <= mask; ++it) {
+        if (!jt.key64) {
+            uint64_t w[ST_RPL];
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j)
+                if (act & (1u << j)) w[j] = __ldg((const unsigned long long*)jt.slots + slot[j]);
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) {
+                if (!(act & (1u << j))) continue;
+                const uint32_t wk = (uint32_t)w[j];
+                if (wk == (uint32_t)key[j]) {
+                    pay[j] = (uint32_t)(w[j] >> 32);
+                    act &= ~(1u << j);
+                } else if (wk == EMPTY32) {
+                    pm &= ~(1u << j);
+                    act &= ~(1u << j);
+                } else {
+                    slot[j] = (slot[j] + 1) & mask;
+                }
+            }
+        } else {
+            ulonglong2 w[ST_RPL];
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j)
+                if (act & (1u << j)) w[j] = __ldg((const ulonglong2*)jt.slots + slot[j]);
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) {
+                if (!(act & (1u << j))) continue;
+                if (w[j].x == (uint64_t)key[j]) {
+                    pay[j] = (uint32_t)w[j].y;
+                    act &= ~(1u << j);
+                } else if (w[j].x == EMPTY64) {
+                    pm &= ~(1u << j);
+                    act &= ~(1u << j);
+                } else {
+                    slot[j] = (slot[j] + 1) & mask;
+                }
+            }
+        }
+    }
+    if (act) {
+        atomicOr(err, ERR_INTERNAL);
+        pm &= ~act;
+    }
+}
+
+// Loads rows r0 + 32 j (j < 8) of a column tile held in shared memory.
+__device__ __forceinline__ void load8_smem(const unsigned char* base, int type, uint32_t r0, int64_t v[ST_RPL]) {
+    switch (type) {
+    case T_I32:
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) v[j] = ((const int*)base)[r0 + 32 * j];
+        break;
+    case T_I64:
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) v[j] = ((const long long*)base)[r0 + 32 * j];
+        break;
+    default:
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) v[j] = base[r0 + 32 * j];
+        break;
+    }
+}
+
+// Probes of a 32-bit-key join table for the rows in pm, branch-light: every
+// round issues the loads of all rows still searching.
+__device__ __forceinline__ void probe8_k32(const JoinTable& jt, const int64_t key[ST_RPL], uint32_t& pm,
+                                           uint32_t pay[ST_RPL], uint32_t* err) {
+    const uint32_t mask = (uint32_t)jt.mask;
+    uint32_t k[ST_RPL], slot[ST_RPL];
+    uint32_t act = 0;
+#pragma unroll
+    for (int j = 0; j < ST_RPL; ++j) {
+        const bool in32 = key[j] >= INT32_MIN && key[j] <= INT32_MAX;
+        k[j] = (uint32_t)key[j];
+        slot[j] = fmix32(k[j]) & mask;
+        pay[j] = 0;
+        if (!in32) pm &= ~(1u << j);
+        if (in32 && k[j] == EMPTY32) {  // the key equal to the empty pattern lives in the side cell
+            if (__ldg(jt.side) != 0) pay[j] = __ldg(jt.side + 1);
+            else pm &= ~(1u << j);
+        } else if (pm & (1u << j)) {
+            act |= 1u << j;
+        }
+    }
+    const unsigned long long* slots = (const unsigned long long*)jt.slots;
+    for (uint32_t it = 0; act && it <= mask; ++it) {
+        uint64_t w[ST_RPL];
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) w[j] = (act & (1u << j)) ? __ldg(slots + slot[j]) : 0ull;
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) {
+            const uint32_t wk = (uint32_t)w[j];
+            const bool on = (act >> j) & 1u;
+            const bool hit = on && wk == k[j];
+            const bool miss = on && wk == EMPTY32;
+            if (hit) pay[j] = (uint32_t)(w[j] >> 32);
+            if (hit || miss) act &= ~(1u << j);
+            if (miss) pm &= ~(1u << j);
+            slot[j] = (slot[j] + 1) & mask;
+        }
+    }
+    if (act) {
+        atomicOr(err, ERR_INTERNAL);
+        pm &= ~act;
+    }
+}
+
+// Column source for one tile: its copy in the stage, or global memory (a
+// column the layout does not stage is read only for rows still alive).
+struct ColSrc {
+    const unsigned char* p;
+    int type;
+    bool smem;
+};
+
+__device__ __forceinline__ int esize_dev(int type) { return type == T_I64 ? 8 : (type == T_I32 ? 4 : 1); }
+
+__device__ __forceinline__ ColSrc col_src(const StageLayout& L, int slot, const DevCol& c,
+                                          const unsigned char* stage, uint64_t row0) {
+    const int k = L.col_of_slot[slot];
+    if (k >= 0) return ColSrc{stage + L.off[k], c.type, true};
+    return ColSrc{(const unsigned char*)c.ptr + row0 * esize_dev(c.type), c.type, false};
+}
+
+// Rows r0 + 32 j of a tile; from global memory only the rows set in pm.
+__device__ __forceinline__ void load_rows(const ColSrc& c, uint32_t r0, uint32_t pm, int64_t v[ST_RPL]) {
+    if (c.smem) {
+        load8_smem(c.p, c.type, r0, v);
+        return;
+    }
+    switch (c.type) {
+    case T_I32:
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) v[j] = (pm >> j & 1u) ? (int64_t)__ldcs((const int*)c.p + r0 + 32 * j) : 0;
+        break;
+    case T_I64:
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j)
+            v[j] = (pm >> j & 1u) ? (int64_t)__ldcs((const long long*)c.p + r0 + 32 * j) : 0;
+        break;
+    default:
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j)
+            v[j] = (pm >> j & 1u) ? (int64_t)__ldcs((const unsigned char*)c.p + r0 + 32 * j) : 0;
+        break;
+    }
+}
+
+// Drives the bulk-copy pipeline over the whole tiles of [0, n) that this CTA
+// owns (tiles blockIdx.x, blockIdx.x + gridDim.x, ...).  `area` is dynamic
+// shared memory for 2 * ST_MAX_STAGES mbarriers followed by L.n_stages
+// stages.  Warp 0 lane 0 produces; warps 1..ST_CONSUMERS call
+// consume(stage, row0, r0) for each tile, r0 being the lane's first
+// tile-local row.  Returns after this thread's part of the pipeline is done;
+// the caller synchronises the CTA before reading what consumers produced.
+template <class Consume>
+__device__ __forceinline__ void run_pipeline(const QueryDev& q, const StageLayout& L, uint64_t n,
+                                             unsigned char* area, Consume&& consume) {
+    uint64_t* full = (uint64_t*)area;
+    uint64_t* empty = full + ST_MAX_STAGES;
+    unsigned char* stages = area + 2 * ST_MAX_STAGES * sizeof(uint64_t);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < L.n_stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], ST_CONSUMERS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t ntiles = n / ST_TILE;
+    if (warp == 0) {
+        if (lane != 0) return;
+        const uint64_t pol = l2_evict_first();
+        uint32_t i = 0;
+        int last_fill[ST_MAX_STAGES];
+        for (int s = 0; s < ST_MAX_STAGES; ++s) last_fill[s] = -1;
+        bool ok = true;
+        for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const int s = (int)(i % (uint32_t)L.n_stages);
+            const uint32_t u = i / (uint32_t)L.n_stages;
+            if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1u, L.wait_ns)) {
+                atomicOr(q.err, ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+            mbar_arrive_expect_tx(&full[s], L.tile_bytes);
+            unsigned char* dst = stages + (uint64_t)s * L.stage_bytes;
+            for (int c = 0; c < L.n_cols; ++c) {
+                const uint32_t bytes = (uint32_t)ST_TILE * (uint32_t)L.esize[c];
+                bulk_load(dst + L.off[c], (const unsigned char*)L.src[c] + t * bytes, bytes, &full[s], pol);
+            }
+            last_fill[s] = (int)u;
+        }
+        if (!ok) {  // consumers gave up: let the copies already issued land before exit
+            for (int s = 0; s < L.n_stages; ++s)
+                if (last_fill[s] >= 0) mbar_wait(&full[s], (uint32_t)last_fill[s] & 1u, L.wait_ns);
+        }
+        return;
+    }
+    const uint32_t r0 = (uint32_t)(warp - 1) * ST_SUB + (uint32_t)lane;
+    uint32_t i = 0;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        const int s = (int)(i % (uint32_t)L.n_stages);
+        const uint32_t u = i / (uint32_t)L.n_stages;
+        if (!mbar_wait(&full[s], u & 1u, L.wait_ns)) {
+            atomicOr(q.err, ERR_TIMEOUT);
+            return;
+        }
+        consume(stages + (uint64_t)s * L.stage_bytes, t * ST_TILE, r0);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+    }
+}
+
+}  // namespace tpk

@@ -111,6 +111,9 @@ struct tp_table {
     std::vector<tp::Batch> batches;
     std::vector<void*> dev_cols;       // device / wrapped placement
     uint64_t dev_reserved = 0;
+    // per-column minimum and maximum over all rows (valid when rows > 0): the
+    // bounds that prove when 64-bit accumulation cannot overflow
+    std::vector<int64_t> cmin, cmax;
 };
 
 struct tp_plan {

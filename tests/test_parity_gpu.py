@@ -203,3 +203,28 @@ def test_budget_refusal_and_release(eng):
     assert eng.budget()[0] == used0
     check(eng, wl.fact, wl.dim, wl.query)
     assert eng.budget()[0] == used0
+
+
+@pytest.mark.parametrize("flags", [0, T.TP_FLAG_EXACT_ONLY, T.TP_FLAG_NO_STAGED])
+def test_every_kernel_path(flags):
+    """Staged 64-bit (bounds prove no overflow), staged exact 128-bit, and the
+    plain-load kernel all give the oracle's result."""
+    e = T.Engine(page_bytes=4 << 20, n_pages=256, batch_rows=700_000, flags=flags)
+    try:
+        wl = W.config2("a", n_fact=2_000_011, n_dim=200_000)
+        for placement in (T.TP_DEVICE, T.TP_HOST_PAGES):
+            check(e, wl.fact, wl.dim, wl.query, placement=placement)
+        fact, dim = _tiny(8, 40_000, 600, 800, signed=True)
+        q = dict(filter=dict(col="qty", lo=-100, hi=2500), join=dict(fact_col="fk", dim_col="pk"),
+                 group=[("dim", "attr", 5), ("fact", "flag", 2)],
+                 aggs=[("count",), ("avg", "disc"), ("sum_mul_sub", "price", -3, "qty"), ("sum", "price")])
+        check(e, fact, dim, q)
+        # values whose sums need all 128 bits: the exact path must carry
+        n = 5_000
+        big = dict(a=np.full(n, (1 << 62) + 12345, np.int64), b=np.full(n, -(1 << 62), np.int64),
+                   g=(np.arange(n) % 3).astype(np.uint8), d=datagen.uniform(4, 4, np.int32, n, 0, 9))
+        qb = dict(filter=dict(col="d", lo=1, hi=8), join=None, group=[("fact", "g", 2)],
+                  aggs=[("sum_mul_sub", "a", (1 << 62), "b"), ("sum", "a"), ("avg", "b")])
+        check(e, big, None, qb)
+    finally:
+        e.close()
