@@ -45,7 +45,7 @@ METRIC = "fact rows/s & HBM GB/s (join+agg); served p50/p99 latency vs plain"
 WORKLOAD = "star-60M-lowcard"
 BYTES_PER_FACT_ROW = 4 + 4 + 8 + 8 + 8 + 1 + 1      # date, fk, qty, price, disc, flag, status
 BYTES_PER_DIM_ROW = 4 + 4                            # pk, attr
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_agg_shared_star12M.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_agg_shared_staged_star12M.md")
 
 
 def parse_args():
@@ -154,7 +154,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.cuh"):
+    for f in ("kernels.cu", "kernels.cuh", "device.cuh", "pipeline.cuh", "staged.cu"):
         with open(os.path.join(ROOT, "paper_2508_05029_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -363,7 +363,7 @@ def main():
             "hbm_gbs": step_gbs,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_agg_shared", "kernel_ms": k_ms,
+                         "kernel": "k_agg_shared_staged", "kernel_ms": k_ms,
                          "alg_bytes_per_launch": alg_bytes},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "extra": extra,
         }

@@ -68,81 +68,6 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 
 // ------------------------------------------------------------ row passes
 
-// Eight probes at once; clears the bits of rows whose key is absent.  Join
-// tables of the staged path have fewer than 2^32 slots.
-__device__ __forceinline__ void probe8(const JoinTable& jt, const int64_t key[ST_RPL], uint32_t& pm,
-                                       uint32_t pay[ST_RPL], uint32_t* err) {
-    uint32_t slot[ST_RPL];
-    const uint32_t mask = (uint32_t)jt.mask;
-    uint32_t act = 0;
-#pragma unroll
-    for (int j = 0; j < ST_RPL; ++j) {
-        pay[j] = 0;
-        if (!(pm & (1u << j))) continue;
-        bool special;
-        if (jt.key64) {
-            special = (uint64_t)key[j] == EMPTY64;
-        } else {
-            if (key[j] < INT32_MIN || key[j] > INT32_MAX) {
-                pm &= ~(1u << j);
-                continue;
-            }
-            special = (uint32_t)key[j] == EMPTY32;
-        }
-        if (special) {
-            if (__ldg(jt.side) != 0) pay[j] = __ldg(jt.side + 1);
-            else pm &= ~(1u << j);
-            continue;
-        }
-        slot[j] = (uint32_t)join_hash(jt, key[j]) & mask;
-        act |= 1u << j;
-    }
-    for (uint32_t it = 0; act && it <= mask; ++it) {
-        if (!jt.key64) {
-            uint64_t w[ST_RPL];
-#pragma unroll
-            for (int j = 0; j < ST_RPL; ++j)
-                if (act & (1u << j)) w[j] = __ldg((const unsigned long long*)jt.slots + slot[j]);
-#pragma unroll
-            for (int j = 0; j < ST_RPL; ++j) {
-                if (!(act & (1u << j))) continue;
-                const uint32_t wk = (uint32_t)w[j];
-                if (wk == (uint32_t)key[j]) {
-                    pay[j] = (uint32_t)(w[j] >> 32);
-                    act &= ~(1u << j);
-                } else if (wk == EMPTY32) {
-                    pm &= ~(1u << j);
-                    act &= ~(1u << j);
-                } else {
-                    slot[j] = (slot[j] + 1) & mask;
-                }
-            }
-        } else {
-            ulonglong2 w[ST_RPL];
-#pragma unroll
-            for (int j = 0; j < ST_RPL; ++j)
-                if (act & (1u << j)) w[j] = __ldg((const ulonglong2*)jt.slots + slot[j]);
-#pragma unroll
-            for (int j = 0; j < ST_RPL; ++j) {
-                if (!(act & (1u << j))) continue;
-                if (w[j].x == (uint64_t)key[j]) {
-                    pay[j] = (uint32_t)w[j].y;
-                    act &= ~(1u << j);
-                } else if (w[j].x == EMPTY64) {
-                    pm &= ~(1u << j);
-                    act &= ~(1u << j);
-                } else {
-                    slot[j] = (slot[j] + 1) & mask;
-                }
-            }
-        }
-    }
-    if (act) {
-        atomicOr(err, ERR_INTERNAL);
-        pm &= ~act;
-    }
-}
-
 // Loads rows r0 + 32 j (j < 8) of a column tile held in shared memory.
 __device__ __forceinline__ void load8_smem(const unsigned char* base, int type, uint32_t r0, int64_t v[ST_RPL]) {
     switch (type) {
@@ -161,18 +86,28 @@ __device__ __forceinline__ void load8_smem(const unsigned char* base, int type, 
     }
 }
 
-// Probes of a 32-bit-key join table for the rows in pm, branch-light: every
-// round issues the loads of all rows still searching.
-__device__ __forceinline__ void probe8_k32(const JoinTable& jt, const int64_t key[ST_RPL], uint32_t& pm,
-                                           uint32_t pay[ST_RPL], uint32_t* err) {
+// Batched join probes, one aligned 32-byte sector ("bucket") per round.
+//
+// The table is filled by slot-wise linear probing from hash & mask.  A lookup
+// reads the whole aligned sector holding its current slot (4 slots of a
+// 32-bit-key table, 2 of a 64-bit-key table) and examines every slot from its
+// position to the end of the sector: a match is the key (keys are unique),
+// an empty slot ends the search.  Slots before the starting position in the
+// first sector belong to other probe sequences and are skipped.  A lane's
+// rows advance independently, so a round costs one sector load per live row
+// and most lookups finish in the first round.  pm loses the rows whose key
+// is absent; pay receives the payload of the others.
+
+__device__ __forceinline__ void probe_rows_k32(const JoinTable& jt, const int64_t key[ST_RPL], uint32_t& pm,
+                                               uint32_t pay[ST_RPL], uint32_t* err) {
     const uint32_t mask = (uint32_t)jt.mask;
-    uint32_t k[ST_RPL], slot[ST_RPL];
+    uint32_t k[ST_RPL], pos[ST_RPL];
     uint32_t act = 0;
 #pragma unroll
     for (int j = 0; j < ST_RPL; ++j) {
         const bool in32 = key[j] >= INT32_MIN && key[j] <= INT32_MAX;
         k[j] = (uint32_t)key[j];
-        slot[j] = fmix32(k[j]) & mask;
+        pos[j] = fmix32(k[j]) & mask;
         pay[j] = 0;
         if (!in32) pm &= ~(1u << j);
         if (in32 && k[j] == EMPTY32) {  // the key equal to the empty pattern lives in the side cell
@@ -182,27 +117,99 @@ __device__ __forceinline__ void probe8_k32(const JoinTable& jt, const int64_t ke
             act |= 1u << j;
         }
     }
-    const unsigned long long* slots = (const unsigned long long*)jt.slots;
-    for (uint32_t it = 0; act && it <= mask; ++it) {
-        uint64_t w[ST_RPL];
-#pragma unroll
-        for (int j = 0; j < ST_RPL; ++j) w[j] = (act & (1u << j)) ? __ldg(slots + slot[j]) : 0ull;
+    const ulonglong2* sectors = (const ulonglong2*)jt.slots;
+    for (uint32_t it = 0; act && it <= mask; it += 4) {
 #pragma unroll
         for (int j = 0; j < ST_RPL; ++j) {
-            const uint32_t wk = (uint32_t)w[j];
-            const bool on = (act >> j) & 1u;
-            const bool hit = on && wk == k[j];
-            const bool miss = on && wk == EMPTY32;
-            if (hit) pay[j] = (uint32_t)(w[j] >> 32);
-            if (hit || miss) act &= ~(1u << j);
-            if (miss) pm &= ~(1u << j);
-            slot[j] = (slot[j] + 1) & mask;
+            if (!(act & (1u << j))) continue;
+            const uint32_t base = pos[j] & ~3u;
+            const ulonglong2 lo = __ldg(sectors + (base >> 1));
+            const ulonglong2 hi = __ldg(sectors + (base >> 1) + 1);
+            const uint64_t w[4] = {lo.x, lo.y, hi.x, hi.y};
+            const uint32_t first = pos[j] & 3u;
+            bool done = false;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                if (done || (uint32_t)m < first) continue;
+                const uint32_t wk = (uint32_t)w[m];
+                if (wk == k[j]) {
+                    pay[j] = (uint32_t)(w[m] >> 32);
+                    done = true;
+                } else if (wk == EMPTY32) {
+                    pm &= ~(1u << j);
+                    done = true;
+                }
+            }
+            if (done) act &= ~(1u << j);
+            else pos[j] = (base + 4) & mask;
         }
     }
     if (act) {
         atomicOr(err, ERR_INTERNAL);
         pm &= ~act;
     }
+}
+
+__device__ __forceinline__ void probe_rows_k64(const JoinTable& jt, const int64_t key[ST_RPL], uint32_t& pm,
+                                               uint32_t pay[ST_RPL], uint32_t* err) {
+    const uint32_t mask = (uint32_t)jt.mask;
+    uint32_t pos[ST_RPL];
+    uint32_t act = 0;
+#pragma unroll
+    for (int j = 0; j < ST_RPL; ++j) {
+        pay[j] = 0;
+        pos[j] = (uint32_t)fmix64((uint64_t)key[j]) & mask;
+        if (!(pm & (1u << j))) continue;
+        if ((uint64_t)key[j] == EMPTY64) {
+            if (__ldg(jt.side) != 0) pay[j] = __ldg(jt.side + 1);
+            else pm &= ~(1u << j);
+            continue;
+        }
+        act |= 1u << j;
+    }
+    const ulonglong2* slots = (const ulonglong2*)jt.slots;
+    for (uint32_t it = 0; act && it <= mask; it += 2) {
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) {
+            if (!(act & (1u << j))) continue;
+            const uint32_t base = pos[j] & ~1u;
+            const ulonglong2 s0 = __ldg(slots + base);
+            const ulonglong2 s1 = __ldg(slots + base + 1);
+            bool done = false;
+            if ((pos[j] & 1u) == 0) {
+                if (s0.x == (uint64_t)key[j]) {
+                    pay[j] = (uint32_t)s0.y;
+                    done = true;
+                } else if (s0.x == EMPTY64) {
+                    pm &= ~(1u << j);
+                    done = true;
+                }
+            }
+            if (!done) {
+                if (s1.x == (uint64_t)key[j]) {
+                    pay[j] = (uint32_t)s1.y;
+                    done = true;
+                } else if (s1.x == EMPTY64) {
+                    pm &= ~(1u << j);
+                    done = true;
+                }
+            }
+            if (done) act &= ~(1u << j);
+            else pos[j] = (base + 2) & mask;
+        }
+    }
+    if (act) {
+        atomicOr(err, ERR_INTERNAL);
+        pm &= ~act;
+    }
+}
+
+// Probes for the rows in pm of either table kind; tables of the staged path
+// have fewer than 2^32 slots.
+__device__ __forceinline__ void probe_rows(const JoinTable& jt, const int64_t key[ST_RPL], uint32_t& pm,
+                                           uint32_t pay[ST_RPL], uint32_t* err) {
+    if (!jt.key64) probe_rows_k32(jt, key, pm, pay, err);
+    else probe_rows_k64(jt, key, pm, pay, err);
 }
 
 // Column source for one tile: its copy in the stage, or global memory (a

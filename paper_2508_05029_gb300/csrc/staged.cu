@@ -77,11 +77,7 @@ __device__ __forceinline__ void consume_dense_full(const QueryDev& q, const Stag
     uint32_t pay[ST_RPL];
     if (q.has_join) {
         load8_smem(stage + L.off[L.col_of_slot[SL_FK]], q.fk.type, r0, v);
-        if (!q.jt.key64) {
-            probe8_k32(q.jt, v, pm, pay, q.err);
-        } else {
-            probe8(q.jt, v, pm, pay, q.err);
-        }
+        probe_rows(q.jt, v, pm, pay, q.err);
         uint32_t bad = 0;
 #pragma unroll
         for (int j = 0; j < ST_RPL; ++j) bad |= (uint32_t)((pay[j] & PAYLOAD_BAD) != 0) << j;

@@ -47,8 +47,7 @@ __device__ __forceinline__ uint32_t eval_keys64(const QueryDev& q, const StageLa
     for (int j = 0; j < ST_RPL; ++j) pay[j] = 0;
     if (q.has_join && pm) {
         load_rows(col_src(L, SL_FK, q.fk, stage, row0), r0, pm, v);
-        if (!q.jt.key64) probe8_k32(q.jt, v, pm, pay, q.err);
-        else probe8(q.jt, v, pm, pay, q.err);
+        probe_rows(q.jt, v, pm, pay, q.err);
         uint32_t bad = 0;
 #pragma unroll
         for (int j = 0; j < ST_RPL; ++j) bad |= (uint32_t)((pay[j] & PAYLOAD_BAD) != 0) << j;
