@@ -92,8 +92,11 @@ enum { TP_AGG_AUTO = 0, TP_AGG_SHARED = 1, TP_AGG_GLOBAL = 2 };
  *                         kernels (plain-load kernels only).
  *                         TP_FLAG_EXACT_ONLY: never use 64-bit accumulation,
  *                         even where column bounds prove it cannot overflow.
+ *                         TP_FLAG_NO_DIRECT_JOIN: always hash the join keys,
+ *                         even when they are dense enough for a
+ *                         direct-mapped table (key range <= 2 x rows).
  */
-enum { TP_FLAG_TIME_KERNELS = 1, TP_FLAG_NO_STAGED = 2, TP_FLAG_EXACT_ONLY = 4 };
+enum { TP_FLAG_TIME_KERNELS = 1, TP_FLAG_NO_STAGED = 2, TP_FLAG_EXACT_ONLY = 4, TP_FLAG_NO_DIRECT_JOIN = 8 };
 typedef struct {
     uint64_t page_bytes;
     uint32_t n_pages;
@@ -255,6 +258,51 @@ void tp_plan_destroy(tp_plan* p);
  * *out receives a result that stays on the device until read.
  */
 tp_status tp_execute(tp_plan* p, tp_result** out);
+
+/* --------------------------------------------------------- batched execution */
+
+/*
+ * Many uneven queries in one persistent kernel launch, captured once in a CUDA
+ * graph and replayed by every tp_batch_execute.  Section 3.1 has operators
+ * spawn tasks over batches and Section 3.3.1 has the Compute Executor run
+ * them asynchronously; here the tasks of all queries -- hash-build chunks,
+ * probe tiles, finalisation -- form one work queue that resident CTAs drain in
+ * order.  A probe tile of query q waits (bounded, TP_E_TIMEOUT on expiry)
+ * until every build chunk of q is done, and q's finalisation until every
+ * probe tile of q is done; tasks are taken in queue order, so every task
+ * waited on is already held by a running CTA.
+ *
+ * Every fact and dimension table must be on the device (TP_DEVICE or
+ * wrapped) and every group key at most 20 bits wide (the groups of a query
+ * live in a dense device table of 2^bits entries); otherwise TP_E_INVALID.
+ * The batch reserves and owns all device memory it needs (join tables,
+ * accumulators, results); TP_E_BUDGET if that does not fit.
+ *
+ *   tuning_path  optional table written by tp_autotune: per query class
+ *                (fact-size, group-width and dimension-size buckets) the
+ *                join load factor, rows per warp of a probe tile, and
+ *                shared-memory versus device-memory aggregation.  NULL or a
+ *                missing file: built-in defaults.
+ */
+typedef struct tp_batch tp_batch;
+tp_status tp_batch_create(tp_engine* eng, tp_plan* const* plans, int32_t n, const char* tuning_path,
+                          tp_batch** out);
+/* Replays the batch and fills results[0..n) (ownership as tp_execute's, but
+ * the arrays live in the batch: a result stays valid until the next
+ * tp_batch_execute or tp_batch_destroy of its batch). */
+tp_status tp_batch_execute(tp_batch* b, tp_result** results);
+/* Device time of the last tp_batch_execute in milliseconds (CUDA events). */
+double tp_batch_last_ms(const tp_batch* b);
+void tp_batch_destroy(tp_batch* b);
+
+/*
+ * Autotuner: for every query class present in plans[0..n), tries the join
+ * load factor (0.5, 0.7), the rows per warp of a probe tile (128, 256, 512,
+ * 1024) and shared-memory versus device-memory aggregation, one knob at a
+ * time, timing the batch of that class's queries; writes the best choice per
+ * class to tuning_path (text).  The plans' own results are unaffected.
+ */
+tp_status tp_autotune(tp_engine* eng, tp_plan* const* plans, int32_t n, const char* tuning_path);
 
 /* ----------------------------------------------------------------- results */
 

@@ -114,10 +114,34 @@ __device__ __forceinline__ void atomic_add_i128(uint64_t* lo, uint64_t* hi, I128
 
 // ------------------------------------------------------------------ probing
 
+// Table word load: through the read-only path (NC), or coherent at L2 for
+// tables written earlier in the same kernel launch.
+template <bool NC, typename T>
+__device__ __forceinline__ T ld_table(const T* p) {
+    if constexpr (NC) return __ldg(p);
+    else return __ldcg(p);
+}
+
 // Looks up four keys at once so their table loads overlap.  pass[i] is
 // cleared for rows whose key is absent.
+template <bool NC = true>
 __device__ __forceinline__ void probe4(const JoinTable& jt, const int64_t key[4], bool pass[4],
                                        uint32_t payload[4], uint32_t* err) {
+    if (jt.direct) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint64_t idx = (uint64_t)key[i] - (uint64_t)jt.kmin;
+            const bool in = pass[i] && idx < jt.range;
+            w[i] = in ? ld_table<NC>((const unsigned int*)jt.slots + idx) : EMPTY32;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            pass[i] = pass[i] && w[i] != EMPTY32;
+            payload[i] = w[i];
+        }
+        return;
+    }
     uint64_t slot[4];
     bool act[4];
 #pragma unroll
@@ -137,8 +161,8 @@ __device__ __forceinline__ void probe4(const JoinTable& jt, const int64_t key[4]
             special = (uint32_t)key[i] == EMPTY32;
         }
         if (special) {
-            pass[i] = __ldg(jt.side) != 0;
-            payload[i] = __ldg(jt.side + 1);
+            pass[i] = ld_table<NC>(jt.side) != 0;
+            payload[i] = ld_table<NC>(jt.side + 1);
             act[i] = false;
             continue;
         }
@@ -150,7 +174,7 @@ __device__ __forceinline__ void probe4(const JoinTable& jt, const int64_t key[4]
             uint64_t w[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (act[i]) w[i] = __ldg((const unsigned long long*)jt.slots + slot[i]);
+                if (act[i]) w[i] = ld_table<NC>((const unsigned long long*)jt.slots + slot[i]);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (!act[i]) continue;
@@ -170,7 +194,7 @@ __device__ __forceinline__ void probe4(const JoinTable& jt, const int64_t key[4]
             ulonglong2 w[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (act[i]) w[i] = __ldg((const ulonglong2*)jt.slots + slot[i]);
+                if (act[i]) w[i] = ld_table<NC>((const ulonglong2*)jt.slots + slot[i]);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (!act[i]) continue;
@@ -205,7 +229,7 @@ __device__ __forceinline__ bool any4(const bool p[4]) { return p[0] || p[1] || p
 
 // Filter, join and key packing of the lane's four rows in warp tile t0.
 // Returns false when no row of the lane survives.
-template <bool FULL>
+template <bool FULL, bool NC = true>
 __device__ __forceinline__ bool eval_keys(const QueryDev& q, uint64_t t0, uint64_t n, int lane,
                                           bool pass[4], uint64_t key[4]) {
     const uint64_t r = t0 + 2ull * (uint64_t)lane;
@@ -222,7 +246,7 @@ __device__ __forceinline__ bool eval_keys(const QueryDev& q, uint64_t t0, uint64
     uint32_t payload[4] = {0, 0, 0, 0};
     if (q.has_join) {
         load_rows<FULL>(q.fk, r, n, pass, v);
-        probe4(q.jt, v, pass, payload, q.err);
+        probe4<NC>(q.jt, v, pass, payload, q.err);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (pass[i] && (payload[i] & PAYLOAD_BAD)) {
@@ -276,6 +300,145 @@ __device__ __forceinline__ void eval_terms(const QueryDev& q, int s, uint64_t t0
     }
 }
 
+
+// ---------------------------------------------------------------- finalise
+
+// Correctly rounded conversion of a 128-bit integer to double.  Values that
+// fit in 64 bits use the hardware conversion directly.  Wider magnitudes keep
+// their top 64 bits and fold every discarded bit into the lowest kept bit
+// (a "sticky" bit): with 64 kept bits and 53 significand bits the rounding
+// decision (round bit plus "anything below it") is unchanged, so one
+// round-to-nearest conversion of the 64-bit value, scaled by an exact power
+// of two, is the correctly rounded result.
+__device__ __forceinline__ double i128_to_double(uint64_t lo, uint64_t hi) {
+    if (hi == (uint64_t)((int64_t)lo >> 63)) return __ll2double_rn((long long)lo);
+    const bool neg = (int64_t)hi < 0;
+    uint64_t mlo = lo, mhi = hi;
+    if (neg) {  // two's complement negate; -2^127 maps to 2^127 as unsigned
+        mlo = ~lo + 1ull;
+        mhi = ~hi + (mlo == 0 ? 1ull : 0ull);
+    }
+    double d;
+    if (mhi == 0) {
+        d = __ull2double_rn(mlo);
+    } else {
+        const int lz = __clzll((long long)mhi);
+        const int s = 64 - lz;  // 1..64
+        uint64_t top, sticky;
+        if (s == 64) {
+            top = mhi;
+            sticky = mlo != 0;
+        } else {
+            top = (mhi << (64 - s)) | (mlo >> s);
+            sticky = (mlo & ((1ull << s) - 1ull)) != 0;
+        }
+        d = ldexp(__ull2double_rn(top | sticky), s);
+    }
+    return neg ? -d : d;
+}
+
+__device__ __forceinline__ void write_row(const OutDev& o, uint64_t pos, uint64_t key, uint64_t c,
+                                          const uint64_t* lo_hi, int n_sum) {
+    o.keys[pos] = key;
+    o.counts[pos] = (int64_t)c;
+    for (int s = 0; s < n_sum; ++s) {
+        o.sums[s][2 * pos] = lo_hi[2 * s];
+        o.sums[s][2 * pos + 1] = lo_hi[2 * s + 1];
+        if (o.has_avg[s])
+            o.avgs[s][pos] = __ddiv_rn(i128_to_double(lo_hi[2 * s], lo_hi[2 * s + 1]),
+                                       __ll2double_rn((long long)c));
+    }
+}
+
+// One CTA writes the non-empty groups of a dense table (count[G], then lo/hi
+// per sum) in key order, so the output is sorted; lo_only: high words are the
+// sign extension of the low words.  Every thread of the CTA must call it.
+__device__ __forceinline__ void final_dense_block(const uint64_t* __restrict__ gacc, uint32_t G, int n_sum,
+                                                  const OutDev& o, bool lo_only) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint64_t base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t c0 = 0; c0 < G; c0 += blockDim.x) {
+        const uint32_t g = c0 + threadIdx.x;
+        const bool has = g < G && gacc[g] != 0;
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        if (lane == 0) warp_tot[warp] = __popc(m);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < warp) before += warp_tot[w];
+            total += warp_tot[w];
+        }
+        if (has) {
+            const uint64_t pos = base + before + __popc(m & ((1u << lane) - 1u));
+            uint64_t lh[2 * MAX_SUM];
+            for (int s = 0; s < n_sum; ++s) {
+                lh[2 * s] = gacc[(uint64_t)G * (1 + 2 * s) + g];
+                lh[2 * s + 1] = lo_only ? (uint64_t)((int64_t)lh[2 * s] >> 63) : gacc[(uint64_t)G * (2 + 2 * s) + g];
+            }
+            write_row(o, pos, g, gacc[g], lh, n_sum);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *o.n_groups = base;
+}
+
+// ------------------------------------------------------------- join build
+
+// Inserts dimension row i into the join table: CAS on the key (32-bit keys:
+// key and payload in one word), ERR_DUP on a repeated key.
+__device__ __forceinline__ void build_insert(const BuildDev& b, uint64_t i) {
+    const JoinTable& jt = b.jt;
+    int64_t key = ld1(b.key, i);
+    // Dimension group fields packed into bits 0..30 of the payload; bit 31
+    // marks a row with a field outside its width.  That is an error only
+    // if a surviving fact row joins to it, which the probe side reports.
+    uint32_t payload = 0;
+    for (int f = 0; f < b.n_dfield; ++f) {
+        int64_t v = ld1(b.dcol[f], i);
+        if (v < 0 || ((uint64_t)v >> b.dbits[f]) != 0) payload |= PAYLOAD_BAD;
+        else payload |= (uint32_t)((uint64_t)v << b.dpos[f]);
+    }
+    if (jt.direct) {  // slot key - kmin: the host sized the table to the key range
+        const uint32_t v = (payload & PAYLOAD_BAD) ? PAYLOAD_BAD : payload;
+        const uint64_t idx = (uint64_t)key - (uint64_t)jt.kmin;
+        if (idx >= jt.range) { atomicOr(b.err, ERR_INTERNAL); return; }
+        if (atomicCAS((unsigned int*)jt.slots + idx, EMPTY32, v) != EMPTY32) atomicOr(b.err, ERR_DUP);
+        return;
+    }
+    bool special = jt.key64 ? (uint64_t)key == EMPTY64 : (uint32_t)key == EMPTY32;
+    if (special) {
+        if (atomicCAS(jt.side, 0u, 1u) != 0u) atomicOr(b.err, ERR_DUP);
+        else jt.side[1] = payload;
+        return;
+    }
+    uint64_t s = join_hash(jt, key) & jt.mask;
+    bool placed = false;
+    for (uint64_t it = 0; it <= jt.mask; ++it) {
+        if (!jt.key64) {
+            unsigned long long want = ((unsigned long long)payload << 32) | (uint32_t)key;
+            unsigned long long prev =
+                atomicCAS((unsigned long long*)jt.slots + s, (unsigned long long)EMPTY64, want);
+            if (prev == EMPTY64) { placed = true; break; }
+            if ((uint32_t)prev == (uint32_t)key) { atomicOr(b.err, ERR_DUP); placed = true; break; }
+        } else {
+            unsigned long long prev = atomicCAS((unsigned long long*)jt.slots + 2 * s,
+                                                (unsigned long long)EMPTY64, (unsigned long long)key);
+            if (prev == EMPTY64) {
+                jt.slots[2 * s + 1] = payload;
+                placed = true;
+                break;
+            }
+            if (prev == (unsigned long long)key) { atomicOr(b.err, ERR_DUP); placed = true; break; }
+        }
+        s = (s + 1) & jt.mask;
+    }
+    if (!placed) atomicOr(b.err, ERR_INTERNAL);
+}
 
 // ------------------------------------------------------- global aggregation slot
 

@@ -141,43 +141,7 @@ tpk::DevCol devcol(const tp_table* t, int c, const void* ptr) {
 // QueryDev for one batch: colptr[c] is the device address of fact column c's
 // first row in this batch (nullptr for columns the query does not read).
 tpk::QueryDev make_query(const ExecState& S, const std::vector<const void*>& colptr) {
-    const tp_plan_desc& d = S.p->d;
-    tpk::QueryDev q{};
-    q.has_filter = d.filter.col >= 0;
-    if (q.has_filter) {
-        q.fcol = devcol(S.fact, d.filter.col, colptr[d.filter.col]);
-        q.flo = d.filter.lo;
-        q.fhi = d.filter.hi;
-    }
-    q.has_join = d.join.fact_col >= 0;
-    if (q.has_join) {
-        q.fk = devcol(S.fact, d.join.fact_col, colptr[d.join.fact_col]);
-        q.jt = S.jt;
-    }
-    q.n_group = d.n_group;
-    for (int g = 0; g < d.n_group; ++g) {
-        q.gside[g] = d.group[g].side;
-        q.gbits[g] = d.group[g].bits;
-        q.gdpos[g] = S.p->gdpos[g];
-        if (d.group[g].side == TP_SIDE_FACT) q.gcol[g] = devcol(S.fact, d.group[g].col, colptr[d.group[g].col]);
-    }
-    q.n_sum = S.p->n_sum;
-    for (int a = 0; a < d.n_agg; ++a) {
-        const int s = S.p->sum_of_agg[a];
-        if (s < 0) continue;
-        const tp_agg& ag = d.aggs[a];
-        q.sa[s] = devcol(S.fact, ag.col_a, colptr[ag.col_a]);
-        if (ag.kind == TP_AGG_SUM_MUL_SUB) {
-            q.skind[s] = tpk::S_MUL_SUB;
-            q.sb[s] = devcol(S.fact, ag.col_b, colptr[ag.col_b]);
-            q.sk[s] = ag.k;
-        } else {
-            q.skind[s] = tpk::S_SUM;
-        }
-    }
-    q.eager = S.eager ? 1 : 0;
-    q.err = S.err;
-    return q;
+    return tp::plan_query_dev(S.p, colptr, S.jt, S.err, S.eager);
 }
 
 tp_status cuda_check(cudaError_t e, const char* what) {
@@ -349,56 +313,6 @@ tp_status sample_selectivity(ExecState& S) {
     return TP_OK;
 }
 
-// True when column bounds prove that every sum of the query stays inside
-// int64 over all n fact rows, so kernels may accumulate 64-bit values without
-// carry handling.  |a| <= A and |K - b| <= D give |term| <= A * D < 2^127.
-bool sums_fit_int64(const tp_plan* p, const tp_table* fact) {
-    const uint64_t n = fact->rows;
-    if (n == 0) return true;
-    if (n >= (1ull << 32)) return false;   // per-CTA 32-bit counts
-    const tp_plan_desc& d = p->d;
-    typedef __int128 i128;
-    auto mag = [](i128 v) { return v < 0 ? -v : v; };
-    const i128 limit = ((i128)1 << 63) - 1;
-    for (int a = 0; a < d.n_agg; ++a) {
-        const tp_agg& ag = d.aggs[a];
-        if (ag.kind == TP_AGG_COUNT) continue;
-        const i128 A = std::max(mag(fact->cmin[ag.col_a]), mag(fact->cmax[ag.col_a]));
-        i128 B = A;
-        if (ag.kind == TP_AGG_SUM_MUL_SUB) {
-            const i128 D = std::max(mag((i128)ag.k - fact->cmin[ag.col_b]), mag((i128)ag.k - fact->cmax[ag.col_b]));
-            if (D > limit) return false;
-            B = A * D;
-        }
-        if (B > limit / (i128)n) return false;
-    }
-    return true;
-}
-
-// Per-row term range of every sum slot, from column statistics.
-void term_bounds(const tp_plan* p, const tp_table* fact, tpk::TermBounds* out) {
-    const tp_plan_desc& d = p->d;
-    typedef __int128 i128;
-    for (int a = 0; a < d.n_agg; ++a) {
-        const int s = p->sum_of_agg[a];
-        if (s < 0) continue;
-        const tp_agg& ag = d.aggs[a];
-        i128 lo = fact->cmin[ag.col_a], hi = fact->cmax[ag.col_a];
-        if (ag.kind == TP_AGG_SUM_MUL_SUB) {
-            const i128 d0 = (i128)ag.k - fact->cmax[ag.col_b], d1 = (i128)ag.k - fact->cmin[ag.col_b];
-            const i128 c[4] = {lo * d0, lo * d1, hi * d0, hi * d1};
-            lo = hi = c[0];
-            for (int i = 1; i < 4; ++i) {
-                lo = c[i] < lo ? c[i] : lo;
-                hi = c[i] > hi ? c[i] : hi;
-            }
-        }
-        // only used when sums_fit_int64 holds, so both ends fit in int64
-        out[s].lo = (int64_t)lo;
-        out[s].span = (uint64_t)(hi - lo);
-    }
-}
-
 tp_status map_err(uint32_t err) {
     if (err & tpk::ERR_DUP) return fail(TP_E_DUP_KEY, "join build side holds a duplicate key");
     if (err & tpk::ERR_RANGE) return fail(TP_E_RANGE, "a group field value does not fit its bit width");
@@ -502,10 +416,20 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
     S.eager = p->selectivity >= 0.25;
     // ---- reservation estimate (Section 3.3.2)
     uint64_t est = 0;
+    uint64_t join_bytes = 0;
     if (S.dim) {
         S.key64 = S.dim->types[d.join.dim_col] == TP_I64;
-        S.join_cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(S.dim->rows / lf)));
-        est += align256(S.join_cap * (S.key64 ? 16 : 8));
+        uint64_t range = 0;
+        if (!(e->cfg.flags & TP_FLAG_NO_DIRECT_JOIN) && direct_join_range(S.dim, d.join.dim_col, &range)) {
+            S.jt.direct = 1;
+            S.jt.kmin = S.dim->cmin[d.join.dim_col];
+            S.jt.range = range;
+            join_bytes = range * 4;
+        } else {
+            S.join_cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(S.dim->rows / lf)));
+            join_bytes = S.join_cap * (S.key64 ? 16 : 8);
+        }
+        est += align256(join_bytes);
         if (S.dim->placement == PL_PAGES) est += 4 * align256(S.dim->batch_rows * 8);
     }
     if (S.fact->placement == PL_PAGES) {
@@ -536,11 +460,10 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
     // ---- join table
     if (S.dim) {
         void* slots = nullptr;
-        const uint64_t jbytes = S.join_cap * (S.key64 ? 16 : 8);
-        if ((s = sc.alloc(&slots, jbytes))) return s;
-        TP_TRY_CUDA(cudaMemsetAsync(slots, 0xFF, jbytes, st));
+        if ((s = sc.alloc(&slots, join_bytes))) return s;
+        TP_TRY_CUDA(cudaMemsetAsync(slots, 0xFF, join_bytes, st));
         S.jt.slots = (uint64_t*)slots;
-        S.jt.mask = S.join_cap - 1;
+        S.jt.mask = S.join_cap ? S.join_cap - 1 : 0;
         S.jt.side = (uint32_t*)((uint8_t*)misc + 128);
         S.jt.key64 = S.key64 ? 1 : 0;
         if ((s = build_join(S, sc))) return s;
@@ -702,6 +625,109 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
 }
 
 }  // namespace
+
+namespace tp {
+
+tpk::QueryDev plan_query_dev(const tp_plan* p, const std::vector<const void*>& colptr, const tpk::JoinTable& jt,
+                             uint32_t* err, bool eager) {
+    const tp_plan_desc& d = p->d;
+    tpk::QueryDev q{};
+    q.has_filter = d.filter.col >= 0;
+    if (q.has_filter) {
+        q.fcol = devcol(p->d.fact, d.filter.col, colptr[d.filter.col]);
+        q.flo = d.filter.lo;
+        q.fhi = d.filter.hi;
+    }
+    q.has_join = d.join.fact_col >= 0;
+    if (q.has_join) {
+        q.fk = devcol(p->d.fact, d.join.fact_col, colptr[d.join.fact_col]);
+        q.jt = jt;
+    }
+    q.n_group = d.n_group;
+    for (int g = 0; g < d.n_group; ++g) {
+        q.gside[g] = d.group[g].side;
+        q.gbits[g] = d.group[g].bits;
+        q.gdpos[g] = p->gdpos[g];
+        if (d.group[g].side == TP_SIDE_FACT) q.gcol[g] = devcol(p->d.fact, d.group[g].col, colptr[d.group[g].col]);
+    }
+    q.n_sum = p->n_sum;
+    for (int a = 0; a < d.n_agg; ++a) {
+        const int s = p->sum_of_agg[a];
+        if (s < 0) continue;
+        const tp_agg& ag = d.aggs[a];
+        q.sa[s] = devcol(p->d.fact, ag.col_a, colptr[ag.col_a]);
+        if (ag.kind == TP_AGG_SUM_MUL_SUB) {
+            q.skind[s] = tpk::S_MUL_SUB;
+            q.sb[s] = devcol(p->d.fact, ag.col_b, colptr[ag.col_b]);
+            q.sk[s] = ag.k;
+        } else {
+            q.skind[s] = tpk::S_SUM;
+        }
+    }
+    q.eager = eager ? 1 : 0;
+    q.err = err;
+    return q;
+}
+
+// True when column bounds prove that every sum of the query stays inside
+// int64 over all n fact rows, so kernels may accumulate 64-bit values without
+// carry handling.  |a| <= A and |K - b| <= D give |term| <= A * D < 2^127.
+bool direct_join_range(const tp_table* dim, int col, uint64_t* range) {
+    if (dim->rows == 0) return false;
+    const __int128 r = (__int128)dim->cmax[col] - (__int128)dim->cmin[col] + 1;
+    if (r <= 0 || r > (__int128)2 * (__int128)dim->rows || r >= ((__int128)1 << 31)) return false;
+    *range = (uint64_t)r;
+    return true;
+}
+
+bool sums_fit_int64(const tp_plan* p, const tp_table* fact) {
+    const uint64_t n = fact->rows;
+    if (n == 0) return true;
+    if (n >= (1ull << 32)) return false;   // per-CTA 32-bit counts
+    const tp_plan_desc& d = p->d;
+    typedef __int128 i128;
+    auto mag = [](i128 v) { return v < 0 ? -v : v; };
+    const i128 limit = ((i128)1 << 63) - 1;
+    for (int a = 0; a < d.n_agg; ++a) {
+        const tp_agg& ag = d.aggs[a];
+        if (ag.kind == TP_AGG_COUNT) continue;
+        const i128 A = std::max(mag(fact->cmin[ag.col_a]), mag(fact->cmax[ag.col_a]));
+        i128 B = A;
+        if (ag.kind == TP_AGG_SUM_MUL_SUB) {
+            const i128 D = std::max(mag((i128)ag.k - fact->cmin[ag.col_b]), mag((i128)ag.k - fact->cmax[ag.col_b]));
+            if (D > limit) return false;
+            B = A * D;
+        }
+        if (B > limit / (i128)n) return false;
+    }
+    return true;
+}
+
+// Per-row term range of every sum slot, from column statistics.
+void term_bounds(const tp_plan* p, const tp_table* fact, tpk::TermBounds* out) {
+    const tp_plan_desc& d = p->d;
+    typedef __int128 i128;
+    for (int a = 0; a < d.n_agg; ++a) {
+        const int s = p->sum_of_agg[a];
+        if (s < 0) continue;
+        const tp_agg& ag = d.aggs[a];
+        i128 lo = fact->cmin[ag.col_a], hi = fact->cmax[ag.col_a];
+        if (ag.kind == TP_AGG_SUM_MUL_SUB) {
+            const i128 d0 = (i128)ag.k - fact->cmax[ag.col_b], d1 = (i128)ag.k - fact->cmin[ag.col_b];
+            const i128 c[4] = {lo * d0, lo * d1, hi * d0, hi * d1};
+            lo = hi = c[0];
+            for (int i = 1; i < 4; ++i) {
+                lo = c[i] < lo ? c[i] : lo;
+                hi = c[i] > hi ? c[i] : hi;
+            }
+        }
+        // only used when sums_fit_int64 holds, so both ends fit in int64
+        out[s].lo = (int64_t)lo;
+        out[s].span = (uint64_t)(hi - lo);
+    }
+}
+
+}  // namespace tp
 
 extern "C" {
 

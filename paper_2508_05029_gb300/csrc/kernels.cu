@@ -48,48 +48,9 @@ cudaError_t launch_init_agg(uint64_t* slots, uint64_t n_slots, uint32_t words, c
 // -------------------------------------------------------------------- build
 
 __global__ void __launch_bounds__(256) k_build(const __grid_constant__ BuildDev b, uint64_t n) {
-    const JoinTable& jt = b.jt;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        int64_t key = ld1(b.key, i);
-        // Dimension group fields packed into bits 0..30 of the payload; bit 31
-        // marks a row with a field outside its width.  That is an error only
-        // if a surviving fact row joins to it, which the probe side reports.
-        uint32_t payload = 0;
-        for (int f = 0; f < b.n_dfield; ++f) {
-            int64_t v = ld1(b.dcol[f], i);
-            if (v < 0 || ((uint64_t)v >> b.dbits[f]) != 0) payload |= PAYLOAD_BAD;
-            else payload |= (uint32_t)((uint64_t)v << b.dpos[f]);
-        }
-        bool special = jt.key64 ? (uint64_t)key == EMPTY64 : (uint32_t)key == EMPTY32;
-        if (special) {
-            if (atomicCAS(jt.side, 0u, 1u) != 0u) atomicOr(b.err, ERR_DUP);
-            else jt.side[1] = payload;
-            continue;
-        }
-        uint64_t s = join_hash(jt, key) & jt.mask;
-        bool placed = false;
-        for (uint64_t it = 0; it <= jt.mask; ++it) {
-            if (!jt.key64) {
-                unsigned long long want = ((unsigned long long)payload << 32) | (uint32_t)key;
-                unsigned long long prev =
-                    atomicCAS((unsigned long long*)jt.slots + s, (unsigned long long)EMPTY64, want);
-                if (prev == EMPTY64) { placed = true; break; }
-                if ((uint32_t)prev == (uint32_t)key) { atomicOr(b.err, ERR_DUP); placed = true; break; }
-            } else {
-                unsigned long long prev = atomicCAS((unsigned long long*)jt.slots + 2 * s,
-                                                    (unsigned long long)EMPTY64, (unsigned long long)key);
-                if (prev == EMPTY64) {
-                    jt.slots[2 * s + 1] = payload;
-                    placed = true;
-                    break;
-                }
-                if (prev == (unsigned long long)key) { atomicOr(b.err, ERR_DUP); placed = true; break; }
-            }
-            s = (s + 1) & jt.mask;
-        }
-        if (!placed) atomicOr(b.err, ERR_INTERNAL);
-    }
+         i += (uint64_t)gridDim.x * blockDim.x)
+        build_insert(b, i);
 }
 
 cudaError_t launch_build(const BuildDev& b, uint64_t n, int num_sms, cudaStream_t st) {
@@ -279,86 +240,10 @@ cudaError_t launch_agg_global(const QueryDev& q, uint64_t n, const AggTable& t, 
 
 // ---------------------------------------------------------------- finalise
 
-// Correctly rounded conversion of a 128-bit integer to double.  Values that
-// fit in 64 bits use the hardware conversion directly.  Wider magnitudes keep
-// their top 64 bits and fold every discarded bit into the lowest kept bit
-// (a "sticky" bit): with 64 kept bits and 53 significand bits the rounding
-// decision (round bit plus "anything below it") is unchanged, so one
-// round-to-nearest conversion of the 64-bit value, scaled by an exact power
-// of two, is the correctly rounded result.
-__device__ __forceinline__ double i128_to_double(uint64_t lo, uint64_t hi) {
-    if (hi == (uint64_t)((int64_t)lo >> 63)) return __ll2double_rn((long long)lo);
-    const bool neg = (int64_t)hi < 0;
-    uint64_t mlo = lo, mhi = hi;
-    if (neg) {  // two's complement negate; -2^127 maps to 2^127 as unsigned
-        mlo = ~lo + 1ull;
-        mhi = ~hi + (mlo == 0 ? 1ull : 0ull);
-    }
-    double d;
-    if (mhi == 0) {
-        d = __ull2double_rn(mlo);
-    } else {
-        const int lz = __clzll((long long)mhi);
-        const int s = 64 - lz;  // 1..64
-        uint64_t top, sticky;
-        if (s == 64) {
-            top = mhi;
-            sticky = mlo != 0;
-        } else {
-            top = (mhi << (64 - s)) | (mlo >> s);
-            sticky = (mlo & ((1ull << s) - 1ull)) != 0;
-        }
-        d = ldexp(__ull2double_rn(top | sticky), s);
-    }
-    return neg ? -d : d;
-}
-
-__device__ __forceinline__ void write_row(const OutDev& o, uint64_t pos, uint64_t key, uint64_t c,
-                                          const uint64_t* lo_hi, int n_sum) {
-    o.keys[pos] = key;
-    o.counts[pos] = (int64_t)c;
-    for (int s = 0; s < n_sum; ++s) {
-        o.sums[s][2 * pos] = lo_hi[2 * s];
-        o.sums[s][2 * pos + 1] = lo_hi[2 * s + 1];
-        if (o.has_avg[s])
-            o.avgs[s][pos] = __ddiv_rn(i128_to_double(lo_hi[2 * s], lo_hi[2 * s + 1]),
-                                       __ll2double_rn((long long)c));
-    }
-}
-
 // One CTA walks the dense table in key order, so the output is sorted.
 __global__ void __launch_bounds__(1024) k_final_dense(const uint64_t* __restrict__ gacc, uint32_t G,
                                                      int n_sum, const __grid_constant__ OutDev o, int lo_only) {
-    __shared__ uint32_t warp_tot[32];
-    __shared__ uint64_t base;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t c0 = 0; c0 < G; c0 += blockDim.x) {
-        const uint32_t g = c0 + threadIdx.x;
-        const bool has = g < G && gacc[g] != 0;
-        const unsigned m = __ballot_sync(0xffffffffu, has);
-        if (lane == 0) warp_tot[warp] = __popc(m);
-        __syncthreads();
-        uint32_t before = 0, total = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            if (w < warp) before += warp_tot[w];
-            total += warp_tot[w];
-        }
-        if (has) {
-            const uint64_t pos = base + before + __popc(m & ((1u << lane) - 1u));
-            uint64_t lh[2 * MAX_SUM];
-            for (int s = 0; s < n_sum; ++s) {
-                lh[2 * s] = gacc[(uint64_t)G * (1 + 2 * s) + g];
-                lh[2 * s + 1] = lo_only ? (uint64_t)((int64_t)lh[2 * s] >> 63) : gacc[(uint64_t)G * (2 + 2 * s) + g];
-            }
-            write_row(o, pos, g, gacc[g], lh, n_sum);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) base += total;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *o.n_groups = base;
+    final_dense_block(gacc, G, n_sum, o, lo_only != 0);
 }
 
 cudaError_t launch_final_dense(const uint64_t* gacc, uint32_t key_bits, int n_sum, const OutDev& o,

@@ -35,16 +35,23 @@ struct DevCol {
     int32_t pad;
 };
 
-// Join hash table.  32-bit keys: one 64-bit word per slot, payload << 32 | key,
-// EMPTY = all ones.  64-bit keys: two words per slot {key, payload}, EMPTY key
-// = all ones.  A key equal to the EMPTY pattern lives in side[]:
-// side[0] = 1 when present, side[1] = its payload.
+// Join table.
+//   Hash: 32-bit keys: one 64-bit word per slot, payload << 32 | key, EMPTY =
+//   all ones.  64-bit keys: two words per slot {key, payload}, EMPTY key = all
+//   ones.  A key equal to the EMPTY pattern lives in side[]: side[0] = 1 when
+//   present, side[1] = its payload.
+//   Direct (dense keys: the key range is at most twice the row count): one
+//   32-bit payload word per key in [kmin, kmin + range), at slot key - kmin;
+//   EMPTY32 = absent (an out-of-range payload is stored as exactly
+//   PAYLOAD_BAD, so no present payload equals EMPTY32).
 struct JoinTable {
     uint64_t* slots;
-    uint64_t mask;          // capacity - 1 (capacity a power of two)
-    uint32_t* side;         // 2 words
+    uint64_t mask;          // hash: capacity - 1 (capacity a power of two)
+    uint32_t* side;         // hash: 2 words
     int32_t key64;
-    int32_t pad;
+    int32_t direct;         // 1: direct-mapped table
+    int64_t kmin;           // direct: smallest key
+    uint64_t range;         // direct: number of slots
 };
 
 // The query as the per-batch kernels see it.  Column pointers address the
@@ -159,6 +166,43 @@ struct TermBounds {
     int64_t lo;      // minimum term
     uint64_t span;   // maximum term - minimum term
 };
+
+// --------------------------------------------------------- batched execution
+
+enum : uint32_t { BI_BUILD = 0, BI_PROBE = 1, BI_FINAL = 2 };
+
+// One task of the batch queue.
+struct BatchItem {
+    uint32_t q;        // query index
+    uint32_t kind;     // BI_*
+    uint64_t r0, r1;   // row range (build: dimension rows, probe: fact rows)
+    uint64_t pad;
+};
+
+// One query of a batch, as the persistent kernel sees it.
+struct BatchQuery {
+    QueryDev q;                 // columns, filter, join table, groups, sums; err = batch error word
+    BuildDev b;                 // build side, same join table
+    uint64_t* acc;              // dense table of 2^key_bits groups: count, then lo/hi per sum
+    OutDev out;
+    uint32_t key_bits;
+    int32_t smem;               // aggregate a probe tile in shared memory first (needs fast)
+    int32_t fast;               // 64-bit accumulation proved safe: low words only
+    uint32_t build_items;
+    uint32_t probe_items;
+    int32_t pad;
+    int8_t sum_mode[MAX_SUM];   // shared-memory table: 1 low word, 2 low + carry word
+    int64_t sum_off[MAX_SUM];   // term offsets making terms non-negative
+};
+
+constexpr int BATCH_THREADS = 512;
+
+// Runs the whole queue: n_items tasks, ctr[0] the next task index,
+// done[q] build chunks finished, done[n_q + q] probe tiles finished.
+cudaError_t launch_batch(const BatchQuery* qs, const BatchItem* items, uint32_t n_items, uint32_t n_q,
+                         unsigned* ctr, uint32_t* err, uint64_t wait_ns, uint32_t smem_bytes, int grid,
+                         cudaStream_t st);
+int batch_grid(uint32_t smem_bytes, int num_sms);
 
 // The same query over the rows from `row` on: every fact column pointer
 // advanced by `row` elements.

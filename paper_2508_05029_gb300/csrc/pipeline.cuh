@@ -208,6 +208,20 @@ __device__ __forceinline__ void probe_rows_k64(const JoinTable& jt, const int64_
 // have fewer than 2^32 slots.
 __device__ __forceinline__ void probe_rows(const JoinTable& jt, const int64_t key[ST_RPL], uint32_t& pm,
                                            uint32_t pay[ST_RPL], uint32_t* err) {
+    if (jt.direct) {  // one payload word per key
+        uint32_t w[ST_RPL];
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) {
+            const uint64_t idx = (uint64_t)key[j] - (uint64_t)jt.kmin;
+            w[j] = ((pm >> j) & 1u) && idx < jt.range ? __ldg((const unsigned int*)jt.slots + idx) : EMPTY32;
+        }
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) {
+            if (w[j] == EMPTY32) pm &= ~(1u << j);
+            pay[j] = w[j];
+        }
+        return;
+    }
     if (!jt.key64) probe_rows_k32(jt, key, pm, pay, err);
     else probe_rows_k64(jt, key, pm, pay, err);
 }

@@ -160,6 +160,18 @@ namespace tp {
 // budget helpers
 tp_status reserve(tp_engine* e, uint64_t bytes);
 void release(tp_engine* e, uint64_t bytes);
+// QueryDev of a plan for one batch of fact columns (colptr[c] = device
+// address of fact column c's first row; nullptr for unread columns).
+tpk::QueryDev plan_query_dev(const tp_plan* p, const std::vector<const void*>& colptr, const tpk::JoinTable& jt,
+                             uint32_t* err, bool eager);
+// Dense dimension keys: the key range of column col is at most twice the
+// row count (and below 2^31), so a direct-mapped join table of *range slots
+// serves it.
+bool direct_join_range(const tp_table* dim, int col, uint64_t* range);
+// Column bounds prove every sum of the plan stays inside int64 over the fact table.
+bool sums_fit_int64(const tp_plan* p, const tp_table* fact);
+// Per-row term range of every sum slot (valid when sums_fit_int64 holds).
+void term_bounds(const tp_plan* p, const tp_table* fact, tpk::TermBounds* out);
 // device memory (stream-ordered allocator on the compute stream)
 tp_status dev_alloc(tp_engine* e, void** p, uint64_t bytes, cudaStream_t st);
 void dev_free(tp_engine* e, void* p, cudaStream_t st);

@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid", 2: "pool_empty", 3: "budget", 4: "dup_key
 TP_AGG_AUTO, TP_AGG_SHARED, TP_AGG_GLOBAL = 0, 1, 2
 TP_I32, TP_I64, TP_U8 = 0, 1, 2
 TP_HOST_PAGES, TP_DEVICE = 1, 2
-TP_FLAG_TIME_KERNELS, TP_FLAG_NO_STAGED, TP_FLAG_EXACT_ONLY = 1, 2, 4
+TP_FLAG_TIME_KERNELS, TP_FLAG_NO_STAGED, TP_FLAG_EXACT_ONLY, TP_FLAG_NO_DIRECT_JOIN = 1, 2, 4, 8
 TP_SIDE_FACT, TP_SIDE_DIM = 0, 1
 TP_AGG_SUM, TP_AGG_SUM_MUL_SUB, TP_AGG_COUNT, TP_AGG_AVG = 0, 1, 2, 3
 
@@ -134,6 +134,11 @@ SIGNATURES = {
     "tp_last_error": (ctypes.c_char_p, []),
     "tp_stats_get": (_i32, [_vp, ctypes.POINTER(tp_stats)]),
     "tp_debug_fail_next_alloc": (_i32, [_vp, _i32]),
+    "tp_batch_create": (_i32, [_vp, _PP, _i32, ctypes.c_char_p, _PP]),
+    "tp_batch_execute": (_i32, [_vp, _PP]),
+    "tp_batch_last_ms": (ctypes.c_double, [_vp]),
+    "tp_batch_destroy": (None, [_vp]),
+    "tp_autotune": (_i32, [_vp, _PP, _i32, ctypes.c_char_p]),
     "tp_execute_noalloc": (_i32, [ctypes.POINTER(tp_plan_desc), _PP, ctypes.POINTER(_i32), _i32, _u64, _PP,
                                   ctypes.POINTER(_i32), _i32, _u64, _vp, _vp, _PP, _PP, ctypes.POINTER(_u64),
                                   _vp]),
@@ -298,6 +303,38 @@ class Engine:
         h = ctypes.c_void_p()
         _check(self.lib.tp_plan_create(self.h, ctypes.byref(d), ctypes.byref(h)))
         return Plan(self, h, list(query["aggs"]))
+
+
+class Batch:
+    """Many plans in one persistent, graph-captured launch (tp_batch_*)."""
+
+    def __init__(self, eng: Engine, plans, tuning_path=None):
+        self.eng, self.plans = eng, list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.h for p in self.plans])
+        h = ctypes.c_void_p()
+        tp = tuning_path.encode() if tuning_path else None
+        _check(eng.lib.tp_batch_create(eng.h, arr, len(self.plans), tp, ctypes.byref(h)))
+        self.h = h
+
+    def execute(self) -> list:
+        """Results in plan order; valid until the next execute() or destroy()."""
+        out = (ctypes.c_void_p * len(self.plans))()
+        _check(self.eng.lib.tp_batch_execute(self.h, out))
+        return [Result(self.eng, ctypes.c_void_p(out[i]), p.aggs) for i, p in enumerate(self.plans)]
+
+    @property
+    def last_ms(self) -> float:
+        return self.eng.lib.tp_batch_last_ms(self.h)
+
+    def destroy(self):
+        if self.h:
+            self.eng.lib.tp_batch_destroy(self.h)
+            self.h = None
+
+
+def autotune(eng: Engine, plans, path: str):
+    arr = (ctypes.c_void_p * len(plans))(*[p.h for p in plans])
+    _check(eng.lib.tp_autotune(eng.h, arr, len(plans), path.encode()))
 
 
 class Table:

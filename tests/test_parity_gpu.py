@@ -205,10 +205,12 @@ def test_budget_refusal_and_release(eng):
     assert eng.budget()[0] == used0
 
 
-@pytest.mark.parametrize("flags", [0, T.TP_FLAG_EXACT_ONLY, T.TP_FLAG_NO_STAGED])
+@pytest.mark.parametrize("flags", [0, T.TP_FLAG_EXACT_ONLY, T.TP_FLAG_NO_STAGED, T.TP_FLAG_NO_DIRECT_JOIN,
+                                   T.TP_FLAG_NO_STAGED | T.TP_FLAG_NO_DIRECT_JOIN])
 def test_every_kernel_path(flags):
-    """Staged 64-bit (bounds prove no overflow), staged exact 128-bit, and the
-    plain-load kernel all give the oracle's result."""
+    """Staged 64-bit (bounds prove no overflow), staged exact 128-bit, the
+    plain-load kernel, and hashed instead of direct-mapped join tables all
+    give the oracle's result."""
     e = T.Engine(page_bytes=4 << 20, n_pages=256, batch_rows=700_000, flags=flags)
     try:
         wl = W.config2("a", n_fact=2_000_011, n_dim=200_000)
