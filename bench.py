@@ -59,6 +59,10 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample-rows", type=int, default=6_000_000)
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary queries")
+    ap.add_argument("--batch-scale", type=float, default=0.25,
+                    help="fact-size scale of the 256-query batched mix (1.0 = the full ~394M rows)")
+    ap.add_argument("--serve-seconds", type=float, default=1.5, help="arrival window per served rate")
+    ap.add_argument("--no-patterns", action="store_true", help="skip the batched and served measurements")
     return ap.parse_args()
 
 
@@ -175,6 +179,25 @@ def profiled_traffic(n_rows: int):
     return int(int(m_b.group(1)) * n_rows / int(m_r.group(1)))
 
 
+def link_peak_gbs(dev, pinned_bytes=2 << 30, page=64 << 20):
+    """Host-to-device copy peak of this machine: cudaMemcpyAsync of 64 MiB pinned
+    pages (torch tensors), best of three passes."""
+    import torch
+    h = torch.empty(pinned_bytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(pinned_bytes, dtype=torch.uint8, device=dev)
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for off in range(0, pinned_bytes, page):
+            d[off:off + page].copy_(h[off:off + page], non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, pinned_bytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del h, d
+    return best
+
+
 # ------------------------------------------------------------- CPU oracle leg
 def cpu_oracle(fact, dim, query, sample_rows):
     import oracle
@@ -218,6 +241,119 @@ def reference_arm(args, world, rank):
         "e2e": {"value": value, "unit": "fact rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+
+# ------------------------------------------------------ batched and served
+def _mix_tables(eng, T, W, torch, dev, n_queries, scale, n_dims=None):
+    """The batched mix: per query its own fact table (lognormal size), a
+    dimension (log-uniform size) and a group count; dims shared round-robin
+    when n_dims is given."""
+    sz = W.config4_sizes(n_queries=n_queries)
+    tabs, plans = [], []
+    dims = {}
+    rows = 0
+    for q in range(n_queries):
+        dq = q % n_dims if n_dims else q
+        wl = W.config4_query(dq, int(sz["fact"][q]), int(sz["dim"][dq]), int(sz["cutoff"][q]),
+                             int(sz["groups"][dq]), fact_scale=scale)
+        if n_dims and q >= n_dims:   # own fact rows, keys of the shared dimension
+            own = W.config4_query(q, int(sz["fact"][q]), int(sz["dim"][dq]), int(sz["cutoff"][q]),
+                                  int(sz["groups"][dq]), fact_scale=scale).fact
+            own["fk"] = wl.dim["pk"][np.arange(own["fk"].size) * 7919 % wl.dim["pk"].size]
+            wl = W.Workload(wl.name, own, wl.dim, wl.query)
+        if dq not in dims:
+            dims[dq] = eng.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in wl.dim.items()})
+            tabs.append(dims[dq])
+        ft = eng.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in wl.fact.items()})
+        tabs.append(ft)
+        rows += wl.n_fact
+        plans.append(eng.plan(ft, dims[dq], wl.query))
+    return tabs, plans, rows
+
+
+def batched_measure(T, W, torch, dev, stream, scale, reps=3):
+    eng = T.Engine(compute_stream=stream.cuda_stream)
+    tabs, plans, rows = _mix_tables(eng, T, W, torch, dev, 256, scale)
+    b = T.Batch(eng, plans)
+    best_b = 1e30
+    for i in range(reps + 1):
+        for r in b.execute():
+            r.free()
+        if i:
+            best_b = min(best_b, b.last_ms)
+    torch.cuda.synchronize()
+    best_p = 1e30
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for p in plans:
+            p.execute().free()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best_p = min(best_p, e0.elapsed_time(e1))
+    b.destroy()
+    for p in plans:
+        p.destroy()
+    for t in tabs:
+        t.destroy()
+    eng.close()
+    return {"queries": 256, "fact_rows": rows, "fact_scale": scale, "batched_ms": best_b, "plain_ms": best_p,
+            "speedup": best_p / best_b, "batched_rows_per_s": rows / (best_b / 1e3),
+            "how": "one persistent graph-captured launch vs 256 tp_execute calls on one stream"}
+
+
+def served_measure(T, W, torch, dev, rates, seconds, scale):
+    """Open-loop Poisson arrivals; latency = scheduled arrival -> result on host."""
+    import threading
+    import time as _t
+    eng = T.Engine()
+    tabs, plans, _ = _mix_tables(eng, T, W, torch, dev, 256, scale, n_dims=64)
+    for p in plans:     # warm: plan history, selectivity samples
+        p.execute().free()
+    out = {}
+    rng = np.random.default_rng(0x7E5E0005)
+    for mode in ("served", "plain"):
+        for rate in rates:
+            srv = T.Server(eng, workers=8, cache_dims=True) if mode == "served" else \
+                T.Server(eng, workers=1, max_inflight=1, cache_dims=False)
+            n = max(8, int(rate * seconds))
+            gaps = rng.exponential(1.0 / rate, n)
+            order = rng.integers(0, len(plans), n)
+            sched, tickets = [], []
+            lat = []
+
+            def collect():
+                for i in range(n):
+                    while len(tickets) <= i:
+                        _t.sleep(0.0002)
+                    res, times = srv.wait(tickets[i], timeout_s=600)
+                    res.free()
+                    lat.append((times[2] - sched[i]) / 1e6)
+            th = threading.Thread(target=collect)
+            th.start()
+            t0 = _t.monotonic_ns()
+            at = t0
+            for i in range(n):
+                at += int(gaps[i] * 1e9)
+                while _t.monotonic_ns() < at:
+                    pass
+                sched.append(at)
+                tickets.append(srv.submit(plans[order[i]]))
+            th.join()
+            wall = (_t.monotonic_ns() - t0) / 1e9
+            st = srv.stats()
+            srv.stop()
+            lat.sort()
+            out[f"{mode}@{rate}"] = {"requests": n, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(len(lat) * 0.99) - 1],
+                                     "qps": n / wall, "cache_hits": st["cache_hits"],
+                                     "inflight_peak": st["inflight_peak"]}
+    for p in plans:
+        p.destroy()
+    for t in tabs:
+        t.destroy()
+    eng.close()
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -334,7 +470,10 @@ def main():
         torch.cuda.synchronize()
         t_e2e = max_over_ranks(time.perf_counter() - t0, world)
         s1 = eng2.stats()
+        link = link_peak_gbs(dev)
+        h2d_gbs = (s1["h2d_bytes"] - s0["h2d_bytes"]) / t_e2e / 1e9
         e2e = {"value": world * n_fact * args.e2e_steps / t_e2e, "unit": "fact rows/s",
+               "link_peak_gbs": link, "link_frac": h2d_gbs / link,
                "h2d_bytes_per_step": (s1["h2d_bytes"] - s0["h2d_bytes"]) // args.e2e_steps,
                "d2h_bytes_per_step": (s1["d2h_bytes"] - s0["d2h_bytes"]) // args.e2e_steps,
                "h2d_gbs": (s1["h2d_bytes"] - s0["h2d_bytes"]) / t_e2e / 1e9,
@@ -343,6 +482,12 @@ def main():
         ft2.destroy()
         dt2.destroy()
         eng2.close()
+
+    patterns = None
+    if not args.no_patterns:
+        patterns = {"batched": batched_measure(T, W, torch, dev, stream, args.batch_scale),
+                    "served": served_measure(T, W, torch, dev, (200, 500, 1000, 2000), args.serve_seconds,
+                                             args.batch_scale)}
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample_rows > 0:
@@ -366,6 +511,7 @@ def main():
                          "kernel": "k_agg_shared_staged", "kernel_ms": k_ms,
                          "alg_bytes_per_launch": alg_bytes},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "extra": extra,
+            "patterns": patterns,
         }
         print(json.dumps(line), flush=True)
     barrier(world)

@@ -238,6 +238,14 @@ typedef struct {
     int32_t agg_strategy;           /* TP_AGG_*; AUTO = engine choice */
     float load_factor;              /* 0 = engine default */
     uint64_t expected_groups;       /* sizing hint for TP_AGG_GLOBAL; 0 = estimate */
+    /* Join partitions P (Section 3.3.2: spill what does not fit).  0 = auto:
+     * a hashed join whose table would take more than half of the free budget
+     * runs as a hybrid hash join with 64 partitions; 1 = never partition;
+     * 2..64 (a power of two) = always partition into P.  Partitions whose
+     * table fits a quarter of the free budget stay resident; the others'
+     * build and fact rows are spilled to pool pages and joined one partition
+     * at a time (TP_E_POOL_EMPTY when the pool cannot hold them). */
+    int32_t join_partitions;
 } tp_plan_desc;
 
 /* Validates and stores a plan.  TP_E_INVALID on any inconsistency. */
@@ -303,6 +311,52 @@ void tp_batch_destroy(tp_batch* b);
  * class to tuning_path (text).  The plans' own results are unaffected.
  */
 tp_status tp_autotune(tp_engine* eng, tp_plan* const* plans, int32_t n, const char* tuning_path);
+
+/* ------------------------------------------------------------------ serving */
+
+/*
+ * A request server over one engine: queries are submitted as they arrive and
+ * run concurrently on `workers` lanes, each a host thread with its own compute
+ * and copy streams, so their kernels overlap on the device (Section 3.3.1: each
+ * Compute Executor thread drives its own CUDA stream).  Admission is by
+ * device-memory reservation (Section 3.3.2): a request whose reservation does
+ * not fit waits in the queue while others run and is admitted as soon as
+ * completions release memory; it fails with TP_E_BUDGET only when it cannot fit
+ * even with nothing else running.  At most max_inflight requests run at once
+ * (0 = workers); requests of the same plan object run one at a time.
+ *
+ * With TP_SERVE_CACHE_DIM the join table of a dimension stays on the device
+ * across requests, keyed by dimension table, key column, dimension group
+ * fields and load factor; cached tables hold their reservation until evicted
+ * (least recently used, when a reservation does not fit) or the server stops.
+ * Hashed joins that would be partitioned bypass the cache.
+ */
+enum { TP_SERVE_CACHE_DIM = 1 };
+typedef struct tp_server tp_server;
+typedef uint64_t tp_ticket;
+
+tp_status tp_server_start(tp_engine* eng, int32_t workers, int32_t max_inflight, uint32_t flags,
+                          tp_server** out);
+/* Queues one execution of p; returns at once with a ticket. */
+tp_status tp_submit(tp_server* srv, tp_plan* p, tp_ticket* out);
+/*
+ * Waits up to timeout_ns (< 0: forever) for a ticket.  TP_E_TIMEOUT if it is
+ * still queued or running (the ticket stays valid); otherwise the request's
+ * own status, with *out its result on TP_OK.  times (may be NULL) receives
+ * three steady-clock nanosecond stamps: submitted, started, finished.  A
+ * finished ticket is consumed by the call.
+ */
+tp_status tp_wait(tp_server* srv, tp_ticket t, int64_t timeout_ns, tp_result** out, int64_t* times);
+typedef struct {
+    uint64_t submitted, completed, failed;
+    uint64_t budget_waits;        /* admissions deferred because the reservation did not fit */
+    uint64_t cache_hits, cache_misses, cache_evictions;
+    uint32_t inflight_peak;
+    uint32_t pad;
+} tp_server_stats;
+tp_status tp_server_stats_get(tp_server* srv, tp_server_stats* out);
+/* Finishes queued and running requests, frees cached tables and lanes. */
+void tp_server_stop(tp_server* srv);
 
 /* ----------------------------------------------------------------- results */
 

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(const BatchQuery* __res
 }
 
 int batch_grid(uint32_t smem_bytes, int num_sms) {
-    cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    ensure_smem_limit((const void*)k_batch, (int)smem_bytes);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BATCH_THREADS, smem_bytes) != cudaSuccess ||
         per_sm < 1)

@@ -114,6 +114,11 @@ __device__ __forceinline__ void atomic_add_i128(uint64_t* lo, uint64_t* hi, I128
 
 // ------------------------------------------------------------------ probing
 
+// Partitioned joins: does this key's partition have its rows in the table?
+__device__ __forceinline__ bool part_resident(const JoinTable& jt, int64_t key) {
+    return jt.part_shift == 0 || ((jt.part_mask >> (fmix64((uint64_t)key) >> jt.part_shift)) & 1ull) != 0;
+}
+
 // Table word load: through the read-only path (NC), or coherent at L2 for
 // tables written earlier in the same kernel launch.
 template <bool NC, typename T>
@@ -127,6 +132,10 @@ __device__ __forceinline__ T ld_table(const T* p) {
 template <bool NC = true>
 __device__ __forceinline__ void probe4(const JoinTable& jt, const int64_t key[4], bool pass[4],
                                        uint32_t payload[4], uint32_t* err) {
+    if (jt.part_shift != 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pass[i] = pass[i] && part_resident(jt, key[i]);
+    }
     if (jt.direct) {
         uint32_t w[4];
 #pragma unroll

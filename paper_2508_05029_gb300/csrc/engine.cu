@@ -151,6 +151,9 @@ tp_status tp_init(const tp_config* cfg, tp_engine** out) {
         for (uint32_t i = 0; i < pp.n_pages; ++i) pp.free_stack[i] = pp.n_pages - 1 - i;
         pp.lent.assign(pp.n_pages, 0);
     }
+    e->lane0.compute = e->compute;
+    e->lane0.copy = e->copy;
+    e->lane0.host_words = e->host_words;
     *out = e.release();
     return TP_OK;
 }
@@ -449,6 +452,7 @@ void tp_table_destroy(tp_table* t) {
     tp_engine* e = t->eng;
     if (t->placement == PL_PAGES) {
         for (auto& b : t->batches) free_batch_pages(e, b);
+        for (uint32_t p : t->chain) tp_page_free(e, p);
     } else if (t->placement == PL_DEVICE) {
         cudaSetDevice(e->device);
         cudaStreamSynchronize(e->compute);

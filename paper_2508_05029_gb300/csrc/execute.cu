@@ -9,7 +9,10 @@
 // them (Section 3.3.3, compute-task pre-loading); with prefetch_depth 0 the
 // compute stream copies each batch itself.
 #include <algorithm>
+#include <climits>
 #include <cmath>
+#include <cstdio>
+#include <string>
 
 #include "tp_internal.h"
 
@@ -81,6 +84,7 @@ struct ExecState {
     uint32_t* err = nullptr;        // device error word
     unsigned long long* counters = nullptr;   // [0] agg used, [1] compact count, [2] max key, [3] sample
     bool eager = true;
+    Lane* lane = nullptr;           // streams and status words of this execution
 };
 
 void mark_launch(tp_engine* e) { e->launches++; }
@@ -155,7 +159,7 @@ tp_status cuda_check(cudaError_t e, const char* what) {
 tp_status build_join(ExecState& S, Scratch& sc) {
     tp_engine* e = S.e;
     const tp_plan_desc& d = S.p->d;
-    cudaStream_t st = e->compute;
+    cudaStream_t st = S.lane->compute;
     tpk::BuildDev b{};
     b.jt = S.jt;
     b.err = S.err;
@@ -209,7 +213,8 @@ tp_status build_join(ExecState& S, Scratch& sc) {
 
 // ------------------------------------------------------- fact batch driver
 
-// Runs `kernel(q, rows)` over every batch of the fact table.
+// Runs `kernel(q, rows, colptr)` over every batch of the fact table; colptr[c]
+// is the device address of column c in the batch (nullptr when unused).
 template <class F>
 tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
     tp_engine* e = S.e;
@@ -221,7 +226,7 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
         if (t->rows == 0) return TP_OK;
         tpk::QueryDev q = make_query(S, colptr);
         e->batches++;
-        return kernel(q, t->rows);
+        return kernel(q, t->rows, colptr);
     }
     if (t->batches.empty()) return TP_OK;
     uint64_t max_rows = 0;
@@ -242,14 +247,14 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
     }
     tp_status rc = TP_OK;
     if (prefetch) {  // the copy stream may touch the slots only after they exist
-        cudaEventRecord(freed[0], e->compute);
-        cudaStreamWaitEvent(e->copy, freed[0], 0);
+        cudaEventRecord(freed[0], S.lane->compute);
+        cudaStreamWaitEvent(S.lane->copy, freed[0], 0);
     }
-    cudaStream_t cs = prefetch ? e->copy : e->compute;
+    cudaStream_t cs = prefetch ? S.lane->copy : S.lane->compute;
     for (size_t bi = 0; bi < t->batches.size() && rc == TP_OK; ++bi) {
         const Batch& b = t->batches[bi];
         const int s = (int)(bi % n_slots);
-        if (prefetch && bi >= (size_t)n_slots) cudaStreamWaitEvent(e->copy, freed[s], 0);
+        if (prefetch && bi >= (size_t)n_slots) cudaStreamWaitEvent(S.lane->copy, freed[s], 0);
         for (int c : S.used) {
             uint8_t* dst = (uint8_t*)slot[s][c];
             for (const Extent& x : b.cols[c]) {
@@ -264,21 +269,25 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
         }
         if (rc) break;
         if (prefetch) {
-            cudaEventRecord(loaded[s], e->copy);
-            cudaStreamWaitEvent(e->compute, loaded[s], 0);
+            cudaEventRecord(loaded[s], S.lane->copy);
+            cudaStreamWaitEvent(S.lane->compute, loaded[s], 0);
         }
         tpk::QueryDev q = make_query(S, colptr);
-        rc = kernel(q, b.rows);
+        rc = kernel(q, b.rows, colptr);
         e->batches++;
-        if (prefetch) cudaEventRecord(freed[s], e->compute);
+        if (prefetch) cudaEventRecord(freed[s], S.lane->compute);
     }
     if (prefetch) {  // the slots are freed on the compute stream after the last copy
-        cudaEventRecord(loaded[0], e->copy);
-        cudaStreamWaitEvent(e->compute, loaded[0], 0);
+        cudaEventRecord(loaded[0], S.lane->copy);
+        cudaStreamWaitEvent(S.lane->compute, loaded[0], 0);
     }
     for (int s = 0; s < n_slots; ++s) {
         cudaEventDestroy(loaded[s]);
         cudaEventDestroy(freed[s]);
+        for (int c : S.used) {  // the staging slots go back to the pool after the last kernel
+            dev_free(e, slot[s][c], S.lane->compute);
+            sc.ptrs.erase(std::find(sc.ptrs.begin(), sc.ptrs.end(), slot[s][c]));
+        }
     }
     return rc;
 }
@@ -304,12 +313,12 @@ tp_status sample_selectivity(ExecState& S) {
     for (int c : S.used) colptr[c] = t->dev_cols[c];
     tpk::QueryDev q = make_query(S, colptr);
     tp_engine* e = S.e;
-    TP_TRY_CUDA(cudaMemsetAsync(S.counters + 3, 0, sizeof(unsigned long long), e->compute));
-    TP_TRY_CUDA(tpk::launch_sample_filter(q, t->rows, samples, S.counters + 3, e->compute));
+    TP_TRY_CUDA(cudaMemsetAsync(S.counters + 3, 0, sizeof(unsigned long long), S.lane->compute));
+    TP_TRY_CUDA(tpk::launch_sample_filter(q, t->rows, samples, S.counters + 3, S.lane->compute));
     mark_launch(e);
-    TP_TRY_CUDA(cudaMemcpyAsync(e->host_words, S.counters + 3, 8, cudaMemcpyDeviceToHost, e->compute));
-    TP_TRY_CUDA(cudaStreamSynchronize(e->compute));
-    p->selectivity = (double)e->host_words[0] / samples;
+    TP_TRY_CUDA(cudaMemcpyAsync(S.lane->host_words, S.counters + 3, 8, cudaMemcpyDeviceToHost, S.lane->compute));
+    TP_TRY_CUDA(cudaStreamSynchronize(S.lane->compute));
+    p->selectivity = (double)S.lane->host_words[0] / samples;
     return TP_OK;
 }
 
@@ -323,7 +332,7 @@ tp_status map_err(uint32_t err) {
 
 // Output arrays for `cap` groups carved from one allocation.
 tp_status alloc_result(tp_engine* e, tp_plan* p, uint64_t cap, tp_result** out, tpk::OutDev* od,
-                       unsigned long long* n_groups_dev) {
+                       unsigned long long* n_groups_dev, cudaStream_t st) {
     const tp_plan_desc& d = p->d;
     int n_avg = 0;
     for (int a = 0; a < d.n_agg; ++a) n_avg += d.aggs[a].kind == TP_AGG_AVG;
@@ -334,8 +343,9 @@ tp_status alloc_result(tp_engine* e, tp_plan* p, uint64_t cap, tp_result** out, 
     tp_result* r = new (std::nothrow) tp_result();
     if (!r) { release(e, bytes); return fail(TP_E_NOMEM, "result: out of host memory"); }
     r->eng = e;
+    r->stream = st;
     r->reserved = bytes;
-    s = dev_alloc(e, &r->dev, bytes, e->compute);
+    s = dev_alloc(e, &r->dev, bytes, st);
     if (s) { release(e, bytes); delete r; return s; }
     uint8_t* base = (uint8_t*)r->dev;
     r->d_keys = (uint64_t*)base; base += align256(c * 8);
@@ -372,14 +382,446 @@ tp_status alloc_result(tp_engine* e, tp_plan* p, uint64_t cap, tp_result** out, 
     return TP_OK;
 }
 
+// ------------------------------------------------------ hybrid hash join
+//
+// A hashed join whose table does not fit the device budget runs partitioned
+// (Section 3.3.2: reserve, and spill what is not needed soon; Section 3.1:
+// Batch Holders move data to a larger tier).  The build keys are split into
+// P partitions by the top bits of fmix64(key).  Partitions whose table fits
+// the table budget stay resident: their rows are inserted into one table and
+// the fact stream probes it, skipping rows of other partitions.  The build
+// and fact rows of the other partitions are spilled to pool pages, then
+// joined one partition at a time against the same accumulators.
+
+struct PartJoin {
+    bool on = false;
+    int P = 0;
+    int shift = 0;
+    uint64_t spill_mask = 0;               // partitions not resident
+    std::vector<uint64_t> dim_count;
+    std::vector<tp_table*> build_spill;    // (key i64, payload i32) per spilled partition
+    std::vector<tp_table*> fact_spill;     // fact-shaped tables per spilled partition
+    unsigned long long* counts = nullptr;  // device: P per-batch counters
+    unsigned long long* cursor = nullptr;  // device: P cursors
+    bool spill_fact = true;                // false on a retry: the fact spill already happened
+    uint64_t table_budget = 0;             // bytes one partition table may take
+    ~PartJoin() {
+        for (tp_table* t : build_spill) tp_table_destroy(t);
+        for (tp_table* t : fact_spill) tp_table_destroy(t);
+    }
+};
+
+tp_table* spill_table(tp_engine* e, const std::vector<int32_t>& types) {
+    tp_table* t = new (std::nothrow) tp_table();
+    if (!t) return nullptr;
+    t->eng = e;
+    t->types = types;
+    t->scales.assign(types.size(), 0);
+    t->names.assign(types.size(), "");
+    t->batch_rows = e->cfg.batch_rows;
+    t->cmin.assign(types.size(), INT64_MIN);
+    t->cmax.assign(types.size(), INT64_MAX);
+    return t;
+}
+
+// Appends nrows rows held in device memory (dev[c] per column, nullptr for a
+// column that is not kept) to a spill table as one batch.  The batch's
+// columns lie back to back where the previous append ended, in the table's
+// page chain (new pool pages as needed), so a partition wastes at most one
+// partial page.  Device -> host copies on the compute stream, synchronised.
+tp_status append_device_rows(tp_engine* e, tp_table* t, const std::vector<const void*>& dev, uint64_t nrows,
+                             cudaStream_t st) {
+    if (nrows == 0) return TP_OK;
+    const uint64_t pb = e->pool.page_bytes;
+    const int nc = (int)t->types.size();
+    Batch b;
+    b.row0 = t->rows;
+    b.rows = nrows;
+    b.cols.resize(nc);
+    uint64_t pos = t->chain_used;
+    for (int c = 0; c < nc; ++c) {
+        if (!dev[c]) continue;
+        pos = align256(pos);
+        const uint8_t* src = (const uint8_t*)dev[c];
+        uint64_t left = nrows * type_size(t->types[c]);
+        while (left) {
+            const uint64_t pi = pos / pb, po = pos % pb, take = std::min<uint64_t>(left, pb - po);
+            while (t->chain.size() <= pi) {
+                tp_page pg;
+                if (tp_page_alloc(e, &pg)) {
+                    cudaStreamSynchronize(st);
+                    return fail(TP_E_POOL_EMPTY, "spilling a join partition: the page pool is exhausted");
+                }
+                t->chain.push_back(pg);
+            }
+            TP_TRY_CUDA(cudaMemcpyAsync((uint8_t*)tp_page_ptr(e, t->chain[pi]) + po, src, take,
+                                        cudaMemcpyDeviceToHost, st));
+            b.cols[c].push_back(Extent{t->chain[pi], 0, po, take});
+            e->d2h_bytes += take;
+            src += take;
+            pos += take;
+            left -= take;
+        }
+    }
+    TP_TRY_CUDA(cudaStreamSynchronize(st));
+    t->chain_used = pos;
+    t->batches.push_back(std::move(b));
+    t->rows += nrows;
+    return TP_OK;
+}
+
+// Calls fn(build, rows) for every batch of the dimension table with the key
+// and group-field columns on the device.
+template <class F>
+tp_status for_each_dim_batch(ExecState& S, Scratch& sc, const tpk::BuildDev& proto, F&& fn) {
+    tp_engine* e = S.e;
+    const tp_plan_desc& d = S.p->d;
+    tp_table* t = S.dim;
+    std::vector<int> bcols = {d.join.dim_col};
+    for (int g = 0; g < d.n_group; ++g)
+        if (d.group[g].side == TP_SIDE_DIM) bcols.push_back(d.group[g].col);
+    tpk::BuildDev b = proto;
+    auto bind = [&](const std::vector<const void*>& ptr) {
+        b.key = devcol(t, bcols[0], ptr[0]);
+        for (int k = 1; k < (int)bcols.size(); ++k) b.dcol[k - 1] = devcol(t, bcols[k], ptr[k]);
+    };
+    if (t->placement != PL_PAGES) {
+        std::vector<const void*> ptr;
+        for (int c : bcols) ptr.push_back(t->dev_cols[c]);
+        bind(ptr);
+        return fn(b, t->rows);
+    }
+    uint64_t max_rows = 0;
+    for (auto& bt : t->batches) max_rows = std::max(max_rows, bt.rows);
+    std::vector<void*> stage(bcols.size(), nullptr);
+    for (size_t i = 0; i < bcols.size(); ++i) {
+        tp_status s = sc.alloc(&stage[i], align256(max_rows * type_size(t->types[bcols[i]])));
+        if (s) return s;
+    }
+    for (auto& bt : t->batches) {
+        for (size_t i = 0; i < bcols.size(); ++i) {
+            uint8_t* dst = (uint8_t*)stage[i];
+            for (const Extent& x : bt.cols[bcols[i]]) {
+                TP_TRY_CUDA(cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes,
+                                            cudaMemcpyHostToDevice, S.lane->compute));
+                dst += x.bytes;
+                e->h2d_bytes += x.bytes;
+            }
+        }
+        bind(std::vector<const void*>(stage.begin(), stage.end()));
+        tp_status s = fn(b, bt.rows);
+        if (s) return s;
+    }
+    return TP_OK;
+}
+
+// Histogram of the build keys, residency by table budget, the resident table
+// (into S.jt, with the partition filter) and the build-side spill.
+tp_status part_setup(ExecState& S, Scratch& sc, PartJoin& pj, uint64_t table_budget, float lf,
+                     tpk::BuildDev proto) {
+    tp_engine* e = S.e;
+    cudaStream_t st = S.lane->compute;
+    const int P = pj.P;
+    void* words = nullptr;
+    tp_status s = sc.alloc(&words, 2 * 8 * (uint64_t)P);
+    if (s) return s;
+    pj.counts = (unsigned long long*)words;
+    pj.cursor = pj.counts + P;
+    TP_TRY_CUDA(cudaMemsetAsync(pj.counts, 0, 8 * (uint64_t)P, st));
+    s = for_each_dim_batch(S, sc, proto, [&](const tpk::BuildDev& b, uint64_t rows) {
+        mark_launch(e);
+        return cuda_check(tpk::launch_part_hist(b.key, rows, pj.shift, pj.counts, e->num_sms, st), "partition");
+    });
+    if (s) return s;
+    std::vector<unsigned long long> cnt(P);
+    TP_TRY_CUDA(cudaMemcpyAsync(cnt.data(), pj.counts, 8 * (uint64_t)P, cudaMemcpyDeviceToHost, st));
+    TP_TRY_CUDA(cudaStreamSynchronize(st));
+    pj.dim_count.assign(cnt.begin(), cnt.end());
+    const uint64_t slot = S.key64 ? 16 : 8;
+    auto table_bytes = [&](uint64_t rows) {
+        return pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(rows / lf))) * slot;
+    };
+    uint64_t resident_rows = 0, mask = 0;
+    for (int p = 0; p < P; ++p) {
+        if (table_bytes(resident_rows + cnt[p]) <= table_budget) {
+            resident_rows += cnt[p];
+            mask |= 1ull << p;
+        }
+    }
+    pj.spill_mask = (P == 64 ? ~0ull : ((1ull << P) - 1)) & ~mask;
+    // the resident table
+    const uint64_t cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(resident_rows / lf)));
+    void* slots = nullptr;
+    if ((s = sc.alloc(&slots, cap * slot))) return s;
+    TP_TRY_CUDA(cudaMemsetAsync(slots, 0xFF, cap * slot, st));
+    S.jt.slots = (uint64_t*)slots;
+    S.jt.mask = cap - 1;
+    S.jt.part_mask = mask;
+    S.jt.part_shift = pj.shift;
+    proto.jt = S.jt;
+    pj.build_spill.assign(P, nullptr);
+    pj.fact_spill.assign(P, nullptr);
+    for (int p = 0; p < P; ++p) {
+        if (!((pj.spill_mask >> p) & 1ull)) continue;
+        pj.build_spill[p] = spill_table(e, {TP_I64, TP_I32});
+        pj.fact_spill[p] = spill_table(e, S.fact->types);
+        if (!pj.build_spill[p] || !pj.fact_spill[p]) return fail(TP_E_NOMEM, "partition tables: out of host memory");
+    }
+    // insert resident rows, spill the others
+    void *skeys = nullptr, *spays = nullptr;
+    uint64_t max_rows = S.dim->placement == PL_PAGES ? 0 : S.dim->rows;
+    for (auto& bt : S.dim->batches) max_rows = std::max(max_rows, bt.rows);
+    if (pj.spill_mask) {
+        if ((s = sc.alloc(&skeys, align256(max_rows * 8))) || (s = sc.alloc(&spays, align256(max_rows * 4)))) return s;
+    }
+    return for_each_dim_batch(S, sc, proto, [&](const tpk::BuildDev& b, uint64_t rows) -> tp_status {
+        mark_launch(e);
+        if (!pj.spill_mask) return cuda_check(tpk::launch_build(b, rows, e->num_sms, st), "build");
+        TP_TRY_CUDA(cudaMemsetAsync(pj.counts, 0, 2 * 8 * (uint64_t)P, st));
+        TP_TRY_CUDA(tpk::launch_part_hist(b.key, rows, pj.shift, pj.counts, e->num_sms, st));
+        std::vector<unsigned long long> bc(P), base(P, 0);
+        TP_TRY_CUDA(cudaMemcpyAsync(bc.data(), pj.counts, 8 * (uint64_t)P, cudaMemcpyDeviceToHost, st));
+        TP_TRY_CUDA(cudaStreamSynchronize(st));
+        uint64_t run = 0;
+        for (int p = 0; p < P; ++p) {
+            base[p] = run;
+            if ((pj.spill_mask >> p) & 1ull) run += bc[p];
+        }
+        TP_TRY_CUDA(cudaMemcpyAsync(pj.counts, base.data(), 8 * (uint64_t)P, cudaMemcpyHostToDevice, st));
+        mark_launch(e);
+        TP_TRY_CUDA(tpk::launch_build_part(b, rows, pj.counts, pj.cursor, (int64_t*)skeys, (uint32_t*)spays,
+                                           e->num_sms, st));
+        for (int p = 0; p < P; ++p) {
+            if (!((pj.spill_mask >> p) & 1ull) || bc[p] == 0) continue;
+            tp_status r = append_device_rows(e, pj.build_spill[p],
+                                             {(const int64_t*)skeys + base[p], (const uint32_t*)spays + base[p]}, bc[p],
+                                             st);
+            if (r) return r;
+        }
+        return TP_OK;
+    });
+}
+
+// Fact rows of spilled partitions in this batch go to their spill tables.
+tp_status part_spill_fact(ExecState& S, Scratch& sc, PartJoin& pj, const tpk::QueryDev& q, uint64_t rows,
+                          const std::vector<const void*>& colptr) {
+    if (!pj.spill_mask || !pj.spill_fact || rows == 0) return TP_OK;
+    tp_engine* e = S.e;
+    cudaStream_t st = S.lane->compute;
+    const int P = pj.P;
+    TP_TRY_CUDA(cudaMemsetAsync(pj.counts, 0, 2 * 8 * (uint64_t)P, st));
+    mark_launch(e);
+    TP_TRY_CUDA(tpk::launch_part_hist_fact(q, rows, pj.shift, pj.spill_mask, pj.counts, e->num_sms, st));
+    std::vector<unsigned long long> bc(P), base(P, 0);
+    TP_TRY_CUDA(cudaMemcpyAsync(bc.data(), pj.counts, 8 * (uint64_t)P, cudaMemcpyDeviceToHost, st));
+    TP_TRY_CUDA(cudaStreamSynchronize(st));
+    uint64_t total = 0;
+    for (int p = 0; p < P; ++p) {
+        base[p] = total;
+        total += bc[p];
+    }
+    if (total == 0) return TP_OK;
+    TP_TRY_CUDA(cudaMemcpyAsync(pj.counts, base.data(), 8 * (uint64_t)P, cudaMemcpyHostToDevice, st));
+    tpk::SpillCols cols{};
+    std::vector<void*> out(S.fact->types.size(), nullptr);
+    for (int c : S.used) {
+        tp_status s = sc.alloc(&out[c], align256(total * type_size(S.fact->types[c])));
+        if (s) return s;
+        cols.src[cols.n] = colptr[c];
+        cols.dst[cols.n] = out[c];
+        cols.esize[cols.n] = type_size(S.fact->types[c]);
+        ++cols.n;
+    }
+    mark_launch(e);
+    TP_TRY_CUDA(tpk::launch_fact_spill(q, rows, pj.spill_mask, cols, pj.counts, pj.cursor, e->num_sms, st));
+    tp_status s = TP_OK;
+    for (int p = 0; p < P && s == TP_OK; ++p) {
+        if (bc[p] == 0) continue;
+        std::vector<const void*> part(S.fact->types.size(), nullptr);
+        for (int c : S.used) part[c] = (const uint8_t*)out[c] + base[p] * type_size(S.fact->types[c]);
+        s = append_device_rows(e, pj.fact_spill[p], part, bc[p], st);
+    }
+    for (int c : S.used) {  // staging goes back once its copies are done (append synchronised)
+        dev_free(e, out[c], st);
+        sc.ptrs.erase(std::find(sc.ptrs.begin(), sc.ptrs.end(), out[c]));
+    }
+    return s;
+}
+
+// Joins every spilled partition: its table from the spilled build pairs, then
+// its spilled fact rows through agg (the same per-batch launcher).
+template <class F>
+tp_status part_phase2(ExecState& S, Scratch& sc, PartJoin& pj, float lf, F&& agg) {
+    if (!pj.spill_mask) return TP_OK;
+    tp_engine* e = S.e;
+    cudaStream_t st = S.lane->compute;
+    const uint64_t slot = S.key64 ? 16 : 8;
+    uint64_t max_cap = 64, max_rows = 0;
+    for (int p = 0; p < pj.P; ++p) {
+        if (!((pj.spill_mask >> p) & 1ull)) continue;
+        max_cap = std::max(max_cap, pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(pj.dim_count[p] / lf))));
+        for (auto& bt : pj.build_spill[p]->batches) max_rows = std::max(max_rows, bt.rows);
+    }
+    if (max_cap * slot > pj.table_budget)
+        return fail(TP_E_BUDGET, "a spilled join partition needs a %llu-byte table, over the %llu-byte budget; "
+                    "use more partitions", (unsigned long long)(max_cap * slot),
+                    (unsigned long long)pj.table_budget);
+    void *slots = nullptr, *keys = nullptr, *pays = nullptr, *side = nullptr;
+    tp_status s;
+    if ((s = sc.alloc(&slots, max_cap * slot)) || (s = sc.alloc(&side, 256)) ||
+        (s = sc.alloc(&keys, align256(std::max<uint64_t>(1, max_rows) * 8))) ||
+        (s = sc.alloc(&pays, align256(std::max<uint64_t>(1, max_rows) * 4))))
+        return s;
+    tp_table* fact = S.fact;
+    const tpk::JoinTable resident = S.jt;
+    for (int p = 0; p < pj.P && s == TP_OK; ++p) {
+        if (!((pj.spill_mask >> p) & 1ull) || pj.fact_spill[p]->rows == 0) continue;
+        const uint64_t cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(pj.dim_count[p] / lf)));
+        TP_TRY_CUDA(cudaMemsetAsync(slots, 0xFF, cap * slot, st));
+        TP_TRY_CUDA(cudaMemsetAsync(side, 0, 256, st));
+        tpk::JoinTable jt = resident;
+        jt.slots = (uint64_t*)slots;
+        jt.mask = cap - 1;
+        jt.side = (uint32_t*)side;
+        jt.part_shift = 0;
+        jt.part_mask = 0;
+        for (auto& bt : pj.build_spill[p]->batches) {
+            void* dst[2] = {keys, pays};
+            for (int c = 0; c < 2; ++c) {
+                uint8_t* o = (uint8_t*)dst[c];
+                for (const Extent& x : bt.cols[c]) {
+                    TP_TRY_CUDA(cudaMemcpyAsync(o, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes,
+                                                cudaMemcpyHostToDevice, st));
+                    o += x.bytes;
+                    e->h2d_bytes += x.bytes;
+                }
+            }
+            mark_launch(e);
+            TP_TRY_CUDA(tpk::launch_build_pairs(jt, (const int64_t*)keys, (const uint32_t*)pays, bt.rows, S.err,
+                                                e->num_sms, st));
+        }
+        S.fact = pj.fact_spill[p];
+        S.jt = jt;
+        s = for_each_batch(S, sc, agg);
+        S.fact = fact;
+        S.jt = resident;
+    }
+    return s;
+}
+
+
+// ------------------------------------------------------- dimension cache
+
+// One execution's use of the dimension cache: a hit (S.jt from the cache), or
+// the build of a new entry into cu.mem.
+struct CacheUse {
+    DimCache* cache = nullptr;
+    std::string key;
+    bool hit = false;
+    bool building = false;
+    void* mem = nullptr;
+    uint64_t bytes = 0;
+    ~CacheUse() {
+        if (!cache || (!hit && !building)) return;
+        std::lock_guard<std::mutex> lk(cache->mu);
+        auto it = cache->entries.find(key);
+        if (it != cache->entries.end() && it->second.users > 0) --it->second.users;
+        cache->cv.notify_all();
+    }
+};
+
+std::string cache_key(const ExecState& S) {
+    const tp_plan_desc& d = S.p->d;
+    char buf[160];
+    snprintf(buf, sizeof(buf), "%p:%d:%d:%d:%.4f", (const void*)S.dim, d.join.dim_col, S.jt.direct, S.key64 ? 1 : 0,
+             (double)S.p->load_factor);
+    std::string k = buf;
+    for (int g = 0; g < d.n_group; ++g) {
+        if (d.group[g].side != TP_SIDE_DIM) continue;
+        snprintf(buf, sizeof(buf), "|%d:%d:%d", d.group[g].col, d.group[g].bits, S.p->gdpos[g]);
+        k += buf;
+    }
+    return k;
+}
+
+tp_status cache_lookup_or_build(ExecState& S, Scratch& sc, DimCache* c, uint64_t join_bytes, CacheUse* cu) {
+    (void)sc;
+    cu->cache = c;
+    cu->key = cache_key(S);
+    std::unique_lock<std::mutex> lk(c->mu);
+    for (;;) {
+        auto it = c->entries.find(cu->key);
+        if (it == c->entries.end()) break;
+        if (it->second.ready) {
+            ++it->second.users;
+            it->second.last_use = ++c->tick;
+            ++c->hits;
+            cu->hit = true;
+            S.jt = it->second.jt;
+            return TP_OK;
+        }
+        c->cv.wait(lk);   // another lane is building it
+    }
+    DimCache::Entry& en = c->entries[cu->key];
+    en.users = 1;
+    ++c->misses;
+    lk.unlock();
+    const uint64_t bytes = align256(join_bytes) + 256;   // table + side cell
+    tp_status s = reserve(S.e, bytes);
+    if (!s) s = dev_alloc(S.e, &cu->mem, bytes, S.lane->compute);
+    if (s) {
+        if (cu->mem) dev_free(S.e, cu->mem, S.lane->compute);
+        lk.lock();
+        c->entries.erase(cu->key);
+        c->cv.notify_all();
+        cu->cache = nullptr;
+        return s;
+    }
+    cu->bytes = bytes;
+    cu->building = true;
+    return TP_OK;
+}
+
+// After S.jt points into cu->mem: build, check the build on this lane, publish.
+tp_status cache_publish(ExecState& S, Scratch& sc, DimCache* c, CacheUse* cu) {
+    tp_status s = build_join(S, sc);
+    uint32_t err = 0;
+    if (!s) {
+        cudaError_t ce = cudaMemcpyAsync(&err, S.err, 4, cudaMemcpyDeviceToHost, S.lane->compute);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(S.lane->compute);
+        if (ce != cudaSuccess) s = fail(TP_E_CUDA, "cached join build: %s", cudaGetErrorString(ce));
+        else if (err & tpk::ERR_DUP) s = fail(TP_E_DUP_KEY, "join build side holds a duplicate key");
+        else if (err & tpk::ERR_INTERNAL) s = fail(TP_E_INTERNAL, "device consistency check failed");
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (s) {
+        dev_free(S.e, cu->mem, S.lane->compute);
+        release(S.e, cu->bytes);
+        c->entries.erase(cu->key);
+        cu->building = false;
+        cu->cache = nullptr;
+        c->cv.notify_all();
+        return s;
+    }
+    DimCache::Entry& en = c->entries[cu->key];
+    en.jt = S.jt;
+    en.mem = cu->mem;
+    en.bytes = cu->bytes;
+    en.ready = true;
+    en.last_use = ++c->tick;
+    c->cv.notify_all();
+    return TP_OK;
+}
+
 // ------------------------------------------------------------- execution
 
-tp_status execute_locked(tp_plan* p, tp_result** out) {
+tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** out) {
     tp_engine* e = p->eng;
     const tp_plan_desc& d = p->d;
-    cudaStream_t st = e->compute;
+    cudaStream_t st = lane->compute;
     TP_TRY_CUDA(cudaSetDevice(e->device));
     ExecState S;
+    S.lane = lane;
     S.p = p;
     S.e = e;
     S.fact = d.fact;
@@ -414,9 +856,38 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
     // and the first size estimate of a global aggregation table)
     if (p->selectivity < 0 && (s = sample_selectivity(S))) return s;
     S.eager = p->selectivity >= 0.25;
-    // ---- reservation estimate (Section 3.3.2)
+    // ---- reservation estimate (Section 3.3.2): streaming buffers and the
+    // aggregation table first; a hashed join table that would crowd what is
+    // left runs partitioned, its table budget taken from the remainder
     uint64_t est = 0;
+    if (S.fact->placement == PL_PAGES) {
+        const int n_slots = e->cfg.prefetch_depth > 0 ? e->cfg.prefetch_depth + 1 : 1;
+        uint64_t max_rows = 0;
+        for (auto& b : S.fact->batches) max_rows = std::max(max_rows, b.rows);
+        for (int c : S.used) est += n_slots * align256(max_rows * type_size(S.fact->types[c]));
+    }
+    const bool shared = p->strategy == TP_AGG_SHARED;
+    const uint32_t G = shared ? (1u << p->key_bits) : 0;
+    uint64_t agg_cap = 0;
+    const uint32_t words = 2 + 2 * ns;
+    uint64_t result_groups = G;
+    if (shared) {
+        est += align256((uint64_t)G * (1 + 2 * ns) * 8);
+    } else {
+        uint64_t groups = d.expected_groups ? d.expected_groups : p->history_groups;
+        if (groups == 0) {
+            groups = (uint64_t)std::ceil(S.fact->rows * std::min(1.0, p->selectivity * 1.25)) + 16;
+            if (p->key_bits < 40) groups = std::min<uint64_t>(groups, 1ull << p->key_bits);
+        }
+        result_groups = groups;
+        agg_cap = pow2_at_least(std::max<uint64_t>(1024, (uint64_t)std::ceil(groups / lf)));
+        // table + compaction/sort arrays
+        est += align256((agg_cap + 1) * words * 8) + 2 * align256((agg_cap + 1) * 12) +
+               align256(tpk::radix_sort_hist_words(agg_cap + 1) * 4);
+    }
     uint64_t join_bytes = 0;
+    PartJoin pj;
+    uint64_t part_table_budget = 0;
     if (S.dim) {
         S.key64 = S.dim->types[d.join.dim_col] == TP_I64;
         uint64_t range = 0;
@@ -429,44 +900,78 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
             S.join_cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(S.dim->rows / lf)));
             join_bytes = S.join_cap * (S.key64 ? 16 : 8);
         }
-        est += align256(join_bytes);
-        if (S.dim->placement == PL_PAGES) est += 4 * align256(S.dim->batch_rows * 8);
-    }
-    if (S.fact->placement == PL_PAGES) {
-        const int n_slots = e->cfg.prefetch_depth > 0 ? e->cfg.prefetch_depth + 1 : 1;
-        uint64_t max_rows = 0;
-        for (auto& b : S.fact->batches) max_rows = std::max(max_rows, b.rows);
-        for (int c : S.used) est += n_slots * align256(max_rows * type_size(S.fact->types[c]));
-    }
-    const bool shared = p->strategy == TP_AGG_SHARED;
-    const uint32_t G = shared ? (1u << p->key_bits) : 0;
-    uint64_t agg_cap = 0;
-    const uint32_t words = 2 + 2 * ns;
-    if (shared) {
-        est += align256((uint64_t)G * (1 + 2 * ns) * 8);
-    } else {
-        uint64_t groups = d.expected_groups ? d.expected_groups : p->history_groups;
-        if (groups == 0) {
-            groups = (uint64_t)std::ceil(S.fact->rows * std::min(1.0, p->selectivity * 1.25)) + 16;
-            if (p->key_bits < 40) groups = std::min<uint64_t>(groups, 1ull << p->key_bits);
+        const uint64_t dim_stage = S.dim->placement == PL_PAGES ? 4 * align256(S.dim->batch_rows * 8) : 0;
+        if (!S.jt.direct) {  // hybrid hash join when the table would crowd the budget
+            uint64_t reserved_now = 0, cap_now = 0;
+            tp_budget_query(e, &reserved_now, &cap_now);
+            // the result arrays are reserved when the groups are known
+            int n_avg = 0;
+            for (int a = 0; a < d.n_agg; ++a) n_avg += d.aggs[a].kind == TP_AGG_AVG;
+            const uint64_t result_est = result_groups * (16 + 16 * (uint64_t)ns + 8 * (uint64_t)n_avg);
+            const uint64_t taken = reserved_now + est + dim_stage + result_est;
+            const uint64_t avail = cap_now > taken ? cap_now - taken : 0;
+            const int jp = d.join_partitions;
+            if (jp > 1 || (jp == 0 && join_bytes > avail / 2)) {
+                pj.on = true;
+                pj.P = jp > 1 ? jp : 64;
+                pj.shift = 64;
+                for (int v = pj.P; v > 1; v >>= 1) --pj.shift;
+                uint64_t fact_rows = 0;
+                for (auto& bt : S.fact->batches) fact_rows = std::max(fact_rows, bt.rows);
+                if (S.fact->placement != PL_PAGES) fact_rows = S.fact->rows;
+                uint64_t used_bytes = 0;
+                for (int c : S.used) used_bytes += type_size(S.fact->types[c]);
+                // build-pair and fact spill staging, then two tables (the
+                // resident one and one spilled partition's) share the rest
+                const uint64_t stage = align256(S.dim->batch_rows * 12) + align256(fact_rows * used_bytes);
+                part_table_budget = avail > stage ? (avail - stage) * 2 / 5 : 0;
+                pj.table_budget = part_table_budget;
+                join_bytes = 2 * part_table_budget + stage;
+            }
         }
-        agg_cap = pow2_at_least(std::max<uint64_t>(1024, (uint64_t)std::ceil(groups / lf)));
-        // table + compaction/sort arrays
-        est += align256((agg_cap + 1) * words * 8) + 2 * align256((agg_cap + 1) * 12) +
-               align256(tpk::radix_sort_hist_words(agg_cap + 1) * 4);
+        if (!(cache && !pj.on)) est += align256(join_bytes);   // a cached table holds its own reservation
+        est += dim_stage;
     }
     if ((s = reserve(e, est))) return s;
     sc.reserved += est;
     // ---- join table
-    if (S.dim) {
+    CacheUse cu;
+    if (S.dim && cache && !pj.on) {
+        s = cache_lookup_or_build(S, sc, cache, join_bytes, &cu);
+        if (s) return s;
+    }
+    if (S.dim && !cu.hit) {
         void* slots = nullptr;
-        if ((s = sc.alloc(&slots, join_bytes))) return s;
-        TP_TRY_CUDA(cudaMemsetAsync(slots, 0xFF, join_bytes, st));
+        if (cu.building) {
+            slots = cu.mem;
+            TP_TRY_CUDA(cudaMemsetAsync(slots, 0xFF, join_bytes, st));
+            TP_TRY_CUDA(cudaMemsetAsync((uint8_t*)slots + align256(join_bytes), 0, 256, st));
+        } else if (!pj.on) {
+            if ((s = sc.alloc(&slots, join_bytes))) return s;
+            TP_TRY_CUDA(cudaMemsetAsync(slots, 0xFF, join_bytes, st));
+        }
         S.jt.slots = (uint64_t*)slots;
         S.jt.mask = S.join_cap ? S.join_cap - 1 : 0;
-        S.jt.side = (uint32_t*)((uint8_t*)misc + 128);
+        S.jt.side = cu.building ? (uint32_t*)((uint8_t*)slots + align256(join_bytes))
+                                : (uint32_t*)((uint8_t*)misc + 128);
         S.jt.key64 = S.key64 ? 1 : 0;
-        if ((s = build_join(S, sc))) return s;
+        if (pj.on) {
+            tpk::BuildDev proto{};
+            proto.err = S.err;
+            int nf = 0;
+            for (int g = 0; g < d.n_group; ++g) {
+                if (d.group[g].side != TP_SIDE_DIM) continue;
+                proto.dbits[nf] = d.group[g].bits;
+                proto.dpos[nf] = p->gdpos[g];
+                ++nf;
+            }
+            proto.n_dfield = nf;
+            if ((s = part_setup(S, sc, pj, part_table_budget, lf, proto))) return s;
+        } else if (cu.building) {
+            if ((s = cache_publish(S, sc, cache, &cu))) return s;
+        } else if ((s = build_join(S, sc))) {
+            return s;
+        }
     }
     // ---- aggregate
     tp_result* res = nullptr;
@@ -482,7 +987,7 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
         tpk::TermBounds bounds[tpk::MAX_SUM] = {};
         if (fast) term_bounds(p, S.fact, bounds);
         int mode = -1;  // 0 plain exact, 1 staged exact, 2 staged 64-bit
-        s = for_each_batch(S, sc, [&](const tpk::QueryDev& q, uint64_t rows) {
+        auto shared_core = [&](const tpk::QueryDev& q, uint64_t rows) -> tp_status {
             tpk::StageLayout L;
             bool can = want_staged && tpk::staged_layout_shared(q, p->key_bits, mode != 1 && fast, bounds, rows,
                                                                 e->num_sms, &L);
@@ -508,19 +1013,29 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
             return cuda_check(timer.run(st, rows, [&] {
                 return tpk::launch_agg_shared(q, rows, (uint64_t*)gacc, p->key_bits, grid, st);
             }), "aggregate");
-        });
+        };
+        auto shared_batch = [&](const tpk::QueryDev& q, uint64_t rows, const std::vector<const void*>& colptr) {
+            tp_status r = shared_core(q, rows);
+            if (r == TP_OK && pj.on) r = part_spill_fact(S, sc, pj, q, rows, colptr);
+            return r;
+        };
+        s = for_each_batch(S, sc, shared_batch);
+        if (s == TP_OK && pj.on) {
+            pj.spill_fact = false;
+            s = part_phase2(S, sc, pj, lf, shared_batch);
+        }
         if (s) return s;
         tpk::OutDev od;
-        if ((s = alloc_result(e, p, G, &res, &od, S.counters + 1))) return s;
+        if ((s = alloc_result(e, p, G, &res, &od, S.counters + 1, st))) return s;
         std::unique_ptr<tp_result, void (*)(tp_result*)> guard(res, tp_result_free);
         TP_TRY_CUDA(tpk::launch_final_dense((const uint64_t*)gacc, p->key_bits, ns, od, st, mode == 2));
         mark_launch(e);
-        TP_TRY_CUDA(cudaMemcpyAsync(e->host_words, misc, 8, cudaMemcpyDeviceToHost, st));
-        TP_TRY_CUDA(cudaMemcpyAsync(e->host_words + 1, S.counters + 1, 8, cudaMemcpyDeviceToHost, st));
+        TP_TRY_CUDA(cudaMemcpyAsync(lane->host_words, misc, 8, cudaMemcpyDeviceToHost, st));
+        TP_TRY_CUDA(cudaMemcpyAsync(lane->host_words + 1, S.counters + 1, 8, cudaMemcpyDeviceToHost, st));
         TP_TRY_CUDA(cudaStreamSynchronize(st));
         e->d2h_bytes += 16;
-        if ((s = map_err((uint32_t)e->host_words[0]))) return s;
-        res->n_groups = e->host_words[1];
+        if ((s = map_err((uint32_t)lane->host_words[0]))) return s;
+        res->n_groups = lane->host_words[1];
         timer.collect();
         guard.release();
     } else {
@@ -546,7 +1061,7 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
             at.words = words;
             at.used = S.counters;
             at.max_used = (uint64_t)(agg_cap * 0.9);
-            s = for_each_batch(S, sc, [&](const tpk::QueryDev& q, uint64_t rows) {
+            auto global_core = [&](const tpk::QueryDev& q, uint64_t rows) -> tp_status {
                 mark_launch(e);
                 tpk::StageLayout L;
                 if (g_staged && tpk::staged_layout_global(q, stage_all, &L)) {
@@ -562,19 +1077,29 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
                 return cuda_check(timer.run(st, rows, [&] {
                     return tpk::launch_agg_global(q, rows, at, e->num_sms, st);
                 }), "aggregate");
-            });
+            };
+            auto global_batch = [&](const tpk::QueryDev& q, uint64_t rows, const std::vector<const void*>& colptr) {
+                tp_status r = global_core(q, rows);
+                if (r == TP_OK && pj.on) r = part_spill_fact(S, sc, pj, q, rows, colptr);
+                return r;
+            };
+            s = for_each_batch(S, sc, global_batch);
+            if (s == TP_OK && pj.on) {
+                pj.spill_fact = false;   // a retry re-reads the spilled partitions, it does not spill again
+                s = part_phase2(S, sc, pj, lf, global_batch);
+            }
             if (s) return s;
-            TP_TRY_CUDA(cudaMemcpyAsync(e->host_words, misc, 8, cudaMemcpyDeviceToHost, st));
-            TP_TRY_CUDA(cudaMemcpyAsync(e->host_words + 1, S.counters, 8, cudaMemcpyDeviceToHost, st));
+            TP_TRY_CUDA(cudaMemcpyAsync(lane->host_words, misc, 8, cudaMemcpyDeviceToHost, st));
+            TP_TRY_CUDA(cudaMemcpyAsync(lane->host_words + 1, S.counters, 8, cudaMemcpyDeviceToHost, st));
             TP_TRY_CUDA(cudaStreamSynchronize(st));
-            const uint32_t err = (uint32_t)e->host_words[0];
+            const uint32_t err = (uint32_t)lane->host_words[0];
             if ((s = map_err(err))) return s;
             if (err & tpk::ERR_OVERFLOW) {
                 timer.ev.clear();  // a discarded attempt is not counted
                 if (attempt >= 6) return fail(TP_E_INTERNAL, "aggregation table overflow after retries");
                 // retry with a table sized from what was seen so far (Section 3.3.2:
                 // a task that ran out of memory is retried with a better estimate)
-                const uint64_t seen = std::max<uint64_t>(e->host_words[1], agg_cap);
+                const uint64_t seen = std::max<uint64_t>(lane->host_words[1], agg_cap);
                 const uint64_t ncap = pow2_at_least((uint64_t)std::ceil(4.0 * seen / lf));
                 dev_free(e, tab, st);
                 sc.ptrs.erase(std::find(sc.ptrs.begin(), sc.ptrs.end(), tab));
@@ -597,11 +1122,11 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
             TP_TRY_CUDA(tpk::launch_compact_global(at, agg_cap + 1, (uint64_t*)k0, (uint32_t*)v0, S.counters + 1,
                                                    S.counters + 2, e->num_sms, st));
             mark_launch(e);
-            TP_TRY_CUDA(cudaMemcpyAsync(e->host_words, S.counters + 1, 16, cudaMemcpyDeviceToHost, st));
+            TP_TRY_CUDA(cudaMemcpyAsync(lane->host_words, S.counters + 1, 16, cudaMemcpyDeviceToHost, st));
             TP_TRY_CUDA(cudaStreamSynchronize(st));
             e->d2h_bytes += 32;
-            const uint64_t n = e->host_words[0];
-            const uint64_t maxkey = e->host_words[1];
+            const uint64_t n = lane->host_words[0];
+            const uint64_t maxkey = lane->host_words[1];
             int bits = 0;
             while (bits < 64 && (maxkey >> bits) != 0) ++bits;
             uint64_t *kk = (uint64_t*)k0, *tk = (uint64_t*)k1;
@@ -609,7 +1134,7 @@ tp_status execute_locked(tp_plan* p, tp_result** out) {
             TP_TRY_CUDA(tpk::radix_sort_pairs(&kk, &vv, &tk, &tv, (uint32_t*)hist, n, bits, st));
             e->launches += 3 * ((bits + 7) / 8);
             tpk::OutDev od;
-            if ((s = alloc_result(e, p, n, &res, &od, S.counters + 1))) return s;
+            if ((s = alloc_result(e, p, n, &res, &od, S.counters + 1, st))) return s;
             TP_TRY_CUDA(tpk::launch_gather_global(at, kk, vv, n, ns, od, e->num_sms, st, gfast));
             mark_launch(e);
             TP_TRY_CUDA(cudaStreamSynchronize(st));
@@ -727,6 +1252,35 @@ void term_bounds(const tp_plan* p, const tp_table* fact, tpk::TermBounds* out) {
     }
 }
 
+tp_status execute_on_lane(tp_plan* p, Lane* lane, DimCache* cache, tp_result** out) {
+    clear_error();
+    if (!p || !out || !lane) return fail(TP_E_INVALID, "execute: NULL argument");
+    *out = nullptr;
+    return execute_locked(p, lane, cache, out);
+}
+
+int cache_evict_idle(tp_engine* e, DimCache* c, uint64_t need) {
+    std::lock_guard<std::mutex> lk(c->mu);
+    int n = 0;
+    uint64_t freed = 0;
+    for (;;) {
+        auto victim = c->entries.end();
+        for (auto it = c->entries.begin(); it != c->entries.end(); ++it)
+            if (it->second.ready && it->second.users == 0 &&
+                (victim == c->entries.end() || it->second.last_use < victim->second.last_use))
+                victim = it;
+        if (victim == c->entries.end()) break;
+        cudaFree(victim->second.mem);   // idle: no work of any stream references it
+        release(e, victim->second.bytes);
+        freed += victim->second.bytes;
+        c->entries.erase(victim);
+        ++c->evictions;
+        ++n;
+        if (need && freed >= need) break;
+    }
+    return n;
+}
+
 }  // namespace tp
 
 extern "C" {
@@ -792,6 +1346,9 @@ tp_status tp_plan_create(tp_engine* e, const tp_plan_desc* d, tp_plan** out) {
     p->dim_bits = dim_bits;
     p->load_factor = d->load_factor > 0 ? d->load_factor : e->cfg.load_factor;
     if (!(p->load_factor > 0.05f && p->load_factor <= 0.9f)) return fail(TP_E_INVALID, "plan: bad load factor");
+    const int jp = d->join_partitions;
+    if (jp < 0 || jp > 64 || (jp > 1 && (jp & (jp - 1)) != 0))
+        return fail(TP_E_INVALID, "plan: join_partitions must be 0, 1 or a power of two up to 64");
     const int want = d->agg_strategy ? d->agg_strategy : e->cfg.agg_strategy;
     const bool fits_shared = key_bits <= 12 && tpk::agg_shared_smem_bytes(key_bits, ns) <= 160 * 1024;
     if (want == TP_AGG_SHARED && !fits_shared)
@@ -809,7 +1366,7 @@ tp_status tp_execute(tp_plan* p, tp_result** out) {
     if (!p || !out) return fail(TP_E_INVALID, "tp_execute: NULL argument");
     *out = nullptr;
     std::lock_guard<std::mutex> lk(p->eng->exec_mu);
-    return execute_locked(p, out);
+    return execute_locked(p, &p->eng->lane0, nullptr, out);
 }
 
 // ----------------------------------------------------------------- results
@@ -891,8 +1448,9 @@ void tp_result_free(tp_result* r) {
     tp_engine* e = r->eng;
     if (r->dev) {
         cudaSetDevice(e->device);
-        cudaStreamSynchronize(e->compute);
-        dev_free(e, r->dev, e->compute);
+        cudaStream_t rs = r->stream ? r->stream : e->compute;
+        cudaStreamSynchronize(rs);
+        dev_free(e, r->dev, rs);
     }
     if (r->reserved) release(e, r->reserved);
     delete r;

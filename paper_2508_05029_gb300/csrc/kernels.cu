@@ -10,9 +10,28 @@
 // holds rows {2l, 2l+1, 64+2l, 64+2l+1}, so every column is read with two
 // fully coalesced vector loads per lane whatever its width (8-bit: 2 bytes,
 // 32-bit: 8 bytes, 64-bit: 16 bytes per load).
+#include <map>
+#include <mutex>
+
 #include "device.cuh"
 
 namespace tpk {
+
+// ------------------------------------------------------ launch attributes
+
+cudaError_t ensure_smem_limit(const void* fn, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> limit;   // (device, kernel) -> bytes set
+    int dev = 0;
+    cudaError_t g = cudaGetDevice(&dev);
+    if (g != cudaSuccess) return g;
+    std::lock_guard<std::mutex> lk(mu);
+    int& cur = limit[{dev, fn}];
+    if (bytes <= cur) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 // --------------------------------------------------------------------- fill
 
@@ -143,7 +162,7 @@ static void* agg_shared_kernel(int n_sum) {
 int agg_shared_grid(uint32_t key_bits, int n_sum, int num_sms) {
     size_t smem = agg_shared_smem_bytes(key_bits, n_sum);
     void* fn = agg_shared_kernel(n_sum);
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ensure_smem_limit(fn, (int)smem);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, AGG_THREADS, smem) != cudaSuccess ||
         per_sm < 1)

@@ -52,6 +52,12 @@ struct JoinTable {
     int32_t direct;         // 1: direct-mapped table
     int64_t kmin;           // direct: smallest key
     uint64_t range;         // direct: number of slots
+    // partitioned join (part_shift != 0): a row joins only when bit
+    // (fmix64(key) >> part_shift) of part_mask is set; part_shift == 0 (the
+    // zero-initialised default) means no partition filter
+    uint64_t part_mask;
+    int32_t part_shift;
+    int32_t pad2;
 };
 
 // The query as the per-batch kernels see it.  Column pointers address the
@@ -226,6 +232,11 @@ inline QueryDev offset_rows(const QueryDev& q, uint64_t row) {
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return cudaGetLastError().
 
+// Raises (never lowers) a kernel's dynamic shared-memory limit to `bytes`.
+// The attribute is process-wide, so lowering it could fail a concurrent
+// launch of the same kernel on another stream that needs more.
+cudaError_t ensure_smem_limit(const void* fn, int bytes);
+
 cudaError_t launch_fill_u64(uint64_t* p, uint64_t n, uint64_t v, cudaStream_t st);
 // aggregation table slots: key word = EMPTY64, every other word 0
 cudaError_t launch_init_agg(uint64_t* slots, uint64_t n_slots, uint32_t words, cudaStream_t st);
@@ -262,6 +273,36 @@ cudaError_t launch_agg_shared_staged(const QueryDev& q, const StageLayout& L, ui
 bool staged_layout_global(const QueryDev& q, bool stage_all, StageLayout* L);
 cudaError_t launch_agg_global_staged(const QueryDev& q, const StageLayout& L, uint64_t n, const AggTable& t,
                                      bool fast, bool fold, int num_sms, cudaStream_t st);
+
+// ------------------------------------------------------- partitioned join
+//
+// Partition of a join key: the top log2(P) bits of fmix64(key), for every key
+// width.  counts[p] += rows of partition p (keys from `key`, rows passing
+// the query's filter when q is given).
+cudaError_t launch_part_hist(const DevCol& key, uint64_t n, int shift, unsigned long long* counts, int num_sms,
+                             cudaStream_t st);
+cudaError_t launch_part_hist_fact(const QueryDev& q, uint64_t n, int shift, uint64_t spill_mask,
+                                  unsigned long long* counts, int num_sms, cudaStream_t st);
+// Build side: rows of resident partitions (bit set in b.jt.part_mask) are
+// inserted; the others go to (keys, pays) at base[p] + cursor[p]++.
+cudaError_t launch_build_part(const BuildDev& b, uint64_t n, const unsigned long long* base,
+                              unsigned long long* cursor, int64_t* keys, uint32_t* pays, int num_sms,
+                              cudaStream_t st);
+// Inserts (key, payload) pairs spilled by launch_build_part.
+cudaError_t launch_build_pairs(const JoinTable& jt, const int64_t* keys, const uint32_t* pays, uint64_t n,
+                               uint32_t* err, int num_sms, cudaStream_t st);
+// Fact side: rows that pass the filter and whose key falls in a partition of
+// spill_mask are copied, column by column (cols[c] != nullptr), to
+// out[c] + (base[p] + cursor[p]++) * size.
+struct SpillCols {
+    const void* src[32];
+    void* dst[32];
+    int32_t esize[32];
+    int32_t n;
+};
+cudaError_t launch_fact_spill(const QueryDev& q, uint64_t n, uint64_t spill_mask, const SpillCols& cols,
+                              const unsigned long long* base, unsigned long long* cursor, int num_sms,
+                              cudaStream_t st);
 
 // Minimum and maximum of a column (out[0] = min, out[1] = max, initialised by
 // the caller to INT64_MAX / INT64_MIN).

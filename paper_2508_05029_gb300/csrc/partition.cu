@@ -1,0 +1,194 @@
+// Radix partitioning for the out-of-core (hybrid) hash join.
+//
+// Paper basis: Section 3.1 (Batch Holders move data to a larger memory tier
+// when the GPU's is scarce), Section 3.3.2 (the Memory Executor spills data
+// that is not needed soon), Section 3.2 (the exchange hash-partitions both
+// join sides).  On one GPU both sides of the join are split into P = 2^k
+// partitions by the top k bits of fmix64(key).  Partitions whose hash table
+// fits the device budget stay resident and are probed while the fact table
+// streams; the build and fact rows of the other partitions are written out
+// (these kernels) and spilled to pinned host pages, then joined one partition
+// at a time.
+#include "device.cuh"
+
+namespace tpk {
+
+__device__ __forceinline__ uint32_t part_of(int64_t key, int shift) {
+    return (uint32_t)(fmix64((uint64_t)key) >> shift);
+}
+
+// Per-block shared histogram, merged into counts.
+__global__ void k_part_hist(const __grid_constant__ DevCol key, uint64_t n, int shift, unsigned long long* counts) {
+    __shared__ unsigned h[256];
+    const uint32_t P = 1u << (64 - shift);
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[part_of(ld1(key, i), shift)], 1u);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+        if (h[i]) atomicAdd(&counts[i], (unsigned long long)h[i]);
+}
+
+cudaError_t launch_part_hist(const DevCol& key, uint64_t n, int shift, unsigned long long* counts, int num_sms,
+                             cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (shift < 56 || shift > 63) return cudaErrorInvalidValue;   // 2..256 partitions
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > (uint64_t)num_sms * 4) blocks = (uint64_t)num_sms * 4;
+    k_part_hist<<<(unsigned)blocks, 256, 0, st>>>(key, n, shift, counts);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ bool fact_row_passes(const QueryDev& q, uint64_t i) {
+    if (!q.has_filter) return true;
+    const int64_t v = ld1(q.fcol, i);
+    return v >= q.flo && v <= q.fhi;
+}
+
+// Fact rows that pass the filter and fall in a spilled partition, per partition.
+__global__ void k_part_hist_fact(const __grid_constant__ QueryDev q, uint64_t n, int shift, uint64_t spill_mask,
+                                 unsigned long long* counts) {
+    __shared__ unsigned h[256];
+    const uint32_t P = 1u << (64 - shift);
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (!fact_row_passes(q, i)) continue;
+        const uint32_t p = part_of(ld1(q.fk, i), shift);
+        if ((spill_mask >> p) & 1ull) atomicAdd(&h[p], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
+        if (h[i]) atomicAdd(&counts[i], (unsigned long long)h[i]);
+}
+
+cudaError_t launch_part_hist_fact(const QueryDev& q, uint64_t n, int shift, uint64_t spill_mask,
+                                  unsigned long long* counts, int num_sms, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    if (shift < 58 || shift > 63) return cudaErrorInvalidValue;   // masks cover at most 64 partitions
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > (uint64_t)num_sms * 4) blocks = (uint64_t)num_sms * 4;
+    k_part_hist_fact<<<(unsigned)blocks, 256, 0, st>>>(q, n, shift, spill_mask, counts);
+    return cudaGetLastError();
+}
+
+// Build rows: insert the resident partitions, spill the others as pairs.
+__global__ void k_build_part(const __grid_constant__ BuildDev b, uint64_t n, const unsigned long long* base,
+                             unsigned long long* cursor, int64_t* keys, uint32_t* pays) {
+    const JoinTable& jt = b.jt;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int64_t key = ld1(b.key, i);
+        const uint32_t p = part_of(key, jt.part_shift);
+        if ((jt.part_mask >> p) & 1ull) {
+            build_insert(b, i);
+            continue;
+        }
+        uint32_t payload = 0;
+        for (int f = 0; f < b.n_dfield; ++f) {
+            const int64_t v = ld1(b.dcol[f], i);
+            if (v < 0 || ((uint64_t)v >> b.dbits[f]) != 0) payload |= PAYLOAD_BAD;
+            else payload |= (uint32_t)((uint64_t)v << b.dpos[f]);
+        }
+        const uint64_t at = base[p] + atomicAdd(&cursor[p], 1ull);
+        keys[at] = key;
+        pays[at] = payload;
+    }
+}
+
+cudaError_t launch_build_part(const BuildDev& b, uint64_t n, const unsigned long long* base,
+                              unsigned long long* cursor, int64_t* keys, uint32_t* pays, int num_sms,
+                              cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > (uint64_t)num_sms * 8) blocks = (uint64_t)num_sms * 8;
+    k_build_part<<<(unsigned)blocks, 256, 0, st>>>(b, n, base, cursor, keys, pays);
+    return cudaGetLastError();
+}
+
+// Insert spilled (key, payload) pairs: the same table layout build_insert makes.
+__global__ void k_build_pairs(const __grid_constant__ JoinTable jt, const int64_t* keys, const uint32_t* pays,
+                              uint64_t n, uint32_t* err) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        // the payload is already packed: the same table logic as build_insert
+        const int64_t key = keys[i];
+        const uint32_t payload = pays[i];
+        if (jt.direct) {
+            const uint32_t v = (payload & PAYLOAD_BAD) ? PAYLOAD_BAD : payload;
+            const uint64_t idx = (uint64_t)key - (uint64_t)jt.kmin;
+            if (idx >= jt.range) { atomicOr(err, ERR_INTERNAL); continue; }
+            if (atomicCAS((unsigned int*)jt.slots + idx, EMPTY32, v) != EMPTY32) atomicOr(err, ERR_DUP);
+            continue;
+        }
+        const bool special = jt.key64 ? (uint64_t)key == EMPTY64 : (uint32_t)key == EMPTY32;
+        if (special) {
+            if (atomicCAS(jt.side, 0u, 1u) != 0u) atomicOr(err, ERR_DUP);
+            else jt.side[1] = payload;
+            continue;
+        }
+        uint64_t s = join_hash(jt, key) & jt.mask;
+        bool placed = false;
+        for (uint64_t it = 0; it <= jt.mask; ++it) {
+            if (!jt.key64) {
+                const unsigned long long want = ((unsigned long long)payload << 32) | (uint32_t)key;
+                const unsigned long long prev =
+                    atomicCAS((unsigned long long*)jt.slots + s, (unsigned long long)EMPTY64, want);
+                if (prev == EMPTY64) { placed = true; break; }
+                if ((uint32_t)prev == (uint32_t)key) { atomicOr(err, ERR_DUP); placed = true; break; }
+            } else {
+                const unsigned long long prev = atomicCAS((unsigned long long*)jt.slots + 2 * s,
+                                                          (unsigned long long)EMPTY64, (unsigned long long)key);
+                if (prev == EMPTY64) {
+                    jt.slots[2 * s + 1] = payload;
+                    placed = true;
+                    break;
+                }
+                if (prev == (unsigned long long)key) { atomicOr(err, ERR_DUP); placed = true; break; }
+            }
+            s = (s + 1) & jt.mask;
+        }
+        if (!placed) atomicOr(err, ERR_INTERNAL);
+    }
+}
+
+cudaError_t launch_build_pairs(const JoinTable& jt, const int64_t* keys, const uint32_t* pays, uint64_t n,
+                               uint32_t* err, int num_sms, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > (uint64_t)num_sms * 8) blocks = (uint64_t)num_sms * 8;
+    k_build_pairs<<<(unsigned)blocks, 256, 0, st>>>(jt, keys, pays, n, err);
+    return cudaGetLastError();
+}
+
+// Fact rows of spilled partitions: copy every requested column to its
+// partition's run in the staging columns.
+__global__ void k_fact_spill(const __grid_constant__ QueryDev q, uint64_t n, uint64_t spill_mask,
+                             const __grid_constant__ SpillCols cols, const unsigned long long* base,
+                             unsigned long long* cursor) {
+    const int shift = q.jt.part_shift;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (!fact_row_passes(q, i)) continue;
+        const uint32_t p = part_of(ld1(q.fk, i), shift);
+        if (!((spill_mask >> p) & 1ull)) continue;
+        const uint64_t at = base[p] + atomicAdd(&cursor[p], 1ull);
+        for (int c = 0; c < cols.n; ++c) {
+            switch (cols.esize[c]) {
+            case 8: ((int64_t*)cols.dst[c])[at] = ((const int64_t*)cols.src[c])[i]; break;
+            case 4: ((int32_t*)cols.dst[c])[at] = ((const int32_t*)cols.src[c])[i]; break;
+            default: ((uint8_t*)cols.dst[c])[at] = ((const uint8_t*)cols.src[c])[i]; break;
+            }
+        }
+    }
+}
+
+cudaError_t launch_fact_spill(const QueryDev& q, uint64_t n, uint64_t spill_mask, const SpillCols& cols,
+                              const unsigned long long* base, unsigned long long* cursor, int num_sms,
+                              cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > (uint64_t)num_sms * 8) blocks = (uint64_t)num_sms * 8;
+    k_fact_spill<<<(unsigned)blocks, 256, 0, st>>>(q, n, spill_mask, cols, base, cursor);
+    return cudaGetLastError();
+}
+
+}  // namespace tpk

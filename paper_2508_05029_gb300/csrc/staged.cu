@@ -290,7 +290,7 @@ template <int NS, bool FAST>
 static cudaError_t launch_staged_t(const QueryDev& q, const StageLayout& L, uint64_t n, uint64_t* gacc,
                                    uint32_t G, int grid, cudaStream_t st) {
     auto fn = k_agg_shared_staged<NS, FAST>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
+    cudaError_t e = ensure_smem_limit((const void*)fn, (int)L.smem_bytes);
     if (e != cudaSuccess) return e;
     fn<<<grid, ST_THREADS, L.smem_bytes, st>>>(q, L, n, gacc, G);
     return cudaGetLastError();

@@ -251,7 +251,7 @@ template <int NS, bool FAST>
 static cudaError_t launch_global_t(const QueryDev& q, const StageLayout& L, uint64_t n, const AggTable& t,
                                    bool fold, int grid, cudaStream_t st) {
     auto fn = k_agg_global_staged<NS, FAST>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
+    cudaError_t e = ensure_smem_limit((const void*)fn, (int)L.smem_bytes);
     if (e != cudaSuccess) return e;
     fn<<<grid, ST_THREADS, L.smem_bytes, st>>>(q, L, n, t, fold ? 1 : 0);
     return cudaGetLastError();

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -77,6 +78,15 @@ struct Batch {
 
 enum Placement : int32_t { PL_PAGES = TP_HOST_PAGES, PL_DEVICE = TP_DEVICE, PL_WRAPPED = 3 };
 
+// The streams and pinned status words one execution uses.  The engine owns
+// one lane (its compute and copy streams); every serving worker owns its own,
+// so executions on different lanes overlap on the device.
+struct Lane {
+    cudaStream_t compute = nullptr;
+    cudaStream_t copy = nullptr;
+    uint64_t* host_words = nullptr;   // 4 KB pinned
+};
+
 }  // namespace tp
 
 struct tp_engine {
@@ -94,6 +104,7 @@ struct tp_engine {
     std::atomic<uint64_t> h2d_bytes{0}, d2h_bytes{0}, batches{0}, launches{0}, retries{0};
     // small pinned scratch for status words read back after an execution
     uint64_t* host_words = nullptr;
+    tp::Lane lane0;                  // compute, copy, host_words of the engine itself
     // fused-kernel timing (TP_FLAG_TIME_KERNELS)
     std::mutex time_mu;
     double agg_ms = 0;
@@ -114,6 +125,9 @@ struct tp_table {
     // per-column minimum and maximum over all rows (valid when rows > 0): the
     // bounds that prove when 64-bit accumulation cannot overflow
     std::vector<int64_t> cmin, cmax;
+    // spill tables: appends continue one page chain owned by the table
+    std::vector<uint32_t> chain;       // pages in order
+    uint64_t chain_used = 0;           // bytes of the chain in use
 };
 
 struct tp_plan {
@@ -134,6 +148,7 @@ struct tp_plan {
 
 struct tp_result {
     tp_engine* eng = nullptr;
+    cudaStream_t stream = nullptr;  // stream its device memory is ordered on (lane compute stream)
     uint64_t n_groups = 0;
     int n_agg = 0;
     int n_sum = 0;
@@ -156,6 +171,31 @@ struct tp_result {
 };
 
 namespace tp {
+
+// Join tables kept on the device across executions (serving): keyed by the
+// dimension table, key column, dimension group fields, load factor and table
+// kind.  An entry is built once by the execution that misses (its lane
+// synchronises and checks the build before publishing it), then shared.
+struct DimCache {
+    struct Entry {
+        tpk::JoinTable jt{};
+        void* mem = nullptr;
+        uint64_t bytes = 0;       // reserved in the engine budget
+        bool ready = false;
+        int users = 0;
+        uint64_t last_use = 0;
+    };
+    std::mutex mu;
+    std::condition_variable cv;
+    std::map<std::string, Entry> entries;
+    uint64_t tick = 0, hits = 0, misses = 0, evictions = 0;
+};
+// Frees idle cached tables (least recently used first) until `need` bytes
+// are released (0: all idle ones); returns the number evicted.
+int cache_evict_idle(tp_engine* e, DimCache* c, uint64_t need);
+// One execution of p on lane (cache may be NULL); the caller serialises
+// executions of the same plan and of the same lane.
+tp_status execute_on_lane(tp_plan* p, Lane* lane, DimCache* cache, tp_result** out);
 
 // budget helpers
 tp_status reserve(tp_engine* e, uint64_t bytes);

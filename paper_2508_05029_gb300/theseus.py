@@ -81,7 +81,8 @@ class tp_plan_desc(ctypes.Structure):
     _fields_ = [("fact", ctypes.c_void_p), ("dim", ctypes.c_void_p), ("filter", tp_filter),
                 ("join", tp_join), ("n_group", ctypes.c_int32), ("group", tp_group_field * 4),
                 ("n_agg", ctypes.c_int32), ("aggs", tp_agg * 8), ("agg_strategy", ctypes.c_int32),
-                ("load_factor", ctypes.c_float), ("expected_groups", ctypes.c_uint64)]
+                ("load_factor", ctypes.c_float), ("expected_groups", ctypes.c_uint64),
+                ("join_partitions", ctypes.c_int32)]
 
 
 class tp_i128(ctypes.Structure):
@@ -94,6 +95,12 @@ class tp_stats(ctypes.Structure):
                 ("retries", ctypes.c_uint64), ("pages_in_use", ctypes.c_uint32),
                 ("pages_total", ctypes.c_uint32), ("agg_kernel_ms", ctypes.c_double),
                 ("agg_kernel_launches", ctypes.c_uint64), ("agg_kernel_rows", ctypes.c_uint64)]
+
+
+class tp_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("budget_waits", ctypes.c_uint64), ("cache_hits", ctypes.c_uint64), ("cache_misses", ctypes.c_uint64),
+                ("cache_evictions", ctypes.c_uint64), ("inflight_peak", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
 _vp, _u64, _i64, _i32, _u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
@@ -139,6 +146,11 @@ SIGNATURES = {
     "tp_batch_last_ms": (ctypes.c_double, [_vp]),
     "tp_batch_destroy": (None, [_vp]),
     "tp_autotune": (_i32, [_vp, _PP, _i32, ctypes.c_char_p]),
+    "tp_server_start": (_i32, [_vp, _i32, _i32, _u32, _PP]),
+    "tp_submit": (_i32, [_vp, _vp, ctypes.POINTER(_u64)]),
+    "tp_wait": (_i32, [_vp, _u64, _i64, _PP, ctypes.POINTER(_i64)]),
+    "tp_server_stats_get": (_i32, [_vp, ctypes.POINTER(tp_server_stats)]),
+    "tp_server_stop": (None, [_vp]),
     "tp_execute_noalloc": (_i32, [ctypes.POINTER(tp_plan_desc), _PP, ctypes.POINTER(_i32), _i32, _u64, _PP,
                                   ctypes.POINTER(_i32), _i32, _u64, _vp, _vp, _PP, _PP, ctypes.POINTER(_u64),
                                   _vp]),
@@ -275,7 +287,7 @@ class Engine:
         return t
 
     def plan(self, fact: "Table", dim: "Table | None", query: dict, agg_strategy=TP_AGG_AUTO,
-             load_factor=0.0, expected_groups=0) -> "Plan":
+             load_factor=0.0, expected_groups=0, join_partitions=0) -> "Plan":
         d = tp_plan_desc()
         d.fact = fact.h
         d.dim = dim.h if dim is not None else None
@@ -300,6 +312,7 @@ class Engine:
             else:
                 raise ValueError(ag)
         d.agg_strategy, d.load_factor, d.expected_groups = agg_strategy, load_factor, expected_groups
+        d.join_partitions = join_partitions
         h = ctypes.c_void_p()
         _check(self.lib.tp_plan_create(self.h, ctypes.byref(d), ctypes.byref(h)))
         return Plan(self, h, list(query["aggs"]))
@@ -330,6 +343,47 @@ class Batch:
         if self.h:
             self.eng.lib.tp_batch_destroy(self.h)
             self.h = None
+
+
+class Server:
+    """Request server (tp_server_*): submit plans, wait for results."""
+
+    def __init__(self, eng: Engine, workers=4, max_inflight=0, cache_dims=True):
+        self.eng = eng
+        h = ctypes.c_void_p()
+        _check(eng.lib.tp_server_start(eng.h, workers, max_inflight, 1 if cache_dims else 0, ctypes.byref(h)))
+        self.h = h
+        self._aggs = {}
+
+    def submit(self, plan: "Plan") -> int:
+        t = ctypes.c_uint64()
+        _check(self.eng.lib.tp_submit(self.h, plan.h, ctypes.byref(t)))
+        self._aggs[t.value] = plan.aggs
+        return t.value
+
+    def wait(self, ticket: int, timeout_s=None):
+        """(Result, (submit_ns, start_ns, end_ns)); raises TPError on failure or timeout."""
+        r = ctypes.c_void_p()
+        times = (ctypes.c_int64 * 3)()
+        ns = -1 if timeout_s is None else int(timeout_s * 1e9)
+        code = self.eng.lib.tp_wait(self.h, ticket, ns, ctypes.byref(r), times)
+        if code != TP_TIMEOUT_CODE:
+            aggs = self._aggs.pop(ticket, [])
+        _check(code)
+        return Result(self.eng, r, aggs), (times[0], times[1], times[2])
+
+    def stats(self) -> dict:
+        s = tp_server_stats()
+        _check(self.eng.lib.tp_server_stats_get(self.h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in tp_server_stats._fields_ if k != "pad"}
+
+    def stop(self):
+        if self.h:
+            self.eng.lib.tp_server_stop(self.h)
+            self.h = None
+
+
+TP_TIMEOUT_CODE = TP_E_TIMEOUT
 
 
 def autotune(eng: Engine, plans, path: str):

@@ -63,7 +63,7 @@ def test_struct_layout_matches_c(tmp_path):
         "tp_config": ["page_bytes", "n_pages", "device_budget_bytes", "prefetch_depth", "batch_rows",
                       "load_factor", "agg_strategy", "compute_stream"],
         "tp_plan_desc": ["fact", "dim", "filter", "join", "n_group", "group", "n_agg", "aggs",
-                         "agg_strategy", "load_factor", "expected_groups"],
+                         "agg_strategy", "load_factor", "expected_groups", "join_partitions"],
         "tp_stats": ["h2d_bytes", "retries", "pages_in_use", "pages_total"],
         "tp_i128": ["lo", "hi"],
         "tp_agg": ["kind", "col_a", "col_b", "k"],
