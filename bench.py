@@ -45,7 +45,12 @@ METRIC = "fact rows/s & HBM GB/s (join+agg); served p50/p99 latency vs plain"
 WORKLOAD = "star-60M-lowcard"
 BYTES_PER_FACT_ROW = 4 + 4 + 8 + 8 + 8 + 1 + 1      # date, fk, qty, price, disc, flag, status
 BYTES_PER_DIM_ROW = 4 + 4                            # pk, attr
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_agg_shared_staged_star12M.md")
+# committed ncu summaries of the dominant kernel, by kernel name: the
+# run-time compiled (plan-specialised) staged kernel, or the ahead-of-time one
+PROFILE_SUMMARY = {"tpj_dense": os.path.join(ROOT, "profiles", "tpj_dense_star12M.md"),
+                   "k_agg_shared_staged": os.path.join(ROOT, "profiles", "k_agg_shared_staged_star12M.md")}
+KERNEL_SOURCES = {"tpj_dense": ("kernels.cuh", "device.cuh", "pipeline.cuh", "jit_dense.cuh", "jit.cu"),
+                  "k_agg_shared_staged": ("kernels.cu", "kernels.cuh", "device.cuh", "pipeline.cuh", "staged.cu")}
 
 
 def parse_args():
@@ -156,25 +161,26 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "kernels.cuh", "device.cuh", "pipeline.cuh", "staged.cu"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2508_05029_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(n_rows: int):
-    """DRAM bytes per launch from the committed ncu summary, scaled to n_rows,
-    or None when the summary is missing or the kernel source changed since."""
+def profiled_traffic(kernel: str, n_rows: int):
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, scaled
+    to n_rows, or None when the summary is missing or the kernel source
+    changed since."""
     try:
-        text = open(PROFILE_SUMMARY).read()
+        text = open(PROFILE_SUMMARY[kernel]).read()
     except OSError:
         return None
     m_src = re.search(r"source_sha\s*=\s*([0-9a-f]+)", text)
     m_b = re.search(r"dram_bytes_per_launch\s*=\s*(\d+)", text)
     m_r = re.search(r"rows_per_launch\s*=\s*(\d+)", text)
-    if not (m_src and m_b and m_r) or m_src.group(1) != kernel_source_hash():
+    if not (m_src and m_b and m_r) or m_src.group(1) != kernel_source_hash(kernel):
         return None
     return int(int(m_b.group(1)) * n_rows / int(m_r.group(1)))
 
@@ -497,7 +503,8 @@ def main():
                "sample": f"first {sample} fact rows of the workload with the full dimension ({secs:.1f} s)"}
 
     if rank == 0:
-        traffic = profiled_traffic(n_fact)
+        kernel = "tpj_dense" if st1["jit_launches"] > st0["jit_launches"] else "k_agg_shared_staged"
+        traffic = profiled_traffic(kernel, n_fact)
         line = {
             "metric": METRIC, "value": value, "unit": "fact rows/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -508,7 +515,7 @@ def main():
             "hbm_gbs": step_gbs,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                         "kernel": "k_agg_shared_staged", "kernel_ms": k_ms,
+                         "kernel": kernel, "kernel_ms": k_ms,
                          "alg_bytes_per_launch": alg_bytes},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "extra": extra,
             "patterns": patterns,

@@ -95,8 +95,22 @@ enum { TP_AGG_AUTO = 0, TP_AGG_SHARED = 1, TP_AGG_GLOBAL = 2 };
  *                         TP_FLAG_NO_DIRECT_JOIN: always hash the join keys,
  *                         even when they are dense enough for a
  *                         direct-mapped table (key range <= 2 x rows).
+ *                         TP_FLAG_NO_JIT: never compile plan-specialised
+ *                         kernels at run time (NVRTC); the ahead-of-time
+ *                         staged kernels run every shape.  Without the flag a
+ *                         plan shape is compiled once per process on first
+ *                         use (tens to hundreds of milliseconds) and cached;
+ *                         when the run-time compiler cannot be loaded or
+ *                         fails, the ahead-of-time kernels run instead and
+ *                         tp_stats counts the failure.
  */
-enum { TP_FLAG_TIME_KERNELS = 1, TP_FLAG_NO_STAGED = 2, TP_FLAG_EXACT_ONLY = 4, TP_FLAG_NO_DIRECT_JOIN = 8 };
+enum {
+    TP_FLAG_TIME_KERNELS = 1,
+    TP_FLAG_NO_STAGED = 2,
+    TP_FLAG_EXACT_ONLY = 4,
+    TP_FLAG_NO_DIRECT_JOIN = 8,
+    TP_FLAG_NO_JIT = 16
+};
 typedef struct {
     uint64_t page_bytes;
     uint32_t n_pages;
@@ -396,6 +410,10 @@ typedef struct {
     double agg_kernel_ms;        /* device time of fused aggregate kernels (TP_FLAG_TIME_KERNELS) */
     uint64_t agg_kernel_launches;
     uint64_t agg_kernel_rows;    /* fact rows those launches processed */
+    uint64_t jit_compiles;       /* plan shapes compiled at run time by this engine */
+    uint64_t jit_failures;       /* shapes whose compilation failed (ahead-of-time kernel used) */
+    uint64_t jit_launches;       /* launches of run-time compiled kernels */
+    double jit_compile_ms;       /* host time spent compiling */
 } tp_stats;
 
 /* Message for the last error on this thread ("" if none). */

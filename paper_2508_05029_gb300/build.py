@@ -2,7 +2,8 @@
 
 Each ``csrc/*.cu`` file compiles to an object in parallel; the objects link
 into one shared library exporting the ``tp_*`` C ABI of
-``include/theseus_gb.h``.  Only the CUDA runtime is linked (statically).
+``include/theseus_gb.h``.  Only the CUDA runtime is linked (statically);
+NVRTC, for plan-specialised kernels, is loaded at run time when present.
 """
 from __future__ import annotations
 
@@ -45,17 +46,44 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _sources() + _headers() + [__file__])
 
 
+# Device headers embedded in the library for run-time (NVRTC) compilation of
+# plan-specialised kernels, in include order.
+JIT_HEADERS = ["kernels.cuh", "device.cuh", "pipeline.cuh", "jit_dense.cuh"]
+
+
+def _write_jit_sources() -> None:
+    """Writes _build/jit_sources.inc: the JIT headers as C++ raw strings."""
+    parts = ["struct JitSource { const char* name; const char* text; };",
+             "const JitSource kJitSources[] = {"]
+    for name in JIT_HEADERS:
+        with open(os.path.join(CSRC, name)) as f:
+            text = f.read()
+        if ')TPJIT"' in text:
+            raise RuntimeError(f"{name} contains the raw-string delimiter")
+        parts.append(f'    {{"{name}", R"TPJIT({text})TPJIT"}},')
+    parts.append("};")
+    out = os.path.join(BUILD_DIR, "jit_sources.inc")
+    new = "\n".join(parts) + "\n"
+    if os.path.exists(out):
+        with open(out) as f:
+            if f.read() == new:
+                return
+    with open(out, "w") as f:
+        f.write(new)
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if not force and up_to_date():
         return LIB
     nvcc = _nvcc()
     os.makedirs(BUILD_DIR, exist_ok=True)
+    _write_jit_sources()
     srcs = _sources()
     objs = [os.path.join(BUILD_DIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(pair):
         src, obj = pair
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-I", BUILD_DIR, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
@@ -68,7 +96,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             if log.strip():
                 print(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-cudart", "static"]
+    cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-cudart", "static", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -472,6 +472,10 @@ tp_status tp_stats_get(tp_engine* e, tp_stats* s) {
     s->batches = e->batches;
     s->kernel_launches = e->launches;
     s->retries = e->retries;
+    s->jit_compiles = e->jit_compiles;
+    s->jit_failures = e->jit_failures;
+    s->jit_launches = e->jit_launches;
+    s->jit_compile_ms = (double)e->jit_us.load() / 1000.0;
     {
         std::lock_guard<std::mutex> lk(e->time_mu);
         s->agg_kernel_ms = e->agg_ms;

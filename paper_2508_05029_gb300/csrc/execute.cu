@@ -986,6 +986,9 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         bool fast = want_staged && !(e->cfg.flags & TP_FLAG_EXACT_ONLY) && sums_fit_int64(p, S.fact);
         tpk::TermBounds bounds[tpk::MAX_SUM] = {};
         if (fast) term_bounds(p, S.fact, bounds);
+        int narrow[tpk::MAX_SUM] = {};
+        narrow_products(p, S.fact, narrow);
+        const bool want_jit = want_staged && !(e->cfg.flags & TP_FLAG_NO_JIT);
         int mode = -1;  // 0 plain exact, 1 staged exact, 2 staged 64-bit
         auto shared_core = [&](const tpk::QueryDev& q, uint64_t rows) -> tp_status {
             tpk::StageLayout L;
@@ -1000,7 +1003,16 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             mark_launch(e);
             if (mode > 0 && can) {
                 const uint64_t whole = rows / tpk::ST_TILE * tpk::ST_TILE;
+                const void* jk = nullptr;
+                if (want_jit && whole) {
+                    std::string why;
+                    jk = jit_kernel(e, dense_shape(q, L, mode == 2, narrow), "tpj_dense", &why);
+                    if (jk) e->jit_launches++;
+                }
                 tp_status r = cuda_check(timer.run(st, whole, [&] {
+                    if (jk)
+                        return tpk::launch_agg_shared_staged_jit(jk, q, L, rows, (uint64_t*)gacc, p->key_bits,
+                                                                 e->num_sms, st);
                     return tpk::launch_agg_shared_staged(q, L, rows, (uint64_t*)gacc, p->key_bits, mode == 2,
                                                          e->num_sms, st);
                 }), "aggregate");
@@ -1226,6 +1238,60 @@ bool sums_fit_int64(const tp_plan* p, const tp_table* fact) {
         if (B > limit / (i128)n) return false;
     }
     return true;
+}
+
+// Sum slots whose product a * (k - b) has both factors inside int32 by the
+// column statistics (the run-time compiled kernels multiply those in 32 bits).
+void narrow_products(const tp_plan* p, const tp_table* fact, int* out) {
+    const tp_plan_desc& d = p->d;
+    for (int a = 0; a < d.n_agg; ++a) {
+        const int s = p->sum_of_agg[a];
+        const tp_agg& ag = d.aggs[a];
+        if (s < 0 || ag.kind != TP_AGG_SUM_MUL_SUB || fact->rows == 0) continue;
+        const __int128 d0 = (__int128)ag.k - fact->cmax[ag.col_b], d1 = (__int128)ag.k - fact->cmin[ag.col_b];
+        out[s] = fact->cmin[ag.col_a] >= INT32_MIN && fact->cmax[ag.col_a] <= INT32_MAX && d0 >= INT32_MIN &&
+                 d1 <= INT32_MAX;
+    }
+}
+
+// Shape of a dense staged launch, as the struct JS the run-time compiled
+// kernel specialises on (layout: jit_dense.cuh).
+std::string dense_shape(const tpk::QueryDev& q, const tpk::StageLayout& L, bool fast, const int* narrow) {
+    auto arr = [](const char* name, const int* v, int n) {
+        std::string r = std::string(name) + "[" + std::to_string(n) + "] = {";
+        for (int i = 0; i < n; ++i) r += (i ? ", " : "") + std::to_string(v[i]);
+        return r + "}";
+    };
+    int gside[tpk::MAX_GROUP] = {}, gtype[tpk::MAX_GROUP] = {}, gbits[tpk::MAX_GROUP] = {};
+    for (int g = 0; g < q.n_group; ++g) {
+        gside[g] = q.gside[g];
+        gtype[g] = q.gside[g] == 0 ? q.gcol[g].type : 0;
+        gbits[g] = q.gbits[g];
+    }
+    int skind[tpk::MAX_SUM] = {}, atype[tpk::MAX_SUM] = {}, btype[tpk::MAX_SUM] = {}, mode[tpk::MAX_SUM] = {},
+        nar[tpk::MAX_SUM] = {};
+    for (int s = 0; s < q.n_sum; ++s) {
+        skind[s] = q.skind[s];
+        atype[s] = q.sa[s].type;
+        btype[s] = q.skind[s] == tpk::S_MUL_SUB ? q.sb[s].type : 0;
+        mode[s] = fast ? L.sum_mode[s] : 0;
+        nar[s] = fast && mode[s] == 2 && q.skind[s] == tpk::S_MUL_SUB ? narrow[s] : 0;
+    }
+    const int join = !q.has_join ? 0 : (q.jt.direct ? 1 : (q.jt.key64 ? 3 : 2));
+    std::string r = "struct JS {\n";
+    r += "    static constexpr int filter = " + std::to_string(q.has_filter ? 1 : 0) +
+         ", ftype = " + std::to_string(q.has_filter ? q.fcol.type : 0) + ", join = " + std::to_string(join) +
+         ", ktype = " + std::to_string(q.has_join ? q.fk.type : 0) +
+         ", part = " + std::to_string(q.has_join && q.jt.part_shift != 0 ? 1 : 0) + ";\n";
+    r += "    static constexpr int ng = " + std::to_string(q.n_group) + ";\n";
+    r += "    static constexpr int " + arr("gside", gside, tpk::MAX_GROUP) + ", " + arr("gtype", gtype, tpk::MAX_GROUP) +
+         ", " + arr("gbits", gbits, tpk::MAX_GROUP) + ";\n";
+    r += "    static constexpr int ns = " + std::to_string(q.n_sum) + ";\n";
+    r += "    static constexpr int " + arr("skind", skind, tpk::MAX_SUM) + ", " + arr("atype", atype, tpk::MAX_SUM) +
+         ", " + arr("btype", btype, tpk::MAX_SUM) + ", " + arr("mode", mode, tpk::MAX_SUM) + ", " +
+         arr("narrow", nar, tpk::MAX_SUM) + ";\n";
+    r += std::string("    static constexpr bool fast = ") + (fast ? "true" : "false") + ";\n};\n";
+    return r;
 }
 
 // Per-row term range of every sum slot, from column statistics.

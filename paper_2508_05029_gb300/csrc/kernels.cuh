@@ -5,8 +5,25 @@
 // (Appleby, public domain) for 64-bit keys and its 32-bit finaliser for join
 // tables with 32-bit keys.
 #pragma once
+#ifdef __CUDACC_RTC__
+// run-time compilation (NVRTC) of the device code: no host headers
+typedef signed char int8_t;
+typedef short int16_t;
+typedef int int32_t;
+typedef long long int64_t;
+typedef unsigned char uint8_t;
+typedef unsigned short uint16_t;
+typedef unsigned int uint32_t;
+typedef unsigned long long uint64_t;
+typedef unsigned long long uintptr_t;
+#define INT32_MIN (-2147483647 - 1)
+#define INT32_MAX 2147483647
+#define INT64_MIN (-9223372036854775807LL - 1)
+#define INT64_MAX 9223372036854775807LL
+#else
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 namespace tpk {
 
@@ -203,13 +220,16 @@ struct BatchQuery {
 
 constexpr int BATCH_THREADS = 512;
 
+#ifndef __CUDACC_RTC__
 // Runs the whole queue: n_items tasks, ctr[0] the next task index,
 // done[q] build chunks finished, done[n_q + q] probe tiles finished.
 cudaError_t launch_batch(const BatchQuery* qs, const BatchItem* items, uint32_t n_items, uint32_t n_q,
                          unsigned* ctr, uint32_t* err, uint64_t wait_ns, uint32_t smem_bytes, int grid,
                          cudaStream_t st);
 int batch_grid(uint32_t smem_bytes, int num_sms);
+#endif
 
+#ifndef __CUDACC_RTC__
 // The same query over the rows from `row` on: every fact column pointer
 // advanced by `row` elements.
 inline QueryDev offset_rows(const QueryDev& q, uint64_t row) {
@@ -264,6 +284,10 @@ bool staged_layout_shared(const QueryDev& q, uint32_t key_bits, bool fast, const
                           uint64_t rows, int num_sms, StageLayout* L);
 cudaError_t launch_agg_shared_staged(const QueryDev& q, const StageLayout& L, uint64_t n, uint64_t* gacc,
                                      uint32_t key_bits, bool fast, int num_sms, cudaStream_t st);
+// The same launch of a run-time compiled, plan-specialised kernel with the
+// signature of tpj_dense (same layout, grid and block).
+cudaError_t launch_agg_shared_staged_jit(const void* kernel, const QueryDev& q, const StageLayout& L, uint64_t n,
+                                         uint64_t* gacc, uint32_t key_bits, int num_sms, cudaStream_t st);
 
 // Staged global-table aggregation.  stage_all = false stages only the filter
 // column (selective filters: the other columns are read for surviving rows
@@ -328,5 +352,6 @@ uint64_t radix_sort_hist_words(uint64_t n);
 cudaError_t radix_sort_pairs(uint64_t** keys, uint32_t** vals, uint64_t** tmp_keys,
                              uint32_t** tmp_vals, uint32_t* hist, uint64_t n, int bits,
                              cudaStream_t st);
+#endif  // __CUDACC_RTC__
 
 }  // namespace tpk

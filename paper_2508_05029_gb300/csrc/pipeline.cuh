@@ -298,13 +298,11 @@ __device__ __forceinline__ void run_pipeline(const QueryDev& q, const StageLayou
     if (warp == 0) {
         if (lane != 0) return;
         const uint64_t pol = l2_evict_first();
-        uint32_t i = 0;
-        int last_fill[ST_MAX_STAGES];
-        for (int s = 0; s < ST_MAX_STAGES; ++s) last_fill[s] = -1;
+        uint32_t filled = 0, fill_parity = 0;   // per stage: ever filled; parity of its last fill
         bool ok = true;
-        for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-            const int s = (int)(i % (uint32_t)L.n_stages);
-            const uint32_t u = i / (uint32_t)L.n_stages;
+        int s = 0;        // stage of this tile
+        uint32_t u = 0;   // how many times the ring has wrapped: stage s's use count
+        for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
             if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1u, L.wait_ns)) {
                 atomicOr(q.err, ERR_TIMEOUT);
                 ok = false;
@@ -316,26 +314,34 @@ __device__ __forceinline__ void run_pipeline(const QueryDev& q, const StageLayou
                 const uint32_t bytes = (uint32_t)ST_TILE * (uint32_t)L.esize[c];
                 bulk_load(dst + L.off[c], (const unsigned char*)L.src[c] + t * bytes, bytes, &full[s], pol);
             }
-            last_fill[s] = (int)u;
+            filled |= 1u << s;
+            fill_parity = (fill_parity & ~(1u << s)) | ((u & 1u) << s);
+            if (++s == L.n_stages) {
+                s = 0;
+                ++u;
+            }
         }
         if (!ok) {  // consumers gave up: let the copies already issued land before exit
             for (int s = 0; s < L.n_stages; ++s)
-                if (last_fill[s] >= 0) mbar_wait(&full[s], (uint32_t)last_fill[s] & 1u, L.wait_ns);
+                if (filled >> s & 1u) mbar_wait(&full[s], fill_parity >> s & 1u, L.wait_ns);
         }
         return;
     }
     const uint32_t r0 = (uint32_t)(warp - 1) * ST_SUB + (uint32_t)lane;
-    uint32_t i = 0;
-    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-        const int s = (int)(i % (uint32_t)L.n_stages);
-        const uint32_t u = i / (uint32_t)L.n_stages;
-        if (!mbar_wait(&full[s], u & 1u, L.wait_ns)) {
+    int s = 0;
+    uint32_t phase = 0;   // parity of stage s's current use
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (!mbar_wait(&full[s], phase, L.wait_ns)) {
             atomicOr(q.err, ERR_TIMEOUT);
             return;
         }
         consume(stages + (uint64_t)s * L.stage_bytes, t * ST_TILE, r0);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == L.n_stages) {
+            s = 0;
+            phase ^= 1u;
+        }
     }
 }
 

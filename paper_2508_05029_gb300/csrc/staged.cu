@@ -316,4 +316,19 @@ cudaError_t launch_agg_shared_staged(const QueryDev& q, const StageLayout& L, ui
     return launch_staged_t<8, false>(q, L, n, gacc, G, grid, st);
 }
 
+cudaError_t launch_agg_shared_staged_jit(const void* kernel, const QueryDev& q, const StageLayout& L, uint64_t n,
+                                         uint64_t* gacc, uint32_t key_bits, int num_sms, cudaStream_t st) {
+    if (n < (uint64_t)ST_TILE) return cudaSuccess;
+    const uint64_t tiles = n / ST_TILE;
+    const uint64_t slots = (uint64_t)num_sms * ST_CTAS;
+    const int grid = (int)(tiles < slots ? tiles : slots);
+    uint32_t G = 1u << key_bits;
+    cudaError_t e = ensure_smem_limit(kernel, (int)L.smem_bytes);
+    if (e != cudaSuccess) return e;
+    QueryDev qa = q;
+    StageLayout la = L;
+    void* args[] = {&qa, &la, &n, &gacc, &G};
+    return cudaLaunchKernel(kernel, dim3(grid), dim3(ST_THREADS), args, L.smem_bytes, st);
+}
+
 }  // namespace tpk

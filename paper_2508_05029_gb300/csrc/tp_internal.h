@@ -102,6 +102,7 @@ struct tp_engine {
     std::mutex obj_mu;
     // statistics
     std::atomic<uint64_t> h2d_bytes{0}, d2h_bytes{0}, batches{0}, launches{0}, retries{0};
+    std::atomic<uint64_t> jit_compiles{0}, jit_failures{0}, jit_launches{0}, jit_us{0};
     // small pinned scratch for status words read back after an execution
     uint64_t* host_words = nullptr;
     tp::Lane lane0;                  // compute, copy, host_words of the engine itself
@@ -197,6 +198,11 @@ int cache_evict_idle(tp_engine* e, DimCache* c, uint64_t need);
 // executions of the same plan and of the same lane.
 tp_status execute_on_lane(tp_plan* p, Lane* lane, DimCache* cache, tp_result** out);
 
+// Kernel `entry` compiled at run time for the shape struct in `prelude`
+// (cached per process); nullptr when run-time compilation is unavailable or
+// failed for this shape, with the reason in *why.
+const void* jit_kernel(tp_engine* e, const std::string& prelude, const char* entry, std::string* why);
+
 // budget helpers
 tp_status reserve(tp_engine* e, uint64_t bytes);
 void release(tp_engine* e, uint64_t bytes);
@@ -212,6 +218,11 @@ bool direct_join_range(const tp_table* dim, int col, uint64_t* range);
 bool sums_fit_int64(const tp_plan* p, const tp_table* fact);
 // Per-row term range of every sum slot (valid when sums_fit_int64 holds).
 void term_bounds(const tp_plan* p, const tp_table* fact, tpk::TermBounds* out);
+// out[s] = 1 for MUL_SUB sum slots whose two factors fit in int32 by the
+// column statistics.
+void narrow_products(const tp_plan* p, const tp_table* fact, int* out);
+// The struct JS source describing a dense staged launch's shape.
+std::string dense_shape(const tpk::QueryDev& q, const tpk::StageLayout& L, bool fast, const int* narrow);
 // device memory (stream-ordered allocator on the compute stream)
 tp_status dev_alloc(tp_engine* e, void** p, uint64_t bytes, cudaStream_t st);
 void dev_free(tp_engine* e, void* p, cudaStream_t st);

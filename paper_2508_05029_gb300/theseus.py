@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid", 2: "pool_empty", 3: "budget", 4: "dup_key
 TP_AGG_AUTO, TP_AGG_SHARED, TP_AGG_GLOBAL = 0, 1, 2
 TP_I32, TP_I64, TP_U8 = 0, 1, 2
 TP_HOST_PAGES, TP_DEVICE = 1, 2
-TP_FLAG_TIME_KERNELS, TP_FLAG_NO_STAGED, TP_FLAG_EXACT_ONLY, TP_FLAG_NO_DIRECT_JOIN = 1, 2, 4, 8
+TP_FLAG_TIME_KERNELS, TP_FLAG_NO_STAGED, TP_FLAG_EXACT_ONLY, TP_FLAG_NO_DIRECT_JOIN, TP_FLAG_NO_JIT = 1, 2, 4, 8, 16
 TP_SIDE_FACT, TP_SIDE_DIM = 0, 1
 TP_AGG_SUM, TP_AGG_SUM_MUL_SUB, TP_AGG_COUNT, TP_AGG_AVG = 0, 1, 2, 3
 
@@ -94,7 +94,9 @@ class tp_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64), ("peak_reserved", ctypes.c_uint64),
                 ("retries", ctypes.c_uint64), ("pages_in_use", ctypes.c_uint32),
                 ("pages_total", ctypes.c_uint32), ("agg_kernel_ms", ctypes.c_double),
-                ("agg_kernel_launches", ctypes.c_uint64), ("agg_kernel_rows", ctypes.c_uint64)]
+                ("agg_kernel_launches", ctypes.c_uint64), ("agg_kernel_rows", ctypes.c_uint64),
+                ("jit_compiles", ctypes.c_uint64), ("jit_failures", ctypes.c_uint64),
+                ("jit_launches", ctypes.c_uint64), ("jit_compile_ms", ctypes.c_double)]
 
 
 class tp_server_stats(ctypes.Structure):

@@ -1,0 +1,74 @@
+"""The run-time compiled kernel source builds under NVRTC for sm_103a, for
+shapes covering every branch of the shape struct (no GPU needed: NVRTC
+compiles to a cubin on the host)."""
+import ctypes
+import os
+
+import pytest
+
+CSRC = os.path.join(os.path.dirname(__file__), "..", "paper_2508_05029_gb300", "csrc")
+HEADERS = ["kernels.cuh", "device.cuh", "pipeline.cuh", "jit_dense.cuh"]
+
+
+def _nvrtc():
+    for name in ("libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("NVRTC not available")
+
+
+def _shape(filter=1, ftype=0, join=1, ktype=0, part=0, groups=((0, 2, 2), (0, 2, 1), (1, 0, 5)),
+           sums=((0, 1, 0, 1, 0), (1, 1, 1, 2, 1), (0, 1, 0, 1, 0)), fast=True):
+    """groups: (side, type, bits); sums: (kind, atype, btype, mode, narrow)."""
+    def arr(name, vals, n):
+        vals = list(vals) + [0] * (n - len(vals))
+        return f"{name}[{n}] = {{{', '.join(map(str, vals))}}}"
+    g = list(zip(*groups)) if groups else ((), (), ())
+    s = list(zip(*sums)) if sums else ((), (), (), (), ())
+    return ("struct JS {\n"
+            f"  static constexpr int filter = {filter}, ftype = {ftype}, join = {join}, ktype = {ktype}, part = {part};\n"
+            f"  static constexpr int ng = {len(groups)};\n"
+            f"  static constexpr int {arr('gside', g[0], 4)}, {arr('gtype', g[1], 4)}, {arr('gbits', g[2], 4)};\n"
+            f"  static constexpr int ns = {len(sums)};\n"
+            f"  static constexpr int {arr('skind', s[0], 8)}, {arr('atype', s[1], 8)}, {arr('btype', s[2], 8)}, "
+            f"{arr('mode', s[3], 8)}, {arr('narrow', s[4], 8)};\n"
+            f"  static constexpr bool fast = {'true' if fast else 'false'};\n}};\n")
+
+
+SHAPES = {
+    "star-lowcard-direct": _shape(),
+    "exact-128": _shape(fast=False, sums=((0, 1, 0, 0, 0), (1, 1, 1, 0, 0))),
+    "hash32-partitioned": _shape(join=2, part=1),
+    "hash64-i64-key": _shape(join=3, ktype=1),
+    "no-filter-no-join": _shape(filter=0, join=0, groups=((0, 0, 4), (0, 1, 3)), sums=((0, 0, 0, 1, 0),)),
+    "i64-filter-u8-wide-field": _shape(ftype=1, groups=((0, 2, 9), (1, 0, 3)), sums=((1, 0, 2, 2, 0),)),
+    "count-only": _shape(sums=()),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SHAPES))
+def test_nvrtc_compiles_shape(name):
+    lib = _nvrtc()
+    texts = [open(os.path.join(CSRC, h)).read().encode() for h in HEADERS]
+    names = [h.encode() for h in HEADERS]
+    src = (SHAPES[name] + '#include "jit_dense.cuh"\n').encode()
+    prog = ctypes.c_void_p()
+    n = len(HEADERS)
+    arr_t = ctypes.c_char_p * n
+    rc = lib.nvrtcCreateProgram(ctypes.byref(prog), src, b"tp_jit.cu", n, arr_t(*texts), arr_t(*names))
+    assert rc == 0
+    opts = [b"--gpu-architecture=sm_103a", b"-std=c++17", b"--device-int128",
+            b"-DTP_ST_CONSUMERS=16", b"-DTP_ST_RPL=2", b"-DTP_ST_CTAS=2"]
+    rc = lib.nvrtcCompileProgram(prog, len(opts), (ctypes.c_char_p * len(opts))(*opts))
+    size = ctypes.c_size_t()
+    lib.nvrtcGetProgramLogSize(prog, ctypes.byref(size))
+    log = ctypes.create_string_buffer(size.value)
+    lib.nvrtcGetProgramLog(prog, log)
+    cubin = ctypes.c_size_t()
+    if rc == 0:
+        lib.nvrtcGetCUBINSize(prog, ctypes.byref(cubin))
+    lib.nvrtcDestroyProgram(ctypes.byref(prog))
+    assert rc == 0, log.value.decode(errors="replace")[:2000]
+    assert cubin.value > 0

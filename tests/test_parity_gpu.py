@@ -206,11 +206,13 @@ def test_budget_refusal_and_release(eng):
 
 
 @pytest.mark.parametrize("flags", [0, T.TP_FLAG_EXACT_ONLY, T.TP_FLAG_NO_STAGED, T.TP_FLAG_NO_DIRECT_JOIN,
-                                   T.TP_FLAG_NO_STAGED | T.TP_FLAG_NO_DIRECT_JOIN])
+                                   T.TP_FLAG_NO_STAGED | T.TP_FLAG_NO_DIRECT_JOIN, T.TP_FLAG_NO_JIT,
+                                   T.TP_FLAG_NO_JIT | T.TP_FLAG_EXACT_ONLY, T.TP_FLAG_NO_JIT | T.TP_FLAG_NO_DIRECT_JOIN])
 def test_every_kernel_path(flags):
     """Staged 64-bit (bounds prove no overflow), staged exact 128-bit, the
-    plain-load kernel, and hashed instead of direct-mapped join tables all
-    give the oracle's result."""
+    plain-load kernel, hashed instead of direct-mapped join tables, and the
+    run-time compiled and ahead-of-time staged kernels all give the oracle's
+    result."""
     e = T.Engine(page_bytes=4 << 20, n_pages=256, batch_rows=700_000, flags=flags)
     try:
         wl = W.config2("a", n_fact=2_000_011, n_dim=200_000)
@@ -228,5 +230,51 @@ def test_every_kernel_path(flags):
         qb = dict(filter=dict(col="d", lo=1, hi=8), join=None, group=[("fact", "g", 2)],
                   aggs=[("sum_mul_sub", "a", (1 << 62), "b"), ("sum", "a"), ("avg", "b")])
         check(e, big, None, qb)
+    finally:
+        e.close()
+
+
+JIT_QUERIES = {
+    # int64 filter column, a uint8 field wider than 8 bits, a product in the
+    # 64-bit carry mode
+    "i64-filter-wide-u8": dict(filter=dict(col="price", lo=200_000, hi=9_000_000),
+                               join=dict(fact_col="fk", dim_col="pk"),
+                               group=[("fact", "flag", 8), ("fact", "status", 1)],
+                               aggs=[("sum_mul_sub", "price", 100, "disc"), ("count",)]),
+    "no-filter-no-join": dict(filter=None, join=None, group=[("fact", "status", 1), ("fact", "flag", 2)],
+                              aggs=[("sum", "qty"), ("avg", "disc")]),
+    "count-only": dict(filter=dict(col="date", lo=0, hi=1800), join=dict(fact_col="fk", dim_col="pk"),
+                       group=[("dim", "attr", 5)], aggs=[("count",)]),
+}
+
+
+@pytest.mark.parametrize("name", sorted(JIT_QUERIES))
+@pytest.mark.parametrize("flags", [0, T.TP_FLAG_NO_DIRECT_JOIN])
+def test_jit_shapes_match_oracle(name, flags):
+    """Plan shapes compiled at run time give the oracle's result, and the
+    run-time compiled kernel is the one that ran."""
+    wl = W.config2("a", n_fact=1_500_007, n_dim=100_000)
+    e = T.Engine(page_bytes=4 << 20, n_pages=256, flags=flags)
+    try:
+        s0 = e.stats()
+        check(e, wl.fact, wl.dim, JIT_QUERIES[name])
+        s1 = e.stats()
+        assert s1["jit_failures"] == 0
+        assert s1["jit_launches"] > s0["jit_launches"]
+    finally:
+        e.close()
+
+
+def test_jit_fact_field_range_error():
+    """A fact-side group field outside its bit width is reported by the
+    run-time compiled kernel too."""
+    wl = W.config2("a", n_fact=300_007, n_dim=100_000)
+    e = T.Engine(page_bytes=4 << 20, n_pages=64)
+    try:
+        q = dict(filter=None, join=None, group=[("fact", "qty", 3)], aggs=[("count",)])
+        with pytest.raises(T.TPError) as err:
+            run_gpu(e, wl.fact, wl.dim, q)
+        assert err.value.status == "range"
+        assert e.stats()["jit_launches"] > 0
     finally:
         e.close()
