@@ -20,6 +20,7 @@ using namespace tp;
 
 namespace {
 
+
 uint64_t pow2_at_least(uint64_t x) {
     uint64_t p = 1;
     while (p < x) p <<= 1;
@@ -993,22 +994,31 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         auto shared_core = [&](const tpk::QueryDev& q, uint64_t rows) -> tp_status {
             tpk::StageLayout L;
             bool can = want_staged && tpk::staged_layout_shared(q, p->key_bits, mode != 1 && fast, bounds, rows,
-                                                                e->num_sms, &L);
+                                                                e->num_sms, tpk::AOT_GEOM, tpk::ST_MAX_STAGES, &L);
             if (mode < 0 && !can && fast) {  // no 32-bit table fits: exact staged table instead
                 fast = false;
-                can = want_staged && tpk::staged_layout_shared(q, p->key_bits, false, bounds, rows, e->num_sms, &L);
+                can = want_staged && tpk::staged_layout_shared(q, p->key_bits, false, bounds, rows, e->num_sms,
+                                                               tpk::AOT_GEOM, tpk::ST_MAX_STAGES, &L);
             }
             if (mode < 0) mode = can ? (fast ? 2 : 1) : 0;
             if (mode == 2 && !can) return fail(TP_E_INTERNAL, "staged layout changed between batches");
             mark_launch(e);
             if (mode > 0 && can) {
-                const uint64_t whole = rows / tpk::ST_TILE * tpk::ST_TILE;
                 const void* jk = nullptr;
-                if (want_jit && whole) {
-                    std::string why;
-                    jk = jit_kernel(e, dense_shape(q, L, mode == 2, narrow), "tpj_dense", &why);
-                    if (jk) e->jit_launches++;
+                if (want_jit) {
+                    tpk::StageLayout LJ;
+                    if (tpk::staged_layout_shared(q, p->key_bits, mode == 2, bounds, rows, e->num_sms,
+                                                  tpk::JIT_DENSE_GEOM, tpk::JIT_DENSE_STAGES, &LJ) &&
+                        LJ.n_stages == tpk::JIT_DENSE_STAGES && rows >= (uint64_t)LJ.tile) {
+                        std::string why;
+                        jk = jit_kernel(e, dense_shape(q, LJ, mode == 2, narrow), "tpj_dense", &why);
+                        if (jk) {
+                            L = LJ;   // the ahead-of-time kernel keeps its own layout
+                            e->jit_launches++;
+                        }
+                    }
                 }
+                const uint64_t whole = rows / (uint64_t)L.tile * (uint64_t)L.tile;
                 tp_status r = cuda_check(timer.run(st, whole, [&] {
                     if (jk)
                         return tpk::launch_agg_shared_staged_jit(jk, q, L, rows, (uint64_t*)gacc, p->key_bits,

@@ -107,9 +107,10 @@ Entry build_entry(const std::string& prelude, const char* entry, int device) {
     char arch[64], d_cons[64], d_rpl[64], d_ctas[64];
     // the architecture-specific target (sm_XXXa): the kernels use sm_90+ PTX
     snprintf(arch, sizeof(arch), "--gpu-architecture=sm_%d%da", major, minor);
-    snprintf(d_cons, sizeof(d_cons), "-DTP_ST_CONSUMERS=%d", tpk::ST_CONSUMERS);
-    snprintf(d_rpl, sizeof(d_rpl), "-DTP_ST_RPL=%d", tpk::ST_RPL);
-    snprintf(d_ctas, sizeof(d_ctas), "-DTP_ST_CTAS=%d", tpk::ST_CTAS);
+    // the kernel's own geometry (the host sized its layout with the same)
+    snprintf(d_cons, sizeof(d_cons), "-DTP_ST_CONSUMERS=%d", tpk::JIT_DENSE_GEOM.consumers);
+    snprintf(d_rpl, sizeof(d_rpl), "-DTP_ST_RPL=%d", tpk::JIT_DENSE_GEOM.rpl);
+    snprintf(d_ctas, sizeof(d_ctas), "-DTP_ST_CTAS=%d", tpk::JIT_DENSE_GEOM.ctas);
     const char* opts[] = {arch, "-std=c++17", "--device-int128", d_cons, d_rpl, d_ctas};
     r = g_nvrtc.compile(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
     if (r != NVRTC_SUCCESS) {

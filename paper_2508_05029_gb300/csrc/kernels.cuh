@@ -160,6 +160,23 @@ constexpr int ST_TILE = ST_CONSUMERS * ST_SUB;     // rows per stage
 constexpr int ST_THREADS = 32 * (1 + ST_CONSUMERS);
 constexpr int ST_MAX_COLS = 22;
 constexpr int ST_MAX_STAGES = 8;
+
+// Geometry of a staged kernel: consumer warps per CTA, rows per lane per
+// stage, resident CTAs per SM its shared memory is split for.
+struct StageGeom {
+    int32_t consumers;
+    int32_t rpl;
+    int32_t ctas;
+};
+// The ahead-of-time staged kernels.
+constexpr StageGeom AOT_GEOM{ST_CONSUMERS, ST_RPL, ST_CTAS};
+// The run-time compiled dense kernel: one CTA of 24 consumer warps per SM
+// and a ring of exactly JIT_DENSE_STAGES stages.  Measured on the star
+// query: the shared memory the ring leaves becomes L1 cache, which holds the
+// hot part of the join table (more stages were slower, fewer starved the
+// copies).
+constexpr StageGeom JIT_DENSE_GEOM{24, 2, 1};
+constexpr int JIT_DENSE_STAGES = 3;
 // column slots of a QueryDev: filter, fk, 4 group columns, 8 + 8 sum columns
 enum : int { SL_FILTER = 0, SL_FK = 1, SL_GROUP = 2, SL_SA = 6, SL_SB = 14, SL_COUNT = 22 };
 
@@ -173,6 +190,9 @@ struct StageLayout {
     uint32_t stage_bytes;              // bytes between consecutive stages
     uint32_t tile_bytes;               // bytes one full tile brings in (expect_tx)
     int32_t n_stages;
+    int32_t tile;                      // rows per stage (consumer warps * 32 * rows per lane)
+    int32_t threads;                   // threads per CTA (a producer warp + the consumer warps)
+    int32_t ctas;                      // resident CTAs per SM the shared memory was split for
     uint32_t table_bytes;              // shared-memory aggregation table in front of the stages
     uint32_t smem_bytes;               // total dynamic shared memory
     uint64_t wait_ns;                  // limit of every mbarrier wait
@@ -280,8 +300,11 @@ cudaError_t launch_final_dense(const uint64_t* gacc, uint32_t key_bits, int n_su
 // there: both keep the same low words, and the high words are ignored).
 // With fast, bounds[s] must give every sum's term range; the layout fails
 // when a 32-bit table cannot hold `rows` rows' worth of sums.
+// geom: the kernel's geometry (the ahead-of-time kernel's is AOT_GEOM);
+// max_stages caps the ring, leaving the shared memory it does not take to
+// the L1 cache.
 bool staged_layout_shared(const QueryDev& q, uint32_t key_bits, bool fast, const TermBounds* bounds,
-                          uint64_t rows, int num_sms, StageLayout* L);
+                          uint64_t rows, int num_sms, const StageGeom& geom, int max_stages, StageLayout* L);
 cudaError_t launch_agg_shared_staged(const QueryDev& q, const StageLayout& L, uint64_t n, uint64_t* gacc,
                                      uint32_t key_bits, bool fast, int num_sms, cudaStream_t st);
 // The same launch of a run-time compiled, plan-specialised kernel with the

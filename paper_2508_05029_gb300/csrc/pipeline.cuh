@@ -272,72 +272,90 @@ __device__ __forceinline__ void load_rows(const ColSrc& c, uint32_t r0, uint32_t
     }
 }
 
-// Drives the bulk-copy pipeline over the whole tiles of [0, n) that this CTA
-// owns (tiles blockIdx.x, blockIdx.x + gridDim.x, ...).  `area` is dynamic
-// shared memory for 2 * ST_MAX_STAGES mbarriers followed by L.n_stages
-// stages.  Warp 0 lane 0 produces; warps 1..ST_CONSUMERS call
-// consume(stage, row0, r0) for each tile, r0 being the lane's first
-// tile-local row.  Returns after this thread's part of the pipeline is done;
-// the caller synchronises the CTA before reading what consumers produced.
-template <class Consume>
-__device__ __forceinline__ void run_pipeline(const QueryDev& q, const StageLayout& L, uint64_t n,
-                                             unsigned char* area, Consume&& consume) {
-    uint64_t* full = (uint64_t*)area;
-    uint64_t* empty = full + ST_MAX_STAGES;
-    unsigned char* stages = area + 2 * ST_MAX_STAGES * sizeof(uint64_t);
+// The bulk-copy pipeline over the whole tiles of [0, n) that a CTA owns
+// (tiles blockIdx.x, blockIdx.x + gridDim.x, ...).  Its ring lives in
+// dynamic shared memory: 2 * ST_MAX_STAGES mbarriers ("full" then "empty"
+// per stage) followed by L.n_stages stages.
+struct Ring {
+    uint64_t* full;
+    uint64_t* empty;
+    unsigned char* stages;
+};
+
+// Initialises the ring's barriers; every thread of the CTA calls it.
+__device__ __forceinline__ Ring pipeline_setup(const StageLayout& L, unsigned char* area) {
+    Ring r{(uint64_t*)area, (uint64_t*)area + ST_MAX_STAGES, area + 2 * ST_MAX_STAGES * sizeof(uint64_t)};
     if (threadIdx.x == 0) {
         for (int s = 0; s < L.n_stages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], ST_CONSUMERS);
+            mbar_init(&r.full[s], 1);
+            mbar_init(&r.empty[s], ST_CONSUMERS);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    return r;
+}
+
+// The producer (one lane): for every tile of this CTA, waits until the
+// consumers released its stage, then issues the tile's bulk copies.
+__device__ __forceinline__ void pipeline_produce(const QueryDev& q, const StageLayout& L, uint64_t ntiles,
+                                                 const Ring& R) {
+    const uint64_t pol = l2_evict_first();
+    uint32_t filled = 0, fill_parity = 0;   // per stage: ever filled; parity of its last fill
+    bool ok = true;
+    int s = 0;        // stage of this tile
+    uint32_t u = 0;   // how many times the ring has wrapped: stage s's use count
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (u > 0 && !mbar_wait(&R.empty[s], (u - 1) & 1u, L.wait_ns)) {
+            atomicOr(q.err, ERR_TIMEOUT);
+            ok = false;
+            break;
+        }
+        mbar_arrive_expect_tx(&R.full[s], L.tile_bytes);
+        unsigned char* dst = R.stages + (uint64_t)s * L.stage_bytes;
+        for (int c = 0; c < L.n_cols; ++c) {
+            const uint32_t bytes = (uint32_t)ST_TILE * (uint32_t)L.esize[c];
+            bulk_load(dst + L.off[c], (const unsigned char*)L.src[c] + t * bytes, bytes, &R.full[s], pol);
+        }
+        filled |= 1u << s;
+        fill_parity = (fill_parity & ~(1u << s)) | ((u & 1u) << s);
+        if (++s == L.n_stages) {
+            s = 0;
+            ++u;
+        }
+    }
+    if (!ok) {  // consumers gave up: let the copies already issued land before exit
+        for (int s = 0; s < L.n_stages; ++s)
+            if (filled >> s & 1u) mbar_wait(&R.full[s], fill_parity >> s & 1u, L.wait_ns);
+    }
+}
+
+// Runs the pipeline over the first floor(n / ST_TILE) tiles: warp 0 lane 0
+// produces, warps 1..ST_CONSUMERS call consume(stage, tile's first row, r0)
+// for each tile, r0 being the lane's first tile-local row.  Returns after
+// this thread's part of the pipeline is done; the caller synchronises the
+// CTA before reading what consumers produced.
+template <class Consume>
+__device__ __forceinline__ void run_pipeline(const QueryDev& q, const StageLayout& L, uint64_t n,
+                                             unsigned char* area, Consume&& consume) {
+    const Ring R = pipeline_setup(L, area);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t ntiles = n / ST_TILE;
     if (warp == 0) {
-        if (lane != 0) return;
-        const uint64_t pol = l2_evict_first();
-        uint32_t filled = 0, fill_parity = 0;   // per stage: ever filled; parity of its last fill
-        bool ok = true;
-        int s = 0;        // stage of this tile
-        uint32_t u = 0;   // how many times the ring has wrapped: stage s's use count
-        for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1u, L.wait_ns)) {
-                atomicOr(q.err, ERR_TIMEOUT);
-                ok = false;
-                break;
-            }
-            mbar_arrive_expect_tx(&full[s], L.tile_bytes);
-            unsigned char* dst = stages + (uint64_t)s * L.stage_bytes;
-            for (int c = 0; c < L.n_cols; ++c) {
-                const uint32_t bytes = (uint32_t)ST_TILE * (uint32_t)L.esize[c];
-                bulk_load(dst + L.off[c], (const unsigned char*)L.src[c] + t * bytes, bytes, &full[s], pol);
-            }
-            filled |= 1u << s;
-            fill_parity = (fill_parity & ~(1u << s)) | ((u & 1u) << s);
-            if (++s == L.n_stages) {
-                s = 0;
-                ++u;
-            }
-        }
-        if (!ok) {  // consumers gave up: let the copies already issued land before exit
-            for (int s = 0; s < L.n_stages; ++s)
-                if (filled >> s & 1u) mbar_wait(&full[s], fill_parity >> s & 1u, L.wait_ns);
-        }
+        if (lane == 0) pipeline_produce(q, L, ntiles, R);
         return;
     }
     const uint32_t r0 = (uint32_t)(warp - 1) * ST_SUB + (uint32_t)lane;
     int s = 0;
     uint32_t phase = 0;   // parity of stage s's current use
     for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        if (!mbar_wait(&full[s], phase, L.wait_ns)) {
+        if (!mbar_wait(&R.full[s], phase, L.wait_ns)) {
             atomicOr(q.err, ERR_TIMEOUT);
             return;
         }
-        consume(stages + (uint64_t)s * L.stage_bytes, t * ST_TILE, r0);
+        consume(R.stages + (uint64_t)s * L.stage_bytes, t * ST_TILE, r0);
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
+        if (lane == 0) mbar_arrive(&R.empty[s]);
         if (++s == L.n_stages) {
             s = 0;
             phase ^= 1u;

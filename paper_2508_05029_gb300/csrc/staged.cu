@@ -208,7 +208,7 @@ static uint32_t align128(uint64_t x) { return (uint32_t)((x + 127) & ~127ull); }
 static int esize_host(int type) { return type == T_I64 ? 8 : (type == T_I32 ? 4 : 1); }
 
 bool staged_layout_shared(const QueryDev& q, uint32_t key_bits, bool fast, const TermBounds* bounds,
-                          uint64_t rows, int num_sms, StageLayout* L) {
+                          uint64_t rows, int num_sms, const StageGeom& geom, int max_stages, StageLayout* L) {
     memset(L, 0, sizeof(*L));
     for (int i = 0; i < SL_COUNT; ++i) L->col_of_slot[i] = -1;
     auto add = [&](int slot, const DevCol& c) -> bool {
@@ -235,19 +235,23 @@ bool staged_layout_shared(const QueryDev& q, uint32_t key_bits, bool fast, const
         if (q.skind[s] == S_MUL_SUB) ok = ok && add(SL_SB + s, q.sb[s]);
     }
     if (!ok) return false;
+    const uint32_t tile = (uint32_t)geom.consumers * 32u * (uint32_t)geom.rpl;
+    L->tile = (int32_t)tile;
+    L->threads = 32 * (1 + geom.consumers);
+    L->ctas = geom.ctas;
     uint32_t off = 0;
     for (int k = 0; k < L->n_cols; ++k) {
         L->off[k] = off;
-        L->tile_bytes += (uint32_t)ST_TILE * L->esize[k];
-        off = align128(off + (uint64_t)ST_TILE * L->esize[k]);
+        L->tile_bytes += tile * L->esize[k];
+        off = align128(off + (uint64_t)tile * L->esize[k]);
     }
     L->stage_bytes = off ? off : 128;
     const uint64_t G = 1ull << key_bits;
     if (fast) {
         // rows one CTA can see in this launch bound every 32-bit word
-        const uint64_t tiles = rows / ST_TILE;
-        const uint64_t ctas = std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)num_sms * ST_CTAS));
-        const uint64_t r_cta = (tiles + ctas - 1) / ctas * (uint64_t)ST_TILE;
+        const uint64_t tiles = rows / tile;
+        const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)num_sms * geom.ctas));
+        const uint64_t r_cta = (tiles + grid - 1) / grid * (uint64_t)tile;
         if (r_cta >= (1ull << 32)) return false;
         uint32_t block = 1;   // block 0: counts
         for (int s = 0; s < q.n_sum; ++s) {
@@ -273,11 +277,12 @@ bool staged_layout_shared(const QueryDev& q, uint32_t key_bits, bool fast, const
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
         return false;
-    // each of the ST_CTAS resident CTAs gets its share (1 KB per CTA stays reserved by the runtime)
-    const uint64_t budget = std::min<uint64_t>((uint64_t)optin, (uint64_t)per_sm / ST_CTAS - 1024);
+    // each of the resident CTAs gets its share (1 KB per CTA stays reserved by the runtime)
+    const uint64_t budget = std::min<uint64_t>((uint64_t)optin, (uint64_t)per_sm / geom.ctas - 1024);
     const uint64_t fixed = L->table_bytes + 2 * ST_MAX_STAGES * sizeof(uint64_t);
     if (budget <= fixed) return false;
     int stages = (int)((budget - fixed) / L->stage_bytes);
+    if (stages > max_stages) stages = max_stages;
     if (stages > ST_MAX_STAGES) stages = ST_MAX_STAGES;
     if (stages < 2) return false;
     L->n_stages = stages;
@@ -318,9 +323,9 @@ cudaError_t launch_agg_shared_staged(const QueryDev& q, const StageLayout& L, ui
 
 cudaError_t launch_agg_shared_staged_jit(const void* kernel, const QueryDev& q, const StageLayout& L, uint64_t n,
                                          uint64_t* gacc, uint32_t key_bits, int num_sms, cudaStream_t st) {
-    if (n < (uint64_t)ST_TILE) return cudaSuccess;
-    const uint64_t tiles = n / ST_TILE;
-    const uint64_t slots = (uint64_t)num_sms * ST_CTAS;
+    if (n < (uint64_t)L.tile) return cudaSuccess;
+    const uint64_t tiles = n / (uint64_t)L.tile;
+    const uint64_t slots = (uint64_t)num_sms * L.ctas;
     const int grid = (int)(tiles < slots ? tiles : slots);
     uint32_t G = 1u << key_bits;
     cudaError_t e = ensure_smem_limit(kernel, (int)L.smem_bytes);
@@ -328,7 +333,7 @@ cudaError_t launch_agg_shared_staged_jit(const void* kernel, const QueryDev& q, 
     QueryDev qa = q;
     StageLayout la = L;
     void* args[] = {&qa, &la, &n, &gacc, &G};
-    return cudaLaunchKernel(kernel, dim3(grid), dim3(ST_THREADS), args, L.smem_bytes, st);
+    return cudaLaunchKernel(kernel, dim3(grid), dim3(L.threads), args, L.smem_bytes, st);
 }
 
 }  // namespace tpk

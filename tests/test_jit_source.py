@@ -60,7 +60,7 @@ def test_nvrtc_compiles_shape(name):
     rc = lib.nvrtcCreateProgram(ctypes.byref(prog), src, b"tp_jit.cu", n, arr_t(*texts), arr_t(*names))
     assert rc == 0
     opts = [b"--gpu-architecture=sm_103a", b"-std=c++17", b"--device-int128",
-            b"-DTP_ST_CONSUMERS=16", b"-DTP_ST_RPL=2", b"-DTP_ST_CTAS=2"]
+            b"-DTP_ST_CONSUMERS=24", b"-DTP_ST_RPL=2", b"-DTP_ST_CTAS=1"]
     rc = lib.nvrtcCompileProgram(prog, len(opts), (ctypes.c_char_p * len(opts))(*opts))
     size = ctypes.c_size_t()
     lib.nvrtcGetProgramLogSize(prog, ctypes.byref(size))
