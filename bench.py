@@ -49,7 +49,7 @@ BYTES_PER_DIM_ROW = 4 + 4                            # pk, attr
 # run-time compiled (plan-specialised) staged kernel, or the ahead-of-time one
 PROFILE_SUMMARY = {"tpj_dense": os.path.join(ROOT, "profiles", "tpj_dense_star12M.md"),
                    "k_agg_shared_staged": os.path.join(ROOT, "profiles", "k_agg_shared_staged_star12M.md")}
-KERNEL_SOURCES = {"tpj_dense": ("kernels.cuh", "device.cuh", "pipeline.cuh", "jit_dense.cuh", "jit.cu"),
+KERNEL_SOURCES = {"tpj_dense": ("kernels.cuh", "device.cuh", "pipeline.cuh", "jit_dense.cuh", "jit.cu", "staged.cu"),
                   "k_agg_shared_staged": ("kernels.cu", "kernels.cuh", "device.cuh", "pipeline.cuh", "staged.cu")}
 
 

@@ -1018,7 +1018,8 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
                         }
                     }
                 }
-                const uint64_t whole = rows / (uint64_t)L.tile * (uint64_t)L.tile;
+                // the run-time compiled kernel takes the ragged tail itself
+                const uint64_t whole = jk ? rows : rows / (uint64_t)L.tile * (uint64_t)L.tile;
                 tp_status r = cuda_check(timer.run(st, whole, [&] {
                     if (jk)
                         return tpk::launch_agg_shared_staged_jit(jk, q, L, rows, (uint64_t*)gacc, p->key_bits,

@@ -9,7 +9,8 @@
 // is folded into the global dense table at the end.  What differs: the plan's
 // shape is a compile-time constant here, so a row costs only the loads,
 // compares and atomics its query needs -- no type switches, no loops over
-// runtime field counts, 32-bit arithmetic where only a low word is kept.
+// runtime field counts, 32-bit arithmetic where only a low word is kept --
+// and the rows after the last whole tile are evaluated in the same launch.
 //
 // The host prepends a generated struct JS describing the shape:
 //   filter, ftype            filter present; its column type (T_*)
@@ -154,8 +155,8 @@ __device__ __forceinline__ void sums(const QueryDev& q, const StageLayout& L, co
 // One consumer warp's rows of a full stage: filter -> probe -> group key ->
 // count and sums.
 __device__ __forceinline__ void consume(const QueryDev& q, const StageLayout& L, const Ctx& c,
-                                        const unsigned char* stage, uint32_t r0) {
-    uint32_t pm = (1u << ST_RPL) - 1u;
+                                        const unsigned char* stage, uint32_t r0, uint32_t valid) {
+    uint32_t pm = valid;
     if constexpr (JS::filter) {
         pm = 0;
 #pragma unroll
@@ -168,6 +169,7 @@ __device__ __forceinline__ void consume(const QueryDev& q, const StageLayout& L,
                 pm |= (uint32_t)(v >= c.flo32 && v <= c.fhi32) << j;
             }
         }
+        pm &= valid;
         if (!pm) return;
     }
     uint32_t pay[ST_RPL];
@@ -280,10 +282,32 @@ extern "C" __global__ void __launch_bounds__(tpk::ST_THREADS, tpk::ST_CTAS)
     if constexpr (JS::filter) c.off_f = L.off[L.col_of_slot[SL_FILTER]];
     if constexpr (JS::join != J_NONE) c.off_k = L.off[L.col_of_slot[SL_FK]];
     stage_offsets<0, 0>(L, c);
+    constexpr uint32_t all = (1u << ST_RPL) - 1u;
     run_pipeline(q, L, n, smem + L.table_bytes, [&](const unsigned char* stage, uint64_t, uint32_t r0) {
-        consume(q, L, c, stage, r0);
+        consume(q, L, c, stage, r0, all);
     });
     __syncthreads();
+    // rows after the last whole tile: one CTA copies them into the (now
+    // idle) first stage with plain loads and evaluates them with a row mask
+    const uint64_t ntiles = n / ST_TILE, whole = ntiles * ST_TILE;
+    if (whole < n && blockIdx.x == ntiles % gridDim.x) {
+        const uint32_t rows = (uint32_t)(n - whole);
+        unsigned char* stage = smem + L.table_bytes + 2 * ST_MAX_STAGES * sizeof(uint64_t);
+        for (int k = 0; k < L.n_cols; ++k) {
+            const uint32_t es = (uint32_t)L.esize[k];
+            const unsigned char* src = (const unsigned char*)L.src[k] + whole * es;
+            for (uint32_t i = threadIdx.x; i < rows * es; i += blockDim.x) stage[L.off[k] + i] = src[i];
+        }
+        __syncthreads();
+        if (threadIdx.x >= 32) {
+            const uint32_t r0 = (threadIdx.x / 32 - 1) * (uint32_t)ST_SUB + (threadIdx.x & 31u);
+            uint32_t valid = 0;
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) valid |= (uint32_t)(r0 + 32 * j < rows) << j;
+            if (valid) consume(q, L, c, stage, r0, valid);
+        }
+        __syncthreads();
+    }
     // fold this CTA's table into the global dense table (count[G], lo/hi[s][G])
     for (uint32_t gi = threadIdx.x; gi < G; gi += blockDim.x) {
         uint64_t cnt;

@@ -308,7 +308,8 @@ bool staged_layout_shared(const QueryDev& q, uint32_t key_bits, bool fast, const
 cudaError_t launch_agg_shared_staged(const QueryDev& q, const StageLayout& L, uint64_t n, uint64_t* gacc,
                                      uint32_t key_bits, bool fast, int num_sms, cudaStream_t st);
 // The same launch of a run-time compiled, plan-specialised kernel with the
-// signature of tpj_dense (same layout, grid and block).
+// signature of tpj_dense (grid and block from the layout); it covers all n
+// rows, the ragged tail included (n must hold at least one whole tile).
 cudaError_t launch_agg_shared_staged_jit(const void* kernel, const QueryDev& q, const StageLayout& L, uint64_t n,
                                          uint64_t* gacc, uint32_t key_bits, int num_sms, cudaStream_t st);
 
