@@ -68,6 +68,11 @@ def parse_args():
                     help="fact-size scale of the 256-query batched mix (1.0 = the full ~394M rows)")
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="arrival window per served rate")
     ap.add_argument("--no-patterns", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--no-outofcore", action="store_true", help="skip the out-of-core (paged, spilling) query")
+    ap.add_argument("--ooc-fact", type=int, default=600_000_000, help="out-of-core fact rows")
+    ap.add_argument("--ooc-dim", type=int, default=150_000_000, help="out-of-core build rows")
+    ap.add_argument("--ooc-budgets", default="16,2", help="device budgets (GiB) of the out-of-core runs")
+    ap.add_argument("--ooc-steps", type=int, default=2)
     return ap.parse_args()
 
 
@@ -309,6 +314,77 @@ def batched_measure(T, W, torch, dev, stream, scale, reps=3):
             "how": "one persistent graph-captured launch vs 256 tp_execute calls on one stream"}
 
 
+def host_ram_bytes() -> int:
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES")
+    except (ValueError, OSError):
+        return 0
+
+
+def outofcore_measure(T, W, torch, dev, n_fact, n_dim, budgets_gb, steps, link):
+    """The out-of-core star query: fact and build tables in 64 MiB pinned pages,
+    streamed through the device; the join runs radix-partitioned 64 ways and
+    spills the partitions the budget cannot hold.  Rows are scaled down (and
+    the line says so) when host memory cannot hold the pages."""
+    page = 64 << 20
+    fact_b, dim_b = 38, 12                       # bytes per fact row (native widths) and build row
+    ram = host_ram_bytes()
+    scale = 1.0
+    # the tables (each batch rounded up to whole pages) plus room to spill all
+    # of them, plus one partly filled page per spilled partition and table
+    need = lambda s: 2.5 * (n_fact * fact_b + n_dim * dim_b) * s + 128 * page
+    while ram and need(scale) > 0.6 * ram and scale > 0.05:
+        scale /= 2
+    nf, nd = int(n_fact * scale), int(n_dim * scale)
+    n_pages = int(need(scale) // page) + 1
+    t0 = time.perf_counter()
+    eng = T.Engine(page_bytes=page, n_pages=n_pages, batch_rows=6_000_000, prefetch_depth=2,
+                   cuda_device=dev.index or 0)
+    chunk = 25_000_000
+    dt = eng.table_from_chunks(W.config3_dim(nd, row0=r, n=min(chunk, nd - r)) for r in range(0, nd, chunk))
+    passing = [0]   # fact rows the filter keeps: every fk has a partner, so the total count must match
+
+    def fact_chunks():
+        for r in range(0, nf, chunk):
+            c = W.config3_fact(r, min(chunk, nf - r), n_dim=nd)
+            passing[0] += int((c["date"] <= W.CUTOFF_98).sum())
+            yield c
+
+    ft = eng.table_from_chunks(fact_chunks())
+    setup_s = time.perf_counter() - t0
+    out = {"fact_rows": nf, "dim_rows": nd, "scale": scale, "pages": n_pages, "setup_s": round(setup_s, 1),
+           "host_ram_gb": round(ram / 2**30, 1), "link_peak_gbs": link}
+    alg = nf * fact_b + nd * dim_b
+    for b in budgets_gb:
+        eng.set_budget(int(b * 2**30))
+        p = eng.plan(ft, dt, W.q_lowcard(), join_partitions=64)
+        p.execute().free()
+        s0 = eng.stats()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        groups, total = 0, 0
+        for _ in range(steps):
+            with p.execute() as r:
+                groups = r.n_groups
+                total = int(r.counts().sum())
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t1) / steps
+        s1 = eng.stats()
+        h2d = (s1["h2d_bytes"] - s0["h2d_bytes"]) / steps
+        d2h = (s1["d2h_bytes"] - s0["d2h_bytes"]) / steps
+        out[f"budget_{b:g}GB"] = {
+            "ms_per_step": sec * 1e3, "fact_rows_per_s": nf / sec, "groups": groups,
+            "count_check": total == passing[0],
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "alg_gbs": alg / sec / 1e9, "link_frac_alg": alg / sec / 1e9 / link,
+            "link_frac_moved": (h2d + d2h) / sec / 1e9 / link}
+        p.destroy()
+    ft.destroy()
+    dt.destroy()
+    eng.close()
+    return out
+
+
 def served_measure(T, W, torch, dev, rates, seconds, scale):
     """Open-loop Poisson arrivals; latency = scheduled arrival -> result on host."""
     import threading
@@ -488,6 +564,12 @@ def main():
         ft2.destroy()
         dt2.destroy()
         eng2.close()
+
+    if not args.no_outofcore and rank == 0:
+        link_ooc = e2e["link_peak_gbs"] if e2e else link_peak_gbs(dev)
+        extra["star-600M-outofcore"] = outofcore_measure(
+            T, W, torch, dev, args.ooc_fact, args.ooc_dim, [float(x) for x in args.ooc_budgets.split(",")],
+            args.ooc_steps, link_ooc)
 
     patterns = None
     if not args.no_patterns:

@@ -255,10 +255,14 @@ typedef struct {
     /* Join partitions P (Section 3.3.2: spill what does not fit).  0 = auto:
      * a hashed join whose table would take more than half of the free budget
      * runs as a hybrid hash join with 64 partitions; 1 = never partition;
-     * 2..64 (a power of two) = always partition into P.  Partitions whose
-     * table fits a quarter of the free budget stay resident; the others'
-     * build and fact rows are spilled to pool pages and joined one partition
-     * at a time (TP_E_POOL_EMPTY when the pool cannot hold them). */
+     * 2..64 (a power of two) = always partition into P.  A partitioned join
+     * reserves the free budget that streaming buffers, the aggregation table
+     * and the result leave.  Every partition stays resident when one table
+     * of all build rows fits it; otherwise room for the largest partition's
+     * table is kept and partitions are made resident in order while the
+     * rest fits.  The other partitions' build and fact rows are spilled to
+     * pool pages and joined one partition at a time (TP_E_POOL_EMPTY when
+     * the pool cannot hold them). */
     int32_t join_partitions;
 } tp_plan_desc;
 
@@ -316,6 +320,14 @@ tp_status tp_batch_execute(tp_batch* b, tp_result** results);
 /* Device time of the last tp_batch_execute in milliseconds (CUDA events). */
 double tp_batch_last_ms(const tp_batch* b);
 void tp_batch_destroy(tp_batch* b);
+/* Fault injection for tests of the bounded device waits: from the next
+ * tp_batch_execute on, every dependency wait of the batch's persistent kernel
+ * gives up after wait_ns (instead of 2 s) and the finalisation of query
+ * `query` waits for one probe tile more than exists, so that wait runs out:
+ * tp_batch_execute returns TP_E_TIMEOUT with the device context intact.
+ * query = -1 restores the batch (2 s limit, true tile counts).  The paper
+ * has no counterpart (its tasks wait on the host). */
+tp_status tp_debug_batch_stall(tp_batch* b, int32_t query, uint64_t wait_ns);
 
 /*
  * Autotuner: for every query class present in plans[0..n), tries the join

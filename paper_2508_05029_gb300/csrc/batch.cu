@@ -130,8 +130,9 @@ __device__ void batch_probe(const BatchQuery& B, uint64_t r0, uint64_t r1, unsig
 __global__ void __launch_bounds__(BATCH_THREADS) k_batch(const BatchQuery* __restrict__ qs,
                                                         const BatchItem* __restrict__ items, uint32_t n_items,
                                                         uint32_t n_q, unsigned* ctr, uint32_t* err,
-                                                        uint64_t wait_ns) {
+                                                        const uint64_t* __restrict__ wait) {
     extern __shared__ __align__(16) unsigned char smem[];
+    const uint64_t wait_ns = *wait;   // device word, so a captured graph can be given another limit
     __shared__ uint32_t cur;
     __shared__ int flag;
     unsigned* build_done = ctr + 1;
@@ -177,7 +178,7 @@ int batch_grid(uint32_t smem_bytes, int num_sms) {
 }
 
 cudaError_t launch_batch(const BatchQuery* qs, const BatchItem* items, uint32_t n_items, uint32_t n_q,
-                         unsigned* ctr, uint32_t* err, uint64_t wait_ns, uint32_t smem_bytes, int grid,
+                         unsigned* ctr, uint32_t* err, const uint64_t* wait_ns, uint32_t smem_bytes, int grid,
                          cudaStream_t st) {
     k_batch<<<grid, BATCH_THREADS, smem_bytes, st>>>(qs, items, n_items, n_q, ctr, err, wait_ns);
     return cudaGetLastError();
@@ -266,11 +267,15 @@ struct tp_batch {
     uint64_t zero_bytes = 0;
     uint32_t smem = 0;
     int grid = 0;
+    uint64_t* d_wait = nullptr;          // limit of every dependency wait, ns (device word)
+    std::vector<uint32_t> probe_items;   // per query, as laid out (tp_debug_batch_stall restores it)
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = 0;
     std::vector<tpk::OutDev> outs;
 };
+
+static constexpr uint64_t BATCH_WAIT_NS = 2000000000ull;   // 2 s
 
 static void batch_free(tp_batch* b) {
     if (!b) return;
@@ -366,7 +371,7 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
     if (n_items >= (1ull << 32)) return fail(TP_E_INVALID, "tp_batch_create: too many tasks");
     const uint64_t qbytes = a256(sizeof(tpk::BatchQuery) * n);
     const uint64_t ibytes = a256(sizeof(tpk::BatchItem) * n_items);
-    const uint64_t total = ff + zero + qbytes + ibytes + outb;
+    const uint64_t total = ff + zero + qbytes + ibytes + outb + 256;   // + the wait-limit word
     tp_status s = reserve(e, total);
     if (s) return s;
     b->reserved = total;
@@ -390,6 +395,7 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
     b->d_q = (tpk::BatchQuery*)qp;
     b->d_items = (tpk::BatchItem*)(qp + qbytes);
     unsigned char* op = qp + qbytes + ibytes;
+    b->d_wait = (uint64_t*)(base + total - 256);
     // ---- descriptors and tasks on the host
     std::vector<tpk::BatchQuery> hq(n);
     std::vector<tpk::BatchItem> items;
@@ -477,6 +483,9 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
     }
     for (int i = 0; i < n; ++i) items.push_back(tpk::BatchItem{(uint32_t)i, tpk::BI_FINAL, 0, 0, 0});
     b->n_items = (uint32_t)items.size();
+    b->probe_items.resize(n);
+    for (int i = 0; i < n; ++i) b->probe_items[i] = hq[i].probe_items;
+    TP_TRY_CUDA(cudaMemcpyAsync(b->d_wait, &BATCH_WAIT_NS, 8, cudaMemcpyHostToDevice, e->compute));
     TP_TRY_CUDA(cudaMemcpyAsync(b->d_q, hq.data(), sizeof(tpk::BatchQuery) * n, cudaMemcpyHostToDevice, e->compute));
     TP_TRY_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(tpk::BatchItem) * items.size(),
                                 cudaMemcpyHostToDevice, e->compute));
@@ -489,7 +498,7 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
     cudaError_t ce = cudaMemsetAsync(b->ff_base, 0xFF, b->ff_bytes, e->compute);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(b->zero_base, 0, b->zero_bytes, e->compute);
     if (ce == cudaSuccess)
-        ce = tpk::launch_batch(b->d_q, b->d_items, b->n_items, (uint32_t)n, b->d_ctr, b->d_err, 2000000000ull, b->smem,
+        ce = tpk::launch_batch(b->d_q, b->d_items, b->n_items, (uint32_t)n, b->d_ctr, b->d_err, b->d_wait, b->smem,
                                b->grid, e->compute);
     cudaError_t ce2 = cudaStreamEndCapture(e->compute, &graph);
     if (ce != cudaSuccess || ce2 != cudaSuccess) {
@@ -583,6 +592,22 @@ tp_status tp_batch_execute(tp_batch* b, tp_result** results) {
 }
 
 double tp_batch_last_ms(const tp_batch* b) { return b ? b->last_ms : 0.0; }
+
+tp_status tp_debug_batch_stall(tp_batch* b, int32_t query, uint64_t wait_ns) {
+    clear_error();
+    if (!b || query >= (int32_t)b->plans.size() || (query >= 0 && wait_ns == 0))
+        return fail(TP_E_INVALID, "tp_debug_batch_stall: bad arguments");
+    std::lock_guard<std::mutex> lk(b->e->exec_mu);
+    TP_TRY_CUDA(cudaSetDevice(b->e->device));
+    const uint64_t w = query >= 0 ? wait_ns : BATCH_WAIT_NS;
+    TP_TRY_CUDA(cudaMemcpy(b->d_wait, &w, 8, cudaMemcpyHostToDevice));
+    for (int i = 0; i < (int)b->plans.size(); ++i) {
+        // the stalled query's finalisation waits for one probe tile more than exists
+        const uint32_t want = b->probe_items[i] + (i == query ? 1u : 0u);
+        TP_TRY_CUDA(cudaMemcpy(&b->d_q[i].probe_items, &want, 4, cudaMemcpyHostToDevice));
+    }
+    return TP_OK;
+}
 
 void tp_batch_destroy(tp_batch* b) { batch_free(b); }
 

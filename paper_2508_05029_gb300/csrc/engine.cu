@@ -126,6 +126,7 @@ tp_status tp_init(const tp_config* cfg, tp_engine** out) {
     uint64_t threshold = ~0ull;
     TP_TRY_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold));
     TP_TRY_CUDA(cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking));
+    TP_TRY_CUDA(cudaStreamCreateWithFlags(&e->spill, cudaStreamNonBlocking));
     if (cfg->compute_stream) {
         e->compute = (cudaStream_t)cfg->compute_stream;
     } else {
@@ -143,6 +144,7 @@ tp_status tp_init(const tp_config* cfg, tp_engine** out) {
             cudaGetLastError();
             cudaFreeHost(e->host_words);
             cudaStreamDestroy(e->copy);
+            cudaStreamDestroy(e->spill);
             if (e->own_compute) cudaStreamDestroy(e->compute);
             return fail(TP_E_NOMEM, "page pool of %u x %llu bytes could not be pinned: %s", pp.n_pages,
                         (unsigned long long)pp.page_bytes, cudaGetErrorString(err));
@@ -153,6 +155,7 @@ tp_status tp_init(const tp_config* cfg, tp_engine** out) {
     }
     e->lane0.compute = e->compute;
     e->lane0.copy = e->copy;
+    e->lane0.spill = e->spill;
     e->lane0.host_words = e->host_words;
     *out = e.release();
     return TP_OK;
@@ -163,9 +166,11 @@ void tp_shutdown(tp_engine* e) {
     cudaSetDevice(e->device);
     cudaStreamSynchronize(e->compute);
     cudaStreamSynchronize(e->copy);
+    cudaStreamSynchronize(e->spill);
     if (e->pool.base) cudaFreeHost(e->pool.base);
     if (e->host_words) cudaFreeHost(e->host_words);
     cudaStreamDestroy(e->copy);
+    cudaStreamDestroy(e->spill);
     if (e->own_compute) cudaStreamDestroy(e->compute);
     delete e;
 }

@@ -394,6 +394,10 @@ tp_status alloc_result(tp_engine* e, tp_plan* p, uint64_t cap, tp_result** out, 
 // and fact rows of the other partitions are spilled to pool pages, then
 // joined one partition at a time against the same accumulators.
 
+// Batches whose fact spill copies may still be running when the next batch
+// spills (each holds a staging buffer).
+constexpr size_t SPILL_BACKLOG = 2;
+
 struct PartJoin {
     bool on = false;
     int P = 0;
@@ -405,8 +409,14 @@ struct PartJoin {
     unsigned long long* counts = nullptr;  // device: P per-batch counters
     unsigned long long* cursor = nullptr;  // device: P cursors
     bool spill_fact = true;                // false on a retry: the fact spill already happened
-    uint64_t table_budget = 0;             // bytes one partition table may take
+    std::deque<cudaEvent_t> inflight;      // fact spill copies still running on the spill stream
+    uint64_t table_budget = 0;             // bytes the resident table and one phase-2 table may take
+    uint64_t resident_bytes = 0;           // bytes of the resident table
     ~PartJoin() {
+        for (cudaEvent_t ev : inflight) {
+            cudaEventSynchronize(ev);
+            cudaEventDestroy(ev);
+        }
         for (tp_table* t : build_spill) tp_table_destroy(t);
         for (tp_table* t : fact_spill) tp_table_destroy(t);
     }
@@ -429,9 +439,10 @@ tp_table* spill_table(tp_engine* e, const std::vector<int32_t>& types) {
 // column that is not kept) to a spill table as one batch.  The batch's
 // columns lie back to back where the previous append ended, in the table's
 // page chain (new pool pages as needed), so a partition wastes at most one
-// partial page.  Device -> host copies on the compute stream, synchronised.
+// partial page.  Device -> host copies on `st`, synchronised unless !sync
+// (the caller then synchronises st before the pages are read).
 tp_status append_device_rows(tp_engine* e, tp_table* t, const std::vector<const void*>& dev, uint64_t nrows,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool sync = true) {
     if (nrows == 0) return TP_OK;
     const uint64_t pb = e->pool.page_bytes;
     const int nc = (int)t->types.size();
@@ -464,7 +475,7 @@ tp_status append_device_rows(tp_engine* e, tp_table* t, const std::vector<const 
             left -= take;
         }
     }
-    TP_TRY_CUDA(cudaStreamSynchronize(st));
+    if (sync) TP_TRY_CUDA(cudaStreamSynchronize(st));
     t->chain_used = pos;
     t->batches.push_back(std::move(b));
     t->rows += nrows;
@@ -529,36 +540,58 @@ tp_status part_setup(ExecState& S, Scratch& sc, PartJoin& pj, uint64_t table_bud
     pj.counts = (unsigned long long*)words;
     pj.cursor = pj.counts + P;
     TP_TRY_CUDA(cudaMemsetAsync(pj.counts, 0, 8 * (uint64_t)P, st));
-    s = for_each_dim_batch(S, sc, proto, [&](const tpk::BuildDev& b, uint64_t rows) {
-        mark_launch(e);
-        return cuda_check(tpk::launch_part_hist(b.key, rows, pj.shift, pj.counts, e->num_sms, st), "partition");
-    });
-    if (s) return s;
-    std::vector<unsigned long long> cnt(P);
-    TP_TRY_CUDA(cudaMemcpyAsync(cnt.data(), pj.counts, 8 * (uint64_t)P, cudaMemcpyDeviceToHost, st));
-    TP_TRY_CUDA(cudaStreamSynchronize(st));
-    pj.dim_count.assign(cnt.begin(), cnt.end());
     const uint64_t slot = S.key64 ? 16 : 8;
     auto table_bytes = [&](uint64_t rows) {
         return pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(rows / lf))) * slot;
     };
-    uint64_t resident_rows = 0, mask = 0;
+    // the per-partition counts decide residency only when not every build
+    // row fits: otherwise the histogram pass over the build side is skipped
+    std::vector<unsigned long long> cnt(P, 0);
+    if (table_bytes(S.dim->rows) > table_budget) {
+        s = for_each_dim_batch(S, sc, proto, [&](const tpk::BuildDev& b, uint64_t rows) {
+            mark_launch(e);
+            return cuda_check(tpk::launch_part_hist(b.key, rows, pj.shift, pj.counts, e->num_sms, st),
+                              "partition");
+        });
+        if (s) return s;
+        TP_TRY_CUDA(cudaMemcpyAsync(cnt.data(), pj.counts, 8 * (uint64_t)P, cudaMemcpyDeviceToHost, st));
+        TP_TRY_CUDA(cudaStreamSynchronize(st));
+    } else {
+        cnt[0] = S.dim->rows;   // only the total matters below
+    }
+    pj.dim_count.assign(cnt.begin(), cnt.end());
+    // every partition resident when one table of all rows fits; otherwise
+    // keep room for the largest partition's own table (phase 2) and fill the
+    // rest with resident partitions, in partition order
+    const uint64_t all_mask = P == 64 ? ~0ull : ((1ull << P) - 1);
+    uint64_t resident_rows = 0, mask = 0, total_rows = 0, largest = 0;
     for (int p = 0; p < P; ++p) {
-        if (table_bytes(resident_rows + cnt[p]) <= table_budget) {
-            resident_rows += cnt[p];
-            mask |= 1ull << p;
+        total_rows += cnt[p];
+        largest = std::max<uint64_t>(largest, table_bytes(cnt[p]));
+    }
+    if (table_bytes(total_rows) <= table_budget) {
+        mask = all_mask;
+        resident_rows = total_rows;
+    } else {
+        const uint64_t room = table_budget > largest ? table_budget - largest : 0;
+        for (int p = 0; p < P; ++p) {
+            if (table_bytes(resident_rows + cnt[p]) <= room) {
+                resident_rows += cnt[p];
+                mask |= 1ull << p;
+            }
         }
     }
-    pj.spill_mask = (P == 64 ? ~0ull : ((1ull << P) - 1)) & ~mask;
+    pj.spill_mask = all_mask & ~mask;
     // the resident table
     const uint64_t cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(resident_rows / lf)));
+    pj.resident_bytes = cap * slot;
     void* slots = nullptr;
     if ((s = sc.alloc(&slots, cap * slot))) return s;
     TP_TRY_CUDA(cudaMemsetAsync(slots, 0xFF, cap * slot, st));
     S.jt.slots = (uint64_t*)slots;
     S.jt.mask = cap - 1;
     S.jt.part_mask = mask;
-    S.jt.part_shift = pj.shift;
+    S.jt.part_shift = pj.spill_mask ? pj.shift : 0;   // no filter when every partition is resident
     proto.jt = S.jt;
     pj.build_spill.assign(P, nullptr);
     pj.fact_spill.assign(P, nullptr);
@@ -623,6 +656,12 @@ tp_status part_spill_fact(ExecState& S, Scratch& sc, PartJoin& pj, const tpk::Qu
     }
     if (total == 0) return TP_OK;
     TP_TRY_CUDA(cudaMemcpyAsync(pj.counts, base.data(), 8 * (uint64_t)P, cudaMemcpyHostToDevice, st));
+    // at most SPILL_BACKLOG batches' staging waits on its device -> host copies
+    while (pj.inflight.size() >= SPILL_BACKLOG) {
+        TP_TRY_CUDA(cudaEventSynchronize(pj.inflight.front()));
+        cudaEventDestroy(pj.inflight.front());
+        pj.inflight.pop_front();
+    }
     tpk::SpillCols cols{};
     std::vector<void*> out(S.fact->types.size(), nullptr);
     for (int c : S.used) {
@@ -635,17 +674,33 @@ tp_status part_spill_fact(ExecState& S, Scratch& sc, PartJoin& pj, const tpk::Qu
     }
     mark_launch(e);
     TP_TRY_CUDA(tpk::launch_fact_spill(q, rows, pj.spill_mask, cols, pj.counts, pj.cursor, e->num_sms, st));
+    // the copies to host pages run on the spill stream (the link's other
+    // direction from the prefetch), overlapping the next batches
+    cudaStream_t sp = S.lane->spill;
+    cudaEvent_t ready = nullptr, done = nullptr;
+    TP_TRY_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    cudaError_t ce = cudaEventRecord(ready, st);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(sp, ready, 0);
+    cudaEventDestroy(ready);
+    TP_TRY_CUDA(ce);
     tp_status s = TP_OK;
     for (int p = 0; p < P && s == TP_OK; ++p) {
         if (bc[p] == 0) continue;
         std::vector<const void*> part(S.fact->types.size(), nullptr);
         for (int c : S.used) part[c] = (const uint8_t*)out[c] + base[p] * type_size(S.fact->types[c]);
-        s = append_device_rows(e, pj.fact_spill[p], part, bc[p], st);
+        s = append_device_rows(e, pj.fact_spill[p], part, bc[p], sp, false);
     }
-    for (int c : S.used) {  // staging goes back once its copies are done (append synchronised)
-        dev_free(e, out[c], st);
+    for (int c : S.used) {  // staging goes back (stream-ordered) once its copies are done
+        dev_free(e, out[c], sp);
         sc.ptrs.erase(std::find(sc.ptrs.begin(), sc.ptrs.end(), out[c]));
     }
+    TP_TRY_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    ce = cudaEventRecord(done, sp);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(done);
+        TP_TRY_CUDA(ce);
+    }
+    pj.inflight.push_back(done);
     return s;
 }
 
@@ -656,6 +711,9 @@ tp_status part_phase2(ExecState& S, Scratch& sc, PartJoin& pj, float lf, F&& agg
     if (!pj.spill_mask) return TP_OK;
     tp_engine* e = S.e;
     cudaStream_t st = S.lane->compute;
+    TP_TRY_CUDA(cudaStreamSynchronize(S.lane->spill));   // every spilled fact row is in its pages
+    for (cudaEvent_t ev : pj.inflight) cudaEventDestroy(ev);
+    pj.inflight.clear();
     const uint64_t slot = S.key64 ? 16 : 8;
     uint64_t max_cap = 64, max_rows = 0;
     for (int p = 0; p < pj.P; ++p) {
@@ -663,7 +721,7 @@ tp_status part_phase2(ExecState& S, Scratch& sc, PartJoin& pj, float lf, F&& agg
         max_cap = std::max(max_cap, pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(pj.dim_count[p] / lf))));
         for (auto& bt : pj.build_spill[p]->batches) max_rows = std::max(max_rows, bt.rows);
     }
-    if (max_cap * slot > pj.table_budget)
+    if (max_cap * slot > pj.table_budget - std::min(pj.table_budget, pj.resident_bytes))
         return fail(TP_E_BUDGET, "a spilled join partition needs a %llu-byte table, over the %llu-byte budget; "
                     "use more partitions", (unsigned long long)(max_cap * slot),
                     (unsigned long long)pj.table_budget);
@@ -908,7 +966,9 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             // the result arrays are reserved when the groups are known
             int n_avg = 0;
             for (int a = 0; a < d.n_agg; ++a) n_avg += d.aggs[a].kind == TP_AGG_AVG;
-            const uint64_t result_est = result_groups * (16 + 16 * (uint64_t)ns + 8 * (uint64_t)n_avg);
+            const uint64_t rg = std::max<uint64_t>(1, result_groups);
+            const uint64_t result_est =
+                2 * align256(rg * 8) + ns * align256(rg * 16) + (uint64_t)n_avg * align256(rg * 8);
             const uint64_t taken = reserved_now + est + dim_stage + result_est;
             const uint64_t avail = cap_now > taken ? cap_now - taken : 0;
             const int jp = d.join_partitions;
@@ -924,10 +984,12 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
                 for (int c : S.used) used_bytes += type_size(S.fact->types[c]);
                 // build-pair and fact spill staging, then two tables (the
                 // resident one and one spilled partition's) share the rest
-                const uint64_t stage = align256(S.dim->batch_rows * 12) + align256(fact_rows * used_bytes);
-                part_table_budget = avail > stage ? (avail - stage) * 2 / 5 : 0;
+                const uint64_t stage =
+                    align256(S.dim->batch_rows * 12) + (SPILL_BACKLOG + 1) * align256(fact_rows * used_bytes);
+                // a tenth stays free for retries of a table that outgrew its estimate
+                part_table_budget = avail > stage ? (avail - stage) / 10 * 9 : 0;
                 pj.table_budget = part_table_budget;
-                join_bytes = 2 * part_table_budget + stage;
+                join_bytes = part_table_budget + stage;
             }
         }
         if (!(cache && !pj.on)) est += align256(join_bytes);   // a cached table holds its own reservation

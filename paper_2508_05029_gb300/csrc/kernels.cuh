@@ -244,7 +244,7 @@ constexpr int BATCH_THREADS = 512;
 // Runs the whole queue: n_items tasks, ctr[0] the next task index,
 // done[q] build chunks finished, done[n_q + q] probe tiles finished.
 cudaError_t launch_batch(const BatchQuery* qs, const BatchItem* items, uint32_t n_items, uint32_t n_q,
-                         unsigned* ctr, uint32_t* err, uint64_t wait_ns, uint32_t smem_bytes, int grid,
+                         unsigned* ctr, uint32_t* err, const uint64_t* wait_ns, uint32_t smem_bytes, int grid,
                          cudaStream_t st);
 int batch_grid(uint32_t smem_bytes, int num_sms);
 #endif

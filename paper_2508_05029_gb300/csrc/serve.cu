@@ -137,6 +137,7 @@ tp_status tp_server_start(tp_engine* e, int32_t workers, int32_t max_inflight, u
     for (Lane& l : sv->lanes) {
         TP_TRY_CUDA(cudaStreamCreateWithFlags(&l.compute, cudaStreamNonBlocking));
         TP_TRY_CUDA(cudaStreamCreateWithFlags(&l.copy, cudaStreamNonBlocking));
+        TP_TRY_CUDA(cudaStreamCreateWithFlags(&l.spill, cudaStreamNonBlocking));
         TP_TRY_CUDA(cudaHostAlloc((void**)&l.host_words, 4096, cudaHostAllocDefault));
     }
     for (int i = 0; i < workers; ++i) sv->threads.emplace_back(worker, sv.get(), i);
@@ -209,6 +210,7 @@ void tp_server_stop(tp_server* sv) {
     for (Lane& l : sv->lanes) {
         cudaStreamSynchronize(l.compute);
         cudaStreamSynchronize(l.copy);
+        cudaStreamSynchronize(l.spill);
     }
     for (auto& kv : sv->reqs)   // finished but never collected
         if (kv.second->result) tp_result_free(kv.second->result);
@@ -216,6 +218,7 @@ void tp_server_stop(tp_server* sv) {
     for (Lane& l : sv->lanes) {
         cudaStreamDestroy(l.compute);
         cudaStreamDestroy(l.copy);
+        cudaStreamDestroy(l.spill);
         cudaFreeHost(l.host_words);
     }
     delete sv;

@@ -83,7 +83,8 @@ enum Placement : int32_t { PL_PAGES = TP_HOST_PAGES, PL_DEVICE = TP_DEVICE, PL_W
 // so executions on different lanes overlap on the device.
 struct Lane {
     cudaStream_t compute = nullptr;
-    cudaStream_t copy = nullptr;
+    cudaStream_t copy = nullptr;      // host -> device prefetch
+    cudaStream_t spill = nullptr;     // device -> host spill copies (the other link direction)
     uint64_t* host_words = nullptr;   // 4 KB pinned
 };
 
@@ -97,6 +98,7 @@ struct tp_engine {
     tp::Budget budget;
     cudaStream_t compute = nullptr;
     cudaStream_t copy = nullptr;
+    cudaStream_t spill = nullptr;
     bool own_compute = false;
     std::mutex exec_mu;          // one execution at a time on the engine streams
     std::mutex obj_mu;

@@ -146,6 +146,7 @@ SIGNATURES = {
     "tp_batch_create": (_i32, [_vp, _PP, _i32, ctypes.c_char_p, _PP]),
     "tp_batch_execute": (_i32, [_vp, _PP]),
     "tp_batch_last_ms": (ctypes.c_double, [_vp]),
+    "tp_debug_batch_stall": (_i32, [_vp, _i32, _u64]),
     "tp_batch_destroy": (None, [_vp]),
     "tp_autotune": (_i32, [_vp, _PP, _i32, ctypes.c_char_p]),
     "tp_server_start": (_i32, [_vp, _i32, _i32, _u32, _PP]),
@@ -271,6 +272,26 @@ class Engine:
             raise
         return t
 
+    def table_from_chunks(self, chunks, batch_rows=0) -> "Table":
+        """A host-page table appended chunk by chunk (dicts of equal-length
+        numpy columns, the same names and dtypes in every chunk)."""
+        t = None
+        try:
+            for columns in chunks:
+                arrs = [np.ascontiguousarray(columns[n]) for n in columns]
+                if t is None:
+                    d, keep = self._desc(list(columns), [a.dtype for a in arrs], batch_rows)
+                    h = ctypes.c_void_p()
+                    _check(self.lib.tp_table_create(self.h, ctypes.byref(d), ctypes.byref(h)))
+                    t = Table(self, h, list(columns))
+                ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+                _check(self.lib.tp_table_append(t.h, ptrs, len(arrs[0])))
+        except Exception:
+            if t is not None:
+                t.destroy()
+            raise
+        return t
+
     def table_from_torch(self, columns: dict) -> "Table":
         """Registers CUDA tensors without copying (they must outlive the table)."""
         import torch
@@ -340,6 +361,11 @@ class Batch:
     @property
     def last_ms(self) -> float:
         return self.eng.lib.tp_batch_last_ms(self.h)
+
+    def debug_stall(self, query: int, wait_ns: int = 0):
+        """Makes query's finalisation wait for a tile that never comes (query
+        -1 restores); the bounded wait gives up after wait_ns."""
+        _check(self.eng.lib.tp_debug_batch_stall(self.h, query, wait_ns))
 
     def destroy(self):
         if self.h:

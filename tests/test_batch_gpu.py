@@ -128,3 +128,28 @@ def test_autotune_table_roundtrip(eng, tmp_path):
         p.destroy()
     for t in tabs:
         t.destroy()
+
+
+def test_bounded_wait_times_out_and_context_survives(eng):
+    """A dependency that is never published: the persistent kernel's bounded
+    wait gives up, the host reports TP_E_TIMEOUT, and the same batch (and
+    device context) runs correctly afterwards."""
+    wls = _mix(n=4)
+    tabs, plans = _device_plans(eng, wls)
+    refs = [oracle.run(wl) for wl in wls]
+    b = T.Batch(eng, plans)
+    try:
+        b.debug_stall(2, wait_ns=20_000_000)       # query 2 waits for a tile that never comes; 20 ms limit
+        with pytest.raises(T.TPError) as err:
+            b.execute()
+        assert err.value.status == "timeout"
+        b.debug_stall(-1)
+        for wl, ref, r in zip(wls, refs, b.execute()):
+            assert_matches_oracle(r, ref, wl.query["aggs"])
+            r.free()
+    finally:
+        b.destroy()
+        for p in plans:
+            p.destroy()
+        for t in tabs:
+            t.destroy()
