@@ -95,6 +95,10 @@ enum { TP_AGG_AUTO = 0, TP_AGG_SHARED = 1, TP_AGG_GLOBAL = 2 };
  *                         TP_FLAG_NO_DIRECT_JOIN: always hash the join keys,
  *                         even when they are dense enough for a
  *                         direct-mapped table (key range <= 2 x rows).
+ *                         TP_FLAG_NO_DIRECT_AGG: always hash the group keys of
+ *                         the device-memory aggregation, even when column
+ *                         bounds show a dense key range (a direct-addressed
+ *                         table needs no probing and yields sorted groups).
  *                         TP_FLAG_NO_JIT: never compile plan-specialised
  *                         kernels at run time (NVRTC); the ahead-of-time
  *                         staged kernels run every shape.  Without the flag a
@@ -109,7 +113,8 @@ enum {
     TP_FLAG_NO_STAGED = 2,
     TP_FLAG_EXACT_ONLY = 4,
     TP_FLAG_NO_DIRECT_JOIN = 8,
-    TP_FLAG_NO_JIT = 16
+    TP_FLAG_NO_JIT = 16,
+    TP_FLAG_NO_DIRECT_AGG = 32
 };
 typedef struct {
     uint64_t page_bytes;

@@ -474,4 +474,18 @@ __device__ __forceinline__ uint64_t* agg_slot(const AggTable& t, uint64_t key, u
     return nullptr;
 }
 
+// Slot of a key in either kind of global table (direct: key - kmin, in
+// range by the column bounds the host checked).
+__device__ __forceinline__ uint64_t* agg_slot_any(const AggTable& t, uint64_t key, uint32_t* err) {
+    if (t.direct) {
+        const uint64_t s = key - t.kmin;
+        if (s > t.mask) {
+            atomicOr(err, ERR_INTERNAL);
+            return nullptr;
+        }
+        return t.slots + s * t.words;
+    }
+    return agg_slot(t, key, err);
+}
+
 }  // namespace tpk

@@ -394,6 +394,12 @@ tp_status alloc_result(tp_engine* e, tp_plan* p, uint64_t cap, tp_result** out, 
 // and fact rows of the other partitions are spilled to pool pages, then
 // joined one partition at a time against the same accumulators.
 
+// Direct-addressed aggregation tables: at most this many slots, and used
+// when the key range is at most four times the expected groups (or below
+// DIRECT_AGG_ALWAYS slots).
+constexpr uint64_t DIRECT_AGG_MAX_SLOTS = 1ull << 27;
+constexpr uint64_t DIRECT_AGG_ALWAYS = 1ull << 20;
+
 // Batches whose fact spill copies may still be running when the next batch
 // spills (each holds a staging buffer).
 constexpr size_t SPILL_BACKLOG = 2;
@@ -928,6 +934,8 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
     const bool shared = p->strategy == TP_AGG_SHARED;
     const uint32_t G = shared ? (1u << p->key_bits) : 0;
     uint64_t agg_cap = 0;
+    bool gdirect = false;           // direct-addressed global table over [dmin, dmin + dspan)
+    uint64_t dmin = 0, dspan = 0;
     const uint32_t words = 2 + 2 * ns;
     uint64_t result_groups = G;
     if (shared) {
@@ -939,10 +947,20 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             if (p->key_bits < 40) groups = std::min<uint64_t>(groups, 1ull << p->key_bits);
         }
         result_groups = groups;
-        agg_cap = pow2_at_least(std::max<uint64_t>(1024, (uint64_t)std::ceil(groups / lf)));
-        // table + compaction/sort arrays
-        est += align256((agg_cap + 1) * words * 8) + 2 * align256((agg_cap + 1) * 12) +
-               align256(tpk::radix_sort_hist_words(agg_cap + 1) * 4);
+        // a dense key range (column bounds) that the groups fill well enough
+        // gets a direct-addressed table: no probing, groups come out sorted
+        if (!(e->cfg.flags & TP_FLAG_NO_DIRECT_AGG) && direct_group_range(p, S.fact, S.dim, &dmin, &dspan) &&
+            dspan <= DIRECT_AGG_MAX_SLOTS && dspan <= 4 * std::max<uint64_t>(groups, DIRECT_AGG_ALWAYS)) {
+            gdirect = true;
+            result_groups = std::min(groups, dspan);
+            const uint64_t n_chunks = (dspan + tpk::DIRECT_CHUNK - 1) / tpk::DIRECT_CHUNK;
+            est += align256(dspan * words * 8) + align256(n_chunks * 4) + align256((n_chunks + 1) * 8);
+        } else {
+            agg_cap = pow2_at_least(std::max<uint64_t>(1024, (uint64_t)std::ceil(groups / lf)));
+            // table + compaction/sort arrays
+            est += align256((agg_cap + 1) * words * 8) + 2 * align256((agg_cap + 1) * 12) +
+                   align256(tpk::radix_sort_hist_words(agg_cap + 1) * 4);
+        }
     }
     uint64_t join_bytes = 0;
     PartJoin pj;
@@ -1135,15 +1153,21 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         for (int g = 0; g < d.n_group; ++g) fold = fold && d.group[g].side == TP_SIDE_FACT;
         for (int attempt = 0;; ++attempt) {
             void* tab = nullptr;
-            const uint64_t tbytes = (agg_cap + 1) * words * 8;
+            const uint64_t tbytes = gdirect ? dspan * words * 8 : (agg_cap + 1) * words * 8;
             if ((s = sc.alloc(&tab, tbytes))) return s;
-            TP_TRY_CUDA(tpk::launch_init_agg((uint64_t*)tab, agg_cap + 1, words, st));
-            mark_launch(e);
+            if (gdirect) {
+                TP_TRY_CUDA(cudaMemsetAsync(tab, 0, tbytes, st));
+            } else {
+                TP_TRY_CUDA(tpk::launch_init_agg((uint64_t*)tab, agg_cap + 1, words, st));
+                mark_launch(e);
+            }
             TP_TRY_CUDA(cudaMemsetAsync(S.counters, 0, 3 * sizeof(unsigned long long), st));
             tpk::AggTable at{};
             at.slots = (uint64_t*)tab;
-            at.mask = agg_cap - 1;
+            at.mask = gdirect ? dspan - 1 : agg_cap - 1;
             at.words = words;
+            at.direct = gdirect ? 1 : 0;
+            at.kmin = dmin;
             at.used = S.counters;
             at.max_used = (uint64_t)(agg_cap * 0.9);
             auto global_core = [&](const tpk::QueryDev& q, uint64_t rows) -> tp_status {
@@ -1197,6 +1221,32 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
                 TP_TRY_CUDA(cudaMemsetAsync(misc, 0, 4, st));
                 e->retries++;
                 continue;
+            }
+            if (gdirect) {
+                // occupied slots are already in key order: count per chunk,
+                // scan, write the rows at their offsets
+                const uint64_t n_chunks = (dspan + tpk::DIRECT_CHUNK - 1) / tpk::DIRECT_CHUNK;
+                void *cnts = nullptr, *offs = nullptr;
+                if ((s = sc.alloc(&cnts, n_chunks * 4)) || (s = sc.alloc(&offs, (n_chunks + 1) * 8))) return s;
+                TP_TRY_CUDA(tpk::launch_direct_count(at, dspan, (uint32_t*)cnts, e->num_sms, st));
+                TP_TRY_CUDA(tpk::launch_direct_scan((const uint32_t*)cnts, n_chunks, (unsigned long long*)offs, st));
+                mark_launch(e);
+                mark_launch(e);
+                TP_TRY_CUDA(cudaMemcpyAsync(lane->host_words, (unsigned long long*)offs + n_chunks, 8,
+                                            cudaMemcpyDeviceToHost, st));
+                TP_TRY_CUDA(cudaStreamSynchronize(st));
+                e->d2h_bytes += 8;
+                const uint64_t n = lane->host_words[0];
+                tpk::OutDev od;
+                if ((s = alloc_result(e, p, n, &res, &od, S.counters + 1, st))) return s;
+                TP_TRY_CUDA(tpk::launch_direct_emit(at, dspan, (const unsigned long long*)offs, ns, od, gfast,
+                                                    e->num_sms, st));
+                mark_launch(e);
+                TP_TRY_CUDA(cudaStreamSynchronize(st));
+                res->n_groups = n;
+                p->history_groups = n;
+                timer.collect();
+                break;
             }
             // compact occupied slots, sort them by key, gather the rows
             void *k0 = nullptr, *k1 = nullptr, *v0 = nullptr, *v1 = nullptr, *hist = nullptr;
@@ -1310,6 +1360,24 @@ bool sums_fit_int64(const tp_plan* p, const tp_table* fact) {
         }
         if (B > limit / (i128)n) return false;
     }
+    return true;
+}
+
+bool direct_group_range(const tp_plan* p, const tp_table* fact, const tp_table* dim, uint64_t* kmin,
+                        uint64_t* span) {
+    const tp_plan_desc& d = p->d;
+    if (d.n_group == 0) return false;
+    unsigned __int128 lo = 0, hi = 0;
+    for (int g = 0; g < d.n_group; ++g) {
+        const tp_table* t = d.group[g].side == TP_SIDE_FACT ? fact : dim;
+        const int col = d.group[g].col, bits = d.group[g].bits;
+        if (!t || t->rows == 0 || t->cmin[col] < 0) return false;
+        if (bits < 64 && ((uint64_t)t->cmax[col] >> bits) != 0) return false;
+        lo = (lo << bits) | (uint64_t)t->cmin[col];
+        hi = (hi << bits) | (uint64_t)t->cmax[col];
+    }
+    *kmin = (uint64_t)lo;
+    *span = (uint64_t)(hi - lo + 1);
     return true;
 }
 

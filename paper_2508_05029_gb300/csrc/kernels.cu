@@ -10,6 +10,7 @@
 // holds rows {2l, 2l+1, 64+2l, 64+2l+1}, so every column is read with two
 // fully coalesced vector loads per lane whatever its width (8-bit: 2 bytes,
 // 32-bit: 8 bytes, 64-bit: 16 bytes per load).
+#include <algorithm>
 #include <map>
 #include <mutex>
 
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(256) k_agg_global(const __grid_constant__ Quer
         for (int i = 0; i < 4; ++i) {
             slot[i] = nullptr;
             if (!pass[i] || ((i & 1) && fold[i >> 1])) continue;
-            slot[i] = agg_slot(t, key[i], q.err);
+            slot[i] = agg_slot_any(t, key[i], q.err);
             if (slot[i])
                 atomicAdd((unsigned long long*)(slot[i] + 1), (i & 1) == 0 && fold[i >> 1] ? 2ull : 1ull);
         }
@@ -272,6 +273,120 @@ cudaError_t launch_final_dense(const uint64_t* gacc, uint32_t key_bits, int n_su
 }
 
 // Occupied slots of the global table -> (key, slot index); also the max key.
+// ------------------------------------------------------------ direct tables
+
+// Occupied slots (count word non-zero) of each chunk of DIRECT_CHUNK slots.
+__global__ void k_direct_count(const __grid_constant__ AggTable t, uint64_t n_slots, uint32_t* __restrict__ counts) {
+    __shared__ uint32_t warp_sum[32];
+    const uint64_t n_chunks = (n_slots + DIRECT_CHUNK - 1) / DIRECT_CHUNK;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        uint32_t n = 0;
+        for (uint32_t i = threadIdx.x; i < DIRECT_CHUNK; i += blockDim.x) {
+            const uint64_t s = c * DIRECT_CHUNK + i;
+            if (s < n_slots && t.slots[s * t.words + 1] != 0) ++n;
+        }
+        for (int off = 16; off > 0; off >>= 1) n += __shfl_xor_sync(0xffffffffu, n, off);
+        if (lane == 0) warp_sum[warp] = n;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += warp_sum[w];
+            counts[c] = tot;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_direct_count(const AggTable& t, uint64_t n_slots, uint32_t* counts, int num_sms,
+                                cudaStream_t st) {
+    if (n_slots == 0) return cudaSuccess;
+    const uint64_t n_chunks = (n_slots + DIRECT_CHUNK - 1) / DIRECT_CHUNK;
+    const uint64_t blocks = std::min<uint64_t>(n_chunks, (uint64_t)num_sms * 8);
+    k_direct_count<<<(unsigned)blocks, 256, 0, st>>>(t, n_slots, counts);
+    return cudaGetLastError();
+}
+
+// Exclusive scan of the chunk counts by one CTA; offsets[n_chunks] = total.
+__global__ void k_direct_scan(const uint32_t* __restrict__ counts, uint64_t n_chunks,
+                              unsigned long long* __restrict__ offsets) {
+    __shared__ unsigned long long part[1024];
+    const uint64_t per = (n_chunks + blockDim.x - 1) / blockDim.x;
+    const uint64_t b = threadIdx.x * per, e = b + per < n_chunks ? b + per : n_chunks;
+    unsigned long long sum = 0;
+    for (uint64_t i = b; i < e; ++i) sum += counts[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (uint32_t i = 0; i < blockDim.x; ++i) {
+            const unsigned long long v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        offsets[n_chunks] = run;
+    }
+    __syncthreads();
+    unsigned long long run = part[threadIdx.x];
+    for (uint64_t i = b; i < e; ++i) {
+        offsets[i] = run;
+        run += counts[i];
+    }
+}
+
+cudaError_t launch_direct_scan(const uint32_t* counts, uint64_t n_chunks, unsigned long long* offsets,
+                               cudaStream_t st) {
+    k_direct_scan<<<1, 1024, 0, st>>>(counts, n_chunks, offsets);
+    return cudaGetLastError();
+}
+
+// Each chunk writes its occupied slots in slot (= key) order at its offset.
+__global__ void k_direct_emit(const __grid_constant__ AggTable t, uint64_t n_slots,
+                              const unsigned long long* __restrict__ offsets, int n_sum,
+                              const __grid_constant__ OutDev o, int lo_only) {
+    __shared__ uint32_t warp_tot[32];
+    __shared__ unsigned long long base;
+    const uint64_t n_chunks = (n_slots + DIRECT_CHUNK - 1) / DIRECT_CHUNK;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (uint64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        if (threadIdx.x == 0) base = offsets[c];
+        __syncthreads();
+        for (uint32_t i0 = 0; i0 < DIRECT_CHUNK; i0 += blockDim.x) {
+            const uint64_t s = c * DIRECT_CHUNK + i0 + threadIdx.x;
+            const uint64_t* p = t.slots + s * t.words;
+            const bool has = s < n_slots && p[1] != 0;
+            const unsigned m = __ballot_sync(0xffffffffu, has);
+            if (lane == 0) warp_tot[warp] = __popc(m);
+            __syncthreads();
+            uint32_t before = 0, total = 0;
+            for (int w = 0; w < nwarps; ++w) {
+                if (w < warp) before += warp_tot[w];
+                total += warp_tot[w];
+            }
+            if (has) {
+                uint64_t lh[2 * MAX_SUM];
+                for (int x = 0; x < n_sum; ++x) {
+                    lh[2 * x] = p[2 + 2 * x];
+                    lh[2 * x + 1] = lo_only ? (uint64_t)((int64_t)lh[2 * x] >> 63) : p[3 + 2 * x];
+                }
+                write_row(o, base + before + __popc(m & ((1u << lane) - 1u)), s + t.kmin, p[1], lh, n_sum);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) base += total;
+            __syncthreads();
+        }
+    }
+}
+
+cudaError_t launch_direct_emit(const AggTable& t, uint64_t n_slots, const unsigned long long* offsets, int n_sum,
+                               const OutDev& o, bool lo_only, int num_sms, cudaStream_t st) {
+    if (n_slots == 0) return cudaSuccess;
+    const uint64_t n_chunks = (n_slots + DIRECT_CHUNK - 1) / DIRECT_CHUNK;
+    const uint64_t blocks = std::min<uint64_t>(n_chunks, (uint64_t)num_sms * 8);
+    k_direct_emit<<<(unsigned)blocks, 256, 0, st>>>(t, n_slots, offsets, n_sum, o, lo_only ? 1 : 0);
+    return cudaGetLastError();
+}
+
 __global__ void k_compact_global(const __grid_constant__ AggTable t, uint64_t cap_with_side,
                                  uint64_t* __restrict__ keys, uint32_t* __restrict__ idx,
                                  unsigned long long* count, unsigned long long* maxkey) {

@@ -117,13 +117,17 @@ struct BuildDev {
 // Global aggregation table: slot = {key, count, (lo, hi) per sum}, EMPTY key =
 // all ones; the all-ones key itself is kept in a dedicated side slot placed
 // after the last regular slot.
+//   Direct (dense key range, direct != 0): the slot of key k is k - kmin,
+//   mask + 1 slots cover every key the column bounds allow; the key word is
+//   unused (zero) and a slot is occupied when its count is non-zero.
 struct AggTable {
     uint64_t* slots;
     uint64_t mask;
     uint32_t words;          // 64-bit words per slot = 2 + 2 * n_sum
-    uint32_t pad;
-    unsigned long long* used;   // occupied slots counter
-    uint64_t max_used;          // beyond this, new keys set ERR_OVERFLOW
+    int32_t direct;
+    unsigned long long* used;   // occupied slots counter (hashed)
+    uint64_t max_used;          // beyond this, new keys set ERR_OVERFLOW (hashed)
+    uint64_t kmin;              // direct: smallest key
 };
 
 // Output arrays of one result (device memory).
@@ -355,6 +359,16 @@ cudaError_t launch_fact_spill(const QueryDev& q, uint64_t n, uint64_t spill_mask
 // Minimum and maximum of a column (out[0] = min, out[1] = max, initialised by
 // the caller to INT64_MAX / INT64_MIN).
 cudaError_t launch_minmax(const DevCol& c, uint64_t n, long long* out, int num_sms, cudaStream_t st);
+// Direct tables: the output rows in key order without a sort.  Occupied
+// slots per chunk of DIRECT_CHUNK slots, an exclusive scan of those counts
+// (offsets[n_chunks] = total), then each chunk writes its rows.
+constexpr uint32_t DIRECT_CHUNK = 4096;
+cudaError_t launch_direct_count(const AggTable& t, uint64_t n_slots, uint32_t* counts, int num_sms,
+                                cudaStream_t st);
+cudaError_t launch_direct_scan(const uint32_t* counts, uint64_t n_chunks, unsigned long long* offsets,
+                               cudaStream_t st);
+cudaError_t launch_direct_emit(const AggTable& t, uint64_t n_slots, const unsigned long long* offsets, int n_sum,
+                               const OutDev& o, bool lo_only, int num_sms, cudaStream_t st);
 // compaction of the global table into (key, slot) pairs + max key
 cudaError_t launch_compact_global(const AggTable& t, uint64_t cap_with_side, uint64_t* keys,
                                   uint32_t* idx, unsigned long long* count,

@@ -141,7 +141,7 @@ __device__ __forceinline__ void consume_global(const QueryDev& q, const StageLay
                 }
             }
             if (!head) continue;
-            uint64_t* p = agg_slot(tab, key[j], q.err);
+            uint64_t* p = agg_slot_any(tab, key[j], q.err);
             if (!p) continue;
             atomicAdd((unsigned long long*)(p + 1), (unsigned long long)cnt);
 #pragma unroll
@@ -154,7 +154,7 @@ __device__ __forceinline__ void consume_global(const QueryDev& q, const StageLay
         for (int j = 0; j < ST_RPL; ++j) {
             slot[j] = nullptr;
             if (!((pm >> j) & 1u)) continue;
-            slot[j] = agg_slot(tab, key[j], q.err);
+            slot[j] = agg_slot_any(tab, key[j], q.err);
             if (slot[j]) atomicAdd((unsigned long long*)(slot[j] + 1), 1ull);
         }
 #pragma unroll

@@ -216,6 +216,11 @@ tpk::QueryDev plan_query_dev(const tp_plan* p, const std::vector<const void*>& c
 // row count (and below 2^31), so a direct-mapped join table of *range slots
 // serves it.
 bool direct_join_range(const tp_table* dim, int col, uint64_t* range);
+// Dense group keys: from the group fields' column bounds, every packed key of
+// a surviving row lies in [*kmin, *kmin + *span) (false when a bound is
+// negative or wider than its field).
+bool direct_group_range(const tp_plan* p, const tp_table* fact, const tp_table* dim, uint64_t* kmin,
+                        uint64_t* span);
 // Column bounds prove every sum of the plan stays inside int64 over the fact table.
 bool sums_fit_int64(const tp_plan* p, const tp_table* fact);
 // Per-row term range of every sum slot (valid when sums_fit_int64 holds).

@@ -207,7 +207,8 @@ def test_budget_refusal_and_release(eng):
 
 @pytest.mark.parametrize("flags", [0, T.TP_FLAG_EXACT_ONLY, T.TP_FLAG_NO_STAGED, T.TP_FLAG_NO_DIRECT_JOIN,
                                    T.TP_FLAG_NO_STAGED | T.TP_FLAG_NO_DIRECT_JOIN, T.TP_FLAG_NO_JIT,
-                                   T.TP_FLAG_NO_JIT | T.TP_FLAG_EXACT_ONLY, T.TP_FLAG_NO_JIT | T.TP_FLAG_NO_DIRECT_JOIN])
+                                   T.TP_FLAG_NO_JIT | T.TP_FLAG_EXACT_ONLY, T.TP_FLAG_NO_JIT | T.TP_FLAG_NO_DIRECT_JOIN,
+                                   T.TP_FLAG_NO_DIRECT_AGG])
 def test_every_kernel_path(flags):
     """Staged 64-bit (bounds prove no overflow), staged exact 128-bit, the
     plain-load kernel, hashed instead of direct-mapped join tables, and the
@@ -276,5 +277,21 @@ def test_jit_fact_field_range_error():
             run_gpu(e, wl.fact, wl.dim, q)
         assert err.value.status == "range"
         assert e.stats()["jit_launches"] > 0
+    finally:
+        e.close()
+
+
+@pytest.mark.parametrize("flags", [0, T.TP_FLAG_NO_DIRECT_AGG, T.TP_FLAG_EXACT_ONLY,
+                                   T.TP_FLAG_EXACT_ONLY | T.TP_FLAG_NO_DIRECT_AGG, T.TP_FLAG_NO_STAGED])
+@pytest.mark.parametrize("which", ["b", "b2"])
+def test_many_groups_direct_and_hashed(flags, which):
+    """Many groups: the direct-addressed table (dense order keys, sorted output
+    without a sort) and the hashed table (with compaction and radix sort) give
+    the oracle's result, in 64-bit and exact accumulation."""
+    wl = W.config2(which, n_fact=2_400_011, n_dim=150_000)
+    e = T.Engine(page_bytes=8 << 20, n_pages=256, batch_rows=1_000_000, flags=flags)
+    try:
+        check(e, wl.fact, wl.dim, wl.query)
+        check(e, wl.fact, wl.dim, wl.query, placement=T.TP_HOST_PAGES)
     finally:
         e.close()
