@@ -49,7 +49,8 @@ BYTES_PER_DIM_ROW = 4 + 4                            # pk, attr
 # run-time compiled (plan-specialised) staged kernel, or the ahead-of-time one
 PROFILE_SUMMARY = {"tpj_dense": os.path.join(ROOT, "profiles", "tpj_dense_star12M.md"),
                    "k_agg_shared_staged": os.path.join(ROOT, "profiles", "k_agg_shared_staged_star12M.md")}
-KERNEL_SOURCES = {"tpj_dense": ("kernels.cuh", "device.cuh", "pipeline.cuh", "jit_dense.cuh", "jit.cu", "staged.cu"),
+KERNEL_SOURCES = {"tpj_dense": ("kernels.cuh", "device.cuh", "pipeline.cuh", "jit_common.cuh", "jit_dense.cuh",
+                                "jit.cu", "staged.cu"),
                   "k_agg_shared_staged": ("kernels.cu", "kernels.cuh", "device.cuh", "pipeline.cuh", "staged.cu")}
 
 
@@ -64,8 +65,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample-rows", type=int, default=6_000_000)
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary queries")
-    ap.add_argument("--batch-scale", type=float, default=0.25,
-                    help="fact-size scale of the 256-query batched mix (1.0 = the full ~394M rows)")
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="fact-size scale of the 256-query batched and served mixes (1.0 = the full ~394M rows)")
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="arrival window per served rate")
     ap.add_argument("--no-patterns", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--no-outofcore", action="store_true", help="skip the out-of-core (paged, spilling) query")
@@ -256,14 +257,18 @@ def reference_arm(args, world, rank):
 
 
 # ------------------------------------------------------ batched and served
-def _mix_tables(eng, T, W, torch, dev, n_queries, scale, n_dims=None):
+def _mix_tables(eng, T, W, torch, dev, n_queries, scale, n_dims=None, fact_pages=False):
     """The batched mix: per query its own fact table (lognormal size), a
     dimension (log-uniform size) and a group count; dims shared round-robin
-    when n_dims is given."""
+    when n_dims is given.  Fact tables are device-resident, or in the engine's
+    pinned pages (streamed per query) with fact_pages.  Returns the tables,
+    plans, fact rows and algorithmic bytes (34 B per fact row, 8 B per
+    dimension row of each query)."""
     sz = W.config4_sizes(n_queries=n_queries)
     tabs, plans = [], []
     dims = {}
     rows = 0
+    alg = 0
     for q in range(n_queries):
         dq = q % n_dims if n_dims else q
         wl = W.config4_query(dq, int(sz["fact"][q]), int(sz["dim"][dq]), int(sz["cutoff"][q]),
@@ -276,16 +281,20 @@ def _mix_tables(eng, T, W, torch, dev, n_queries, scale, n_dims=None):
         if dq not in dims:
             dims[dq] = eng.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in wl.dim.items()})
             tabs.append(dims[dq])
-        ft = eng.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in wl.fact.items()})
+        if fact_pages:
+            ft = eng.table_from_numpy(wl.fact, placement=T.TP_HOST_PAGES)
+        else:
+            ft = eng.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in wl.fact.items()})
         tabs.append(ft)
         rows += wl.n_fact
+        alg += 34 * wl.n_fact + 8 * wl.dim["pk"].size
         plans.append(eng.plan(ft, dims[dq], wl.query))
-    return tabs, plans, rows
+    return tabs, plans, rows, alg
 
 
-def batched_measure(T, W, torch, dev, stream, scale, reps=3):
+def batched_measure(T, W, torch, dev, stream, scale, peak, reps=3):
     eng = T.Engine(compute_stream=stream.cuda_stream)
-    tabs, plans, rows = _mix_tables(eng, T, W, torch, dev, 256, scale)
+    tabs, plans, rows, alg = _mix_tables(eng, T, W, torch, dev, 256, scale)
     b = T.Batch(eng, plans)
     best_b = 1e30
     for i in range(reps + 1):
@@ -309,8 +318,11 @@ def batched_measure(T, W, torch, dev, stream, scale, reps=3):
     for t in tabs:
         t.destroy()
     eng.close()
+    gbs = alg / (best_b / 1e3) / 1e9
     return {"queries": 256, "fact_rows": rows, "fact_scale": scale, "batched_ms": best_b, "plain_ms": best_p,
             "speedup": best_p / best_b, "batched_rows_per_s": rows / (best_b / 1e3),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "alg_bytes": alg},
             "how": "one persistent graph-captured launch vs 256 tp_execute calls on one stream"}
 
 
@@ -385,12 +397,18 @@ def outofcore_measure(T, W, torch, dev, n_fact, n_dim, budgets_gb, steps, link):
     return out
 
 
-def served_measure(T, W, torch, dev, rates, seconds, scale):
-    """Open-loop Poisson arrivals; latency = scheduled arrival -> result on host."""
+def served_measure(T, W, torch, dev, rates, seconds, scale, fact_pages=False):
+    """Open-loop Poisson arrivals; latency = scheduled arrival -> result on host.
+    fact_pages: every request streams its fact table from pinned pages."""
     import threading
     import time as _t
-    eng = T.Engine()
-    tabs, plans, _ = _mix_tables(eng, T, W, torch, dev, 256, scale, n_dims=64)
+    page = 16 << 20
+    n_pages = 0
+    if fact_pages:
+        sz = W.config4_sizes(n_queries=256)
+        n_pages = int(sum(int(f * scale) * 34 * 1.1 + page for f in sz["fact"]) // page) + 64
+    eng = T.Engine(page_bytes=page, n_pages=n_pages, batch_rows=4 << 20)
+    tabs, plans, _, _ = _mix_tables(eng, T, W, torch, dev, 256, scale, n_dims=64, fact_pages=fact_pages)
     for p in plans:     # warm: plan history, selectivity samples
         p.execute().free()
     out = {}
@@ -573,9 +591,12 @@ def main():
 
     patterns = None
     if not args.no_patterns:
-        patterns = {"batched": batched_measure(T, W, torch, dev, stream, args.batch_scale),
+        peak_hbm, _ = measured_peaks()
+        patterns = {"batched": batched_measure(T, W, torch, dev, stream, args.batch_scale, peak_hbm),
                     "served": served_measure(T, W, torch, dev, (200, 500, 1000, 2000), args.serve_seconds,
-                                             args.batch_scale)}
+                                             args.batch_scale),
+                    "served_streamed": served_measure(T, W, torch, dev, (200, 500, 1000, 2000),
+                                                      args.serve_seconds, args.batch_scale, fact_pages=True)}
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample_rows > 0:

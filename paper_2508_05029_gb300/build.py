@@ -48,7 +48,7 @@ def up_to_date() -> bool:
 
 # Device headers embedded in the library for run-time (NVRTC) compilation of
 # plan-specialised kernels, in include order.
-JIT_HEADERS = ["kernels.cuh", "device.cuh", "pipeline.cuh", "jit_dense.cuh"]
+JIT_HEADERS = ["kernels.cuh", "device.cuh", "pipeline.cuh", "jit_common.cuh", "jit_dense.cuh", "jit_batch.cuh"]
 
 
 def _write_jit_sources() -> None:

@@ -268,6 +268,7 @@ struct tp_batch {
     uint32_t smem = 0;
     int grid = 0;
     uint64_t* d_wait = nullptr;          // limit of every dependency wait, ns (device word)
+    bool jit = false;                    // the run-time compiled kernel runs the queue
     std::vector<uint32_t> probe_items;   // per query, as laid out (tp_debug_batch_stall restores it)
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -276,6 +277,18 @@ struct tp_batch {
 };
 
 static constexpr uint64_t BATCH_WAIT_NS = 2000000000ull;   // 2 s
+
+// Resident CTAs of the run-time compiled queue kernel: every SM, as many as fit.
+static int jit_batch_grid(const void* k, uint32_t smem_bytes, int num_sms) {
+    tpk::ensure_smem_limit(k, (int)smem_bytes);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, tpk::BATCH_THREADS, smem_bytes) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * num_sms;
+}
 
 static void batch_free(tp_batch* b) {
     if (!b) return;
@@ -483,6 +496,34 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
     }
     for (int i = 0; i < n; ++i) items.push_back(tpk::BatchItem{(uint32_t)i, tpk::BI_FINAL, 0, 0, 0});
     b->n_items = (uint32_t)items.size();
+    // run-time compiled probe tasks: one shape struct per distinct query shape
+    const void* jk = nullptr;
+    if (!(e->cfg.flags & TP_FLAG_NO_JIT)) {
+        std::map<std::string, int> ids;
+        std::string src;
+        for (int i = 0; i < n; ++i) {
+            int narrow[tpk::MAX_SUM] = {};
+            narrow_products(plans[i], plans[i]->d.fact, narrow);
+            const Q& x = qs[i];
+            const std::string key = shape_struct("JS_", hq[i].q, x.mode, x.smem, x.fast, narrow);
+            auto it = ids.find(key);
+            if (it == ids.end()) {
+                const int id = (int)ids.size();
+                it = ids.emplace(key, id).first;
+                src += shape_struct("JS_" + std::to_string(id), hq[i].q, x.mode, x.smem, x.fast, narrow);
+            }
+            hq[i].shape = it->second;
+        }
+        src += "#include \"jit_batch.cuh\"\n"
+               "__device__ void tpj::dispatch_probe(const tpk::BatchQuery& B, uint64_t r0, uint64_t r1, "
+               "unsigned char* smem) {\n    switch (B.shape) {\n";
+        for (size_t k = 0; k < ids.size(); ++k)
+            src += "    case " + std::to_string(k) + ": probe_tile<JS_" + std::to_string(k) + ">(B, r0, r1, smem); break;\n";
+        src += "    default: break;\n    }\n}\n";
+        std::string why;
+        jk = jit_kernel(e, src, "tpj_batch", &why);
+    }
+    b->jit = jk != nullptr;
     b->probe_items.resize(n);
     for (int i = 0; i < n; ++i) b->probe_items[i] = hq[i].probe_items;
     TP_TRY_CUDA(cudaMemcpyAsync(b->d_wait, &BATCH_WAIT_NS, 8, cudaMemcpyHostToDevice, e->compute));
@@ -491,15 +532,25 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
                                 cudaMemcpyHostToDevice, e->compute));
     TP_TRY_CUDA(cudaStreamSynchronize(e->compute));
     b->smem = smem_max;
-    b->grid = tpk::batch_grid(b->smem, e->num_sms);
+    b->grid = jk ? jit_batch_grid(jk, b->smem, e->num_sms) : tpk::batch_grid(b->smem, e->num_sms);
     // ---- capture: reset tables and counters, run the queue
     cudaGraph_t graph = nullptr;
     TP_TRY_CUDA(cudaStreamBeginCapture(e->compute, cudaStreamCaptureModeThreadLocal));
     cudaError_t ce = cudaMemsetAsync(b->ff_base, 0xFF, b->ff_bytes, e->compute);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(b->zero_base, 0, b->zero_bytes, e->compute);
-    if (ce == cudaSuccess)
+    if (ce == cudaSuccess && jk) {
+        const tpk::BatchQuery* a_q = b->d_q;
+        const tpk::BatchItem* a_items = b->d_items;
+        uint32_t a_n = b->n_items, a_nq = (uint32_t)n;
+        unsigned* a_ctr = b->d_ctr;
+        uint32_t* a_err = b->d_err;
+        const uint64_t* a_wait = b->d_wait;
+        void* args[] = {&a_q, &a_items, &a_n, &a_nq, &a_ctr, &a_err, &a_wait};
+        ce = cudaLaunchKernel(jk, dim3(b->grid), dim3(tpk::BATCH_THREADS), args, b->smem, e->compute);
+    } else if (ce == cudaSuccess) {
         ce = tpk::launch_batch(b->d_q, b->d_items, b->n_items, (uint32_t)n, b->d_ctr, b->d_err, b->d_wait, b->smem,
                                b->grid, e->compute);
+    }
     cudaError_t ce2 = cudaStreamEndCapture(e->compute, &graph);
     if (ce != cudaSuccess || ce2 != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -524,6 +575,7 @@ static tp_status batch_run(tp_batch* b, std::vector<tp_result*>* results) {
     TP_TRY_CUDA(cudaGraphLaunch(b->exec, e->compute));
     TP_TRY_CUDA(cudaEventRecord(b->ev1, e->compute));
     e->launches += 1;
+    if (b->jit) e->jit_launches++;
     std::vector<unsigned long long> groups(n);
     uint32_t err = 0;
     TP_TRY_CUDA(cudaMemcpyAsync(groups.data(), b->d_groups, 8ull * n, cudaMemcpyDeviceToHost, e->compute));

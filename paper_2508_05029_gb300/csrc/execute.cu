@@ -1395,11 +1395,13 @@ void narrow_products(const tp_plan* p, const tp_table* fact, int* out) {
     }
 }
 
-// Shape of a dense staged launch, as the struct JS the run-time compiled
-// kernel specialises on (layout: jit_dense.cuh).
-std::string dense_shape(const tpk::QueryDev& q, const tpk::StageLayout& L, bool fast, const int* narrow) {
-    auto arr = [](const char* name, const int* v, int n) {
-        std::string r = std::string(name) + "[" + std::to_string(n) + "] = {";
+// A plan shape as a struct of compile-time constants for the run-time
+// compiled kernels (fields: jit_common.cuh).  mode[s]: 32-bit accumulation
+// mode of sum s (fast only).
+std::string shape_struct(const std::string& name, const tpk::QueryDev& q, const int8_t* mode_in, bool fast,
+                         bool lo_only, const int* narrow) {
+    auto arr = [](const char* nm, const int* v, int n) {
+        std::string r = std::string(nm) + "[" + std::to_string(n) + "] = {";
         for (int i = 0; i < n; ++i) r += (i ? ", " : "") + std::to_string(v[i]);
         return r + "}";
     };
@@ -1415,11 +1417,11 @@ std::string dense_shape(const tpk::QueryDev& q, const tpk::StageLayout& L, bool 
         skind[s] = q.skind[s];
         atype[s] = q.sa[s].type;
         btype[s] = q.skind[s] == tpk::S_MUL_SUB ? q.sb[s].type : 0;
-        mode[s] = fast ? L.sum_mode[s] : 0;
+        mode[s] = fast ? mode_in[s] : 0;
         nar[s] = fast && mode[s] == 2 && q.skind[s] == tpk::S_MUL_SUB ? narrow[s] : 0;
     }
     const int join = !q.has_join ? 0 : (q.jt.direct ? 1 : (q.jt.key64 ? 3 : 2));
-    std::string r = "struct JS {\n";
+    std::string r = "struct " + name + " {\n";
     r += "    static constexpr int filter = " + std::to_string(q.has_filter ? 1 : 0) +
          ", ftype = " + std::to_string(q.has_filter ? q.fcol.type : 0) + ", join = " + std::to_string(join) +
          ", ktype = " + std::to_string(q.has_join ? q.fk.type : 0) +
@@ -1431,8 +1433,14 @@ std::string dense_shape(const tpk::QueryDev& q, const tpk::StageLayout& L, bool 
     r += "    static constexpr int " + arr("skind", skind, tpk::MAX_SUM) + ", " + arr("atype", atype, tpk::MAX_SUM) +
          ", " + arr("btype", btype, tpk::MAX_SUM) + ", " + arr("mode", mode, tpk::MAX_SUM) + ", " +
          arr("narrow", nar, tpk::MAX_SUM) + ";\n";
-    r += std::string("    static constexpr bool fast = ") + (fast ? "true" : "false") + ";\n};\n";
+    r += std::string("    static constexpr bool fast = ") + (fast ? "true" : "false") +
+         ", lo_only = " + (!fast && lo_only ? "true" : "false") + ";\n};\n";
     return r;
+}
+
+// The source of a dense staged launch's run-time compiled kernel.
+std::string dense_shape(const tpk::QueryDev& q, const tpk::StageLayout& L, bool fast, const int* narrow) {
+    return shape_struct("JS", q, L.sum_mode, fast, false, narrow) + "#include \"jit_dense.cuh\"\n";
 }
 
 // Per-row term range of every sum slot, from column statistics.

@@ -23,7 +23,7 @@
 namespace {
 
 // Embedded sources: {include name, text} pairs, generated by the build from
-// kernels.cuh, device.cuh, pipeline.cuh and jit_dense.cuh.
+// the device headers the run-time compiled kernels include.
 #include "jit_sources.inc"
 
 struct Nvrtc {
@@ -84,8 +84,8 @@ void load_nvrtc() {
     n.loaded = true;
 }
 
-// Compiles `prelude` + the kernel source for this device's architecture and
-// loads it (caller holds g_mu).
+// Compiles `prelude` (shape structs, then the include of the kernel's header)
+// for this device's architecture and loads it (caller holds g_mu).
 Entry build_entry(const std::string& prelude, const char* entry, int device) {
     Entry en;
     int major = 0, minor = 0;
@@ -96,7 +96,7 @@ Entry build_entry(const std::string& prelude, const char* entry, int device) {
         hdr_name.push_back(s.name);
         hdr_text.push_back(s.text);
     }
-    const std::string src = prelude + "#include \"jit_dense.cuh\"\n";
+    const std::string& src = prelude;   // shape structs and the kernel's include
     nvrtcProgram prog = nullptr;
     nvrtcResult r = g_nvrtc.create(&prog, src.c_str(), "tp_jit.cu", (int)hdr_text.size(), hdr_text.data(),
                                    hdr_name.data());

@@ -1,0 +1,298 @@
+// Row evaluation of the run-time compiled kernels, specialised on a plan
+// shape S (a struct of compile-time constants written by the host).
+//
+// Paper basis: Section 3.1 (operators over batches of equal-length columns),
+// Section 3.2 (join), Section 4 (decimals held as 128-bit integers).  A
+// consumer warp evaluates 32 * ST_RPL rows -- lane l takes rows l, l + 32, ...
+// of a row block whose columns are given by pointers (a stage in shared
+// memory, or the columns in device memory) -- through filter -> probe ->
+// group key -> count and sums, accumulating into a dense table of G groups.
+//
+// A shape S provides:
+//   filter, ftype            filter present; its column type (T_*)
+//   join, ktype              J_NONE / J_DIRECT / J_HASH32 / J_HASH64; fk type
+//   part                     partition filter on the join (hybrid join)
+//   ng, gside[], gtype[], gbits[]   group fields, first field highest
+//   ns, skind[], atype[], btype[]   sums: S_SUM / S_MUL_SUB and column types
+//   mode[]                   1: low word, 2: low + carry word (fast), 0: exact
+//   narrow[]                 mode 2 MUL_SUB operands proved to fit in int32
+//   fast                     32-bit dense table (column bounds proved every
+//                            sum stays inside int64); otherwise the table holds
+//                            count[G], lo[s][G], hi[s][G] 64-bit words
+//   lo_only                  (not fast) sums proved to stay inside int64: add
+//                            64-bit terms to the low words only (the high words
+//                            are their sign extension); otherwise exact 128-bit
+// Runtime values (filter bounds, join table, term offsets, multipliers, the
+// table's word layout) come from the launch, so one compiled kernel serves
+// every plan and batch of the same shape.
+#pragma once
+#include "pipeline.cuh"
+
+namespace tpj {
+using namespace tpk;
+
+enum : int { J_NONE = 0, J_DIRECT = 1, J_HASH32 = 2, J_HASH64 = 3 };
+
+template <int T> struct ColT;
+template <> struct ColT<T_I32> { using type = int32_t; using utype = uint32_t; };
+template <> struct ColT<T_I64> { using type = int64_t; using utype = uint64_t; };
+template <> struct ColT<T_U8> { using type = uint8_t; using utype = uint8_t; };
+
+template <int T>
+__device__ __forceinline__ typename ColT<T>::type lds(const unsigned char* col, uint32_t r) {
+    return ((const typename ColT<T>::type*)col)[r];
+}
+
+// Low 32 bits of row r of a column (of an int64 column: its low word).
+template <int T>
+__device__ __forceinline__ uint32_t lds_lo(const unsigned char* col, uint32_t r) {
+    if constexpr (T == T_I64) return ((const uint32_t*)col)[2 * r];
+    else return (uint32_t)lds<T>(col, r);
+}
+
+// The columns of one row block in device memory (row 0 of the block at each
+// pointer).  Row evaluation reads columns through a column source C with
+// f(), k(), g(F), a(I), b(I); StageCols (jit_dense.cuh) is the other one.
+struct Cols {
+    const unsigned char* pf;
+    const unsigned char* pk;
+    const unsigned char* pg[MAX_GROUP];
+    const unsigned char* pa[MAX_SUM];
+    const unsigned char* pb[MAX_SUM];
+    __device__ __forceinline__ const unsigned char* f() const { return pf; }
+    __device__ __forceinline__ const unsigned char* k() const { return pk; }
+    __device__ __forceinline__ const unsigned char* g(int i) const { return pg[i]; }
+    __device__ __forceinline__ const unsigned char* a(int i) const { return pa[i]; }
+    __device__ __forceinline__ const unsigned char* b(int i) const { return pb[i]; }
+};
+
+// Filter bounds, also clamped to int32 for narrow columns (1 > 0 when nothing
+// passes).
+struct Flt {
+    int64_t lo, hi;
+    int32_t lo32, hi32;
+};
+
+__device__ __forceinline__ Flt make_flt(const QueryDev& q) {
+    Flt f;
+    f.lo = q.flo;
+    f.hi = q.fhi;
+    if (q.flo > q.fhi || q.flo > INT32_MAX || q.fhi < INT32_MIN) {
+        f.lo32 = 1;
+        f.hi32 = 0;
+    } else {
+        f.lo32 = (int32_t)(q.flo < INT32_MIN ? (int64_t)INT32_MIN : q.flo);
+        f.hi32 = (int32_t)(q.fhi > INT32_MAX ? (int64_t)INT32_MAX : q.fhi);
+    }
+    return f;
+}
+
+// The dense table rows accumulate into: G groups; fast: 32-bit words, block 0
+// the counts, then per sum its low-word block and, in mode 2, a carry block
+// (sum_word<S, I>), terms offset by sum_off[I]; exact: count[G], lo[s][G],
+// hi[s][G] 64-bit words.
+struct Tab {
+    unsigned char* base;
+    uint32_t G;
+    const int64_t* sum_off;
+};
+
+// Block of sum I's low words in a fast table: 1 + the blocks of sums before it.
+template <class S, int I>
+__device__ __forceinline__ constexpr uint32_t sum_word() {
+    uint32_t w = 1;
+    for (int s = 0; s < I; ++s) w += (uint32_t)S::mode[s];
+    return w;
+}
+
+// Group field F (compile-time recursion over the fields).
+template <class S, int F, class C>
+__device__ __forceinline__ void group_fields(const QueryDev& q, const C& c, uint32_t r0,
+                                             const uint32_t pay[ST_RPL], uint32_t g[ST_RPL], uint32_t& pm) {
+    if constexpr (F < S::ng) {
+        constexpr int bits = S::gbits[F];
+        if constexpr (S::gside[F] == 0) {
+            constexpr int T = S::gtype[F];
+            using U = typename ColT<T>::utype;
+            uint32_t bad = 0;
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) {
+                const U v = (U)lds<T>(c.g(F), r0 + 32 * j);
+                if constexpr (bits < 8 * (int)sizeof(U)) bad |= (uint32_t)((v >> bits) != 0) << j;
+                else if constexpr (T != T_U8) bad |= (uint32_t)((typename ColT<T>::type)v < 0) << j;
+                g[j] = (g[j] << bits) | (uint32_t)v;
+            }
+            if (bad & pm) {
+                atomicOr(q.err, ERR_RANGE);
+                pm &= ~bad;
+            }
+        } else {
+            const uint32_t mask = (bits >= 32) ? ~0u : ((1u << bits) - 1u);
+            const int pos = q.gdpos[F];
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) g[j] = (g[j] << bits) | ((pay[j] >> pos) & mask);
+        }
+        group_fields<S, F + 1, C>(q, c, r0, pay, g, pm);
+    }
+}
+
+// Sum I of the rows in pm (compile-time recursion over the sums).
+template <class S, int I, class C>
+__device__ __forceinline__ void sums(const QueryDev& q, const Tab& t, const C& c, uint32_t r0,
+                                     const uint32_t g[ST_RPL], uint32_t pm) {
+    if constexpr (I < S::ns) {
+        constexpr int TA = S::atype[I];
+        constexpr int TB = S::btype[I];
+        constexpr bool MS = S::skind[I] == S_MUL_SUB;
+        const unsigned char* ca = c.a(I);
+        const unsigned char* cb = MS ? c.b(I) : nullptr;
+        if constexpr (S::fast && S::mode[I] == 1) {
+            // the sums of (term - offset) fit in 32 bits: only the low word of
+            // every term matters, and it is exact mod 2^32
+            uint32_t* lo = (uint32_t*)t.base + (uint64_t)sum_word<S, I>() * t.G;
+            const uint32_t off = (uint32_t)(uint64_t)t.sum_off[I];
+            const uint32_t k = (uint32_t)(uint64_t)q.sk[I];
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) {
+                uint32_t v = lds_lo<TA>(ca, r0 + 32 * j);
+                if constexpr (MS) v *= k - lds_lo<TB>(cb, r0 + 32 * j);
+                if (pm >> j & 1u) atomicAdd(lo + g[j], v - off);
+            }
+        } else if constexpr (S::fast) {
+            uint32_t* lo = (uint32_t*)t.base + (uint64_t)sum_word<S, I>() * t.G;
+            uint32_t* hi = lo + t.G;
+            const int64_t off = t.sum_off[I];
+            const int64_t k = q.sk[I];
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) {
+                int64_t v = (int64_t)lds<TA>(ca, r0 + 32 * j);
+                if constexpr (MS) {
+                    const int64_t d = k - (int64_t)lds<TB>(cb, r0 + 32 * j);
+                    if constexpr (S::narrow[I]) v = (int64_t)(int32_t)v * (int64_t)(int32_t)d;
+                    else v *= d;
+                }
+                const uint64_t w = (uint64_t)(v - off);
+                if (pm >> j & 1u) {
+                    const uint32_t old = atomicAdd(lo + g[j], (uint32_t)w);
+                    const uint32_t h = (uint32_t)(w >> 32) + ((old + (uint32_t)w) < old ? 1u : 0u);
+                    if (h) atomicAdd(hi + g[j], h);
+                }
+            }
+        } else {
+            uint64_t* lo = (uint64_t*)t.base + (uint64_t)t.G * (1 + 2 * I);
+            uint64_t* hi = (uint64_t*)t.base + (uint64_t)t.G * (2 + 2 * I);
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) {
+                if (!(pm >> j & 1u)) continue;
+                const int64_t a = (int64_t)lds<TA>(ca, r0 + 32 * j);
+                if constexpr (S::lo_only) {
+                    int64_t v = a;
+                    if constexpr (MS) v *= q.sk[I] - (int64_t)lds<TB>(cb, r0 + 32 * j);
+                    atomicAdd((unsigned long long*)(lo + g[j]), (unsigned long long)v);
+                } else if constexpr (MS) {
+                    atomic_add_i128(lo + g[j], hi + g[j], mul_sub(a, q.sk[I], (int64_t)lds<TB>(cb, r0 + 32 * j)));
+                } else {
+                    atomic_add_i128(lo + g[j], hi + g[j], i128_from_i64(a));
+                }
+            }
+        }
+        sums<S, I + 1, C>(q, t, c, r0, g, pm);
+    }
+}
+
+// One warp's rows of a block (rows r0 + 32 j whose bit j is set in valid):
+// filter -> probe -> group key -> count and sums.
+template <class S, class C>
+__device__ __forceinline__ void consume(const QueryDev& q, const Flt& flt, const Tab& t, const C& c, uint32_t r0,
+                                        uint32_t valid) {
+    uint32_t pm = valid;
+    if constexpr (S::filter) {
+        pm = 0;
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) {
+            if constexpr (S::ftype == T_I64) {
+                const int64_t v = lds<T_I64>(c.f(), r0 + 32 * j);
+                pm |= (uint32_t)(v >= flt.lo && v <= flt.hi) << j;
+            } else {
+                const int32_t v = (int32_t)lds<S::ftype>(c.f(), r0 + 32 * j);
+                pm |= (uint32_t)(v >= flt.lo32 && v <= flt.hi32) << j;
+            }
+        }
+        pm &= valid;
+        if (!pm) return;
+    }
+    uint32_t pay[ST_RPL];
+#pragma unroll
+    for (int j = 0; j < ST_RPL; ++j) pay[j] = 0;
+    if constexpr (S::join == J_DIRECT) {
+        const unsigned int* dt = (const unsigned int*)q.jt.slots;
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) {
+            const uint64_t idx = (uint64_t)((int64_t)lds<S::ktype>(c.k(), r0 + 32 * j) - q.jt.kmin);
+            pay[j] = ((pm >> j) & 1u) && idx < q.jt.range ? __ldg(dt + idx) : EMPTY32;
+        }
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j)
+            if (pay[j] == EMPTY32) pm &= ~(1u << j);
+    } else if constexpr (S::join == J_HASH32 || S::join == J_HASH64) {
+        int64_t key[ST_RPL];
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) key[j] = (int64_t)lds<S::ktype>(c.k(), r0 + 32 * j);
+        if constexpr (S::part) {
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j)
+                if (!part_resident(q.jt, key[j])) pm &= ~(1u << j);
+        }
+        if constexpr (S::join == J_HASH32) probe_rows_k32(q.jt, key, pm, pay, q.err);
+        else probe_rows_k64(q.jt, key, pm, pay, q.err);
+    }
+    if constexpr (S::join != J_NONE) {
+        uint32_t bad = 0;
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) bad |= (uint32_t)((pay[j] & PAYLOAD_BAD) != 0) << j;
+        if (bad & pm) {
+            atomicOr(q.err, ERR_RANGE);
+            pm &= ~bad;
+        }
+        if (!pm) return;
+    }
+    uint32_t g[ST_RPL];
+#pragma unroll
+    for (int j = 0; j < ST_RPL; ++j) g[j] = 0;
+    group_fields<S, 0, C>(q, c, r0, pay, g, pm);
+    if (!pm) return;
+#pragma unroll
+    for (int j = 0; j < ST_RPL; ++j) {
+        if (!(pm >> j & 1u)) continue;
+        if constexpr (S::fast) atomicAdd((unsigned int*)t.base + g[j], 1u);
+        else atomicAdd((unsigned long long*)t.base + g[j], 1ull);
+    }
+    sums<S, 0, C>(q, t, c, r0, g, pm);
+}
+
+// Column pointers of a block starting at row `row` of the query's columns in
+// device memory (compile-time recursion over the fields and sums).
+template <class S, int F, int I>
+__device__ __forceinline__ void query_cols_rest(const QueryDev& q, uint64_t row, Cols& c) {
+    if constexpr (F < S::ng) {
+        if constexpr (S::gside[F] == 0)
+            c.pg[F] = (const unsigned char*)q.gcol[F].ptr + row * sizeof(typename ColT<S::gtype[F]>::type);
+        query_cols_rest<S, F + 1, I>(q, row, c);
+    } else if constexpr (I < S::ns) {
+        c.pa[I] = (const unsigned char*)q.sa[I].ptr + row * sizeof(typename ColT<S::atype[I]>::type);
+        if constexpr (S::skind[I] == S_MUL_SUB)
+            c.pb[I] = (const unsigned char*)q.sb[I].ptr + row * sizeof(typename ColT<S::btype[I]>::type);
+        query_cols_rest<S, F, I + 1>(q, row, c);
+    }
+}
+
+template <class S>
+__device__ __forceinline__ Cols query_cols(const QueryDev& q, uint64_t row) {
+    Cols c{};
+    if constexpr (S::filter) c.pf = (const unsigned char*)q.fcol.ptr + row * sizeof(typename ColT<S::ftype>::type);
+    if constexpr (S::join != J_NONE) c.pk = (const unsigned char*)q.fk.ptr + row * sizeof(typename ColT<S::ktype>::type);
+    query_cols_rest<S, 0, 0>(q, row, c);
+    return c;
+}
+
+}  // namespace tpj

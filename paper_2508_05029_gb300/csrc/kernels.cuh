@@ -237,7 +237,7 @@ struct BatchQuery {
     int32_t fast;               // 64-bit accumulation proved safe: low words only
     uint32_t build_items;
     uint32_t probe_items;
-    int32_t pad;
+    int32_t shape;              // shape id of the run-time compiled probe task
     int8_t sum_mode[MAX_SUM];   // shared-memory table: 1 low word, 2 low + carry word
     int64_t sum_off[MAX_SUM];   // term offsets making terms non-negative
 };

@@ -228,7 +228,13 @@ void term_bounds(const tp_plan* p, const tp_table* fact, tpk::TermBounds* out);
 // out[s] = 1 for MUL_SUB sum slots whose two factors fit in int32 by the
 // column statistics.
 void narrow_products(const tp_plan* p, const tp_table* fact, int* out);
-// The struct JS source describing a dense staged launch's shape.
+// A plan shape as a struct named `name` of compile-time constants for the
+// run-time compiled kernels; mode[s] is sum s's 32-bit accumulation mode
+// (fast only); lo_only (not fast): 64-bit low-word sums.
+std::string shape_struct(const std::string& name, const tpk::QueryDev& q, const int8_t* mode, bool fast,
+                         bool lo_only, const int* narrow);
+// The source (shape struct JS and the kernel include) of a dense staged
+// launch's run-time compiled kernel.
 std::string dense_shape(const tpk::QueryDev& q, const tpk::StageLayout& L, bool fast, const int* narrow);
 // device memory (stream-ordered allocator on the compute stream)
 tp_status dev_alloc(tp_engine* e, void** p, uint64_t bytes, cudaStream_t st);

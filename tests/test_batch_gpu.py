@@ -44,30 +44,38 @@ def _device_plans(eng, wls, **kw):
     return tabs, plans
 
 
-def test_batch_matches_oracle_and_replays(eng):
+@pytest.mark.parametrize("flags", [0, T.TP_FLAG_NO_JIT])
+def test_batch_matches_oracle_and_replays(flags):
     wls = _mix()
     wls.append(W.config1(n_fact=300_007))                       # 8-bit key: shared-memory tables
     fact, dim = _tiny(3, 5000, 300, 400, signed=True)         # misses, signed values
     wls.append(W.Workload("tiny", fact, dim, W.q_lowcard()))
-    tabs, plans = _device_plans(eng, wls)
-    refs = [oracle.run(wl) for wl in wls]
-    b = T.Batch(eng, plans)
-    for rep in range(2):                                        # graph replay gives the same answers
-        res = b.execute()
-        for wl, ref, r in zip(wls, refs, res):
-            assert_matches_oracle(r, ref, wl.query["aggs"])
-            r.free()
-    assert b.last_ms > 0
-    b.destroy()
-    for p in plans:
-        p.destroy()
-    for t in tabs:
-        t.destroy()
+    eng = T.Engine(page_bytes=8 << 20, n_pages=256, batch_rows=1 << 20, flags=flags)
+    try:
+        tabs, plans = _device_plans(eng, wls)
+        refs = [oracle.run(wl) for wl in wls]
+        b = T.Batch(eng, plans)
+        for rep in range(2):                                        # graph replay gives the same answers
+            res = b.execute()
+            for wl, ref, r in zip(wls, refs, res):
+                assert_matches_oracle(r, ref, wl.query["aggs"])
+                r.free()
+        assert b.last_ms > 0
+        assert (eng.stats()["jit_launches"] > 0) == (flags == 0)
+        b.destroy()
+        for p in plans:
+            p.destroy()
+        for t in tabs:
+            t.destroy()
+    finally:
+        eng.close()
 
 
-def test_batch_exact_and_hash_paths():
-    """Sums that need 128 bits, and hashed (not direct-mapped) join keys."""
-    e = T.Engine(page_bytes=8 << 20, n_pages=64, batch_rows=1 << 20, flags=T.TP_FLAG_NO_DIRECT_JOIN)
+@pytest.mark.parametrize("flags", [0, T.TP_FLAG_NO_JIT])
+def test_batch_exact_and_hash_paths(flags):
+    """Sums that need 128 bits, and hashed (not direct-mapped) join keys; the
+    run-time compiled and the ahead-of-time queue kernels."""
+    e = T.Engine(page_bytes=8 << 20, n_pages=64, batch_rows=1 << 20, flags=T.TP_FLAG_NO_DIRECT_JOIN | flags)
     try:
         n = 20_000
         big = dict(a=np.full(n, (1 << 62) + 7, np.int64), b=np.full(n, -(1 << 62), np.int64),
@@ -78,8 +86,11 @@ def test_batch_exact_and_hash_paths():
         wls = [W.Workload("big", big, dim, qb)] + _mix(4)
         tabs, plans = _device_plans(e, wls)
         b = T.Batch(e, plans)
+        j0 = e.stats()["jit_launches"]
         for wl, r in zip(wls, b.execute()):
             assert_matches_oracle(r, oracle.run(wl), wl.query["aggs"])
+        assert (e.stats()["jit_launches"] > j0) == (flags == 0)
+        assert e.stats()["jit_failures"] == 0
         b.destroy()
         for p in plans:
             p.destroy()

@@ -7,7 +7,7 @@ import os
 import pytest
 
 CSRC = os.path.join(os.path.dirname(__file__), "..", "paper_2508_05029_gb300", "csrc")
-HEADERS = ["kernels.cuh", "device.cuh", "pipeline.cuh", "jit_dense.cuh"]
+HEADERS = ["kernels.cuh", "device.cuh", "pipeline.cuh", "jit_common.cuh", "jit_dense.cuh", "jit_batch.cuh"]
 
 
 def _nvrtc():
@@ -34,7 +34,7 @@ def _shape(filter=1, ftype=0, join=1, ktype=0, part=0, groups=((0, 2, 2), (0, 2,
             f"  static constexpr int ns = {len(sums)};\n"
             f"  static constexpr int {arr('skind', s[0], 8)}, {arr('atype', s[1], 8)}, {arr('btype', s[2], 8)}, "
             f"{arr('mode', s[3], 8)}, {arr('narrow', s[4], 8)};\n"
-            f"  static constexpr bool fast = {'true' if fast else 'false'};\n}};\n")
+            f"  static constexpr bool fast = {'true' if fast else 'false'}, lo_only = false;\n}};\n")
 
 
 SHAPES = {
@@ -50,10 +50,13 @@ SHAPES = {
 
 @pytest.mark.parametrize("name", sorted(SHAPES))
 def test_nvrtc_compiles_shape(name):
-    lib = _nvrtc()
+    _compile(_nvrtc(), SHAPES[name] + '#include "jit_dense.cuh"\n')
+
+
+def _compile(lib, source):
     texts = [open(os.path.join(CSRC, h)).read().encode() for h in HEADERS]
     names = [h.encode() for h in HEADERS]
-    src = (SHAPES[name] + '#include "jit_dense.cuh"\n').encode()
+    src = source.encode()
     prog = ctypes.c_void_p()
     n = len(HEADERS)
     arr_t = ctypes.c_char_p * n
@@ -72,3 +75,17 @@ def test_nvrtc_compiles_shape(name):
     lib.nvrtcDestroyProgram(ctypes.byref(prog))
     assert rc == 0, log.value.decode(errors="replace")[:2000]
     assert cubin.value > 0
+
+
+def test_nvrtc_compiles_batch_kernel():
+    """The batched queue kernel with two shapes (shared-memory 32-bit table;
+    device-memory 64-bit low words) and the dispatcher the host writes."""
+    lib = _nvrtc()
+    a = _shape().replace("struct JS {", "struct JS_0 {")
+    b = _shape(fast=False, join=2, sums=((0, 1, 0, 0, 0), (1, 1, 1, 0, 0))).replace("struct JS {", "struct JS_1 {")
+    b = b.replace("lo_only = false", "lo_only = true")
+    disp = ("__device__ void tpj::dispatch_probe(const tpk::BatchQuery& B, uint64_t r0, uint64_t r1, "
+            "unsigned char* smem) {\n    switch (B.shape) {\n"
+            "    case 0: probe_tile<JS_0>(B, r0, r1, smem); break;\n"
+            "    case 1: probe_tile<JS_1>(B, r0, r1, smem); break;\n    default: break;\n    }\n}\n")
+    _compile(lib, a + b + '#include "jit_batch.cuh"\n' + disp)
