@@ -216,6 +216,9 @@ tp_status build_join(ExecState& S, Scratch& sc) {
 
 // Runs `kernel(q, rows, colptr)` over every batch of the fact table; colptr[c]
 // is the device address of column c in the batch (nullptr when unused).
+// Consecutive batches smaller than the table's batch size (a spilled
+// partition gets one per fact batch that spilled into it) are copied into one
+// staging slot and run as one, up to that size.
 template <class F>
 tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
     tp_engine* e = S.e;
@@ -230,8 +233,18 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
         return kernel(q, t->rows, colptr);
     }
     if (t->batches.empty()) return TP_OK;
+    // groups of consecutive batches [first, last) of at most `merge` rows
+    const uint64_t merge = std::max<uint64_t>(t->batch_rows, 1);
+    std::vector<std::pair<size_t, size_t>> groups;
     uint64_t max_rows = 0;
-    for (auto& b : t->batches) max_rows = std::max(max_rows, b.rows);
+    for (size_t i = 0; i < t->batches.size();) {
+        size_t j = i;
+        uint64_t rows = 0;
+        while (j < t->batches.size() && (j == i || rows + t->batches[j].rows <= merge)) rows += t->batches[j++].rows;
+        groups.emplace_back(i, j);
+        max_rows = std::max(max_rows, rows);
+        i = j;
+    }
     const bool prefetch = e->cfg.prefetch_depth > 0;
     const int n_slots = prefetch ? e->cfg.prefetch_depth + 1 : 1;
     // staging slots: every used column of one batch
@@ -252,29 +265,41 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
         cudaStreamWaitEvent(S.lane->copy, freed[0], 0);
     }
     cudaStream_t cs = prefetch ? S.lane->copy : S.lane->compute;
-    for (size_t bi = 0; bi < t->batches.size() && rc == TP_OK; ++bi) {
-        const Batch& b = t->batches[bi];
-        const int s = (int)(bi % n_slots);
-        if (prefetch && bi >= (size_t)n_slots) cudaStreamWaitEvent(S.lane->copy, freed[s], 0);
+    std::vector<std::vector<const void*>> gptr(n_slots, std::vector<const void*>(nc, nullptr));
+    // copies of group g into slot g % n_slots (after the kernel that last used it)
+    auto issue = [&](size_t g) -> tp_status {
+        const int s = (int)(g % n_slots);
+        if (prefetch && g >= (size_t)n_slots) cudaStreamWaitEvent(S.lane->copy, freed[s], 0);
         for (int c : S.used) {
             uint8_t* dst = (uint8_t*)slot[s][c];
-            for (const Extent& x : b.cols[c]) {
-                rc = cuda_check(cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes,
-                                                cudaMemcpyHostToDevice, cs), "batch copy");
-                if (rc) break;
-                dst += x.bytes;
-                e->h2d_bytes += x.bytes;
+            for (size_t bi = groups[g].first; bi < groups[g].second; ++bi) {
+                for (const Extent& x : t->batches[bi].cols[c]) {
+                    tp_status r = cuda_check(cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset,
+                                                             x.bytes, cudaMemcpyHostToDevice, cs), "batch copy");
+                    if (r) return r;
+                    dst += x.bytes;
+                    e->h2d_bytes += x.bytes;
+                }
             }
-            if (rc) break;
-            colptr[c] = slot[s][c];
+            gptr[s][c] = slot[s][c];
         }
-        if (rc) break;
-        if (prefetch) {
-            cudaEventRecord(loaded[s], S.lane->copy);
-            cudaStreamWaitEvent(S.lane->compute, loaded[s], 0);
-        }
+        if (prefetch) cudaEventRecord(loaded[s], S.lane->copy);
+        return TP_OK;
+    };
+    // the copy stream runs prefetch_depth groups ahead of the kernels, even
+    // while the host waits inside a kernel callback
+    const size_t ahead = prefetch ? (size_t)e->cfg.prefetch_depth : 0;
+    for (size_t g = 0; g < std::min(ahead, groups.size()) && rc == TP_OK; ++g) rc = issue(g);
+    for (size_t g = 0; g < groups.size() && rc == TP_OK; ++g) {
+        const int s = (int)(g % n_slots);
+        if (g + ahead < groups.size() && (rc = issue(g + ahead))) break;
+        if (!prefetch && (rc = issue(g))) break;
+        uint64_t rows = 0;
+        for (size_t bi = groups[g].first; bi < groups[g].second; ++bi) rows += t->batches[bi].rows;
+        if (prefetch) cudaStreamWaitEvent(S.lane->compute, loaded[s], 0);
+        for (int c : S.used) colptr[c] = gptr[s][c];
         tpk::QueryDev q = make_query(S, colptr);
-        rc = kernel(q, b.rows, colptr);
+        rc = kernel(q, rows, colptr);
         e->batches++;
         if (prefetch) cudaEventRecord(freed[s], S.lane->compute);
     }
@@ -725,7 +750,7 @@ tp_status part_phase2(ExecState& S, Scratch& sc, PartJoin& pj, float lf, F&& agg
     for (int p = 0; p < pj.P; ++p) {
         if (!((pj.spill_mask >> p) & 1ull)) continue;
         max_cap = std::max(max_cap, pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(pj.dim_count[p] / lf))));
-        for (auto& bt : pj.build_spill[p]->batches) max_rows = std::max(max_rows, bt.rows);
+        max_rows = std::max<uint64_t>(max_rows, pj.build_spill[p]->rows);   // a partition's pairs in one launch
     }
     if (max_cap * slot > pj.table_budget - std::min(pj.table_budget, pj.resident_bytes))
         return fail(TP_E_BUDGET, "a spilled join partition needs a %llu-byte table, over the %llu-byte budget; "
@@ -750,21 +775,21 @@ tp_status part_phase2(ExecState& S, Scratch& sc, PartJoin& pj, float lf, F&& agg
         jt.side = (uint32_t*)side;
         jt.part_shift = 0;
         jt.part_mask = 0;
+        // every spilled build batch of the partition back to back, then one insert launch
+        uint8_t* o[2] = {(uint8_t*)keys, (uint8_t*)pays};
         for (auto& bt : pj.build_spill[p]->batches) {
-            void* dst[2] = {keys, pays};
             for (int c = 0; c < 2; ++c) {
-                uint8_t* o = (uint8_t*)dst[c];
                 for (const Extent& x : bt.cols[c]) {
-                    TP_TRY_CUDA(cudaMemcpyAsync(o, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes,
+                    TP_TRY_CUDA(cudaMemcpyAsync(o[c], (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes,
                                                 cudaMemcpyHostToDevice, st));
-                    o += x.bytes;
+                    o[c] += x.bytes;
                     e->h2d_bytes += x.bytes;
                 }
             }
-            mark_launch(e);
-            TP_TRY_CUDA(tpk::launch_build_pairs(jt, (const int64_t*)keys, (const uint32_t*)pays, bt.rows, S.err,
-                                                e->num_sms, st));
         }
+        mark_launch(e);
+        TP_TRY_CUDA(tpk::launch_build_pairs(jt, (const int64_t*)keys, (const uint32_t*)pays, pj.build_spill[p]->rows,
+                                            S.err, e->num_sms, st));
         S.fact = pj.fact_spill[p];
         S.jt = jt;
         s = for_each_batch(S, sc, agg);

@@ -73,26 +73,60 @@ cudaError_t launch_part_hist_fact(const QueryDev& q, uint64_t n, int shift, uint
     return cudaGetLastError();
 }
 
+// Scatter kernels place rows of spilled partitions with one global cursor
+// atomic per (tile, partition): a tile of SP_TILE rows counts its rows per
+// partition in shared memory, reserves each partition's range at once, and
+// every row takes its rank inside its partition's range, so the rows of a
+// partition from one tile land next to each other.
+constexpr int SP_THREADS = 512;
+constexpr int SP_RPT = 4;                          // rows per thread per tile
+constexpr int SP_TILE = SP_THREADS * SP_RPT;
+
 // Build rows: insert the resident partitions, spill the others as pairs.
-__global__ void k_build_part(const __grid_constant__ BuildDev b, uint64_t n, const unsigned long long* base,
-                             unsigned long long* cursor, int64_t* keys, uint32_t* pays) {
+__global__ void __launch_bounds__(SP_THREADS)
+    k_build_part(const __grid_constant__ BuildDev b, uint64_t n, const unsigned long long* base,
+                 unsigned long long* cursor, int64_t* keys, uint32_t* pays) {
+    __shared__ unsigned cnt[64];
+    __shared__ unsigned long long at0[64];
     const JoinTable& jt = b.jt;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const int64_t key = ld1(b.key, i);
-        const uint32_t p = part_of(key, jt.part_shift);
-        if ((jt.part_mask >> p) & 1ull) {
-            build_insert(b, i);
-            continue;
+    for (uint64_t t0 = (uint64_t)blockIdx.x * SP_TILE; t0 < n; t0 += (uint64_t)gridDim.x * SP_TILE) {
+        if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        uint32_t part[SP_RPT], rank[SP_RPT];
+        bool spill[SP_RPT];
+#pragma unroll
+        for (int k = 0; k < SP_RPT; ++k) {
+            const uint64_t i = t0 + (uint64_t)k * SP_THREADS + threadIdx.x;
+            spill[k] = false;
+            if (i >= n) continue;
+            const int64_t key = ld1(b.key, i);
+            part[k] = part_of(key, jt.part_shift);
+            if ((jt.part_mask >> part[k]) & 1ull) {
+                build_insert(b, i);
+            } else {
+                spill[k] = true;
+                rank[k] = atomicAdd(&cnt[part[k]], 1u);
+            }
         }
-        uint32_t payload = 0;
-        for (int f = 0; f < b.n_dfield; ++f) {
-            const int64_t v = ld1(b.dcol[f], i);
-            if (v < 0 || ((uint64_t)v >> b.dbits[f]) != 0) payload |= PAYLOAD_BAD;
-            else payload |= (uint32_t)((uint64_t)v << b.dpos[f]);
+        __syncthreads();
+        if (threadIdx.x < 64 && cnt[threadIdx.x])
+            at0[threadIdx.x] = base[threadIdx.x] + atomicAdd(&cursor[threadIdx.x], (unsigned long long)cnt[threadIdx.x]);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SP_RPT; ++k) {
+            if (!spill[k]) continue;
+            const uint64_t i = t0 + (uint64_t)k * SP_THREADS + threadIdx.x;
+            uint32_t payload = 0;
+            for (int f = 0; f < b.n_dfield; ++f) {
+                const int64_t v = ld1(b.dcol[f], i);
+                if (v < 0 || ((uint64_t)v >> b.dbits[f]) != 0) payload |= PAYLOAD_BAD;
+                else payload |= (uint32_t)((uint64_t)v << b.dpos[f]);
+            }
+            const uint64_t at = at0[part[k]] + rank[k];
+            keys[at] = ld1(b.key, i);
+            pays[at] = payload;
         }
-        const uint64_t at = base[p] + atomicAdd(&cursor[p], 1ull);
-        keys[at] = key;
-        pays[at] = payload;
+        __syncthreads();
     }
 }
 
@@ -100,9 +134,9 @@ cudaError_t launch_build_part(const BuildDev& b, uint64_t n, const unsigned long
                               unsigned long long* cursor, int64_t* keys, uint32_t* pays, int num_sms,
                               cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    uint64_t blocks = (n + 255) / 256;
-    if (blocks > (uint64_t)num_sms * 8) blocks = (uint64_t)num_sms * 8;
-    k_build_part<<<(unsigned)blocks, 256, 0, st>>>(b, n, base, cursor, keys, pays);
+    uint64_t blocks = (n + SP_TILE - 1) / SP_TILE;
+    if (blocks > (uint64_t)num_sms * 4) blocks = (uint64_t)num_sms * 4;
+    k_build_part<<<(unsigned)blocks, SP_THREADS, 0, st>>>(b, n, base, cursor, keys, pays);
     return cudaGetLastError();
 }
 
@@ -161,23 +195,46 @@ cudaError_t launch_build_pairs(const JoinTable& jt, const int64_t* keys, const u
 }
 
 // Fact rows of spilled partitions: copy every requested column to its
-// partition's run in the staging columns.
-__global__ void k_fact_spill(const __grid_constant__ QueryDev q, uint64_t n, uint64_t spill_mask,
-                             const __grid_constant__ SpillCols cols, const unsigned long long* base,
-                             unsigned long long* cursor) {
+// partition's run in the staging columns (tile-aggregated cursors, as above).
+__global__ void __launch_bounds__(SP_THREADS)
+    k_fact_spill(const __grid_constant__ QueryDev q, uint64_t n, uint64_t spill_mask,
+                 const __grid_constant__ SpillCols cols, const unsigned long long* base, unsigned long long* cursor) {
+    __shared__ unsigned cnt[64];
+    __shared__ unsigned long long at0[64];
     const int shift = q.jt.part_shift;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        if (!fact_row_passes(q, i)) continue;
-        const uint32_t p = part_of(ld1(q.fk, i), shift);
-        if (!((spill_mask >> p) & 1ull)) continue;
-        const uint64_t at = base[p] + atomicAdd(&cursor[p], 1ull);
-        for (int c = 0; c < cols.n; ++c) {
-            switch (cols.esize[c]) {
-            case 8: ((int64_t*)cols.dst[c])[at] = ((const int64_t*)cols.src[c])[i]; break;
-            case 4: ((int32_t*)cols.dst[c])[at] = ((const int32_t*)cols.src[c])[i]; break;
-            default: ((uint8_t*)cols.dst[c])[at] = ((const uint8_t*)cols.src[c])[i]; break;
+    for (uint64_t t0 = (uint64_t)blockIdx.x * SP_TILE; t0 < n; t0 += (uint64_t)gridDim.x * SP_TILE) {
+        if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        uint32_t part[SP_RPT], rank[SP_RPT];
+        bool spill[SP_RPT];
+#pragma unroll
+        for (int k = 0; k < SP_RPT; ++k) {
+            const uint64_t i = t0 + (uint64_t)k * SP_THREADS + threadIdx.x;
+            spill[k] = false;
+            if (i >= n || !fact_row_passes(q, i)) continue;
+            part[k] = part_of(ld1(q.fk, i), shift);
+            if (!((spill_mask >> part[k]) & 1ull)) continue;
+            spill[k] = true;
+            rank[k] = atomicAdd(&cnt[part[k]], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 64 && cnt[threadIdx.x])
+            at0[threadIdx.x] = base[threadIdx.x] + atomicAdd(&cursor[threadIdx.x], (unsigned long long)cnt[threadIdx.x]);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < SP_RPT; ++k) {
+            if (!spill[k]) continue;
+            const uint64_t i = t0 + (uint64_t)k * SP_THREADS + threadIdx.x;
+            const uint64_t at = at0[part[k]] + rank[k];
+            for (int c = 0; c < cols.n; ++c) {
+                switch (cols.esize[c]) {
+                case 8: ((int64_t*)cols.dst[c])[at] = ((const int64_t*)cols.src[c])[i]; break;
+                case 4: ((int32_t*)cols.dst[c])[at] = ((const int32_t*)cols.src[c])[i]; break;
+                default: ((uint8_t*)cols.dst[c])[at] = ((const uint8_t*)cols.src[c])[i]; break;
+                }
             }
         }
+        __syncthreads();
     }
 }
 
@@ -185,9 +242,9 @@ cudaError_t launch_fact_spill(const QueryDev& q, uint64_t n, uint64_t spill_mask
                               const unsigned long long* base, unsigned long long* cursor, int num_sms,
                               cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    uint64_t blocks = (n + 255) / 256;
-    if (blocks > (uint64_t)num_sms * 8) blocks = (uint64_t)num_sms * 8;
-    k_fact_spill<<<(unsigned)blocks, 256, 0, st>>>(q, n, spill_mask, cols, base, cursor);
+    uint64_t blocks = (n + SP_TILE - 1) / SP_TILE;
+    if (blocks > (uint64_t)num_sms * 4) blocks = (uint64_t)num_sms * 4;
+    k_fact_spill<<<(unsigned)blocks, SP_THREADS, 0, st>>>(q, n, spill_mask, cols, base, cursor);
     return cudaGetLastError();
 }
 
