@@ -8,7 +8,7 @@
 // carries a shape id, and the task runs the row evaluation compiled for that
 // shape (jit_common.cuh), reading the query's columns in device memory
 // directly (lane l of a warp takes rows l and l + 32 of each 64-row block, so
-// every load is coalesced).
+// every load is coalesced), every column of a block loaded up front.
 //
 // The host prepends the shape structs JS_0, JS_1, ... and appends the
 // definition of dispatch_probe: a switch on the shape id calling
@@ -45,6 +45,22 @@ __device__ __forceinline__ bool wait_count(unsigned* ctr, unsigned want, uint64_
     return *flag != 0;
 }
 
+// Adds sum I (and the following ones) of group gi of a fast shared-memory
+// table to the query's accumulators: carry words * 2^32 + low words + count *
+// offset.
+template <class S, int I>
+__device__ __forceinline__ void flush_sums(const BatchQuery& B, const uint32_t* cnt, uint32_t G, uint32_t gi,
+                                           uint64_t c) {
+    if constexpr (I < S::ns) {
+        const uint32_t* w = cnt + (uint64_t)sum_word<S, I>() * G;
+        uint64_t v = w[gi];
+        if constexpr (S::mode[I] == 2) v += (uint64_t)w[G + gi] << 32;
+        v += c * (uint64_t)B.sum_off[I];
+        atomicAdd((unsigned long long*)&B.acc[(uint64_t)G * (1 + 2 * I) + gi], (unsigned long long)v);
+        flush_sums<S, I + 1>(B, cnt, G, gi, c);
+    }
+}
+
 // Probe tile [r0, r1) of query B with shape S.  fast shapes accumulate into a
 // 32-bit table in shared memory (the layout of the ahead-of-time kernel:
 // counts, then per sum its mode's blocks) folded into B.acc at the end; the
@@ -73,7 +89,10 @@ __device__ __forceinline__ void probe_tile(const BatchQuery& B, uint64_t r0, uin
         uint32_t valid = 0;
 #pragma unroll
         for (int j = 0; j < ST_RPL; ++j) valid |= (uint32_t)((uint64_t)lane + 32 * j < left) << j;
-        consume<S>(q, flt, t, query_cols<S>(q, base), (uint32_t)lane, valid);
+        // all of the shape's columns for these rows in flight at once
+        Eager<S> ev;
+        ev.template fill<0>(query_cols<S>(q, base), (uint32_t)lane, valid);
+        consume<S>(q, flt, t, ev, (uint32_t)lane, valid);
     }
     if constexpr (S::fast) {
         __syncthreads();
@@ -82,15 +101,7 @@ __device__ __forceinline__ void probe_tile(const BatchQuery& B, uint64_t r0, uin
             const uint64_t c = cnt[gi];
             if (!c) continue;
             atomicAdd((unsigned long long*)&B.acc[gi], (unsigned long long)c);
-            for (int s = 0; s < S::ns; ++s) {
-                uint32_t blk = 1;
-                for (int u = 0; u < s; ++u) blk += (uint32_t)S::mode[u];
-                const uint32_t* w = cnt + (uint64_t)blk * G;
-                uint64_t v = w[gi];
-                if (S::mode[s] == 2) v += (uint64_t)w[G + gi] << 32;
-                v += c * (uint64_t)B.sum_off[s];
-                atomicAdd((unsigned long long*)&B.acc[(uint64_t)G * (1 + 2 * s) + gi], (unsigned long long)v);
-            }
+            flush_sums<S, 0>(B, cnt, G, gi, c);
         }
     }
 }

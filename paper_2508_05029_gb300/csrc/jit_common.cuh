@@ -50,20 +50,26 @@ __device__ __forceinline__ uint32_t lds_lo(const unsigned char* col, uint32_t r)
     else return (uint32_t)lds<T>(col, r);
 }
 
-// The columns of one row block in device memory (row 0 of the block at each
-// pointer).  Row evaluation reads columns through a column source C with
-// f(), k(), g(F), a(I), b(I); StageCols (jit_dense.cuh) is the other one.
+// Column ids of a shape's columns: filter, join key, fact group field F,
+// sum I's first and second operand.
+enum : int { CI_F = 0, CI_K = 1, CI_G = 2, CI_A = 2 + MAX_GROUP, CI_B = 2 + MAX_GROUP + MAX_SUM,
+             CI_N = 2 + MAX_GROUP + 2 * MAX_SUM };
+
+// Row evaluation reads column CI's value of row r0 + 32 j through a column
+// source: ld<T, CI>(r0, j) (typed) and ld_lo<T, CI>(r0, j) (low 32 bits).
+// Cols: the columns in device memory at a row block (row 0 of the block at
+// each pointer); StageCols (jit_dense.cuh): a stage in shared memory;
+// Eager: every column of the shape loaded into registers up front.
 struct Cols {
-    const unsigned char* pf;
-    const unsigned char* pk;
-    const unsigned char* pg[MAX_GROUP];
-    const unsigned char* pa[MAX_SUM];
-    const unsigned char* pb[MAX_SUM];
-    __device__ __forceinline__ const unsigned char* f() const { return pf; }
-    __device__ __forceinline__ const unsigned char* k() const { return pk; }
-    __device__ __forceinline__ const unsigned char* g(int i) const { return pg[i]; }
-    __device__ __forceinline__ const unsigned char* a(int i) const { return pa[i]; }
-    __device__ __forceinline__ const unsigned char* b(int i) const { return pb[i]; }
+    const unsigned char* p[CI_N];
+    template <int T, int CI>
+    __device__ __forceinline__ typename ColT<T>::type ld(uint32_t r0, int j) const {
+        return lds<T>(p[CI], r0 + 32 * j);
+    }
+    template <int T, int CI>
+    __device__ __forceinline__ uint32_t ld_lo(uint32_t r0, int j) const {
+        return lds_lo<T>(p[CI], r0 + 32 * j);
+    }
 };
 
 // Filter bounds, also clamped to int32 for narrow columns (1 > 0 when nothing
@@ -117,7 +123,7 @@ __device__ __forceinline__ void group_fields(const QueryDev& q, const C& c, uint
             uint32_t bad = 0;
 #pragma unroll
             for (int j = 0; j < ST_RPL; ++j) {
-                const U v = (U)lds<T>(c.g(F), r0 + 32 * j);
+                const U v = (U)c.template ld<T, CI_G + F>(r0, j);
                 if constexpr (bits < 8 * (int)sizeof(U)) bad |= (uint32_t)((v >> bits) != 0) << j;
                 else if constexpr (T != T_U8) bad |= (uint32_t)((typename ColT<T>::type)v < 0) << j;
                 g[j] = (g[j] << bits) | (uint32_t)v;
@@ -144,8 +150,6 @@ __device__ __forceinline__ void sums(const QueryDev& q, const Tab& t, const C& c
         constexpr int TA = S::atype[I];
         constexpr int TB = S::btype[I];
         constexpr bool MS = S::skind[I] == S_MUL_SUB;
-        const unsigned char* ca = c.a(I);
-        const unsigned char* cb = MS ? c.b(I) : nullptr;
         if constexpr (S::fast && S::mode[I] == 1) {
             // the sums of (term - offset) fit in 32 bits: only the low word of
             // every term matters, and it is exact mod 2^32
@@ -154,8 +158,8 @@ __device__ __forceinline__ void sums(const QueryDev& q, const Tab& t, const C& c
             const uint32_t k = (uint32_t)(uint64_t)q.sk[I];
 #pragma unroll
             for (int j = 0; j < ST_RPL; ++j) {
-                uint32_t v = lds_lo<TA>(ca, r0 + 32 * j);
-                if constexpr (MS) v *= k - lds_lo<TB>(cb, r0 + 32 * j);
+                uint32_t v = c.template ld_lo<TA, CI_A + I>(r0, j);
+                if constexpr (MS) v *= k - c.template ld_lo<TB, CI_B + I>(r0, j);
                 if (pm >> j & 1u) atomicAdd(lo + g[j], v - off);
             }
         } else if constexpr (S::fast) {
@@ -165,9 +169,9 @@ __device__ __forceinline__ void sums(const QueryDev& q, const Tab& t, const C& c
             const int64_t k = q.sk[I];
 #pragma unroll
             for (int j = 0; j < ST_RPL; ++j) {
-                int64_t v = (int64_t)lds<TA>(ca, r0 + 32 * j);
+                int64_t v = (int64_t)c.template ld<TA, CI_A + I>(r0, j);
                 if constexpr (MS) {
-                    const int64_t d = k - (int64_t)lds<TB>(cb, r0 + 32 * j);
+                    const int64_t d = k - (int64_t)c.template ld<TB, CI_B + I>(r0, j);
                     if constexpr (S::narrow[I]) v = (int64_t)(int32_t)v * (int64_t)(int32_t)d;
                     else v *= d;
                 }
@@ -184,13 +188,14 @@ __device__ __forceinline__ void sums(const QueryDev& q, const Tab& t, const C& c
 #pragma unroll
             for (int j = 0; j < ST_RPL; ++j) {
                 if (!(pm >> j & 1u)) continue;
-                const int64_t a = (int64_t)lds<TA>(ca, r0 + 32 * j);
+                const int64_t a = (int64_t)c.template ld<TA, CI_A + I>(r0, j);
                 if constexpr (S::lo_only) {
                     int64_t v = a;
-                    if constexpr (MS) v *= q.sk[I] - (int64_t)lds<TB>(cb, r0 + 32 * j);
+                    if constexpr (MS) v *= q.sk[I] - (int64_t)c.template ld<TB, CI_B + I>(r0, j);
                     atomicAdd((unsigned long long*)(lo + g[j]), (unsigned long long)v);
                 } else if constexpr (MS) {
-                    atomic_add_i128(lo + g[j], hi + g[j], mul_sub(a, q.sk[I], (int64_t)lds<TB>(cb, r0 + 32 * j)));
+                    atomic_add_i128(lo + g[j], hi + g[j],
+                                    mul_sub(a, q.sk[I], (int64_t)c.template ld<TB, CI_B + I>(r0, j)));
                 } else {
                     atomic_add_i128(lo + g[j], hi + g[j], i128_from_i64(a));
                 }
@@ -211,10 +216,10 @@ __device__ __forceinline__ void consume(const QueryDev& q, const Flt& flt, const
 #pragma unroll
         for (int j = 0; j < ST_RPL; ++j) {
             if constexpr (S::ftype == T_I64) {
-                const int64_t v = lds<T_I64>(c.f(), r0 + 32 * j);
+                const int64_t v = c.template ld<T_I64, CI_F>(r0, j);
                 pm |= (uint32_t)(v >= flt.lo && v <= flt.hi) << j;
             } else {
-                const int32_t v = (int32_t)lds<S::ftype>(c.f(), r0 + 32 * j);
+                const int32_t v = (int32_t)c.template ld<S::ftype, CI_F>(r0, j);
                 pm |= (uint32_t)(v >= flt.lo32 && v <= flt.hi32) << j;
             }
         }
@@ -228,7 +233,7 @@ __device__ __forceinline__ void consume(const QueryDev& q, const Flt& flt, const
         const unsigned int* dt = (const unsigned int*)q.jt.slots;
 #pragma unroll
         for (int j = 0; j < ST_RPL; ++j) {
-            const uint64_t idx = (uint64_t)((int64_t)lds<S::ktype>(c.k(), r0 + 32 * j) - q.jt.kmin);
+            const uint64_t idx = (uint64_t)((int64_t)c.template ld<S::ktype, CI_K>(r0, j) - q.jt.kmin);
             pay[j] = ((pm >> j) & 1u) && idx < q.jt.range ? __ldg(dt + idx) : EMPTY32;
         }
 #pragma unroll
@@ -237,7 +242,7 @@ __device__ __forceinline__ void consume(const QueryDev& q, const Flt& flt, const
     } else if constexpr (S::join == J_HASH32 || S::join == J_HASH64) {
         int64_t key[ST_RPL];
 #pragma unroll
-        for (int j = 0; j < ST_RPL; ++j) key[j] = (int64_t)lds<S::ktype>(c.k(), r0 + 32 * j);
+        for (int j = 0; j < ST_RPL; ++j) key[j] = (int64_t)c.template ld<S::ktype, CI_K>(r0, j);
         if constexpr (S::part) {
 #pragma unroll
             for (int j = 0; j < ST_RPL; ++j)
@@ -276,12 +281,12 @@ template <class S, int F, int I>
 __device__ __forceinline__ void query_cols_rest(const QueryDev& q, uint64_t row, Cols& c) {
     if constexpr (F < S::ng) {
         if constexpr (S::gside[F] == 0)
-            c.pg[F] = (const unsigned char*)q.gcol[F].ptr + row * sizeof(typename ColT<S::gtype[F]>::type);
+            c.p[CI_G + F] = (const unsigned char*)q.gcol[F].ptr + row * sizeof(typename ColT<S::gtype[F]>::type);
         query_cols_rest<S, F + 1, I>(q, row, c);
     } else if constexpr (I < S::ns) {
-        c.pa[I] = (const unsigned char*)q.sa[I].ptr + row * sizeof(typename ColT<S::atype[I]>::type);
+        c.p[CI_A + I] = (const unsigned char*)q.sa[I].ptr + row * sizeof(typename ColT<S::atype[I]>::type);
         if constexpr (S::skind[I] == S_MUL_SUB)
-            c.pb[I] = (const unsigned char*)q.sb[I].ptr + row * sizeof(typename ColT<S::btype[I]>::type);
+            c.p[CI_B + I] = (const unsigned char*)q.sb[I].ptr + row * sizeof(typename ColT<S::btype[I]>::type);
         query_cols_rest<S, F, I + 1>(q, row, c);
     }
 }
@@ -289,10 +294,54 @@ __device__ __forceinline__ void query_cols_rest(const QueryDev& q, uint64_t row,
 template <class S>
 __device__ __forceinline__ Cols query_cols(const QueryDev& q, uint64_t row) {
     Cols c{};
-    if constexpr (S::filter) c.pf = (const unsigned char*)q.fcol.ptr + row * sizeof(typename ColT<S::ftype>::type);
-    if constexpr (S::join != J_NONE) c.pk = (const unsigned char*)q.fk.ptr + row * sizeof(typename ColT<S::ktype>::type);
+    if constexpr (S::filter) c.p[CI_F] = (const unsigned char*)q.fcol.ptr + row * sizeof(typename ColT<S::ftype>::type);
+    if constexpr (S::join != J_NONE)
+        c.p[CI_K] = (const unsigned char*)q.fk.ptr + row * sizeof(typename ColT<S::ktype>::type);
     query_cols_rest<S, 0, 0>(q, row, c);
     return c;
 }
 
+// Every column of shape S for this lane's rows r0 + 32 j (bit j of valid),
+// loaded from a column source into registers at once: with columns in device
+// memory the loads of all columns overlap instead of following the filter,
+// probe and group-key dependencies one by one.
+template <class S, int CI>
+struct ColType {   // element type of column CI in shape S (T_I64 for columns the shape does not read)
+    static constexpr int t = CI == CI_F ? (S::filter ? S::ftype : T_I64)
+                           : CI == CI_K ? (S::join != J_NONE ? S::ktype : T_I64)
+                           : CI < CI_A ? (CI - CI_G < S::ng && S::gside[CI - CI_G] == 0 ? S::gtype[CI - CI_G] : T_I64)
+                           : CI < CI_B ? (CI - CI_A < S::ns ? S::atype[CI - CI_A] : T_I64)
+                           : (CI - CI_B < S::ns && S::skind[CI - CI_B] == S_MUL_SUB ? S::btype[CI - CI_B] : T_I64);
+    static constexpr bool used = CI == CI_F ? (bool)S::filter
+                               : CI == CI_K ? S::join != J_NONE
+                               : CI < CI_A ? (CI - CI_G < S::ng && S::gside[CI - CI_G] == 0)
+                               : CI < CI_B ? (CI - CI_A < S::ns)
+                               : (CI - CI_B < S::ns && S::skind[CI - CI_B] == S_MUL_SUB);
+};
+
+template <class S>
+struct Eager {
+    uint64_t v[CI_N][ST_RPL];
+    template <int CI, class C>
+    __device__ __forceinline__ void fill(const C& c, uint32_t r0, uint32_t valid) {
+        if constexpr (CI < CI_N) {
+            if constexpr (ColType<S, CI>::used) {
+#pragma unroll
+                for (int j = 0; j < ST_RPL; ++j)
+                    v[CI][j] = (valid >> j & 1u) ? (uint64_t)(int64_t)c.template ld<ColType<S, CI>::t, CI>(r0, j) : 0;
+            }
+            fill<CI + 1>(c, r0, valid);
+        }
+    }
+    template <int T, int CI>
+    __device__ __forceinline__ typename ColT<T>::type ld(uint32_t, int j) const {
+        return (typename ColT<T>::type)v[CI][j];
+    }
+    template <int T, int CI>
+    __device__ __forceinline__ uint32_t ld_lo(uint32_t, int j) const {
+        return (uint32_t)v[CI][j];
+    }
+};
+
 }  // namespace tpj
+

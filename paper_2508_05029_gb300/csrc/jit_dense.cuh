@@ -22,21 +22,19 @@
 
 namespace tpj {
 
-// Byte offsets of the shape's columns inside a stage.
+// Byte offsets of the shape's columns inside a stage, by column id.
 struct StageOffs {
-    uint32_t f, k;
-    uint32_t g[MAX_GROUP];
-    uint32_t a[MAX_SUM], b[MAX_SUM];
+    uint32_t off[CI_N];
 };
 
 template <class S, int F, int I>
 __device__ __forceinline__ void stage_offsets(const StageLayout& L, StageOffs& o) {
     if constexpr (F < S::ng) {
-        if constexpr (S::gside[F] == 0) o.g[F] = L.off[L.col_of_slot[SL_GROUP + F]];
+        if constexpr (S::gside[F] == 0) o.off[CI_G + F] = L.off[L.col_of_slot[SL_GROUP + F]];
         stage_offsets<S, F + 1, I>(L, o);
     } else if constexpr (I < S::ns) {
-        o.a[I] = L.off[L.col_of_slot[SL_SA + I]];
-        if constexpr (S::skind[I] == S_MUL_SUB) o.b[I] = L.off[L.col_of_slot[SL_SB + I]];
+        o.off[CI_A + I] = L.off[L.col_of_slot[SL_SA + I]];
+        if constexpr (S::skind[I] == S_MUL_SUB) o.off[CI_B + I] = L.off[L.col_of_slot[SL_SB + I]];
         stage_offsets<S, F, I + 1>(L, o);
     }
 }
@@ -45,11 +43,14 @@ __device__ __forceinline__ void stage_offsets(const StageLayout& L, StageOffs& o
 struct StageCols {
     const unsigned char* s;
     const StageOffs* o;
-    __device__ __forceinline__ const unsigned char* f() const { return s + o->f; }
-    __device__ __forceinline__ const unsigned char* k() const { return s + o->k; }
-    __device__ __forceinline__ const unsigned char* g(int i) const { return s + o->g[i]; }
-    __device__ __forceinline__ const unsigned char* a(int i) const { return s + o->a[i]; }
-    __device__ __forceinline__ const unsigned char* b(int i) const { return s + o->b[i]; }
+    template <int T, int CI>
+    __device__ __forceinline__ typename ColT<T>::type ld(uint32_t r0, int j) const {
+        return lds<T>(s + o->off[CI], r0 + 32 * j);
+    }
+    template <int T, int CI>
+    __device__ __forceinline__ uint32_t ld_lo(uint32_t r0, int j) const {
+        return lds_lo<T>(s + o->off[CI], r0 + 32 * j);
+    }
 };
 
 // Adds sum I (and the following ones) of group gi of this CTA's table to the
@@ -90,8 +91,8 @@ extern "C" __global__ void __launch_bounds__(tpk::ST_THREADS, tpk::ST_CTAS)
     t.sum_off = L.sum_off;
     const Flt flt = make_flt(q);
     StageOffs o{};
-    if constexpr (JS::filter) o.f = L.off[L.col_of_slot[SL_FILTER]];
-    if constexpr (JS::join != J_NONE) o.k = L.off[L.col_of_slot[SL_FK]];
+    if constexpr (JS::filter) o.off[CI_F] = L.off[L.col_of_slot[SL_FILTER]];
+    if constexpr (JS::join != J_NONE) o.off[CI_K] = L.off[L.col_of_slot[SL_FK]];
     stage_offsets<JS, 0, 0>(L, o);
     constexpr uint32_t all = (1u << ST_RPL) - 1u;
     run_pipeline(q, L, n, smem + L.table_bytes, [&](const unsigned char* stage, uint64_t, uint32_t r0) {
