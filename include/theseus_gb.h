@@ -99,6 +99,12 @@ enum { TP_AGG_AUTO = 0, TP_AGG_SHARED = 1, TP_AGG_GLOBAL = 2 };
  *                         the device-memory aggregation, even when column
  *                         bounds show a dense key range (a direct-addressed
  *                         table needs no probing and yields sorted groups).
+ *                         TP_FLAG_RAW_PAGES: store appended columns in pages
+ *                         at their full width.  Without it every batch stores
+ *                         each integer column as (value - the batch's minimum)
+ *                         in the fewest bytes (1, 2 or 4) that hold the
+ *                         batch's range, and the device widens it after the
+ *                         copy: fewer bytes cross the host link.
  *                         TP_FLAG_NO_JIT: never compile plan-specialised
  *                         kernels at run time (NVRTC); the ahead-of-time
  *                         staged kernels run every shape.  Without the flag a
@@ -114,7 +120,8 @@ enum {
     TP_FLAG_EXACT_ONLY = 4,
     TP_FLAG_NO_DIRECT_JOIN = 8,
     TP_FLAG_NO_JIT = 16,
-    TP_FLAG_NO_DIRECT_AGG = 32
+    TP_FLAG_NO_DIRECT_AGG = 32,
+    TP_FLAG_RAW_PAGES = 64
 };
 typedef struct {
     uint64_t page_bytes;

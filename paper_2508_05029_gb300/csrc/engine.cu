@@ -75,6 +75,64 @@ tp_status dev_alloc(tp_engine* e, void** p, uint64_t bytes, cudaStream_t st) {
     return TP_OK;
 }
 
+tp_status copy_batch_column(tp_engine* e, const tp_table* t, const Batch& b, int c, void* full, void* enc,
+                            uint64_t row_off, cudaStream_t st) {
+    // a narrow column's rows land at its widest encoding's offsets (enc holds
+    // narrow_width_max bytes per row)
+    const uint64_t sz = b.narrow(c) ? (uint64_t)narrow_width_max(t, c) : type_size(t->types[c]);
+    uint8_t* dst = (uint8_t*)(b.narrow(c) ? enc : full) + row_off * sz;
+    for (const Extent& x : b.cols[c]) {
+        const cudaError_t err =
+            cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes, cudaMemcpyHostToDevice, st);
+        if (err != cudaSuccess) return fail(TP_E_CUDA, "batch copy: %s", cudaGetErrorString(err));
+        dst += x.bytes;
+        e->h2d_bytes += x.bytes;
+    }
+    return TP_OK;
+}
+
+tp_status widen_batch(tp_engine* e, const tp_table* t, const Batch& b, const std::vector<int>& cols,
+                      const std::vector<void*>& full, const std::vector<void*>& enc, uint64_t row_off,
+                      cudaStream_t st) {
+    tpk::DecodeCols d{};
+    auto flush = [&]() -> tp_status {
+        const cudaError_t err = tpk::launch_decode(d, b.rows, e->num_sms, st);
+        if (err != cudaSuccess) return fail(TP_E_CUDA, "widening a batch: %s", cudaGetErrorString(err));
+        if (d.n) e->launches++;
+        d.n = 0;
+        return TP_OK;
+    };
+    for (size_t i = 0; i < cols.size(); ++i) {
+        const int c = cols[i];
+        if (!b.narrow(c)) continue;
+        const uint64_t sz = type_size(t->types[c]);
+        d.src[d.n] = (const uint8_t*)enc[i] + row_off * (uint64_t)narrow_width_max(t, c);
+        d.dst[d.n] = (uint8_t*)full[i] + row_off * sz;
+        d.base[d.n] = b.enc_base[c];
+        d.w[d.n] = b.enc_w[c];
+        d.out[d.n] = (int32_t)sz;
+        if (++d.n == tpk::MAX_DECODE) {
+            tp_status s = flush();
+            if (s) return s;
+        }
+    }
+    return flush();
+}
+
+int narrow_width_max(const tp_table* t, int c) {
+    int w = 0;
+    for (const Batch& b : t->batches)
+        if (b.narrow(c)) w = std::max<int>(w, b.enc_w[c]);
+    return w;
+}
+
+bool has_narrow(const tp_table* t) {
+    for (const Batch& b : t->batches)
+        for (size_t c = 0; c < b.enc_w.size(); ++c)
+            if (b.enc_w[c]) return true;
+    return false;
+}
+
 void dev_free(tp_engine* e, void* p, cudaStream_t st) {
     (void)e;
     if (p) cudaFreeAsync(p, st);
@@ -271,6 +329,28 @@ static void free_batch_pages(tp_engine* e, Batch& b) {
     b.pages.clear();
 }
 
+int tp::Batch::width(int c, int32_t type) const { return narrow(c) ? enc_w[c] : type_size(type); }
+
+namespace {
+
+// Narrowest frame-of-reference width (1, 2 or 4 bytes) for values in
+// [lo, hi] stored in a column of full width `full`, or 0 when it saves nothing.
+int narrow_width(int64_t lo, int64_t hi, int full) {
+    const uint64_t span = (uint64_t)hi - (uint64_t)lo;
+    const int w = span <= 0xFFull ? 1 : span <= 0xFFFFull ? 2 : span <= 0xFFFFFFFFull ? 4 : 8;
+    return w < full ? w : 0;
+}
+
+int64_t value_at(const void* col, int32_t type, uint64_t i) {
+    switch (type) {
+    case TP_I32: return ((const int32_t*)col)[i];
+    case TP_I64: return ((const int64_t*)col)[i];
+    default: return ((const uint8_t*)col)[i];
+    }
+}
+
+}  // namespace
+
 tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) {
     clear_error();
     if (!t || (!cols && nrows)) return fail(TP_E_INVALID, "tp_table_append: NULL argument");
@@ -279,20 +359,35 @@ tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) 
     const uint64_t pb = e->pool.page_bytes;
     const size_t first_new = t->batches.size();
     const int nc = (int)t->types.size();
+    const bool narrow = !(e->cfg.flags & TP_FLAG_RAW_PAGES);
     for (uint64_t r0 = 0; r0 < nrows; r0 += t->batch_rows) {
         const uint64_t rows = std::min<uint64_t>(t->batch_rows, nrows - r0);
+        Batch b;
+        b.row0 = t->rows + r0;
+        b.rows = rows;
+        if (narrow) {  // frame of reference per batch and column: the batch's minimum, the fewest bytes
+            b.enc_w.assign(nc, 0);
+            b.enc_base.assign(nc, 0);
+            for (int c = 0; c < nc; ++c) {
+                int64_t lo = INT64_MAX, hi = INT64_MIN;
+                for (uint64_t i = r0; i < r0 + rows; ++i) {
+                    const int64_t v = value_at(cols[c], t->types[c], i);
+                    lo = std::min(lo, v);
+                    hi = std::max(hi, v);
+                }
+                b.enc_w[c] = (uint8_t)narrow_width(lo, hi, type_size(t->types[c]));
+                b.enc_base[c] = lo;
+            }
+        }
         // columns back to back, each starting on a 256-byte boundary
         std::vector<uint64_t> off(nc);
         uint64_t total = 0;
         for (int c = 0; c < nc; ++c) {
             total = (total + 255) & ~255ull;
             off[c] = total;
-            total += rows * type_size(t->types[c]);
+            total += rows * b.width(c, t->types[c]);
         }
         const uint64_t n_pages = (total + pb - 1) / pb;
-        Batch b;
-        b.row0 = t->rows + r0;
-        b.rows = rows;
         for (uint64_t i = 0; i < n_pages; ++i) {
             tp_page p;
             tp_status s = tp_page_alloc(e, &p);
@@ -305,10 +400,20 @@ tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) 
             b.pages.push_back(p);
         }
         b.cols.resize(nc);
+        std::vector<uint8_t> enc;
         for (int c = 0; c < nc; ++c) {
             const int sz = type_size(t->types[c]);
             const uint8_t* src = (const uint8_t*)cols[c] + r0 * sz;
-            uint64_t pos = off[c], left = rows * sz;
+            const int w = b.width(c, t->types[c]);
+            if (b.narrow(c)) {  // little-endian low bytes of (value - base)
+                enc.resize(rows * w);
+                for (uint64_t i = 0; i < rows; ++i) {
+                    const uint64_t d = (uint64_t)value_at(cols[c], t->types[c], r0 + i) - (uint64_t)b.enc_base[c];
+                    for (int k = 0; k < w; ++k) enc[i * w + k] = (uint8_t)(d >> (8 * k));
+                }
+                src = enc.data();
+            }
+            uint64_t pos = off[c], left = rows * w;
             while (left) {
                 const uint64_t pi = pos / pb, po = pos % pb;
                 const uint64_t take = std::min<uint64_t>(left, pb - po);
@@ -373,25 +478,37 @@ tp_status tp_table_place(tp_table* t, int32_t placement) {
             return s;
         }
     }
-    cudaStreamSynchronize(e->compute);
-    for (auto& b : t->batches) {
-        for (int c = 0; c < nc; ++c) {
-            uint8_t* dst = (uint8_t*)cols[c] + b.row0 * type_size(t->types[c]);
-            for (const Extent& x : b.cols[c]) {
-                cudaError_t err = cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes,
-                                                  cudaMemcpyHostToDevice, e->copy);
-                if (err != cudaSuccess) {
-                    cudaStreamSynchronize(e->copy);
-                    for (void* p : cols) dev_free(e, p, e->compute);
-                    release(e, bytes);
-                    return fail(TP_E_CUDA, "tp_table_place: copy failed: %s", cudaGetErrorString(err));
-                }
-                dst += x.bytes;
-                e->h2d_bytes += x.bytes;
-            }
-        }
+    // narrow batches are copied into a scratch buffer of one batch, then widened in place
+    uint64_t max_rows = 0;
+    for (auto& b : t->batches) max_rows = std::max(max_rows, b.rows);
+    void* scratch = nullptr;
+    if (has_narrow(t) && (s = dev_alloc(e, &scratch, max_rows * 8 * (uint64_t)nc, e->compute))) {
+        for (void* p : cols) dev_free(e, p, e->compute);
+        release(e, bytes);
+        return s;
     }
-    TP_TRY_CUDA(cudaStreamSynchronize(e->copy));
+    cudaStreamSynchronize(e->compute);
+    std::vector<int> all(nc);
+    for (int c = 0; c < nc; ++c) all[c] = c;
+    for (auto& b : t->batches) {
+        std::vector<void*> full(nc), enc(nc);
+        for (int c = 0; c < nc; ++c) {
+            full[c] = (uint8_t*)cols[c] + b.row0 * type_size(t->types[c]);
+            enc[c] = scratch ? (uint8_t*)scratch + (uint64_t)c * max_rows * 8 : nullptr;
+            if (!s) s = copy_batch_column(e, t, b, c, full[c], enc[c], 0, e->compute);
+        }
+        if (!s) s = widen_batch(e, t, b, all, full, enc, 0, e->compute);   // same stream: the scratch is reused in order
+        if (s) break;
+    }
+    if (scratch) dev_free(e, scratch, e->compute);
+    const cudaError_t done = cudaStreamSynchronize(e->compute);
+    if (!s && done != cudaSuccess) s = fail(TP_E_CUDA, "tp_table_place: %s", cudaGetErrorString(done));
+    if (s) {
+        cudaStreamSynchronize(e->compute);
+        for (void* p : cols) dev_free(e, p, e->compute);
+        release(e, bytes);
+        return s;
+    }
     for (auto& b : t->batches) free_batch_pages(e, b);
     t->batches.clear();
     t->dev_cols = cols;

@@ -36,11 +36,16 @@ int64_t paged_value(const tp_table* t, int c, uint64_t row) {
     auto it = std::upper_bound(t->batches.begin(), t->batches.end(), row,
                                [](uint64_t r, const Batch& b) { return r < b.row0; });
     const Batch& b = *(it - 1);
-    const int sz = type_size(t->types[c]);
+    const int sz = b.width(c, t->types[c]);
     uint64_t off = (row - b.row0) * sz;
     for (const Extent& x : b.cols[c]) {
-        if (off < x.bytes) {
+        if (off < x.bytes) {   // column starts are 256-byte aligned and pages whole 4 KiB multiples: no value straddles two extents
             const uint8_t* p = (const uint8_t*)tp_page_ptr(t->eng, x.page) + x.offset + off;
+            if (b.narrow(c)) {
+                uint64_t d = 0;
+                for (int k = 0; k < sz; ++k) d |= (uint64_t)p[k] << (8 * k);
+                return (int64_t)((uint64_t)b.enc_base[c] + d);
+            }
             switch (t->types[c]) {
             case TP_I32: { int32_t v; memcpy(&v, p, 4); return v; }
             case TP_I64: { int64_t v; memcpy(&v, p, 8); return v; }
@@ -187,21 +192,22 @@ tp_status build_join(ExecState& S, Scratch& sc) {
     // paged dimension: copy each batch's key and field columns, then insert
     uint64_t max_rows = 0;
     for (auto& bt : t->batches) max_rows = std::max(max_rows, bt.rows);
-    std::vector<void*> stage(bcols.size(), nullptr);
+    std::vector<void*> stage(bcols.size(), nullptr), enc(bcols.size(), nullptr);
+    const bool narrow = has_narrow(t);
     for (size_t i = 0; i < bcols.size(); ++i) {
         tp_status s = sc.alloc(&stage[i], align256(max_rows * type_size(t->types[bcols[i]])));
+        const int w = narrow ? narrow_width_max(t, bcols[i]) : 0;
+        if (!s && w) s = sc.alloc(&enc[i], align256(max_rows * (uint64_t)w));
         if (s) return s;
     }
     for (auto& bt : t->batches) {
         for (size_t i = 0; i < bcols.size(); ++i) {
-            uint8_t* dst = (uint8_t*)stage[i];
-            for (const Extent& x : bt.cols[bcols[i]]) {
-                tp_status s = cuda_check(cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes,
-                                                         cudaMemcpyHostToDevice, st), "dim copy");
-                if (s) return s;
-                dst += x.bytes;
-                e->h2d_bytes += x.bytes;
-            }
+            tp_status s = copy_batch_column(e, t, bt, bcols[i], stage[i], enc[i], 0, st);
+            if (s) return s;
+        }
+        if (narrow) {
+            tp_status s = widen_batch(e, t, bt, bcols, stage, enc, 0, st);
+            if (s) return s;
         }
         b.key = devcol(t, bcols[0], stage[0]);
         for (int k = 0; k < nf; ++k) b.dcol[k] = devcol(t, bcols[1 + k], stage[1 + k]);
@@ -247,12 +253,20 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
     }
     const bool prefetch = e->cfg.prefetch_depth > 0;
     const int n_slots = prefetch ? e->cfg.prefetch_depth + 1 : 1;
-    // staging slots: every used column of one batch
+    // staging slots: every used column of one group, and where batches store
+    // narrow columns a second set they are copied into before widening
+    const bool narrow = has_narrow(t);
     std::vector<std::vector<void*>> slot(n_slots, std::vector<void*>(nc, nullptr));
+    std::vector<std::vector<void*>> enc(n_slots, std::vector<void*>(nc, nullptr));
+    std::vector<std::vector<void*>> full_used(n_slots), enc_used(n_slots);
     for (int s = 0; s < n_slots; ++s)
         for (int c : S.used) {
             tp_status st = sc.alloc(&slot[s][c], align256(max_rows * type_size(t->types[c])));
+            const int w = narrow ? narrow_width_max(t, c) : 0;
+            if (!st && w) st = sc.alloc(&enc[s][c], align256(max_rows * (uint64_t)w));
             if (st) return st;
+            full_used[s].push_back(slot[s][c]);
+            enc_used[s].push_back(enc[s][c]);
         }
     std::vector<cudaEvent_t> loaded(n_slots), freed(n_slots);
     for (int s = 0; s < n_slots; ++s) {
@@ -271,15 +285,11 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
         const int s = (int)(g % n_slots);
         if (prefetch && g >= (size_t)n_slots) cudaStreamWaitEvent(S.lane->copy, freed[s], 0);
         for (int c : S.used) {
-            uint8_t* dst = (uint8_t*)slot[s][c];
+            uint64_t row_off = 0;
             for (size_t bi = groups[g].first; bi < groups[g].second; ++bi) {
-                for (const Extent& x : t->batches[bi].cols[c]) {
-                    tp_status r = cuda_check(cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset,
-                                                             x.bytes, cudaMemcpyHostToDevice, cs), "batch copy");
-                    if (r) return r;
-                    dst += x.bytes;
-                    e->h2d_bytes += x.bytes;
-                }
+                tp_status r = copy_batch_column(e, t, t->batches[bi], c, slot[s][c], enc[s][c], row_off, cs);
+                if (r) return r;
+                row_off += t->batches[bi].rows;
             }
             gptr[s][c] = slot[s][c];
         }
@@ -297,6 +307,14 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
         uint64_t rows = 0;
         for (size_t bi = groups[g].first; bi < groups[g].second; ++bi) rows += t->batches[bi].rows;
         if (prefetch) cudaStreamWaitEvent(S.lane->compute, loaded[s], 0);
+        if (narrow) {  // widen the narrow columns in place of the copy's layout
+            uint64_t row_off = 0;
+            for (size_t bi = groups[g].first; bi < groups[g].second && rc == TP_OK; ++bi) {
+                rc = widen_batch(e, t, t->batches[bi], S.used, full_used[s], enc_used[s], row_off, S.lane->compute);
+                row_off += t->batches[bi].rows;
+            }
+            if (rc) break;
+        }
         for (int c : S.used) colptr[c] = gptr[s][c];
         tpk::QueryDev q = make_query(S, colptr);
         rc = kernel(q, rows, colptr);
@@ -311,8 +329,11 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
         cudaEventDestroy(loaded[s]);
         cudaEventDestroy(freed[s]);
         for (int c : S.used) {  // the staging slots go back to the pool after the last kernel
-            dev_free(e, slot[s][c], S.lane->compute);
-            sc.ptrs.erase(std::find(sc.ptrs.begin(), sc.ptrs.end(), slot[s][c]));
+            for (void* p : {slot[s][c], enc[s][c]}) {
+                if (!p) continue;
+                dev_free(e, p, S.lane->compute);
+                sc.ptrs.erase(std::find(sc.ptrs.begin(), sc.ptrs.end(), p));
+            }
         }
     }
     return rc;
@@ -536,20 +557,22 @@ tp_status for_each_dim_batch(ExecState& S, Scratch& sc, const tpk::BuildDev& pro
     }
     uint64_t max_rows = 0;
     for (auto& bt : t->batches) max_rows = std::max(max_rows, bt.rows);
-    std::vector<void*> stage(bcols.size(), nullptr);
+    std::vector<void*> stage(bcols.size(), nullptr), enc(bcols.size(), nullptr);
+    const bool narrow = has_narrow(t);
     for (size_t i = 0; i < bcols.size(); ++i) {
         tp_status s = sc.alloc(&stage[i], align256(max_rows * type_size(t->types[bcols[i]])));
+        const int w = narrow ? narrow_width_max(t, bcols[i]) : 0;
+        if (!s && w) s = sc.alloc(&enc[i], align256(max_rows * (uint64_t)w));
         if (s) return s;
     }
     for (auto& bt : t->batches) {
         for (size_t i = 0; i < bcols.size(); ++i) {
-            uint8_t* dst = (uint8_t*)stage[i];
-            for (const Extent& x : bt.cols[bcols[i]]) {
-                TP_TRY_CUDA(cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes,
-                                            cudaMemcpyHostToDevice, S.lane->compute));
-                dst += x.bytes;
-                e->h2d_bytes += x.bytes;
-            }
+            tp_status s = copy_batch_column(e, t, bt, bcols[i], stage[i], enc[i], 0, S.lane->compute);
+            if (s) return s;
+        }
+        if (narrow) {
+            tp_status s = widen_batch(e, t, bt, bcols, stage, enc, 0, S.lane->compute);
+            if (s) return s;
         }
         bind(std::vector<const void*>(stage.begin(), stage.end()));
         tp_status s = fn(b, bt.rows);
@@ -954,7 +977,9 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         const int n_slots = e->cfg.prefetch_depth > 0 ? e->cfg.prefetch_depth + 1 : 1;
         uint64_t max_rows = 0;
         for (auto& b : S.fact->batches) max_rows = std::max(max_rows, b.rows);
-        for (int c : S.used) est += n_slots * align256(max_rows * type_size(S.fact->types[c]));
+        for (int c : S.used)   // full-width slots, and the narrow copies widened into them
+            est += n_slots * (align256(max_rows * type_size(S.fact->types[c])) +
+                              align256(max_rows * (uint64_t)narrow_width_max(S.fact, c)));
     }
     const bool shared = p->strategy == TP_AGG_SHARED;
     const uint32_t G = shared ? (1u << p->key_bits) : 0;
@@ -1002,7 +1027,8 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             S.join_cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(S.dim->rows / lf)));
             join_bytes = S.join_cap * (S.key64 ? 16 : 8);
         }
-        const uint64_t dim_stage = S.dim->placement == PL_PAGES ? 4 * align256(S.dim->batch_rows * 8) : 0;
+        const uint64_t dim_stage =
+            S.dim->placement == PL_PAGES ? (has_narrow(S.dim) ? 6 : 4) * align256(S.dim->batch_rows * 8) : 0;
         if (!S.jt.direct) {  // hybrid hash join when the table would crowd the budget
             uint64_t reserved_now = 0, cap_now = 0;
             tp_budget_query(e, &reserved_now, &cap_now);

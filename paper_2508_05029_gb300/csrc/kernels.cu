@@ -273,6 +273,40 @@ cudaError_t launch_final_dense(const uint64_t* gacc, uint32_t key_bits, int n_su
 }
 
 // Occupied slots of the global table -> (key, slot index); also the max key.
+// ------------------------------------------------------------ narrow pages
+
+template <typename U>
+__device__ __forceinline__ void decode_col(const U* __restrict__ src, int64_t base, void* dst, int out,
+                                           uint64_t rows) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (out == 8) {
+        int64_t* d = (int64_t*)dst;
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows; i += stride)
+            d[i] = (int64_t)((uint64_t)base + (uint64_t)__ldcs(src + i));
+    } else {
+        int32_t* d = (int32_t*)dst;
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows; i += stride)
+            d[i] = (int32_t)(uint32_t)((uint64_t)base + (uint64_t)__ldcs(src + i));
+    }
+}
+
+__global__ void k_decode(const __grid_constant__ DecodeCols d, uint64_t rows) {
+    for (int c = 0; c < d.n; ++c) {
+        switch (d.w[c]) {
+        case 1: decode_col((const uint8_t*)d.src[c], d.base[c], d.dst[c], d.out[c], rows); break;
+        case 2: decode_col((const uint16_t*)d.src[c], d.base[c], d.dst[c], d.out[c], rows); break;
+        default: decode_col((const uint32_t*)d.src[c], d.base[c], d.dst[c], d.out[c], rows); break;
+        }
+    }
+}
+
+cudaError_t launch_decode(const DecodeCols& d, uint64_t rows, int num_sms, cudaStream_t st) {
+    if (rows == 0 || d.n == 0) return cudaSuccess;
+    const uint64_t blocks = std::min<uint64_t>((rows + 255) / 256, (uint64_t)num_sms * 4);
+    k_decode<<<(unsigned)blocks, 256, 0, st>>>(d, rows);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ direct tables
 
 // Occupied slots (count word non-zero) of each chunk of DIRECT_CHUNK slots.

@@ -378,6 +378,20 @@ cudaError_t launch_gather_global(const AggTable& t, const uint64_t* sorted_keys,
                                  const uint32_t* sorted_idx, uint64_t n, int n_sum, const OutDev& o,
                                  int num_sms, cudaStream_t st, bool lo_only = false);
 
+// Narrow columns of a host-page batch widened after their copy: column c
+// stores w[c] bytes per row (1, 2 or 4) of (value - base[c]) as an unsigned
+// little-endian integer; dst gets the out[c]-byte (4 or 8) value.
+constexpr int MAX_DECODE = 16;
+struct DecodeCols {
+    const void* src[MAX_DECODE];
+    void* dst[MAX_DECODE];
+    int64_t base[MAX_DECODE];
+    int32_t w[MAX_DECODE];
+    int32_t out[MAX_DECODE];
+    int32_t n;
+};
+cudaError_t launch_decode(const DecodeCols& d, uint64_t rows, int num_sms, cudaStream_t st);
+
 // Rows of the filter column that pass, among `samples` evenly spaced rows.
 cudaError_t launch_sample_filter(const QueryDev& q, uint64_t n, uint32_t samples,
                                  unsigned long long* out, cudaStream_t st);

@@ -69,11 +69,18 @@ struct Extent {
 
 // One batch of a paged table: a row range whose columns lie back to back
 // across a run of pages.
+// One batch of a host-page table.  A column may be stored narrow (frame of
+// reference): enc_w[c] bytes per row of (value - enc_base[c]) as an unsigned
+// integer, enc_w[c] = 0 meaning the full width of the column's type.
 struct Batch {
     uint64_t row0 = 0;
     uint64_t rows = 0;
     std::vector<std::vector<Extent>> cols;   // per column
     std::vector<uint32_t> pages;
+    std::vector<uint8_t> enc_w;              // per column (empty: every column full width)
+    std::vector<int64_t> enc_base;
+    int width(int c, int32_t type) const;    // bytes per row of column c as stored
+    bool narrow(int c) const { return !enc_w.empty() && enc_w[c] != 0; }
 };
 
 enum Placement : int32_t { PL_PAGES = TP_HOST_PAGES, PL_DEVICE = TP_DEVICE, PL_WRAPPED = 3 };
@@ -236,6 +243,21 @@ std::string shape_struct(const std::string& name, const tpk::QueryDev& q, const 
 // The source (shape struct JS and the kernel include) of a dense staged
 // launch's run-time compiled kernel.
 std::string dense_shape(const tpk::QueryDev& q, const tpk::StageLayout& L, bool fast, const int* narrow);
+// Host-to-device copy of column c of batch b (t's page layout) on `st`: a
+// full-width column lands at full + row_off * size, a narrow one at
+// enc + row_off * size (enc is then widened by widen_batch).  Adds the bytes
+// to the engine's counter.
+tp_status copy_batch_column(tp_engine* e, const tp_table* t, const Batch& b, int c, void* full, void* enc,
+                            uint64_t row_off, cudaStream_t st);
+// Widens batch b's narrow columns among cols (enc -> full, the offsets of
+// copy_batch_column) with one launch on st.
+tp_status widen_batch(tp_engine* e, const tp_table* t, const Batch& b, const std::vector<int>& cols,
+                      const std::vector<void*>& full, const std::vector<void*>& enc, uint64_t row_off,
+                      cudaStream_t st);
+// Whether any batch of t stores a narrow column.
+bool has_narrow(const tp_table* t);
+// The widest narrow encoding of column c over t's batches (0: never narrow).
+int narrow_width_max(const tp_table* t, int c);
 // device memory (stream-ordered allocator on the compute stream)
 tp_status dev_alloc(tp_engine* e, void** p, uint64_t bytes, cudaStream_t st);
 void dev_free(tp_engine* e, void* p, cudaStream_t st);

@@ -28,7 +28,7 @@ TP_AGG_AUTO, TP_AGG_SHARED, TP_AGG_GLOBAL = 0, 1, 2
 TP_I32, TP_I64, TP_U8 = 0, 1, 2
 TP_HOST_PAGES, TP_DEVICE = 1, 2
 TP_FLAG_TIME_KERNELS, TP_FLAG_NO_STAGED, TP_FLAG_EXACT_ONLY, TP_FLAG_NO_DIRECT_JOIN, TP_FLAG_NO_JIT = 1, 2, 4, 8, 16
-TP_FLAG_NO_DIRECT_AGG = 32
+TP_FLAG_NO_DIRECT_AGG, TP_FLAG_RAW_PAGES = 32, 64
 TP_SIDE_FACT, TP_SIDE_DIM = 0, 1
 TP_AGG_SUM, TP_AGG_SUM_MUL_SUB, TP_AGG_COUNT, TP_AGG_AVG = 0, 1, 2, 3
 

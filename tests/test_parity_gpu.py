@@ -208,7 +208,7 @@ def test_budget_refusal_and_release(eng):
 @pytest.mark.parametrize("flags", [0, T.TP_FLAG_EXACT_ONLY, T.TP_FLAG_NO_STAGED, T.TP_FLAG_NO_DIRECT_JOIN,
                                    T.TP_FLAG_NO_STAGED | T.TP_FLAG_NO_DIRECT_JOIN, T.TP_FLAG_NO_JIT,
                                    T.TP_FLAG_NO_JIT | T.TP_FLAG_EXACT_ONLY, T.TP_FLAG_NO_JIT | T.TP_FLAG_NO_DIRECT_JOIN,
-                                   T.TP_FLAG_NO_DIRECT_AGG])
+                                   T.TP_FLAG_NO_DIRECT_AGG, T.TP_FLAG_RAW_PAGES])
 def test_every_kernel_path(flags):
     """Staged 64-bit (bounds prove no overflow), staged exact 128-bit, the
     plain-load kernel, hashed instead of direct-mapped join tables, and the
@@ -293,5 +293,38 @@ def test_many_groups_direct_and_hashed(flags, which):
     try:
         check(e, wl.fact, wl.dim, wl.query)
         check(e, wl.fact, wl.dim, wl.query, placement=T.TP_HOST_PAGES)
+    finally:
+        e.close()
+
+
+@pytest.mark.parametrize("flags", [0, T.TP_FLAG_RAW_PAGES])
+def test_narrow_pages_round_trip(flags):
+    """Host-page columns stored narrow (per batch: value - minimum in 1, 2 or 4
+    bytes) or at full width give the oracle's result, for negative values,
+    spans that need every width, and spans too wide to narrow."""
+    n = 300_017
+    rng = np.random.default_rng(11)
+    fact = dict(
+        fk=rng.integers(-50, 50, n).astype(np.int64),                       # negative, 1 byte
+        w2=rng.integers(-30_000, 30_000, n).astype(np.int64),               # 2 bytes
+        w4=rng.integers(-(1 << 31), 1 << 31, n).astype(np.int64),           # 4 bytes
+        w8=(rng.integers(0, 1 << 62, n) - (1 << 61)).astype(np.int64),      # full width
+        i32=rng.integers(-(1 << 31), (1 << 31) - 1, n).astype(np.int32),    # full width
+        d=rng.integers(0, 2557, n).astype(np.int32),
+        g=rng.integers(0, 3, n).astype(np.uint8),
+    )
+    dim = dict(pk=np.arange(-50, 50, dtype=np.int64), attr=(np.arange(100) % 7).astype(np.int32))
+    q = dict(filter=dict(col="d", lo=10, hi=2400), join=dict(fact_col="fk", dim_col="pk"),
+             group=[("dim", "attr", 3), ("fact", "g", 2)],
+             aggs=[("sum", "w2"), ("sum", "w4"), ("sum", "w8"), ("sum", "i32"), ("count",), ("avg", "w2")])
+    e = T.Engine(page_bytes=1 << 20, n_pages=256, batch_rows=40_000, flags=flags)
+    try:
+        check(e, fact, dim, q, placement=T.TP_HOST_PAGES)
+        ft = e.table_from_numpy(fact, placement=T.TP_DEVICE)      # placed from (narrow) pages
+        dt = e.table_from_numpy(dim, placement=T.TP_DEVICE)
+        p = e.plan(ft, dt, q)
+        with p.execute() as r:
+            assert_matches_oracle(r, oracle.run_query(fact, dim, q), q["aggs"])
+        p.destroy(); ft.destroy(); dt.destroy()
     finally:
         e.close()
