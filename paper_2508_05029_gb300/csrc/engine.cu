@@ -119,6 +119,12 @@ tp_status widen_batch(tp_engine* e, const tp_table* t, const Batch& b, const std
     return flush();
 }
 
+int frame_width(int64_t lo, int64_t hi, int full) {
+    const uint64_t span = (uint64_t)hi - (uint64_t)lo;
+    const int w = span <= 0xFFull ? 1 : span <= 0xFFFFull ? 2 : span <= 0xFFFFFFFFull ? 4 : 8;
+    return w < full ? w : 0;
+}
+
 int narrow_width_max(const tp_table* t, int c) {
     int w = 0;
     for (const Batch& b : t->batches)
@@ -333,14 +339,6 @@ int tp::Batch::width(int c, int32_t type) const { return narrow(c) ? enc_w[c] : 
 
 namespace {
 
-// Narrowest frame-of-reference width (1, 2 or 4 bytes) for values in
-// [lo, hi] stored in a column of full width `full`, or 0 when it saves nothing.
-int narrow_width(int64_t lo, int64_t hi, int full) {
-    const uint64_t span = (uint64_t)hi - (uint64_t)lo;
-    const int w = span <= 0xFFull ? 1 : span <= 0xFFFFull ? 2 : span <= 0xFFFFFFFFull ? 4 : 8;
-    return w < full ? w : 0;
-}
-
 int64_t value_at(const void* col, int32_t type, uint64_t i) {
     switch (type) {
     case TP_I32: return ((const int32_t*)col)[i];
@@ -375,7 +373,7 @@ tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) 
                     lo = std::min(lo, v);
                     hi = std::max(hi, v);
                 }
-                b.enc_w[c] = (uint8_t)narrow_width(lo, hi, type_size(t->types[c]));
+                b.enc_w[c] = (uint8_t)frame_width(lo, hi, type_size(t->types[c]));
                 b.enc_base[c] = lo;
             }
         }

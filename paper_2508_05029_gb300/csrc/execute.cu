@@ -492,9 +492,11 @@ tp_table* spill_table(tp_engine* e, const std::vector<int32_t>& types) {
 // columns lie back to back where the previous append ended, in the table's
 // page chain (new pool pages as needed), so a partition wastes at most one
 // partial page.  Device -> host copies on `st`, synchronised unless !sync
-// (the caller then synchronises st before the pages are read).
+// (the caller then synchronises st before the pages are read).  enc_w /
+// enc_base: the columns arrive narrow, with that encoding.
 tp_status append_device_rows(tp_engine* e, tp_table* t, const std::vector<const void*>& dev, uint64_t nrows,
-                             cudaStream_t st, bool sync = true) {
+                             cudaStream_t st, bool sync = true, const std::vector<uint8_t>* enc_w = nullptr,
+                             const std::vector<int64_t>* enc_base = nullptr) {
     if (nrows == 0) return TP_OK;
     const uint64_t pb = e->pool.page_bytes;
     const int nc = (int)t->types.size();
@@ -502,12 +504,16 @@ tp_status append_device_rows(tp_engine* e, tp_table* t, const std::vector<const 
     b.row0 = t->rows;
     b.rows = nrows;
     b.cols.resize(nc);
+    if (enc_w) {   // the rows arrive narrow (frame of reference)
+        b.enc_w = *enc_w;
+        b.enc_base = *enc_base;
+    }
     uint64_t pos = t->chain_used;
     for (int c = 0; c < nc; ++c) {
         if (!dev[c]) continue;
         pos = align256(pos);
         const uint8_t* src = (const uint8_t*)dev[c];
-        uint64_t left = nrows * type_size(t->types[c]);
+        uint64_t left = nrows * b.width(c, t->types[c]);
         while (left) {
             const uint64_t pi = pos / pb, po = pos % pb, take = std::min<uint64_t>(left, pb - po);
             while (t->chain.size() <= pi) {
@@ -716,14 +722,27 @@ tp_status part_spill_fact(ExecState& S, Scratch& sc, PartJoin& pj, const tpk::Qu
         cudaEventDestroy(pj.inflight.front());
         pj.inflight.pop_front();
     }
+    // spilled rows travel narrow where the fact table's bounds allow, as
+    // host pages do: fewer bytes each way over the link
+    const int nct = (int)S.fact->types.size();
+    std::vector<uint8_t> enc_w(nct, 0);
+    std::vector<int64_t> enc_base(nct, 0);
+    const bool narrow = !(e->cfg.flags & TP_FLAG_RAW_PAGES);
     tpk::SpillCols cols{};
     std::vector<void*> out(S.fact->types.size(), nullptr);
+    std::vector<int> width(nct, 0);
     for (int c : S.used) {
-        tp_status s = sc.alloc(&out[c], align256(total * type_size(S.fact->types[c])));
+        const int full = type_size(S.fact->types[c]);
+        enc_w[c] = narrow ? (uint8_t)frame_width(S.fact->cmin[c], S.fact->cmax[c], full) : 0;
+        enc_base[c] = S.fact->cmin[c];
+        width[c] = enc_w[c] ? enc_w[c] : full;
+        tp_status s = sc.alloc(&out[c], align256(total * (uint64_t)width[c]));
         if (s) return s;
         cols.src[cols.n] = colptr[c];
         cols.dst[cols.n] = out[c];
-        cols.esize[cols.n] = type_size(S.fact->types[c]);
+        cols.esize[cols.n] = full;
+        cols.w[cols.n] = width[c];
+        cols.base[cols.n] = enc_base[c];
         ++cols.n;
     }
     mark_launch(e);
@@ -741,8 +760,8 @@ tp_status part_spill_fact(ExecState& S, Scratch& sc, PartJoin& pj, const tpk::Qu
     for (int p = 0; p < P && s == TP_OK; ++p) {
         if (bc[p] == 0) continue;
         std::vector<const void*> part(S.fact->types.size(), nullptr);
-        for (int c : S.used) part[c] = (const uint8_t*)out[c] + base[p] * type_size(S.fact->types[c]);
-        s = append_device_rows(e, pj.fact_spill[p], part, bc[p], sp, false);
+        for (int c : S.used) part[c] = (const uint8_t*)out[c] + base[p] * (uint64_t)width[c];
+        s = append_device_rows(e, pj.fact_spill[p], part, bc[p], sp, false, &enc_w, &enc_base);
     }
     for (int c : S.used) {  // staging goes back (stream-ordered) once its copies are done
         dev_free(e, out[c], sp);

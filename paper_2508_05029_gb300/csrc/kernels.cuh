@@ -346,10 +346,14 @@ cudaError_t launch_build_pairs(const JoinTable& jt, const int64_t* keys, const u
 // Fact side: rows that pass the filter and whose key falls in a partition of
 // spill_mask are copied, column by column (cols[c] != nullptr), to
 // out[c] + (base[p] + cursor[p]++) * size.
+// A column's rows are stored narrow when w[c] < esize[c]: (value - base[c])
+// in w[c] bytes (frame of reference, as host pages store them).
 struct SpillCols {
     const void* src[32];
     void* dst[32];
+    int64_t base[32];
     int32_t esize[32];
+    int32_t w[32];
     int32_t n;
 };
 cudaError_t launch_fact_spill(const QueryDev& q, uint64_t n, uint64_t spill_mask, const SpillCols& cols,

@@ -195,7 +195,8 @@ cudaError_t launch_build_pairs(const JoinTable& jt, const int64_t* keys, const u
 }
 
 // Fact rows of spilled partitions: copy every requested column to its
-// partition's run in the staging columns (tile-aggregated cursors, as above).
+// partition's run in the staging columns, narrow where cols says so
+// (tile-aggregated cursors, as above).
 __global__ void __launch_bounds__(SP_THREADS)
     k_fact_spill(const __grid_constant__ QueryDev q, uint64_t n, uint64_t spill_mask,
                  const __grid_constant__ SpillCols cols, const unsigned long long* base, unsigned long long* cursor) {
@@ -227,10 +228,18 @@ __global__ void __launch_bounds__(SP_THREADS)
             const uint64_t i = t0 + (uint64_t)k * SP_THREADS + threadIdx.x;
             const uint64_t at = at0[part[k]] + rank[k];
             for (int c = 0; c < cols.n; ++c) {
+                int64_t v;
                 switch (cols.esize[c]) {
-                case 8: ((int64_t*)cols.dst[c])[at] = ((const int64_t*)cols.src[c])[i]; break;
-                case 4: ((int32_t*)cols.dst[c])[at] = ((const int32_t*)cols.src[c])[i]; break;
-                default: ((uint8_t*)cols.dst[c])[at] = ((const uint8_t*)cols.src[c])[i]; break;
+                case 8: v = ((const int64_t*)cols.src[c])[i]; break;
+                case 4: v = ((const int32_t*)cols.src[c])[i]; break;
+                default: v = ((const uint8_t*)cols.src[c])[i]; break;
+                }
+                const uint64_t d = cols.w[c] < cols.esize[c] ? (uint64_t)v - (uint64_t)cols.base[c] : (uint64_t)v;
+                switch (cols.w[c]) {
+                case 8: ((uint64_t*)cols.dst[c])[at] = d; break;
+                case 4: ((uint32_t*)cols.dst[c])[at] = (uint32_t)d; break;
+                case 2: ((uint16_t*)cols.dst[c])[at] = (uint16_t)d; break;
+                default: ((uint8_t*)cols.dst[c])[at] = (uint8_t)d; break;
                 }
             }
         }

@@ -254,6 +254,9 @@ tp_status copy_batch_column(tp_engine* e, const tp_table* t, const Batch& b, int
 tp_status widen_batch(tp_engine* e, const tp_table* t, const Batch& b, const std::vector<int>& cols,
                       const std::vector<void*>& full, const std::vector<void*>& enc, uint64_t row_off,
                       cudaStream_t st);
+// Narrowest frame-of-reference width (1, 2 or 4 bytes) for values in [lo,
+// hi] of a column of full width `full`, or 0 when it saves nothing.
+int frame_width(int64_t lo, int64_t hi, int full);
 // Whether any batch of t stores a narrow column.
 bool has_narrow(const tp_table* t);
 // The widest narrow encoding of column c over t's batches (0: never narrow).
