@@ -93,10 +93,11 @@ tp_status copy_batch_column(tp_engine* e, const tp_table* t, const Batch& b, int
 
 tp_status widen_batch(tp_engine* e, const tp_table* t, const Batch& b, const std::vector<int>& cols,
                       const std::vector<void*>& full, const std::vector<void*>& enc, uint64_t row_off,
-                      cudaStream_t st) {
+                      cudaStream_t st, uint64_t rows) {
+    if (rows == 0) rows = b.rows;
     tpk::DecodeCols d{};
     auto flush = [&]() -> tp_status {
-        const cudaError_t err = tpk::launch_decode(d, b.rows, e->num_sms, st);
+        const cudaError_t err = tpk::launch_decode(d, rows, e->num_sms, st);
         if (err != cudaSuccess) return fail(TP_E_CUDA, "widening a batch: %s", cudaGetErrorString(err));
         if (d.n) e->launches++;
         d.n = 0;
