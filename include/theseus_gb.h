@@ -438,6 +438,7 @@ typedef struct {
     uint64_t jit_failures;       /* shapes whose compilation failed (ahead-of-time kernel used) */
     uint64_t jit_launches;       /* launches of run-time compiled kernels */
     double jit_compile_ms;       /* host time spent compiling */
+    uint64_t agg_split_passes;   /* extra passes of aggregations split by key range to fit the budget */
 } tp_stats;
 
 /* Message for the last error on this thread ("" if none). */

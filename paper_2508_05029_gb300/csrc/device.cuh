@@ -477,6 +477,7 @@ __device__ __forceinline__ uint64_t* agg_slot(const AggTable& t, uint64_t key, u
 // Slot of a key in either kind of global table (direct: key - kmin, in
 // range by the column bounds the host checked).
 __device__ __forceinline__ uint64_t* agg_slot_any(const AggTable& t, uint64_t key, uint32_t* err) {
+    if (t.split && (key < t.key_lo || key > t.key_hi)) return nullptr;   // another pass's key range
     if (t.direct) {
         const uint64_t s = key - t.kmin;
         if (s > t.mask) {

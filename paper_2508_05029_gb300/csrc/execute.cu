@@ -440,6 +440,71 @@ tp_status alloc_result(tp_engine* e, tp_plan* p, uint64_t cap, tp_result** out, 
     return TP_OK;
 }
 
+// Copies rows [0, n) of every array of src to rows [at, at + n) of dst (both
+// results of the same plan), on the device.
+tp_status copy_result_rows(tp_result* dst, uint64_t at, const tp_result* src, uint64_t n, int n_sum,
+                           cudaStream_t st) {
+    if (n == 0) return TP_OK;
+    TP_TRY_CUDA(cudaMemcpyAsync(dst->d_keys + at, src->d_keys, n * 8, cudaMemcpyDeviceToDevice, st));
+    TP_TRY_CUDA(cudaMemcpyAsync(dst->d_counts + at, src->d_counts, n * 8, cudaMemcpyDeviceToDevice, st));
+    for (int si = 0; si < n_sum; ++si) {
+        TP_TRY_CUDA(cudaMemcpyAsync(dst->d_sums[si] + 2 * at, src->d_sums[si], n * 16, cudaMemcpyDeviceToDevice, st));
+        if (dst->d_avgs[si])
+            TP_TRY_CUDA(cudaMemcpyAsync(dst->d_avgs[si] + at, src->d_avgs[si], n * 8, cudaMemcpyDeviceToDevice, st));
+    }
+    return TP_OK;
+}
+
+// Rows [0, n) of every array of r copied to host memory (keys, counts, then
+// per sum slot the sums and, where present, the averages), and back.
+tp_status stash_result_rows(const tp_result* r, uint64_t n, int n_sum, std::vector<uint8_t>* out, cudaStream_t st) {
+    uint64_t bytes = 16 * n;
+    for (int si = 0; si < n_sum; ++si) bytes += n * (r->d_avgs[si] ? 24 : 16);
+    out->resize(bytes);
+    uint8_t* h = out->data();
+    auto get = [&](const void* dev, uint64_t b) {
+        cudaError_t c = cudaMemcpyAsync(h, dev, b, cudaMemcpyDeviceToHost, st);
+        h += b;
+        return c;
+    };
+    TP_TRY_CUDA(get(r->d_keys, n * 8));
+    TP_TRY_CUDA(get(r->d_counts, n * 8));
+    for (int si = 0; si < n_sum; ++si) {
+        TP_TRY_CUDA(get(r->d_sums[si], n * 16));
+        if (r->d_avgs[si]) TP_TRY_CUDA(get(r->d_avgs[si], n * 8));
+    }
+    TP_TRY_CUDA(cudaStreamSynchronize(st));
+    return TP_OK;
+}
+
+tp_status unstash_result_rows(tp_result* r, uint64_t n, int n_sum, const std::vector<uint8_t>& in, cudaStream_t st) {
+    const uint8_t* h = in.data();
+    auto put = [&](void* dev, uint64_t b) {
+        cudaError_t c = cudaMemcpyAsync(dev, h, b, cudaMemcpyHostToDevice, st);
+        h += b;
+        return c;
+    };
+    TP_TRY_CUDA(put(r->d_keys, n * 8));
+    TP_TRY_CUDA(put(r->d_counts, n * 8));
+    for (int si = 0; si < n_sum; ++si) {
+        TP_TRY_CUDA(put(r->d_sums[si], n * 16));
+        if (r->d_avgs[si]) TP_TRY_CUDA(put(r->d_avgs[si], n * 8));
+    }
+    TP_TRY_CUDA(cudaStreamSynchronize(st));
+    return TP_OK;
+}
+
+// Output arrays of od moved on by `at` rows.
+tpk::OutDev out_at(tpk::OutDev od, uint64_t at, int n_sum) {
+    od.keys += at;
+    od.counts += at;
+    for (int si = 0; si < n_sum; ++si) {
+        od.sums[si] += 2 * at;
+        if (od.avgs[si]) od.avgs[si] += at;
+    }
+    return od;
+}
+
 // ------------------------------------------------------ hybrid hash join
 //
 // A hashed join whose table does not fit the device budget runs partitioned
@@ -456,6 +521,24 @@ tp_status alloc_result(tp_engine* e, tp_plan* p, uint64_t cap, tp_result** out, 
 // DIRECT_AGG_ALWAYS slots).
 constexpr uint64_t DIRECT_AGG_MAX_SLOTS = 1ull << 27;
 constexpr uint64_t DIRECT_AGG_ALWAYS = 1ull << 20;
+
+// A global aggregation whose table cannot be reserved runs as passes over
+// disjoint ranges of the packed group key, each range halved until its table
+// fits (Section 3.3.2: a task that runs out of memory is divided up and
+// retried); at most this many ranges.
+constexpr size_t MAX_AGG_RANGES = 256;
+
+// Device bytes of a global aggregation table and the arrays that turn it into
+// a result: direct (span slots, chunk counts and offsets) or hashed (cap + 1
+// slots, compaction keys and indices, radix sort histograms).
+uint64_t agg_table_bytes(bool direct, uint64_t span, uint64_t cap, uint32_t words) {
+    if (direct) {
+        const uint64_t n_chunks = (span + tpk::DIRECT_CHUNK - 1) / tpk::DIRECT_CHUNK;
+        return align256(span * words * 8) + align256(n_chunks * 4) + align256((n_chunks + 1) * 8);
+    }
+    return align256((cap + 1) * words * 8) + 2 * align256((cap + 1) * 12) +
+           align256(tpk::radix_sort_hist_words(cap + 1) * 4);
+}
 
 // Batches whose fact spill copies may still be running when the next batch
 // spills (each holds a staging buffer).
@@ -1014,33 +1097,35 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
     const bool shared = p->strategy == TP_AGG_SHARED;
     const uint32_t G = shared ? (1u << p->key_bits) : 0;
     uint64_t agg_cap = 0;
-    bool gdirect = false;           // direct-addressed global table over [dmin, dmin + dspan)
-    uint64_t dmin = 0, dspan = 0;
+    bool gdirect = false;           // direct-addressed global table over [rmin, rmin + rspan)
+    bool have_range = false;        // packed group keys inside [rmin, rmin + rspan) by the column bounds
+    uint64_t rmin = 0, rspan = 0;
+    uint64_t groups = 0;            // expected groups (global aggregation)
+    uint64_t agg_est = 0;           // global table bytes inside est, reserved per key range later
     const uint32_t words = 2 + 2 * ns;
     uint64_t result_groups = G;
     if (shared) {
         est += align256((uint64_t)G * (1 + 2 * ns) * 8);
     } else {
-        uint64_t groups = d.expected_groups ? d.expected_groups : p->history_groups;
+        groups = d.expected_groups ? d.expected_groups : p->history_groups;
         if (groups == 0) {
             groups = (uint64_t)std::ceil(S.fact->rows * std::min(1.0, p->selectivity * 1.25)) + 16;
             if (p->key_bits < 40) groups = std::min<uint64_t>(groups, 1ull << p->key_bits);
         }
         result_groups = groups;
+        have_range = direct_group_range(p, S.fact, S.dim, &rmin, &rspan) && rspan > 0;
         // a dense key range (column bounds) that the groups fill well enough
         // gets a direct-addressed table: no probing, groups come out sorted
-        if (!(e->cfg.flags & TP_FLAG_NO_DIRECT_AGG) && direct_group_range(p, S.fact, S.dim, &dmin, &dspan) &&
-            dspan <= DIRECT_AGG_MAX_SLOTS && dspan <= 4 * std::max<uint64_t>(groups, DIRECT_AGG_ALWAYS)) {
+        if (!(e->cfg.flags & TP_FLAG_NO_DIRECT_AGG) && have_range && rspan <= DIRECT_AGG_MAX_SLOTS &&
+            rspan <= 4 * std::max<uint64_t>(groups, DIRECT_AGG_ALWAYS)) {
             gdirect = true;
-            result_groups = std::min(groups, dspan);
-            const uint64_t n_chunks = (dspan + tpk::DIRECT_CHUNK - 1) / tpk::DIRECT_CHUNK;
-            est += align256(dspan * words * 8) + align256(n_chunks * 4) + align256((n_chunks + 1) * 8);
+            result_groups = std::min(groups, rspan);
+            agg_est = agg_table_bytes(true, rspan, 0, words);
         } else {
             agg_cap = pow2_at_least(std::max<uint64_t>(1024, (uint64_t)std::ceil(groups / lf)));
-            // table + compaction/sort arrays
-            est += align256((agg_cap + 1) * words * 8) + 2 * align256((agg_cap + 1) * 12) +
-                   align256(tpk::radix_sort_hist_words(agg_cap + 1) * 4);
+            agg_est = agg_table_bytes(false, 0, agg_cap, words);
         }
+        est += agg_est;
     }
     uint64_t join_bytes = 0;
     PartJoin pj;
@@ -1094,6 +1179,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         if (!(cache && !pj.on)) est += align256(join_bytes);   // a cached table holds its own reservation
         est += dim_stage;
     }
+    est -= agg_est;   // the global table is reserved per key range
     if ((s = reserve(e, est))) return s;
     sc.reserved += est;
     // ---- join table
@@ -1232,36 +1318,149 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         const bool stage_all = p->selectivity >= 0.25;
         bool fold = d.n_group > 0;
         for (int g = 0; g < d.n_group; ++g) fold = fold && d.group[g].side == TP_SIDE_FACT;
-        for (int attempt = 0;; ++attempt) {
+        // key ranges still to aggregate, the next one at the back (ascending
+        // keys come out in order); one range covering every key unless a
+        // table had to be split
+        struct KeyRange {
+            uint64_t lo, span;     // packed keys [lo, lo + span); span 0 = every key
+            uint64_t min_cap;      // hashed: capacity learned from an overflow
+        };
+        std::vector<KeyRange> todo{{rmin, have_range ? rspan : 0, 0}};
+        // the result the ranges append to in key order: rows [0, res_at) written
+        // of res_cap; a split aggregation sizes it from the keys covered so
+        // far and grows it when a later range brings more groups
+        uint64_t res_cap = 0, res_at = 0;
+        tpk::OutDev res_od{};
+        std::unique_ptr<tp_result, void (*)(tp_result*)> res_guard(nullptr, tp_result_free);
+        size_t n_ranges = 1;
+        uint64_t table_reserved = 0;   // reservation held for the current range's table
+        double gscale = 1.0;           // growth of the group estimate learned from overflows
+        int attempt = 0;
+        auto drop = [&](void* ptr) {
+            dev_free(e, ptr, st);
+            sc.ptrs.erase(std::find(sc.ptrs.begin(), sc.ptrs.end(), ptr));
+        };
+        int n_avg = 0;
+        for (int a = 0; a < d.n_agg; ++a) n_avg += d.aggs[a].kind == TP_AGG_AVG;
+        const uint64_t row_bytes = 16 + 16 * (uint64_t)ns + 8 * (uint64_t)n_avg;
+        // room for n more rows in the result (span_end: end of the keys covered)
+        auto result_room = [&](uint64_t n, uint64_t span_end) -> tp_status {
+            if (res_guard && res_at + n <= res_cap) return TP_OK;
+            const uint64_t need_rows = res_at + n;
+            uint64_t want = need_rows;
+            if (todo.size() > 1) {   // more ranges follow: extrapolate over the key range
+                const double covered = (double)(span_end - rmin);
+                const double x = std::ceil((double)need_rows * 1.125 * (double)rspan / std::max(1.0, covered));
+                want = std::max(need_rows, (uint64_t)std::min(x, (double)rspan));
+            }
+            const uint64_t want0 = want;
+            tp_result* r = nullptr;
+            tpk::OutDev od;
+            auto alloc_rows = [&]() {   // the extrapolated capacity, else just the rows needed
+                tp_status t = alloc_result(e, p, want, &r, &od, nullptr, st);
+                if (t == TP_E_BUDGET && want > need_rows) {
+                    want = need_rows;
+                    t = alloc_result(e, p, want, &r, &od, nullptr, st);
+                }
+                return t;
+            };
+            tp_status t = alloc_rows();
+            std::vector<uint8_t> stash;
+            if (t == TP_E_BUDGET && res_guard) {
+                // no room for the old and the new result at once: the rows so
+                // far wait in host memory meanwhile (Section 3.1: data moves
+                // to a larger memory tier)
+                if ((t = stash_result_rows(res_guard.get(), res_at, ns, &stash, st))) return t;
+                e->d2h_bytes += stash.size();
+                res_guard.reset();
+                want = want0;
+                t = alloc_rows();
+            }
+            if (t) return t;
+            std::unique_ptr<tp_result, void (*)(tp_result*)> fresh(r, tp_result_free);
+            if (!stash.empty()) {
+                if ((t = unstash_result_rows(r, res_at, ns, stash, st))) return t;
+                e->h2d_bytes += stash.size();
+            } else if (res_guard) {
+                if ((t = copy_result_rows(r, 0, res_guard.get(), res_at, ns, st))) return t;
+                TP_TRY_CUDA(cudaStreamSynchronize(st));
+            }
+            res_guard.reset(fresh.release());
+            res_od = od;
+            res_cap = want;
+            return TP_OK;
+        };
+        while (!todo.empty()) {
+            const KeyRange kr = todo.back();
+            const bool whole = kr.span == 0 || (kr.lo == rmin && kr.span == rspan);
+            bool rdirect = gdirect;
+            uint64_t rcap = std::max(agg_cap, kr.min_cap);
+            if (!whole) {   // table of a part of the key range, sized in proportion
+                const uint64_t g = (uint64_t)std::ceil((double)groups * gscale * (double)kr.span / (double)rspan) + 1;
+                rdirect = !(e->cfg.flags & TP_FLAG_NO_DIRECT_AGG) && kr.span <= DIRECT_AGG_MAX_SLOTS &&
+                          kr.span <= 4 * std::max<uint64_t>(g, DIRECT_AGG_ALWAYS);
+                rcap = rdirect ? 0 : std::max(kr.min_cap, pow2_at_least(std::max<uint64_t>(1024, (uint64_t)std::ceil(g / lf))));
+            }
+            const uint64_t need = agg_table_bytes(rdirect, kr.span, rcap, words);
+            s = TP_OK;
+            if (need > table_reserved) {
+                s = reserve(e, need - table_reserved);
+                if (s == TP_OK) sc.reserved += need - table_reserved;
+            } else {
+                release(e, table_reserved - need);
+                sc.reserved -= table_reserved - need;
+            }
+            if (s == TP_OK) table_reserved = need;
+            if (s == TP_OK && have_range) {
+                // the range's result rows must fit beside its table: those
+                // beyond the result's capacity, at the expected groups
+                const double share = whole ? 1.0 : (double)kr.span / (double)rspan;
+                const uint64_t g = std::min(kr.span, (uint64_t)std::ceil((double)groups * gscale * share));
+                const uint64_t rows = res_at + g > res_cap ? res_at + g - res_cap : 0;
+                const uint64_t room = rows ? align256(rows * row_bytes) + 4096 : 0;
+                if (room && (s = reserve(e, room)) == TP_OK) release(e, room);
+            }
+            if (s == TP_E_BUDGET && have_range && kr.span > 1 && n_ranges < MAX_AGG_RANGES) {
+                // halve the range (Section 3.3.2: divide the task and retry)
+                const uint64_t h = kr.span / 2;
+                todo.back() = {kr.lo + h, kr.span - h, 0};
+                todo.push_back({kr.lo, h, 0});
+                ++n_ranges;
+                continue;
+            }
+            if (s) return s;
             void* tab = nullptr;
-            const uint64_t tbytes = gdirect ? dspan * words * 8 : (agg_cap + 1) * words * 8;
+            const uint64_t tbytes = rdirect ? kr.span * words * 8 : (rcap + 1) * words * 8;
             if ((s = sc.alloc(&tab, tbytes))) return s;
-            if (gdirect) {
+            if (rdirect) {
                 TP_TRY_CUDA(cudaMemsetAsync(tab, 0, tbytes, st));
             } else {
-                TP_TRY_CUDA(tpk::launch_init_agg((uint64_t*)tab, agg_cap + 1, words, st));
+                TP_TRY_CUDA(tpk::launch_init_agg((uint64_t*)tab, rcap + 1, words, st));
                 mark_launch(e);
             }
             TP_TRY_CUDA(cudaMemsetAsync(S.counters, 0, 3 * sizeof(unsigned long long), st));
             tpk::AggTable at{};
             at.slots = (uint64_t*)tab;
-            at.mask = gdirect ? dspan - 1 : agg_cap - 1;
+            at.mask = rdirect ? kr.span - 1 : rcap - 1;
             at.words = words;
-            at.direct = gdirect ? 1 : 0;
-            at.kmin = dmin;
+            at.direct = rdirect ? 1 : 0;
+            at.kmin = kr.lo;
             at.used = S.counters;
-            at.max_used = (uint64_t)(agg_cap * 0.9);
+            at.max_used = (uint64_t)(rcap * 0.9);
+            at.split = whole ? 0 : 1;
+            at.key_lo = kr.lo;
+            at.key_hi = kr.lo + (kr.span - 1);
             auto global_core = [&](const tpk::QueryDev& q, uint64_t rows) -> tp_status {
                 mark_launch(e);
                 tpk::StageLayout L;
                 if (g_staged && tpk::staged_layout_global(q, stage_all, &L)) {
-                    const uint64_t whole = rows / tpk::ST_TILE * tpk::ST_TILE;
-                    tp_status r = cuda_check(timer.run(st, whole, [&] {
+                    const uint64_t whole_rows = rows / tpk::ST_TILE * tpk::ST_TILE;
+                    tp_status r = cuda_check(timer.run(st, whole_rows, [&] {
                         return tpk::launch_agg_global_staged(q, L, rows, at, gfast, fold, e->num_sms, st);
                     }), "aggregate");
-                    if (r || whole == rows) return r;
+                    if (r || whole_rows == rows) return r;
                     mark_launch(e);  // rows after the last whole tile
-                    return cuda_check(tpk::launch_agg_global(tpk::offset_rows(q, whole), rows - whole, at,
+                    return cuda_check(tpk::launch_agg_global(tpk::offset_rows(q, whole_rows), rows - whole_rows, at,
                                                              e->num_sms, st), "aggregate tail");
                 }
                 return cuda_check(timer.run(st, rows, [&] {
@@ -1275,7 +1474,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             };
             s = for_each_batch(S, sc, global_batch);
             if (s == TP_OK && pj.on) {
-                pj.spill_fact = false;   // a retry re-reads the spilled partitions, it does not spill again
+                pj.spill_fact = false;   // later passes re-read the spilled partitions, they do not spill again
                 s = part_phase2(S, sc, pj, lf, global_batch);
             }
             if (s) return s;
@@ -1286,30 +1485,29 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             if ((s = map_err(err))) return s;
             if (err & tpk::ERR_OVERFLOW) {
                 timer.ev.clear();  // a discarded attempt is not counted
-                if (attempt >= 6) return fail(TP_E_INTERNAL, "aggregation table overflow after retries");
+                if (++attempt > 6) return fail(TP_E_INTERNAL, "aggregation table overflow after retries");
                 // retry with a table sized from what was seen so far (Section 3.3.2:
-                // a task that ran out of memory is retried with a better estimate)
-                const uint64_t seen = std::max<uint64_t>(lane->host_words[1], agg_cap);
+                // a task that ran out of memory is retried with a better estimate);
+                // a table that no longer fits the budget splits the range
+                const uint64_t seen = std::max<uint64_t>(lane->host_words[1], rcap);
                 const uint64_t ncap = pow2_at_least((uint64_t)std::ceil(4.0 * seen / lf));
-                dev_free(e, tab, st);
-                sc.ptrs.erase(std::find(sc.ptrs.begin(), sc.ptrs.end(), tab));
-                const uint64_t extra = align256((ncap + 1) * words * 8) - align256((agg_cap + 1) * words * 8) +
-                                       2 * (align256((ncap + 1) * 12) - align256((agg_cap + 1) * 12)) +
-                                       align256(tpk::radix_sort_hist_words(ncap + 1) * 4);
-                if ((s = reserve(e, extra))) return s;
-                sc.reserved += extra;
-                agg_cap = ncap;
+                drop(tab);
+                gscale *= (double)ncap / (double)rcap;
+                if (whole) agg_cap = ncap;
+                else todo.back().min_cap = ncap;
                 TP_TRY_CUDA(cudaMemsetAsync(misc, 0, 4, st));
                 e->retries++;
                 continue;
             }
-            if (gdirect) {
+            const uint64_t span_end = kr.lo + kr.span;   // wraps to 0 only for a whole 64-bit range
+            uint64_t n = 0;
+            if (rdirect) {
                 // occupied slots are already in key order: count per chunk,
                 // scan, write the rows at their offsets
-                const uint64_t n_chunks = (dspan + tpk::DIRECT_CHUNK - 1) / tpk::DIRECT_CHUNK;
+                const uint64_t n_chunks = (kr.span + tpk::DIRECT_CHUNK - 1) / tpk::DIRECT_CHUNK;
                 void *cnts = nullptr, *offs = nullptr;
                 if ((s = sc.alloc(&cnts, n_chunks * 4)) || (s = sc.alloc(&offs, (n_chunks + 1) * 8))) return s;
-                TP_TRY_CUDA(tpk::launch_direct_count(at, dspan, (uint32_t*)cnts, e->num_sms, st));
+                TP_TRY_CUDA(tpk::launch_direct_count(at, kr.span, (uint32_t*)cnts, e->num_sms, st));
                 TP_TRY_CUDA(tpk::launch_direct_scan((const uint32_t*)cnts, n_chunks, (unsigned long long*)offs, st));
                 mark_launch(e);
                 mark_launch(e);
@@ -1317,48 +1515,51 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
                                             cudaMemcpyDeviceToHost, st));
                 TP_TRY_CUDA(cudaStreamSynchronize(st));
                 e->d2h_bytes += 8;
-                const uint64_t n = lane->host_words[0];
-                tpk::OutDev od;
-                if ((s = alloc_result(e, p, n, &res, &od, S.counters + 1, st))) return s;
-                TP_TRY_CUDA(tpk::launch_direct_emit(at, dspan, (const unsigned long long*)offs, ns, od, gfast,
-                                                    e->num_sms, st));
+                n = lane->host_words[0];
+                if ((s = result_room(n, span_end))) return s;
+                TP_TRY_CUDA(tpk::launch_direct_emit(at, kr.span, (const unsigned long long*)offs, ns,
+                                                    out_at(res_od, res_at, ns), gfast, e->num_sms, st));
                 mark_launch(e);
                 TP_TRY_CUDA(cudaStreamSynchronize(st));
-                res->n_groups = n;
-                p->history_groups = n;
-                timer.collect();
-                break;
+                drop(cnts);
+                drop(offs);
+            } else {
+                // compact occupied slots, sort them by key, gather the rows
+                void *k0 = nullptr, *k1 = nullptr, *v0 = nullptr, *v1 = nullptr, *hist = nullptr;
+                if ((s = sc.alloc(&k0, (rcap + 1) * 8)) || (s = sc.alloc(&k1, (rcap + 1) * 8)) ||
+                    (s = sc.alloc(&v0, (rcap + 1) * 4)) || (s = sc.alloc(&v1, (rcap + 1) * 4)) ||
+                    (s = sc.alloc(&hist, tpk::radix_sort_hist_words(rcap + 1) * 4)))
+                    return s;
+                TP_TRY_CUDA(tpk::launch_compact_global(at, rcap + 1, (uint64_t*)k0, (uint32_t*)v0, S.counters + 1,
+                                                       S.counters + 2, e->num_sms, st));
+                mark_launch(e);
+                TP_TRY_CUDA(cudaMemcpyAsync(lane->host_words, S.counters + 1, 16, cudaMemcpyDeviceToHost, st));
+                TP_TRY_CUDA(cudaStreamSynchronize(st));
+                e->d2h_bytes += 32;
+                n = lane->host_words[0];
+                const uint64_t maxkey = lane->host_words[1];
+                int bits = 0;
+                while (bits < 64 && (maxkey >> bits) != 0) ++bits;
+                uint64_t *kk = (uint64_t*)k0, *tk = (uint64_t*)k1;
+                uint32_t *vv = (uint32_t*)v0, *tv = (uint32_t*)v1;
+                TP_TRY_CUDA(tpk::radix_sort_pairs(&kk, &vv, &tk, &tv, (uint32_t*)hist, n, bits, st));
+                e->launches += 3 * ((bits + 7) / 8);
+                if ((s = result_room(n, span_end))) return s;
+                TP_TRY_CUDA(tpk::launch_gather_global(at, kk, vv, n, ns, out_at(res_od, res_at, ns), e->num_sms,
+                                                      st, gfast));
+                mark_launch(e);
+                TP_TRY_CUDA(cudaStreamSynchronize(st));
+                for (void* ptr : {k0, k1, v0, v1, hist}) drop(ptr);
             }
-            // compact occupied slots, sort them by key, gather the rows
-            void *k0 = nullptr, *k1 = nullptr, *v0 = nullptr, *v1 = nullptr, *hist = nullptr;
-            if ((s = sc.alloc(&k0, (agg_cap + 1) * 8)) || (s = sc.alloc(&k1, (agg_cap + 1) * 8)) ||
-                (s = sc.alloc(&v0, (agg_cap + 1) * 4)) || (s = sc.alloc(&v1, (agg_cap + 1) * 4)) ||
-                (s = sc.alloc(&hist, tpk::radix_sort_hist_words(agg_cap + 1) * 4)))
-                return s;
-            TP_TRY_CUDA(tpk::launch_compact_global(at, agg_cap + 1, (uint64_t*)k0, (uint32_t*)v0, S.counters + 1,
-                                                   S.counters + 2, e->num_sms, st));
-            mark_launch(e);
-            TP_TRY_CUDA(cudaMemcpyAsync(lane->host_words, S.counters + 1, 16, cudaMemcpyDeviceToHost, st));
-            TP_TRY_CUDA(cudaStreamSynchronize(st));
-            e->d2h_bytes += 32;
-            const uint64_t n = lane->host_words[0];
-            const uint64_t maxkey = lane->host_words[1];
-            int bits = 0;
-            while (bits < 64 && (maxkey >> bits) != 0) ++bits;
-            uint64_t *kk = (uint64_t*)k0, *tk = (uint64_t*)k1;
-            uint32_t *vv = (uint32_t*)v0, *tv = (uint32_t*)v1;
-            TP_TRY_CUDA(tpk::radix_sort_pairs(&kk, &vv, &tk, &tv, (uint32_t*)hist, n, bits, st));
-            e->launches += 3 * ((bits + 7) / 8);
-            tpk::OutDev od;
-            if ((s = alloc_result(e, p, n, &res, &od, S.counters + 1, st))) return s;
-            TP_TRY_CUDA(tpk::launch_gather_global(at, kk, vv, n, ns, od, e->num_sms, st, gfast));
-            mark_launch(e);
-            TP_TRY_CUDA(cudaStreamSynchronize(st));
-            res->n_groups = n;
-            p->history_groups = n;
+            res_at += n;
+            drop(tab);
             timer.collect();
-            break;
+            todo.pop_back();
         }
+        e->split_passes += n_ranges - 1;
+        res = res_guard.release();
+        res->n_groups = res_at;
+        p->history_groups = res_at;
     }
     sc.free_all();
     *out = res;

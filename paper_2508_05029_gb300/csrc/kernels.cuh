@@ -128,6 +128,11 @@ struct AggTable {
     unsigned long long* used;   // occupied slots counter (hashed)
     uint64_t max_used;          // beyond this, new keys set ERR_OVERFLOW (hashed)
     uint64_t kmin;              // direct: smallest key
+    // key-range pass of a split aggregation (split != 0): keys outside
+    // [key_lo, key_hi] are skipped, another pass takes them
+    uint64_t key_lo, key_hi;
+    int32_t split;
+    int32_t pad2;
 };
 
 // Output arrays of one result (device memory).

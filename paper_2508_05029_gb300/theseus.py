@@ -97,7 +97,8 @@ class tp_stats(ctypes.Structure):
                 ("pages_total", ctypes.c_uint32), ("agg_kernel_ms", ctypes.c_double),
                 ("agg_kernel_launches", ctypes.c_uint64), ("agg_kernel_rows", ctypes.c_uint64),
                 ("jit_compiles", ctypes.c_uint64), ("jit_failures", ctypes.c_uint64),
-                ("jit_launches", ctypes.c_uint64), ("jit_compile_ms", ctypes.c_double)]
+                ("jit_launches", ctypes.c_uint64), ("jit_compile_ms", ctypes.c_double),
+                ("agg_split_passes", ctypes.c_uint64)]
 
 
 class tp_server_stats(ctypes.Structure):
@@ -369,9 +370,9 @@ class Batch:
         _check(self.eng.lib.tp_debug_batch_stall(self.h, query, wait_ns))
 
     def destroy(self):
-        if self.h:
+        if self.h and self.eng.h:   # tp_shutdown already freed it otherwise
             self.eng.lib.tp_batch_destroy(self.h)
-            self.h = None
+        self.h = None
 
 
 class Server:
@@ -439,9 +440,9 @@ class Table:
         _check(self.eng.lib.tp_table_place(self.h, placement))
 
     def destroy(self):
-        if self.h:
+        if self.h and self.eng.h:   # tp_shutdown already freed it otherwise
             self.eng.lib.tp_table_destroy(self.h)
-            self.h = None
+        self.h = None
 
 
 class Plan:
@@ -454,9 +455,9 @@ class Plan:
         return Result(self.eng, r, self.aggs)
 
     def destroy(self):
-        if self.h:
+        if self.h and self.eng.h:   # tp_shutdown already freed it otherwise
             self.eng.lib.tp_plan_destroy(self.h)
-            self.h = None
+        self.h = None
 
 
 class Result:
@@ -494,9 +495,9 @@ class Result:
         return self._arr(self.eng.lib.tp_result_avg(self.h, agg), np.float64, self.n_groups)
 
     def free(self):
-        if self.h:
+        if self.h and self.eng.h:   # tp_shutdown already freed it otherwise
             self.eng.lib.tp_result_free(self.h)
-            self.h = None
+        self.h = None
 
     def __enter__(self):
         return self

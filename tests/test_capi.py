@@ -65,7 +65,7 @@ def test_struct_layout_matches_c(tmp_path):
         "tp_plan_desc": ["fact", "dim", "filter", "join", "n_group", "group", "n_agg", "aggs",
                          "agg_strategy", "load_factor", "expected_groups", "join_partitions"],
         "tp_stats": ["h2d_bytes", "retries", "pages_in_use", "pages_total", "agg_kernel_rows", "jit_compiles",
-                     "jit_launches", "jit_compile_ms"],
+                     "jit_launches", "jit_compile_ms", "agg_split_passes"],
         "tp_i128": ["lo", "hi"],
         "tp_agg": ["kind", "col_a", "col_b", "k"],
         "tp_table_desc": ["n_cols", "cols", "batch_rows"],
