@@ -54,6 +54,7 @@ class _Query(ctypes.Structure):
         ("n_group", ctypes.c_int32), ("group_side", ctypes.c_int32 * 4),
         ("group_col", ctypes.c_int32 * 4), ("group_bits", ctypes.c_int32 * 4),
         ("n_agg", ctypes.c_int32), ("aggs", _Agg * 8),
+        ("dim_filter_col", ctypes.c_int32), ("dim_filter_lo", ctypes.c_int64), ("dim_filter_hi", ctypes.c_int64),
     ]
 
 
@@ -142,6 +143,11 @@ def run_query(fact: dict, dim: dict | None, query: dict) -> OracleResult:
         q.join_fact_col, q.join_dim_col = -1, -1
     else:
         q.join_fact_col, q.join_dim_col = fnames.index(j["fact_col"]), dnames.index(j["dim_col"])
+    df = query.get("dim_filter")
+    if df is None:
+        q.dim_filter_col, q.dim_filter_lo, q.dim_filter_hi = -1, 0, 0
+    else:
+        q.dim_filter_col, q.dim_filter_lo, q.dim_filter_hi = dnames.index(df["col"]), df["lo"], df["hi"]
     q.n_group = len(query["group"])
     for i, (side, col, bits) in enumerate(query["group"]):
         q.group_side[i] = 0 if side == "fact" else 1

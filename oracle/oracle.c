@@ -7,8 +7,11 @@
  *      lo <= f.filter_col <= hi.
  *   2. Join (Section 3.2, the Adaptive Join; here a PK-FK inner equi-join):
  *      pair f with the unique dimension row d whose key equals f's foreign
- *      key; rows without a partner drop out.  The dimension keys are sorted
- *      and searched by bisection; duplicate keys are an error.
+ *      key; rows without a partner drop out.  A dimension predicate, when
+ *      given, first keeps only dimension rows with lo <= d.col <= hi (the
+ *      predicate whose surviving keys lookahead information passing,
+ *      Section 5, hands to the fact side).  The surviving dimension keys are
+ *      sorted and searched by bisection; duplicates among them are an error.
  *   3. Group and aggregate: the group key concatenates the group fields, the
  *      first field in the highest bits.  Surviving (key, row) pairs are sorted
  *      and each run of equal keys is reduced with exact 128-bit integer sums
@@ -68,6 +71,8 @@ static int32_t validate(const orc_query* q) {
     if (q->join_fact_col >= 0 &&
         (!valid_col(q->join_fact_col, q->n_fact_cols) || !valid_col(q->join_dim_col, q->n_dim_cols)))
         return ORC_INVALID;
+    if (q->dim_filter_col >= 0 && (q->join_fact_col < 0 || !valid_col(q->dim_filter_col, q->n_dim_cols)))
+        return ORC_INVALID;
     for (int g = 0; g < q->n_group; ++g) {
         int bits = q->group_bits[g];
         if (bits < 1 || bits > 64) return ORC_INVALID;
@@ -103,17 +108,24 @@ int32_t orc_run(const orc_query* q, orc_result* out) {
     memset(out, 0, sizeof(*out));
     if (rc != ORC_OK) return rc;
 
-    /* Join side: sort (pk, row) and reject duplicate keys. */
+    /* Join side: keep the dimension rows the predicate admits, sort their
+     * (pk, row) and reject duplicate keys. */
     key_row* dim = NULL;
+    uint64_t n_dim = 0;
     if (q->join_fact_col >= 0 && q->n_dim > 0) {
         dim = (key_row*)malloc(q->n_dim * sizeof(key_row));
         if (!dim) return ORC_NOMEM;
         for (uint64_t i = 0; i < q->n_dim; ++i) {
-            dim[i].key = col_at(&q->dim[q->join_dim_col], i);
-            dim[i].row = i;
+            if (q->dim_filter_col >= 0) {
+                int64_t v = col_at(&q->dim[q->dim_filter_col], i);
+                if (v < q->dim_filter_lo || v > q->dim_filter_hi) continue;
+            }
+            dim[n_dim].key = col_at(&q->dim[q->join_dim_col], i);
+            dim[n_dim].row = i;
+            ++n_dim;
         }
-        qsort(dim, q->n_dim, sizeof(key_row), cmp_key_row_signed);
-        for (uint64_t i = 1; i < q->n_dim; ++i)
+        qsort(dim, n_dim, sizeof(key_row), cmp_key_row_signed);
+        for (uint64_t i = 1; i < n_dim; ++i)
             if (dim[i].key == dim[i - 1].key) { free(dim); return ORC_DUP_KEY; }
     }
 
@@ -129,7 +141,7 @@ int32_t orc_run(const orc_query* q, orc_result* out) {
         int64_t d = -1;
         if (q->join_fact_col >= 0) {
             if (dim == NULL) continue;
-            d = find_dim_row(dim, q->n_dim, col_at(&q->fact[q->join_fact_col], i));
+            d = find_dim_row(dim, n_dim, col_at(&q->fact[q->join_fact_col], i));
             if (d < 0) continue;
         }
         uint64_t key = 0;

@@ -11,7 +11,8 @@
  * 128-bit integers):
  *
  *   R = { (g, aggregates) : f in Fact, d in Dim,
- *         filter_lo <= f.filter_col <= filter_hi, f.fk == d.pk,
+ *         filter_lo <= f.filter_col <= filter_hi,
+ *         dim_filter_lo <= d.dim_filter_col <= dim_filter_hi, f.fk == d.pk,
  *         g = packed(group fields of f and d) }
  *
  * sorted ascending by the packed 64-bit key g.
@@ -58,6 +59,10 @@ typedef struct {
     int32_t group_bits[4];           /* 1..64, total <= 64 */
     int32_t n_agg;                   /* 0..8 */
     orc_agg aggs[8];
+    /* dimension predicate: only dimension rows with lo <= value <= hi join
+     * (and only their keys must be unique); column -1 = every row */
+    int32_t dim_filter_col;
+    int64_t dim_filter_lo, dim_filter_hi;
 } orc_query;
 
 typedef struct {

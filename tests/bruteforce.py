@@ -13,11 +13,14 @@ def evaluate(fact: dict, dim: dict | None, query: dict):
     n_fact = len(next(iter(fact.values()))) if fact else 0
     n_dim = len(next(iter(dim.values()))) if dim else 0
     join = query.get("join")
+    dflt = query.get("dim_filter")
+    # dimension rows the dimension predicate admits (all when there is none)
+    live = [dflt is None or dflt["lo"] <= _val(dim[dflt["col"]], d) <= dflt["hi"] for d in range(n_dim)]
     if join is not None:
         pk = [int(x) for x in dim[join["dim_col"]]] if dim else []
         for a in range(n_dim):
             for b in range(a + 1, n_dim):
-                if pk[a] == pk[b]:
+                if live[a] and live[b] and pk[a] == pk[b]:
                     raise ValueError("dup_key")
     groups = []  # list of [key, count, sums]
     aggs = query["aggs"]
@@ -30,7 +33,7 @@ def evaluate(fact: dict, dim: dict | None, query: dict):
         partners = [None]
         if join is not None:
             fk = _val(fact[join["fact_col"]], i)
-            partners = [d for d in range(n_dim) if pk[d] == fk]
+            partners = [d for d in range(n_dim) if live[d] and pk[d] == fk]
         for d in partners:
             key = 0
             for side, col, bits in query["group"]:

@@ -122,6 +122,41 @@ def test_errors_duplicate_key_and_range():
     assert e.value.status == "invalid"
 
 
+@pytest.mark.parametrize("seed,lo,hi", [
+    (20, 3, 10),            # a band of attribute values
+    (21, 7, 7),             # a single value: inclusive bounds
+    (22, 0, 24),            # every dimension row passes: same as no predicate
+    (23, 30, 40),           # none passes: empty result
+    (24, -5, 2),            # the low edge
+])
+def test_dim_filter_matches_bruteforce(seed, lo, hi):
+    fact, dim = _tiny(seed, 1500, 180, 220)
+    q = dict(W.q_lowcard(), dim_filter=dict(col="attr", lo=lo, hi=hi))
+    got = _check_against_brute(fact, dim, q)
+    live = set(int(k) for k, a in zip(dim["pk"], dim["attr"]) if lo <= a <= hi)
+    want = sum(1 for fk, dt in zip(fact["fk"], fact["date"]) if int(fk) in live and dt <= W.CUTOFF_98)
+    assert int(got.counts.sum()) == want
+    if lo <= 0 and hi >= 24:   # all rows admitted: the query without the predicate
+        plain = oracle.run_query(fact, dim, W.q_lowcard())
+        assert np.array_equal(plain.keys, got.keys) and np.array_equal(plain.sums, got.sums)
+    if lo > 24:
+        assert got.n_groups == 0
+
+
+def test_dim_filter_duplicates_only_among_admitted_rows():
+    fact, dim = _tiny(25, 400, 40, 40)
+    dim["pk"][5] = dim["pk"][6]
+    dim["attr"][5], dim["attr"][6] = 1, 20
+    q = dict(W.q_lowcard(), dim_filter=dict(col="attr", lo=10, hi=24))   # row 5 is out: no clash
+    _check_against_brute(fact, dim, q)
+    q = dict(W.q_lowcard(), dim_filter=dict(col="attr", lo=0, hi=24))    # both in: duplicate key
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.run_query(fact, dim, q)
+    assert e.value.status == "dup_key"
+    with pytest.raises(ValueError, match="dup_key"):
+        bruteforce.evaluate(fact, dim, q)
+
+
 def _modular_closed_form(n_fact, n_dim):
     """Per-group (count, SUM qty, SUM price*(100-disc), SUM disc) on the
     modular dataset, from arithmetic series.  Row i has flag = i mod 3,
@@ -166,6 +201,10 @@ def _torch_int64(fact, dim, query):
     d = {k: torch.from_numpy(np.asarray(v).astype(np.int64)) for k, v in dim.items()}
     flt = query["filter"]
     keep = (f[flt["col"]] >= flt["lo"]) & (f[flt["col"]] <= flt["hi"])
+    dflt = query.get("dim_filter")
+    if dflt is not None:   # drop the dimension rows the predicate rejects
+        dk = (d[dflt["col"]] >= dflt["lo"]) & (d[dflt["col"]] <= dflt["hi"])
+        d = {k: v[dk] for k, v in d.items()}
     pk_sorted, order = torch.sort(d[query["join"]["dim_col"]])
     fk = f[query["join"]["fact_col"]]
     pos = torch.searchsorted(pk_sorted, fk).clamp(max=pk_sorted.numel() - 1)
@@ -192,12 +231,14 @@ def _torch_int64(fact, dim, query):
     return uniq.numpy(), cnt.numpy(), [c.numpy() for c in cols]
 
 
-@pytest.mark.parametrize("maker", ["config1", "config2a"])
+@pytest.mark.parametrize("maker", ["config1", "config2a", "config2a_dimfilter"])
 def test_second_oracle_torch_int64(maker):
     if maker == "config1":
         wl = W.config1(n_fact=300_000, n_dim=10_000)
     else:
         wl = W.config2("a", n_fact=300_000, n_dim=50_000)
+    if maker.endswith("dimfilter"):
+        wl.query["dim_filter"] = dict(col="attr", lo=3, hi=7)
     got = oracle.run(wl)
     keys, cnt, sums = _torch_int64(wl.fact, wl.dim, wl.query)
     assert np.array_equal(got.keys.astype(np.int64), keys)
