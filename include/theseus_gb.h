@@ -225,9 +225,11 @@ enum { TP_SIDE_FACT = 0, TP_SIDE_DIM = 1 };
 enum { TP_AGG_SUM = 0, TP_AGG_SUM_MUL_SUB = 1, TP_AGG_COUNT = 2, TP_AGG_AVG = 3 };
 
 typedef struct {
-    int32_t col;          /* fact column, -1 = no filter */
+    int32_t col;          /* column (fact, or dimension for dim_filter), -1 = no filter */
     int64_t lo, hi;       /* keep rows with lo <= value <= hi (inclusive) */
 } tp_filter;
+
+enum { TP_LIP_AUTO = 0, TP_LIP_OFF = 1, TP_LIP_ON = 2 };
 
 typedef struct {
     int32_t fact_col;     /* fact foreign-key column, -1 = no join */
@@ -276,6 +278,21 @@ typedef struct {
      * pool pages and joined one partition at a time (TP_E_POOL_EMPTY when
      * the pool cannot hold them). */
     int32_t join_partitions;
+    /* Dimension predicate, applied when dim_filter_on != 0 (a zeroed
+     * descriptor has none): only dimension rows with lo <= value <= hi of
+     * dimension column dim_filter.col take part in the join, and only their
+     * keys must be unique. */
+    tp_filter dim_filter;
+    int32_t dim_filter_on;
+    /* Lookahead information passing (Section 5): a blocked Bloom filter of
+     * the keys the dimension predicate admits, built with the join table and
+     * tested on each fact row's key before its probe, and before a
+     * partitioned join spills the row.  TP_LIP_AUTO: with a dimension
+     * predicate, when the join table would not stay in L2 (64 MB or more) or the
+     * join is partitioned; TP_LIP_ON: whenever there is a dimension predicate;
+     * TP_LIP_OFF: never.  Join tables shared through the server's cache and
+     * batched executions run without it.  Results never depend on it. */
+    int32_t lip;
 } tp_plan_desc;
 
 /* Validates and stores a plan.  TP_E_INVALID on any inconsistency. */
@@ -439,6 +456,7 @@ typedef struct {
     uint64_t jit_launches;       /* launches of run-time compiled kernels */
     double jit_compile_ms;       /* host time spent compiling */
     uint64_t agg_split_passes;   /* extra passes of aggregations split by key range to fit the budget */
+    uint64_t lip_filters;        /* lookahead filters built */
 } tp_stats;
 
 /* Message for the last error on this thread ("" if none). */

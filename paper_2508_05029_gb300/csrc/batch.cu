@@ -459,6 +459,13 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
             B.b.n_dfield = nf;
             B.b.jt = jt;
             B.b.err = b->d_err;
+            if (d.dim_filter.col >= 0) {   // the dimension predicate gates the build
+                B.b.has_filter = 1;
+                B.b.fcol.ptr = d.dim->dev_cols[d.dim_filter.col];
+                B.b.fcol.type = d.dim->types[d.dim_filter.col];
+                B.b.flo = d.dim_filter.lo;
+                B.b.fhi = d.dim_filter.hi;
+            }
         }
         // outputs
         const uint64_t G = 1ull << p->key_bits;

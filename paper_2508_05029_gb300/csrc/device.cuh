@@ -112,6 +112,54 @@ __device__ __forceinline__ void atomic_add_i128(uint64_t* lo, uint64_t* hi, I128
     if (h != 0) atomicAdd((unsigned long long*)hi, (unsigned long long)h);
 }
 
+// ------------------------------------------------------ lookahead filter
+//
+// Lookahead information passing (Section 5): the keys of the dimension rows
+// that pass the dimension predicate go into a blocked Bloom filter, and fact
+// rows test their key before the probe (and before a partitioned join spills
+// them).  With h = fmix64(key), the top bits of h pick one 256-bit block (an
+// aligned 32-byte sector) and word w of the block holds bit
+// (lo32(h) * M_w) >> 27 with the odd multiplier M_w = 0x9E3779B1 * (2w + 1).
+// A test reads one sector; an inserted key always passes.
+
+__device__ __forceinline__ uint32_t lip_bit(uint32_t h, uint32_t w) {
+    return 1u << ((h * (0x9E3779B1u * (2u * w + 1u))) >> 27);
+}
+
+__device__ __forceinline__ bool lip_test(const JoinTable& jt, int64_t key) {
+    const uint64_t h = fmix64((uint64_t)key);
+    const uint4* blk = reinterpret_cast<const uint4*>(jt.lip + ((h >> jt.lip_shift) << 3));
+    const uint4 a = __ldg(blk), b = __ldg(blk + 1);
+    const uint32_t l = (uint32_t)h;
+    const uint32_t miss = (~a.x & lip_bit(l, 0)) | (~a.y & lip_bit(l, 1)) | (~a.z & lip_bit(l, 2)) |
+                          (~a.w & lip_bit(l, 3)) | (~b.x & lip_bit(l, 4)) | (~b.y & lip_bit(l, 5)) |
+                          (~b.z & lip_bit(l, 6)) | (~b.w & lip_bit(l, 7));
+    return miss == 0;
+}
+
+__device__ __forceinline__ void lip_insert(const JoinTable& jt, int64_t key) {
+    const uint64_t h = fmix64((uint64_t)key);
+    uint32_t* blk = jt.lip + ((h >> jt.lip_shift) << 3);
+#pragma unroll
+    for (uint32_t w = 0; w < 8; ++w) atomicOr(blk + w, lip_bit((uint32_t)h, w));
+}
+
+// Clears bit j of pm for rows whose key the lookahead filter rules out.
+template <int N>
+__device__ __forceinline__ void lip_mask(const JoinTable& jt, const int64_t* key, uint32_t& pm) {
+    if (jt.lip == nullptr) return;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        if (((pm >> j) & 1u) && !lip_test(jt, key[j])) pm &= ~(1u << j);
+}
+
+// Does dimension row i pass the dimension predicate?
+__device__ __forceinline__ bool dim_row_admitted(const BuildDev& b, uint64_t i) {
+    if (!b.has_filter) return true;
+    const int64_t v = ld1(b.fcol, i);
+    return v >= b.flo && v <= b.fhi;
+}
+
 // ------------------------------------------------------------------ probing
 
 // Partitioned joins: does this key's partition have its rows in the table?
@@ -132,6 +180,10 @@ __device__ __forceinline__ T ld_table(const T* p) {
 template <bool NC = true>
 __device__ __forceinline__ void probe4(const JoinTable& jt, const int64_t key[4], bool pass[4],
                                        uint32_t payload[4], uint32_t* err) {
+    if (jt.lip != nullptr) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) pass[i] = pass[i] && lip_test(jt, key[i]);
+    }
     if (jt.part_shift != 0) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) pass[i] = pass[i] && part_resident(jt, key[i]);
@@ -402,7 +454,9 @@ __device__ __forceinline__ void final_dense_block(const uint64_t* __restrict__ g
 // key and payload in one word), ERR_DUP on a repeated key.
 __device__ __forceinline__ void build_insert(const BuildDev& b, uint64_t i) {
     const JoinTable& jt = b.jt;
+    if (!dim_row_admitted(b, i)) return;
     int64_t key = ld1(b.key, i);
+    if (jt.lip != nullptr) lip_insert(jt, key);
     // Dimension group fields packed into bits 0..30 of the payload; bit 31
     // marks a row with a field outside its width.  That is an error only
     // if a surviving fact row joins to it, which the probe side reports.

@@ -598,6 +598,7 @@ tp_status tp_stats_get(tp_engine* e, tp_stats* s) {
     s->jit_launches = e->jit_launches;
     s->jit_compile_ms = (double)e->jit_us.load() / 1000.0;
     s->agg_split_passes = e->split_passes;
+    s->lip_filters = e->lip_filters;
     {
         std::lock_guard<std::mutex> lk(e->time_mu);
         s->agg_kernel_ms = e->agg_ms;

@@ -162,34 +162,51 @@ tp_status cuda_check(cudaError_t e, const char* what) {
 
 // ----------------------------------------------------------------- build
 
-tp_status build_join(ExecState& S, Scratch& sc) {
-    tp_engine* e = S.e;
+// Build-side parameters of the plan without columns: group fields packed
+// into the payload, the dimension predicate's bounds.
+tpk::BuildDev build_proto(const ExecState& S) {
     const tp_plan_desc& d = S.p->d;
-    cudaStream_t st = S.lane->compute;
     tpk::BuildDev b{};
     b.jt = S.jt;
     b.err = S.err;
     int nf = 0;
-    std::vector<int> bcols = {d.join.dim_col};
     for (int g = 0; g < d.n_group; ++g) {
         if (d.group[g].side != TP_SIDE_DIM) continue;
         b.dbits[nf] = d.group[g].bits;
         b.dpos[nf] = S.p->gdpos[g];
-        bcols.push_back(d.group[g].col);
         ++nf;
     }
     b.n_dfield = nf;
+    b.has_filter = d.dim_filter.col >= 0;
+    b.flo = d.dim_filter.lo;
+    b.fhi = d.dim_filter.hi;
+    return b;
+}
+
+// Calls fn(build, rows) for every batch of the dimension table with the key,
+// group-field and predicate columns on the device.
+template <class F>
+tp_status for_each_dim_batch(ExecState& S, Scratch& sc, const tpk::BuildDev& proto, F&& fn) {
+    tp_engine* e = S.e;
+    const tp_plan_desc& d = S.p->d;
     tp_table* t = S.dim;
+    std::vector<int> bcols = {d.join.dim_col};
+    for (int g = 0; g < d.n_group; ++g)
+        if (d.group[g].side == TP_SIDE_DIM) bcols.push_back(d.group[g].col);
+    const int nf = (int)bcols.size() - 1;
+    if (d.dim_filter.col >= 0) bcols.push_back(d.dim_filter.col);
+    tpk::BuildDev b = proto;
+    auto bind = [&](const std::vector<const void*>& ptr) {
+        b.key = devcol(t, bcols[0], ptr[0]);
+        for (int k = 1; k <= nf; ++k) b.dcol[k - 1] = devcol(t, bcols[k], ptr[k]);
+        if (d.dim_filter.col >= 0) b.fcol = devcol(t, bcols[nf + 1], ptr[nf + 1]);
+    };
     if (t->placement != PL_PAGES) {
-        b.key = devcol(t, d.join.dim_col, t->dev_cols[d.join.dim_col]);
-        int k = 0;
-        for (int g = 0; g < d.n_group; ++g)
-            if (d.group[g].side == TP_SIDE_DIM) { b.dcol[k] = devcol(t, d.group[g].col, t->dev_cols[d.group[g].col]); ++k; }
-        tp_status s = cuda_check(tpk::launch_build(b, t->rows, e->num_sms, st), "build");
-        mark_launch(e);
-        return s;
+        std::vector<const void*> ptr;
+        for (int c : bcols) ptr.push_back(t->dev_cols[c]);
+        bind(ptr);
+        return fn(b, t->rows);
     }
-    // paged dimension: copy each batch's key and field columns, then insert
     uint64_t max_rows = 0;
     for (auto& bt : t->batches) max_rows = std::max(max_rows, bt.rows);
     std::vector<void*> stage(bcols.size(), nullptr), enc(bcols.size(), nullptr);
@@ -202,20 +219,27 @@ tp_status build_join(ExecState& S, Scratch& sc) {
     }
     for (auto& bt : t->batches) {
         for (size_t i = 0; i < bcols.size(); ++i) {
-            tp_status s = copy_batch_column(e, t, bt, bcols[i], stage[i], enc[i], 0, st);
+            tp_status s = copy_batch_column(e, t, bt, bcols[i], stage[i], enc[i], 0, S.lane->compute);
             if (s) return s;
         }
         if (narrow) {
-            tp_status s = widen_batch(e, t, bt, bcols, stage, enc, 0, st);
+            tp_status s = widen_batch(e, t, bt, bcols, stage, enc, 0, S.lane->compute);
             if (s) return s;
         }
-        b.key = devcol(t, bcols[0], stage[0]);
-        for (int k = 0; k < nf; ++k) b.dcol[k] = devcol(t, bcols[1 + k], stage[1 + k]);
-        tp_status s = cuda_check(tpk::launch_build(b, bt.rows, e->num_sms, st), "build");
-        mark_launch(e);
+        bind(std::vector<const void*>(stage.begin(), stage.end()));
+        tp_status s = fn(b, bt.rows);
         if (s) return s;
     }
     return TP_OK;
+}
+
+tp_status build_join(ExecState& S, Scratch& sc) {
+    tp_engine* e = S.e;
+    cudaStream_t st = S.lane->compute;
+    return for_each_dim_batch(S, sc, build_proto(S), [&](const tpk::BuildDev& b, uint64_t rows) {
+        mark_launch(e);
+        return cuda_check(tpk::launch_build(b, rows, e->num_sms, st), "build");
+    });
 }
 
 // ------------------------------------------------------- fact batch driver
@@ -380,6 +404,38 @@ tp_status sample_selectivity(ExecState& S) {
     return TP_OK;
 }
 
+// Pass rate of the dimension predicate on 4096 evenly spaced dimension rows
+// (sizes the lookahead filter).
+tp_status sample_dim_selectivity(ExecState& S) {
+    tp_plan* p = S.p;
+    const tp_plan_desc& d = p->d;
+    tp_table* t = S.dim;
+    const uint32_t samples = 4096;
+    if (d.dim_filter.col < 0 || !t || t->rows == 0) { p->dim_selectivity = 1.0; return TP_OK; }
+    const int c = d.dim_filter.col;
+    if (t->placement == PL_PAGES) {
+        uint64_t pass = 0;
+        for (uint32_t j = 0; j < samples; ++j) {
+            const int64_t v = paged_value(t, c, (uint64_t)(((unsigned __int128)j * t->rows) / samples));
+            pass += (v >= d.dim_filter.lo && v <= d.dim_filter.hi);
+        }
+        p->dim_selectivity = (double)pass / samples;
+        return TP_OK;
+    }
+    tpk::QueryDev q{};
+    q.fcol = devcol(t, c, t->dev_cols[c]);
+    q.flo = d.dim_filter.lo;
+    q.fhi = d.dim_filter.hi;
+    cudaStream_t st = S.lane->compute;
+    TP_TRY_CUDA(cudaMemsetAsync(S.counters + 3, 0, sizeof(unsigned long long), st));
+    TP_TRY_CUDA(tpk::launch_sample_filter(q, t->rows, samples, S.counters + 3, st));
+    mark_launch(S.e);
+    TP_TRY_CUDA(cudaMemcpyAsync(S.lane->host_words, S.counters + 3, 8, cudaMemcpyDeviceToHost, st));
+    TP_TRY_CUDA(cudaStreamSynchronize(st));
+    p->dim_selectivity = (double)S.lane->host_words[0] / samples;
+    return TP_OK;
+}
+
 tp_status map_err(uint32_t err) {
     if (err & tpk::ERR_DUP) return fail(TP_E_DUP_KEY, "join build side holds a duplicate key");
     if (err & tpk::ERR_RANGE) return fail(TP_E_RANGE, "a group field value does not fit its bit width");
@@ -522,6 +578,13 @@ tpk::OutDev out_at(tpk::OutDev od, uint64_t at, int n_sum) {
 constexpr uint64_t DIRECT_AGG_MAX_SLOTS = 1ull << 27;
 constexpr uint64_t DIRECT_AGG_ALWAYS = 1ull << 20;
 
+// Lookahead filter: used automatically when the join table takes at least
+// this; LIP_BITS_PER_KEY filter bits per expected admitted key, at most
+// LIP_MAX_BLOCKS 32-byte blocks (32 MB, a quarter of L2).
+constexpr uint64_t LIP_TABLE_BYTES = 64ull << 20;
+constexpr double LIP_BITS_PER_KEY = 16.0;
+constexpr uint64_t LIP_MAX_BLOCKS = 1ull << 20;
+
 // A global aggregation whose table cannot be reserved runs as passes over
 // disjoint ranges of the packed group key, each range halved until its table
 // fits (Section 3.3.2: a task that runs out of memory is divided up and
@@ -634,53 +697,6 @@ tp_status append_device_rows(tp_engine* e, tp_table* t, const std::vector<const 
     return TP_OK;
 }
 
-// Calls fn(build, rows) for every batch of the dimension table with the key
-// and group-field columns on the device.
-template <class F>
-tp_status for_each_dim_batch(ExecState& S, Scratch& sc, const tpk::BuildDev& proto, F&& fn) {
-    tp_engine* e = S.e;
-    const tp_plan_desc& d = S.p->d;
-    tp_table* t = S.dim;
-    std::vector<int> bcols = {d.join.dim_col};
-    for (int g = 0; g < d.n_group; ++g)
-        if (d.group[g].side == TP_SIDE_DIM) bcols.push_back(d.group[g].col);
-    tpk::BuildDev b = proto;
-    auto bind = [&](const std::vector<const void*>& ptr) {
-        b.key = devcol(t, bcols[0], ptr[0]);
-        for (int k = 1; k < (int)bcols.size(); ++k) b.dcol[k - 1] = devcol(t, bcols[k], ptr[k]);
-    };
-    if (t->placement != PL_PAGES) {
-        std::vector<const void*> ptr;
-        for (int c : bcols) ptr.push_back(t->dev_cols[c]);
-        bind(ptr);
-        return fn(b, t->rows);
-    }
-    uint64_t max_rows = 0;
-    for (auto& bt : t->batches) max_rows = std::max(max_rows, bt.rows);
-    std::vector<void*> stage(bcols.size(), nullptr), enc(bcols.size(), nullptr);
-    const bool narrow = has_narrow(t);
-    for (size_t i = 0; i < bcols.size(); ++i) {
-        tp_status s = sc.alloc(&stage[i], align256(max_rows * type_size(t->types[bcols[i]])));
-        const int w = narrow ? narrow_width_max(t, bcols[i]) : 0;
-        if (!s && w) s = sc.alloc(&enc[i], align256(max_rows * (uint64_t)w));
-        if (s) return s;
-    }
-    for (auto& bt : t->batches) {
-        for (size_t i = 0; i < bcols.size(); ++i) {
-            tp_status s = copy_batch_column(e, t, bt, bcols[i], stage[i], enc[i], 0, S.lane->compute);
-            if (s) return s;
-        }
-        if (narrow) {
-            tp_status s = widen_batch(e, t, bt, bcols, stage, enc, 0, S.lane->compute);
-            if (s) return s;
-        }
-        bind(std::vector<const void*>(stage.begin(), stage.end()));
-        tp_status s = fn(b, bt.rows);
-        if (s) return s;
-    }
-    return TP_OK;
-}
-
 // Histogram of the build keys, residency by table budget, the resident table
 // (into S.jt, with the partition filter) and the build-side spill.
 tp_status part_setup(ExecState& S, Scratch& sc, PartJoin& pj, uint64_t table_budget, float lf,
@@ -704,7 +720,7 @@ tp_status part_setup(ExecState& S, Scratch& sc, PartJoin& pj, uint64_t table_bud
     if (table_bytes(S.dim->rows) > table_budget) {
         s = for_each_dim_batch(S, sc, proto, [&](const tpk::BuildDev& b, uint64_t rows) {
             mark_launch(e);
-            return cuda_check(tpk::launch_part_hist(b.key, rows, pj.shift, pj.counts, e->num_sms, st),
+            return cuda_check(tpk::launch_part_hist(b, rows, pj.shift, pj.counts, e->num_sms, st),
                               "partition");
         });
         if (s) return s;
@@ -766,7 +782,7 @@ tp_status part_setup(ExecState& S, Scratch& sc, PartJoin& pj, uint64_t table_bud
         mark_launch(e);
         if (!pj.spill_mask) return cuda_check(tpk::launch_build(b, rows, e->num_sms, st), "build");
         TP_TRY_CUDA(cudaMemsetAsync(pj.counts, 0, 2 * 8 * (uint64_t)P, st));
-        TP_TRY_CUDA(tpk::launch_part_hist(b.key, rows, pj.shift, pj.counts, e->num_sms, st));
+        TP_TRY_CUDA(tpk::launch_part_hist(b, rows, pj.shift, pj.counts, e->num_sms, st));
         std::vector<unsigned long long> bc(P), base(P, 0);
         TP_TRY_CUDA(cudaMemcpyAsync(bc.data(), pj.counts, 8 * (uint64_t)P, cudaMemcpyDeviceToHost, st));
         TP_TRY_CUDA(cudaStreamSynchronize(st));
@@ -962,6 +978,11 @@ std::string cache_key(const ExecState& S) {
     snprintf(buf, sizeof(buf), "%p:%d:%d:%d:%.4f", (const void*)S.dim, d.join.dim_col, S.jt.direct, S.key64 ? 1 : 0,
              (double)S.p->load_factor);
     std::string k = buf;
+    if (d.dim_filter.col >= 0) {
+        snprintf(buf, sizeof(buf), "|f%d:%lld:%lld", d.dim_filter.col, (long long)d.dim_filter.lo,
+                 (long long)d.dim_filter.hi);
+        k += buf;
+    }
     for (int g = 0; g < d.n_group; ++g) {
         if (d.group[g].side != TP_SIDE_DIM) continue;
         snprintf(buf, sizeof(buf), "|%d:%d:%d", d.group[g].col, d.group[g].bits, S.p->gdpos[g]);
@@ -1081,6 +1102,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
     // ---- filter selectivity from a sample, once per plan (decides eager loads
     // and the first size estimate of a global aggregation table)
     if (p->selectivity < 0 && (s = sample_selectivity(S))) return s;
+    if (S.dim && p->dim_selectivity < 0 && (s = sample_dim_selectivity(S))) return s;
     S.eager = p->selectivity >= 0.25;
     // ---- reservation estimate (Section 3.3.2): streaming buffers and the
     // aggregation table first; a hashed join table that would crowd what is
@@ -1127,7 +1149,9 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         }
         est += agg_est;
     }
-    uint64_t join_bytes = 0;
+    uint64_t join_bytes = 0, full_join_bytes = 0;
+    const bool lip_possible = S.dim && d.dim_filter.col >= 0 && d.lip != TP_LIP_OFF;
+    uint64_t lip_blocks = 0, lip_bytes = 0;   // lookahead filter size, when possible
     PartJoin pj;
     uint64_t part_table_budget = 0;
     if (S.dim) {
@@ -1142,8 +1166,17 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             S.join_cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(S.dim->rows / lf)));
             join_bytes = S.join_cap * (S.key64 ? 16 : 8);
         }
-        const uint64_t dim_stage =
+        full_join_bytes = join_bytes;
+        if (lip_possible) {
+            const double keys = std::ceil((double)S.dim->rows * p->dim_selectivity * 1.5) + 1024;
+            lip_blocks = pow2_at_least((uint64_t)std::ceil(keys * LIP_BITS_PER_KEY / 256.0));
+            lip_blocks = std::min<uint64_t>(std::max<uint64_t>(lip_blocks, 2), LIP_MAX_BLOCKS);
+            lip_bytes = lip_blocks * 32;
+        }
+        uint64_t dim_stage =
             S.dim->placement == PL_PAGES ? (has_narrow(S.dim) ? 6 : 4) * align256(S.dim->batch_rows * 8) : 0;
+        if (S.dim->placement == PL_PAGES && d.dim_filter.col >= 0)   // the predicate column's staging
+            dim_stage += (has_narrow(S.dim) ? 2 : 1) * align256(S.dim->batch_rows * 8);
         if (!S.jt.direct) {  // hybrid hash join when the table would crowd the budget
             uint64_t reserved_now = 0, cap_now = 0;
             tp_budget_query(e, &reserved_now, &cap_now);
@@ -1153,7 +1186,8 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             const uint64_t rg = std::max<uint64_t>(1, result_groups);
             const uint64_t result_est =
                 2 * align256(rg * 8) + ns * align256(rg * 16) + (uint64_t)n_avg * align256(rg * 8);
-            const uint64_t taken = reserved_now + est + dim_stage + result_est;
+            // room for the lookahead filter too, when the plan may use one
+            const uint64_t taken = reserved_now + est + dim_stage + result_est + (lip_possible ? lip_bytes : 0);
             const uint64_t avail = cap_now > taken ? cap_now - taken : 0;
             const int jp = d.join_partitions;
             if (jp > 1 || (jp == 0 && join_bytes > avail / 2)) {
@@ -1182,6 +1216,26 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
     est -= agg_est;   // the global table is reserved per key range
     if ((s = reserve(e, est))) return s;
     sc.reserved += est;
+    // ---- lookahead filter (Section 5): with a dimension predicate, when the
+    // join table would not stay in L2 or the join is partitioned (or asked
+    // for); tables shared through the cache go without.  Optional: when its
+    // reservation is refused the query runs without it.
+    if (lip_possible && !(cache && !pj.on) &&
+        (d.lip == TP_LIP_ON || pj.on || full_join_bytes >= LIP_TABLE_BYTES)) {
+        if (reserve(e, lip_bytes) == TP_OK) {
+            sc.reserved += lip_bytes;
+            void* lip = nullptr;
+            if ((s = sc.alloc(&lip, lip_bytes))) return s;
+            TP_TRY_CUDA(cudaMemsetAsync(lip, 0, lip_bytes, st));
+            int lg = 0;
+            while ((1ull << lg) < lip_blocks) ++lg;
+            S.jt.lip = (uint32_t*)lip;
+            S.jt.lip_shift = 64 - lg;
+            e->lip_filters++;
+        } else {
+            clear_error();
+        }
+    }
     // ---- join table
     CacheUse cu;
     if (S.dim && cache && !pj.on) {
@@ -1204,16 +1258,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
                                 : (uint32_t*)((uint8_t*)misc + 128);
         S.jt.key64 = S.key64 ? 1 : 0;
         if (pj.on) {
-            tpk::BuildDev proto{};
-            proto.err = S.err;
-            int nf = 0;
-            for (int g = 0; g < d.n_group; ++g) {
-                if (d.group[g].side != TP_SIDE_DIM) continue;
-                proto.dbits[nf] = d.group[g].bits;
-                proto.dpos[nf] = p->gdpos[g];
-                ++nf;
-            }
-            proto.n_dfield = nf;
+            const tpk::BuildDev proto = build_proto(S);
             if ((s = part_setup(S, sc, pj, part_table_budget, lf, proto))) return s;
         } else if (cu.building) {
             if ((s = cache_publish(S, sc, cache, &cu))) return s;
@@ -1707,7 +1752,8 @@ std::string shape_struct(const std::string& name, const tpk::QueryDev& q, const 
     r += "    static constexpr int filter = " + std::to_string(q.has_filter ? 1 : 0) +
          ", ftype = " + std::to_string(q.has_filter ? q.fcol.type : 0) + ", join = " + std::to_string(join) +
          ", ktype = " + std::to_string(q.has_join ? q.fk.type : 0) +
-         ", part = " + std::to_string(q.has_join && q.jt.part_shift != 0 ? 1 : 0) + ";\n";
+         ", part = " + std::to_string(q.has_join && q.jt.part_shift != 0 ? 1 : 0) +
+         ", lip = " + std::to_string(q.has_join && q.jt.lip != nullptr ? 1 : 0) + ";\n";
     r += "    static constexpr int ng = " + std::to_string(q.n_group) + ";\n";
     r += "    static constexpr int " + arr("gside", gside, tpk::MAX_GROUP) + ", " + arr("gtype", gtype, tpk::MAX_GROUP) +
          ", " + arr("gbits", gbits, tpk::MAX_GROUP) + ";\n";
@@ -1797,12 +1843,16 @@ tp_status tp_plan_create(tp_engine* e, const tp_plan_desc* d, tp_plan** out) {
     } else if (d->join.fact_col != -1) {
         return fail(TP_E_INVALID, "plan: bad join fact column");
     }
+    if (d->dim_filter_on && (!join || !valid_col(d->dim, d->dim_filter.col)))
+        return fail(TP_E_INVALID, "plan: bad dimension predicate column");
+    if (d->lip < TP_LIP_AUTO || d->lip > TP_LIP_ON) return fail(TP_E_INVALID, "plan: bad lip mode");
     if (d->n_group < 0 || d->n_group > 4) return fail(TP_E_INVALID, "plan: 0..4 group fields");
     if (d->n_agg < 1 || d->n_agg > 8) return fail(TP_E_INVALID, "plan: 1..8 aggregates");
     std::unique_ptr<tp_plan> p(new (std::nothrow) tp_plan());
     if (!p) return fail(TP_E_NOMEM, "plan: out of host memory");
     p->eng = e;
     p->d = *d;
+    if (!d->dim_filter_on) p->d.dim_filter.col = -1;   // internally: col < 0 = no predicate
     int key_bits = 0, dim_bits = 0;
     for (int g = 0; g < d->n_group; ++g) {
         const tp_group_field& gf = d->group[g];

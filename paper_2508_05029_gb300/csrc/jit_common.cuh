@@ -12,6 +12,7 @@
 //   filter, ftype            filter present; its column type (T_*)
 //   join, ktype              J_NONE / J_DIRECT / J_HASH32 / J_HASH64; fk type
 //   part                     partition filter on the join (hybrid join)
+//   lip                      lookahead (Bloom) filter tested before the probe
 //   ng, gside[], gtype[], gbits[]   group fields, first field highest
 //   ns, skind[], atype[], btype[]   sums: S_SUM / S_MUL_SUB and column types
 //   mode[]                   1: low word, 2: low + carry word (fast), 0: exact
@@ -229,6 +230,13 @@ __device__ __forceinline__ void consume(const QueryDev& q, const Flt& flt, const
     uint32_t pay[ST_RPL];
 #pragma unroll
     for (int j = 0; j < ST_RPL; ++j) pay[j] = 0;
+    if constexpr (S::join != J_NONE && S::lip) {
+        int64_t key[ST_RPL];
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) key[j] = (int64_t)c.template ld<S::ktype, CI_K>(r0, j);
+        lip_mask<ST_RPL>(q.jt, key, pm);
+        if (!pm) return;
+    }
     if constexpr (S::join == J_DIRECT) {
         const unsigned int* dt = (const unsigned int*)q.jt.slots;
 #pragma unroll

@@ -75,6 +75,12 @@ struct JoinTable {
     uint64_t part_mask;
     int32_t part_shift;
     int32_t pad2;
+    // lookahead filter (lip != nullptr): a blocked Bloom filter of the
+    // admitted build keys, 8 words per block; a key's block is
+    // fmix64(key) >> lip_shift
+    uint32_t* lip;
+    int32_t lip_shift;
+    int32_t pad3;
 };
 
 // The query as the per-batch kernels see it.  Column pointers address the
@@ -112,6 +118,10 @@ struct BuildDev {
     int32_t dpos[MAX_GROUP];
     JoinTable jt;
     uint32_t* err;
+    DevCol fcol;            // dimension predicate: rows outside [flo, fhi] do not join
+    int64_t flo, fhi;
+    int32_t has_filter;
+    int32_t pad2;
 };
 
 // Global aggregation table: slot = {key, count, (lo, hi) per sum}, EMPTY key =
@@ -334,9 +344,10 @@ cudaError_t launch_agg_global_staged(const QueryDev& q, const StageLayout& L, ui
 // ------------------------------------------------------- partitioned join
 //
 // Partition of a join key: the top log2(P) bits of fmix64(key), for every key
-// width.  counts[p] += rows of partition p (keys from `key`, rows passing
-// the query's filter when q is given).
-cudaError_t launch_part_hist(const DevCol& key, uint64_t n, int shift, unsigned long long* counts, int num_sms,
+// width.  counts[p] += rows of partition p (build rows the dimension
+// predicate admits; fact rows passing the query's filter and the lookahead
+// filter).
+cudaError_t launch_part_hist(const BuildDev& b, uint64_t n, int shift, unsigned long long* counts, int num_sms,
                              cudaStream_t st);
 cudaError_t launch_part_hist_fact(const QueryDev& q, uint64_t n, int shift, uint64_t spill_mask,
                                   unsigned long long* counts, int num_sms, cudaStream_t st);

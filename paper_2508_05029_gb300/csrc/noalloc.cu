@@ -102,10 +102,18 @@ extern "C" tp_status tp_execute_noalloc(const tp_plan_desc* d, const void* const
     }
     if (d->filter.col != -1 && !col_ok(d->filter.col, n_fact_cols))
         return fail(TP_E_INVALID, "tp_execute_noalloc: bad filter column");
+    if (d->dim_filter_on && (!join || !col_ok(d->dim_filter.col, n_dim_cols)))
+        return fail(TP_E_INVALID, "tp_execute_noalloc: bad dimension predicate column");
     if (d->n_group < 0 || d->n_group > 4 || d->n_agg < 1 || d->n_agg > 8)
         return fail(TP_E_INVALID, "tp_execute_noalloc: 0..4 group fields and 1..8 aggregates");
     tpk::QueryDev q{};
     tpk::BuildDev b{};
+    if (d->dim_filter_on) {   // only admitted dimension rows are inserted
+        b.has_filter = 1;
+        b.flo = d->dim_filter.lo;
+        b.fhi = d->dim_filter.hi;
+        if (n_dim) b.fcol = dcol(dim_cols, dim_types, d->dim_filter.col);
+    }
     int key_bits = 0, dim_bits = 0, nf = 0;
     for (int g = 0; g < d->n_group; ++g) {
         const tp_group_field& gf = d->group[g];

@@ -17,26 +17,26 @@ __device__ __forceinline__ uint32_t part_of(int64_t key, int shift) {
     return (uint32_t)(fmix64((uint64_t)key) >> shift);
 }
 
-// Per-block shared histogram, merged into counts.
-__global__ void k_part_hist(const __grid_constant__ DevCol key, uint64_t n, int shift, unsigned long long* counts) {
+// Per-block shared histogram of the admitted build rows, merged into counts.
+__global__ void k_part_hist(const __grid_constant__ BuildDev b, uint64_t n, int shift, unsigned long long* counts) {
     __shared__ unsigned h[256];
     const uint32_t P = 1u << (64 - shift);
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) h[i] = 0;
     __syncthreads();
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        atomicAdd(&h[part_of(ld1(key, i), shift)], 1u);
+        if (dim_row_admitted(b, i)) atomicAdd(&h[part_of(ld1(b.key, i), shift)], 1u);
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
         if (h[i]) atomicAdd(&counts[i], (unsigned long long)h[i]);
 }
 
-cudaError_t launch_part_hist(const DevCol& key, uint64_t n, int shift, unsigned long long* counts, int num_sms,
+cudaError_t launch_part_hist(const BuildDev& b, uint64_t n, int shift, unsigned long long* counts, int num_sms,
                              cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     if (shift < 56 || shift > 63) return cudaErrorInvalidValue;   // 2..256 partitions
     uint64_t blocks = (n + 255) / 256;
     if (blocks > (uint64_t)num_sms * 4) blocks = (uint64_t)num_sms * 4;
-    k_part_hist<<<(unsigned)blocks, 256, 0, st>>>(key, n, shift, counts);
+    k_part_hist<<<(unsigned)blocks, 256, 0, st>>>(b, n, shift, counts);
     return cudaGetLastError();
 }
 
@@ -46,7 +46,8 @@ __device__ __forceinline__ bool fact_row_passes(const QueryDev& q, uint64_t i) {
     return v >= q.flo && v <= q.fhi;
 }
 
-// Fact rows that pass the filter and fall in a spilled partition, per partition.
+// Fact rows that pass the filter and the lookahead filter and fall in a
+// spilled partition, per partition.
 __global__ void k_part_hist_fact(const __grid_constant__ QueryDev q, uint64_t n, int shift, uint64_t spill_mask,
                                  unsigned long long* counts) {
     __shared__ unsigned h[256];
@@ -55,8 +56,9 @@ __global__ void k_part_hist_fact(const __grid_constant__ QueryDev q, uint64_t n,
     __syncthreads();
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         if (!fact_row_passes(q, i)) continue;
-        const uint32_t p = part_of(ld1(q.fk, i), shift);
-        if ((spill_mask >> p) & 1ull) atomicAdd(&h[p], 1u);
+        const int64_t key = ld1(q.fk, i);
+        const uint32_t p = part_of(key, shift);
+        if (((spill_mask >> p) & 1ull) && (q.jt.lip == nullptr || lip_test(q.jt, key))) atomicAdd(&h[p], 1u);
     }
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < P; i += blockDim.x)
@@ -82,7 +84,8 @@ constexpr int SP_THREADS = 512;
 constexpr int SP_RPT = 4;                          // rows per thread per tile
 constexpr int SP_TILE = SP_THREADS * SP_RPT;
 
-// Build rows: insert the resident partitions, spill the others as pairs.
+// Admitted build rows: insert the resident partitions, spill the others as
+// pairs; every admitted key enters the lookahead filter.
 __global__ void __launch_bounds__(SP_THREADS)
     k_build_part(const __grid_constant__ BuildDev b, uint64_t n, const unsigned long long* base,
                  unsigned long long* cursor, int64_t* keys, uint32_t* pays) {
@@ -98,12 +101,13 @@ __global__ void __launch_bounds__(SP_THREADS)
         for (int k = 0; k < SP_RPT; ++k) {
             const uint64_t i = t0 + (uint64_t)k * SP_THREADS + threadIdx.x;
             spill[k] = false;
-            if (i >= n) continue;
+            if (i >= n || !dim_row_admitted(b, i)) continue;
             const int64_t key = ld1(b.key, i);
             part[k] = part_of(key, jt.part_shift);
             if ((jt.part_mask >> part[k]) & 1ull) {
                 build_insert(b, i);
             } else {
+                if (jt.lip != nullptr) lip_insert(jt, key);
                 spill[k] = true;
                 rank[k] = atomicAdd(&cnt[part[k]], 1u);
             }
@@ -213,8 +217,10 @@ __global__ void __launch_bounds__(SP_THREADS)
             const uint64_t i = t0 + (uint64_t)k * SP_THREADS + threadIdx.x;
             spill[k] = false;
             if (i >= n || !fact_row_passes(q, i)) continue;
-            part[k] = part_of(ld1(q.fk, i), shift);
+            const int64_t key = ld1(q.fk, i);
+            part[k] = part_of(key, shift);
             if (!((spill_mask >> part[k]) & 1ull)) continue;
+            if (q.jt.lip != nullptr && !lip_test(q.jt, key)) continue;   // cannot join: not spilled
             spill[k] = true;
             rank[k] = atomicAdd(&cnt[part[k]], 1u);
         }

@@ -208,6 +208,7 @@ __device__ __forceinline__ void probe_rows_k64(const JoinTable& jt, const int64_
 // have fewer than 2^32 slots.
 __device__ __forceinline__ void probe_rows(const JoinTable& jt, const int64_t key[ST_RPL], uint32_t& pm,
                                            uint32_t pay[ST_RPL], uint32_t* err) {
+    lip_mask<ST_RPL>(jt, key, pm);
     if (jt.part_shift != 0) {
 #pragma unroll
         for (int j = 0; j < ST_RPL; ++j)

@@ -112,7 +112,7 @@ struct tp_engine {
     // statistics
     std::atomic<uint64_t> h2d_bytes{0}, d2h_bytes{0}, batches{0}, launches{0}, retries{0};
     std::atomic<uint64_t> jit_compiles{0}, jit_failures{0}, jit_launches{0}, jit_us{0};
-    std::atomic<uint64_t> split_passes{0};
+    std::atomic<uint64_t> split_passes{0}, lip_filters{0};
     // small pinned scratch for status words read back after an execution
     uint64_t* host_words = nullptr;
     tp::Lane lane0;                  // compute, copy, host_words of the engine itself
@@ -155,6 +155,7 @@ struct tp_plan {
     // reservations)
     uint64_t history_groups = 0;
     double selectivity = -1.0;   // sampled filter pass rate, < 0 until measured
+    double dim_selectivity = -1.0;   // sampled dimension predicate pass rate
 };
 
 struct tp_result {

@@ -30,6 +30,7 @@ TP_HOST_PAGES, TP_DEVICE = 1, 2
 TP_FLAG_TIME_KERNELS, TP_FLAG_NO_STAGED, TP_FLAG_EXACT_ONLY, TP_FLAG_NO_DIRECT_JOIN, TP_FLAG_NO_JIT = 1, 2, 4, 8, 16
 TP_FLAG_NO_DIRECT_AGG, TP_FLAG_RAW_PAGES = 32, 64
 TP_SIDE_FACT, TP_SIDE_DIM = 0, 1
+TP_LIP_AUTO, TP_LIP_OFF, TP_LIP_ON = 0, 1, 2
 TP_AGG_SUM, TP_AGG_SUM_MUL_SUB, TP_AGG_COUNT, TP_AGG_AVG = 0, 1, 2, 3
 
 _NP_TYPE = {np.dtype(np.int32): TP_I32, np.dtype(np.int64): TP_I64, np.dtype(np.uint8): TP_U8}
@@ -83,7 +84,8 @@ class tp_plan_desc(ctypes.Structure):
                 ("join", tp_join), ("n_group", ctypes.c_int32), ("group", tp_group_field * 4),
                 ("n_agg", ctypes.c_int32), ("aggs", tp_agg * 8), ("agg_strategy", ctypes.c_int32),
                 ("load_factor", ctypes.c_float), ("expected_groups", ctypes.c_uint64),
-                ("join_partitions", ctypes.c_int32)]
+                ("join_partitions", ctypes.c_int32), ("dim_filter", tp_filter), ("dim_filter_on", ctypes.c_int32),
+                ("lip", ctypes.c_int32)]
 
 
 class tp_i128(ctypes.Structure):
@@ -98,7 +100,7 @@ class tp_stats(ctypes.Structure):
                 ("agg_kernel_launches", ctypes.c_uint64), ("agg_kernel_rows", ctypes.c_uint64),
                 ("jit_compiles", ctypes.c_uint64), ("jit_failures", ctypes.c_uint64),
                 ("jit_launches", ctypes.c_uint64), ("jit_compile_ms", ctypes.c_double),
-                ("agg_split_passes", ctypes.c_uint64)]
+                ("agg_split_passes", ctypes.c_uint64), ("lip_filters", ctypes.c_uint64)]
 
 
 class tp_server_stats(ctypes.Structure):
@@ -312,7 +314,9 @@ class Engine:
         return t
 
     def plan(self, fact: "Table", dim: "Table | None", query: dict, agg_strategy=TP_AGG_AUTO,
-             load_factor=0.0, expected_groups=0, join_partitions=0) -> "Plan":
+             load_factor=0.0, expected_groups=0, join_partitions=0, lip=TP_LIP_AUTO) -> "Plan":
+        """query: filter / join / group / aggs as the oracle takes them, plus an
+        optional dim_filter = dict(col=<dimension column>, lo=, hi=)."""
         d = tp_plan_desc()
         d.fact = fact.h
         d.dim = dim.h if dim is not None else None
@@ -338,6 +342,10 @@ class Engine:
                 raise ValueError(ag)
         d.agg_strategy, d.load_factor, d.expected_groups = agg_strategy, load_factor, expected_groups
         d.join_partitions = join_partitions
+        df = query.get("dim_filter")
+        if df is not None:
+            d.dim_filter, d.dim_filter_on = tp_filter(dim.col(df["col"]), df["lo"], df["hi"]), 1
+        d.lip = lip
         h = ctypes.c_void_p()
         _check(self.lib.tp_plan_create(self.h, ctypes.byref(d), ctypes.byref(h)))
         return Plan(self, h, list(query["aggs"]))

@@ -63,9 +63,10 @@ def test_struct_layout_matches_c(tmp_path):
         "tp_config": ["page_bytes", "n_pages", "device_budget_bytes", "prefetch_depth", "batch_rows",
                       "load_factor", "agg_strategy", "compute_stream"],
         "tp_plan_desc": ["fact", "dim", "filter", "join", "n_group", "group", "n_agg", "aggs",
-                         "agg_strategy", "load_factor", "expected_groups", "join_partitions"],
+                         "agg_strategy", "load_factor", "expected_groups", "join_partitions", "dim_filter",
+                         "dim_filter_on", "lip"],
         "tp_stats": ["h2d_bytes", "retries", "pages_in_use", "pages_total", "agg_kernel_rows", "jit_compiles",
-                     "jit_launches", "jit_compile_ms", "agg_split_passes"],
+                     "jit_launches", "jit_compile_ms", "agg_split_passes", "lip_filters"],
         "tp_i128": ["lo", "hi"],
         "tp_agg": ["kind", "col_a", "col_b", "k"],
         "tp_table_desc": ["n_cols", "cols", "batch_rows"],

@@ -19,7 +19,7 @@ def _nvrtc():
     pytest.skip("NVRTC not available")
 
 
-def _shape(filter=1, ftype=0, join=1, ktype=0, part=0, groups=((0, 2, 2), (0, 2, 1), (1, 0, 5)),
+def _shape(filter=1, ftype=0, join=1, ktype=0, part=0, lip=0, groups=((0, 2, 2), (0, 2, 1), (1, 0, 5)),
            sums=((0, 1, 0, 1, 0), (1, 1, 1, 2, 1), (0, 1, 0, 1, 0)), fast=True):
     """groups: (side, type, bits); sums: (kind, atype, btype, mode, narrow)."""
     def arr(name, vals, n):
@@ -28,7 +28,8 @@ def _shape(filter=1, ftype=0, join=1, ktype=0, part=0, groups=((0, 2, 2), (0, 2,
     g = list(zip(*groups)) if groups else ((), (), ())
     s = list(zip(*sums)) if sums else ((), (), (), (), ())
     return ("struct JS {\n"
-            f"  static constexpr int filter = {filter}, ftype = {ftype}, join = {join}, ktype = {ktype}, part = {part};\n"
+            f"  static constexpr int filter = {filter}, ftype = {ftype}, join = {join}, ktype = {ktype}, part = {part}, "
+            f"lip = {lip};\n"
             f"  static constexpr int ng = {len(groups)};\n"
             f"  static constexpr int {arr('gside', g[0], 4)}, {arr('gtype', g[1], 4)}, {arr('gbits', g[2], 4)};\n"
             f"  static constexpr int ns = {len(sums)};\n"
@@ -45,6 +46,8 @@ SHAPES = {
     "no-filter-no-join": _shape(filter=0, join=0, groups=((0, 0, 4), (0, 1, 3)), sums=((0, 0, 0, 1, 0),)),
     "i64-filter-u8-wide-field": _shape(ftype=1, groups=((0, 2, 9), (1, 0, 3)), sums=((1, 0, 2, 2, 0),)),
     "count-only": _shape(sums=()),
+    "lip-direct": _shape(lip=1),
+    "lip-hash64-partitioned": _shape(join=3, ktype=1, part=1, lip=1),
 }
 
 
