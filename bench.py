@@ -74,6 +74,9 @@ def parse_args():
     ap.add_argument("--ooc-dim", type=int, default=150_000_000, help="out-of-core build rows")
     ap.add_argument("--ooc-budgets", default="16,2", help="device budgets (GiB) of the out-of-core runs")
     ap.add_argument("--ooc-steps", type=int, default=2)
+    ap.add_argument("--ooc-lip-budget", type=float, default=2.0,
+                    help="budget (GiB) of the out-of-core runs with a dimension predicate, lookahead "
+                         "filter off and on; 0 skips them")
     return ap.parse_args()
 
 
@@ -333,7 +336,7 @@ def host_ram_bytes() -> int:
         return 0
 
 
-def outofcore_measure(T, W, torch, dev, n_fact, n_dim, budgets_gb, steps, link):
+def outofcore_measure(T, W, torch, dev, n_fact, n_dim, budgets_gb, steps, link, lip_budget=0.0):
     """The out-of-core star query: fact and build tables in 64 MiB pinned pages,
     streamed through the device; the join runs radix-partitioned 64 ways and
     spills the partitions the budget cannot hold.  Rows are scaled down (and
@@ -391,9 +394,43 @@ def outofcore_measure(T, W, torch, dev, n_fact, n_dim, budgets_gb, steps, link):
             "alg_gbs": alg / sec / 1e9, "link_frac_alg": alg / sec / 1e9 / link,
             "link_frac_moved": (h2d + d2h) / sec / 1e9 / link}
         p.destroy()
+    if lip_budget > 0:
+        out["lookahead"] = lookahead_measure(T, W, torch, eng, ft, dt, nf, lip_budget, steps)
     ft.destroy()
     dt.destroy()
     eng.close()
+    return out
+
+
+def lookahead_measure(T, W, torch, eng, ft, dt, nf, budget_gb, steps):
+    """The out-of-core star query with a predicate admitting 5 of the 25
+    dimension attribute values (20% of the build rows), lookahead filter off
+    and on: the filter keeps fact rows that cannot join out of the probes and
+    out of the partition spill.  Both runs must give the same groups."""
+    eng.set_budget(int(budget_gb * 2**30))
+    q = dict(W.q_lowcard(), dim_filter=dict(col="attr", lo=0, hi=4))
+    out = {"budget_gb": budget_gb, "dim_filter": "attr in [0, 4]: 20% of the build rows"}
+    seen = {}
+    for name, mode in (("off", T.TP_LIP_OFF), ("on", T.TP_LIP_AUTO)):
+        p = eng.plan(ft, dt, q, join_partitions=64, lip=mode)
+        p.execute().free()
+        s0 = eng.stats()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(steps):
+            with p.execute() as r:
+                seen[name] = (r.keys().copy(), r.counts().copy())
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t1) / steps
+        s1 = eng.stats()
+        out[name] = {"ms_per_step": sec * 1e3, "fact_rows_per_s": nf / sec,
+                     "h2d_bytes_per_step": int((s1["h2d_bytes"] - s0["h2d_bytes"]) / steps),
+                     "d2h_bytes_per_step": int((s1["d2h_bytes"] - s0["d2h_bytes"]) / steps),
+                     "filters_built": int(s1["lip_filters"] - s0["lip_filters"])}
+        p.destroy()
+    out["speedup"] = out["off"]["ms_per_step"] / out["on"]["ms_per_step"]
+    out["results_equal"] = bool(np.array_equal(seen["off"][0], seen["on"][0]) and
+                                np.array_equal(seen["off"][1], seen["on"][1]))
     return out
 
 
@@ -587,7 +624,7 @@ def main():
         link_ooc = e2e["link_peak_gbs"] if e2e else link_peak_gbs(dev)
         extra["star-600M-outofcore"] = outofcore_measure(
             T, W, torch, dev, args.ooc_fact, args.ooc_dim, [float(x) for x in args.ooc_budgets.split(",")],
-            args.ooc_steps, link_ooc)
+            args.ooc_steps, link_ooc, args.ooc_lip_budget)
 
     patterns = None
     if not args.no_patterns:
