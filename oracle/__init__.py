@@ -55,6 +55,10 @@ class _Query(ctypes.Structure):
         ("group_col", ctypes.c_int32 * 4), ("group_bits", ctypes.c_int32 * 4),
         ("n_agg", ctypes.c_int32), ("aggs", _Agg * 8),
         ("dim_filter_col", ctypes.c_int32), ("dim_filter_lo", ctypes.c_int64), ("dim_filter_hi", ctypes.c_int64),
+        ("n_extra_dims", ctypes.c_int32), ("n_xdim", ctypes.c_uint64 * 3), ("n_xdim_cols", ctypes.c_int32 * 3),
+        ("xdim", ctypes.POINTER(_Column) * 3), ("xjoin_fact_col", ctypes.c_int32 * 3),
+        ("xjoin_dim_col", ctypes.c_int32 * 3), ("xdim_filter_col", ctypes.c_int32 * 3),
+        ("xdim_filter_lo", ctypes.c_int64 * 3), ("xdim_filter_hi", ctypes.c_int64 * 3),
     ]
 
 
@@ -121,13 +125,18 @@ def _columns(table: dict):
 
 def run(wl) -> OracleResult:
     """Evaluate a workload's query over its tables; raises OracleError."""
-    return run_query(wl.fact, wl.dim, wl.query)
+    return run_query(wl.fact, wl.dim, wl.query, getattr(wl, "extra_dims", None))
 
 
-def run_query(fact: dict, dim: dict | None, query: dict) -> OracleResult:
+def run_query(fact: dict, dim: dict | None, query: dict, extra_dims: list | None = None) -> OracleResult:
+    """query: filter, join, group, aggs, optional dim_filter; a star join adds
+    extra_joins = [dict(fact_col, dim_col, optional dim_filter), ...] over the
+    tables extra_dims, whose group fields use sides "dim1", "dim2", "dim3"."""
     lib = _load()
     fnames, farrs, fcols = _columns(fact)
     dnames, darrs, dcols = _columns(dim if dim is not None else {})
+    xjoins = query.get("extra_joins") or []
+    xd = [_columns(t) for t in (extra_dims or [])]
     n_fact = len(farrs[0]) if farrs else 0
     n_dim = len(darrs[0]) if darrs else 0
     q = _Query()
@@ -148,10 +157,26 @@ def run_query(fact: dict, dim: dict | None, query: dict) -> OracleResult:
         q.dim_filter_col, q.dim_filter_lo, q.dim_filter_hi = -1, 0, 0
     else:
         q.dim_filter_col, q.dim_filter_lo, q.dim_filter_hi = dnames.index(df["col"]), df["lo"], df["hi"]
+    if len(xjoins) > len(xd):
+        raise ValueError("extra_joins needs one table per join in extra_dims")
+    q.n_extra_dims = len(xjoins)
+    for j, xj in enumerate(xjoins):
+        names, arrs, cols = xd[j]
+        q.n_xdim[j] = len(arrs[0]) if arrs else 0
+        q.n_xdim_cols[j] = len(arrs)
+        q.xdim[j] = cols
+        q.xjoin_fact_col[j] = fnames.index(xj["fact_col"])
+        q.xjoin_dim_col[j] = names.index(xj["dim_col"])
+        xf = xj.get("dim_filter")
+        q.xdim_filter_col[j] = -1 if xf is None else names.index(xf["col"])
+        q.xdim_filter_lo[j], q.xdim_filter_hi[j] = (0, 0) if xf is None else (xf["lo"], xf["hi"])
+    sides = {"fact": (0, fnames), "dim": (1, dnames)}
+    for j in range(len(xjoins)):
+        sides[f"dim{j + 1}"] = (2 + j, xd[j][0])
     q.n_group = len(query["group"])
     for i, (side, col, bits) in enumerate(query["group"]):
-        q.group_side[i] = 0 if side == "fact" else 1
-        q.group_col[i] = (fnames if side == "fact" else dnames).index(col)
+        q.group_side[i], names = sides[side]
+        q.group_col[i] = names.index(col)
         q.group_bits[i] = bits
     q.n_agg = len(query["aggs"])
     for i, ag in enumerate(query["aggs"]):
@@ -168,7 +193,9 @@ def run_query(fact: dict, dim: dict | None, query: dict) -> OracleResult:
         else:
             raise ValueError(kind)
     res = _Result()
+    keep = (farrs, darrs, xd)   # the column arrays must outlive the call
     rc = lib.orc_run(ctypes.byref(q), ctypes.byref(res))
+    del keep
     if rc != 0:
         raise OracleError(rc)
     try:

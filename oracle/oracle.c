@@ -12,6 +12,8 @@
  *      predicate whose surviving keys lookahead information passing,
  *      Section 5, hands to the fact side).  The surviving dimension keys are
  *      sorted and searched by bisection; duplicates among them are an error.
+ *      A star join repeats this for every further dimension, each on its own
+ *      fact foreign key: a fact row survives only with a partner in all.
  *   3. Group and aggregate: the group key concatenates the group fields, the
  *      first field in the highest bits.  Surviving (key, row) pairs are sorted
  *      and each run of equal keys is reduced with exact 128-bit integer sums
@@ -64,23 +66,56 @@ static int64_t find_dim_row(const key_row* sorted, uint64_t n, int64_t k) {
 
 static int valid_col(int32_t c, int32_t n) { return c >= 0 && c < n; }
 
+/* One joined dimension: its table, join columns and predicate. */
+typedef struct {
+    uint64_t n;
+    int32_t n_cols;
+    const orc_column* cols;
+    int32_t fact_col, key_col;
+    int32_t filter_col;
+    int64_t filter_lo, filter_hi;
+} dim_side;
+
+/* Dimension k of the query: 0 = the first join, 1 + j = further dimension j. */
+static dim_side side_of(const orc_query* q, int k) {
+    dim_side d;
+    if (k == 0) {
+        d.n = q->n_dim; d.n_cols = q->n_dim_cols; d.cols = q->dim;
+        d.fact_col = q->join_fact_col; d.key_col = q->join_dim_col;
+        d.filter_col = q->dim_filter_col; d.filter_lo = q->dim_filter_lo; d.filter_hi = q->dim_filter_hi;
+    } else {
+        int j = k - 1;
+        d.n = q->n_xdim[j]; d.n_cols = q->n_xdim_cols[j]; d.cols = q->xdim[j];
+        d.fact_col = q->xjoin_fact_col[j]; d.key_col = q->xjoin_dim_col[j];
+        d.filter_col = q->xdim_filter_col[j]; d.filter_lo = q->xdim_filter_lo[j]; d.filter_hi = q->xdim_filter_hi[j];
+    }
+    return d;
+}
+
+static int n_dims(const orc_query* q) { return q->join_fact_col < 0 ? 0 : 1 + q->n_extra_dims; }
+
 static int32_t validate(const orc_query* q) {
     int total = 0;
     if (q->n_group < 0 || q->n_group > 4 || q->n_agg < 0 || q->n_agg > 8) return ORC_INVALID;
     if (q->filter_col >= 0 && !valid_col(q->filter_col, q->n_fact_cols)) return ORC_INVALID;
-    if (q->join_fact_col >= 0 &&
-        (!valid_col(q->join_fact_col, q->n_fact_cols) || !valid_col(q->join_dim_col, q->n_dim_cols)))
+    if (q->n_extra_dims < 0 || q->n_extra_dims > 3 || (q->n_extra_dims > 0 && q->join_fact_col < 0))
         return ORC_INVALID;
-    if (q->dim_filter_col >= 0 && (q->join_fact_col < 0 || !valid_col(q->dim_filter_col, q->n_dim_cols)))
-        return ORC_INVALID;
+    for (int k = 0; k < n_dims(q); ++k) {
+        dim_side d = side_of(q, k);
+        if (!valid_col(d.fact_col, q->n_fact_cols) || !valid_col(d.key_col, d.n_cols)) return ORC_INVALID;
+        if (d.filter_col >= 0 && !valid_col(d.filter_col, d.n_cols)) return ORC_INVALID;
+    }
+    if (q->join_fact_col < 0 && q->dim_filter_col >= 0) return ORC_INVALID;
     for (int g = 0; g < q->n_group; ++g) {
         int bits = q->group_bits[g];
         if (bits < 1 || bits > 64) return ORC_INVALID;
         total += bits;
-        if (q->group_side[g] == 0) {
+        int side = q->group_side[g];
+        if (side == 0) {
             if (!valid_col(q->group_col[g], q->n_fact_cols)) return ORC_INVALID;
         } else {
-            if (q->join_fact_col < 0 || !valid_col(q->group_col[g], q->n_dim_cols)) return ORC_INVALID;
+            if (side < 1 || side > n_dims(q) || !valid_col(q->group_col[g], side_of(q, side - 1).n_cols))
+                return ORC_INVALID;
         }
     }
     if (total > 64) return ORC_INVALID;
@@ -107,53 +142,57 @@ int32_t orc_run(const orc_query* q, orc_result* out) {
     int32_t rc = validate(q);
     memset(out, 0, sizeof(*out));
     if (rc != ORC_OK) return rc;
+    key_row* kept = NULL;
+    uint64_t n_kept = 0;
 
-    /* Join side: keep the dimension rows the predicate admits, sort their
-     * (pk, row) and reject duplicate keys. */
-    key_row* dim = NULL;
-    uint64_t n_dim = 0;
-    if (q->join_fact_col >= 0 && q->n_dim > 0) {
-        dim = (key_row*)malloc(q->n_dim * sizeof(key_row));
-        if (!dim) return ORC_NOMEM;
-        for (uint64_t i = 0; i < q->n_dim; ++i) {
-            if (q->dim_filter_col >= 0) {
-                int64_t v = col_at(&q->dim[q->dim_filter_col], i);
-                if (v < q->dim_filter_lo || v > q->dim_filter_hi) continue;
+    /* Join sides: keep each dimension's rows its predicate admits, sort
+     * their (pk, row) and reject duplicate keys. */
+    const int nd = n_dims(q);
+    key_row* dim[4] = {NULL, NULL, NULL, NULL};
+    uint64_t n_adm[4] = {0, 0, 0, 0};
+    for (int k = 0; k < nd; ++k) {
+        dim_side ds = side_of(q, k);
+        if (ds.n == 0) continue;
+        dim[k] = (key_row*)malloc(ds.n * sizeof(key_row));
+        if (!dim[k]) { rc = ORC_NOMEM; goto out; }
+        for (uint64_t i = 0; i < ds.n; ++i) {
+            if (ds.filter_col >= 0) {
+                int64_t v = col_at(&ds.cols[ds.filter_col], i);
+                if (v < ds.filter_lo || v > ds.filter_hi) continue;
             }
-            dim[n_dim].key = col_at(&q->dim[q->join_dim_col], i);
-            dim[n_dim].row = i;
-            ++n_dim;
+            dim[k][n_adm[k]].key = col_at(&ds.cols[ds.key_col], i);
+            dim[k][n_adm[k]].row = i;
+            ++n_adm[k];
         }
-        qsort(dim, n_dim, sizeof(key_row), cmp_key_row_signed);
-        for (uint64_t i = 1; i < n_dim; ++i)
-            if (dim[i].key == dim[i - 1].key) { free(dim); return ORC_DUP_KEY; }
+        qsort(dim[k], n_adm[k], sizeof(key_row), cmp_key_row_signed);
+        for (uint64_t i = 1; i < n_adm[k]; ++i)
+            if (dim[k][i].key == dim[k][i - 1].key) { rc = ORC_DUP_KEY; goto out; }
     }
 
     /* Filter, join and key every fact row; keep (group key, fact row). */
-    key_row* kept = (key_row*)malloc((q->n_fact ? q->n_fact : 1) * sizeof(key_row));
-    if (!kept) { free(dim); return ORC_NOMEM; }
-    uint64_t n_kept = 0;
+    kept = (key_row*)malloc((q->n_fact ? q->n_fact : 1) * sizeof(key_row));
+    if (!kept) { rc = ORC_NOMEM; goto out; }
     for (uint64_t i = 0; i < q->n_fact; ++i) {
         if (q->filter_col >= 0) {
             int64_t v = col_at(&q->fact[q->filter_col], i);
             if (v < q->filter_lo || v > q->filter_hi) continue;
         }
-        int64_t d = -1;
-        if (q->join_fact_col >= 0) {
-            if (dim == NULL) continue;
-            d = find_dim_row(dim, n_dim, col_at(&q->fact[q->join_fact_col], i));
-            if (d < 0) continue;
+        int64_t d[4] = {-1, -1, -1, -1};
+        int joined = 1;
+        for (int k = 0; k < nd && joined; ++k) {
+            dim_side ds = side_of(q, k);
+            d[k] = dim[k] ? find_dim_row(dim[k], n_adm[k], col_at(&q->fact[ds.fact_col], i)) : -1;
+            joined = d[k] >= 0;
         }
+        if (!joined) continue;
         uint64_t key = 0;
         for (int g = 0; g < q->n_group; ++g) {
             int bits = q->group_bits[g];
-            int64_t v = q->group_side[g] == 0 ? col_at(&q->fact[q->group_col[g]], i)
-                                              : col_at(&q->dim[q->group_col[g]], (uint64_t)d);
+            int side = q->group_side[g];
+            int64_t v = side == 0 ? col_at(&q->fact[q->group_col[g]], i)
+                                  : col_at(&side_of(q, side - 1).cols[q->group_col[g]], (uint64_t)d[side - 1]);
             if (bits < 64) {
-                if (v < 0 || (uint64_t)v >= (1ull << bits)) {
-                    free(dim); free(kept);
-                    return ORC_RANGE;
-                }
+                if (v < 0 || (uint64_t)v >= (1ull << bits)) { rc = ORC_RANGE; goto out; }
                 key = (key << bits) | (uint64_t)v;
             } else {
                 key = (uint64_t)v;
@@ -163,7 +202,7 @@ int32_t orc_run(const orc_query* q, orc_result* out) {
         kept[n_kept].row = i;
         ++n_kept;
     }
-    free(dim);
+    for (int k = 0; k < 4; ++k) { free(dim[k]); dim[k] = NULL; }
     qsort(kept, n_kept, sizeof(key_row), cmp_key_row_unsigned);
 
     /* Count groups, then reduce each run of equal keys. */
@@ -212,6 +251,10 @@ int32_t orc_run(const orc_query* q, orc_result* out) {
     }
     free(kept);
     return ORC_OK;
+out:
+    for (int k = 0; k < 4; ++k) free(dim[k]);
+    free(kept);
+    return rc;
 }
 
 void orc_free(orc_result* r) {

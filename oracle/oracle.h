@@ -10,10 +10,11 @@
  * Filter and Join over them; Section 4 states decimal(11,2) values held in
  * 128-bit integers):
  *
- *   R = { (g, aggregates) : f in Fact, d in Dim,
+ *   R = { (g, aggregates) : f in Fact, d in Dim, e_j in Dim_j (j < n_extra_dims),
  *         filter_lo <= f.filter_col <= filter_hi,
  *         dim_filter_lo <= d.dim_filter_col <= dim_filter_hi, f.fk == d.pk,
- *         g = packed(group fields of f and d) }
+ *         the same for every further dimension e_j on its own foreign key,
+ *         g = packed(group fields of f, d and the e_j) }
  *
  * sorted ascending by the packed 64-bit key g.
  */
@@ -54,7 +55,7 @@ typedef struct {
     int32_t join_fact_col;           /* -1: no join */
     int32_t join_dim_col;
     int32_t n_group;                 /* 0..4 fields */
-    int32_t group_side[4];           /* 0 = fact, 1 = dim */
+    int32_t group_side[4];           /* 0 = fact, 1 = dim, 2 + j = further dimension j */
     int32_t group_col[4];
     int32_t group_bits[4];           /* 1..64, total <= 64 */
     int32_t n_agg;                   /* 0..8 */
@@ -63,6 +64,15 @@ typedef struct {
      * (and only their keys must be unique); column -1 = every row */
     int32_t dim_filter_col;
     int64_t dim_filter_lo, dim_filter_hi;
+    /* further dimensions of a star join, each joined like the first on its
+     * own fact foreign key; group_side 2 + j reads further dimension j */
+    int32_t n_extra_dims;                /* 0..3; needs the first join */
+    uint64_t n_xdim[3];
+    int32_t n_xdim_cols[3];
+    const orc_column* xdim[3];
+    int32_t xjoin_fact_col[3], xjoin_dim_col[3];
+    int32_t xdim_filter_col[3];          /* -1: every row */
+    int64_t xdim_filter_lo[3], xdim_filter_hi[3];
 } orc_query;
 
 typedef struct {

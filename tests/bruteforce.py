@@ -7,21 +7,30 @@ def _val(arr, i):
     return int(arr[i])
 
 
-def evaluate(fact: dict, dim: dict | None, query: dict):
+def evaluate(fact: dict, dim: dict | None, query: dict, extra_dims: list | None = None):
     """Returns a list of (key, count, [sum per agg], [avg per agg or None]),
-    sorted by key; raises ValueError('dup_key' | 'range')."""
+    sorted by key; raises ValueError('dup_key' | 'range').  A star join lists
+    further joins in query["extra_joins"] over the tables extra_dims."""
     n_fact = len(next(iter(fact.values()))) if fact else 0
-    n_dim = len(next(iter(dim.values()))) if dim else 0
-    join = query.get("join")
-    dflt = query.get("dim_filter")
-    # dimension rows the dimension predicate admits (all when there is none)
-    live = [dflt is None or dflt["lo"] <= _val(dim[dflt["col"]], d) <= dflt["hi"] for d in range(n_dim)]
-    if join is not None:
-        pk = [int(x) for x in dim[join["dim_col"]]] if dim else []
+    # every joined dimension: (table, join, predicate), the first one first
+    sides = []
+    if query.get("join") is not None:
+        sides.append((dim, query["join"], query.get("dim_filter")))
+        for j, xj in enumerate(query.get("extra_joins") or []):
+            sides.append((extra_dims[j], xj, xj.get("dim_filter")))
+    names = {"dim": 0, "dim1": 1, "dim2": 2, "dim3": 3}
+    live, pks = [], []
+    for tab, join, dflt in sides:
+        n_dim = len(next(iter(tab.values()))) if tab else 0
+        # dimension rows the dimension predicate admits (all when there is none)
+        lv = [dflt is None or dflt["lo"] <= _val(tab[dflt["col"]], d) <= dflt["hi"] for d in range(n_dim)]
+        pk = [int(x) for x in tab[join["dim_col"]]] if tab else []
         for a in range(n_dim):
             for b in range(a + 1, n_dim):
-                if live[a] and live[b] and pk[a] == pk[b]:
+                if lv[a] and lv[b] and pk[a] == pk[b]:
                     raise ValueError("dup_key")
+        live.append(lv)
+        pks.append(pk)
     groups = []  # list of [key, count, sums]
     aggs = query["aggs"]
     flt = query.get("filter")
@@ -30,14 +39,15 @@ def evaluate(fact: dict, dim: dict | None, query: dict):
             v = _val(fact[flt["col"]], i)
             if not (flt["lo"] <= v <= flt["hi"]):
                 continue
-        partners = [None]
-        if join is not None:
+        combos = [[]]     # every combination of partner rows, one per dimension
+        for k, (tab, join, _) in enumerate(sides):
             fk = _val(fact[join["fact_col"]], i)
-            partners = [d for d in range(n_dim) if live[d] and pk[d] == fk]
-        for d in partners:
+            rows = [d for d in range(len(pks[k])) if live[k][d] and pks[k][d] == fk]
+            combos = [c + [d] for c in combos for d in rows]
+        for ds in combos:
             key = 0
             for side, col, bits in query["group"]:
-                v = _val(fact[col], i) if side == "fact" else _val(dim[col], d)
+                v = _val(fact[col], i) if side == "fact" else _val(sides[names[side]][0][col], ds[names[side]])
                 if bits < 64:
                     if not (0 <= v < (1 << bits)):
                         raise ValueError("range")

@@ -157,6 +157,86 @@ def test_dim_filter_duplicates_only_among_admitted_rows():
         bruteforce.evaluate(fact, dim, q)
 
 
+def _star_tiny(seed, n_fact, sizes, spans):
+    """A fact table with one foreign key per dimension (fk, fk2, fk3, drawn from
+    spans wider than the keys, so some rows miss) and dimensions of the given
+    sizes with permuted unique keys and a 0..24 attribute."""
+    fact, dim = _tiny(seed, n_fact, sizes[0], spans[0])
+    s = 2000 + seed
+    extra = []
+    for j, (n, span) in enumerate(zip(sizes[1:], spans[1:])):
+        extra.append(dict(
+            pk=datagen.fill(s, 10 + j, datagen.PERM, np.int64, n, b=max(n, 1)) if n else np.zeros(0, np.int64),
+            attr=datagen.uniform(s, 20 + j, np.int32, n, 0, 24),
+            band=datagen.uniform(s, 30 + j, np.uint8, n, 0, 3)))
+        fact[f"fk{j + 2}"] = datagen.uniform(s, 40 + j, np.int64, n_fact, 0, span - 1)
+    return fact, dim, extra
+
+
+def _star_query(n_extra, dim_filters=(None, None, None, None)):
+    q = dict(W.q_lowcard(), dim_filter=dim_filters[0])
+    q["extra_joins"] = [dict(fact_col=f"fk{j + 2}", dim_col="pk", dim_filter=dim_filters[j + 1])
+                        for j in range(n_extra)]
+    bands = [(f"dim{j + 1}", "band", 2) for j in range(n_extra)]
+    q["group"] = ([("fact", "flag", 2)] if n_extra < 3 else []) + [("dim", "attr", 5)] + bands   # at most 4 fields
+    return q
+
+
+@pytest.mark.parametrize("seed,n_extra,filters", [
+    (40, 1, (None, None)),
+    (41, 2, (None, dict(col="attr", lo=0, hi=12), None)),
+    (42, 3, (dict(col="attr", lo=5, hi=20), None, dict(col="band", lo=1, hi=2), dict(col="attr", lo=0, hi=0))),
+    (43, 2, (None, dict(col="attr", lo=30, hi=40), None)),       # a dimension admits nothing: empty result
+])
+def test_star_join_matches_bruteforce(seed, n_extra, filters):
+    fact, dim, extra = _star_tiny(seed, 700, [60, 40, 30, 20][:n_extra + 1], [80, 50, 35, 25][:n_extra + 1])
+    q = _star_query(n_extra, filters)
+    ref = bruteforce.evaluate(fact, dim, q, extra)
+    got = oracle.run_query(fact, dim, q, extra)
+    assert got.n_groups == len(ref)
+    for g, (key, count, sums, avgs) in enumerate(ref):
+        assert int(got.keys[g]) == key and int(got.counts[g]) == count
+        for a, ag in enumerate(q["aggs"]):
+            assert got.sum_int(g, a) == sums[a]
+            if ag[0] == "avg":
+                assert got.avgs[g, a] == avgs[a]
+    if filters[-1] is not None and filters[-1]["lo"] > 24:
+        assert got.n_groups == 0
+
+
+def test_star_join_field_equals_derived_fact_column():
+    """A dimension whose attribute is a function of its key: grouping by that
+    attribute through the join equals grouping by the function of the foreign
+    key computed on the fact side, restricted to rows that have a partner."""
+    fact, dim, extra = _star_tiny(44, 3000, [200, 500], [200, 700])
+    extra[0]["band"] = (extra[0]["pk"] % 4).astype(np.uint8)
+    q = _star_query(1)
+    got = oracle.run_query(fact, dim, q, extra)
+    f2 = {k: v.copy() for k, v in fact.items()}
+    hit = f2["fk2"] < 500                                 # keys 0..499 exist in the second dimension
+    f2["date"] = np.where(hit, f2["date"], W.N_DAYS + 10).astype(np.int32)   # drop the misses by the filter
+    f2["band2"] = (f2["fk2"] % 4).astype(np.uint8)
+    q2 = dict(W.q_lowcard(), group=[("fact", "flag", 2), ("dim", "attr", 5), ("fact", "band2", 2)])
+    want = oracle.run_query(f2, dim, q2)
+    assert np.array_equal(got.keys, want.keys) and np.array_equal(got.counts, want.counts)
+    assert np.array_equal(got.sums, want.sums)
+
+
+def test_star_join_order_of_dimensions_is_irrelevant():
+    fact, dim, extra = _star_tiny(45, 2500, [90, 70, 50], [100, 80, 60])
+    q = _star_query(2, (dict(col="attr", lo=0, hi=15), None, dict(col="band", lo=0, hi=2)))
+    base = oracle.run_query(fact, dim, q, extra)
+    # the second further dimension as the first join and the first join as a further one
+    fact_sw = dict(fact, fk=fact["fk3"], fk3=fact["fk"].astype(np.int64))
+    q_sw = dict(q, dim_filter=q["extra_joins"][1]["dim_filter"])
+    q_sw["extra_joins"] = [q["extra_joins"][0], dict(fact_col="fk3", dim_col="pk", dim_filter=q["dim_filter"])]
+    q_sw["group"] = [("fact", "flag", 2), ("dim2", "attr", 5), ("dim1", "band", 2), ("dim", "band", 2)]
+    sw = oracle.run_query(fact_sw, extra[1], q_sw, [extra[0], dim])
+    # the fields land in the same key bits, so the results are identical
+    assert np.array_equal(base.keys, sw.keys) and np.array_equal(base.counts, sw.counts)
+    assert np.array_equal(base.sums, sw.sums)
+
+
 def _modular_closed_form(n_fact, n_dim):
     """Per-group (count, SUM qty, SUM price*(100-disc), SUM disc) on the
     modular dataset, from arithmetic series.  Row i has flag = i mod 3,
