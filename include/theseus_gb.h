@@ -221,7 +221,10 @@ void tp_table_destroy(tp_table* t);
 
 /* ------------------------------------------------------------------- plans */
 
+/* Group field sides: the fact table, the first dimension (TP_SIDE_DIM), or
+ * further dimension j of a star join (TP_SIDE_DIM + 1 + j). */
 enum { TP_SIDE_FACT = 0, TP_SIDE_DIM = 1 };
+#define TP_MAX_EXTRA_DIMS 3
 enum { TP_AGG_SUM = 0, TP_AGG_SUM_MUL_SUB = 1, TP_AGG_COUNT = 2, TP_AGG_AVG = 3 };
 
 typedef struct {
@@ -293,6 +296,22 @@ typedef struct {
      * TP_LIP_OFF: never.  Join tables shared through the server's cache and
      * batched executions run without it.  Results never depend on it. */
     int32_t lip;
+    /* Star join: further dimension tables, each joined like the first
+     * (Section 3.2: a PK-FK inner equi-join) on its own fact foreign key,
+     * extra_join[j].fact_col = key column extra_join[j].dim_col of
+     * extra_dim[j]; a fact row survives only with a partner in every
+     * dimension.  Group fields of extra_dim[j] use side TP_SIDE_DIM + 1 + j;
+     * the fields of each dimension take at most 31 bits.  extra_dim_filter[j]
+     * applies when extra_dim_filter_on[j] != 0, with a lookahead filter of its
+     * own under the rule above.  Needs the first join.  Only the first join
+     * is ever partitioned: the further tables stay resident (TP_E_BUDGET when
+     * they do not fit).  Batched executions and the allocation-free entry
+     * point take one dimension (TP_E_INVALID otherwise). */
+    int32_t n_extra_dims;                         /* 0..TP_MAX_EXTRA_DIMS */
+    tp_table* extra_dim[TP_MAX_EXTRA_DIMS];
+    tp_join extra_join[TP_MAX_EXTRA_DIMS];
+    tp_filter extra_dim_filter[TP_MAX_EXTRA_DIMS];
+    int32_t extra_dim_filter_on[TP_MAX_EXTRA_DIMS];
 } tp_plan_desc;
 
 /* Validates and stores a plan.  TP_E_INVALID on any inconsistency. */

@@ -317,6 +317,24 @@ __device__ __forceinline__ bool eval_keys(const QueryDev& q, uint64_t t0, uint64
         }
         if (!any4(pass)) return false;
     }
+    // star join: every further table must hold the row's key too
+    uint32_t xpay[MAX_XJOIN][4];
+#pragma unroll
+    for (int j = 0; j < MAX_XJOIN; ++j) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) xpay[j][i] = 0;
+        if (j >= q.n_xjoin) continue;
+        load_rows<FULL>(q.fkx[j], r, n, pass, v);
+        probe4<NC>(q.jtx[j], v, pass, xpay[j], q.err);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (pass[i] && (xpay[j][i] & PAYLOAD_BAD)) {
+                atomicOr(q.err, ERR_RANGE);
+                pass[i] = false;
+            }
+        }
+        if (!any4(pass)) return false;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) key[i] = 0;
 #pragma unroll
@@ -327,8 +345,12 @@ __device__ __forceinline__ bool eval_keys(const QueryDev& q, uint64_t t0, uint64
         if (fact_side) load_rows<FULL>(q.gcol[g], r, n, pass, v);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
+            uint32_t pw = payload[i];   // the payload of the field's join
+#pragma unroll
+            for (int j = 0; j < MAX_XJOIN; ++j)
+                if (q.gdim[g] == j + 1) pw = xpay[j][i];
             const uint64_t f = fact_side ? (uint64_t)v[i]
-                                         : (uint64_t)(payload[i] >> q.gdpos[g]) & ((1ull << bits) - 1ull);
+                                         : (uint64_t)(pw >> q.gdpos[g]) & ((1ull << bits) - 1ull);
             if (bits < 64) {
                 if (pass[i] && (f >> bits) != 0) {
                     atomicOr(q.err, ERR_RANGE);

@@ -87,6 +87,7 @@ struct ExecState {
     bool key64 = false;
     uint64_t join_cap = 0;
     tpk::JoinTable jt{};
+    tpk::JoinTable jtx[tpk::MAX_XJOIN] = {};   // further tables of a star join
     uint32_t* err = nullptr;        // device error word
     unsigned long long* counters = nullptr;   // [0] agg used, [1] compact count, [2] max key, [3] sample
     bool eager = true;
@@ -151,7 +152,7 @@ tpk::DevCol devcol(const tp_table* t, int c, const void* ptr) {
 // QueryDev for one batch: colptr[c] is the device address of fact column c's
 // first row in this batch (nullptr for columns the query does not read).
 tpk::QueryDev make_query(const ExecState& S, const std::vector<const void*>& colptr) {
-    return tp::plan_query_dev(S.p, colptr, S.jt, S.err, S.eager);
+    return tp::plan_query_dev(S.p, colptr, S.jt, S.err, S.eager, S.jtx);
 }
 
 tp_status cuda_check(cudaError_t e, const char* what) {
@@ -162,44 +163,45 @@ tp_status cuda_check(cudaError_t e, const char* what) {
 
 // ----------------------------------------------------------------- build
 
-// Build-side parameters of the plan without columns: group fields packed
-// into the payload, the dimension predicate's bounds.
-tpk::BuildDev build_proto(const ExecState& S) {
+// Build-side parameters of dimension k (0: the first join) without columns:
+// its group fields packed into the payload, its predicate's bounds.
+tpk::BuildDev build_proto(const ExecState& S, int k = 0) {
     const tp_plan_desc& d = S.p->d;
     tpk::BuildDev b{};
-    b.jt = S.jt;
+    b.jt = k == 0 ? S.jt : S.jtx[k - 1];
     b.err = S.err;
     int nf = 0;
     for (int g = 0; g < d.n_group; ++g) {
-        if (d.group[g].side != TP_SIDE_DIM) continue;
+        if (S.p->gdim[g] != k) continue;
         b.dbits[nf] = d.group[g].bits;
         b.dpos[nf] = S.p->gdpos[g];
         ++nf;
     }
     b.n_dfield = nf;
-    b.has_filter = d.dim_filter.col >= 0;
-    b.flo = d.dim_filter.lo;
-    b.fhi = d.dim_filter.hi;
+    b.has_filter = S.p->dflt[k].col >= 0;
+    b.flo = S.p->dflt[k].lo;
+    b.fhi = S.p->dflt[k].hi;
     return b;
 }
 
-// Calls fn(build, rows) for every batch of the dimension table with the key,
+// Calls fn(build, rows) for every batch of dimension k with the key,
 // group-field and predicate columns on the device.
 template <class F>
-tp_status for_each_dim_batch(ExecState& S, Scratch& sc, const tpk::BuildDev& proto, F&& fn) {
+tp_status for_each_dim_batch(ExecState& S, Scratch& sc, const tpk::BuildDev& proto, F&& fn, int dk = 0) {
     tp_engine* e = S.e;
     const tp_plan_desc& d = S.p->d;
-    tp_table* t = S.dim;
-    std::vector<int> bcols = {d.join.dim_col};
+    tp_table* t = S.p->dims[dk];
+    const tp_filter& flt = S.p->dflt[dk];
+    std::vector<int> bcols = {S.p->joins[dk].dim_col};
     for (int g = 0; g < d.n_group; ++g)
-        if (d.group[g].side == TP_SIDE_DIM) bcols.push_back(d.group[g].col);
+        if (S.p->gdim[g] == dk) bcols.push_back(d.group[g].col);
     const int nf = (int)bcols.size() - 1;
-    if (d.dim_filter.col >= 0) bcols.push_back(d.dim_filter.col);
+    if (flt.col >= 0) bcols.push_back(flt.col);
     tpk::BuildDev b = proto;
     auto bind = [&](const std::vector<const void*>& ptr) {
         b.key = devcol(t, bcols[0], ptr[0]);
         for (int k = 1; k <= nf; ++k) b.dcol[k - 1] = devcol(t, bcols[k], ptr[k]);
-        if (d.dim_filter.col >= 0) b.fcol = devcol(t, bcols[nf + 1], ptr[nf + 1]);
+        if (flt.col >= 0) b.fcol = devcol(t, bcols[nf + 1], ptr[nf + 1]);
     };
     if (t->placement != PL_PAGES) {
         std::vector<const void*> ptr;
@@ -233,13 +235,14 @@ tp_status for_each_dim_batch(ExecState& S, Scratch& sc, const tpk::BuildDev& pro
     return TP_OK;
 }
 
-tp_status build_join(ExecState& S, Scratch& sc) {
+// Builds the join table of dimension k (S.jt, or S.jtx[k - 1]).
+tp_status build_join(ExecState& S, Scratch& sc, int k = 0) {
     tp_engine* e = S.e;
     cudaStream_t st = S.lane->compute;
-    return for_each_dim_batch(S, sc, build_proto(S), [&](const tpk::BuildDev& b, uint64_t rows) {
+    return for_each_dim_batch(S, sc, build_proto(S, k), [&](const tpk::BuildDev& b, uint64_t rows) {
         mark_launch(e);
         return cuda_check(tpk::launch_build(b, rows, e->num_sms, st), "build");
-    });
+    }, k);
 }
 
 // ------------------------------------------------------- fact batch driver
@@ -404,35 +407,35 @@ tp_status sample_selectivity(ExecState& S) {
     return TP_OK;
 }
 
-// Pass rate of the dimension predicate on 4096 evenly spaced dimension rows
-// (sizes the lookahead filter).
-tp_status sample_dim_selectivity(ExecState& S) {
+// Pass rate of dimension k's predicate on 4096 evenly spaced rows (sizes the
+// lookahead filter).
+tp_status sample_dim_selectivity(ExecState& S, int k) {
     tp_plan* p = S.p;
-    const tp_plan_desc& d = p->d;
-    tp_table* t = S.dim;
+    const tp_filter& f = p->dflt[k];
+    tp_table* t = p->dims[k];
     const uint32_t samples = 4096;
-    if (d.dim_filter.col < 0 || !t || t->rows == 0) { p->dim_selectivity = 1.0; return TP_OK; }
-    const int c = d.dim_filter.col;
+    if (f.col < 0 || !t || t->rows == 0) { p->dim_sel[k] = 1.0; return TP_OK; }
+    const int c = f.col;
     if (t->placement == PL_PAGES) {
         uint64_t pass = 0;
         for (uint32_t j = 0; j < samples; ++j) {
             const int64_t v = paged_value(t, c, (uint64_t)(((unsigned __int128)j * t->rows) / samples));
-            pass += (v >= d.dim_filter.lo && v <= d.dim_filter.hi);
+            pass += (v >= f.lo && v <= f.hi);
         }
-        p->dim_selectivity = (double)pass / samples;
+        p->dim_sel[k] = (double)pass / samples;
         return TP_OK;
     }
     tpk::QueryDev q{};
     q.fcol = devcol(t, c, t->dev_cols[c]);
-    q.flo = d.dim_filter.lo;
-    q.fhi = d.dim_filter.hi;
+    q.flo = f.lo;
+    q.fhi = f.hi;
     cudaStream_t st = S.lane->compute;
     TP_TRY_CUDA(cudaMemsetAsync(S.counters + 3, 0, sizeof(unsigned long long), st));
     TP_TRY_CUDA(tpk::launch_sample_filter(q, t->rows, samples, S.counters + 3, st));
     mark_launch(S.e);
     TP_TRY_CUDA(cudaMemcpyAsync(S.lane->host_words, S.counters + 3, 8, cudaMemcpyDeviceToHost, st));
     TP_TRY_CUDA(cudaStreamSynchronize(st));
-    p->dim_selectivity = (double)S.lane->host_words[0] / samples;
+    p->dim_sel[k] = (double)S.lane->host_words[0] / samples;
     return TP_OK;
 }
 
@@ -984,7 +987,7 @@ std::string cache_key(const ExecState& S) {
         k += buf;
     }
     for (int g = 0; g < d.n_group; ++g) {
-        if (d.group[g].side != TP_SIDE_DIM) continue;
+        if (S.p->gdim[g] != 0) continue;   // fields of the cached (first) dimension
         snprintf(buf, sizeof(buf), "|%d:%d:%d", d.group[g].col, d.group[g].bits, S.p->gdpos[g]);
         k += buf;
     }
@@ -1076,7 +1079,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
     {
         std::vector<bool> u(d.fact->types.size(), false);
         if (d.filter.col >= 0) u[d.filter.col] = true;
-        if (d.join.fact_col >= 0) u[d.join.fact_col] = true;
+        for (int k = 0; k < p->n_dims; ++k) u[p->joins[k].fact_col] = true;
         for (int g = 0; g < d.n_group; ++g)
             if (d.group[g].side == TP_SIDE_FACT) u[d.group[g].col] = true;
         for (int a = 0; a < d.n_agg; ++a) {
@@ -1102,7 +1105,8 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
     // ---- filter selectivity from a sample, once per plan (decides eager loads
     // and the first size estimate of a global aggregation table)
     if (p->selectivity < 0 && (s = sample_selectivity(S))) return s;
-    if (S.dim && p->dim_selectivity < 0 && (s = sample_dim_selectivity(S))) return s;
+    for (int k = 0; k < p->n_dims; ++k)
+        if (p->dim_sel[k] < 0 && (s = sample_dim_selectivity(S, k))) return s;
     S.eager = p->selectivity >= 0.25;
     // ---- reservation estimate (Section 3.3.2): streaming buffers and the
     // aggregation table first; a hashed join table that would crowd what is
@@ -1149,6 +1153,36 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         }
         est += agg_est;
     }
+    // ---- further tables of a star join: always resident, each sized like a
+    // first join's unpartitioned table, with its own lookahead filter under
+    // the same rule
+    struct XTab {
+        bool direct = false, key64 = false;
+        uint64_t range = 0, cap = 0, bytes = 0, lip_blocks = 0;
+    };
+    XTab xt[tpk::MAX_XJOIN];
+    for (int j = 0; j + 1 < p->n_dims; ++j) {
+        tp_table* t = p->dims[1 + j];
+        const int kc = p->joins[1 + j].dim_col;
+        XTab& x = xt[j];
+        x.key64 = t->types[kc] == TP_I64;
+        if (!(e->cfg.flags & TP_FLAG_NO_DIRECT_JOIN) && direct_join_range(t, kc, &x.range)) {
+            x.direct = true;
+            x.bytes = x.range * 4;
+        } else {
+            x.cap = pow2_at_least(std::max<uint64_t>(64, (uint64_t)std::ceil(t->rows / lf)));
+            x.bytes = x.cap * (x.key64 ? 16 : 8);
+        }
+        est += align256(x.bytes);
+        if (t->placement == PL_PAGES)   // build staging: key, fields and predicate columns
+            est += (has_narrow(t) ? 8 : 6) * align256(t->batch_rows * 8);
+        if (p->dflt[1 + j].col >= 0 && d.lip != TP_LIP_OFF && (d.lip == TP_LIP_ON || x.bytes >= LIP_TABLE_BYTES)) {
+            const double keys = std::ceil((double)t->rows * p->dim_sel[1 + j] * 1.5) + 1024;
+            x.lip_blocks = pow2_at_least((uint64_t)std::ceil(keys * LIP_BITS_PER_KEY / 256.0));
+            x.lip_blocks = std::min<uint64_t>(std::max<uint64_t>(x.lip_blocks, 2), LIP_MAX_BLOCKS);
+            est += x.lip_blocks * 32;
+        }
+    }
     uint64_t join_bytes = 0, full_join_bytes = 0;
     const bool lip_possible = S.dim && d.dim_filter.col >= 0 && d.lip != TP_LIP_OFF;
     uint64_t lip_blocks = 0, lip_bytes = 0;   // lookahead filter size, when possible
@@ -1168,7 +1202,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         }
         full_join_bytes = join_bytes;
         if (lip_possible) {
-            const double keys = std::ceil((double)S.dim->rows * p->dim_selectivity * 1.5) + 1024;
+            const double keys = std::ceil((double)S.dim->rows * p->dim_sel[0] * 1.5) + 1024;
             lip_blocks = pow2_at_least((uint64_t)std::ceil(keys * LIP_BITS_PER_KEY / 256.0));
             lip_blocks = std::min<uint64_t>(std::max<uint64_t>(lip_blocks, 2), LIP_MAX_BLOCKS);
             lip_bytes = lip_blocks * 32;
@@ -1266,6 +1300,31 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             return s;
         }
     }
+    for (int j = 0; j + 1 < p->n_dims; ++j) {   // the further tables of a star join
+        const XTab& x = xt[j];
+        tpk::JoinTable& jt = S.jtx[j];
+        void* slots = nullptr;
+        if ((s = sc.alloc(&slots, x.bytes))) return s;
+        TP_TRY_CUDA(cudaMemsetAsync(slots, 0xFF, x.bytes, st));
+        jt.slots = (uint64_t*)slots;
+        jt.direct = x.direct ? 1 : 0;
+        jt.kmin = x.direct ? p->dims[1 + j]->cmin[p->joins[1 + j].dim_col] : 0;
+        jt.range = x.range;
+        jt.mask = x.cap ? x.cap - 1 : 0;
+        jt.side = (uint32_t*)((uint8_t*)misc + 136 + 8 * j);   // zeroed with misc
+        jt.key64 = x.key64 ? 1 : 0;
+        if (x.lip_blocks) {
+            void* lip = nullptr;
+            if ((s = sc.alloc(&lip, x.lip_blocks * 32))) return s;
+            TP_TRY_CUDA(cudaMemsetAsync(lip, 0, x.lip_blocks * 32, st));
+            int lg = 0;
+            while ((1ull << lg) < x.lip_blocks) ++lg;
+            jt.lip = (uint32_t*)lip;
+            jt.lip_shift = 64 - lg;
+            e->lip_filters++;
+        }
+        if ((s = build_join(S, sc, 1 + j))) return s;
+    }
     // ---- aggregate
     tp_result* res = nullptr;
     KernelTimer timer(e);
@@ -1295,6 +1354,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             if (mode < 0) mode = can ? (fast ? 2 : 1) : 0;
             if (mode == 2 && !can) return fail(TP_E_INTERNAL, "staged layout changed between batches");
             mark_launch(e);
+            const bool multi = q.n_xjoin > 0;   // star join: run-time compiled or plain kernels only
             if (mode > 0 && can) {
                 const void* jk = nullptr;
                 if (want_jit) {
@@ -1309,6 +1369,11 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
                             e->jit_launches++;
                         }
                     }
+                }
+                if (multi && !jk) {
+                    return cuda_check(timer.run(st, rows, [&] {
+                        return tpk::launch_agg_shared(q, rows, (uint64_t*)gacc, p->key_bits, grid, st);
+                    }), "aggregate");
                 }
                 // the run-time compiled kernel takes the ragged tail itself
                 const uint64_t whole = jk ? rows : rows / (uint64_t)L.tile * (uint64_t)L.tile;
@@ -1498,7 +1563,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             auto global_core = [&](const tpk::QueryDev& q, uint64_t rows) -> tp_status {
                 mark_launch(e);
                 tpk::StageLayout L;
-                if (g_staged && tpk::staged_layout_global(q, stage_all, &L)) {
+                if (g_staged && q.n_xjoin == 0 && tpk::staged_layout_global(q, stage_all, &L)) {
                     const uint64_t whole_rows = rows / tpk::ST_TILE * tpk::ST_TILE;
                     tp_status r = cuda_check(timer.run(st, whole_rows, [&] {
                         return tpk::launch_agg_global_staged(q, L, rows, at, gfast, fold, e->num_sms, st);
@@ -1616,9 +1681,17 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
 namespace tp {
 
 tpk::QueryDev plan_query_dev(const tp_plan* p, const std::vector<const void*>& colptr, const tpk::JoinTable& jt,
-                             uint32_t* err, bool eager) {
+                             uint32_t* err, bool eager, const tpk::JoinTable* jtx) {
     const tp_plan_desc& d = p->d;
     tpk::QueryDev q{};
+    if (jtx) {   // star join: the further tables and their fact key columns
+        q.n_xjoin = p->n_dims > 1 ? p->n_dims - 1 : 0;
+        for (int j = 0; j < q.n_xjoin; ++j) {
+            const int c = p->joins[1 + j].fact_col;
+            q.fkx[j] = devcol(p->d.fact, c, colptr[c]);
+            q.jtx[j] = jtx[j];
+        }
+    }
     q.has_filter = d.filter.col >= 0;
     if (q.has_filter) {
         q.fcol = devcol(p->d.fact, d.filter.col, colptr[d.filter.col]);
@@ -1632,7 +1705,8 @@ tpk::QueryDev plan_query_dev(const tp_plan* p, const std::vector<const void*>& c
     }
     q.n_group = d.n_group;
     for (int g = 0; g < d.n_group; ++g) {
-        q.gside[g] = d.group[g].side;
+        q.gside[g] = d.group[g].side == TP_SIDE_FACT ? 0 : 1;
+        q.gdim[g] = p->gdim[g] < 0 ? 0 : p->gdim[g];
         q.gbits[g] = d.group[g].bits;
         q.gdpos[g] = p->gdpos[g];
         if (d.group[g].side == TP_SIDE_FACT) q.gcol[g] = devcol(p->d.fact, d.group[g].col, colptr[d.group[g].col]);
@@ -1696,7 +1770,7 @@ bool direct_group_range(const tp_plan* p, const tp_table* fact, const tp_table* 
     if (d.n_group == 0) return false;
     unsigned __int128 lo = 0, hi = 0;
     for (int g = 0; g < d.n_group; ++g) {
-        const tp_table* t = d.group[g].side == TP_SIDE_FACT ? fact : dim;
+        const tp_table* t = p->gdim[g] < 0 ? fact : (p->gdim[g] == 0 ? dim : p->dims[p->gdim[g]]);
         const int col = d.group[g].col, bits = d.group[g].bits;
         if (!t || t->rows == 0 || t->cmin[col] < 0) return false;
         if (bits < 64 && ((uint64_t)t->cmax[col] >> bits) != 0) return false;
@@ -1748,13 +1822,22 @@ std::string shape_struct(const std::string& name, const tpk::QueryDev& q, const 
         nar[s] = fast && mode[s] == 2 && q.skind[s] == tpk::S_MUL_SUB ? narrow[s] : 0;
     }
     const int join = !q.has_join ? 0 : (q.jt.direct ? 1 : (q.jt.key64 ? 3 : 2));
+    int xjoin[tpk::MAX_XJOIN] = {}, xktype[tpk::MAX_XJOIN] = {}, xlip[tpk::MAX_XJOIN] = {}, gdim[tpk::MAX_GROUP] = {};
+    for (int j = 0; j < q.n_xjoin; ++j) {
+        xjoin[j] = q.jtx[j].direct ? 1 : (q.jtx[j].key64 ? 3 : 2);
+        xktype[j] = q.fkx[j].type;
+        xlip[j] = q.jtx[j].lip != nullptr ? 1 : 0;
+    }
+    for (int g = 0; g < q.n_group; ++g) gdim[g] = q.gside[g] != 0 ? q.gdim[g] : 0;
     std::string r = "struct " + name + " {\n";
     r += "    static constexpr int filter = " + std::to_string(q.has_filter ? 1 : 0) +
          ", ftype = " + std::to_string(q.has_filter ? q.fcol.type : 0) + ", join = " + std::to_string(join) +
          ", ktype = " + std::to_string(q.has_join ? q.fk.type : 0) +
          ", part = " + std::to_string(q.has_join && q.jt.part_shift != 0 ? 1 : 0) +
          ", lip = " + std::to_string(q.has_join && q.jt.lip != nullptr ? 1 : 0) + ";\n";
-    r += "    static constexpr int ng = " + std::to_string(q.n_group) + ";\n";
+    r += "    static constexpr int nx = " + std::to_string(q.n_xjoin) + ", " + arr("xjoin", xjoin, tpk::MAX_XJOIN) +
+         ", " + arr("xktype", xktype, tpk::MAX_XJOIN) + ", " + arr("xlip", xlip, tpk::MAX_XJOIN) + ";\n";
+    r += "    static constexpr int ng = " + std::to_string(q.n_group) + ", " + arr("gdim", gdim, tpk::MAX_GROUP) + ";\n";
     r += "    static constexpr int " + arr("gside", gside, tpk::MAX_GROUP) + ", " + arr("gtype", gtype, tpk::MAX_GROUP) +
          ", " + arr("gbits", gbits, tpk::MAX_GROUP) + ";\n";
     r += "    static constexpr int ns = " + std::to_string(q.n_sum) + ";\n";
@@ -1848,29 +1931,56 @@ tp_status tp_plan_create(tp_engine* e, const tp_plan_desc* d, tp_plan** out) {
     if (d->lip < TP_LIP_AUTO || d->lip > TP_LIP_ON) return fail(TP_E_INVALID, "plan: bad lip mode");
     if (d->n_group < 0 || d->n_group > 4) return fail(TP_E_INVALID, "plan: 0..4 group fields");
     if (d->n_agg < 1 || d->n_agg > 8) return fail(TP_E_INVALID, "plan: 1..8 aggregates");
+    if (d->n_extra_dims < 0 || d->n_extra_dims > TP_MAX_EXTRA_DIMS || (d->n_extra_dims > 0 && !join))
+        return fail(TP_E_INVALID, "plan: 0..%d further dimensions, after a first join", TP_MAX_EXTRA_DIMS);
+    for (int j = 0; j < d->n_extra_dims; ++j) {
+        const tp_table* x = d->extra_dim[j];
+        if (!x || x->eng != e || !valid_col(f, d->extra_join[j].fact_col) || !valid_col(x, d->extra_join[j].dim_col))
+            return fail(TP_E_INVALID, "plan: bad further dimension %d or its join columns", j);
+        if (d->extra_dim_filter_on[j] && !valid_col(x, d->extra_dim_filter[j].col))
+            return fail(TP_E_INVALID, "plan: bad predicate column of further dimension %d", j);
+    }
     std::unique_ptr<tp_plan> p(new (std::nothrow) tp_plan());
     if (!p) return fail(TP_E_NOMEM, "plan: out of host memory");
     p->eng = e;
     p->d = *d;
     if (!d->dim_filter_on) p->d.dim_filter.col = -1;   // internally: col < 0 = no predicate
-    int key_bits = 0, dim_bits = 0;
+    if (join) {   // every joined dimension in one list: the first, then the further ones
+        p->n_dims = 1 + d->n_extra_dims;
+        p->dims[0] = d->dim;
+        p->joins[0] = d->join;
+        p->dflt[0] = p->d.dim_filter;
+        for (int j = 0; j < d->n_extra_dims; ++j) {
+            p->dims[1 + j] = d->extra_dim[j];
+            p->joins[1 + j] = d->extra_join[j];
+            p->dflt[1 + j] = d->extra_dim_filter[j];
+            if (!d->extra_dim_filter_on[j]) p->dflt[1 + j].col = -1;
+        }
+    }
+    int key_bits = 0, dim_bits[4] = {0, 0, 0, 0};
     for (int g = 0; g < d->n_group; ++g) {
         const tp_group_field& gf = d->group[g];
         if (gf.bits < 1 || gf.bits > 64) return fail(TP_E_INVALID, "plan: group field %d needs 1..64 bits", g);
         key_bits += gf.bits;
         p->gdpos[g] = 0;
+        p->gdim[g] = -1;
         if (gf.side == TP_SIDE_FACT) {
             if (!valid_col(f, gf.col)) return fail(TP_E_INVALID, "plan: bad group column %d", g);
-        } else if (gf.side == TP_SIDE_DIM) {
-            if (!join || !valid_col(d->dim, gf.col)) return fail(TP_E_INVALID, "plan: bad dimension group column %d", g);
-            p->gdpos[g] = dim_bits;
-            dim_bits += gf.bits;
+        } else if (gf.side >= TP_SIDE_DIM && gf.side < TP_SIDE_DIM + p->n_dims) {
+            const int k = gf.side - TP_SIDE_DIM;   // payload of dimension k
+            if (!valid_col(p->dims[k], gf.col)) return fail(TP_E_INVALID, "plan: bad dimension group column %d", g);
+            p->gdim[g] = k;
+            p->gdpos[g] = dim_bits[k];
+            dim_bits[k] += gf.bits;
         } else {
             return fail(TP_E_INVALID, "plan: bad group side %d", g);
         }
     }
     if (key_bits > 64) return fail(TP_E_INVALID, "plan: group key wider than 64 bits");
-    if (dim_bits > tpk::MAX_DIM_BITS) return fail(TP_E_INVALID, "plan: dimension group fields wider than 31 bits");
+    for (int k = 0; k < 4; ++k)
+        if (dim_bits[k] > tpk::MAX_DIM_BITS)
+            return fail(TP_E_INVALID, "plan: group fields of one dimension wider than 31 bits");
+    const int dim_bits0 = dim_bits[0];
     int ns = 0;
     for (int a = 0; a < d->n_agg; ++a) {
         const tp_agg& ag = d->aggs[a];
@@ -1890,7 +2000,7 @@ tp_status tp_plan_create(tp_engine* e, const tp_plan_desc* d, tp_plan** out) {
     }
     p->n_sum = ns;
     p->key_bits = key_bits;
-    p->dim_bits = dim_bits;
+    p->dim_bits = dim_bits0;
     p->load_factor = d->load_factor > 0 ? d->load_factor : e->cfg.load_factor;
     if (!(p->load_factor > 0.05f && p->load_factor <= 0.9f)) return fail(TP_E_INVALID, "plan: bad load factor");
     const int jp = d->join_partitions;

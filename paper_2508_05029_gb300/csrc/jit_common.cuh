@@ -13,6 +13,10 @@
 //   join, ktype              J_NONE / J_DIRECT / J_HASH32 / J_HASH64; fk type
 //   part                     partition filter on the join (hybrid join)
 //   lip                      lookahead (Bloom) filter tested before the probe
+//   nx, xjoin[], xktype[], xlip[]   further joins of a star query: kind, key
+//                            column type, lookahead filter
+//   gdim[]                   join whose payload holds dimension field F
+//                            (0 = the first, 1 + j = further join j)
 //   ng, gside[], gtype[], gbits[]   group fields, first field highest
 //   ns, skind[], atype[], btype[]   sums: S_SUM / S_MUL_SUB and column types
 //   mode[]                   1: low word, 2: low + carry word (fast), 0: exact
@@ -52,9 +56,9 @@ __device__ __forceinline__ uint32_t lds_lo(const unsigned char* col, uint32_t r)
 }
 
 // Column ids of a shape's columns: filter, join key, fact group field F,
-// sum I's first and second operand.
+// sum I's first and second operand, further join J's key.
 enum : int { CI_F = 0, CI_K = 1, CI_G = 2, CI_A = 2 + MAX_GROUP, CI_B = 2 + MAX_GROUP + MAX_SUM,
-             CI_N = 2 + MAX_GROUP + 2 * MAX_SUM };
+             CI_X = 2 + MAX_GROUP + 2 * MAX_SUM, CI_N = 2 + MAX_GROUP + 2 * MAX_SUM + MAX_XJOIN };
 
 // Row evaluation reads column CI's value of row r0 + 32 j through a column
 // source: ld<T, CI>(r0, j) (typed) and ld_lo<T, CI>(r0, j) (low 32 bits).
@@ -115,7 +119,8 @@ __device__ __forceinline__ constexpr uint32_t sum_word() {
 // Group field F (compile-time recursion over the fields).
 template <class S, int F, class C>
 __device__ __forceinline__ void group_fields(const QueryDev& q, const C& c, uint32_t r0,
-                                             const uint32_t pay[ST_RPL], uint32_t g[ST_RPL], uint32_t& pm) {
+                                             const uint32_t (&pay)[1 + MAX_XJOIN][ST_RPL], uint32_t g[ST_RPL],
+                                             uint32_t& pm) {
     if constexpr (F < S::ng) {
         constexpr int bits = S::gbits[F];
         if constexpr (S::gside[F] == 0) {
@@ -137,7 +142,7 @@ __device__ __forceinline__ void group_fields(const QueryDev& q, const C& c, uint
             const uint32_t mask = (bits >= 32) ? ~0u : ((1u << bits) - 1u);
             const int pos = q.gdpos[F];
 #pragma unroll
-            for (int j = 0; j < ST_RPL; ++j) g[j] = (g[j] << bits) | ((pay[j] >> pos) & mask);
+            for (int j = 0; j < ST_RPL; ++j) g[j] = (g[j] << bits) | ((pay[S::gdim[F]][j] >> pos) & mask);
         }
         group_fields<S, F + 1, C>(q, c, r0, pay, g, pm);
     }
@@ -206,6 +211,45 @@ __device__ __forceinline__ void sums(const QueryDev& q, const Tab& t, const C& c
     }
 }
 
+// Star join: further join J (and the following ones) of the rows in pm --
+// lookahead filter, probe of its own table, payload into pays[1 + J]; rows
+// without a partner leave pm.
+template <class S, int J, class C>
+__device__ __forceinline__ void further_joins(const QueryDev& q, const C& c, uint32_t r0,
+                                              uint32_t (&pays)[1 + MAX_XJOIN][ST_RPL], uint32_t& pm) {
+    if constexpr (J < S::nx) {
+        const JoinTable& jt = q.jtx[J];
+        int64_t key[ST_RPL];
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) key[j] = (int64_t)c.template ld<S::xktype[J], CI_X + J>(r0, j);
+        if constexpr (S::xlip[J]) lip_mask<ST_RPL>(jt, key, pm);
+        uint32_t* pay = pays[1 + J];
+        if constexpr (S::xjoin[J] == J_DIRECT) {
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) {
+                const uint64_t idx = (uint64_t)(key[j] - jt.kmin);
+                pay[j] = ((pm >> j) & 1u) && idx < jt.range ? __ldg((const unsigned int*)jt.slots + idx) : EMPTY32;
+            }
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j)
+                if (pay[j] == EMPTY32) pm &= ~(1u << j);
+        } else if constexpr (S::xjoin[J] == J_HASH32) {
+            probe_rows_k32(jt, key, pm, pay, q.err);
+        } else {
+            probe_rows_k64(jt, key, pm, pay, q.err);
+        }
+        uint32_t bad = 0;
+#pragma unroll
+        for (int j = 0; j < ST_RPL; ++j) bad |= (uint32_t)((pay[j] & PAYLOAD_BAD) != 0) << j;
+        if (bad & pm) {
+            atomicOr(q.err, ERR_RANGE);
+            pm &= ~bad;
+        }
+        if (!pm) return;
+        further_joins<S, J + 1, C>(q, c, r0, pays, pm);
+    }
+}
+
 // One warp's rows of a block (rows r0 + 32 j whose bit j is set in valid):
 // filter -> probe -> group key -> count and sums.
 template <class S, class C>
@@ -227,7 +271,8 @@ __device__ __forceinline__ void consume(const QueryDev& q, const Flt& flt, const
         pm &= valid;
         if (!pm) return;
     }
-    uint32_t pay[ST_RPL];
+    uint32_t pays[1 + MAX_XJOIN][ST_RPL];   // payloads of the first join and the further ones
+    uint32_t (&pay)[ST_RPL] = pays[0];
 #pragma unroll
     for (int j = 0; j < ST_RPL; ++j) pay[j] = 0;
     if constexpr (S::join != J_NONE && S::lip) {
@@ -269,10 +314,14 @@ __device__ __forceinline__ void consume(const QueryDev& q, const Flt& flt, const
         }
         if (!pm) return;
     }
+    if constexpr (S::nx > 0) {
+        further_joins<S, 0, C>(q, c, r0, pays, pm);
+        if (!pm) return;
+    }
     uint32_t g[ST_RPL];
 #pragma unroll
     for (int j = 0; j < ST_RPL; ++j) g[j] = 0;
-    group_fields<S, 0, C>(q, c, r0, pay, g, pm);
+    group_fields<S, 0, C>(q, c, r0, pays, g, pm);
     if (!pm) return;
 #pragma unroll
     for (int j = 0; j < ST_RPL; ++j) {
@@ -299,6 +348,14 @@ __device__ __forceinline__ void query_cols_rest(const QueryDev& q, uint64_t row,
     }
 }
 
+template <class S, int J>
+__device__ __forceinline__ void query_cols_x(const QueryDev& q, uint64_t row, Cols& c) {
+    if constexpr (J < S::nx) {
+        c.p[CI_X + J] = (const unsigned char*)q.fkx[J].ptr + row * sizeof(typename ColT<S::xktype[J]>::type);
+        query_cols_x<S, J + 1>(q, row, c);
+    }
+}
+
 template <class S>
 __device__ __forceinline__ Cols query_cols(const QueryDev& q, uint64_t row) {
     Cols c{};
@@ -306,6 +363,7 @@ __device__ __forceinline__ Cols query_cols(const QueryDev& q, uint64_t row) {
     if constexpr (S::join != J_NONE)
         c.p[CI_K] = (const unsigned char*)q.fk.ptr + row * sizeof(typename ColT<S::ktype>::type);
     query_cols_rest<S, 0, 0>(q, row, c);
+    query_cols_x<S, 0>(q, row, c);
     return c;
 }
 
@@ -319,12 +377,15 @@ struct ColType {   // element type of column CI in shape S (T_I64 for columns th
                            : CI == CI_K ? (S::join != J_NONE ? S::ktype : T_I64)
                            : CI < CI_A ? (CI - CI_G < S::ng && S::gside[CI - CI_G] == 0 ? S::gtype[CI - CI_G] : T_I64)
                            : CI < CI_B ? (CI - CI_A < S::ns ? S::atype[CI - CI_A] : T_I64)
-                           : (CI - CI_B < S::ns && S::skind[CI - CI_B] == S_MUL_SUB ? S::btype[CI - CI_B] : T_I64);
+                           : CI < CI_X ? (CI - CI_B < S::ns && S::skind[CI - CI_B] == S_MUL_SUB ? S::btype[CI - CI_B]
+                                                                                               : T_I64)
+                           : (CI - CI_X < S::nx ? S::xktype[CI - CI_X] : T_I64);
     static constexpr bool used = CI == CI_F ? (bool)S::filter
                                : CI == CI_K ? S::join != J_NONE
                                : CI < CI_A ? (CI - CI_G < S::ng && S::gside[CI - CI_G] == 0)
                                : CI < CI_B ? (CI - CI_A < S::ns)
-                               : (CI - CI_B < S::ns && S::skind[CI - CI_B] == S_MUL_SUB);
+                               : CI < CI_X ? (CI - CI_B < S::ns && S::skind[CI - CI_B] == S_MUL_SUB)
+                               : (CI - CI_X < S::nx);
 };
 
 template <class S>

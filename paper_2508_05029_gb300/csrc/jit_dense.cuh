@@ -93,6 +93,8 @@ extern "C" __global__ void __launch_bounds__(tpk::ST_THREADS, tpk::ST_CTAS)
     StageOffs o{};
     if constexpr (JS::filter) o.off[CI_F] = L.off[L.col_of_slot[SL_FILTER]];
     if constexpr (JS::join != J_NONE) o.off[CI_K] = L.off[L.col_of_slot[SL_FK]];
+#pragma unroll
+    for (int j = 0; j < JS::nx; ++j) o.off[CI_X + j] = L.off[L.col_of_slot[SL_FKX + j]];
     stage_offsets<JS, 0, 0>(L, o);
     constexpr uint32_t all = (1u << ST_RPL) - 1u;
     run_pipeline(q, L, n, smem + L.table_bytes, [&](const unsigned char* stage, uint64_t, uint32_t r0) {

@@ -45,6 +45,7 @@ constexpr int MAX_DIM_BITS = 31;                // dimension group fields share 
 constexpr uint32_t EMPTY32 = ~0u;
 constexpr int MAX_GROUP = 4;
 constexpr int MAX_SUM = 8;
+constexpr int MAX_XJOIN = 3;                    // further joins of a star query
 
 struct DevCol {
     const void* ptr;
@@ -106,6 +107,14 @@ struct QueryDev {
     DevCol sb[MAX_SUM];
     int64_t sk[MAX_SUM];
     uint32_t* err;
+    // star join: further joins, each on its own fact key column; a row must
+    // find a partner in every table.  gdim[g]: the join whose payload holds
+    // dimension field g (0 = jt, 1 + j = jtx[j])
+    int32_t n_xjoin;
+    int32_t gdim[MAX_GROUP];
+    int32_t pad_x;
+    DevCol fkx[MAX_XJOIN];
+    JoinTable jtx[MAX_XJOIN];
 };
 
 // Build-side parameters: key column, dim group fields packed into the payload.
@@ -197,7 +206,7 @@ constexpr StageGeom AOT_GEOM{ST_CONSUMERS, ST_RPL, ST_CTAS};
 constexpr StageGeom JIT_DENSE_GEOM{24, 2, 1};
 constexpr int JIT_DENSE_STAGES = 3;
 // column slots of a QueryDev: filter, fk, 4 group columns, 8 + 8 sum columns
-enum : int { SL_FILTER = 0, SL_FK = 1, SL_GROUP = 2, SL_SA = 6, SL_SB = 14, SL_COUNT = 22 };
+enum : int { SL_FILTER = 0, SL_FK = 1, SL_GROUP = 2, SL_SA = 6, SL_SB = 14, SL_FKX = 22, SL_COUNT = 25 };
 
 struct StageLayout {
     const void* src[ST_MAX_COLS];      // global base of each staged column
@@ -280,6 +289,7 @@ inline QueryDev offset_rows(const QueryDev& q, uint64_t row) {
     };
     adv(r.fcol);
     adv(r.fk);
+    for (int j = 0; j < MAX_XJOIN; ++j) adv(r.fkx[j]);
     for (int g = 0; g < MAX_GROUP; ++g) adv(r.gcol[g]);
     for (int s = 0; s < MAX_SUM; ++s) {
         adv(r.sa[s]);

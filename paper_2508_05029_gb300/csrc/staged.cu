@@ -228,6 +228,7 @@ bool staged_layout_shared(const QueryDev& q, uint32_t key_bits, bool fast, const
     bool ok = true;
     if (q.has_filter) ok = ok && add(SL_FILTER, q.fcol);
     if (q.has_join) ok = ok && add(SL_FK, q.fk);
+    for (int j = 0; j < q.n_xjoin; ++j) ok = ok && add(SL_FKX + j, q.fkx[j]);   // run-time compiled kernel only
     for (int g = 0; g < q.n_group; ++g)
         if (q.gside[g] == 0) ok = ok && add(SL_GROUP + g, q.gcol[g]);
     for (int s = 0; s < q.n_sum; ++s) {

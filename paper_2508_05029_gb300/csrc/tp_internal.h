@@ -155,7 +155,14 @@ struct tp_plan {
     // reservations)
     uint64_t history_groups = 0;
     double selectivity = -1.0;   // sampled filter pass rate, < 0 until measured
-    double dim_selectivity = -1.0;   // sampled dimension predicate pass rate
+    // joined dimensions: none, or the first (d.dim) and the star join's
+    // further ones, each with its join columns and predicate (col < 0: none)
+    int n_dims = 0;
+    tp_table* dims[4] = {};
+    tp_join joins[4] = {};
+    tp_filter dflt[4] = {};
+    double dim_sel[4] = {-1.0, -1.0, -1.0, -1.0};   // sampled predicate pass rates
+    int gdim[4] = {-1, -1, -1, -1};                 // dimension of group field g, -1: fact
 };
 
 struct tp_result {
@@ -218,9 +225,10 @@ const void* jit_kernel(tp_engine* e, const std::string& prelude, const char* ent
 tp_status reserve(tp_engine* e, uint64_t bytes);
 void release(tp_engine* e, uint64_t bytes);
 // QueryDev of a plan for one batch of fact columns (colptr[c] = device
-// address of fact column c's first row; nullptr for unread columns).
+// address of fact column c's first row; nullptr for unread columns); jtx:
+// the further tables of a star join.
 tpk::QueryDev plan_query_dev(const tp_plan* p, const std::vector<const void*>& colptr, const tpk::JoinTable& jt,
-                             uint32_t* err, bool eager);
+                             uint32_t* err, bool eager, const tpk::JoinTable* jtx = nullptr);
 // Dense dimension keys: the key range of column col is at most twice the
 // row count (and below 2^31), so a direct-mapped join table of *range slots
 // serves it.

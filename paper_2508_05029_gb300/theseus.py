@@ -85,7 +85,9 @@ class tp_plan_desc(ctypes.Structure):
                 ("n_agg", ctypes.c_int32), ("aggs", tp_agg * 8), ("agg_strategy", ctypes.c_int32),
                 ("load_factor", ctypes.c_float), ("expected_groups", ctypes.c_uint64),
                 ("join_partitions", ctypes.c_int32), ("dim_filter", tp_filter), ("dim_filter_on", ctypes.c_int32),
-                ("lip", ctypes.c_int32)]
+                ("lip", ctypes.c_int32), ("n_extra_dims", ctypes.c_int32), ("extra_dim", ctypes.c_void_p * 3),
+                ("extra_join", tp_join * 3), ("extra_dim_filter", tp_filter * 3),
+                ("extra_dim_filter_on", ctypes.c_int32 * 3)]
 
 
 class tp_i128(ctypes.Structure):
@@ -314,9 +316,16 @@ class Engine:
         return t
 
     def plan(self, fact: "Table", dim: "Table | None", query: dict, agg_strategy=TP_AGG_AUTO,
-             load_factor=0.0, expected_groups=0, join_partitions=0, lip=TP_LIP_AUTO) -> "Plan":
+             load_factor=0.0, expected_groups=0, join_partitions=0, lip=TP_LIP_AUTO,
+             extra_dims=None) -> "Plan":
         """query: filter / join / group / aggs as the oracle takes them, plus an
-        optional dim_filter = dict(col=<dimension column>, lo=, hi=)."""
+        optional dim_filter = dict(col=<dimension column>, lo=, hi=); a star join
+        adds extra_joins = [dict(fact_col, dim_col, optional dim_filter)] over the
+        tables extra_dims, their group fields on sides "dim1".."dim3"."""
+        xjoins = query.get("extra_joins") or []
+        extra_dims = list(extra_dims or [])
+        if len(xjoins) != len(extra_dims):
+            raise ValueError("one table in extra_dims per entry of extra_joins")
         d = tp_plan_desc()
         d.fact = fact.h
         d.dim = dim.h if dim is not None else None
@@ -324,10 +333,13 @@ class Engine:
         d.filter = tp_filter(-1, 0, 0) if f is None else tp_filter(fact.col(f["col"]), f["lo"], f["hi"])
         j = query.get("join")
         d.join = tp_join(-1, -1) if j is None else tp_join(fact.col(j["fact_col"]), dim.col(j["dim_col"]))
+        sides = {"fact": (TP_SIDE_FACT, fact), "dim": (TP_SIDE_DIM, dim)}
+        for j, t in enumerate(extra_dims):
+            sides[f"dim{j + 1}"] = (TP_SIDE_DIM + 1 + j, t)
         d.n_group = len(query["group"])
         for i, (side, col, bits) in enumerate(query["group"]):
-            tab = fact if side == "fact" else dim
-            d.group[i] = tp_group_field(TP_SIDE_FACT if side == "fact" else TP_SIDE_DIM, tab.col(col), bits)
+            code, tab = sides[side]
+            d.group[i] = tp_group_field(code, tab.col(col), bits)
         d.n_agg = len(query["aggs"])
         for i, ag in enumerate(query["aggs"]):
             if ag[0] == "sum":
@@ -346,6 +358,13 @@ class Engine:
         if df is not None:
             d.dim_filter, d.dim_filter_on = tp_filter(dim.col(df["col"]), df["lo"], df["hi"]), 1
         d.lip = lip
+        d.n_extra_dims = len(xjoins)
+        for j, (xj, t) in enumerate(zip(xjoins, extra_dims)):
+            d.extra_dim[j] = t.h
+            d.extra_join[j] = tp_join(fact.col(xj["fact_col"]), t.col(xj["dim_col"]))
+            xf = xj.get("dim_filter")
+            if xf is not None:
+                d.extra_dim_filter[j], d.extra_dim_filter_on[j] = tp_filter(t.col(xf["col"]), xf["lo"], xf["hi"]), 1
         h = ctypes.c_void_p()
         _check(self.lib.tp_plan_create(self.h, ctypes.byref(d), ctypes.byref(h)))
         return Plan(self, h, list(query["aggs"]))

@@ -20,8 +20,9 @@ def _nvrtc():
 
 
 def _shape(filter=1, ftype=0, join=1, ktype=0, part=0, lip=0, groups=((0, 2, 2), (0, 2, 1), (1, 0, 5)),
-           sums=((0, 1, 0, 1, 0), (1, 1, 1, 2, 1), (0, 1, 0, 1, 0)), fast=True):
-    """groups: (side, type, bits); sums: (kind, atype, btype, mode, narrow)."""
+           sums=((0, 1, 0, 1, 0), (1, 1, 1, 2, 1), (0, 1, 0, 1, 0)), fast=True, xjoins=(), gdim=(0, 0, 0, 0)):
+    """groups: (side, type, bits); sums: (kind, atype, btype, mode, narrow);
+    xjoins: further joins (kind, key type, lookahead); gdim: join of each dimension field."""
     def arr(name, vals, n):
         vals = list(vals) + [0] * (n - len(vals))
         return f"{name}[{n}] = {{{', '.join(map(str, vals))}}}"
@@ -30,7 +31,9 @@ def _shape(filter=1, ftype=0, join=1, ktype=0, part=0, lip=0, groups=((0, 2, 2),
     return ("struct JS {\n"
             f"  static constexpr int filter = {filter}, ftype = {ftype}, join = {join}, ktype = {ktype}, part = {part}, "
             f"lip = {lip};\n"
-            f"  static constexpr int ng = {len(groups)};\n"
+            f"  static constexpr int nx = {len(xjoins)}, {arr('xjoin', [x[0] for x in xjoins], 3)}, "
+            f"{arr('xktype', [x[1] for x in xjoins], 3)}, {arr('xlip', [x[2] for x in xjoins], 3)};\n"
+            f"  static constexpr int ng = {len(groups)}, {arr('gdim', gdim, 4)};\n"
             f"  static constexpr int {arr('gside', g[0], 4)}, {arr('gtype', g[1], 4)}, {arr('gbits', g[2], 4)};\n"
             f"  static constexpr int ns = {len(sums)};\n"
             f"  static constexpr int {arr('skind', s[0], 8)}, {arr('atype', s[1], 8)}, {arr('btype', s[2], 8)}, "
@@ -48,6 +51,8 @@ SHAPES = {
     "count-only": _shape(sums=()),
     "lip-direct": _shape(lip=1),
     "lip-hash64-partitioned": _shape(join=3, ktype=1, part=1, lip=1),
+    "star-three-further-joins": _shape(xjoins=((1, 0, 0), (2, 1, 1), (3, 1, 0)),
+                                       groups=((1, 0, 3), (1, 0, 4), (1, 0, 2), (1, 0, 2)), gdim=(0, 1, 2, 3)),
 }
 
 
