@@ -33,9 +33,9 @@ RANGE_1PCT = 25        # [lo, lo + 25] keeps 26/2557 = 1.02%
 SEEDS = {1: 0x7E5E0001, 2: 0x7E5E0002, 3: 0x7E5E0003, 4: 0x7E5E0004, 5: 0x7E5E0005}
 
 # stream ids: table * 64 + column
-_FACT, _DIM, _META = 0, 1, 2
-S_FK, S_DATE, S_QTY, S_PRICE, S_DISC, S_FLAG, S_STATUS, S_OKEY = range(8)
-S_PK, S_ATTR = 0, 1
+_FACT, _DIM, _META, _XDIM = 0, 1, 2, 3
+S_FK, S_DATE, S_QTY, S_PRICE, S_DISC, S_FLAG, S_STATUS, S_OKEY, S_FKX = range(9)
+S_PK, S_ATTR, S_BAND = 0, 1, 2
 
 
 def _s(table, col, sub=0):
@@ -164,6 +164,22 @@ def config3(n_fact=600_000_000, n_dim=150_000_000, seed=SEEDS[3]) -> Workload:
     idx = index(seed, _s(_FACT, S_FK), n_dim, n_fact)
     fact = dict(fk=gather(dim["pk"], idx), **_measures(seed, n_fact))
     return Workload(f"star-{n_fact}-outofcore", fact, dim, q_lowcard())
+
+
+def star_dim(n_dim, seed, j=0):
+    """Further dimension j of a star join: unique sparse int64 keys (raw
+    SplitMix64 outputs, distinct per row), attr in 25 values, band in 4."""
+    return dict(
+        pk=fill(seed, _s(_XDIM, S_PK, j), RAW64, np.int64, n_dim),
+        attr=uniform(seed, _s(_XDIM, S_ATTR, j), np.int32, n_dim, 0, 24),
+        band=uniform(seed, _s(_XDIM, S_BAND, j), np.uint8, n_dim, 0, 3),
+    )
+
+
+def star_fk(n_fact, n_dim, seed, j=0):
+    """The fact foreign key into star_dim(n_dim, seed, j): uniform over its rows."""
+    idx = index(seed, _s(_FACT, S_FKX, j), n_dim, n_fact)
+    return raw_at(seed, _s(_XDIM, S_PK, j), idx)
 
 
 def config4_sizes(n_queries=256, seed=SEEDS[4], fact_lo=10_000, fact_hi=50_000_000,
