@@ -59,6 +59,7 @@ class _Query(ctypes.Structure):
         ("xdim", ctypes.POINTER(_Column) * 3), ("xjoin_fact_col", ctypes.c_int32 * 3),
         ("xjoin_dim_col", ctypes.c_int32 * 3), ("xdim_filter_col", ctypes.c_int32 * 3),
         ("xdim_filter_lo", ctypes.c_int64 * 3), ("xdim_filter_hi", ctypes.c_int64 * 3),
+        ("join_many", ctypes.c_int32),
     ]
 
 
@@ -129,7 +130,8 @@ def run(wl) -> OracleResult:
 
 
 def run_query(fact: dict, dim: dict | None, query: dict, extra_dims: list | None = None) -> OracleResult:
-    """query: filter, join, group, aggs, optional dim_filter; a star join adds
+    """query: filter, join (with many=True: repeated build keys, fan-out), group,
+    aggs, optional dim_filter; a star join adds
     extra_joins = [dict(fact_col, dim_col, optional dim_filter), ...] over the
     tables extra_dims, whose group fields use sides "dim1", "dim2", "dim3"."""
     lib = _load()
@@ -152,6 +154,7 @@ def run_query(fact: dict, dim: dict | None, query: dict, extra_dims: list | None
         q.join_fact_col, q.join_dim_col = -1, -1
     else:
         q.join_fact_col, q.join_dim_col = fnames.index(j["fact_col"]), dnames.index(j["dim_col"])
+        q.join_many = 1 if j.get("many") else 0
     df = query.get("dim_filter")
     if df is None:
         q.dim_filter_col, q.dim_filter_lo, q.dim_filter_hi = -1, 0, 0

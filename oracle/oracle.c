@@ -14,6 +14,9 @@
  *      sorted and searched by bisection; duplicates among them are an error.
  *      A star join repeats this for every further dimension, each on its own
  *      fact foreign key: a fact row survives only with a partner in all.
+ *      With join_many the first dimension's keys may repeat: the fact row
+ *      pairs with each of its partners there, and every pair is a row of the
+ *      join (the relational inner join without the key constraint).
  *   3. Group and aggregate: the group key concatenates the group fields, the
  *      first field in the highest bits.  Surviving (key, row) pairs are sorted
  *      and each run of equal keys is reduced with exact 128-bit integer sums
@@ -165,12 +168,15 @@ int32_t orc_run(const orc_query* q, orc_result* out) {
             ++n_adm[k];
         }
         qsort(dim[k], n_adm[k], sizeof(key_row), cmp_key_row_signed);
+        if (k == 0 && q->join_many) continue;   /* repeated keys are partners, not an error */
         for (uint64_t i = 1; i < n_adm[k]; ++i)
             if (dim[k][i].key == dim[k][i - 1].key) { rc = ORC_DUP_KEY; goto out; }
     }
 
-    /* Filter, join and key every fact row; keep (group key, fact row). */
-    kept = (key_row*)malloc((q->n_fact ? q->n_fact : 1) * sizeof(key_row));
+    /* Filter, join and key every fact row; keep (group key, fact row) per
+     * joined row. */
+    uint64_t cap_kept = q->n_fact ? q->n_fact : 1;
+    kept = (key_row*)malloc(cap_kept * sizeof(key_row));
     if (!kept) { rc = ORC_NOMEM; goto out; }
     for (uint64_t i = 0; i < q->n_fact; ++i) {
         if (q->filter_col >= 0) {
@@ -185,6 +191,22 @@ int32_t orc_run(const orc_query* q, orc_result* out) {
             joined = d[k] >= 0;
         }
         if (!joined) continue;
+        /* partners in the first dimension: one, or with join_many every
+         * admitted row with the key (the sorted run starting at the first) */
+        uint64_t first = 0, n_partner = 1;
+        if (nd > 0 && q->join_many) {
+            const int64_t fk = col_at(&q->fact[q->join_fact_col], i);
+            uint64_t lo = 0, hi = n_adm[0];
+            while (lo < hi) {
+                uint64_t mid = lo + (hi - lo) / 2;
+                if (dim[0][mid].key < fk) lo = mid + 1; else hi = mid;
+            }
+            first = lo;
+            n_partner = 0;
+            while (first + n_partner < n_adm[0] && dim[0][first + n_partner].key == fk) ++n_partner;
+        }
+        for (uint64_t m = 0; m < n_partner; ++m) {
+        if (nd > 0 && q->join_many) d[0] = (int64_t)dim[0][first + m].row;
         uint64_t key = 0;
         for (int g = 0; g < q->n_group; ++g) {
             int bits = q->group_bits[g];
@@ -198,9 +220,16 @@ int32_t orc_run(const orc_query* q, orc_result* out) {
                 key = (uint64_t)v;
             }
         }
+        if (n_kept == cap_kept) {
+            key_row* grown = (key_row*)realloc(kept, 2 * cap_kept * sizeof(key_row));
+            if (!grown) { rc = ORC_NOMEM; goto out; }
+            kept = grown;
+            cap_kept *= 2;
+        }
         kept[n_kept].key = (int64_t)key;
         kept[n_kept].row = i;
         ++n_kept;
+        }
     }
     for (int k = 0; k < 4; ++k) { free(dim[k]); dim[k] = NULL; }
     qsort(kept, n_kept, sizeof(key_row), cmp_key_row_unsigned);

@@ -73,6 +73,10 @@ typedef struct {
     int32_t xjoin_fact_col[3], xjoin_dim_col[3];
     int32_t xdim_filter_col[3];          /* -1: every row */
     int64_t xdim_filter_lo[3], xdim_filter_hi[3];
+    /* first join with repeated build keys allowed: a fact row pairs with
+     * every admitted dimension row holding its key (fan-out), and every pair
+     * counts once in its group */
+    int32_t join_many;
 } orc_query;
 
 typedef struct {

@@ -27,7 +27,7 @@ def evaluate(fact: dict, dim: dict | None, query: dict, extra_dims: list | None 
         pk = [int(x) for x in tab[join["dim_col"]]] if tab else []
         for a in range(n_dim):
             for b in range(a + 1, n_dim):
-                if lv[a] and lv[b] and pk[a] == pk[b]:
+                if lv[a] and lv[b] and pk[a] == pk[b] and not join.get("many"):
                     raise ValueError("dup_key")
         live.append(lv)
         pks.append(pk)

@@ -237,6 +237,65 @@ def test_star_join_order_of_dimensions_is_irrelevant():
     assert np.array_equal(base.sums, sw.sums)
 
 
+def _fanout_tiny(seed, n_fact, n_keys, span):
+    """A dimension whose keys repeat: key k appears 1 + (k mod 4) times (some
+    rows with different attributes), shuffled."""
+    fact, _ = _tiny(seed, n_fact, 0, span)
+    reps = 1 + np.arange(n_keys) % 4
+    pk = np.repeat(np.arange(n_keys, dtype=np.int32), reps)
+    perm = datagen.fill(3000 + seed, 1, datagen.PERM, np.int64, len(pk), b=len(pk))
+    dim = dict(pk=pk[perm], attr=datagen.uniform(3000 + seed, 2, np.int32, len(pk), 0, 24))
+    return fact, dim
+
+
+@pytest.mark.parametrize("seed,dflt", [(70, None), (71, dict(col="attr", lo=4, hi=15)), (72, dict(col="attr", lo=30, hi=31))])
+def test_fanout_join_matches_bruteforce(seed, dflt):
+    fact, dim = _fanout_tiny(seed, 800, 60, 75)
+    q = dict(W.q_lowcard(), join=dict(fact_col="fk", dim_col="pk", many=True), dim_filter=dflt)
+    got = _check_against_brute(fact, dim, q)
+    partners = {}
+    for k, a in zip(dim["pk"], dim["attr"]):
+        if dflt is None or dflt["lo"] <= a <= dflt["hi"]:
+            partners[int(k)] = partners.get(int(k), 0) + 1
+    want = sum(partners.get(int(fk), 0) for fk, dt in zip(fact["fk"], fact["date"]) if dt <= W.CUTOFF_98)
+    assert int(got.counts.sum()) == want
+    if dflt is None:   # without fan-out the repeated keys are an error
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.run_query(fact, dim, dict(q, join=dict(fact_col="fk", dim_col="pk")))
+        assert e.value.status == "dup_key"
+
+
+def test_fanout_of_identical_rows_doubles_everything():
+    """Every dimension row present twice: each group's count and sums are
+    exactly twice those of the join with unique keys."""
+    fact, dim = _tiny(73, 5000, 300, 350, signed=True)
+    twice = {k: np.concatenate([v, v]) for k, v in dim.items()}
+    q = W.q_lowcard()
+    one = oracle.run_query(fact, dim, q)
+    two = oracle.run_query(fact, twice, dict(q, join=dict(q["join"], many=True)))
+    assert np.array_equal(one.keys, two.keys)
+    assert np.array_equal(2 * one.counts, two.counts)
+    for g in range(one.n_groups):
+        for a in (0, 1, 2):
+            assert two.sum_int(g, a) == 2 * one.sum_int(g, a)
+
+
+def test_fanout_with_a_further_dimension():
+    fact, dim = _fanout_tiny(74, 600, 40, 50)
+    _, _, extra = _star_tiny(74, 600, [40, 30], [50, 40])
+    fact["fk2"] = datagen.uniform(4074, 5, np.int64, 600, 0, 39)
+    q = dict(W.q_lowcard(), join=dict(fact_col="fk", dim_col="pk", many=True),
+             extra_joins=[dict(fact_col="fk2", dim_col="pk", dim_filter=dict(col="band", lo=0, hi=2))])
+    q["group"] = [("fact", "flag", 2), ("dim", "attr", 5), ("dim1", "band", 2)]
+    ref = bruteforce.evaluate(fact, dim, q, extra)
+    got = oracle.run_query(fact, dim, q, extra)
+    assert got.n_groups == len(ref)
+    for g, (key, count, sums, _) in enumerate(ref):
+        assert int(got.keys[g]) == key and int(got.counts[g]) == count
+        for a in range(len(q["aggs"])):
+            assert got.sum_int(g, a) == sums[a]
+
+
 def _modular_closed_form(n_fact, n_dim):
     """Per-group (count, SUM qty, SUM price*(100-disc), SUM disc) on the
     modular dataset, from arithmetic series.  Row i has flag = i mod 3,
