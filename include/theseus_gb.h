@@ -312,6 +312,14 @@ typedef struct {
     tp_join extra_join[TP_MAX_EXTRA_DIMS];
     tp_filter extra_dim_filter[TP_MAX_EXTRA_DIMS];
     int32_t extra_dim_filter_on[TP_MAX_EXTRA_DIMS];
+    /* Fan-out: the first join's build keys may repeat.  A fact row then pairs
+     * with every admitted dimension row holding its key (an inner join
+     * without the key constraint) and every pair counts once in its group.
+     * The build sorts the admitted rows by key and indexes the first row of
+     * each key.  Never partitioned (join_partitions must be 0 or 1;
+     * TP_E_BUDGET when the table does not fit), not cached by the server;
+     * batched executions and the allocation-free entry point refuse it. */
+    int32_t join_many;
 } tp_plan_desc;
 
 /* Validates and stores a plan.  TP_E_INVALID on any inconsistency. */

@@ -314,6 +314,7 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
         if (p->d.fact->placement == PL_PAGES || (p->d.join.fact_col >= 0 && p->d.dim->placement == PL_PAGES))
             return fail(TP_E_INVALID, "tp_batch_create: plan %d reads a table in host pages", i);
         if (p->n_dims > 1) return fail(TP_E_INVALID, "tp_batch_create: plan %d is a star join (one dimension here)", i);
+        if (p->d.join_many) return fail(TP_E_INVALID, "tp_batch_create: plan %d has a fan-out join", i);
         if (p->key_bits > 20) return fail(TP_E_INVALID, "tp_batch_create: plan %d has a %d-bit group key (at most 20)", i,
                                           p->key_bits);
     }

@@ -292,7 +292,7 @@ __device__ __forceinline__ bool any4(const bool p[4]) { return p[0] || p[1] || p
 // Returns false when no row of the lane survives.
 template <bool FULL, bool NC = true>
 __device__ __forceinline__ bool eval_keys(const QueryDev& q, uint64_t t0, uint64_t n, int lane,
-                                          bool pass[4], uint64_t key[4]) {
+                                          bool pass[4], uint64_t key[4], uint32_t m = 0) {
     const uint64_t r = t0 + 2ull * (uint64_t)lane;
     const uint64_t rows[4] = {r, r + 1, r + 64, r + 65};
 #pragma unroll
@@ -308,6 +308,15 @@ __device__ __forceinline__ bool eval_keys(const QueryDev& q, uint64_t t0, uint64
     if (q.has_join) {
         load_rows<FULL>(q.fk, r, n, pass, v);
         probe4<NC>(q.jt, v, pass, payload, q.err);
+        if (q.jt.many) {   // fan-out: the m-th row of the key's run, if the run is that long
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (!pass[i]) continue;
+                const uint64_t at = (uint64_t)payload[i] + m;
+                pass[i] = at < q.jt.mn && __ldg(q.jt.mkeys + at) == (uint64_t)v[i];
+                if (pass[i]) payload[i] = __ldg(q.jt.mpay + at);
+            }
+        }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (pass[i] && (payload[i] & PAYLOAD_BAD)) {

@@ -245,6 +245,56 @@ tp_status build_join(ExecState& S, Scratch& sc, int k = 0) {
     }, k);
 }
 
+// Fan-out build of the first join: the admitted rows' (key, payload) pairs
+// sorted by key; the table maps each key to the index of its run's first row.
+tp_status build_join_many(ExecState& S, Scratch& sc) {
+    tp_engine* e = S.e;
+    cudaStream_t st = S.lane->compute;
+    const uint64_t n_rows = S.dim->rows;
+    void *k0 = nullptr, *v0 = nullptr, *k1 = nullptr, *v1 = nullptr, *hist = nullptr, *hk = nullptr, *hv = nullptr,
+         *ctr = nullptr;
+    const uint64_t c = n_rows ? n_rows : 1;
+    tp_status s;
+    if ((s = sc.alloc(&k0, c * 8)) || (s = sc.alloc(&v0, c * 4)) || (s = sc.alloc(&k1, c * 8)) ||
+        (s = sc.alloc(&v1, c * 4)) || (s = sc.alloc(&hist, tpk::radix_sort_hist_words(c) * 4)) ||
+        (s = sc.alloc(&hk, c * 8)) || (s = sc.alloc(&hv, c * 4)) || (s = sc.alloc(&ctr, 16)))
+        return s;
+    TP_TRY_CUDA(cudaMemsetAsync(ctr, 0, 16, st));
+    unsigned long long* cnt = (unsigned long long*)ctr;
+    s = for_each_dim_batch(S, sc, build_proto(S), [&](const tpk::BuildDev& b, uint64_t rows) {
+        mark_launch(e);
+        return cuda_check(tpk::launch_many_collect(b, rows, (uint64_t*)k0, (uint32_t*)v0, cnt, e->num_sms, st),
+                          "fan-out build");
+    });
+    if (s) return s;
+    TP_TRY_CUDA(cudaMemcpyAsync(S.lane->host_words, cnt, 8, cudaMemcpyDeviceToHost, st));
+    TP_TRY_CUDA(cudaStreamSynchronize(st));
+    const uint64_t n = S.lane->host_words[0];
+    if (n >= (1ull << 31)) return fail(TP_E_INVALID, "fan-out join: more than 2^31 build rows");
+    uint64_t *kk = (uint64_t*)k0, *tk = (uint64_t*)k1;
+    uint32_t *vv = (uint32_t*)v0, *tv = (uint32_t*)v1;
+    TP_TRY_CUDA(tpk::radix_sort_pairs(&kk, &vv, &tk, &tv, (uint32_t*)hist, n, 64, st));
+    e->launches += 3 * 8;
+    TP_TRY_CUDA(tpk::launch_many_heads(kk, n, (int64_t*)hk, (uint32_t*)hv, cnt + 1, e->num_sms, st));
+    mark_launch(e);
+    TP_TRY_CUDA(cudaMemcpyAsync(S.lane->host_words, cnt + 1, 8, cudaMemcpyDeviceToHost, st));
+    TP_TRY_CUDA(cudaStreamSynchronize(st));
+    const uint64_t heads = S.lane->host_words[0];
+    TP_TRY_CUDA(tpk::launch_build_pairs(S.jt, (const int64_t*)hk, (const uint32_t*)hv, heads, S.err, e->num_sms, st));
+    mark_launch(e);
+    S.jt.mkeys = kk;
+    S.jt.mpay = vv;
+    S.jt.mn = n;
+    S.jt.many = 1;
+    return TP_OK;
+}
+
+// Bytes build_join_many allocates for a dimension of n rows.
+uint64_t many_build_bytes(uint64_t n) {
+    const uint64_t c = n ? n : 1;
+    return 3 * align256(c * 8) + 3 * align256(c * 4) + align256(tpk::radix_sort_hist_words(c) * 4) + 256;
+}
+
 // ------------------------------------------------------- fact batch driver
 
 // Runs `kernel(q, rows, colptr)` over every batch of the fact table; colptr[c]
@@ -1224,7 +1274,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             const uint64_t taken = reserved_now + est + dim_stage + result_est + (lip_possible ? lip_bytes : 0);
             const uint64_t avail = cap_now > taken ? cap_now - taken : 0;
             const int jp = d.join_partitions;
-            if (jp > 1 || (jp == 0 && join_bytes > avail / 2)) {
+            if (!d.join_many && (jp > 1 || (jp == 0 && join_bytes > avail / 2))) {   // fan-out: never partitioned
                 pj.on = true;
                 pj.P = jp > 1 ? jp : 64;
                 pj.shift = 64;
@@ -1244,7 +1294,8 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
                 join_bytes = part_table_budget + stage;
             }
         }
-        if (!(cache && !pj.on)) est += align256(join_bytes);   // a cached table holds its own reservation
+        if (!(cache && !pj.on) || d.join_many) est += align256(join_bytes);   // a cached table holds its own reservation
+        if (d.join_many) est += many_build_bytes(S.dim->rows);
         est += dim_stage;
     }
     est -= agg_est;   // the global table is reserved per key range
@@ -1254,7 +1305,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
     // join table would not stay in L2 or the join is partitioned (or asked
     // for); tables shared through the cache go without.  Optional: when its
     // reservation is refused the query runs without it.
-    if (lip_possible && !(cache && !pj.on) &&
+    if (lip_possible && !(cache && !pj.on && !d.join_many) &&
         (d.lip == TP_LIP_ON || pj.on || full_join_bytes >= LIP_TABLE_BYTES)) {
         if (reserve(e, lip_bytes) == TP_OK) {
             sc.reserved += lip_bytes;
@@ -1272,7 +1323,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
     }
     // ---- join table
     CacheUse cu;
-    if (S.dim && cache && !pj.on) {
+    if (S.dim && cache && !pj.on && !d.join_many) {
         s = cache_lookup_or_build(S, sc, cache, join_bytes, &cu);
         if (s) return s;
     }
@@ -1294,6 +1345,8 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         if (pj.on) {
             const tpk::BuildDev proto = build_proto(S);
             if ((s = part_setup(S, sc, pj, part_table_budget, lf, proto))) return s;
+        } else if (d.join_many) {
+            if ((s = build_join_many(S, sc))) return s;
         } else if (cu.building) {
             if ((s = cache_publish(S, sc, cache, &cu))) return s;
         } else if ((s = build_join(S, sc))) {
@@ -1354,7 +1407,8 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             if (mode < 0) mode = can ? (fast ? 2 : 1) : 0;
             if (mode == 2 && !can) return fail(TP_E_INTERNAL, "staged layout changed between batches");
             mark_launch(e);
-            const bool multi = q.n_xjoin > 0;   // star join: run-time compiled or plain kernels only
+            // star joins and fan-out: run-time compiled or plain kernels only
+            const bool multi = q.n_xjoin > 0 || q.jt.many;
             if (mode > 0 && can) {
                 const void* jk = nullptr;
                 if (want_jit) {
@@ -1563,7 +1617,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             auto global_core = [&](const tpk::QueryDev& q, uint64_t rows) -> tp_status {
                 mark_launch(e);
                 tpk::StageLayout L;
-                if (g_staged && q.n_xjoin == 0 && tpk::staged_layout_global(q, stage_all, &L)) {
+                if (g_staged && q.n_xjoin == 0 && !q.jt.many && tpk::staged_layout_global(q, stage_all, &L)) {
                     const uint64_t whole_rows = rows / tpk::ST_TILE * tpk::ST_TILE;
                     tp_status r = cuda_check(timer.run(st, whole_rows, [&] {
                         return tpk::launch_agg_global_staged(q, L, rows, at, gfast, fold, e->num_sms, st);
@@ -1834,7 +1888,8 @@ std::string shape_struct(const std::string& name, const tpk::QueryDev& q, const 
          ", ftype = " + std::to_string(q.has_filter ? q.fcol.type : 0) + ", join = " + std::to_string(join) +
          ", ktype = " + std::to_string(q.has_join ? q.fk.type : 0) +
          ", part = " + std::to_string(q.has_join && q.jt.part_shift != 0 ? 1 : 0) +
-         ", lip = " + std::to_string(q.has_join && q.jt.lip != nullptr ? 1 : 0) + ";\n";
+         ", lip = " + std::to_string(q.has_join && q.jt.lip != nullptr ? 1 : 0) +
+         ", many = " + std::to_string(q.has_join && q.jt.many ? 1 : 0) + ";\n";
     r += "    static constexpr int nx = " + std::to_string(q.n_xjoin) + ", " + arr("xjoin", xjoin, tpk::MAX_XJOIN) +
          ", " + arr("xktype", xktype, tpk::MAX_XJOIN) + ", " + arr("xlip", xlip, tpk::MAX_XJOIN) + ";\n";
     r += "    static constexpr int ng = " + std::to_string(q.n_group) + ", " + arr("gdim", gdim, tpk::MAX_GROUP) + ";\n";
@@ -1931,6 +1986,8 @@ tp_status tp_plan_create(tp_engine* e, const tp_plan_desc* d, tp_plan** out) {
     if (d->lip < TP_LIP_AUTO || d->lip > TP_LIP_ON) return fail(TP_E_INVALID, "plan: bad lip mode");
     if (d->n_group < 0 || d->n_group > 4) return fail(TP_E_INVALID, "plan: 0..4 group fields");
     if (d->n_agg < 1 || d->n_agg > 8) return fail(TP_E_INVALID, "plan: 1..8 aggregates");
+    if (d->join_many && (!join || d->join_partitions > 1))
+        return fail(TP_E_INVALID, "plan: a fan-out join needs a join and is never partitioned");
     if (d->n_extra_dims < 0 || d->n_extra_dims > TP_MAX_EXTRA_DIMS || (d->n_extra_dims > 0 && !join))
         return fail(TP_E_INVALID, "plan: 0..%d further dimensions, after a first join", TP_MAX_EXTRA_DIMS);
     for (int j = 0; j < d->n_extra_dims; ++j) {

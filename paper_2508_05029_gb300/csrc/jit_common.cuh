@@ -17,6 +17,7 @@
 //                            column type, lookahead filter
 //   gdim[]                   join whose payload holds dimension field F
 //                            (0 = the first, 1 + j = further join j)
+//   many                     the first join fans out (repeated build keys)
 //   ng, gside[], gtype[], gbits[]   group fields, first field highest
 //   ns, skind[], atype[], btype[]   sums: S_SUM / S_MUL_SUB and column types
 //   mode[]                   1: low word, 2: low + carry word (fast), 0: exact
@@ -211,6 +212,24 @@ __device__ __forceinline__ void sums(const QueryDev& q, const Tab& t, const C& c
     }
 }
 
+// Group key, count and sums of the rows in pm, whose join payloads are pays.
+template <class S, class C>
+__device__ __forceinline__ void accumulate(const QueryDev& q, const Tab& t, const C& c, uint32_t r0,
+                                           const uint32_t (&pays)[1 + MAX_XJOIN][ST_RPL], uint32_t pm) {
+    uint32_t g[ST_RPL];
+#pragma unroll
+    for (int j = 0; j < ST_RPL; ++j) g[j] = 0;
+    group_fields<S, 0, C>(q, c, r0, pays, g, pm);
+    if (!pm) return;
+#pragma unroll
+    for (int j = 0; j < ST_RPL; ++j) {
+        if (!(pm >> j & 1u)) continue;
+        if constexpr (S::fast) atomicAdd((unsigned int*)t.base + g[j], 1u);
+        else atomicAdd((unsigned long long*)t.base + g[j], 1ull);
+    }
+    sums<S, 0, C>(q, t, c, r0, g, pm);
+}
+
 // Star join: further join J (and the following ones) of the rows in pm --
 // lookahead filter, probe of its own table, payload into pays[1 + J]; rows
 // without a partner leave pm.
@@ -318,18 +337,37 @@ __device__ __forceinline__ void consume(const QueryDev& q, const Flt& flt, const
         further_joins<S, 0, C>(q, c, r0, pays, pm);
         if (!pm) return;
     }
-    uint32_t g[ST_RPL];
+    if constexpr (S::many) {
+        // fan-out: pay[j] is the first row of the key's run in the sorted
+        // build rows; pair the row with each row of the run in turn
+        uint32_t first[ST_RPL];
+        int64_t key[ST_RPL];
 #pragma unroll
-    for (int j = 0; j < ST_RPL; ++j) g[j] = 0;
-    group_fields<S, 0, C>(q, c, r0, pays, g, pm);
-    if (!pm) return;
+        for (int j = 0; j < ST_RPL; ++j) {
+            first[j] = pay[j];
+            key[j] = (int64_t)c.template ld<S::ktype, CI_K>(r0, j);
+        }
+        uint32_t live = pm;
+        for (uint32_t m = 0; live; ++m) {
 #pragma unroll
-    for (int j = 0; j < ST_RPL; ++j) {
-        if (!(pm >> j & 1u)) continue;
-        if constexpr (S::fast) atomicAdd((unsigned int*)t.base + g[j], 1u);
-        else atomicAdd((unsigned long long*)t.base + g[j], 1ull);
+            for (int j = 0; j < ST_RPL; ++j) {
+                if (!((live >> j) & 1u)) continue;
+                const uint64_t at = (uint64_t)first[j] + m;
+                if (at < q.jt.mn && __ldg(q.jt.mkeys + at) == (uint64_t)key[j]) pay[j] = __ldg(q.jt.mpay + at);
+                else live &= ~(1u << j);
+            }
+            uint32_t pmm = live, bad = 0;
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) bad |= (uint32_t)((pay[j] & PAYLOAD_BAD) != 0) << j;
+            if (bad & pmm) {
+                atomicOr(q.err, ERR_RANGE);
+                pmm &= ~bad;
+            }
+            if (pmm) accumulate<S, C>(q, t, c, r0, pays, pmm);
+        }
+        return;
     }
-    sums<S, 0, C>(q, t, c, r0, g, pm);
+    accumulate<S, C>(q, t, c, r0, pays, pm);
 }
 
 // Column pointers of a block starting at row `row` of the query's columns in

@@ -106,24 +106,28 @@ __global__ void __launch_bounds__(AGG_THREADS) k_agg_shared(const __grid_constan
     const uint64_t nfull = n / 128;
     for (uint64_t t = blockIdx.x * nwarps + (threadIdx.x >> 5); t < ntiles; t += gridDim.x * nwarps) {
         const bool full = t < nfull;
-        bool pass[4];
-        uint64_t key[4];
-        const bool any = full ? eval_keys<true>(q, t * 128, n, lane, pass, key)
-                              : eval_keys<false>(q, t * 128, n, lane, pass, key);
-        if (!any) continue;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (pass[i]) atomicAdd((unsigned long long*)&cnt[(uint32_t)key[i]], 1ull);
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            I128 tm[4];
-            if (full) eval_terms<true>(q, s, t * 128, n, lane, pass, tm);
-            else eval_terms<false>(q, s, t * 128, n, lane, pass, tm);
-            uint64_t* lo = sm + G * (1 + 2 * s);
-            uint64_t* hi = sm + G * (2 + 2 * s);
+        // fan-out joins pair a row with each partner in turn (m); otherwise one pass
+        for (uint32_t m = 0;; ++m) {
+            bool pass[4];
+            uint64_t key[4];
+            const bool any = full ? eval_keys<true>(q, t * 128, n, lane, pass, key, m)
+                                  : eval_keys<false>(q, t * 128, n, lane, pass, key, m);
+            if (!any) break;
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                if (pass[i]) atomic_add_i128(lo + (uint32_t)key[i], hi + (uint32_t)key[i], tm[i]);
+                if (pass[i]) atomicAdd((unsigned long long*)&cnt[(uint32_t)key[i]], 1ull);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                I128 tm[4];
+                if (full) eval_terms<true>(q, s, t * 128, n, lane, pass, tm);
+                else eval_terms<false>(q, s, t * 128, n, lane, pass, tm);
+                uint64_t* lo = sm + G * (1 + 2 * s);
+                uint64_t* hi = sm + G * (2 + 2 * s);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (pass[i]) atomic_add_i128(lo + (uint32_t)key[i], hi + (uint32_t)key[i], tm[i]);
+            }
+            if (!q.jt.many) break;
         }
     }
     __syncthreads();
@@ -205,38 +209,42 @@ __global__ void __launch_bounds__(256) k_agg_global(const __grid_constant__ Quer
     const uint64_t nfull = n / 128;
     for (uint64_t tt = blockIdx.x * nwarps + (threadIdx.x >> 5); tt < ntiles; tt += gridDim.x * nwarps) {
         const bool full = tt < nfull;
-        bool pass[4];
-        uint64_t key[4];
-        const bool any = full ? eval_keys<true>(q, tt * 128, n, lane, pass, key)
-                              : eval_keys<false>(q, tt * 128, n, lane, pass, key);
-        if (!any) continue;
-        // rows (0,1) and (2,3) are adjacent: fold the second into the first
-        // when their keys agree
-        bool fold[2];
-        uint64_t* slot[4];
+        // fan-out joins pair a row with each partner in turn (m); otherwise one pass
+        for (uint32_t m = 0;; ++m) {
+            bool pass[4];
+            uint64_t key[4];
+            const bool any = full ? eval_keys<true>(q, tt * 128, n, lane, pass, key, m)
+                                  : eval_keys<false>(q, tt * 128, n, lane, pass, key, m);
+            if (!any) break;
+            // rows (0,1) and (2,3) are adjacent: fold the second into the first
+            // when their keys agree
+            bool fold[2];
+            uint64_t* slot[4];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            fold[j] = pass[2 * j] && pass[2 * j + 1] && key[2 * j] == key[2 * j + 1];
-        }
+            for (int j = 0; j < 2; ++j) {
+                fold[j] = pass[2 * j] && pass[2 * j + 1] && key[2 * j] == key[2 * j + 1];
+            }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            slot[i] = nullptr;
-            if (!pass[i] || ((i & 1) && fold[i >> 1])) continue;
-            slot[i] = agg_slot_any(t, key[i], q.err);
-            if (slot[i])
-                atomicAdd((unsigned long long*)(slot[i] + 1), (i & 1) == 0 && fold[i >> 1] ? 2ull : 1ull);
-        }
+            for (int i = 0; i < 4; ++i) {
+                slot[i] = nullptr;
+                if (!pass[i] || ((i & 1) && fold[i >> 1])) continue;
+                slot[i] = agg_slot_any(t, key[i], q.err);
+                if (slot[i])
+                    atomicAdd((unsigned long long*)(slot[i] + 1), (i & 1) == 0 && fold[i >> 1] ? 2ull : 1ull);
+            }
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            I128 tm[4];
-            if (full) eval_terms<true>(q, s, tt * 128, n, lane, pass, tm);
-            else eval_terms<false>(q, s, tt * 128, n, lane, pass, tm);
+            for (int s = 0; s < NS; ++s) {
+                I128 tm[4];
+                if (full) eval_terms<true>(q, s, tt * 128, n, lane, pass, tm);
+                else eval_terms<false>(q, s, tt * 128, n, lane, pass, tm);
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
-                if (fold[j]) tm[2 * j] = i128_add(tm[2 * j], tm[2 * j + 1]);
+                for (int j = 0; j < 2; ++j)
+                    if (fold[j]) tm[2 * j] = i128_add(tm[2 * j], tm[2 * j + 1]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (slot[i]) atomic_add_i128(slot[i] + 2 + 2 * s, slot[i] + 3 + 2 * s, tm[i]);
+                for (int i = 0; i < 4; ++i)
+                    if (slot[i]) atomic_add_i128(slot[i] + 2 + 2 * s, slot[i] + 3 + 2 * s, tm[i]);
+            }
+            if (!q.jt.many) break;
         }
     }
 }

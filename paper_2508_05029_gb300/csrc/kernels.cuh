@@ -82,6 +82,15 @@ struct JoinTable {
     uint32_t* lip;
     int32_t lip_shift;
     int32_t pad3;
+    // fan-out (many != 0, repeated build keys): the table maps a key to the
+    // index of its first row in mkeys/mpay, the admitted build rows sorted by
+    // key; a fact row pairs with rows first, first + 1, ... while mkeys
+    // holds its key
+    const uint64_t* mkeys;
+    const uint32_t* mpay;
+    uint64_t mn;
+    int32_t many;
+    int32_t pad4;
 };
 
 // The query as the per-batch kernels see it.  Column pointers address the
@@ -359,6 +368,13 @@ cudaError_t launch_agg_global_staged(const QueryDev& q, const StageLayout& L, ui
 // filter).
 cudaError_t launch_part_hist(const BuildDev& b, uint64_t n, int shift, unsigned long long* counts, int num_sms,
                              cudaStream_t st);
+// Fan-out build: the admitted rows' (key, payload) pairs appended at *ctr
+// (and their keys into the lookahead filter); after sorting by key, the first
+// row of every run of equal keys as (key, its index) pairs at *ctr.
+cudaError_t launch_many_collect(const BuildDev& b, uint64_t n, uint64_t* keys, uint32_t* pays,
+                                unsigned long long* ctr, int num_sms, cudaStream_t st);
+cudaError_t launch_many_heads(const uint64_t* keys, uint64_t n, int64_t* hkeys, uint32_t* hidx,
+                              unsigned long long* ctr, int num_sms, cudaStream_t st);
 cudaError_t launch_part_hist_fact(const QueryDev& q, uint64_t n, int shift, uint64_t spill_mask,
                                   unsigned long long* counts, int num_sms, cudaStream_t st);
 // Build side: rows of resident partitions (bit set in b.jt.part_mask) are

@@ -105,6 +105,7 @@ extern "C" tp_status tp_execute_noalloc(const tp_plan_desc* d, const void* const
     if (d->dim_filter_on && (!join || !col_ok(d->dim_filter.col, n_dim_cols)))
         return fail(TP_E_INVALID, "tp_execute_noalloc: bad dimension predicate column");
     if (d->n_extra_dims != 0) return fail(TP_E_INVALID, "tp_execute_noalloc: one dimension at most");
+    if (d->join_many) return fail(TP_E_INVALID, "tp_execute_noalloc: no fan-out joins");
     if (d->n_group < 0 || d->n_group > 4 || d->n_agg < 1 || d->n_agg > 8)
         return fail(TP_E_INVALID, "tp_execute_noalloc: 0..4 group fields and 1..8 aggregates");
     tpk::QueryDev q{};

@@ -263,4 +263,52 @@ cudaError_t launch_fact_spill(const QueryDev& q, uint64_t n, uint64_t spill_mask
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------- fan-out build
+
+__global__ void k_many_collect(const __grid_constant__ BuildDev b, uint64_t n, uint64_t* __restrict__ keys,
+                               uint32_t* __restrict__ pays, unsigned long long* ctr) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (!dim_row_admitted(b, i)) continue;
+        const int64_t key = ld1(b.key, i);
+        if (b.jt.lip != nullptr) lip_insert(b.jt, key);
+        uint32_t payload = 0;
+        for (int f = 0; f < b.n_dfield; ++f) {
+            const int64_t v = ld1(b.dcol[f], i);
+            if (v < 0 || ((uint64_t)v >> b.dbits[f]) != 0) payload |= PAYLOAD_BAD;
+            else payload |= (uint32_t)((uint64_t)v << b.dpos[f]);
+        }
+        const unsigned long long at = atomicAdd(ctr, 1ull);
+        keys[at] = (uint64_t)key;
+        pays[at] = payload;
+    }
+}
+
+cudaError_t launch_many_collect(const BuildDev& b, uint64_t n, uint64_t* keys, uint32_t* pays,
+                                unsigned long long* ctr, int num_sms, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > (uint64_t)num_sms * 8) blocks = (uint64_t)num_sms * 8;
+    k_many_collect<<<(unsigned)blocks, 256, 0, st>>>(b, n, keys, pays, ctr);
+    return cudaGetLastError();
+}
+
+__global__ void k_many_heads(const uint64_t* __restrict__ keys, uint64_t n, int64_t* __restrict__ hkeys,
+                             uint32_t* __restrict__ hidx, unsigned long long* ctr) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (i > 0 && keys[i] == keys[i - 1]) continue;
+        const unsigned long long at = atomicAdd(ctr, 1ull);
+        hkeys[at] = (int64_t)keys[i];
+        hidx[at] = (uint32_t)i;
+    }
+}
+
+cudaError_t launch_many_heads(const uint64_t* keys, uint64_t n, int64_t* hkeys, uint32_t* hidx,
+                              unsigned long long* ctr, int num_sms, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > (uint64_t)num_sms * 8) blocks = (uint64_t)num_sms * 8;
+    k_many_heads<<<(unsigned)blocks, 256, 0, st>>>(keys, n, hkeys, hidx, ctr);
+    return cudaGetLastError();
+}
+
 }  // namespace tpk

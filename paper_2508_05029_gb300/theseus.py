@@ -87,7 +87,7 @@ class tp_plan_desc(ctypes.Structure):
                 ("join_partitions", ctypes.c_int32), ("dim_filter", tp_filter), ("dim_filter_on", ctypes.c_int32),
                 ("lip", ctypes.c_int32), ("n_extra_dims", ctypes.c_int32), ("extra_dim", ctypes.c_void_p * 3),
                 ("extra_join", tp_join * 3), ("extra_dim_filter", tp_filter * 3),
-                ("extra_dim_filter_on", ctypes.c_int32 * 3)]
+                ("extra_dim_filter_on", ctypes.c_int32 * 3), ("join_many", ctypes.c_int32)]
 
 
 class tp_i128(ctypes.Structure):
@@ -318,7 +318,8 @@ class Engine:
     def plan(self, fact: "Table", dim: "Table | None", query: dict, agg_strategy=TP_AGG_AUTO,
              load_factor=0.0, expected_groups=0, join_partitions=0, lip=TP_LIP_AUTO,
              extra_dims=None) -> "Plan":
-        """query: filter / join / group / aggs as the oracle takes them, plus an
+        """query: filter / join (many=True: repeated build keys, fan-out) / group /
+        aggs as the oracle takes them, plus an
         optional dim_filter = dict(col=<dimension column>, lo=, hi=); a star join
         adds extra_joins = [dict(fact_col, dim_col, optional dim_filter)] over the
         tables extra_dims, their group fields on sides "dim1".."dim3"."""
@@ -333,6 +334,7 @@ class Engine:
         d.filter = tp_filter(-1, 0, 0) if f is None else tp_filter(fact.col(f["col"]), f["lo"], f["hi"])
         j = query.get("join")
         d.join = tp_join(-1, -1) if j is None else tp_join(fact.col(j["fact_col"]), dim.col(j["dim_col"]))
+        d.join_many = 1 if j is not None and j.get("many") else 0
         sides = {"fact": (TP_SIDE_FACT, fact), "dim": (TP_SIDE_DIM, dim)}
         for j, t in enumerate(extra_dims):
             sides[f"dim{j + 1}"] = (TP_SIDE_DIM + 1 + j, t)

@@ -65,7 +65,7 @@ def test_struct_layout_matches_c(tmp_path):
         "tp_plan_desc": ["fact", "dim", "filter", "join", "n_group", "group", "n_agg", "aggs",
                          "agg_strategy", "load_factor", "expected_groups", "join_partitions", "dim_filter",
                          "dim_filter_on", "lip", "n_extra_dims", "extra_dim", "extra_join", "extra_dim_filter",
-                         "extra_dim_filter_on"],
+                         "extra_dim_filter_on", "join_many"],
         "tp_stats": ["h2d_bytes", "retries", "pages_in_use", "pages_total", "agg_kernel_rows", "jit_compiles",
                      "jit_launches", "jit_compile_ms", "agg_split_passes", "lip_filters"],
         "tp_i128": ["lo", "hi"],

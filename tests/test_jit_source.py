@@ -19,7 +19,7 @@ def _nvrtc():
     pytest.skip("NVRTC not available")
 
 
-def _shape(filter=1, ftype=0, join=1, ktype=0, part=0, lip=0, groups=((0, 2, 2), (0, 2, 1), (1, 0, 5)),
+def _shape(filter=1, ftype=0, join=1, ktype=0, part=0, lip=0, many=0, groups=((0, 2, 2), (0, 2, 1), (1, 0, 5)),
            sums=((0, 1, 0, 1, 0), (1, 1, 1, 2, 1), (0, 1, 0, 1, 0)), fast=True, xjoins=(), gdim=(0, 0, 0, 0)):
     """groups: (side, type, bits); sums: (kind, atype, btype, mode, narrow);
     xjoins: further joins (kind, key type, lookahead); gdim: join of each dimension field."""
@@ -30,7 +30,7 @@ def _shape(filter=1, ftype=0, join=1, ktype=0, part=0, lip=0, groups=((0, 2, 2),
     s = list(zip(*sums)) if sums else ((), (), (), (), ())
     return ("struct JS {\n"
             f"  static constexpr int filter = {filter}, ftype = {ftype}, join = {join}, ktype = {ktype}, part = {part}, "
-            f"lip = {lip};\n"
+            f"lip = {lip}, many = {many};\n"
             f"  static constexpr int nx = {len(xjoins)}, {arr('xjoin', [x[0] for x in xjoins], 3)}, "
             f"{arr('xktype', [x[1] for x in xjoins], 3)}, {arr('xlip', [x[2] for x in xjoins], 3)};\n"
             f"  static constexpr int ng = {len(groups)}, {arr('gdim', gdim, 4)};\n"
@@ -51,6 +51,7 @@ SHAPES = {
     "count-only": _shape(sums=()),
     "lip-direct": _shape(lip=1),
     "lip-hash64-partitioned": _shape(join=3, ktype=1, part=1, lip=1),
+    "fan-out-hash64": _shape(join=3, ktype=1, many=1),
     "star-three-further-joins": _shape(xjoins=((1, 0, 0), (2, 1, 1), (3, 1, 0)),
                                        groups=((1, 0, 3), (1, 0, 4), (1, 0, 2), (1, 0, 2)), gdim=(0, 1, 2, 3)),
 }
