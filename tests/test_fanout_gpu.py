@@ -129,3 +129,55 @@ def test_fanout_refusals():
         dt.destroy()
     finally:
         e.close()
+
+
+def test_empty_sides_of_fanout_and_star_joins():
+    """A further dimension without rows, a fan-out side whose predicate admits
+    nothing, lookahead filters over empty key sets, and a split aggregation
+    over a fan-out star join: each equals the oracle (mostly: no groups)."""
+    fact, dim = _fanout_tables(85, 120_000, 3_000, 3_500)
+    _, _, extra = _star_tiny(85, 10, [10, 50], [10, 60])
+    fact["fk2"] = datagen.uniform(5085, 7, np.int64, 120_000, 0, 59)
+    empty = {k: v[:0] for k, v in extra[0].items()}
+    base = _fanout_query()
+    base["extra_joins"] = [dict(fact_col="fk2", dim_col="pk")]
+    base["group"] = [("fact", "flag", 2), ("dim", "attr", 5), ("dim1", "band", 2)]
+    cases = [
+        (base, [empty], {}),                                                       # no partner anywhere
+        (dict(base, dim_filter=dict(col="attr", lo=40, hi=50)), extra, dict(lip=T.TP_LIP_ON)),
+        (dict(base, extra_joins=[dict(fact_col="fk2", dim_col="pk", dim_filter=dict(col="attr", lo=99, hi=99))]),
+         extra, dict(lip=T.TP_LIP_ON)),
+    ]
+    e = T.Engine(page_bytes=8 << 20, n_pages=64, batch_rows=1 << 20)
+    try:
+        for q, xd, kw in cases:
+            ref = oracle.run_query(fact, dim, q, xd)
+            assert ref.n_groups == 0
+            with _run(e, fact, dim, q, extra=xd, **kw) as r:
+                assert_matches_oracle(r, ref, q["aggs"])
+    finally:
+        e.close()
+    # many groups under a budget that forces key-range passes
+    fact["okey"] = (np.arange(120_000, dtype=np.int64) * 7919) % 30_011
+    q = dict(base, group=[("fact", "okey", 15), ("dim", "attr", 5), ("dim1", "band", 2)])
+    ref = oracle.run_query(fact, dim, q, extra)
+    for flags in (0, T.TP_FLAG_NO_DIRECT_AGG):
+        e = T.Engine(page_bytes=8 << 20, n_pages=64, batch_rows=1 << 20, flags=flags)
+        try:
+            with _run(e, fact, dim, q, extra=extra) as r:
+                assert_matches_oracle(r, ref, q["aggs"])
+            peak = e.stats()["peak_reserved"]
+        finally:
+            e.close()
+        e = T.Engine(page_bytes=8 << 20, n_pages=64, batch_rows=1 << 20, flags=flags)
+        try:
+            e.set_budget(int(peak * 0.8))
+            try:
+                r = _run(e, fact, dim, q, extra=extra)
+            except T.TPError as err:
+                assert err.status == "budget"
+                continue
+            with r:
+                assert_matches_oracle(r, ref, q["aggs"])
+        finally:
+            e.close()
