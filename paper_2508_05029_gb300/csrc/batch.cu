@@ -193,7 +193,17 @@ namespace {
 using namespace tp;
 
 constexpr uint64_t BUILD_CHUNK = 65536;      // dimension rows per build task
-constexpr uint32_t SMEM_TABLE_MAX = 48 * 1024;
+#ifndef TP_BATCH_SMEM_MAX
+#define TP_BATCH_SMEM_MAX (96 * 1024)
+#endif
+#ifndef TP_BATCH_SMEM_BITS
+#define TP_BATCH_SMEM_BITS 12
+#endif
+// queries whose 32-bit group table fits this many bytes of shared memory
+// (and keys of at most SMEM_TABLE_BITS bits) accumulate per tile in shared
+// memory; the others add straight into device memory
+constexpr uint32_t SMEM_TABLE_MAX = TP_BATCH_SMEM_MAX;
+constexpr int SMEM_TABLE_BITS = TP_BATCH_SMEM_BITS;
 
 struct Tune {
     float lf;              // join load factor (0: the plan's)
@@ -358,7 +368,7 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
         // shared-memory tables: 32-bit words, per tile; needs 64-bit safety
         x.smem = false;
         x.smem_bytes = 0;
-        if (x.fast && t.agg != TP_AGG_GLOBAL && p->key_bits <= 12) {
+        if (x.fast && t.agg != TP_AGG_GLOBAL && p->key_bits <= SMEM_TABLE_BITS) {
             term_bounds(p, p->d.fact, x.bounds);
             uint32_t words = 1;
             bool ok = true;
