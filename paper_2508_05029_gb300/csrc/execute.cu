@@ -674,11 +674,34 @@ struct PartJoin {
     std::deque<cudaEvent_t> inflight;      // fact spill copies still running on the spill stream
     uint64_t table_budget = 0;             // bytes the resident table and one phase-2 table may take
     uint64_t resident_bytes = 0;           // bytes of the resident table
+    uint64_t stage_bytes = 0;              // fact spill staging reserved in the budget
+    // fact spill accumulation: two device buffer sets, each holding a region
+    // of acc_cap rows per spilled partition (every used column, narrow); one
+    // set fills over several fact batches while the other's copies to host
+    // pages run, so the link sees fewer and larger copies each way
+    struct Acc {
+        std::vector<void*> col;            // per fact column
+        std::vector<uint64_t> fill;        // rows held per partition
+        cudaEvent_t done = nullptr;        // its last flush's copies
+    };
+    Acc acc[2];
+    int acc_cur = 0;
+    uint64_t acc_cap = 0;                  // rows per partition region; 0 = accumulation off
+    bool acc_tried = false;
+    std::vector<uint64_t> acc_region;      // first row of each partition's region
+    std::vector<uint8_t> enc_w;            // the spill encoding (by the fact table's bounds)
+    std::vector<int64_t> enc_base;
+    std::vector<int> width;
     ~PartJoin() {
         for (cudaEvent_t ev : inflight) {
             cudaEventSynchronize(ev);
             cudaEventDestroy(ev);
         }
+        for (Acc& a : acc)
+            if (a.done) {
+                cudaEventSynchronize(a.done);
+                cudaEventDestroy(a.done);
+            }
         for (tp_table* t : build_spill) tp_table_destroy(t);
         for (tp_table* t : fact_spill) tp_table_destroy(t);
     }
@@ -859,6 +882,71 @@ tp_status part_setup(ExecState& S, Scratch& sc, PartJoin& pj, uint64_t table_bud
     });
 }
 
+// Copies every partition's accumulated rows of the current set to its spill
+// table (on the spill stream, after the scatters queued so far) and switches
+// to the other set once its own previous copies are done.
+tp_status part_acc_flush(ExecState& S, PartJoin& pj) {
+    PartJoin::Acc& a = pj.acc[pj.acc_cur];
+    bool any = false;
+    for (uint64_t f : a.fill) any = any || f > 0;
+    if (!any) return TP_OK;
+    tp_engine* e = S.e;
+    cudaStream_t sp = S.lane->spill;
+    cudaEvent_t ready = nullptr;
+    TP_TRY_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    cudaError_t ce = cudaEventRecord(ready, S.lane->compute);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(sp, ready, 0);
+    cudaEventDestroy(ready);
+    TP_TRY_CUDA(ce);
+    tp_status s = TP_OK;
+    for (int p = 0; p < pj.P && s == TP_OK; ++p) {
+        if (a.fill[p] == 0) continue;
+        std::vector<const void*> part(S.fact->types.size(), nullptr);
+        for (int c : S.used) part[c] = (const uint8_t*)a.col[c] + pj.acc_region[p] * (uint64_t)pj.width[c];
+        s = append_device_rows(e, pj.fact_spill[p], part, a.fill[p], sp, false, &pj.enc_w, &pj.enc_base);
+        a.fill[p] = 0;
+    }
+    if (s) return s;
+    if (!a.done) TP_TRY_CUDA(cudaEventCreateWithFlags(&a.done, cudaEventDisableTiming));
+    TP_TRY_CUDA(cudaEventRecord(a.done, sp));
+    pj.acc_cur ^= 1;
+    PartJoin::Acc& b = pj.acc[pj.acc_cur];
+    if (b.done) TP_TRY_CUDA(cudaStreamWaitEvent(S.lane->compute, b.done, 0));   // its copies read it
+    return TP_OK;
+}
+
+// Sets up the accumulation sets in the spill staging the plan reserved (once;
+// off when a partition's region would hold fewer than 4096 rows).
+tp_status part_acc_setup(ExecState& S, Scratch& sc, PartJoin& pj) {
+    pj.acc_tried = true;
+    int n_sp = 0;
+    for (int p = 0; p < pj.P; ++p) n_sp += (pj.spill_mask >> p) & 1ull;
+    uint64_t row_bytes = 0;
+    for (int c : S.used) row_bytes += (uint64_t)pj.width[c];
+    if (n_sp == 0 || row_bytes == 0) return TP_OK;
+    const uint64_t slack = 2 * 256 * (uint64_t)S.used.size();
+    const uint64_t set_bytes = pj.stage_bytes > 2 * slack ? (pj.stage_bytes - 2 * slack) / 2 : 0;
+    const uint64_t cap = set_bytes / row_bytes / (uint64_t)n_sp;
+    if (cap < 4096) return TP_OK;
+    pj.acc_region.assign(pj.P, 0);
+    uint64_t at = 0;
+    for (int p = 0; p < pj.P; ++p)
+        if ((pj.spill_mask >> p) & 1ull) {
+            pj.acc_region[p] = at;
+            at += cap;
+        }
+    for (PartJoin::Acc& a : pj.acc) {
+        a.col.assign(S.fact->types.size(), nullptr);
+        a.fill.assign(pj.P, 0);
+        for (int c : S.used) {
+            tp_status s = sc.alloc(&a.col[c], align256(at * (uint64_t)pj.width[c]));
+            if (s) return s;
+        }
+    }
+    pj.acc_cap = cap;
+    return TP_OK;
+}
+
 // Fact rows of spilled partitions in this batch go to their spill tables.
 tp_status part_spill_fact(ExecState& S, Scratch& sc, PartJoin& pj, const tpk::QueryDev& q, uint64_t rows,
                           const std::vector<const void*>& colptr) {
@@ -878,6 +966,55 @@ tp_status part_spill_fact(ExecState& S, Scratch& sc, PartJoin& pj, const tpk::Qu
         total += bc[p];
     }
     if (total == 0) return TP_OK;
+    if (pj.width.empty()) {   // the spill encoding: narrow by the fact table's bounds, as host pages are
+        const int nct = (int)S.fact->types.size();
+        const bool narrow = !(e->cfg.flags & TP_FLAG_RAW_PAGES);
+        pj.enc_w.assign(nct, 0);
+        pj.enc_base.assign(nct, 0);
+        pj.width.assign(nct, 0);
+        for (int c : S.used) {
+            const int full = type_size(S.fact->types[c]);
+            pj.enc_w[c] = narrow ? (uint8_t)frame_width(S.fact->cmin[c], S.fact->cmax[c], full) : 0;
+            pj.enc_base[c] = S.fact->cmin[c];
+            pj.width[c] = pj.enc_w[c] ? pj.enc_w[c] : full;
+        }
+    }
+    if (!pj.acc_tried) {
+        tp_status r = part_acc_setup(S, sc, pj);
+        if (r) return r;
+    }
+    bool fits = pj.acc_cap > 0;
+    for (int p = 0; p < P && fits; ++p) fits = bc[p] <= pj.acc_cap;
+    if (fits) {   // accumulate: scatter into the current set, flushing it first when it is full
+        bool full = false;
+        for (int p = 0; p < P && !full; ++p) full = pj.acc[pj.acc_cur].fill[p] + bc[p] > pj.acc_cap;
+        if (full) {
+            tp_status r = part_acc_flush(S, pj);
+            if (r) return r;
+        }
+        PartJoin::Acc& a = pj.acc[pj.acc_cur];
+        for (int p = 0; p < P; ++p) base[p] = (pj.spill_mask >> p) & 1ull ? pj.acc_region[p] + a.fill[p] : 0;
+        TP_TRY_CUDA(cudaMemcpyAsync(pj.counts, base.data(), 8 * (uint64_t)P, cudaMemcpyHostToDevice, st));
+        tpk::SpillCols cols{};
+        for (int c : S.used) {
+            cols.src[cols.n] = colptr[c];
+            cols.dst[cols.n] = a.col[c];
+            cols.esize[cols.n] = type_size(S.fact->types[c]);
+            cols.w[cols.n] = pj.width[c];
+            cols.base[cols.n] = pj.enc_base[c];
+            ++cols.n;
+        }
+        mark_launch(e);
+        TP_TRY_CUDA(tpk::launch_fact_spill(q, rows, pj.spill_mask, cols, pj.counts, pj.cursor, e->num_sms, st));
+        for (int p = 0; p < P; ++p) a.fill[p] += bc[p];
+        return TP_OK;
+    }
+    // a partition got more rows from this batch than a region holds: flush,
+    // then spill this batch on its own
+    if (pj.acc_cap) {
+        tp_status r = part_acc_flush(S, pj);
+        if (r) return r;
+    }
     TP_TRY_CUDA(cudaMemcpyAsync(pj.counts, base.data(), 8 * (uint64_t)P, cudaMemcpyHostToDevice, st));
     // at most SPILL_BACKLOG batches' staging waits on its device -> host copies
     while (pj.inflight.size() >= SPILL_BACKLOG) {
@@ -947,6 +1084,10 @@ tp_status part_phase2(ExecState& S, Scratch& sc, PartJoin& pj, float lf, F&& agg
     if (!pj.spill_mask) return TP_OK;
     tp_engine* e = S.e;
     cudaStream_t st = S.lane->compute;
+    if (pj.acc_cap) {   // the rows still accumulated on the device
+        tp_status r = part_acc_flush(S, pj);
+        if (r) return r;
+    }
     TP_TRY_CUDA(cudaStreamSynchronize(S.lane->spill));   // every spilled fact row is in its pages
     for (cudaEvent_t ev : pj.inflight) cudaEventDestroy(ev);
     pj.inflight.clear();
@@ -1291,6 +1432,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
                 // a tenth stays free for retries of a table that outgrew its estimate
                 part_table_budget = avail > stage ? (avail - stage) / 10 * 9 : 0;
                 pj.table_budget = part_table_budget;
+                pj.stage_bytes = (SPILL_BACKLOG + 1) * align256(fact_rows * used_bytes);
                 join_bytes = part_table_budget + stage;
             }
         }
