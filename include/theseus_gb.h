@@ -484,6 +484,10 @@ typedef struct {
     double jit_compile_ms;       /* host time spent compiling */
     uint64_t agg_split_passes;   /* extra passes of aggregations split by key range to fit the budget */
     uint64_t lip_filters;        /* lookahead filters built */
+    /* host wall time of the partitioned joins' phases: build side (histogram,
+     * resident inserts, build spill), fact stream (probe and spill), joins of
+     * the spilled partitions */
+    double part_build_ms, part_stream_ms, part_spilled_ms;
 } tp_stats;
 
 /* Message for the last error on this thread ("" if none). */

@@ -602,6 +602,9 @@ tp_status tp_stats_get(tp_engine* e, tp_stats* s) {
     {
         std::lock_guard<std::mutex> lk(e->time_mu);
         s->agg_kernel_ms = e->agg_ms;
+        s->part_build_ms = e->part_ms[0];
+        s->part_stream_ms = e->part_ms[1];
+        s->part_spilled_ms = e->part_ms[2];
         s->agg_kernel_launches = e->agg_launches;
         s->agg_kernel_rows = e->agg_rows;
     }

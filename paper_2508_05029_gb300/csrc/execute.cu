@@ -9,6 +9,7 @@
 // them (Section 3.3.3, compute-task pre-loading); with prefetch_depth 0 the
 // compute stream copies each batch itself.
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -95,6 +96,21 @@ struct ExecState {
 };
 
 void mark_launch(tp_engine* e) { e->launches++; }
+
+// Host wall time of one phase of a partitioned join, added to the engine's
+// statistics (phase < 0: not timed).
+struct PhaseTimer {
+    tp_engine* e;
+    int phase;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    PhaseTimer(tp_engine* eng, int ph) : e(eng), phase(ph) {}
+    ~PhaseTimer() {
+        if (phase < 0) return;
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        std::lock_guard<std::mutex> lk(e->time_mu);
+        e->part_ms[phase] += ms;
+    }
+};
 
 // Brackets fused-kernel launches with events on the compute stream when the
 // engine was created with TP_FLAG_TIME_KERNELS; totals are folded into the
@@ -1486,6 +1502,7 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         S.jt.key64 = S.key64 ? 1 : 0;
         if (pj.on) {
             const tpk::BuildDev proto = build_proto(S);
+            PhaseTimer pt(e, 0);
             if ((s = part_setup(S, sc, pj, part_table_budget, lf, proto))) return s;
         } else if (d.join_many) {
             if ((s = build_join_many(S, sc))) return s;
@@ -1595,9 +1612,13 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             if (r == TP_OK && pj.on) r = part_spill_fact(S, sc, pj, q, rows, colptr);
             return r;
         };
-        s = for_each_batch(S, sc, shared_batch);
+        {
+            PhaseTimer pt(e, pj.on ? 1 : -1);
+            s = for_each_batch(S, sc, shared_batch);
+        }
         if (s == TP_OK && pj.on) {
             pj.spill_fact = false;
+            PhaseTimer pt(e, 2);
             s = part_phase2(S, sc, pj, lf, shared_batch);
         }
         if (s) return s;
@@ -1778,9 +1799,13 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
                 if (r == TP_OK && pj.on) r = part_spill_fact(S, sc, pj, q, rows, colptr);
                 return r;
             };
-            s = for_each_batch(S, sc, global_batch);
+            {
+                PhaseTimer pt(e, pj.on ? 1 : -1);
+                s = for_each_batch(S, sc, global_batch);
+            }
             if (s == TP_OK && pj.on) {
                 pj.spill_fact = false;   // later passes re-read the spilled partitions, they do not spill again
+                PhaseTimer pt(e, 2);
                 s = part_phase2(S, sc, pj, lf, global_batch);
             }
             if (s) return s;

@@ -119,6 +119,7 @@ struct tp_engine {
     // fused-kernel timing (TP_FLAG_TIME_KERNELS)
     std::mutex time_mu;
     double agg_ms = 0;
+    double part_ms[3] = {0, 0, 0};   // partitioned join phases: build side, fact stream, spilled partitions
     uint64_t agg_launches = 0, agg_rows = 0;
 };
 

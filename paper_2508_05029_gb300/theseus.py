@@ -102,7 +102,9 @@ class tp_stats(ctypes.Structure):
                 ("agg_kernel_launches", ctypes.c_uint64), ("agg_kernel_rows", ctypes.c_uint64),
                 ("jit_compiles", ctypes.c_uint64), ("jit_failures", ctypes.c_uint64),
                 ("jit_launches", ctypes.c_uint64), ("jit_compile_ms", ctypes.c_double),
-                ("agg_split_passes", ctypes.c_uint64), ("lip_filters", ctypes.c_uint64)]
+                ("agg_split_passes", ctypes.c_uint64), ("lip_filters", ctypes.c_uint64),
+                ("part_build_ms", ctypes.c_double), ("part_stream_ms", ctypes.c_double),
+                ("part_spilled_ms", ctypes.c_double)]
 
 
 class tp_server_stats(ctypes.Structure):

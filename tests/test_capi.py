@@ -67,7 +67,8 @@ def test_struct_layout_matches_c(tmp_path):
                          "dim_filter_on", "lip", "n_extra_dims", "extra_dim", "extra_join", "extra_dim_filter",
                          "extra_dim_filter_on", "join_many"],
         "tp_stats": ["h2d_bytes", "retries", "pages_in_use", "pages_total", "agg_kernel_rows", "jit_compiles",
-                     "jit_launches", "jit_compile_ms", "agg_split_passes", "lip_filters"],
+                     "jit_launches", "jit_compile_ms", "agg_split_passes", "lip_filters",
+                     "part_build_ms", "part_stream_ms", "part_spilled_ms"],
         "tp_i128": ["lo", "hi"],
         "tp_agg": ["kind", "col_a", "col_b", "k"],
         "tp_table_desc": ["n_cols", "cols", "batch_rows"],
