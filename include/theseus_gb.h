@@ -306,7 +306,8 @@ typedef struct {
      * own under the rule above.  Needs the first join.  Only the first join
      * is ever partitioned: the further tables stay resident (TP_E_BUDGET when
      * they do not fit).  Batched executions and the allocation-free entry
-     * point take one dimension (TP_E_INVALID otherwise). */
+     * point take one dimension (TP_E_INVALID otherwise).  The tables belong
+     * to the caller's engine and must outlive the plan, like fact and dim. */
     int32_t n_extra_dims;                         /* 0..TP_MAX_EXTRA_DIMS */
     tp_table* extra_dim[TP_MAX_EXTRA_DIMS];
     tp_join extra_join[TP_MAX_EXTRA_DIMS];
@@ -318,7 +319,8 @@ typedef struct {
      * The build sorts the admitted rows by key and indexes the first row of
      * each key.  Never partitioned (join_partitions must be 0 or 1;
      * TP_E_BUDGET when the table does not fit), not cached by the server;
-     * batched executions and the allocation-free entry point refuse it. */
+     * batched executions and the allocation-free entry point refuse it.  At
+     * most 2^31 admitted build rows (TP_E_INVALID at execution). */
     int32_t join_many;
 } tp_plan_desc;
 
