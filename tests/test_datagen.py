@@ -49,3 +49,21 @@ def test_config_shapes():
     sizes = W.config4_sizes()
     assert sizes["fact"].min() >= 10_000 and sizes["fact"].max() <= 50_000_000
     assert 1e8 < sizes["fact"].sum() < 1e9
+
+
+def test_star_dimension_and_foreign_keys():
+    """A further star dimension: unique sparse keys, attributes in range, and
+    every generated foreign key names one of its rows (regenerated by row)."""
+    from datagen import workloads as W
+    seed = W.SEEDS[2] + 100
+    d = W.star_dim(50_000, seed)
+    assert len(np.unique(d["pk"])) == 50_000
+    assert d["attr"].min() >= 0 and d["attr"].max() <= 24 and d["band"].max() <= 3
+    fk = W.star_fk(200_000, 50_000, seed)
+    assert np.isin(fk, d["pk"]).all()
+    # uniform over the rows: every row is hit about 4 times
+    _, hits = np.unique(fk, return_counts=True)
+    assert len(hits) > 0.97 * 50_000 and hits.max() < 20
+    # row ranges regenerate independently, and another dimension index gives other keys
+    assert np.array_equal(W.star_dim(50_000, seed)["pk"][:100], d["pk"][:100])
+    assert not np.isin(W.star_dim(1_000, seed, j=1)["pk"], d["pk"]).any()
