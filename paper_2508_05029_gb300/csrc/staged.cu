@@ -249,10 +249,13 @@ bool staged_layout_shared(const QueryDev& q, uint32_t key_bits, bool fast, const
     L->stage_bytes = off ? off : 128;
     const uint64_t G = 1ull << key_bits;
     if (fast) {
-        // rows one CTA can see in this launch bound every 32-bit word
+        // rows one CTA can see in this launch bound every 32-bit word: its
+        // share of the whole tiles plus, for the run-time compiled kernel, the
+        // rows after the last whole tile, which CTA (tiles % grid) evaluates
+        // too -- CTA 0, holding a full share, when tiles is a multiple of grid
         const uint64_t tiles = rows / tile;
         const uint64_t grid = std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)num_sms * geom.ctas));
-        const uint64_t r_cta = (tiles + grid - 1) / grid * (uint64_t)tile;
+        const uint64_t r_cta = (tiles + grid - 1) / grid * (uint64_t)tile + (rows - tiles * (uint64_t)tile);
         if (r_cta >= (1ull << 32)) return false;
         uint32_t block = 1;   // block 0: counts
         for (int s = 0; s < q.n_sum; ++s) {
