@@ -172,6 +172,22 @@ tp_status tp_set_device_budget(tp_engine* eng, uint64_t bytes);
 /* Bytes currently reserved and the cap. Either pointer may be NULL. */
 tp_status tp_budget_query(tp_engine* eng, uint64_t* reserved, uint64_t* cap);
 
+/* ------------------------------------------------------- transfer options */
+
+/*
+ * How batches in host pages reach the device, for the executions that start
+ * after the call (call it while none runs).  prefetch_depth: batches copied
+ * ahead of the kernels on the copy stream (Section 3.3.3, pre-loading); 0
+ * copies each batch and then runs it, on one stream.  flags:
+ * TP_COPY_PINNED_PER_BATCH copies every batch first into a page-locked buffer
+ * allocated for it (cudaHostAlloc) and freed once its copies are done, as an
+ * engine without a pinned page pool would (Section 3.4: pinning memory is
+ * slow, which is why the pool is allocated once); results are unchanged.
+ * TP_E_INVALID for a negative depth or unknown flags.
+ */
+enum { TP_COPY_PINNED_PER_BATCH = 1 };
+tp_status tp_set_copy_options(tp_engine* eng, int32_t prefetch_depth, uint32_t flags);
+
 /* ------------------------------------------------------------------ tables */
 
 enum { TP_I32 = 0, TP_I64 = 1, TP_U8 = 2 };
@@ -399,23 +415,41 @@ tp_status tp_autotune(tp_engine* eng, tp_plan* const* plans, int32_t n, const ch
 /* ------------------------------------------------------------------ serving */
 
 /*
- * A request server over one engine: queries are submitted as they arrive and
- * run concurrently on `workers` lanes, each a host thread with its own compute
- * and copy streams, so their kernels overlap on the device (Section 3.3.1: each
- * Compute Executor thread drives its own CUDA stream).  Admission is by
- * device-memory reservation (Section 3.3.2): a request whose reservation does
- * not fit waits in the queue while others run and is admitted as soon as
- * completions release memory; it fails with TP_E_BUDGET only when it cannot fit
- * even with nothing else running.  At most max_inflight requests run at once
- * (0 = workers); requests of the same plan object run one at a time.
+ * A request server over one engine: queries are submitted as they arrive
+ * (Section 3.3.1: executors take tasks from a queue; Section 3.3.2: a task is
+ * admitted by its device-memory reservation).
+ *
+ * With TP_SERVE_BATCH (continuous batching), a dispatcher thread takes every
+ * queued request a batched launch can run (the conditions of tp_batch_create:
+ * device-resident tables, at most one join, no fan-out, at most 20 key bits),
+ * up to max_inflight of them (0 = 256) and as many as the budget admits, and
+ * starts them as one persistent queue launch; requests arriving meanwhile
+ * form the next launch, which starts at once on a second stream and overlaps
+ * the running one on the device.  Each request has its own join table,
+ * accumulators, error word and result: its result and its status are the
+ * ones it gets alone.  The probe tasks are compiled at run time for every
+ * plan shape the server has seen; the first request of a new shape waits for
+ * that compilation.
+ *
+ * Other requests (and every request without TP_SERVE_BATCH) run on `workers`
+ * lanes, each a host thread with its own compute and copy streams, so their
+ * kernels overlap on the device (each Compute Executor thread drives its own
+ * CUDA stream).  At most max_inflight run on lanes at once (0 = workers);
+ * requests of the same plan object run one at a time there.
+ *
+ * Admission: a request whose reservation does not fit waits in the queue
+ * while others run and is admitted as soon as completions release memory; it
+ * fails with TP_E_BUDGET only when it cannot fit even with nothing else
+ * running.  Plans must outlive their requests.
  *
  * With TP_SERVE_CACHE_DIM the join table of a dimension stays on the device
- * across requests, keyed by dimension table, key column, dimension group
+ * across lane requests, keyed by dimension table, key column, dimension group
  * fields and load factor; cached tables hold their reservation until evicted
  * (least recently used, when a reservation does not fit) or the server stops.
- * Hashed joins that would be partitioned bypass the cache.
+ * Hashed joins that would be partitioned bypass the cache.  Batched requests
+ * build their join tables inside their launch.
  */
-enum { TP_SERVE_CACHE_DIM = 1 };
+enum { TP_SERVE_CACHE_DIM = 1, TP_SERVE_BATCH = 2 };
 typedef struct tp_server tp_server;
 typedef uint64_t tp_ticket;
 
@@ -428,15 +462,16 @@ tp_status tp_submit(tp_server* srv, tp_plan* p, tp_ticket* out);
  * still queued or running (the ticket stays valid); otherwise the request's
  * own status, with *out its result on TP_OK.  times (may be NULL) receives
  * three steady-clock nanosecond stamps: submitted, started, finished.  A
- * finished ticket is consumed by the call.
+ * finished ticket is consumed by the call.  One thread at a time may wait on
+ * a ticket: a second concurrent tp_wait on it returns TP_E_INVALID.
  */
 tp_status tp_wait(tp_server* srv, tp_ticket t, int64_t timeout_ns, tp_result** out, int64_t* times);
 typedef struct {
     uint64_t submitted, completed, failed;
     uint64_t budget_waits;        /* admissions deferred because the reservation did not fit */
     uint64_t cache_hits, cache_misses, cache_evictions;
-    uint32_t inflight_peak;
-    uint32_t pad;
+    uint32_t inflight_peak;       /* most requests running at once (lanes and batched launches) */
+    uint32_t batches;             /* batched launches started (TP_SERVE_BATCH) */
 } tp_server_stats;
 tp_status tp_server_stats_get(tp_server* srv, tp_server_stats* out);
 /* Finishes queued and running requests, frees cached tables and lanes. */

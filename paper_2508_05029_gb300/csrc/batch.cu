@@ -192,7 +192,6 @@ namespace {
 
 using namespace tp;
 
-constexpr uint64_t BUILD_CHUNK = 65536;      // dimension rows per build task
 #ifndef TP_BATCH_SMEM_MAX
 #define TP_BATCH_SMEM_MAX (96 * 1024)
 #endif
@@ -314,19 +313,164 @@ static void batch_free(tp_batch* b) {
     delete b;
 }
 
+namespace tp {
+
+tp_status batch_check_plan(const tp_engine* e, const tp_plan* p, int i) {
+    if (!p || p->eng != e) return fail(TP_E_INVALID, "plan %d missing or from another engine", i);
+    if (p->d.fact->placement == PL_PAGES || (p->d.join.fact_col >= 0 && p->d.dim->placement == PL_PAGES))
+        return fail(TP_E_INVALID, "plan %d reads a table in host pages", i);
+    if (p->n_dims > 1) return fail(TP_E_INVALID, "plan %d is a star join (one dimension here)", i);
+    if (p->d.join_many) return fail(TP_E_INVALID, "plan %d has a fan-out join", i);
+    if (p->key_bits > 20) return fail(TP_E_INVALID, "plan %d has a %d-bit group key (at most 20)", i, p->key_bits);
+    return TP_OK;
+}
+
+void batch_prep(const tp_engine* e, const tp_plan* p, float lf_tuned, uint32_t rows_per_warp, int agg,
+                BatchPrep* out) {
+    BatchPrep& x = *out;
+    x = BatchPrep{};
+    const float lf = lf_tuned > 0 ? lf_tuned : p->load_factor;
+    x.join = p->d.join.fact_col >= 0;
+    x.key64 = x.join && p->d.dim->types[p->d.join.dim_col] == TP_I64;
+    x.direct = x.join && !(e->cfg.flags & TP_FLAG_NO_DIRECT_JOIN) && direct_join_range(p->d.dim, p->d.join.dim_col,
+                                                                                        &x.range);
+    x.join_cap = x.join && !x.direct ? p2(std::max<uint64_t>(64, (uint64_t)std::ceil(p->d.dim->rows / lf))) : 0;
+    x.join_bytes = x.direct ? a256(x.range * 4) : a256(x.join_cap * (x.key64 ? 16 : 8));
+    const uint64_t G = 1ull << p->key_bits;
+    x.acc_bytes = a256(G * 8 * (1 + 2 * (uint64_t)p->n_sum));
+    int n_avg = 0;
+    for (int a = 0; a < p->d.n_agg; ++a) n_avg += p->d.aggs[a].kind == TP_AGG_AVG;
+    x.out_bytes = a256(G * 8) * 2 + a256(G * 16) * p->n_sum + a256(G * 8) * n_avg;
+    x.tile = (uint64_t)std::min<uint32_t>(std::max<uint32_t>(rows_per_warp, 128), 1u << 16) / 128 * 128 *
+             (tpk::BATCH_THREADS / 32);
+    x.fast = !(e->cfg.flags & TP_FLAG_EXACT_ONLY) && sums_fit_int64(p, p->d.fact);
+    // shared-memory tables: 32-bit words, per tile; needs 64-bit safety
+    if (x.fast && agg != TP_AGG_GLOBAL && p->key_bits <= SMEM_TABLE_BITS) {
+        term_bounds(p, p->d.fact, x.bounds);
+        uint32_t words = 1;
+        bool ok = true;
+        for (int s = 0; s < p->n_sum; ++s) {
+            const unsigned __int128 r = x.tile;
+            if (r * x.bounds[s].span <= 0xFFFFFFFFull) x.mode[s] = 1;
+            else if (r * ((x.bounds[s].span >> 32) + 1) <= 0xFFFFFFFFull) x.mode[s] = 2;
+            else ok = false;
+            words += ok ? (uint32_t)x.mode[s] : 0;
+        }
+        const uint64_t bytes = 4 * G * words;
+        if (ok && bytes <= SMEM_TABLE_MAX) {
+            x.smem = true;
+            x.smem_bytes = (uint32_t)bytes;
+        }
+    }
+    if (!x.smem)
+        for (int s = 0; s < tpk::MAX_SUM; ++s) x.mode[s] = 0;
+    x.build_items = x.join ? (p->d.dim->rows + BATCH_BUILD_CHUNK - 1) / BATCH_BUILD_CHUNK : 0;
+    x.probe_items = (p->d.fact->rows + x.tile - 1) / x.tile;
+}
+
+void batch_query_desc(const tp_plan* p, const BatchPrep& x, void* join_slots, uint32_t* side, uint64_t* acc,
+                      uint32_t* err, const tpk::OutDev& out, tpk::BatchQuery* Bp) {
+    const tp_plan_desc& d = p->d;
+    tpk::BatchQuery& B = *Bp;
+    memset(&B, 0, sizeof(B));
+    tpk::JoinTable jt{};
+    if (x.join) {
+        jt.slots = (uint64_t*)join_slots;
+        jt.mask = x.join_cap ? x.join_cap - 1 : 0;
+        jt.key64 = x.key64 ? 1 : 0;
+        jt.side = side;
+        jt.direct = x.direct ? 1 : 0;
+        jt.kmin = x.direct ? d.dim->cmin[d.join.dim_col] : 0;
+        jt.range = x.direct ? x.range : 0;
+    }
+    std::vector<const void*> colptr(d.fact->types.size(), nullptr);
+    for (size_t c = 0; c < colptr.size(); ++c) colptr[c] = d.fact->dev_cols[c];
+    B.q = plan_query_dev(p, colptr, jt, err, true);
+    B.acc = acc;
+    B.key_bits = (uint32_t)p->key_bits;
+    B.smem = x.smem ? 1 : 0;
+    B.fast = x.fast ? 1 : 0;
+    for (int t = 0; t < p->n_sum; ++t) {
+        B.sum_mode[t] = x.smem ? x.mode[t] : 0;
+        B.sum_off[t] = x.smem ? x.bounds[t].lo : 0;
+    }
+    if (x.join) {
+        B.b.key.ptr = d.dim->dev_cols[d.join.dim_col];
+        B.b.key.type = d.dim->types[d.join.dim_col];
+        int nf = 0;
+        for (int g = 0; g < d.n_group; ++g) {
+            if (d.group[g].side != TP_SIDE_DIM) continue;
+            B.b.dcol[nf].ptr = d.dim->dev_cols[d.group[g].col];
+            B.b.dcol[nf].type = d.dim->types[d.group[g].col];
+            B.b.dbits[nf] = d.group[g].bits;
+            B.b.dpos[nf] = p->gdpos[g];
+            ++nf;
+        }
+        B.b.n_dfield = nf;
+        B.b.jt = jt;
+        B.b.err = err;
+        if (d.dim_filter.col >= 0) {   // the dimension predicate gates the build
+            B.b.has_filter = 1;
+            B.b.fcol.ptr = d.dim->dev_cols[d.dim_filter.col];
+            B.b.fcol.type = d.dim->types[d.dim_filter.col];
+            B.b.flo = d.dim_filter.lo;
+            B.b.fhi = d.dim_filter.hi;
+        }
+    }
+    B.out = out;
+    B.build_items = (uint32_t)x.build_items;
+    B.probe_items = (uint32_t)x.probe_items;
+}
+
+void batch_items(const tp_plan* p, const BatchPrep& x, uint32_t qi, int kind, std::vector<tpk::BatchItem>* items) {
+    if (kind == tpk::BI_BUILD) {
+        for (uint64_t k = 0; k < x.build_items; ++k)
+            items->push_back(tpk::BatchItem{qi, tpk::BI_BUILD, k * BATCH_BUILD_CHUNK,
+                                            std::min<uint64_t>(p->d.dim->rows, (k + 1) * BATCH_BUILD_CHUNK), 0});
+    } else if (kind == tpk::BI_PROBE) {
+        const uint64_t rows = p->d.fact->rows;
+        for (uint64_t k = 0; k < x.probe_items; ++k)
+            items->push_back(tpk::BatchItem{qi, tpk::BI_PROBE, k * x.tile, std::min(rows, (k + 1) * x.tile), 0});
+    } else {
+        items->push_back(tpk::BatchItem{qi, tpk::BI_FINAL, 0, 0, 0});
+    }
+}
+
+std::string batch_shape(const tp_plan* p, const tpk::BatchQuery& B, const BatchPrep& x, const std::string& name) {
+    int narrow[tpk::MAX_SUM] = {};
+    narrow_products(p, p->d.fact, narrow);
+    return shape_struct(name, B.q, x.mode, x.smem, x.fast, narrow);
+}
+
+std::string batch_kernel_source(const std::vector<std::string>& shapes) {
+    std::string src;
+    for (size_t k = 0; k < shapes.size(); ++k) src += shapes[k];
+    src += "#include \"jit_batch.cuh\"\n"
+           "__device__ void tpj::dispatch_probe(const tpk::BatchQuery& B, uint64_t r0, uint64_t r1, "
+           "unsigned char* smem) {\n    switch (B.shape) {\n";
+    for (size_t k = 0; k < shapes.size(); ++k)
+        src += "    case " + std::to_string(k) + ": probe_tile<JS_" + std::to_string(k) + ">(B, r0, r1, smem); break;\n";
+    src += "    default: break;\n    }\n}\n";
+    return src;
+}
+
+int batch_kernel_grid(const void* jit_kernel_or_null, uint32_t smem_bytes, int num_sms) {
+    return jit_kernel_or_null ? jit_batch_grid(jit_kernel_or_null, smem_bytes, num_sms)
+                              : tpk::batch_grid(smem_bytes, num_sms);
+}
+
+}  // namespace tp
+
 static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t n, const std::map<int, Tune>& tune,
                                    tp_batch** out) {
     if (!e || !plans || n < 1 || !out) return fail(TP_E_INVALID, "tp_batch_create: bad arguments");
     *out = nullptr;
     for (int i = 0; i < n; ++i) {
-        const tp_plan* p = plans[i];
-        if (!p || p->eng != e) return fail(TP_E_INVALID, "tp_batch_create: plan %d missing or from another engine", i);
-        if (p->d.fact->placement == PL_PAGES || (p->d.join.fact_col >= 0 && p->d.dim->placement == PL_PAGES))
-            return fail(TP_E_INVALID, "tp_batch_create: plan %d reads a table in host pages", i);
-        if (p->n_dims > 1) return fail(TP_E_INVALID, "tp_batch_create: plan %d is a star join (one dimension here)", i);
-        if (p->d.join_many) return fail(TP_E_INVALID, "tp_batch_create: plan %d has a fan-out join", i);
-        if (p->key_bits > 20) return fail(TP_E_INVALID, "tp_batch_create: plan %d has a %d-bit group key (at most 20)", i,
-                                          p->key_bits);
+        tp_status s = batch_check_plan(e, plans[i], i);
+        if (s) {
+            const std::string why = tp_last_error();
+            return fail(s, "tp_batch_create: %s", why.c_str());
+        }
     }
     TP_TRY_CUDA(cudaSetDevice(e->device));
     std::unique_ptr<tp_batch, void (*)(tp_batch*)> b(new (std::nothrow) tp_batch(), batch_free);
@@ -334,64 +478,20 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
     b->e = e;
     b->plans.assign(plans, plans + n);
     // ---- per query sizes and choices
-    struct Q {
-        uint64_t join_cap, join_bytes, acc_bytes, out_bytes, tile, range;
-        bool key64, smem, fast, direct;
-        tpk::TermBounds bounds[tpk::MAX_SUM];
-        int8_t mode[tpk::MAX_SUM];
-        uint32_t smem_bytes;
-    };
-    std::vector<Q> qs(n);
+    std::vector<BatchPrep> qs(n);
     // zeroed every run: counters, error word, group counts, join side cells, accumulators
     uint64_t ff = 0, zero = a256((1 + 2 * (uint64_t)n) * 4) + 256 + a256(8 * (uint64_t)n) * 2, outb = 0;
     uint32_t smem_max = 16;
     uint64_t n_items = 0;
     for (int i = 0; i < n; ++i) {
-        const tp_plan* p = plans[i];
-        Q& x = qs[i];
-        const Tune t = tune_for(tune, p);
-        const float lf = t.lf > 0 ? t.lf : p->load_factor;
-        const bool join = p->d.join.fact_col >= 0;
-        x.key64 = join && p->d.dim->types[p->d.join.dim_col] == TP_I64;
-        x.direct = join && !(e->cfg.flags & TP_FLAG_NO_DIRECT_JOIN) && direct_join_range(p->d.dim, p->d.join.dim_col,
-                                                                                          &x.range);
-        x.join_cap = join && !x.direct ? p2(std::max<uint64_t>(64, (uint64_t)std::ceil(p->d.dim->rows / lf))) : 0;
-        x.join_bytes = x.direct ? a256(x.range * 4) : a256(x.join_cap * (x.key64 ? 16 : 8));
-        const uint64_t G = 1ull << p->key_bits;
-        x.acc_bytes = a256(G * 8 * (1 + 2 * (uint64_t)p->n_sum));
-        int n_avg = 0;
-        for (int a = 0; a < p->d.n_agg; ++a) n_avg += p->d.aggs[a].kind == TP_AGG_AVG;
-        x.out_bytes = a256(G * 8) * 2 + a256(G * 16) * p->n_sum + a256(G * 8) * n_avg;
-        x.tile = (uint64_t)std::min<uint32_t>(std::max<uint32_t>(t.rows_per_warp, 128), 1u << 16) / 128 * 128 *
-                 (tpk::BATCH_THREADS / 32);
-        x.fast = !(e->cfg.flags & TP_FLAG_EXACT_ONLY) && sums_fit_int64(p, p->d.fact);
-        // shared-memory tables: 32-bit words, per tile; needs 64-bit safety
-        x.smem = false;
-        x.smem_bytes = 0;
-        if (x.fast && t.agg != TP_AGG_GLOBAL && p->key_bits <= SMEM_TABLE_BITS) {
-            term_bounds(p, p->d.fact, x.bounds);
-            uint32_t words = 1;
-            bool ok = true;
-            for (int s = 0; s < p->n_sum; ++s) {
-                const unsigned __int128 r = x.tile;
-                if (r * x.bounds[s].span <= 0xFFFFFFFFull) x.mode[s] = 1;
-                else if (r * ((x.bounds[s].span >> 32) + 1) <= 0xFFFFFFFFull) x.mode[s] = 2;
-                else ok = false;
-                words += ok ? (uint32_t)x.mode[s] : 0;
-            }
-            const uint64_t bytes = 4 * G * words;
-            if (ok && bytes <= SMEM_TABLE_MAX) {
-                x.smem = true;
-                x.smem_bytes = (uint32_t)bytes;
-                smem_max = std::max(smem_max, x.smem_bytes);
-            }
-        }
+        const Tune t = tune_for(tune, plans[i]);
+        BatchPrep& x = qs[i];
+        batch_prep(e, plans[i], t.lf, t.rows_per_warp, t.agg, &x);
+        if (x.smem) smem_max = std::max(smem_max, x.smem_bytes);
         ff += x.join_bytes;
         zero += x.acc_bytes;
         outb += x.out_bytes;
-        const uint64_t nb = join ? (p->d.dim->rows + BUILD_CHUNK - 1) / BUILD_CHUNK : 0;
-        const uint64_t np = (p->d.fact->rows + x.tile - 1) / x.tile;
-        n_items += nb + np + 1;
+        n_items += x.build_items + x.probe_items + 1;
     }
     if (n_items >= (1ull << 32)) return fail(TP_E_INVALID, "tp_batch_create: too many tasks");
     const uint64_t qbytes = a256(sizeof(tpk::BatchQuery) * n);
@@ -421,7 +521,8 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
     b->d_items = (tpk::BatchItem*)(qp + qbytes);
     unsigned char* op = qp + qbytes + ibytes;
     b->d_wait = (uint64_t*)(base + total - 256);
-    // ---- descriptors and tasks on the host
+    // ---- descriptors and tasks on the host: every query's build chunks,
+    // then every query's probe tiles, then one finalisation per query
     std::vector<tpk::BatchQuery> hq(n);
     std::vector<tpk::BatchItem> items;
     items.reserve(n_items);
@@ -429,56 +530,7 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
     b->outs.resize(n);
     for (int i = 0; i < n; ++i) {
         const tp_plan* p = plans[i];
-        const Q& x = qs[i];
-        const tp_plan_desc& d = p->d;
-        tpk::BatchQuery& B = hq[i];
-        memset(&B, 0, sizeof(B));
-        tpk::JoinTable jt{};
-        if (d.join.fact_col >= 0) {
-            jt.slots = (uint64_t*)jp;
-            jt.mask = x.join_cap ? x.join_cap - 1 : 0;
-            jt.key64 = x.key64 ? 1 : 0;
-            jt.side = sides + 2 * i;
-            jt.direct = x.direct ? 1 : 0;
-            jt.kmin = x.direct ? p->d.dim->cmin[p->d.join.dim_col] : 0;
-            jt.range = x.direct ? x.range : 0;
-        }
-        jp += x.join_bytes;
-        std::vector<const void*> colptr(d.fact->types.size(), nullptr);
-        for (size_t c = 0; c < colptr.size(); ++c) colptr[c] = d.fact->dev_cols[c];
-        B.q = plan_query_dev(p, colptr, jt, b->d_err, true);
-        B.acc = (uint64_t*)accp;
-        accp += x.acc_bytes;
-        B.key_bits = (uint32_t)p->key_bits;
-        B.smem = x.smem ? 1 : 0;
-        B.fast = x.fast ? 1 : 0;
-        for (int t = 0; t < p->n_sum; ++t) {
-            B.sum_mode[t] = x.smem ? x.mode[t] : 0;
-            B.sum_off[t] = x.smem ? x.bounds[t].lo : 0;
-        }
-        if (d.join.fact_col >= 0) {
-            B.b.key.ptr = d.dim->dev_cols[d.join.dim_col];
-            B.b.key.type = d.dim->types[d.join.dim_col];
-            int nf = 0;
-            for (int g = 0; g < d.n_group; ++g) {
-                if (d.group[g].side != TP_SIDE_DIM) continue;
-                B.b.dcol[nf].ptr = d.dim->dev_cols[d.group[g].col];
-                B.b.dcol[nf].type = d.dim->types[d.group[g].col];
-                B.b.dbits[nf] = d.group[g].bits;
-                B.b.dpos[nf] = p->gdpos[g];
-                ++nf;
-            }
-            B.b.n_dfield = nf;
-            B.b.jt = jt;
-            B.b.err = b->d_err;
-            if (d.dim_filter.col >= 0) {   // the dimension predicate gates the build
-                B.b.has_filter = 1;
-                B.b.fcol.ptr = d.dim->dev_cols[d.dim_filter.col];
-                B.b.fcol.type = d.dim->types[d.dim_filter.col];
-                B.b.flo = d.dim_filter.lo;
-                B.b.fhi = d.dim_filter.hi;
-            }
-        }
+        const BatchPrep& x = qs[i];
         // outputs
         const uint64_t G = 1ull << p->key_bits;
         tpk::OutDev& o = b->outs[i];
@@ -491,56 +543,39 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
             o.sums[t] = (uint64_t*)op;
             op += a256(G * 16);
         }
-        for (int a = 0; a < d.n_agg; ++a) {
-            if (d.aggs[a].kind != TP_AGG_AVG) continue;
+        for (int a = 0; a < p->d.n_agg; ++a) {
+            if (p->d.aggs[a].kind != TP_AGG_AVG) continue;
             const int t = p->sum_of_agg[a];
             o.avgs[t] = (double*)op;
             o.has_avg[t] = 1;
             op += a256(G * 8);
         }
         o.n_groups = b->d_groups + i;
-        B.out = o;
-        const uint64_t nb = d.join.fact_col >= 0 ? (d.dim->rows + BUILD_CHUNK - 1) / BUILD_CHUNK : 0;
-        for (uint64_t k = 0; k < nb; ++k)
-            items.push_back(tpk::BatchItem{(uint32_t)i, tpk::BI_BUILD, k * BUILD_CHUNK,
-                                           std::min<uint64_t>(d.dim->rows, (k + 1) * BUILD_CHUNK), 0});
-        B.build_items = (uint32_t)nb;
+        batch_query_desc(p, x, jp, sides + 2 * i, (uint64_t*)accp, b->d_err, o, &hq[i]);
+        jp += x.join_bytes;
+        accp += x.acc_bytes;
+        batch_items(p, x, (uint32_t)i, tpk::BI_BUILD, &items);
     }
-    for (int i = 0; i < n; ++i) {
-        const uint64_t rows = plans[i]->d.fact->rows, tile = qs[i].tile;
-        const uint64_t np = (rows + tile - 1) / tile;
-        for (uint64_t k = 0; k < np; ++k)
-            items.push_back(tpk::BatchItem{(uint32_t)i, tpk::BI_PROBE, k * tile, std::min(rows, (k + 1) * tile), 0});
-        hq[i].probe_items = (uint32_t)np;
-    }
-    for (int i = 0; i < n; ++i) items.push_back(tpk::BatchItem{(uint32_t)i, tpk::BI_FINAL, 0, 0, 0});
+    for (int i = 0; i < n; ++i) batch_items(plans[i], qs[i], (uint32_t)i, tpk::BI_PROBE, &items);
+    for (int i = 0; i < n; ++i) batch_items(plans[i], qs[i], (uint32_t)i, tpk::BI_FINAL, &items);
     b->n_items = (uint32_t)items.size();
     // run-time compiled probe tasks: one shape struct per distinct query shape
     const void* jk = nullptr;
     if (!(e->cfg.flags & TP_FLAG_NO_JIT)) {
         std::map<std::string, int> ids;
-        std::string src;
+        std::vector<std::string> shapes;
         for (int i = 0; i < n; ++i) {
-            int narrow[tpk::MAX_SUM] = {};
-            narrow_products(plans[i], plans[i]->d.fact, narrow);
-            const Q& x = qs[i];
-            const std::string key = shape_struct("JS_", hq[i].q, x.mode, x.smem, x.fast, narrow);
+            const std::string key = batch_shape(plans[i], hq[i], qs[i], "JS_");
             auto it = ids.find(key);
             if (it == ids.end()) {
                 const int id = (int)ids.size();
                 it = ids.emplace(key, id).first;
-                src += shape_struct("JS_" + std::to_string(id), hq[i].q, x.mode, x.smem, x.fast, narrow);
+                shapes.push_back(batch_shape(plans[i], hq[i], qs[i], "JS_" + std::to_string(id)));
             }
             hq[i].shape = it->second;
         }
-        src += "#include \"jit_batch.cuh\"\n"
-               "__device__ void tpj::dispatch_probe(const tpk::BatchQuery& B, uint64_t r0, uint64_t r1, "
-               "unsigned char* smem) {\n    switch (B.shape) {\n";
-        for (size_t k = 0; k < ids.size(); ++k)
-            src += "    case " + std::to_string(k) + ": probe_tile<JS_" + std::to_string(k) + ">(B, r0, r1, smem); break;\n";
-        src += "    default: break;\n    }\n}\n";
         std::string why;
-        jk = jit_kernel(e, src, "tpj_batch", &why);
+        jk = jit_kernel(e, batch_kernel_source(shapes), "tpj_batch", &why);
     }
     b->jit = jk != nullptr;
     b->probe_items.resize(n);
@@ -551,7 +586,7 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
                                 cudaMemcpyHostToDevice, e->compute));
     TP_TRY_CUDA(cudaStreamSynchronize(e->compute));
     b->smem = smem_max;
-    b->grid = jk ? jit_batch_grid(jk, b->smem, e->num_sms) : tpk::batch_grid(b->smem, e->num_sms);
+    b->grid = batch_kernel_grid(jk, b->smem, e->num_sms);
     // ---- capture: reset tables and counters, run the queue
     cudaGraph_t graph = nullptr;
     TP_TRY_CUDA(cudaStreamBeginCapture(e->compute, cudaStreamCaptureModeThreadLocal));

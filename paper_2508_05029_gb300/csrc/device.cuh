@@ -536,7 +536,13 @@ __device__ __forceinline__ void build_insert(const BuildDev& b, uint64_t i) {
 
 // ------------------------------------------------------- global aggregation slot
 
-__device__ __forceinline__ uint64_t* agg_slot(const AggTable& t, uint64_t key, uint32_t* err) {
+// Slot of key in a hashed global table, claiming an empty slot for a new key;
+// claimed is set when this call took a fresh slot.  Callers count their
+// claims and add them to t.used in bulk (agg_add_claims): one counter word
+// updated once per new key by every thread would serialise at its L2 slice.
+// A table that fills up ends the probe with ERR_OVERFLOW.
+__device__ __forceinline__ uint64_t* agg_slot(const AggTable& t, uint64_t key, uint32_t* err, bool& claimed) {
+    claimed = false;
     if (key == EMPTY64) return t.slots + (t.mask + 1) * t.words;   // side slot
     uint64_t s = fmix64(key) & t.mask;
     for (uint64_t it = 0; it <= t.mask; ++it) {
@@ -547,8 +553,7 @@ __device__ __forceinline__ uint64_t* agg_slot(const AggTable& t, uint64_t key, u
             unsigned long long prev =
                 atomicCAS((unsigned long long*)p, (unsigned long long)EMPTY64, (unsigned long long)key);
             if (prev == EMPTY64) {
-                unsigned long long u = atomicAdd(t.used, 1ull);
-                if (u >= t.max_used) atomicOr(err, ERR_OVERFLOW);
+                claimed = true;
                 return p;
             }
             if (prev == key) return p;
@@ -560,8 +565,9 @@ __device__ __forceinline__ uint64_t* agg_slot(const AggTable& t, uint64_t key, u
 }
 
 // Slot of a key in either kind of global table (direct: key - kmin, in
-// range by the column bounds the host checked).
-__device__ __forceinline__ uint64_t* agg_slot_any(const AggTable& t, uint64_t key, uint32_t* err) {
+// range by the column bounds the host checked; nothing is claimed).
+__device__ __forceinline__ uint64_t* agg_slot_any(const AggTable& t, uint64_t key, uint32_t* err, bool& claimed) {
+    claimed = false;
     if (t.split && (key < t.key_lo || key > t.key_hi)) return nullptr;   // another pass's key range
     if (t.direct) {
         const uint64_t s = key - t.kmin;
@@ -571,7 +577,22 @@ __device__ __forceinline__ uint64_t* agg_slot_any(const AggTable& t, uint64_t ke
         }
         return t.slots + s * t.words;
     }
-    return agg_slot(t, key, err);
+    return agg_slot(t, key, err, claimed);
+}
+
+// Adds n claimed slots to the table's occupancy count; past max_used the
+// execution is retried with a larger table (ERR_OVERFLOW).
+__device__ __forceinline__ void agg_add_claims(const AggTable& t, uint32_t* err, uint32_t n) {
+    if (n == 0 || t.direct) return;
+    const unsigned long long u = atomicAdd(t.used, (unsigned long long)n);
+    if (u + n > t.max_used) atomicOr(err, ERR_OVERFLOW);
+}
+
+// Warp-wide sum of per-lane claim counts, added to the table by lane 0.  All
+// 32 lanes must call it.
+__device__ __forceinline__ void agg_add_claims_warp(const AggTable& t, uint32_t* err, uint32_t n) {
+    const uint32_t tot = __reduce_add_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0) agg_add_claims(t, err, tot);
 }
 
 }  // namespace tpk

@@ -76,14 +76,19 @@ tp_status dev_alloc(tp_engine* e, void** p, uint64_t bytes, cudaStream_t st) {
 }
 
 tp_status copy_batch_column(tp_engine* e, const tp_table* t, const Batch& b, int c, void* full, void* enc,
-                            uint64_t row_off, cudaStream_t st) {
+                            uint64_t row_off, cudaStream_t st, uint8_t** stage) {
     // a narrow column's rows land at its widest encoding's offsets (enc holds
     // narrow_width_max bytes per row)
     const uint64_t sz = b.narrow(c) ? (uint64_t)narrow_width_max(t, c) : type_size(t->types[c]);
     uint8_t* dst = (uint8_t*)(b.narrow(c) ? enc : full) + row_off * sz;
     for (const Extent& x : b.cols[c]) {
-        const cudaError_t err =
-            cudaMemcpyAsync(dst, (uint8_t*)tp_page_ptr(e, x.page) + x.offset, x.bytes, cudaMemcpyHostToDevice, st);
+        const uint8_t* src = (const uint8_t*)tp_page_ptr(e, x.page) + x.offset;
+        if (stage) {
+            memcpy(*stage, src, x.bytes);
+            src = *stage;
+            *stage += x.bytes;
+        }
+        const cudaError_t err = cudaMemcpyAsync(dst, src, x.bytes, cudaMemcpyHostToDevice, st);
         if (err != cudaSuccess) return fail(TP_E_CUDA, "batch copy: %s", cudaGetErrorString(err));
         dst += x.bytes;
         e->h2d_bytes += x.bytes;
@@ -287,6 +292,16 @@ tp_status tp_set_device_budget(tp_engine* e, uint64_t bytes) {
         e->budget.cap = bytes;
     }
     e->budget.cv.notify_all();
+    return TP_OK;
+}
+
+tp_status tp_set_copy_options(tp_engine* e, int32_t prefetch_depth, uint32_t flags) {
+    clear_error();
+    if (!e || prefetch_depth < 0 || prefetch_depth > 64 || (flags & ~(uint32_t)TP_COPY_PINNED_PER_BATCH))
+        return fail(TP_E_INVALID, "tp_set_copy_options: bad arguments");
+    std::lock_guard<std::mutex> lk(e->exec_mu);
+    e->cfg.prefetch_depth = prefetch_depth;
+    e->copy_flags = flags;
     return TP_OK;
 }
 

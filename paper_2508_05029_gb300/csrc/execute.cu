@@ -374,17 +374,42 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
     cudaStream_t cs = prefetch ? S.lane->copy : S.lane->compute;
     std::vector<std::vector<const void*>> gptr(n_slots, std::vector<const void*>(nc, nullptr));
     // copies of group g into slot g % n_slots (after the kernel that last used it)
+    // without a page pool (TP_COPY_PINNED_PER_BATCH, an ablation): each group
+    // goes through a page-locked buffer allocated for it and freed after its
+    // copies
+    const bool per_batch_pinned = (e->copy_flags & TP_COPY_PINNED_PER_BATCH) != 0;
     auto issue = [&](size_t g) -> tp_status {
         const int s = (int)(g % n_slots);
         if (prefetch && g >= (size_t)n_slots) cudaStreamWaitEvent(S.lane->copy, freed[s], 0);
+        uint8_t* buf = nullptr;
+        uint8_t* at = nullptr;
+        if (per_batch_pinned) {
+            uint64_t bytes = 0;
+            for (int c : S.used)
+                for (size_t bi = groups[g].first; bi < groups[g].second; ++bi)
+                    for (const Extent& x : t->batches[bi].cols[c]) bytes += x.bytes;
+            TP_TRY_CUDA(cudaHostAlloc((void**)&buf, bytes ? bytes : 1, cudaHostAllocDefault));
+            at = buf;
+        }
         for (int c : S.used) {
             uint64_t row_off = 0;
             for (size_t bi = groups[g].first; bi < groups[g].second; ++bi) {
-                tp_status r = copy_batch_column(e, t, t->batches[bi], c, slot[s][c], enc[s][c], row_off, cs);
-                if (r) return r;
+                tp_status r = copy_batch_column(e, t, t->batches[bi], c, slot[s][c], enc[s][c], row_off, cs,
+                                                buf ? &at : nullptr);
+                if (r) {
+                    if (buf) {
+                        cudaStreamSynchronize(cs);
+                        cudaFreeHost(buf);
+                    }
+                    return r;
+                }
                 row_off += t->batches[bi].rows;
             }
             gptr[s][c] = slot[s][c];
+        }
+        if (buf) {
+            TP_TRY_CUDA(cudaStreamSynchronize(cs));
+            TP_TRY_CUDA(cudaFreeHost(buf));
         }
         if (prefetch) cudaEventRecord(loaded[s], S.lane->copy);
         return TP_OK;
@@ -513,6 +538,10 @@ tp_status map_err(uint32_t err) {
     return TP_OK;
 }
 
+}  // namespace
+
+namespace tp {
+
 // Output arrays for `cap` groups carved from one allocation.
 tp_status alloc_result(tp_engine* e, tp_plan* p, uint64_t cap, tp_result** out, tpk::OutDev* od,
                        unsigned long long* n_groups_dev, cudaStream_t st) {
@@ -564,6 +593,10 @@ tp_status alloc_result(tp_engine* e, tp_plan* p, uint64_t cap, tp_result** out, 
     *out = r;
     return TP_OK;
 }
+
+}  // namespace tp
+
+namespace {
 
 // Copies rows [0, n) of every array of src to rows [at, at + n) of dst (both
 // results of the same plan), on the device.
@@ -645,6 +678,11 @@ tpk::OutDev out_at(tpk::OutDev od, uint64_t at, int n_sum) {
 // when the key range is at most four times the expected groups (or below
 // DIRECT_AGG_ALWAYS slots).
 constexpr uint64_t DIRECT_AGG_MAX_SLOTS = 1ull << 27;
+// Global aggregation under a filter keeping fewer than this fraction of the
+// rows (sampled) selects the passing rows first, then aggregates them; the
+// selection vector covers at most SEL_SLICE_ROWS rows (4 bytes each) at once.
+constexpr double SELECT_MAX_SELECTIVITY = 0.25;
+constexpr uint64_t SEL_SLICE_ROWS = 1ull << 26;
 constexpr uint64_t DIRECT_AGG_ALWAYS = 1ull << 20;
 
 // Lookahead filter: used automatically when the join table takes at least
@@ -1329,6 +1367,17 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
     }
     const bool shared = p->strategy == TP_AGG_SHARED;
     const uint32_t G = shared ? (1u << p->key_bits) : 0;
+    // many groups under a selective filter: a selection vector of the passing
+    // rows' indices, filled and consumed per slice of at most SEL_SLICE_ROWS
+    // rows of a batch
+    uint64_t sel_rows = 0;
+    if (!shared && !(e->cfg.flags & TP_FLAG_NO_STAGED) && d.filter.col >= 0 && p->n_dims <= 1 && !d.join_many &&
+        p->selectivity < SELECT_MAX_SELECTIVITY) {
+        uint64_t max_rows = S.fact->placement == PL_PAGES ? 0 : S.fact->rows;
+        for (auto& b : S.fact->batches) max_rows = std::max(max_rows, b.rows);
+        sel_rows = std::min<uint64_t>(SEL_SLICE_ROWS, max_rows);
+        est += align256(sel_rows * 4);
+    }
     uint64_t agg_cap = 0;
     bool gdirect = false;           // direct-addressed global table over [rmin, rmin + rspan)
     bool have_range = false;        // packed group keys inside [rmin, rmin + rspan) by the column bounds
@@ -1636,15 +1685,16 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         timer.collect();
         guard.release();
     } else {
-        // staged kernel unless disabled; all columns staged unless the filter is
-        // selective; runs folded when the key comes from fact columns only; 64-bit
-        // low-word updates when column bounds rule out overflow (any mix of the
-        // staged and plain kernels then agrees on the low words)
+        // selective filters: the passing rows are selected first, then
+        // aggregated; otherwise the staged kernel unless disabled (all columns
+        // staged); 64-bit low-word updates when column bounds rule out
+        // overflow (any mix of the kernels then agrees on the low words)
         const bool g_staged = !(e->cfg.flags & TP_FLAG_NO_STAGED);
         const bool gfast = g_staged && !(e->cfg.flags & TP_FLAG_EXACT_ONLY) && sums_fit_int64(p, S.fact);
         const bool stage_all = p->selectivity >= 0.25;
-        bool fold = d.n_group > 0;
-        for (int g = 0; g < d.n_group; ++g) fold = fold && d.group[g].side == TP_SIDE_FACT;
+        uint32_t* sel = nullptr;
+        unsigned long long* sel_cursor = (unsigned long long*)((uint8_t*)misc + 1024);
+        if (sel_rows && (s = sc.alloc((void**)&sel, align256(sel_rows * 4)))) return s;
         // key ranges still to aggregate, the next one at the back (ascending
         // keys come out in order); one range covering every key unless a
         // table had to be split
@@ -1778,12 +1828,29 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             at.key_lo = kr.lo;
             at.key_hi = kr.lo + (kr.span - 1);
             auto global_core = [&](const tpk::QueryDev& q, uint64_t rows) -> tp_status {
+                if (sel && tpk::select_usable(q, std::min(rows, sel_rows))) {
+                    // selective filter: select the passing rows, then aggregate them
+                    for (uint64_t off = 0; off < rows; off += sel_rows) {
+                        const uint64_t nr = std::min(sel_rows, rows - off);
+                        const tpk::QueryDev qs = off ? tpk::offset_rows(q, off) : q;
+                        TP_TRY_CUDA(cudaMemsetAsync(sel_cursor, 0, sizeof(unsigned long long), st));
+                        mark_launch(e);
+                        mark_launch(e);
+                        tp_status r = cuda_check(timer.run(st, nr, [&] {
+                            cudaError_t ce = tpk::launch_select(qs, nr, sel, sel_cursor, e->num_sms, st);
+                            if (ce != cudaSuccess) return ce;
+                            return tpk::launch_agg_selected(qs, sel, sel_cursor, nr, at, gfast, e->num_sms, st);
+                        }), "aggregate");
+                        if (r) return r;
+                    }
+                    return TP_OK;
+                }
                 mark_launch(e);
                 tpk::StageLayout L;
                 if (g_staged && q.n_xjoin == 0 && !q.jt.many && tpk::staged_layout_global(q, stage_all, &L)) {
                     const uint64_t whole_rows = rows / tpk::ST_TILE * tpk::ST_TILE;
                     tp_status r = cuda_check(timer.run(st, whole_rows, [&] {
-                        return tpk::launch_agg_global_staged(q, L, rows, at, gfast, fold, e->num_sms, st);
+                        return tpk::launch_agg_global_staged(q, L, rows, at, gfast, e->num_sms, st);
                     }), "aggregate");
                     if (r || whole_rows == rows) return r;
                     mark_launch(e);  // rows after the last whole tile
@@ -2166,7 +2233,9 @@ tp_status tp_plan_create(tp_engine* e, const tp_plan_desc* d, tp_plan** out) {
     }
     std::unique_ptr<tp_plan> p(new (std::nothrow) tp_plan());
     if (!p) return fail(TP_E_NOMEM, "plan: out of host memory");
+    static std::atomic<uint64_t> next_serial{1};
     p->eng = e;
+    p->serial = next_serial++;
     p->d = *d;
     if (!d->dim_filter_on) p->d.dim_filter.col = -1;   // internally: col < 0 = no predicate
     if (join) {   // every joined dimension in one list: the first, then the further ones

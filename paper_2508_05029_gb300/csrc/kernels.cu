@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(256) k_agg_global(const __grid_constant__ Quer
     const uint64_t nwarps = blockDim.x >> 5;
     const uint64_t ntiles = (n + 127) / 128;
     const uint64_t nfull = n / 128;
+    uint32_t claims = 0;   // fresh slots this lane took, added to the table once per warp at the end
     for (uint64_t tt = blockIdx.x * nwarps + (threadIdx.x >> 5); tt < ntiles; tt += gridDim.x * nwarps) {
         const bool full = tt < nfull;
         // fan-out joins pair a row with each partner in turn (m); otherwise one pass
@@ -228,7 +229,9 @@ __global__ void __launch_bounds__(256) k_agg_global(const __grid_constant__ Quer
             for (int i = 0; i < 4; ++i) {
                 slot[i] = nullptr;
                 if (!pass[i] || ((i & 1) && fold[i >> 1])) continue;
-                slot[i] = agg_slot_any(t, key[i], q.err);
+                bool claimed;
+                slot[i] = agg_slot_any(t, key[i], q.err, claimed);
+                claims += claimed ? 1u : 0u;
                 if (slot[i])
                     atomicAdd((unsigned long long*)(slot[i] + 1), (i & 1) == 0 && fold[i >> 1] ? 2ull : 1ull);
             }
@@ -247,6 +250,7 @@ __global__ void __launch_bounds__(256) k_agg_global(const __grid_constant__ Quer
             if (!q.jt.many) break;
         }
     }
+    agg_add_claims_warp(t, q.err, claims);
 }
 
 cudaError_t launch_agg_global(const QueryDev& q, uint64_t n, const AggTable& t, int num_sms,
@@ -429,32 +433,66 @@ cudaError_t launch_direct_emit(const AggTable& t, uint64_t n_slots, const unsign
     return cudaGetLastError();
 }
 
-__global__ void k_compact_global(const __grid_constant__ AggTable t, uint64_t cap_with_side,
-                                 uint64_t* __restrict__ keys, uint32_t* __restrict__ idx,
-                                 unsigned long long* count, unsigned long long* maxkey) {
-    const int lane = threadIdx.x & 31;
+// Occupied slots of a hashed global table as (key, slot) pairs, in no
+// particular order (a sort by key follows), plus the largest key.  A CTA
+// takes COMPACT_PER * 256 slots at a time (slot = chunk + i * 256 + thread,
+// coalesced), ranks its occupied ones with a block scan and reserves their
+// output range with one atomic, so the shared counter sees one update per
+// chunk instead of one per warp.
+constexpr int COMPACT_PER = 8;
+
+__global__ void __launch_bounds__(256) k_compact_global(const __grid_constant__ AggTable t, uint64_t cap_with_side,
+                                                        uint64_t* __restrict__ keys, uint32_t* __restrict__ idx,
+                                                        unsigned long long* count, unsigned long long* maxkey) {
+    __shared__ uint32_t warp_sums[8];
+    __shared__ unsigned long long base_s;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned long long local_max = 0;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t n_iter = (cap_with_side + stride - 1) / stride;
-    for (uint64_t it = 0; it < n_iter; ++it) {
-        const uint64_t s = it * stride + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-        bool has = false;
-        uint64_t key = 0;
-        if (s < cap_with_side) {
-            const uint64_t* p = t.slots + s * t.words;
-            has = p[1] != 0;
-            key = (s == cap_with_side - 1) ? EMPTY64 : p[0];
+    const uint64_t per_chunk = (uint64_t)COMPACT_PER * 256;
+    const uint64_t n_chunks = (cap_with_side + per_chunk - 1) / per_chunk;
+    for (uint64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        uint32_t occ = 0;
+        uint64_t key[COMPACT_PER];
+#pragma unroll
+        for (int i = 0; i < COMPACT_PER; ++i) {
+            const uint64_t s = ch * per_chunk + (uint64_t)i * 256 + threadIdx.x;
+            key[i] = 0;
+            if (s < cap_with_side) {
+                const uint64_t* p = t.slots + s * t.words;
+                if (p[1] != 0) {
+                    occ |= 1u << i;
+                    key[i] = (s == cap_with_side - 1) ? EMPTY64 : p[0];
+                }
+            }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, has);
-        unsigned long long base = 0;
-        if (lane == 0 && m) base = atomicAdd(count, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (has) {
-            const uint64_t pos = base + __popc(m & ((1u << lane) - 1u));
-            keys[pos] = key;
-            idx[pos] = (uint32_t)s;
-            if (key > local_max) local_max = key;
+        // block-wide exclusive scan of the occupied counts
+        const uint32_t c = (uint32_t)__popc(occ);
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
+        if (lane == 31) warp_sums[w] = inc;
+        __syncthreads();
+        uint32_t before = 0, all = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            before += k < w ? warp_sums[k] : 0u;
+            all += warp_sums[k];
+        }
+        if (threadIdx.x == 0) base_s = all ? atomicAdd(count, (unsigned long long)all) : 0ull;
+        __syncthreads();
+        uint64_t pos = base_s + before + inc - c;
+#pragma unroll
+        for (int i = 0; i < COMPACT_PER; ++i) {
+            if (!(occ >> i & 1u)) continue;
+            keys[pos] = key[i];
+            idx[pos] = (uint32_t)(ch * per_chunk + (uint64_t)i * 256 + threadIdx.x);
+            ++pos;
+            if (key[i] > local_max) local_max = key[i];
+        }
+        __syncthreads();   // warp_sums and base_s are reused by the next chunk
     }
     for (int off = 16; off > 0; off >>= 1) {
         unsigned long long o = __shfl_xor_sync(0xffffffffu, local_max, off);
@@ -466,7 +504,7 @@ __global__ void k_compact_global(const __grid_constant__ AggTable t, uint64_t ca
 cudaError_t launch_compact_global(const AggTable& t, uint64_t cap_with_side, uint64_t* keys,
                                   uint32_t* idx, unsigned long long* count,
                                   unsigned long long* maxkey, int num_sms, cudaStream_t st) {
-    uint64_t blocks = (cap_with_side + 255) / 256;
+    uint64_t blocks = (cap_with_side + COMPACT_PER * 256 - 1) / (COMPACT_PER * 256);
     uint64_t cap = (uint64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;
     k_compact_global<<<(unsigned)blocks, 256, 0, st>>>(t, cap_with_side, keys, idx, count, maxkey);

@@ -353,12 +353,25 @@ cudaError_t launch_agg_shared_staged_jit(const void* kernel, const QueryDev& q, 
 
 // Staged global-table aggregation.  stage_all = false stages only the filter
 // column (selective filters: the other columns are read for surviving rows
-// only).  fast: 64-bit reductions on low words (bounds proved); fold: fold
-// runs of equal keys in consecutive rows.  Whole tiles only, as above; the
+// only).  fast: 64-bit reductions on low words (bounds proved).  Equal keys
+// among a warp's rows update the table once.  Whole tiles only, as above; the
 // caller runs the remaining rows through launch_agg_global.
 bool staged_layout_global(const QueryDev& q, bool stage_all, StageLayout* L);
 cudaError_t launch_agg_global_staged(const QueryDev& q, const StageLayout& L, uint64_t n, const AggTable& t,
-                                     bool fast, bool fold, int num_sms, cudaStream_t st);
+                                     bool fast, int num_sms, cudaStream_t st);
+
+// Global-table aggregation under a selective filter, in two launches:
+// launch_select appends the indices of the rows of [0, n) that pass q's
+// filter to sel (room for n entries) at *cursor (zeroed by the caller), and
+// launch_agg_selected joins, keys and aggregates those *cursor rows (at most
+// max_rows; the filter is not evaluated again).  select_usable: the query and
+// row count suit it (a filter on a 16-byte aligned column, no further joins,
+// no fan-out, fewer than 2^32 rows).
+bool select_usable(const QueryDev& q, uint64_t n);
+cudaError_t launch_select(const QueryDev& q, uint64_t n, uint32_t* sel, unsigned long long* cursor, int num_sms,
+                          cudaStream_t st);
+cudaError_t launch_agg_selected(const QueryDev& q, const uint32_t* sel, const unsigned long long* count,
+                                uint64_t max_rows, const AggTable& t, bool fast, int num_sms, cudaStream_t st);
 
 // ------------------------------------------------------- partitioned join
 //

@@ -1,17 +1,36 @@
-// Request server: continuous admission of queries onto concurrent lanes.
+// Request server: continuous batching of arriving queries, with concurrent
+// lanes for the queries a batched launch cannot take.
 //
-// Paper basis: Section 3.3.1 (Compute Executor threads each drive their own
-// CUDA stream and take tasks from a queue), Section 3.3.2 (tasks reserve
-// device memory before they run; the reservation decides when a task may
-// start).  Each worker thread owns a lane (compute stream, copy stream,
-// pinned status words).  A worker admits the oldest queued request whose plan
-// is not already running, as long as fewer than max_inflight run; the request
-// executes on the worker's lane, overlapping on the device with the others.
-// A request whose reservation does not fit goes back to the head of the queue
-// and is retried after the next completion releases memory (idle cached join
-// tables are evicted first); it fails with TP_E_BUDGET only when nothing else
-// is running.
+// Paper basis: Section 3.3.1 (Compute Executor threads drive their own CUDA
+// streams and take tasks from a queue), Section 3.3.2 (tasks reserve device
+// memory before they run; the reservation decides when a task may start).
+//
+// Batching (TP_SERVE_BATCH): a dispatcher thread takes every queued request
+// that a batched launch can run (device-resident tables, one join), as many as
+// the device budget admits, and starts them together as one persistent queue
+// kernel (batch.cu: build chunks, probe tiles and finalisations of all of
+// them, claimed by resident CTAs) on one of two launch slots, each with its
+// own stream.  Requests that arrive while a batch runs form the next batch,
+// which starts at once on the other slot, so its work overlaps the running
+// batch's tail on the device; a completion thread hands out the results of
+// each finished batch in launch order.  Each request keeps its own result
+// arrays, join table, accumulators and error word, so its result is the one
+// it gets alone.  The probe tasks are compiled at run time for the shapes of
+// every plan the server has seen (one kernel for all of them, rebuilt when a
+// new shape arrives); without run-time compilation the ahead-of-time queue
+// kernel runs them.
+//
+// Lanes: worker threads, each owning a lane (compute, copy and spill
+// streams, pinned status words), run the other requests one tp_execute at a
+// time, overlapping on the device; with batching off they run every request.
+// A lane admits the oldest queued request whose plan is not already running,
+// while fewer than max_inflight run.  A request whose reservation does not fit
+// goes back to the head of the queue and is retried after the next
+// completion releases memory (idle cached join tables are evicted first); it
+// fails with TP_E_BUDGET only when nothing else ran while it tried.
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 
 #include "tp_internal.h"
 
@@ -27,11 +46,40 @@ int64_t now_ns() {
 struct Request {
     uint64_t ticket = 0;
     tp_plan* plan = nullptr;
+    bool batchable = false;   // runs in a batched launch (TP_SERVE_BATCH)
     bool done = false;
+    bool waited = false;      // a tp_wait is blocked on it
     tp_status status = TP_OK;
     std::string message;
     tp_result* result = nullptr;
     int64_t t_submit = 0, t_start = 0, t_end = 0;
+};
+
+uint64_t a256(uint64_t x) { return (x + 255) & ~255ull; }
+
+constexpr uint64_t SERVE_WAIT_NS = 2000000000ull;   // limit of every dependency wait of a batched launch
+constexpr int N_SLOTS = 2;                          // batched launches in flight at once
+
+// What the dispatcher keeps per plan: its batched sizes and its shape id in
+// the server's run-time compiled queue kernel.
+struct PlanInfo {
+    BatchPrep x;
+    int shape = 0;
+    uint64_t result_bytes = 0;   // result arrays for 2^key_bits groups
+};
+
+// One batched launch in flight.
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    unsigned char* h_stage = nullptr;   // pinned: descriptors and tasks (to the device), then status words (back)
+    uint64_t h_cap = 0;
+    void* arena = nullptr;
+    uint64_t reserved = 0;
+    uint64_t status_off = 0;            // offset of the status words in h_stage
+    std::vector<Request*> reqs;
+    std::vector<tp_result*> res;
+    bool busy = false;
 };
 
 }  // namespace
@@ -40,6 +88,8 @@ struct tp_server {
     tp_engine* e = nullptr;
     int max_inflight = 1;
     bool cache_on = false;
+    bool batch_on = false;
+    int max_batch = 256;
     std::vector<Lane> lanes;
     std::vector<std::thread> threads;
     std::mutex mu;
@@ -48,20 +98,43 @@ struct tp_server {
     std::map<uint64_t, std::unique_ptr<Request>> reqs;
     std::map<const tp_plan*, int> running;
     uint64_t next_ticket = 1;
-    int inflight = 0;
+    int inflight = 0;               // lane executions running
     bool stopping = false;
     uint64_t completions = 0;
     tp_server_stats stats{};
     DimCache cache;
+    // batching
+    Slot slots[N_SLOTS];
+    std::deque<int> launched;       // busy slots in launch order
+    bool dispatcher_done = false;
+    std::thread dispatcher, completer;
+    std::map<std::pair<const tp_plan*, uint64_t>, PlanInfo> plans;   // by plan and its serial; dispatcher only
+    std::map<std::string, int> shape_ids;       // dispatcher thread only
+    std::vector<std::string> shapes;
+    const void* kernel = nullptr;               // nullptr: the ahead-of-time queue kernel
+    std::map<std::pair<const void*, uint32_t>, int> grids;
 };
 
 namespace {
 
-// Next admissible request (caller holds sv->mu), or nullptr.
+void finish(tp_server* sv, Request* r, tp_status st, const std::string& msg, tp_result* res) {
+    r->status = st;
+    r->message = msg;
+    r->result = res;
+    r->t_end = now_ns();
+    r->done = true;
+    ++sv->completions;
+    if (st) ++sv->stats.failed;
+    else ++sv->stats.completed;
+}
+
+// ------------------------------------------------------------------ lanes
+
+// Next request for a lane (caller holds sv->mu), or nullptr.
 Request* pick(tp_server* sv) {
     if (sv->inflight >= sv->max_inflight) return nullptr;
     for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
-        if (sv->running.count((*it)->plan)) continue;
+        if ((*it)->batchable || sv->running.count((*it)->plan)) continue;
         Request* r = *it;
         sv->queue.erase(it);
         return r;
@@ -74,17 +147,21 @@ void worker(tp_server* sv, int idx) {
     cudaSetDevice(sv->e->device);
     for (;;) {
         Request* r = nullptr;
+        uint64_t c0 = 0;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
             sv->cv.wait(lk, [&] {
-                return (sv->stopping && sv->queue.empty()) ||
-                       (sv->inflight < sv->max_inflight && !sv->queue.empty() && (r = pick(sv)) != nullptr);
+                bool lane_work = false;
+                for (Request* q : sv->queue) lane_work = lane_work || !q->batchable;
+                return (sv->stopping && !lane_work) ||
+                       (sv->inflight < sv->max_inflight && lane_work && (r = pick(sv)) != nullptr);
             });
-            if (!r) return;   // stopping and nothing left
+            if (!r) return;   // stopping and nothing left for lanes
             ++sv->inflight;
             ++sv->running[r->plan];
             if ((uint32_t)sv->inflight > sv->stats.inflight_peak) sv->stats.inflight_peak = (uint32_t)sv->inflight;
             if (!r->t_start) r->t_start = now_ns();
+            c0 = sv->completions;   // completions before this attempt
         }
         tp_result* res = nullptr;
         DimCache* cache = sv->cache_on ? &sv->cache : nullptr;
@@ -97,25 +174,356 @@ void worker(tp_server* sv, int idx) {
         std::unique_lock<std::mutex> lk(sv->mu);
         --sv->inflight;
         if (--sv->running[r->plan] == 0) sv->running.erase(r->plan);
-        if (st == TP_E_BUDGET && sv->inflight > 0) {
-            // others hold memory: retry this request after the next completion
+        const bool others = sv->inflight > 0 || !sv->launched.empty() || sv->completions != c0;
+        if (st == TP_E_BUDGET && others) {
+            // memory is or was held by other requests: retry after the next completion
             sv->queue.push_front(r);
             ++sv->stats.budget_waits;
-            const uint64_t c0 = sv->completions;
-            sv->cv.wait_for(lk, std::chrono::milliseconds(200), [&] { return sv->completions != c0; });
+            const uint64_t c1 = sv->completions;
+            if (c1 == c0)
+                sv->cv.wait_for(lk, std::chrono::milliseconds(200), [&] { return sv->completions != c1; });
             sv->cv.notify_all();
             continue;
         }
-        r->status = st;
-        r->message = st ? tp_last_error() : "";
-        r->result = res;
-        r->t_end = now_ns();
-        r->done = true;
-        ++sv->completions;
-        if (st) ++sv->stats.failed;
-        else ++sv->stats.completed;
+        finish(sv, r, st, st ? tp_last_error() : "", res);
         sv->cv.notify_all();
     }
+}
+
+// --------------------------------------------------------------- batching
+
+// The dispatcher's record of p: sizes with probe tiles that spread one query
+// over the whole GPU, and its shape in the server's kernel (a new shape
+// rebuilds the kernel).
+const PlanInfo& plan_info(tp_server* sv, tp_plan* p) {
+    auto it = sv->plans.find({p, p->serial});
+    if (it != sv->plans.end()) return it->second;
+    PlanInfo pi;
+    // rows per warp: about four tiles per SM for this query alone, 128..1024
+    const uint64_t per = p->d.fact->rows / ((uint64_t)(tpk::BATCH_THREADS / 32) * 4 * (uint64_t)sv->e->num_sms);
+    uint32_t rpw = 128;
+    while (rpw < 1024 && rpw < per) rpw <<= 1;
+    batch_prep(sv->e, p, 0.0f, rpw, TP_AGG_AUTO, &pi.x);
+    int n_avg = 0;
+    for (int a = 0; a < p->d.n_agg; ++a) n_avg += p->d.aggs[a].kind == TP_AGG_AVG;
+    const uint64_t G = 1ull << p->key_bits;
+    pi.result_bytes = a256(G * 8) * 2 + a256(G * 16) * p->n_sum + a256(G * 8) * n_avg;
+    if (!(sv->e->cfg.flags & TP_FLAG_NO_JIT)) {
+        tpk::BatchQuery B;
+        tpk::OutDev od{};
+        batch_query_desc(p, pi.x, nullptr, nullptr, nullptr, nullptr, od, &B);
+        const std::string key = batch_shape(p, B, pi.x, "JS_");
+        auto s = sv->shape_ids.find(key);
+        if (s == sv->shape_ids.end()) {
+            const int id = (int)sv->shapes.size();
+            s = sv->shape_ids.emplace(key, id).first;
+            sv->shapes.push_back(batch_shape(p, B, pi.x, "JS_" + std::to_string(id)));
+            std::string why;
+            sv->kernel = jit_kernel(sv->e, batch_kernel_source(sv->shapes), "tpj_batch", &why);
+        }
+        pi.shape = s->second;
+    }
+    return sv->plans.emplace(std::make_pair(p, p->serial), pi).first->second;
+}
+
+// Device bytes of a batch of the plans of rs: join tables, counters, error
+// words, group counts, side cells, accumulators, descriptors, tasks, wait word.
+struct BatchSizes {
+    uint64_t ff = 0, zero = 0, qbytes = 0, ibytes = 0, total = 0, results = 0, items = 0;
+    uint32_t smem = 16;
+};
+
+BatchSizes batch_sizes(tp_server* sv, const std::vector<Request*>& rs) {
+    BatchSizes z;
+    const uint64_t n = rs.size();
+    z.zero = a256((1 + 2 * n) * 4) + 256 + a256(8 * n) * 3;   // counters, batch error, groups, sides, query errors
+    for (Request* r : rs) {
+        const PlanInfo& pi = plan_info(sv, r->plan);
+        z.ff += pi.x.join_bytes;
+        z.zero += pi.x.acc_bytes;
+        z.items += pi.x.build_items + pi.x.probe_items + 1;
+        z.results += pi.result_bytes;
+        if (pi.x.smem) z.smem = std::max(z.smem, pi.x.smem_bytes);
+    }
+    z.qbytes = a256(sizeof(tpk::BatchQuery) * n);
+    z.ibytes = a256(sizeof(tpk::BatchItem) * z.items);
+    z.total = z.ff + z.zero + z.qbytes + z.ibytes + 256;
+    return z;
+}
+
+tp_status grow_stage(Slot& sl, uint64_t bytes) {
+    if (bytes <= sl.h_cap) return TP_OK;
+    if (sl.h_stage) cudaFreeHost(sl.h_stage);
+    sl.h_stage = nullptr;
+    sl.h_cap = 0;
+    const uint64_t cap = std::max<uint64_t>(bytes + bytes / 2, 1 << 20);
+    TP_TRY_CUDA(cudaHostAlloc((void**)&sl.h_stage, cap, cudaHostAllocDefault));
+    sl.h_cap = cap;
+    return TP_OK;
+}
+
+// Lays out, copies and launches the batch of sl.reqs on sl's stream; the
+// device reservation of z.total is already held (sl.reserved).
+tp_status launch_slot(tp_server* sv, Slot& sl, const BatchSizes& z) {
+    tp_engine* e = sv->e;
+    const uint64_t n = sl.reqs.size();
+    tp_status s = dev_alloc(e, &sl.arena, z.total, sl.st);
+    if (s) return s;
+    unsigned char* base = (unsigned char*)sl.arena;
+    unsigned char* zp = base + z.ff;
+    unsigned* d_ctr = (unsigned*)zp;
+    zp += a256((1 + 2 * n) * 4);
+    uint32_t* d_err = (uint32_t*)zp;
+    zp += 256;
+    unsigned long long* d_groups = (unsigned long long*)zp;
+    zp += a256(8 * n);
+    uint32_t* sides = (uint32_t*)zp;
+    zp += a256(8 * n);
+    uint32_t* q_err = (uint32_t*)zp;   // one error word per query: one query's failure stays its own
+    zp += a256(8 * n);
+    unsigned char* accp = zp;
+    unsigned char* dq = base + z.ff + z.zero;
+    // host side: descriptors, then tasks, then the wait limit, in the pinned stage
+    const uint64_t status_bytes = 16 * n + 8;
+    if ((s = grow_stage(sl, z.qbytes + z.ibytes + 256 + a256(status_bytes)))) return s;
+    tpk::BatchQuery* hq = (tpk::BatchQuery*)sl.h_stage;
+    tpk::BatchItem* hi = (tpk::BatchItem*)(sl.h_stage + z.qbytes);
+    std::vector<tpk::BatchItem> items;
+    items.reserve(z.items);
+    unsigned char* jp = base;
+    sl.res.assign(n, nullptr);
+    uint32_t smem = 16;
+    for (uint64_t i = 0; i < n; ++i) {
+        tp_plan* p = sl.reqs[i]->plan;
+        const PlanInfo& pi = plan_info(sv, p);
+        tpk::OutDev od;
+        if ((s = alloc_result(e, p, 1ull << p->key_bits, &sl.res[i], &od, d_groups + i, sl.st))) return s;
+        batch_query_desc(p, pi.x, jp, sides + 2 * i, (uint64_t*)accp, q_err + 2 * i, od, &hq[i]);
+        hq[i].shape = pi.shape;
+        jp += pi.x.join_bytes;
+        accp += pi.x.acc_bytes;
+        if (pi.x.smem) smem = std::max(smem, pi.x.smem_bytes);
+        batch_items(p, pi.x, (uint32_t)i, tpk::BI_BUILD, &items);
+    }
+    for (uint64_t i = 0; i < n; ++i) batch_items(sl.reqs[i]->plan, plan_info(sv, sl.reqs[i]->plan).x, (uint32_t)i,
+                                                 tpk::BI_PROBE, &items);
+    for (uint64_t i = 0; i < n; ++i) batch_items(sl.reqs[i]->plan, plan_info(sv, sl.reqs[i]->plan).x, (uint32_t)i,
+                                                 tpk::BI_FINAL, &items);
+    memcpy(hi, items.data(), items.size() * sizeof(tpk::BatchItem));
+    memcpy(sl.h_stage + z.qbytes + z.ibytes, &SERVE_WAIT_NS, 8);
+    const uint64_t* d_wait = (const uint64_t*)(dq + z.qbytes + z.ibytes);
+    TP_TRY_CUDA(cudaMemcpyAsync(dq, sl.h_stage, z.qbytes + z.ibytes + 8, cudaMemcpyHostToDevice, sl.st));
+    if (z.ff) TP_TRY_CUDA(cudaMemsetAsync(base, 0xFF, z.ff, sl.st));
+    TP_TRY_CUDA(cudaMemsetAsync(base + z.ff, 0, z.zero, sl.st));
+    const void* k = sv->kernel;
+    auto g = sv->grids.find({k, smem});
+    if (g == sv->grids.end()) g = sv->grids.emplace(std::make_pair(k, smem), batch_kernel_grid(k, smem, e->num_sms)).first;
+    const tpk::BatchQuery* a_q = (const tpk::BatchQuery*)dq;
+    const tpk::BatchItem* a_items = (const tpk::BatchItem*)(dq + z.qbytes);
+    uint32_t a_n = (uint32_t)items.size(), a_nq = (uint32_t)n;
+    if (k) {
+        void* args[] = {&a_q, &a_items, &a_n, &a_nq, &d_ctr, &d_err, &d_wait};
+        TP_TRY_CUDA(cudaLaunchKernel(k, dim3(g->second), dim3(tpk::BATCH_THREADS), args, smem, sl.st));
+        e->jit_launches++;
+    } else {
+        TP_TRY_CUDA(tpk::launch_batch(a_q, a_items, a_n, a_nq, d_ctr, d_err, d_wait, smem, g->second, sl.st));
+    }
+    e->launches++;
+    // status words back: group counts, per-query error words, the batch error word
+    sl.status_off = z.qbytes + z.ibytes + 256;
+    unsigned char* hs = sl.h_stage + sl.status_off;
+    TP_TRY_CUDA(cudaMemcpyAsync(hs, d_groups, 8 * n, cudaMemcpyDeviceToHost, sl.st));
+    TP_TRY_CUDA(cudaMemcpyAsync(hs + 8 * n, q_err, 8 * n, cudaMemcpyDeviceToHost, sl.st));
+    TP_TRY_CUDA(cudaMemcpyAsync(hs + 16 * n, d_err, 4, cudaMemcpyDeviceToHost, sl.st));
+    TP_TRY_CUDA(cudaEventRecord(sl.ev, sl.st));
+    e->d2h_bytes += 16 * n + 4;
+    ++sv->stats.batches;
+    return TP_OK;
+}
+
+tp_status map_err_word(uint32_t err) {
+    if (err & tpk::ERR_TIMEOUT) return fail(TP_E_TIMEOUT, "a bounded wait of the batched launch expired");
+    if (err & tpk::ERR_DUP) return fail(TP_E_DUP_KEY, "the join build side holds a duplicate key");
+    if (err & tpk::ERR_RANGE) return fail(TP_E_RANGE, "a group field value does not fit its bit width");
+    if (err & tpk::ERR_INTERNAL) return fail(TP_E_INTERNAL, "device consistency check failed");
+    return TP_OK;
+}
+
+// Frees what a slot's batch holds (after its stream is done with it).
+void slot_release(tp_server* sv, Slot& sl) {
+    if (sl.arena) dev_free(sv->e, sl.arena, sl.st);
+    sl.arena = nullptr;
+    if (sl.reserved) release(sv->e, sl.reserved);
+    sl.reserved = 0;
+}
+
+void dispatcher(tp_server* sv) {
+    tp_engine* e = sv->e;
+    cudaSetDevice(e->device);
+    for (;;) {
+        std::vector<Request*> take;
+        int si = -1;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            bool work = false;
+            sv->cv.wait(lk, [&] {
+                work = false;
+                for (Request* q : sv->queue) work = work || q->batchable;
+                si = -1;
+                for (int k = 0; k < N_SLOTS; ++k)
+                    if (!sv->slots[k].busy) si = k;
+                return (sv->stopping && !work) || (work && si >= 0);
+            });
+            if (!work) break;   // stopping, nothing batchable left
+            for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)take.size() < sv->max_batch;) {
+                if ((*it)->batchable) {
+                    take.push_back(*it);
+                    it = sv->queue.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            sv->slots[si].busy = true;
+        }
+        // admission by the device budget: the longest prefix (in arrival order)
+        // whose batch and result arrays fit beside what else is reserved
+        Slot& sl = sv->slots[si];
+        size_t n = take.size();
+        BatchSizes z;
+        tp_status st = TP_E_BUDGET;
+        while (n > 0) {
+            std::vector<Request*> part(take.begin(), take.begin() + n);
+            z = batch_sizes(sv, part);
+            if (reserve(e, z.total + z.results) == TP_OK) {
+                release(e, z.results);   // the result arrays reserve their own share below
+                st = TP_OK;
+                break;
+            }
+            n /= 2;
+        }
+        std::unique_lock<std::mutex> lk(sv->mu);
+        if (st != TP_OK) {
+            // nothing fits now: wait for a running batch or lane, else fail the oldest
+            const bool others = sv->inflight > 0 || !sv->launched.empty();
+            for (auto it = take.rbegin(); it != take.rend(); ++it) sv->queue.push_front(*it);
+            sl.busy = false;
+            if (others) {
+                ++sv->stats.budget_waits;
+                const uint64_t c0 = sv->completions;
+                sv->cv.wait_for(lk, std::chrono::milliseconds(200), [&] { return sv->completions != c0; });
+            } else {
+                Request* r = sv->queue.front();
+                sv->queue.pop_front();
+                if (!r->t_start) r->t_start = now_ns();
+                finish(sv, r, TP_E_BUDGET, tp_last_error(), nullptr);
+            }
+            sv->cv.notify_all();
+            continue;
+        }
+        for (size_t i = n; i < take.size(); ++i) sv->queue.insert(sv->queue.begin() + (long)(i - n), take[i]);
+        take.resize(n);
+        const int64_t t0 = now_ns();
+        for (Request* r : take)
+            if (!r->t_start) r->t_start = t0;
+        sl.reqs = take;
+        sl.reserved = z.total;
+        const uint32_t peak = (uint32_t)(sv->inflight + (int)n);
+        if (peak > sv->stats.inflight_peak) sv->stats.inflight_peak = peak;
+        lk.unlock();
+        st = launch_slot(sv, sl, z);
+        lk.lock();
+        if (st != TP_OK) {
+            const std::string msg = tp_last_error();
+            cudaStreamSynchronize(sl.st);
+            for (size_t i = 0; i < sl.reqs.size(); ++i) {
+                if (i < sl.res.size() && sl.res[i]) tp_result_free(sl.res[i]);
+                finish(sv, sl.reqs[i], st, msg, nullptr);
+            }
+            slot_release(sv, sl);
+            sl.reqs.clear();
+            sl.res.clear();
+            sl.busy = false;
+            sv->cv.notify_all();
+            continue;
+        }
+        sv->launched.push_back(si);
+        sv->cv.notify_all();
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->dispatcher_done = true;
+    sv->cv.notify_all();
+}
+
+void completer(tp_server* sv) {
+    cudaSetDevice(sv->e->device);
+    for (;;) {
+        int si;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv.wait(lk, [&] { return !sv->launched.empty() || sv->dispatcher_done; });
+            if (sv->launched.empty()) return;
+            si = sv->launched.front();
+        }
+        Slot& sl = sv->slots[si];
+        const cudaError_t ce = cudaEventSynchronize(sl.ev);
+        const size_t n = sl.reqs.size();
+        const unsigned char* hs = sl.h_stage + sl.status_off;
+        const uint32_t batch_err = ce == cudaSuccess ? *(const uint32_t*)(hs + 16 * n) : 0;
+        std::vector<tp_status> sts(n, TP_OK);
+        std::vector<std::string> msgs(n);
+        for (size_t i = 0; i < n; ++i) {
+            tp_result* r = sl.res[i];
+            if (ce != cudaSuccess) {
+                sts[i] = fail(TP_E_CUDA, "batched launch: %s", cudaGetErrorString(ce));
+            } else {
+                const uint32_t err = batch_err | *(const uint32_t*)(hs + 8 * n + 8 * i);
+                sts[i] = map_err_word(err);
+            }
+            if (sts[i]) {
+                msgs[i] = tp_last_error();
+                tp_result_free(r);
+                sl.res[i] = nullptr;
+            } else {
+                r->n_groups = ((const uint64_t*)hs)[i];
+                r->stream = nullptr;   // its memory may be freed on the engine's stream
+            }
+        }
+        slot_release(sv, sl);
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (size_t i = 0; i < n; ++i) finish(sv, sl.reqs[i], sts[i], msgs[i], sl.res[i]);
+        sl.reqs.clear();
+        sl.res.clear();
+        sl.busy = false;
+        sv->launched.pop_front();
+        sv->cv.notify_all();
+    }
+}
+
+void server_free(tp_server* sv) {
+    if (!sv) return;
+    cudaSetDevice(sv->e->device);
+    for (Lane& l : sv->lanes) {
+        if (l.compute) cudaStreamSynchronize(l.compute);
+        if (l.copy) cudaStreamSynchronize(l.copy);
+        if (l.spill) cudaStreamSynchronize(l.spill);
+    }
+    for (Slot& sl : sv->slots)
+        if (sl.st) cudaStreamSynchronize(sl.st);
+    for (auto& kv : sv->reqs)   // finished but never collected
+        if (kv.second->result) tp_result_free(kv.second->result);
+    cache_evict_idle(sv->e, &sv->cache, 0);
+    for (Lane& l : sv->lanes) {
+        if (l.compute) cudaStreamDestroy(l.compute);
+        if (l.copy) cudaStreamDestroy(l.copy);
+        if (l.spill) cudaStreamDestroy(l.spill);
+        if (l.host_words) cudaFreeHost(l.host_words);
+    }
+    for (Slot& sl : sv->slots) {
+        if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.st) cudaStreamDestroy(sl.st);
+        if (sl.h_stage) cudaFreeHost(sl.h_stage);
+    }
+    delete sv;
 }
 
 }  // namespace
@@ -127,11 +535,13 @@ tp_status tp_server_start(tp_engine* e, int32_t workers, int32_t max_inflight, u
     if (!e || !out || workers < 1 || workers > 64 || max_inflight < 0)
         return fail(TP_E_INVALID, "tp_server_start: bad arguments");
     *out = nullptr;
-    std::unique_ptr<tp_server> sv(new (std::nothrow) tp_server());
+    std::unique_ptr<tp_server, void (*)(tp_server*)> sv(new (std::nothrow) tp_server(), server_free);
     if (!sv) return fail(TP_E_NOMEM, "tp_server_start: out of host memory");
     sv->e = e;
     sv->max_inflight = max_inflight ? max_inflight : workers;
     sv->cache_on = (flags & TP_SERVE_CACHE_DIM) != 0;
+    sv->batch_on = (flags & TP_SERVE_BATCH) != 0;
+    if (sv->batch_on && max_inflight) sv->max_batch = max_inflight;
     TP_TRY_CUDA(cudaSetDevice(e->device));
     sv->lanes.resize(workers);
     for (Lane& l : sv->lanes) {
@@ -139,6 +549,14 @@ tp_status tp_server_start(tp_engine* e, int32_t workers, int32_t max_inflight, u
         TP_TRY_CUDA(cudaStreamCreateWithFlags(&l.copy, cudaStreamNonBlocking));
         TP_TRY_CUDA(cudaStreamCreateWithFlags(&l.spill, cudaStreamNonBlocking));
         TP_TRY_CUDA(cudaHostAlloc((void**)&l.host_words, 4096, cudaHostAllocDefault));
+    }
+    if (sv->batch_on) {
+        for (Slot& sl : sv->slots) {
+            TP_TRY_CUDA(cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking));
+            TP_TRY_CUDA(cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming));
+        }
+        sv->dispatcher = std::thread(dispatcher, sv.get());
+        sv->completer = std::thread(completer, sv.get());
     }
     for (int i = 0; i < workers; ++i) sv->threads.emplace_back(worker, sv.get(), i);
     *out = sv.release();
@@ -151,6 +569,8 @@ tp_status tp_submit(tp_server* sv, tp_plan* p, tp_ticket* out) {
     std::unique_ptr<Request> r(new (std::nothrow) Request());
     if (!r) return fail(TP_E_NOMEM, "tp_submit: out of host memory");
     r->plan = p;
+    r->batchable = sv->batch_on && batch_check_plan(sv->e, p, 0) == TP_OK;
+    clear_error();
     r->t_submit = now_ns();
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->stopping) return fail(TP_E_INVALID, "tp_submit: server is stopping");
@@ -171,10 +591,16 @@ tp_status tp_wait(tp_server* sv, tp_ticket t, int64_t timeout_ns, tp_result** ou
     auto it = sv->reqs.find(t);
     if (it == sv->reqs.end()) return fail(TP_E_INVALID, "tp_wait: unknown ticket %llu", (unsigned long long)t);
     Request* r = it->second.get();
+    if (r->waited) return fail(TP_E_INVALID, "tp_wait: ticket %llu is being waited on by another thread",
+                               (unsigned long long)t);
+    r->waited = true;
     auto ready = [&] { return r->done; };
-    if (timeout_ns < 0) sv->cv.wait(lk, ready);
-    else if (!sv->cv.wait_for(lk, std::chrono::nanoseconds(timeout_ns), ready))
+    if (timeout_ns < 0) {
+        sv->cv.wait(lk, ready);
+    } else if (!sv->cv.wait_for(lk, std::chrono::nanoseconds(timeout_ns), ready)) {
+        r->waited = false;
         return fail(TP_E_TIMEOUT, "tp_wait: ticket %llu not finished", (unsigned long long)t);
+    }
     if (times) {
         times[0] = r->t_submit;
         times[1] = r->t_start;
@@ -183,7 +609,7 @@ tp_status tp_wait(tp_server* sv, tp_ticket t, int64_t timeout_ns, tp_result** ou
     const tp_status st = r->status;
     if (st == TP_OK) *out = r->result;
     else fail(st, "%s", r->message.c_str());
-    sv->reqs.erase(it);
+    sv->reqs.erase(sv->reqs.find(t));
     return st;
 }
 
@@ -206,22 +632,9 @@ void tp_server_stop(tp_server* sv) {
     }
     sv->cv.notify_all();
     for (auto& th : sv->threads) th.join();
-    cudaSetDevice(sv->e->device);
-    for (Lane& l : sv->lanes) {
-        cudaStreamSynchronize(l.compute);
-        cudaStreamSynchronize(l.copy);
-        cudaStreamSynchronize(l.spill);
-    }
-    for (auto& kv : sv->reqs)   // finished but never collected
-        if (kv.second->result) tp_result_free(kv.second->result);
-    cache_evict_idle(sv->e, &sv->cache, 0);
-    for (Lane& l : sv->lanes) {
-        cudaStreamDestroy(l.compute);
-        cudaStreamDestroy(l.copy);
-        cudaStreamDestroy(l.spill);
-        cudaFreeHost(l.host_words);
-    }
-    delete sv;
+    if (sv->dispatcher.joinable()) sv->dispatcher.join();
+    if (sv->completer.joinable()) sv->completer.join();
+    server_free(sv);
 }
 
 }  // extern "C"

@@ -10,11 +10,12 @@
 //    only the filter column; every other column is read from global memory
 //    for the surviving rows only, so a 1%-selective scan moves little more
 //    than the filter column.
-//  * Run folding.  For a fixed j the 32 lanes of a warp hold 32 consecutive
-//    rows.  Consecutive rows with the same key (an order key repeated over its
-//    line items) are folded into the first lane of the run with a segmented
-//    suffix sum over shuffles, so a run costs one table update, not one per
-//    row.
+//  * Warp aggregation.  Lanes whose rows carry the same group key find each
+//    other with __match_any_sync; the lowest lane of each set adds the
+//    others' count and terms (shuffles) and updates the table once, so a key
+//    repeated within a warp's rows costs one table update, not one per row.
+//  * Bulk occupancy counting.  New slots of a hashed table are counted per
+//    lane and added to the table's counter once per CTA.
 //  * 64-bit updates.  When column bounds prove every sum stays in int64
 //    (FAST), counts and sums are fire-and-forget 64-bit global reductions on
 //    the low words; the high words are filled in by sign extension when the
@@ -22,9 +23,14 @@
 //    carry propagation.
 #include <algorithm>
 
+#include "agg_warp.cuh"
 #include "pipeline.cuh"
 
 namespace tpk {
+
+// bytes in front of the ring: the CTA's claimed-slot counter (keeps the
+// stages 128-byte aligned)
+constexpr uint32_t GLOBAL_RING_OFFSET = 128;
 
 // Filter, probe and pack the 64-bit group keys of this lane's rows; returns
 // the mask of surviving rows (no early exit: callers use warp shuffles).
@@ -101,92 +107,62 @@ __device__ __forceinline__ void eval_terms64(const QueryDev& q, const StageLayou
 template <int NS, bool FAST>
 __device__ __forceinline__ void consume_global(const QueryDev& q, const StageLayout& L, const AggTable& tab,
                                                const unsigned char* stage, uint64_t row0, uint32_t r0,
-                                               bool fold) {
+                                               uint32_t& claims) {
     uint64_t key[ST_RPL];
     const uint32_t pm = eval_keys64(q, L, stage, row0, r0, key);
     if (__ballot_sync(0xffffffffu, pm != 0) == 0) return;   // warp-uniform exit
-    const int lane = threadIdx.x & 31;
-    if constexpr (FAST) {
-        int64_t t[NS > 0 ? NS : 1][ST_RPL];
+    int64_t t[NS > 0 ? NS : 1][ST_RPL];
+    I128 tm[NS > 0 ? NS : 1][ST_RPL];
 #pragma unroll
-        for (int s = 0; s < NS; ++s)
-            if (s < q.n_sum) eval_terms64(q, L, s, stage, row0, r0, pm, t[s]);
-#pragma unroll
-        for (int j = 0; j < ST_RPL; ++j) {
-            const bool valid = (pm >> j) & 1u;
-            bool head = valid;
-            uint64_t cnt = 1;
-            if (fold) {
-                // runs of equal keys over consecutive lanes fold into their first lane
-                const uint64_t k = key[j];
-                const uint64_t kp = __shfl_up_sync(0xffffffffu, k, 1);
-                const bool vp = __shfl_up_sync(0xffffffffu, (int)valid, 1) != 0;
-                const uint64_t kn = __shfl_down_sync(0xffffffffu, k, 1);
-                const bool vn = __shfl_down_sync(0xffffffffu, (int)valid, 1) != 0;
-                head = valid && (lane == 0 || !vp || kp != k);
-                const bool brk = valid && (lane == 31 || !vn || kn != k);
-                const uint32_t ends = __ballot_sync(0xffffffffu, brk);
-                const int end = __ffs(ends & (0xffffffffu << lane)) - 1;   // last lane of this lane's run
-                cnt = (uint64_t)(end - lane + 1);
-#pragma unroll
-                for (int s = 0; s < NS; ++s) {
-                    if (s >= q.n_sum) break;
-                    int64_t x = t[s][j];
-#pragma unroll
-                    for (int off = 1; off < 32; off <<= 1) {
-                        const int64_t y = __shfl_down_sync(0xffffffffu, x, off);
-                        if (lane + off <= end) x += y;
-                    }
-                    t[s][j] = x;
-                }
-            }
-            if (!head) continue;
-            uint64_t* p = agg_slot_any(tab, key[j], q.err);
-            if (!p) continue;
-            atomicAdd((unsigned long long*)(p + 1), (unsigned long long)cnt);
-#pragma unroll
-            for (int s = 0; s < NS; ++s)
-                if (s < q.n_sum) atomicAdd((unsigned long long*)(p + 2 + 2 * s), (unsigned long long)t[s][j]);
-        }
-    } else {
-        uint64_t* slot[ST_RPL];
-#pragma unroll
-        for (int j = 0; j < ST_RPL; ++j) {
-            slot[j] = nullptr;
-            if (!((pm >> j) & 1u)) continue;
-            slot[j] = agg_slot_any(tab, key[j], q.err);
-            if (slot[j]) atomicAdd((unsigned long long*)(slot[j] + 1), 1ull);
-        }
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            if (s >= q.n_sum) break;
+    for (int s = 0; s < NS; ++s) {
+        if (s >= q.n_sum) break;
+        if constexpr (FAST) {
+            eval_terms64(q, L, s, stage, row0, r0, pm, t[s]);
+        } else {
             int64_t a[ST_RPL];
             load_rows(col_src(L, SL_SA + s, q.sa[s], stage, row0), r0, pm, a);
-            I128 tm[ST_RPL];
             if (q.skind[s] == S_MUL_SUB) {
                 int64_t b[ST_RPL];
                 load_rows(col_src(L, SL_SB + s, q.sb[s], stage, row0), r0, pm, b);
 #pragma unroll
-                for (int j = 0; j < ST_RPL; ++j) tm[j] = mul_sub(a[j], q.sk[s], b[j]);
+                for (int j = 0; j < ST_RPL; ++j) tm[s][j] = mul_sub(a[j], q.sk[s], b[j]);
             } else {
 #pragma unroll
-                for (int j = 0; j < ST_RPL; ++j) tm[j] = i128_from_i64(a[j]);
+                for (int j = 0; j < ST_RPL; ++j) tm[s][j] = i128_from_i64(a[j]);
             }
-#pragma unroll
-            for (int j = 0; j < ST_RPL; ++j)
-                if (slot[j]) atomic_add_i128(slot[j] + 2 + 2 * s, slot[j] + 3 + 2 * s, tm[j]);
         }
+    }
+#pragma unroll
+    for (int j = 0; j < ST_RPL; ++j) {
+        int64_t tj[NS > 0 ? NS : 1];
+        I128 tmj[NS > 0 ? NS : 1];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if constexpr (FAST) tj[s] = t[s][j];
+            else tmj[s] = tm[s][j];
+        }
+        agg_warp_row<NS, FAST>(tab, q.err, q.n_sum, (pm >> j) & 1u, key[j], tj, tmj, claims);
     }
 }
 
 template <int NS, bool FAST>
 __global__ void __launch_bounds__(ST_THREADS, ST_CTAS)
     k_agg_global_staged(const __grid_constant__ QueryDev q, const __grid_constant__ StageLayout L, uint64_t n,
-                        const __grid_constant__ AggTable tab, int fold) {
+                        const __grid_constant__ AggTable tab) {
     extern __shared__ __align__(128) unsigned char smem[];
-    run_pipeline(q, L, n, smem, [&](const unsigned char* stage, uint64_t row0, uint32_t r0) {
-        consume_global<NS, FAST>(q, L, tab, stage, row0, r0, fold != 0);
+    // the CTA's claimed-slot count sits in front of the ring
+    unsigned int* cta_claims = (unsigned int*)smem;
+    if (threadIdx.x == 0) *cta_claims = 0;
+    uint32_t claims = 0;
+    run_pipeline(q, L, n, smem + GLOBAL_RING_OFFSET, [&](const unsigned char* stage, uint64_t row0, uint32_t r0) {
+        consume_global<NS, FAST>(q, L, tab, stage, row0, r0, claims);
     });
+    if (threadIdx.x >= 32) {
+        const uint32_t w = __reduce_add_sync(0xffffffffu, claims);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(cta_claims, w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) agg_add_claims(tab, q.err, *cta_claims);
 }
 
 // ------------------------------------------------------------------- host
@@ -237,7 +213,7 @@ bool staged_layout_global(const QueryDev& q, bool stage_all, StageLayout* L) {
         cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
         return false;
     const uint64_t budget = std::min<uint64_t>((uint64_t)optin, (uint64_t)per_sm / ST_CTAS - 1024);
-    const uint64_t fixed = 2 * ST_MAX_STAGES * sizeof(uint64_t);
+    const uint64_t fixed = GLOBAL_RING_OFFSET + 2 * ST_MAX_STAGES * sizeof(uint64_t);
     int stages = (int)((budget - fixed) / L->stage_bytes);
     if (stages > ST_MAX_STAGES) stages = ST_MAX_STAGES;
     if (stages < 2) return false;
@@ -249,31 +225,31 @@ bool staged_layout_global(const QueryDev& q, bool stage_all, StageLayout* L) {
 
 template <int NS, bool FAST>
 static cudaError_t launch_global_t(const QueryDev& q, const StageLayout& L, uint64_t n, const AggTable& t,
-                                   bool fold, int grid, cudaStream_t st) {
+                                   int grid, cudaStream_t st) {
     auto fn = k_agg_global_staged<NS, FAST>;
     cudaError_t e = ensure_smem_limit((const void*)fn, (int)L.smem_bytes);
     if (e != cudaSuccess) return e;
-    fn<<<grid, ST_THREADS, L.smem_bytes, st>>>(q, L, n, t, fold ? 1 : 0);
+    fn<<<grid, ST_THREADS, L.smem_bytes, st>>>(q, L, n, t);
     return cudaGetLastError();
 }
 
 cudaError_t launch_agg_global_staged(const QueryDev& q, const StageLayout& L, uint64_t n, const AggTable& t,
-                                     bool fast, bool fold, int num_sms, cudaStream_t st) {
+                                     bool fast, int num_sms, cudaStream_t st) {
     if (n < (uint64_t)ST_TILE) return cudaSuccess;
     const uint64_t tiles = n / ST_TILE;
     const uint64_t slots = (uint64_t)num_sms * ST_CTAS;
     const int grid = (int)(tiles < slots ? tiles : slots);
     const int ns = q.n_sum;
     if (fast) {
-        if (ns <= 1) return launch_global_t<1, true>(q, L, n, t, fold, grid, st);
-        if (ns <= 2) return launch_global_t<2, true>(q, L, n, t, fold, grid, st);
-        if (ns <= 4) return launch_global_t<4, true>(q, L, n, t, fold, grid, st);
-        return launch_global_t<8, true>(q, L, n, t, fold, grid, st);
+        if (ns <= 1) return launch_global_t<1, true>(q, L, n, t, grid, st);
+        if (ns <= 2) return launch_global_t<2, true>(q, L, n, t, grid, st);
+        if (ns <= 4) return launch_global_t<4, true>(q, L, n, t, grid, st);
+        return launch_global_t<8, true>(q, L, n, t, grid, st);
     }
-    if (ns <= 1) return launch_global_t<1, false>(q, L, n, t, fold, grid, st);
-    if (ns <= 2) return launch_global_t<2, false>(q, L, n, t, fold, grid, st);
-    if (ns <= 4) return launch_global_t<4, false>(q, L, n, t, fold, grid, st);
-    return launch_global_t<8, false>(q, L, n, t, fold, grid, st);
+    if (ns <= 1) return launch_global_t<1, false>(q, L, n, t, grid, st);
+    if (ns <= 2) return launch_global_t<2, false>(q, L, n, t, grid, st);
+    if (ns <= 4) return launch_global_t<4, false>(q, L, n, t, grid, st);
+    return launch_global_t<8, false>(q, L, n, t, grid, st);
 }
 
 }  // namespace tpk

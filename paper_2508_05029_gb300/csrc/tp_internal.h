@@ -107,6 +107,7 @@ struct tp_engine {
     cudaStream_t copy = nullptr;
     cudaStream_t spill = nullptr;
     bool own_compute = false;
+    uint32_t copy_flags = 0;     // TP_COPY_* (tp_set_copy_options)
     std::mutex exec_mu;          // one execution at a time on the engine streams
     std::mutex obj_mu;
     // statistics
@@ -144,6 +145,7 @@ struct tp_table {
 
 struct tp_plan {
     tp_engine* eng = nullptr;
+    uint64_t serial = 0;    // unique per plan created in this process
     tp_plan_desc d{};
     int n_sum = 0;
     int sum_of_agg[8];      // sum slot of each aggregate, -1 for COUNT
@@ -257,9 +259,10 @@ std::string dense_shape(const tpk::QueryDev& q, const tpk::StageLayout& L, bool 
 // Host-to-device copy of column c of batch b (t's page layout) on `st`: a
 // full-width column lands at full + row_off * size, a narrow one at
 // enc + row_off * size (enc is then widened by widen_batch).  Adds the bytes
-// to the engine's counter.
+// to the engine's counter.  With stage, the bytes are first copied on the
+// host to *stage (page-locked, advanced past them) and sent from there.
 tp_status copy_batch_column(tp_engine* e, const tp_table* t, const Batch& b, int c, void* full, void* enc,
-                            uint64_t row_off, cudaStream_t st);
+                            uint64_t row_off, cudaStream_t st, uint8_t** stage = nullptr);
 // Widens batch b's narrow columns among cols (enc -> full, the offsets of
 // copy_batch_column) with one launch on st; rows (0: b.rows) lets one launch
 // cover consecutive batches that share b's encoding.
@@ -273,6 +276,46 @@ int frame_width(int64_t lo, int64_t hi, int full);
 bool has_narrow(const tp_table* t);
 // The widest narrow encoding of column c over t's batches (0: never narrow).
 int narrow_width_max(const tp_table* t, int c);
+// ----------------------------------------------------- batched execution
+// Sizes and choices of one query inside a persistent batched launch (the
+// queue kernel of batch.cu): its join table, dense accumulators and output
+// arrays, probe tile, and whether a tile accumulates in a 32-bit
+// shared-memory table first (mode[s]: 1 low word, 2 low + carry word).
+constexpr uint64_t BATCH_BUILD_CHUNK = 65536;   // dimension rows per build task
+struct BatchPrep {
+    uint64_t join_cap = 0, join_bytes = 0, acc_bytes = 0, out_bytes = 0, tile = 0, range = 0;
+    uint64_t build_items = 0, probe_items = 0;
+    bool join = false, key64 = false, smem = false, fast = false, direct = false;
+    tpk::TermBounds bounds[tpk::MAX_SUM] = {};
+    int8_t mode[tpk::MAX_SUM] = {};
+    uint32_t smem_bytes = 0;
+};
+// Whether plan p (index i, for the message) can run in a batched launch:
+// device-resident tables, at most one join, no fan-out, at most 20 key bits.
+tp_status batch_check_plan(const tp_engine* e, const tp_plan* p, int i);
+// Sizes and choices of p: join load factor lf_tuned (0: the plan's), probe
+// tiles of rows_per_warp rows per warp, agg TP_AGG_GLOBAL to keep tiles out
+// of shared memory.
+void batch_prep(const tp_engine* e, const tp_plan* p, float lf_tuned, uint32_t rows_per_warp, int agg, BatchPrep* x);
+// The device descriptor of p in a batch: its join table at join_slots (side
+// cell at side), accumulators at acc, outputs in out; shape id 0.
+void batch_query_desc(const tp_plan* p, const BatchPrep& x, void* join_slots, uint32_t* side, uint64_t* acc,
+                      uint32_t* err, const tpk::OutDev& out, tpk::BatchQuery* B);
+// Appends query qi's tasks of one kind (BI_BUILD chunks, BI_PROBE tiles or
+// its BI_FINAL) to items.
+void batch_items(const tp_plan* p, const BatchPrep& x, uint32_t qi, int kind, std::vector<tpk::BatchItem>* items);
+// The shape struct `name` of a batched query for the run-time compiled queue
+// kernel, and that kernel's source for shapes JS_0 .. JS_{n-1}.
+std::string batch_shape(const tp_plan* p, const tpk::BatchQuery& B, const BatchPrep& x, const std::string& name);
+std::string batch_kernel_source(const std::vector<std::string>& shapes);
+// Resident CTAs of the queue kernel (run-time compiled, or the ahead-of-time
+// one for nullptr) with smem_bytes of dynamic shared memory.
+int batch_kernel_grid(const void* jit_kernel_or_null, uint32_t smem_bytes, int num_sms);
+// Result arrays for `cap` groups of p (reserved and allocated on st); od gets
+// their device addresses, its group count pointing at n_groups_dev.
+tp_status alloc_result(tp_engine* e, tp_plan* p, uint64_t cap, tp_result** out, tpk::OutDev* od,
+                       unsigned long long* n_groups_dev, cudaStream_t st);
+
 // device memory (stream-ordered allocator on the compute stream)
 tp_status dev_alloc(tp_engine* e, void** p, uint64_t bytes, cudaStream_t st);
 void dev_free(tp_engine* e, void* p, cudaStream_t st);

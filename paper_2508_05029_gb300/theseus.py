@@ -32,6 +32,8 @@ TP_FLAG_NO_DIRECT_AGG, TP_FLAG_RAW_PAGES = 32, 64
 TP_SIDE_FACT, TP_SIDE_DIM = 0, 1
 TP_LIP_AUTO, TP_LIP_OFF, TP_LIP_ON = 0, 1, 2
 TP_AGG_SUM, TP_AGG_SUM_MUL_SUB, TP_AGG_COUNT, TP_AGG_AVG = 0, 1, 2, 3
+TP_SERVE_CACHE_DIM, TP_SERVE_BATCH = 1, 2
+TP_COPY_PINNED_PER_BATCH = 1
 
 _NP_TYPE = {np.dtype(np.int32): TP_I32, np.dtype(np.int64): TP_I64, np.dtype(np.uint8): TP_U8}
 _TYPE_NP = {v: k for k, v in _NP_TYPE.items()}
@@ -110,7 +112,7 @@ class tp_stats(ctypes.Structure):
 class tp_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
                 ("budget_waits", ctypes.c_uint64), ("cache_hits", ctypes.c_uint64), ("cache_misses", ctypes.c_uint64),
-                ("cache_evictions", ctypes.c_uint64), ("inflight_peak", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("cache_evictions", ctypes.c_uint64), ("inflight_peak", ctypes.c_uint32), ("batches", ctypes.c_uint32)]
 
 
 _vp, _u64, _i64, _i32, _u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
@@ -128,6 +130,7 @@ SIGNATURES = {
     "tp_pages_free": (_u32, [_vp]),
     "tp_set_device_budget": (_i32, [_vp, _u64]),
     "tp_budget_query": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "tp_set_copy_options": (_i32, [_vp, _i32, _u32]),
     "tp_table_create": (_i32, [_vp, ctypes.POINTER(tp_table_desc), _PP]),
     "tp_table_append": (_i32, [_vp, _PP, _u64]),
     "tp_table_place": (_i32, [_vp, _i32]),
@@ -236,6 +239,10 @@ class Engine:
 
     def set_budget(self, nbytes: int):
         _check(self.lib.tp_set_device_budget(self.h, nbytes))
+
+    def set_copy_options(self, prefetch_depth: int, pinned_per_batch: bool = False):
+        _check(self.lib.tp_set_copy_options(self.h, prefetch_depth,
+                                            TP_COPY_PINNED_PER_BATCH if pinned_per_batch else 0))
 
     def page_alloc(self) -> int:
         p = _u32()
@@ -409,10 +416,11 @@ class Batch:
 class Server:
     """Request server (tp_server_*): submit plans, wait for results."""
 
-    def __init__(self, eng: Engine, workers=4, max_inflight=0, cache_dims=True):
+    def __init__(self, eng: Engine, workers=4, max_inflight=0, cache_dims=True, batch=False):
         self.eng = eng
         h = ctypes.c_void_p()
-        _check(eng.lib.tp_server_start(eng.h, workers, max_inflight, 1 if cache_dims else 0, ctypes.byref(h)))
+        flags = (TP_SERVE_CACHE_DIM if cache_dims else 0) | (TP_SERVE_BATCH if batch else 0)
+        _check(eng.lib.tp_server_start(eng.h, workers, max_inflight, flags, ctypes.byref(h)))
         self.h = h
         self._aggs = {}
 
@@ -428,7 +436,8 @@ class Server:
         times = (ctypes.c_int64 * 3)()
         ns = -1 if timeout_s is None else int(timeout_s * 1e9)
         code = self.eng.lib.tp_wait(self.h, ticket, ns, ctypes.byref(r), times)
-        if code != TP_TIMEOUT_CODE:
+        aggs = []
+        if code not in (TP_TIMEOUT_CODE, TP_E_INVALID):   # the ticket is consumed
             aggs = self._aggs.pop(ticket, [])
         _check(code)
         return Result(self.eng, r, aggs), (times[0], times[1], times[2])
@@ -436,7 +445,7 @@ class Server:
     def stats(self) -> dict:
         s = tp_server_stats()
         _check(self.eng.lib.tp_server_stats_get(self.h, ctypes.byref(s)))
-        return {k: getattr(s, k) for k, _ in tp_server_stats._fields_ if k != "pad"}
+        return {k: getattr(s, k) for k, _ in tp_server_stats._fields_}
 
     def stop(self):
         if self.h:

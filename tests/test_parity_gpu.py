@@ -101,6 +101,23 @@ def test_prefetch_depths_agree(depth):
         e.close()
 
 
+@pytest.mark.parametrize("depth,pinned", [(0, False), (3, False), (2, True), (0, True)])
+def test_copy_options_agree(depth, pinned):
+    """Prefetch depth and the per-batch pinned buffers (the no-pool ablation)
+    set after the engine starts change nothing in the result."""
+    wl = W.config1(n_fact=700_001, n_dim=5_000)
+    ref = oracle.run(wl)
+    e = T.Engine(page_bytes=1 << 20, n_pages=256, batch_rows=50_000)
+    try:
+        e.set_copy_options(depth, pinned)
+        with run_gpu(e, wl.fact, wl.dim, wl.query, placement=T.TP_HOST_PAGES) as res:
+            assert_matches_oracle(res, ref, wl.query["aggs"])
+        with pytest.raises(T.TPError):
+            e.set_copy_options(-1)
+    finally:
+        e.close()
+
+
 def test_int64_keys_and_sparse_pk(eng):
     dim = W.config3_dim(n_dim=100_000)
     fact = W.config3_fact(0, 1_000_003, n_dim=100_000)
