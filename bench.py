@@ -63,11 +63,13 @@ def parse_args():
     ap.add_argument("--n-fact", type=int, default=60_000_000)
     ap.add_argument("--n-dim", type=int, default=2_000_000)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-sample-rows", type=int, default=6_000_000)
+    ap.add_argument("--cpu-sample-rows", type=int, default=20_000_000)
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary queries")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="fact-size scale of the 256-query batched and served mixes (1.0 = the full ~394M rows)")
-    ap.add_argument("--serve-seconds", type=float, default=1.5, help="arrival window per served rate")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window per served rate")
+    ap.add_argument("--serve-requests", type=int, default=20_000,
+                    help="requests per served rate at most (and of the closed-loop throughput run)")
     ap.add_argument("--no-patterns", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--no-outofcore", action="store_true", help="skip the out-of-core (paged, spilling) query")
     ap.add_argument("--ooc-fact", type=int, default=600_000_000, help="out-of-core fact rows")
@@ -180,6 +182,41 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def roofline_obj(alg_bytes: float, ms: float, peak: float, bound="hbm", peak_kind="measured", **extra):
+    """Algorithmic bytes over a duration against a peak (GB/s)."""
+    gbs = alg_bytes / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    d = {"bound": bound, "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak if peak else None,
+         "peak_kind": peak_kind, "alg_bytes": int(alg_bytes), "ms": ms}
+    d.update(extra)
+    return d
+
+
+def time_plan(torch, stream, eng, p, reps=5, warm=2):
+    """(ms per query, the aggregate kernels' ms per query, groups, joined rows)
+    of plan p: CUDA events on the engine's stream around reps executions; the
+    kernel time comes from the engine's event-timed aggregate launches."""
+    for _ in range(warm):
+        p.execute().free()
+    torch.cuda.synchronize()
+    s0 = eng.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = None
+    for i in range(reps):
+        r = p.execute()
+        if i + 1 < reps:
+            r.free()
+        else:
+            res = r
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s1 = eng.stats()
+    groups, joined = res.n_groups, int(res.counts().sum()) if res.n_groups else 0
+    res.free()
+    ms = e0.elapsed_time(e1) / reps
+    return ms, (s1["agg_kernel_ms"] - s0["agg_kernel_ms"]) / reps, groups, joined
+
+
 def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel]:
@@ -224,45 +261,104 @@ def link_peak_gbs(dev, pinned_bytes=2 << 30, page=64 << 20):
 
 
 # ------------------------------------------------------------- CPU oracle leg
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def cpu_oracle(fact, dim, query, sample_rows):
+    """The oracle as it stands, one thread, on the first sample_rows fact rows."""
     import oracle
     sub = {k: v[:sample_rows] for k, v in fact.items()}
     t0 = time.perf_counter()
-    oracle.run_query(sub, dim, query)
+    res = oracle.run_query(sub, dim, query)
     dt = time.perf_counter() - t0
-    return sample_rows / dt, dt
+    return sample_rows / dt, dt, res
+
+
+def _merge_partials(parts):
+    """Groups of several oracle results over disjoint row ranges, merged by
+    key: counts and exact sums add; AVG is the merged sum over the merged
+    count, rounded once (Python's int -> float conversion rounds correctly)."""
+    acc = {}
+    for r in parts:
+        for g in range(r.n_groups):
+            k = int(r.keys[g])
+            c, sums = acc.get(k, (0, [0] * len(r.aggs)))
+            acc[k] = (c + int(r.counts[g]), [sums[a] + r.sum_int(g, a) for a in range(len(r.aggs))])
+    keys = sorted(acc)
+    return keys, [acc[k][0] for k in keys], [acc[k][1] for k in keys]
+
+
+def cpu_oracle_threads(fact, dim, query, sample_rows, threads):
+    """The oracle on `threads` row ranges of the sample at once (the C calls
+    release the GIL, so they run on separate cores), each with its own copy of
+    the dimension lookup, and the partial groups merged by key.  Returns
+    (rows/s, seconds, merged groups)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    cut = np.linspace(0, sample_rows, threads + 1).astype(np.int64)
+    parts = [{k: v[cut[i]:cut[i + 1]] for k, v in fact.items()} for i in range(threads)]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(lambda f: oracle.run_query(f, dim, query), parts))
+    merged = _merge_partials(res)
+    dt = time.perf_counter() - t0
+    return sample_rows / dt, dt, merged
+
+
+def cpu_baseline_obj(fact, dim, query, sample_rows, threads=None):
+    """cpu_baseline object: the oracle on every host core (row ranges, merged)
+    and on one core, both on the same bounded sample; the merged groups are
+    checked against the one-core result."""
+    threads = threads or host_cores()
+    r1, s1, ref = cpu_oracle(fact, dim, query, sample_rows)
+    rn, sn, merged = cpu_oracle_threads(fact, dim, query, sample_rows, threads)
+    same = merged[0] == [int(k) for k in ref.keys] and merged[1] == [int(c) for c in ref.counts] and \
+        all(merged[2][g][a] == ref.sum_int(g, a) for g in range(ref.n_groups) for a in range(len(ref.aggs)))
+    return {"value": rn, "unit": "fact rows/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {sample_rows} fact rows with the full dimension, {threads} row ranges on "
+                      f"{threads} threads merged by key ({sn:.2f} s); merge equals the one-core result: {same}",
+            "single_core": {"value": r1, "unit": "fact rows/s", "cores": 1, "seconds": s1}}
 
 
 def reference_arm(args, world, rank):
-    """The CPU oracle as it stands on this host: each step evaluates a bounded
-    row sample of the same workload."""
+    """The CPU oracle as it stands on this host's cores: each step evaluates a
+    bounded row sample of the same workload as row ranges on every core,
+    merged by key (one core's rate is reported beside it)."""
     if rank != 0:
         return
     from datagen import workloads as W
     q = W.q_lowcard()
+    threads = host_cores()
     # size each step's row sample so warm-up plus timed steps take ~2 minutes
-    probe_rows = 200_000
+    probe_rows = 400_000
     fact, dim = W.config2_tables(n_fact=probe_rows, n_dim=args.n_dim)
-    _, secs = cpu_oracle(fact, dim, q, probe_rows)
+    _, secs, _ = cpu_oracle_threads(fact, dim, q, probe_rows, threads)
     per_row = secs / probe_rows
     budget_s = 120.0 / max(1, args.warmup + args.steps)
-    sample = int(min(args.cpu_sample_rows, args.n_fact, max(probe_rows, budget_s / per_row)))
+    sample = int(min(args.n_fact, max(probe_rows, budget_s / per_row)))
     fact, dim = W.config2_tables(n_fact=sample, n_dim=args.n_dim)
     rates = []
     for i in range(args.warmup + args.steps):
-        r, _ = cpu_oracle(fact, dim, q, sample)
+        r, _, _ = cpu_oracle_threads(fact, dim, q, sample, threads)
         if i >= args.warmup:
             rates.append(r)
-    t_step = sample / statistics.mean(rates)
+    r1, s1, _ = cpu_oracle(fact, dim, q, min(sample, 4_000_000))
     value = statistics.mean(rates)
+    t_step = sample / value
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "fact rows/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "fact_rows": args.n_fact, "dim_rows": args.n_dim,
                    "step_sample_rows": sample},
-        "cpu_baseline": {"value": value, "unit": "fact rows/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {sample} fact rows of the workload, full dimension"},
+        "cpu_baseline": {"value": value, "unit": "fact rows/s", "cores": threads, "kind": "oracle",
+                         "sample": f"first {sample} fact rows of the workload, full dimension, {threads} row "
+                                   f"ranges on {threads} threads merged by key",
+                         "single_core": {"value": r1, "unit": "fact rows/s", "cores": 1, "seconds": s1}},
         "e2e": {"value": value, "unit": "fact rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -346,7 +442,7 @@ def host_ram_bytes() -> int:
         return 0
 
 
-def outofcore_measure(T, W, torch, dev, n_fact, n_dim, budgets_gb, steps, link, lip_budget=0.0):
+def outofcore_measure(T, W, torch, dev, n_fact, n_dim, budgets_gb, steps, link, lip_budget=0.0, with_cpu=True):
     """The out-of-core star query: fact and build tables in 64 MiB pinned pages,
     streamed through the device; the join runs radix-partitioned 64 ways and
     spills the partitions the budget cannot hold.  Rows are scaled down (and
@@ -402,13 +498,50 @@ def outofcore_measure(T, W, torch, dev, n_fact, n_dim, budgets_gb, steps, link, 
             "count_check": total == passing[0],
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "alg_gbs": alg / sec / 1e9, "link_frac_alg": alg / sec / 1e9 / link,
-            "link_frac_moved": (h2d + d2h) / sec / 1e9 / link}
+            "link_frac_moved": (h2d + d2h) / sec / 1e9 / link,
+            "phase_ms": {k: (s1[f"part_{k}_ms"] - s0[f"part_{k}_ms"]) / steps for k in ("build", "stream", "spilled")},
+            "roofline": roofline_obj(alg, sec * 1e3, link, bound="link", peak_kind="measured in this run",
+                                     note="fact (38 B/row) and build (12 B/row) bytes at native width over "
+                                          "the host-to-device link peak")}
         p.destroy()
+    # ablations at the largest budget (every partition resident): no
+    # prefetch (Section 3.3.3), and per-batch pinned buffers instead of the
+    # page pool (Section 3.4)
+    b = max(budgets_gb)
+    eng.set_budget(int(b * 2**30))
+    for name, depth, pinned in (("prefetch_0", 0, False), ("pinned_per_batch", 2, True)):
+        eng.set_copy_options(depth, pinned)
+        p = eng.plan(ft, dt, W.q_lowcard(), join_partitions=64)
+        p.execute().free()
+        s0 = eng.stats()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(steps):
+            with p.execute() as r:
+                total = int(r.counts().sum())
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t1) / steps
+        s1 = eng.stats()
+        out.setdefault("ablations", {})[name] = {
+            "budget_gb": b, "ms_per_step": sec * 1e3, "count_check": total == passing[0],
+            "h2d_bytes_per_step": int((s1["h2d_bytes"] - s0["h2d_bytes"]) / steps),
+            "slowdown_vs_default": sec * 1e3 / out[f"budget_{b:g}GB"]["ms_per_step"]}
+        p.destroy()
+    eng.set_copy_options(2, False)
+    out["ablations"]["managed_memory"] = ("not built: the join table in managed memory, paged between host and "
+                                          "device by the driver instead of partitioned and spilled")
     if lip_budget > 0:
         out["lookahead"] = lookahead_measure(T, W, torch, eng, ft, dt, nf, lip_budget, steps)
     ft.destroy()
     dt.destroy()
     eng.close()
+    if with_cpu:
+        # the oracle on the same query at 1/100 of the rows (fact and build
+        # side in the same ratio), regenerated from the counter-based generator
+        sf, sd = max(1, n_fact // 100), max(1, n_dim // 100)
+        cb = cpu_baseline_obj(W.config3_fact(0, sf, n_dim=sd), W.config3_dim(sd), W.q_lowcard(), sf)
+        cb["sample"] = f"scaled workload: {sf} fact rows over a {sd}-row build side; " + cb["sample"]
+        out["cpu_baseline"] = cb
     return out
 
 
@@ -444,7 +577,7 @@ def lookahead_measure(T, W, torch, eng, ft, dt, nf, budget_gb, steps):
     return out
 
 
-def star_measure(T, W, torch, dev, stream, eng, fact, dt, n_fact, n_xdim=32_000_000, reps=5):
+def star_measure(T, W, torch, dev, stream, eng, fact, dt, n_fact, peak, n_xdim=32_000_000, reps=5):
     """The 60M-row star query joined to a second dimension of n_xdim rows with
     unique sparse int64 keys (a hashed table of 1 GB, far over L2), whose
     predicate admits 3 of 25 attribute values (12%); grouped by the two fact
@@ -479,9 +612,13 @@ def star_measure(T, W, torch, dev, stream, eng, fact, dt, n_fact, n_xdim=32_000_
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         s1 = eng.stats()
+        # fact: the star query's 34 B plus fk2 (8 B); first dimension 8 B per
+        # row; second dimension pk, attr, band (13 B per row) for its build
+        alg = n_fact * (BYTES_PER_FACT_ROW + 8) + int(dt.rows) * BYTES_PER_DIM_ROW + n_xdim * 13
         out[name] = {"ms_per_step": ms, "fact_rows_per_s": n_fact / (ms / 1e3), "groups": int(seen[name][0].size),
                      "compiled_kernel": s1["jit_launches"] > s0["jit_launches"],
-                     "filters_built": int(s1["lip_filters"] - s0["lip_filters"]) // reps}
+                     "filters_built": int(s1["lip_filters"] - s0["lip_filters"]) // reps,
+                     "roofline": roofline_obj(alg, ms, peak, note="whole query, both builds included")}
         p.destroy()
     out["lookahead_speedup"] = out["lookahead_off"]["ms_per_step"] / out["lookahead_on"]["ms_per_step"]
     out["results_equal"] = bool(np.array_equal(seen["lookahead_off"][0], seen["lookahead_on"][0]) and
@@ -491,11 +628,60 @@ def star_measure(T, W, torch, dev, stream, eng, fact, dt, n_fact, n_xdim=32_000_
     return out
 
 
-def served_measure(T, W, torch, dev, rates, seconds, scale, fact_pages=False):
-    """Open-loop Poisson arrivals; latency = scheduled arrival -> result on host.
-    fact_pages: every request streams its fact table from pinned pages."""
+def _open_loop(srv, plans, rate, n, rng):
+    """Poisson arrivals at `rate` for n requests; latency = scheduled arrival
+    -> result on the host.  Returns (latencies ms, wall s)."""
     import threading
     import time as _t
+    gaps = rng.exponential(1.0 / rate, n)
+    order = rng.integers(0, len(plans), n)
+    sched, tickets, lat = [], [], []
+
+    def collect():
+        for i in range(n):
+            while len(tickets) <= i:
+                _t.sleep(0.0001)
+            res, times = srv.wait(tickets[i], timeout_s=600)
+            res.free()
+            lat.append((times[2] - sched[i]) / 1e6)
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = _t.monotonic_ns()
+    at = t0
+    for i in range(n):
+        at += int(gaps[i] * 1e9)
+        while _t.monotonic_ns() < at:
+            pass
+        sched.append(at)
+        tickets.append(srv.submit(plans[order[i]]))
+    th.join()
+    return lat, (_t.monotonic_ns() - t0) / 1e9
+
+
+def _closed_loop(srv, plans, n, rng):
+    """n requests submitted back to back (at most 512 outstanding): the
+    server's maximum throughput in queries/s."""
+    import time as _t
+    order = rng.integers(0, len(plans), n)
+    pending = []
+    t0 = _t.monotonic()
+    for i in range(n):
+        if len(pending) >= 512:
+            srv.wait(pending.pop(0), timeout_s=600)[0].free()
+        pending.append(srv.submit(plans[order[i]]))
+    for t in pending:
+        srv.wait(t, timeout_s=600)[0].free()
+    return n / (_t.monotonic() - t0)
+
+
+def served_measure(T, W, torch, dev, rates, seconds, max_requests, scale, fact_pages=False, closed_n=0):
+    """The served pattern against plain per-query execution on the same
+    arrival traces.  served: continuous batching (every request a batched
+    launch can run joins the next launch; the rest run on 8 lanes with cached
+    join tables); plain: one request at a time, no cache.  Open-loop Poisson
+    arrivals per rate for `seconds` or `max_requests`; then a closed loop of
+    closed_n requests for the maximum throughput.  fact_pages: every request
+    streams its fact table from pinned pages (lanes only)."""
     page = 16 << 20
     n_pages = 0
     if fact_pages:
@@ -505,48 +691,170 @@ def served_measure(T, W, torch, dev, rates, seconds, scale, fact_pages=False):
     tabs, plans, _, _ = _mix_tables(eng, T, W, torch, dev, 256, scale, n_dims=64, fact_pages=fact_pages)
     for p in plans:     # warm: plan history, selectivity samples
         p.execute().free()
-    out = {}
-    rng = np.random.default_rng(0x7E5E0005)
+    out = {"requests_per_rate": f"min({max_requests}, {seconds:g} s x rate)"}
     for mode in ("served", "plain"):
+        srv = T.Server(eng, workers=8, cache_dims=True, batch=True) if mode == "served" else \
+            T.Server(eng, workers=1, max_inflight=1, cache_dims=False)
+        for p in plans:   # warm: run-time compiled shapes, cached join tables
+            srv.wait(srv.submit(p), timeout_s=600)[0].free()
+        rng = np.random.default_rng(0x7E5E0005)
         for rate in rates:
-            srv = T.Server(eng, workers=8, cache_dims=True) if mode == "served" else \
-                T.Server(eng, workers=1, max_inflight=1, cache_dims=False)
-            n = max(8, int(rate * seconds))
-            gaps = rng.exponential(1.0 / rate, n)
-            order = rng.integers(0, len(plans), n)
-            sched, tickets = [], []
-            lat = []
-
-            def collect():
-                for i in range(n):
-                    while len(tickets) <= i:
-                        _t.sleep(0.0002)
-                    res, times = srv.wait(tickets[i], timeout_s=600)
-                    res.free()
-                    lat.append((times[2] - sched[i]) / 1e6)
-            th = threading.Thread(target=collect)
-            th.start()
-            t0 = _t.monotonic_ns()
-            at = t0
-            for i in range(n):
-                at += int(gaps[i] * 1e9)
-                while _t.monotonic_ns() < at:
-                    pass
-                sched.append(at)
-                tickets.append(srv.submit(plans[order[i]]))
-            th.join()
-            wall = (_t.monotonic_ns() - t0) / 1e9
-            st = srv.stats()
-            srv.stop()
+            st0 = srv.stats()
+            n = max(8, min(max_requests, int(rate * seconds)))
+            lat, wall = _open_loop(srv, plans, rate, n, rng)
+            st1 = srv.stats()
             lat.sort()
-            out[f"{mode}@{rate}"] = {"requests": n, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(len(lat) * 0.99) - 1],
-                                     "qps": n / wall, "cache_hits": st["cache_hits"],
-                                     "inflight_peak": st["inflight_peak"]}
+            launches = st1["batches"] - st0["batches"]
+            out[f"{mode}@{rate}"] = {
+                "requests": n, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[max(0, int(len(lat) * 0.99) - 1)],
+                "qps": n / wall, "failed": st1["failed"] - st0["failed"],
+                "batched_launches": launches,
+                "requests_per_launch": (n / launches) if launches else None}
+        if closed_n:
+            out[f"{mode}@max"] = {"requests": closed_n, "qps": _closed_loop(srv, plans, closed_n, rng)}
+        srv.stop()
     for p in plans:
         p.destroy()
     for t in tabs:
         t.destroy()
     eng.close()
+    return out
+
+
+def e2e_measure(T, W, torch, dev, stream, local, world, fact, dim, n_fact, n_dim, steps, link, flags):
+    """The headline query through tp_execute from 64 MiB pinned host pages,
+    every host-to-device copy and the read-back of every result array inside
+    the timed region.  flags = TP_FLAG_RAW_PAGES keeps every column at full
+    width in the pages (no frame-of-reference narrowing)."""
+    page = 64 << 20
+    need = (n_fact * (BYTES_PER_FACT_ROW + 8) + n_dim * BYTES_PER_DIM_ROW) * 1.1
+    n_pages = int(need // page) + 16
+    eng2 = T.Engine(page_bytes=page, n_pages=n_pages, batch_rows=4 << 20, prefetch_depth=2,
+                    compute_stream=stream.cuda_stream, cuda_device=local, flags=flags)
+    ft2 = eng2.table_from_numpy(fact, placement=T.TP_HOST_PAGES)
+    dt2 = eng2.table_from_numpy(dim, placement=T.TP_HOST_PAGES)
+    p3 = eng2.plan(ft2, dt2, W.q_lowcard())
+
+    def e2e_step():
+        with p3.execute() as r:
+            r.keys(), r.counts()
+            for a in range(4):
+                if a != 2:
+                    r.sum_words(a)
+            r.avg(3)
+
+    for _ in range(2):
+        e2e_step()
+    s0 = eng2.stats()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, world)
+    s1 = eng2.stats()
+    h2d_gbs = (s1["h2d_bytes"] - s0["h2d_bytes"]) / t_e2e / 1e9
+    out = {"value": world * n_fact * steps / t_e2e, "unit": "fact rows/s",
+           "link_peak_gbs": link, "link_frac": h2d_gbs / link,
+           "h2d_bytes_per_step": (s1["h2d_bytes"] - s0["h2d_bytes"]) // steps,
+           "d2h_bytes_per_step": (s1["d2h_bytes"] - s0["d2h_bytes"]) // steps,
+           "h2d_gbs": h2d_gbs,
+           "source": "pinned page pool, 64 MiB pages, prefetch depth 2" +
+                     (", full-width columns" if flags & T.TP_FLAG_RAW_PAGES else ", narrow (frame-of-reference) columns")}
+    p3.destroy()
+    ft2.destroy()
+    dt2.destroy()
+    eng2.close()
+    return out
+
+
+def config1_measure(T, W, torch, dev, stream, peak, with_cpu=True, reps=50):
+    """Config 1: 1M fact rows, 10k-row dimension, device-resident, one batch.
+    At 34 MB of input (about 5 us of HBM traffic) the query is bound by
+    launch and synchronisation latency, not by bandwidth; the roofline
+    fraction is reported all the same."""
+    wl = W.config1()
+    eng1 = T.Engine(compute_stream=stream.cuda_stream, flags=T.TP_FLAG_TIME_KERNELS)
+    ft = eng1.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in wl.fact.items()})
+    dt = eng1.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in wl.dim.items()})
+    torch.cuda.synchronize()
+    p = eng1.plan(ft, dt, wl.query)
+    ms, kms, groups, _ = time_plan(torch, stream, eng1, p, reps=reps, warm=5)
+    n = wl.n_fact
+    alg = BYTES_PER_FACT_ROW * n + BYTES_PER_DIM_ROW * wl.n_dim
+    out = {"fact_rows": n, "dim_rows": wl.n_dim, "groups": groups, "ms_per_step": ms,
+           "fact_rows_per_s": n / (ms / 1e3), "kernel_ms": kms,
+           "roofline": roofline_obj(BYTES_PER_FACT_ROW * n, kms, peak, note="latency-bound: launch and "
+                                    "synchronisation dominate a 34 MB input"),
+           "query_roofline": roofline_obj(alg, ms, peak)}
+    if with_cpu:
+        out["cpu_baseline"] = cpu_baseline_obj(wl.fact, wl.dim, wl.query, n)
+    p.destroy()
+    ft.destroy()
+    dt.destroy()
+    eng1.close()
+    return out
+
+
+def highcard_measure(T, W, torch, dev, stream, eng, ft, dt, fact, dim, n_fact, peak):
+    """Config 2b (1%-selective date range, group by order key: about 600k
+    groups), 2b' (the same at ~98%: 15M groups) with the direct-addressed
+    table the dense order keys allow, and 2b' with the hashed table (sparse
+    keys' general case, TP_FLAG_NO_DIRECT_AGG).  Algorithmic bytes: the filter
+    column for every row, fk/orderkey/price/disc (28 B) for every passing row,
+    and 32 B per output group (key, count, 128-bit sum)."""
+    lo = W.config2_range_lo()
+    engh = T.Engine(compute_stream=stream.cuda_stream, flags=T.TP_FLAG_TIME_KERNELS | T.TP_FLAG_NO_DIRECT_AGG)
+    fth = engh.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in fact.items()})
+    dth = engh.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in dim.items()})
+    torch.cuda.synchronize()
+    out = {}
+    for name, q, e, f_t, d_t in (
+            ("star-60M-highcard-1pct", W.q_highcard(lo, lo + W.RANGE_1PCT), eng, ft, dt),
+            ("star-60M-highcard-98pct", W.q_highcard(0, W.CUTOFF_98), eng, ft, dt),
+            ("star-60M-highcard-98pct-hashed", W.q_highcard(0, W.CUTOFF_98), engh, fth, dth)):
+        p = e.plan(f_t, d_t, q)
+        ms, kms, groups, joined = time_plan(torch, stream, e, p, reps=5)
+        alg = 4 * n_fact + 28 * joined + 32 * groups
+        out[name] = {"ms_per_step": ms, "fact_rows_per_s": n_fact / (ms / 1e3), "groups": groups,
+                     "passing_rows": joined, "kernel_ms": kms,
+                     "table": "hashed" if e is engh else "auto (direct-addressed when the key range is dense)",
+                     "roofline": roofline_obj(alg, kms, peak, note="aggregate kernels (selection and gather, "
+                                              "or the staged scan) per query"),
+                     "query_roofline": roofline_obj(alg, ms, peak)}
+        p.destroy()
+    fth.destroy()
+    dth.destroy()
+    engh.close()
+    return out
+
+
+def hashed_join_measure(T, W, torch, dev, stream, n_fact, n_dim, peak, reps=10):
+    """Config 2a with unique sparse int64 dimension keys: the join needs the
+    open-addressing table (2M keys at load factor 0.5: 4M 16-byte slots) and
+    the foreign key is int64, so 38 B per fact row and 12 B per dimension
+    row."""
+    fact, dim = W.config2_tables(n_fact=n_fact, n_dim=n_dim, sparse_keys=True)
+    fact.pop("okey")
+    e = T.Engine(compute_stream=stream.cuda_stream, flags=T.TP_FLAG_TIME_KERNELS)
+    ft = e.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in fact.items()})
+    dt = e.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in dim.items()})
+    torch.cuda.synchronize()
+    p = e.plan(ft, dt, W.q_lowcard())
+    s0 = e.stats()
+    ms, kms, groups, _ = time_plan(torch, stream, e, p, reps=reps, warm=3)
+    s1 = e.stats()
+    per_row = BYTES_PER_FACT_ROW + 4
+    out = {"fact_rows": n_fact, "dim_rows": n_dim, "groups": groups, "ms_per_step": ms,
+           "fact_rows_per_s": n_fact / (ms / 1e3), "kernel_ms": kms,
+           "compiled_kernel": s1["jit_launches"] > s0["jit_launches"],
+           "roofline": roofline_obj(per_row * n_fact, kms, peak, note="fused filter/probe/aggregate kernel"),
+           "query_roofline": roofline_obj(per_row * n_fact + 12 * n_dim, ms, peak)}
+    p.destroy()
+    ft.destroy()
+    dt.destroy()
+    e.close()
     return out
 
 
@@ -609,25 +917,10 @@ def main():
 
     extra = {}
     if not args.no_extra:
-        for name, q in (("star-60M-highcard-1pct", W.q_highcard(W.config2_range_lo(), W.config2_range_lo() + W.RANGE_1PCT)),
-                        ("star-60M-highcard-98pct", W.q_highcard(0, W.CUTOFF_98))):
-            p2 = eng.plan(ft, dt, q)
-            for _ in range(2):
-                p2.execute().free()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            reps = 3
-            for _ in range(reps):
-                r = p2.execute()
-                groups = r.n_groups
-                r.free()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / reps
-            extra[name] = {"ms_per_step": ms, "fact_rows_per_s": n_fact / (ms / 1e3), "groups": groups}
-            p2.destroy()
-        extra["star-60M-two-dims"] = star_measure(T, W, torch, dev, stream, eng, fact, dt, n_fact)
+        extra["star-1M-lowcard"] = config1_measure(T, W, torch, dev, stream, peak, args.cpu_sample_rows > 0)
+        extra.update(highcard_measure(T, W, torch, dev, stream, eng, ft, dt, fact, dim, n_fact, peak))
+        extra["star-60M-two-dims"] = star_measure(T, W, torch, dev, stream, eng, fact, dt, n_fact, peak)
+        extra["star-60M-lowcard-hashed"] = hashed_join_measure(T, W, torch, dev, stream, n_fact, n_dim, peak)
     plan.destroy()
     ft.destroy()
     dt.destroy()
@@ -637,46 +930,11 @@ def main():
     # ---- end to end: host pages -> device -> result arrays on the host
     e2e = None
     if args.e2e_steps > 0:
-        page = 64 << 20
-        need = (n_fact * (BYTES_PER_FACT_ROW + 8) + n_dim * BYTES_PER_DIM_ROW) * 1.1
-        n_pages = int(need // page) + 16
-        eng2 = T.Engine(page_bytes=page, n_pages=n_pages, batch_rows=4 << 20, prefetch_depth=2,
-                        compute_stream=stream.cuda_stream, cuda_device=local)
-        ft2 = eng2.table_from_numpy(fact, placement=T.TP_HOST_PAGES)
-        dt2 = eng2.table_from_numpy(dim, placement=T.TP_HOST_PAGES)
-        p3 = eng2.plan(ft2, dt2, W.q_lowcard())
-
-        def e2e_step():
-            with p3.execute() as r:
-                r.keys(), r.counts()
-                for a in range(4):
-                    if a != 2:
-                        r.sum_words(a)
-                r.avg(3)
-
-        for _ in range(2):
-            e2e_step()
-        s0 = eng2.stats()
-        barrier(world)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        torch.cuda.synchronize()
-        t_e2e = max_over_ranks(time.perf_counter() - t0, world)
-        s1 = eng2.stats()
         link = link_peak_gbs(dev)
-        h2d_gbs = (s1["h2d_bytes"] - s0["h2d_bytes"]) / t_e2e / 1e9
-        e2e = {"value": world * n_fact * args.e2e_steps / t_e2e, "unit": "fact rows/s",
-               "link_peak_gbs": link, "link_frac": h2d_gbs / link,
-               "h2d_bytes_per_step": (s1["h2d_bytes"] - s0["h2d_bytes"]) // args.e2e_steps,
-               "d2h_bytes_per_step": (s1["d2h_bytes"] - s0["d2h_bytes"]) // args.e2e_steps,
-               "h2d_gbs": (s1["h2d_bytes"] - s0["h2d_bytes"]) / t_e2e / 1e9,
-               "source": "pinned page pool, 64 MiB pages, prefetch depth 2"}
-        p3.destroy()
-        ft2.destroy()
-        dt2.destroy()
-        eng2.close()
+        e2e = e2e_measure(T, W, torch, dev, stream, local, world, fact, dim, n_fact, n_dim, args.e2e_steps, link, 0)
+        raw = e2e_measure(T, W, torch, dev, stream, local, world, fact, dim, n_fact, n_dim, args.e2e_steps, link,
+                          T.TP_FLAG_RAW_PAGES)
+        e2e["raw_pages"] = {k: raw[k] for k in ("value", "unit", "link_frac", "h2d_bytes_per_step", "h2d_gbs")}
 
     if not args.no_outofcore and rank == 0:
         link_ooc = e2e["link_peak_gbs"] if e2e else link_peak_gbs(dev)
@@ -688,17 +946,15 @@ def main():
     if not args.no_patterns:
         peak_hbm, _ = measured_peaks()
         patterns = {"batched": batched_measure(T, W, torch, dev, stream, args.batch_scale, peak_hbm),
-                    "served": served_measure(T, W, torch, dev, (200, 500, 1000, 2000), args.serve_seconds,
-                                             args.batch_scale),
-                    "served_streamed": served_measure(T, W, torch, dev, (200, 500, 1000, 2000),
-                                                      args.serve_seconds, args.batch_scale, fact_pages=True)}
+                    "served": served_measure(T, W, torch, dev, (200, 500, 1000, 2000, 5000), args.serve_seconds,
+                                             args.serve_requests, args.batch_scale, closed_n=args.serve_requests),
+                    "served_streamed": served_measure(T, W, torch, dev, (200, 1000, 2000),
+                                                      args.serve_seconds, args.serve_requests // 4,
+                                                      args.batch_scale, fact_pages=True)}
 
     cpu = None
     if rank == 0 and world == 1 and args.cpu_sample_rows > 0:
-        sample = min(args.cpu_sample_rows, n_fact)
-        rate, secs = cpu_oracle(fact, dim, W.q_lowcard(), sample)
-        cpu = {"value": rate, "unit": "fact rows/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {sample} fact rows of the workload with the full dimension ({secs:.1f} s)"}
+        cpu = cpu_baseline_obj(fact, dim, W.q_lowcard(), min(args.cpu_sample_rows, n_fact))
 
     if rank == 0:
         kernel = "tpj_dense" if st1["jit_launches"] > st0["jit_launches"] else "k_agg_shared_staged"

@@ -103,14 +103,18 @@ def config1(n_fact=1_000_000, n_dim=10_000, seed=SEEDS[1], cutoff=CUTOFF_98) -> 
     return Workload("star-1M-lowcard", fact, dim, q_lowcard(cutoff))
 
 
-def config2_tables(n_fact=60_000_000, n_dim=2_000_000, n_okey=None, seed=SEEDS[2], zipf_s=0.8):
+def config2_tables(n_fact=60_000_000, n_dim=2_000_000, n_okey=None, seed=SEEDS[2], zipf_s=0.8,
+                   sparse_keys=False):
     """60M fact rows (+ int64 orderkey, 4 adjacent rows per key, keys a seeded
     permutation), 2M-row dimension with unique scrambled int32 pk, fk Zipf(s)
-    over the dimension rows with the hot rows scattered."""
+    over the dimension rows with the hot rows scattered.  sparse_keys: the
+    dimension keys are unique sparse int64 values (raw SplitMix64 outputs) and
+    fk is int64, so the join needs a hashed table."""
     if n_okey is None:
         n_okey = max(1, n_fact // 4)
     dim = dict(
-        pk=fill(seed, _s(_DIM, S_PK), PERM, np.int32, n_dim, b=n_dim),
+        pk=fill(seed, _s(_DIM, S_PK), RAW64, np.int64, n_dim) if sparse_keys else
+        fill(seed, _s(_DIM, S_PK), PERM, np.int32, n_dim, b=n_dim),
         attr=uniform(seed, _s(_DIM, S_ATTR), np.int32, n_dim, 0, 24),
     )
     cdf = zipf_cdf(zipf_s, n_dim)

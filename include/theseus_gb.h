@@ -546,7 +546,8 @@ tp_status tp_debug_fail_next_alloc(tp_engine* eng, int32_t n);
  *
  * It runs the same filter -> join -> low-cardinality group-by as tp_execute,
  * on caller-owned device columns and into caller-owned device outputs, and
- * allocates nothing: no engine, no cudaMalloc/cudaFree, no host heap.  Its
+ * allocates nothing: no engine, no cudaMalloc/cudaFree, no host heap (the
+ * driver places the array and the kernels at the first call; see below).  Its
  * scratch (join hash table, per-group accumulators, status words) is one
  * fixed device array of 8,945,920 bytes inside this library, which every GPU
  * that loads the library holds until the process exits.
@@ -571,11 +572,14 @@ tp_status tp_debug_fail_next_alloc(tp_engine* eng, int32_t n);
  * default load factor 0.5.  Other errors as tp_execute (TP_E_DUP_KEY,
  * TP_E_RANGE, TP_E_CUDA).
  *
- * The first call on a device looks up the scratch array's device address
- * with that device current; make that first call before any stream capture.
- * Every call reuses the array and clears what must start at zero; calls
- * whose GPU work overlaps (other streams or host threads) race on it, so the
- * caller must serialise them.
+ * The first call on a device sets it up, with that device current: it looks
+ * up the scratch array's device address and loads the kernels the call uses,
+ * which is when the CUDA driver places the array and the kernel code in
+ * device memory.  Make that first call at start-up -- before handing the rest
+ * of device memory to another allocator, and before any stream capture;
+ * later calls allocate no device memory.  Every call reuses the array and
+ * clears what must start at zero; calls whose GPU work overlaps (other
+ * streams or host threads) race on it, so the caller must serialise them.
  */
 tp_status tp_execute_noalloc(const tp_plan_desc* d, const void* const* fact_cols, const int32_t* fact_types,
                              int32_t n_fact_cols, uint64_t n_fact, const void* const* dim_cols,

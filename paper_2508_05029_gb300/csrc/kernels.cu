@@ -589,4 +589,15 @@ cudaError_t launch_minmax(const DevCol& c, uint64_t n, long long* out, int num_s
     return cudaGetLastError();
 }
 
+cudaError_t load_plain_kernels() {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k_build);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_final_dense);
+#define TPK_LOAD(K) \
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_agg_shared<K>);
+    TPK_LOAD(0) TPK_LOAD(1) TPK_LOAD(2) TPK_LOAD(3) TPK_LOAD(4) TPK_LOAD(5) TPK_LOAD(6) TPK_LOAD(7) TPK_LOAD(8)
+#undef TPK_LOAD
+    return e;
+}
+
 }  // namespace tpk

@@ -329,6 +329,10 @@ cudaError_t launch_agg_global(const QueryDev& q, uint64_t n, const AggTable& t, 
 // out by column bounds); their high words are the sign extension of the low.
 cudaError_t launch_final_dense(const uint64_t* gacc, uint32_t key_bits, int n_sum, const OutDev& o,
                                cudaStream_t st, bool lo_only = false);
+// Loads the build, plain shared-memory aggregation and dense finalisation
+// kernels on the current device now (with lazy module loading the first
+// launch would load them, placing their code in device memory then).
+cudaError_t load_plain_kernels();
 
 // Staged shared-memory aggregation.  staged_layout_shared() fills *L for the
 // query (false when the staged kernel cannot run it: misaligned columns,

@@ -12,12 +12,16 @@
 // accumulators, status words) lives in one fixed, file-scope device array.
 //
 // The array is NOLOC_SCRATCH_BYTES long and is held by every GPU that loads
-// this library until the process exits.  Its device address is looked up
-// once per device, on the first call made with that device current; make
-// that first call before any stream capture.  Every call shares the array
-// and starts by clearing what must start at zero; calls whose work overlaps
-// on the GPU (different streams, or different host threads) race on it and
-// must be serialised by the caller.
+// this library until the process exits.  The first call made with a device
+// current sets that device up: it looks up the array's device address and
+// loads the kernels the call launches, which is when the CUDA driver places
+// the array and the kernel code in device memory (with lazy module loading
+// this would otherwise happen at a later first launch).  So make that first
+// call at start-up, before handing the rest of device memory to another
+// allocator, and before any stream capture; later calls allocate nothing.
+// Every call shares the array and starts by clearing what must start at
+// zero; calls whose work overlaps on the GPU (different streams, or different
+// host threads) race on it and must be serialised by the caller.
 #include <cmath>
 #include <mutex>
 
@@ -52,6 +56,11 @@ tp_status noloc_scratch(void** out) {
         if (e != cudaSuccess || p == nullptr) {
             cudaGetLastError();
             return tp::fail(TP_E_CUDA, "tp_execute_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        }
+        e = tpk::load_plain_kernels();
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return tp::fail(TP_E_CUDA, "tp_execute_noalloc: loading its kernels failed: %s", cudaGetErrorString(e));
         }
         g_noloc_addr[dev] = p;
     }

@@ -67,3 +67,14 @@ def test_star_dimension_and_foreign_keys():
     # row ranges regenerate independently, and another dimension index gives other keys
     assert np.array_equal(W.star_dim(50_000, seed)["pk"][:100], d["pk"][:100])
     assert not np.isin(W.star_dim(1_000, seed, j=1)["pk"], d["pk"]).any()
+
+
+def test_sparse_star_keys_unique_and_joinable():
+    """The sparse-key star tables: int64 dimension keys, all distinct and far
+    from dense, and every foreign key one of them."""
+    fact, dim = W.config2_tables(n_fact=50_000, n_dim=4_000, sparse_keys=True)
+    pk = dim["pk"]
+    assert pk.dtype == np.int64 and fact["fk"].dtype == np.int64
+    assert np.unique(pk).size == pk.size
+    assert int(pk.max()) - int(pk.min()) > 1000 * pk.size
+    assert np.isin(fact["fk"], pk).all()

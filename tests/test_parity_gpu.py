@@ -61,8 +61,10 @@ def test_config1_ragged(eng, n_fact, n_dim):
 
 @pytest.mark.parametrize("which,strategy", [("a", T.TP_AGG_AUTO), ("a", T.TP_AGG_GLOBAL),
                                             ("b", T.TP_AGG_AUTO), ("b2", T.TP_AGG_AUTO)])
-def test_config2_small(eng, which, strategy):
-    wl = W.config2(which, n_fact=3_000_017, n_dim=300_000)
+@pytest.mark.parametrize("sparse", [False, True])
+def test_config2_small(eng, which, strategy, sparse):
+    """sparse: unique sparse int64 dimension keys, so the join is hashed."""
+    wl = W.config2(which, n_fact=3_000_017, n_dim=300_000, sparse_keys=sparse)
     check(eng, wl.fact, wl.dim, wl.query, agg_strategy=strategy)
 
 

@@ -8,7 +8,9 @@ ABI twice in a row (the second call reuses the array the first one left
 behind) and requires the same groups, counts, exact sums and averages as the
 regular entry point, tp_execute, on the same device columns.  It runs last so
 that a failure here leaves every other test already run, and it passes both
-alone in a fresh process and after the rest of the suite.
+alone in a fresh process and after the rest of the suite.  After a first call
+has set the device up, further calls of other shapes leave the device's free
+memory unchanged.
 """
 import ctypes
 
@@ -154,3 +156,69 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(T.TPError) as e:
         _noalloc(torch, fact, small, q, stream)
     assert e.value.status == "invalid" and "12 bits" in str(e.value)
+
+
+def _call_into(torch, lib, fact, dim, query, stream, out):
+    """One tp_execute_noalloc call into preallocated outputs (no tensor is
+    created here); returns the group count."""
+    fn, dn = list(fact), list(dim)
+    ft = [fact[k] for k in fn]
+    dt = [dim[k] for k in dn]
+    d = _desc(query, fn, dn)
+    tmap = {torch.int32: T.TP_I32, torch.int64: T.TP_I64, torch.uint8: T.TP_U8}
+    fcols = (ctypes.c_void_p * len(ft))(*[x.data_ptr() for x in ft])
+    ftyp = (ctypes.c_int32 * len(ft))(*[tmap[x.dtype] for x in ft])
+    dcols = (ctypes.c_void_p * max(1, len(dt)))(*[x.data_ptr() for x in dt])
+    dtyp = (ctypes.c_int32 * max(1, len(dt)))(*[tmap[x.dtype] for x in dt])
+    sp = (ctypes.c_void_p * 8)(*[out["sums"][a].data_ptr() if a < len(query["aggs"]) and
+                                 query["aggs"][a][0] != "count" else None for a in range(8)])
+    ap = (ctypes.c_void_p * 8)(*[out["avgs"][a].data_ptr() if a < len(query["aggs"]) and
+                                 query["aggs"][a][0] == "avg" else None for a in range(8)])
+    ng = ctypes.c_uint64(0)
+    rc = lib.tp_execute_noalloc(ctypes.byref(d), fcols, ftyp, len(ft), ft[0].numel(), dcols, dtyp, len(dt),
+                                dt[0].numel() if dt else 0, out["keys"].data_ptr(), out["counts"].data_ptr(), sp,
+                                ap, ctypes.byref(ng), stream.cuda_stream)
+    if rc != T.TP_OK:
+        raise T.TPError(rc, T.last_error())
+    return ng.value
+
+
+def test_noalloc_calls_after_the_first_leave_free_memory_unchanged():
+    """A warm-up call sets the device up; then a small key, a 12-bit key, a
+    query without a join and one with a 64-bit key join run without changing
+    the device's free memory (cudaMemGetInfo)."""
+    torch = pytest.importorskip("torch")
+    from paper_2508_05029_gb300 import build
+    build.build()
+    lib = T.load()
+    dev = torch.device("cuda", 0)
+    f1, d1 = W.config2_tables(n_fact=400_003, n_dim=100_000)
+    f3, d3 = W.config3_fact(0, 300_001, n_dim=50_000), W.config3_dim(50_000)
+    fact1 = {k: torch.from_numpy(v).to(dev) for k, v in f1.items()}
+    dim1 = {k: torch.from_numpy(v).to(dev) for k, v in d1.items()}
+    fact3 = {k: torch.from_numpy(v).to(dev) for k, v in f3.items()}
+    dim3 = {k: torch.from_numpy(v).to(dev) for k, v in d3.items()}
+    q_small = W.q_lowcard()                                            # 8-bit key
+    q_wide = dict(W.q_lowcard(attr_bits=9), group=[("fact", "flag", 2), ("fact", "status", 1),
+                                                   ("dim", "attr", 9)])  # 12-bit key
+    q_nojoin = dict(filter=dict(col="date", lo=0, hi=1500), join=None,
+                    group=[("fact", "flag", 2), ("fact", "status", 1)],
+                    aggs=[("sum", "price"), ("count",), ("avg", "qty")])
+    cap = 1 << 12
+    out = dict(keys=torch.empty(cap, dtype=torch.int64, device=dev),
+               counts=torch.empty(cap, dtype=torch.int64, device=dev),
+               sums=[torch.empty(cap * 2, dtype=torch.int64, device=dev) for _ in range(8)],
+               avgs=[torch.empty(cap, dtype=torch.float64, device=dev) for _ in range(8)])
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    _call_into(torch, lib, fact1, dim1, q_small, stream, out)          # sets the device up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    groups = []
+    for fact, dim, q in ((fact1, dim1, q_small), (fact1, dim1, q_wide), (fact1, dim1, q_nojoin),
+                         (fact3, dim3, q_small), (fact1, dim1, q_wide)):
+        groups.append(_call_into(torch, lib, fact, dim, q, stream, out))
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info(dev)[0]
+    assert free1 == free0, (free0, free1)
+    assert groups[0] == groups[1] == groups[3] == groups[4] == 150 and groups[2] == 6
