@@ -404,11 +404,15 @@ void tp_batch_destroy(tp_batch* b);
 tp_status tp_debug_batch_stall(tp_batch* b, int32_t query, uint64_t wait_ns);
 
 /*
- * Autotuner: for every query class present in plans[0..n), tries the join
- * load factor (0.5, 0.7), the rows per warp of a probe tile (128, 256, 512,
- * 1024) and shared-memory versus device-memory aggregation, one knob at a
- * time, timing the batch of that class's queries; writes the best choice per
- * class to tuning_path (text).  The plans' own results are unaffected.
+ * Autotuner: for every query class present in plans[0..n) (buckets of fact
+ * rows, group-key bits and dimension rows), tries the rows per warp of a
+ * probe tile (128, 256, 512, 1024), shared-memory versus device-memory
+ * aggregation and the join load factor (0.5, 0.7), one knob at a time.  Each
+ * candidate value is applied to every class in one batched launch of all n
+ * plans; the launch records, per query, the CTA time its tasks took, and a
+ * class keeps the value when its queries' time fell by 2% or more (best of
+ * three runs).  Writes the choice per class to tuning_path (text), which
+ * tp_batch_create reads.  The plans' own results are unaffected.
  */
 tp_status tp_autotune(tp_engine* eng, tp_plan* const* plans, int32_t n, const char* tuning_path);
 
@@ -427,9 +431,10 @@ tp_status tp_autotune(tp_engine* eng, tp_plan* const* plans, int32_t n, const ch
  * form the next launch, which starts at once on a second stream and overlaps
  * the running one on the device.  Each request has its own join table,
  * accumulators, error word and result: its result and its status are the
- * ones it gets alone.  The probe tasks are compiled at run time for every
- * plan shape the server has seen; the first request of a new shape waits for
- * that compilation.
+ * ones it gets alone.  A lone request on an idle GPU runs at once as a single
+ * query instead of waiting for company.  The probe tasks are compiled at run
+ * time for every plan shape the server has seen; the first batched launch
+ * after a new shape arrives waits for that compilation.
  *
  * Other requests (and every request without TP_SERVE_BATCH) run on `workers`
  * lanes, each a host thread with its own compute and copy streams, so their

@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(const BatchQuery* __res
     const uint64_t wait_ns = *wait;   // device word, so a captured graph can be given another limit
     __shared__ uint32_t cur;
     __shared__ int flag;
+    __shared__ uint64_t first_row;
     unsigned* build_done = ctr + 1;
     unsigned* probe_done = ctr + 1 + n_q;
     for (;;) {
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(const BatchQuery* __res
         if (i >= n_items) return;
         const BatchItem it = items[i];
         const BatchQuery& B = qs[it.q];
+        const uint64_t t_claim = B.task_ns ? batch_ns() : 0;
         if (it.kind == BI_BUILD) {
             for (uint64_t r = it.r0 + threadIdx.x; r < it.r1; r += blockDim.x) build_insert(B.b, r);
             __syncthreads();
@@ -162,9 +164,25 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch(const BatchQuery* __res
             }
         } else {
             if (!cta_wait_count(&probe_done[it.q], B.probe_items, wait_ns, err, &flag)) continue;
-            final_dense_block(B.acc, 1u << B.key_bits, B.q.n_sum, B.out, B.fast != 0);
+            // groups [r0, r1): count them, wait for the ranges before to publish
+            // where their rows end, publish this range's end, write the rows
+            const uint32_t G = 1u << B.key_bits;
+            const uint32_t g0 = (uint32_t)it.r0, g1 = (uint32_t)it.r1, k = g0 / FINAL_CHUNK;
+            const uint32_t cnt = dense_range_count(B.acc, g0, g1);
+            if (!cta_wait_count(B.final_done, k, wait_ns, err, &flag)) continue;
+            if (threadIdx.x == 0) {
+                const uint64_t first = k ? *(volatile unsigned long long*)B.final_end : 0ull;
+                first_row = first;
+                *(volatile unsigned long long*)B.final_end = first + cnt;
+                __threadfence();
+                atomicAdd(B.final_done, 1u);
+                if (g1 == G) *B.out.n_groups = first + cnt;
+            }
+            __syncthreads();
+            dense_range_emit(B.acc, G, g0, g1, B.q.n_sum, B.out, B.fast != 0, first_row);
         }
         __syncthreads();
+        if (B.task_ns && threadIdx.x == 0) atomicAdd(B.task_ns, (unsigned long long)(batch_ns() - t_claim));
     }
 }
 
@@ -270,6 +288,7 @@ struct tp_batch {
     unsigned* d_ctr = nullptr;
     uint32_t* d_err = nullptr;
     unsigned long long* d_groups = nullptr;
+    unsigned long long* d_task_ns = nullptr;   // per query: CTA nanoseconds of its tasks (last run)
     unsigned char* ff_base = nullptr;
     uint64_t ff_bytes = 0;
     unsigned char* zero_base = nullptr;
@@ -366,10 +385,12 @@ void batch_prep(const tp_engine* e, const tp_plan* p, float lf_tuned, uint32_t r
         for (int s = 0; s < tpk::MAX_SUM; ++s) x.mode[s] = 0;
     x.build_items = x.join ? (p->d.dim->rows + BATCH_BUILD_CHUNK - 1) / BATCH_BUILD_CHUNK : 0;
     x.probe_items = (p->d.fact->rows + x.tile - 1) / x.tile;
+    x.final_items = (G + tpk::FINAL_CHUNK - 1) / tpk::FINAL_CHUNK;
 }
 
 void batch_query_desc(const tp_plan* p, const BatchPrep& x, void* join_slots, uint32_t* side, uint64_t* acc,
-                      uint32_t* err, const tpk::OutDev& out, tpk::BatchQuery* Bp) {
+                      uint32_t* err, const tpk::OutDev& out, tpk::BatchQuery* Bp, unsigned* final_done,
+                      unsigned long long* final_end) {
     const tp_plan_desc& d = p->d;
     tpk::BatchQuery& B = *Bp;
     memset(&B, 0, sizeof(B));
@@ -420,6 +441,8 @@ void batch_query_desc(const tp_plan* p, const BatchPrep& x, void* join_slots, ui
     B.out = out;
     B.build_items = (uint32_t)x.build_items;
     B.probe_items = (uint32_t)x.probe_items;
+    B.final_done = final_done;
+    B.final_end = final_end;
 }
 
 void batch_items(const tp_plan* p, const BatchPrep& x, uint32_t qi, int kind, std::vector<tpk::BatchItem>* items) {
@@ -432,7 +455,10 @@ void batch_items(const tp_plan* p, const BatchPrep& x, uint32_t qi, int kind, st
         for (uint64_t k = 0; k < x.probe_items; ++k)
             items->push_back(tpk::BatchItem{qi, tpk::BI_PROBE, k * x.tile, std::min(rows, (k + 1) * x.tile), 0});
     } else {
-        items->push_back(tpk::BatchItem{qi, tpk::BI_FINAL, 0, 0, 0});
+        const uint64_t G = 1ull << p->key_bits;
+        for (uint64_t k = 0; k < x.final_items; ++k)
+            items->push_back(tpk::BatchItem{qi, tpk::BI_FINAL, k * tpk::FINAL_CHUNK,
+                                            std::min<uint64_t>(G, (k + 1) * tpk::FINAL_CHUNK), 0});
     }
 }
 
@@ -480,7 +506,7 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
     // ---- per query sizes and choices
     std::vector<BatchPrep> qs(n);
     // zeroed every run: counters, error word, group counts, join side cells, accumulators
-    uint64_t ff = 0, zero = a256((1 + 2 * (uint64_t)n) * 4) + 256 + a256(8 * (uint64_t)n) * 2, outb = 0;
+    uint64_t ff = 0, zero = a256((1 + 2 * (uint64_t)n) * 4) + 256 + a256(8 * (uint64_t)n) * 5, outb = 0;
     uint32_t smem_max = 16;
     uint64_t n_items = 0;
     for (int i = 0; i < n; ++i) {
@@ -491,7 +517,7 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
         ff += x.join_bytes;
         zero += x.acc_bytes;
         outb += x.out_bytes;
-        n_items += x.build_items + x.probe_items + 1;
+        n_items += x.build_items + x.probe_items + x.final_items;
     }
     if (n_items >= (1ull << 32)) return fail(TP_E_INVALID, "tp_batch_create: too many tasks");
     const uint64_t qbytes = a256(sizeof(tpk::BatchQuery) * n);
@@ -514,6 +540,12 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
     b->d_groups = (unsigned long long*)zp;
     zp += a256(8 * (uint64_t)n);
     uint32_t* sides = (uint32_t*)zp;   // two words per query: present flag, payload
+    zp += a256(8 * (uint64_t)n);
+    b->d_task_ns = (unsigned long long*)zp;
+    zp += a256(8 * (uint64_t)n);
+    unsigned* final_done = (unsigned*)zp;
+    zp += a256(8 * (uint64_t)n);
+    unsigned long long* final_end = (unsigned long long*)zp;
     zp += a256(8 * (uint64_t)n);
     unsigned char* accp = zp;
     unsigned char* qp = b->zero_base + zero;
@@ -551,7 +583,9 @@ static tp_status batch_create_impl(tp_engine* e, tp_plan* const* plans, int32_t 
             op += a256(G * 8);
         }
         o.n_groups = b->d_groups + i;
-        batch_query_desc(p, x, jp, sides + 2 * i, (uint64_t*)accp, b->d_err, o, &hq[i]);
+        batch_query_desc(p, x, jp, sides + 2 * i, (uint64_t*)accp, b->d_err, o, &hq[i], final_done + 2 * i,
+                         final_end + i);
+        hq[i].task_ns = b->d_task_ns + i;
         jp += x.join_bytes;
         accp += x.acc_bytes;
         batch_items(p, x, (uint32_t)i, tpk::BI_BUILD, &items);
@@ -721,52 +755,67 @@ tp_status tp_autotune(tp_engine* e, tp_plan* const* plans, int32_t n, const char
     clear_error();
     if (!e || !plans || n < 1 || !path) return fail(TP_E_INVALID, "tp_autotune: bad arguments");
     std::lock_guard<std::mutex> lk(e->exec_mu);
-    // classes, largest total fact volume first
-    std::map<int, std::vector<tp_plan*>> members;
-    std::map<int, uint64_t> volume;
-    for (int i = 0; i < n; ++i) {
-        const int c = query_class(plans[i]);
-        members[c].push_back(plans[i]);
-        volume[c] += plans[i]->d.fact->rows;
-    }
-    std::vector<int> order;
-    for (auto& kv : members) order.push_back(kv.first);
-    std::sort(order.begin(), order.end(), [&](int a, int b) { return volume[a] > volume[b]; });
+    // every class is tuned in the same runs of the whole set: a candidate
+    // value of one knob is tried for every class at once, and each class
+    // keeps it when its own queries' CTA time (summed over their tasks, read
+    // from the device) fell by 2% or more
+    std::vector<int> cls(n);
     std::map<int, Tune> table;
-    auto time_class = [&](int c, double* ms) -> tp_status {
+    for (int i = 0; i < n; ++i) {
+        cls[i] = query_class(plans[i]);
+        table[cls[i]] = Tune{0.5f, 1024, TP_AGG_AUTO};
+    }
+    auto class_cost = [&](const std::map<int, Tune>& t, std::map<int, double>* cost) -> tp_status {
         tp_batch* b = nullptr;
-        tp_status s = batch_create_impl(e, members[c].data(), (int)members[c].size(), table, &b);
+        tp_status s = batch_create_impl(e, plans, n, t, &b);
         if (s) return s;
-        double best = 1e30;
-        for (int rep = 0; rep < 3 && s == TP_OK; ++rep) {
+        cost->clear();
+        std::vector<unsigned long long> ns(n);
+        for (int rep = 0; rep < 3 && s == TP_OK; ++rep) {   // the best of three runs per query
             s = batch_run(b, nullptr);
-            best = std::min(best, b->last_ms);
+            if (s) break;
+            cudaError_t ce = cudaMemcpy(ns.data(), b->d_task_ns, 8ull * n, cudaMemcpyDeviceToHost);
+            if (ce != cudaSuccess) {
+                s = fail(TP_E_CUDA, "tp_autotune: %s", cudaGetErrorString(ce));
+                break;
+            }
+            std::map<int, double> c;
+            for (int i = 0; i < n; ++i) c[cls[i]] += (double)ns[i];
+            for (auto& kv : c) {
+                auto it = cost->find(kv.first);
+                if (it == cost->end() || kv.second < it->second) (*cost)[kv.first] = kv.second;
+            }
         }
         batch_free(b);
-        *ms = best;
         return s;
     };
-    for (int c : order) {
-        table[c] = Tune{0.5f, 1024, TP_AGG_AUTO};
-        double best;
-        tp_status s = time_class(c, &best);
-        if (s) return s;
-        const uint32_t rpw[] = {128, 256, 512, 1024};
-        const int aggs[] = {TP_AGG_AUTO, TP_AGG_GLOBAL};
-        const float lfs[] = {0.5f, 0.7f};
-        for (int knob = 0; knob < 3; ++knob) {
-            const int nv = knob == 0 ? 4 : 2;
-            for (int v = 0; v < nv; ++v) {
-                Tune cand = table[c];
-                if (knob == 0) cand.rows_per_warp = rpw[v];
-                if (knob == 1) cand.agg = aggs[v];
-                if (knob == 2) cand.lf = lfs[v];
-                const Tune keep = table[c];
-                table[c] = cand;
-                double ms;
-                if ((s = time_class(c, &ms))) return s;
-                if (ms < best * 0.98) best = ms;
-                else table[c] = keep;
+    std::map<int, double> best;
+    tp_status s = class_cost(table, &best);
+    if (s) return s;
+    const uint32_t rpw[] = {128, 256, 512, 1024};
+    const int aggs[] = {TP_AGG_AUTO, TP_AGG_GLOBAL};
+    const float lfs[] = {0.5f, 0.7f};
+    for (int knob = 0; knob < 3; ++knob) {
+        const int nv = knob == 0 ? 4 : 2;
+        for (int v = 0; v < nv; ++v) {
+            std::map<int, Tune> cand = table;
+            bool differs = false;
+            for (auto& kv : cand) {
+                Tune t = kv.second;
+                if (knob == 0) t.rows_per_warp = rpw[v];
+                if (knob == 1) t.agg = aggs[v];
+                if (knob == 2) t.lf = lfs[v];
+                differs = differs || memcmp(&t, &kv.second, sizeof(Tune)) != 0;
+                kv.second = t;
+            }
+            if (!differs) continue;
+            std::map<int, double> cost;
+            if ((s = class_cost(cand, &cost))) return s;
+            for (auto& kv : cost) {
+                if (kv.second < best[kv.first] * 0.98) {
+                    best[kv.first] = kv.second;
+                    table[kv.first] = cand[kv.first];
+                }
             }
         }
     }

@@ -442,19 +442,37 @@ __device__ __forceinline__ void write_row(const OutDev& o, uint64_t pos, uint64_
     }
 }
 
-// One CTA writes the non-empty groups of a dense table (count[G], then lo/hi
-// per sum) in key order, so the output is sorted; lo_only: high words are the
+// Non-empty groups among [g0, g1) of a dense table (count[G] first); every
+// thread of the CTA calls it and gets the total.
+__device__ __forceinline__ uint32_t dense_range_count(const uint64_t* __restrict__ gacc, uint32_t g0, uint32_t g1) {
+    __shared__ uint32_t warp_cnt[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t c = 0;
+    for (uint32_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) c += gacc[g] != 0 ? 1u : 0u;
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if (lane == 0) warp_cnt[warp] = c;
+    __syncthreads();
+    uint32_t total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += warp_cnt[w];
+    __syncthreads();
+    return total;
+}
+
+// One CTA writes the non-empty groups among [g0, g1) of a dense table
+// (count[G], then lo/hi per sum) in key order at output rows first,
+// first + 1, ...; returns how many it wrote.  lo_only: high words are the
 // sign extension of the low words.  Every thread of the CTA must call it.
-__device__ __forceinline__ void final_dense_block(const uint64_t* __restrict__ gacc, uint32_t G, int n_sum,
-                                                  const OutDev& o, bool lo_only) {
+__device__ __forceinline__ uint64_t dense_range_emit(const uint64_t* __restrict__ gacc, uint32_t G, uint32_t g0,
+                                                     uint32_t g1, int n_sum, const OutDev& o, bool lo_only,
+                                                     uint64_t first) {
     __shared__ uint32_t warp_tot[32];
     __shared__ uint64_t base;
-    if (threadIdx.x == 0) base = 0;
+    if (threadIdx.x == 0) base = first;
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t c0 = 0; c0 < G; c0 += blockDim.x) {
+    for (uint32_t c0 = g0; c0 < g1; c0 += blockDim.x) {
         const uint32_t g = c0 + threadIdx.x;
-        const bool has = g < G && gacc[g] != 0;
+        const bool has = g < g1 && gacc[g] != 0;
         const unsigned m = __ballot_sync(0xffffffffu, has);
         if (lane == 0) warp_tot[warp] = __popc(m);
         __syncthreads();
@@ -476,7 +494,17 @@ __device__ __forceinline__ void final_dense_block(const uint64_t* __restrict__ g
         if (threadIdx.x == 0) base += total;
         __syncthreads();
     }
-    if (threadIdx.x == 0) *o.n_groups = base;
+    const uint64_t n = base - first;
+    __syncthreads();
+    return n;
+}
+
+// One CTA writes every non-empty group of a dense table in key order, so the
+// output is sorted, and the group count.
+__device__ __forceinline__ void final_dense_block(const uint64_t* __restrict__ gacc, uint32_t G, int n_sum,
+                                                  const OutDev& o, bool lo_only) {
+    const uint64_t n = dense_range_emit(gacc, G, 0, G, n_sum, o, lo_only, 0);
+    if (threadIdx.x == 0) *o.n_groups = n;
 }
 
 // ------------------------------------------------------------- join build

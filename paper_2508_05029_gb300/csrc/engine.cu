@@ -197,6 +197,7 @@ tp_status tp_init(const tp_config* cfg, tp_engine** out) {
     TP_TRY_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold));
     TP_TRY_CUDA(cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking));
     TP_TRY_CUDA(cudaStreamCreateWithFlags(&e->spill, cudaStreamNonBlocking));
+    TP_TRY_CUDA(cudaStreamCreateWithFlags(&e->aux, cudaStreamNonBlocking));
     if (cfg->compute_stream) {
         e->compute = (cudaStream_t)cfg->compute_stream;
     } else {
@@ -215,6 +216,7 @@ tp_status tp_init(const tp_config* cfg, tp_engine** out) {
             cudaFreeHost(e->host_words);
             cudaStreamDestroy(e->copy);
             cudaStreamDestroy(e->spill);
+            cudaStreamDestroy(e->aux);
             if (e->own_compute) cudaStreamDestroy(e->compute);
             return fail(TP_E_NOMEM, "page pool of %u x %llu bytes could not be pinned: %s", pp.n_pages,
                         (unsigned long long)pp.page_bytes, cudaGetErrorString(err));
@@ -226,6 +228,7 @@ tp_status tp_init(const tp_config* cfg, tp_engine** out) {
     e->lane0.compute = e->compute;
     e->lane0.copy = e->copy;
     e->lane0.spill = e->spill;
+    e->lane0.aux = e->aux;
     e->lane0.host_words = e->host_words;
     *out = e.release();
     return TP_OK;
@@ -237,10 +240,12 @@ void tp_shutdown(tp_engine* e) {
     cudaStreamSynchronize(e->compute);
     cudaStreamSynchronize(e->copy);
     cudaStreamSynchronize(e->spill);
+    cudaStreamSynchronize(e->aux);
     if (e->pool.base) cudaFreeHost(e->pool.base);
     if (e->host_words) cudaFreeHost(e->host_words);
     cudaStreamDestroy(e->copy);
     cudaStreamDestroy(e->spill);
+    cudaStreamDestroy(e->aux);
     if (e->own_compute) cudaStreamDestroy(e->compute);
     delete e;
 }
@@ -323,9 +328,11 @@ static tp_status check_desc(const tp_table_desc* d) {
 }
 
 static tp_table* new_table(tp_engine* e, const tp_table_desc* d) {
+    static std::atomic<uint64_t> next_serial{1};
     tp_table* t = new (std::nothrow) tp_table();
     if (!t) return nullptr;
     t->eng = e;
+    t->serial = next_serial++;
     t->batch_rows = d->batch_rows ? d->batch_rows : e->cfg.batch_rows;
     for (int i = 0; i < d->n_cols; ++i) {
         t->types.push_back(d->cols[i].type);

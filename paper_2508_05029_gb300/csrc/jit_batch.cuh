@@ -119,6 +119,7 @@ extern "C" __global__ void __launch_bounds__(tpk::BATCH_THREADS)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t cur;
     __shared__ int flag;
+    __shared__ uint64_t first_row;
     const uint64_t wait_ns = *wait;
     unsigned* build_done = ctr + 1;
     unsigned* probe_done = ctr + 1 + n_q;
@@ -130,6 +131,7 @@ extern "C" __global__ void __launch_bounds__(tpk::BATCH_THREADS)
         if (i >= n_items) return;
         const BatchItem it = items[i];
         const BatchQuery& B = qs[it.q];
+        const uint64_t t_claim = B.task_ns ? now_ns() : 0;
         if (it.kind == BI_BUILD) {
             for (uint64_t r = it.r0 + threadIdx.x; r < it.r1; r += blockDim.x) build_insert(B.b, r);
             __syncthreads();
@@ -147,8 +149,24 @@ extern "C" __global__ void __launch_bounds__(tpk::BATCH_THREADS)
             }
         } else {
             if (!wait_count(&probe_done[it.q], B.probe_items, wait_ns, err, &flag)) continue;
-            final_dense_block(B.acc, 1u << B.key_bits, B.q.n_sum, B.out, B.fast != 0);
+            // groups [r0, r1): count them, wait for the ranges before to publish
+            // where their rows end, publish this range's end, write the rows
+            const uint32_t G = 1u << B.key_bits;
+            const uint32_t g0 = (uint32_t)it.r0, g1 = (uint32_t)it.r1, k = g0 / FINAL_CHUNK;
+            const uint32_t cnt = dense_range_count(B.acc, g0, g1);
+            if (!wait_count(B.final_done, k, wait_ns, err, &flag)) continue;
+            if (threadIdx.x == 0) {
+                const uint64_t first = k ? *(volatile unsigned long long*)B.final_end : 0ull;
+                first_row = first;
+                *(volatile unsigned long long*)B.final_end = first + cnt;
+                __threadfence();
+                atomicAdd(B.final_done, 1u);
+                if (g1 == G) *B.out.n_groups = first + cnt;
+            }
+            __syncthreads();
+            dense_range_emit(B.acc, G, g0, g1, B.q.n_sum, B.out, B.fast != 0, first_row);
         }
         __syncthreads();
+        if (B.task_ns && threadIdx.x == 0) atomicAdd(B.task_ns, (unsigned long long)(now_ns() - t_claim));
     }
 }

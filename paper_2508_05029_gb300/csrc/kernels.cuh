@@ -255,9 +255,14 @@ enum : uint32_t { BI_BUILD = 0, BI_PROBE = 1, BI_FINAL = 2 };
 struct BatchItem {
     uint32_t q;        // query index
     uint32_t kind;     // BI_*
-    uint64_t r0, r1;   // row range (build: dimension rows, probe: fact rows)
+    uint64_t r0, r1;   // row range (build: dimension rows, probe: fact rows, final: groups)
     uint64_t pad;
 };
+
+// Groups one finalisation task of a batched query writes: a query's non-empty
+// groups are emitted by ceil(2^key_bits / FINAL_CHUNK) tasks, range k after
+// range k - 1 has published where its rows end.
+constexpr uint32_t FINAL_CHUNK = 8192;
 
 // One query of a batch, as the persistent kernel sees it.
 struct BatchQuery {
@@ -273,6 +278,9 @@ struct BatchQuery {
     int32_t shape;              // shape id of the run-time compiled probe task
     int8_t sum_mode[MAX_SUM];   // shared-memory table: 1 low word, 2 low + carry word
     int64_t sum_off[MAX_SUM];   // term offsets making terms non-negative
+    unsigned long long* task_ns;   // when set: nanoseconds of CTA time this query's tasks took
+    unsigned* final_done;          // finalisation ranges that published their end (zeroed per run)
+    unsigned long long* final_end; // output rows written by the published ranges
 };
 
 constexpr int BATCH_THREADS = 512;

@@ -111,13 +111,23 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(const __grid_constant__ 
     const typename SV::V* src = (const typename SV::V*)c.ptr;
     const SelRange<T> rg(lo, hi);
     const uint64_t n_chunks = (n + CH - 1) / CH;
+    const uint64_t n_full = n / CH;
+    // the next whole chunk's vectors are loaded while this one is ranked and
+    // written, so a CTA keeps a chunk of loads in flight throughout
+    typename SV::V nxt[SEL_LOADS];
+    auto load_chunk = [&](uint64_t ch) {
+#pragma unroll
+        for (int i = 0; i < SEL_LOADS; ++i) nxt[i] = __ldcs(src + ch * CH / N + (uint64_t)i * SEL_THREADS + threadIdx.x);
+    };
+    if (blockIdx.x < n_full) load_chunk(blockIdx.x);
     for (uint64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
         const uint64_t r0 = ch * CH;
         uint32_t m[SEL_LOADS];   // pass bits of each vector
-        if (r0 + CH <= n) {
+        if (ch < n_full) {
             typename SV::V v[SEL_LOADS];
 #pragma unroll
-            for (int i = 0; i < SEL_LOADS; ++i) v[i] = __ldcs(src + r0 / N + (uint64_t)i * SEL_THREADS + threadIdx.x);
+            for (int i = 0; i < SEL_LOADS; ++i) v[i] = nxt[i];
+            if (ch + gridDim.x < n_full) load_chunk(ch + gridDim.x);
 #pragma unroll
             for (int i = 0; i < SEL_LOADS; ++i) {
                 m[i] = 0;
@@ -169,7 +179,7 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(const __grid_constant__ 
 // e0 + 32 j + lane of the selection vector), then warp-aggregated table
 // updates.  *count selected rows; the filter is not evaluated again.
 template <int NS, bool FAST>
-__global__ void __launch_bounds__(256) k_agg_selected(const __grid_constant__ QueryDev q,
+__global__ void __launch_bounds__(256, 2) k_agg_selected(const __grid_constant__ QueryDev q,
                                                       const uint32_t* __restrict__ sel,
                                                       const unsigned long long* count,
                                                       const __grid_constant__ AggTable tab) {
@@ -192,14 +202,32 @@ __global__ void __launch_bounds__(256) k_agg_selected(const __grid_constant__ Qu
         // every column of the selected rows in flight at once: the rows
         // passed the filter, so all of them are needed unless the join drops
         // the row
-        int64_t fk[R], gv[MAX_GROUP][R], a[NSX][R], b[NSX][R];
+        // fact-side group fields go straight to their bit positions of the
+        // packed key (first field highest); dimension fields follow the probe
+        int64_t fk[R], a[NSX][R], b[NSX][R];
+        uint64_t key[R] = {0, 0, 0, 0};
+        bool bad[R] = {false, false, false, false};
 #pragma unroll
         for (int j = 0; j < R; ++j) fk[j] = (q.has_join && pass[j]) ? ld1(q.fk, row[j]) : 0;
+        {
+            int shift = 0;
+            for (int g = q.n_group - 1; g >= 0; --g) {
+                const int bits = q.gbits[g];
+                if (q.gside[g] == 0) {
 #pragma unroll
-        for (int g = 0; g < MAX_GROUP; ++g)
-#pragma unroll
-            for (int j = 0; j < R; ++j)
-                gv[g][j] = (g < q.n_group && q.gside[g] == 0 && pass[j]) ? ld1(q.gcol[g], row[j]) : 0;
+                    for (int j = 0; j < R; ++j) {
+                        const uint64_t f = pass[j] ? (uint64_t)ld1(q.gcol[g], row[j]) : 0;
+                        if (bits < 64) {
+                            bad[j] = bad[j] || (f >> bits) != 0;
+                            key[j] |= f << shift;
+                        } else {
+                            key[j] = f;
+                        }
+                    }
+                }
+                shift += bits;
+            }
+        }
 #pragma unroll
         for (int s = 0; s < NSX; ++s) {
 #pragma unroll
@@ -220,38 +248,37 @@ __global__ void __launch_bounds__(256) k_agg_selected(const __grid_constant__ Qu
                 }
             }
         }
-        uint64_t key[R] = {0, 0, 0, 0};
+        {
+            int shift = 0;
+            for (int g = q.n_group - 1; g >= 0; --g) {
+                const int bits = q.gbits[g];
+                if (q.gside[g] != 0) {   // dimension fields fit their bits by construction of the payload
 #pragma unroll
-        for (int g = 0; g < MAX_GROUP; ++g) {
-            if (g >= q.n_group) break;
-            const int bits = q.gbits[g];
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const uint64_t f = q.gside[g] == 0 ? (uint64_t)gv[g][j]
-                                                   : (uint64_t)(pay[j] >> q.gdpos[g]) & ((1ull << bits) - 1ull);
-                if (bits < 64) {
-                    if (pass[j] && (f >> bits) != 0) {
-                        atomicOr(q.err, ERR_RANGE);
-                        pass[j] = false;
-                    }
-                    key[j] = (key[j] << bits) | f;
-                } else {
-                    key[j] = f;
+                    for (int j = 0; j < R; ++j) key[j] |= ((uint64_t)(pay[j] >> q.gdpos[g]) & ((1ull << bits) - 1ull))
+                                                          << shift;
                 }
+                shift += bits;
             }
         }
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            int64_t tj[NSX];
-            I128 tmj[NSX];
-#pragma unroll
-            for (int s = 0; s < NSX; ++s) {
-                const bool ms = q.skind[s] == S_MUL_SUB;
-                if constexpr (FAST) tj[s] = ms ? a[s][j] * (q.sk[s] - b[s][j]) : a[s][j];
-                else tmj[s] = ms ? mul_sub(a[s][j], q.sk[s], b[s][j]) : i128_from_i64(a[s][j]);
+            if (pass[j] && bad[j]) {
+                atomicOr(q.err, ERR_RANGE);
+                pass[j] = false;
             }
-            agg_warp_row<NS, FAST>(tab, q.err, q.n_sum, pass[j], key[j], tj, tmj, claims);
         }
+        int64_t t[NSX][R];
+        I128 tm[NSX][R];
+#pragma unroll
+        for (int s = 0; s < NSX; ++s) {
+            const bool ms = q.skind[s] == S_MUL_SUB;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                if constexpr (FAST) t[s][j] = ms ? a[s][j] * (q.sk[s] - b[s][j]) : a[s][j];
+                else tm[s][j] = ms ? mul_sub(a[s][j], q.sk[s], b[s][j]) : i128_from_i64(a[s][j]);
+            }
+        }
+        agg_warp_rows<NS, FAST, R>(tab, q.err, q.n_sum, pass, key, t, tm, claims);
     }
     agg_add_claims_warp(tab, q.err, claims);
 }

@@ -8,7 +8,9 @@
 //   2. an exclusive scan of that array (k_scan_*);
 //   3. k_digit_scatter: every warp ranks its 512 pairs in input order with
 //      __match_any_sync on the digit, so equal digits keep their order and the
-//      pass is stable.
+//      pass is stable; the tile's pairs are first placed digit-ordered in
+//      shared memory, then written out so that consecutive threads write
+//      consecutive slots of each digit's output run (coalesced stores).
 #include "kernels.cuh"
 
 namespace tpk {
@@ -17,6 +19,7 @@ constexpr int SORT_THREADS = 256;
 constexpr int SORT_WARPS = SORT_THREADS / 32;
 constexpr int SORT_ROUNDS = 16;                                // pairs per lane
 constexpr int SORT_TILE = SORT_THREADS * SORT_ROUNDS;          // 4096
+static_assert(SORT_THREADS == 256, "the scatter scans one digit per thread");
 constexpr int SCAN_THREADS = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;           // 4096
@@ -125,16 +128,25 @@ __global__ void __launch_bounds__(SORT_THREADS) k_digit_hist(const uint64_t* __r
     for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(uint64_t)d * tiles + blockIdx.x] = cnt[d];
 }
 
+// dynamic shared memory of k_digit_scatter: the tile's keys and values in
+// digit order, per-warp digit positions, per-digit tile-local starts
+constexpr size_t SCATTER_SMEM = (size_t)SORT_TILE * 8 + (size_t)SORT_TILE * 4 + SORT_WARPS * 257 * 4 + 257 * 4;
+
 __global__ void __launch_bounds__(SORT_THREADS) k_digit_scatter(
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, uint64_t n, int shift,
     const uint32_t* __restrict__ offsets, uint64_t tiles) {
-    __shared__ uint32_t wpos[SORT_WARPS][257];
+    extern __shared__ __align__(16) unsigned char sm[];
+    uint64_t* sk = (uint64_t*)sm;                                   // [SORT_TILE]
+    uint32_t* sv = (uint32_t*)(sk + SORT_TILE);                     // [SORT_TILE]
+    uint32_t (*wpos)[257] = (uint32_t (*)[257])(sv + SORT_TILE);    // [SORT_WARPS][257]
+    uint32_t* start = &wpos[SORT_WARPS - 1][0] + 257;               // [257]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < SORT_WARPS * 257; i += blockDim.x) (&wpos[0][0])[i] = 0;
     __syncthreads();
     // this warp's 512 pairs, in input order: round r, lane l -> chunk + 32 r + l
-    const uint64_t chunk = (uint64_t)blockIdx.x * SORT_TILE + (uint64_t)warp * (SORT_ROUNDS * 32);
+    const uint64_t tile0 = (uint64_t)blockIdx.x * SORT_TILE;
+    const uint64_t chunk = tile0 + (uint64_t)warp * (SORT_ROUNDS * 32);
     uint64_t k[SORT_ROUNDS];
     uint32_t v[SORT_ROUNDS];
     uint32_t d[SORT_ROUNDS];
@@ -157,9 +169,17 @@ __global__ void __launch_bounds__(SORT_THREADS) k_digit_scatter(
         __syncwarp();
     }
     __syncthreads();
-    // turn counts into this warp's first output position per digit
-    for (int dg = threadIdx.x; dg < 256; dg += blockDim.x) {
-        uint32_t run = offsets[(uint64_t)dg * tiles + blockIdx.x];
+    // tile-local start of every digit (digits in order, warps in order within
+    // a digit), and each warp's first tile-local position per digit
+    {
+        __shared__ uint32_t scan_buf[32];
+        const int dg = threadIdx.x;   // SORT_THREADS == 256: one digit per thread
+        uint32_t tot = 0;
+        for (int w = 0; w < SORT_WARPS; ++w) tot += wpos[w][dg];
+        uint32_t all;
+        uint32_t run = block_excl_scan(tot, scan_buf, &all);
+        start[dg] = run;
+        if (dg == 0) start[256] = all;
         for (int w = 0; w < SORT_WARPS; ++w) {
             const uint32_t c = wpos[w][dg];
             wpos[w][dg] = run;
@@ -171,15 +191,24 @@ __global__ void __launch_bounds__(SORT_THREADS) k_digit_scatter(
 #pragma unroll
     for (int r = 0; r < SORT_ROUNDS; ++r) {
         const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
-        uint32_t pos = 0;
         if (d[r] < 256) {
-            pos = wpos[warp][d[r]] + __popc(peers & below);
-            keys_out[pos] = k[r];
-            vals_out[pos] = v[r];
+            const uint32_t pos = wpos[warp][d[r]] + __popc(peers & below);
+            sk[pos] = k[r];
+            sv[pos] = v[r];
         }
         __syncwarp();
         if (d[r] < 256 && lane == __ffs(peers) - 1) wpos[warp][d[r]] += __popc(peers);
         __syncwarp();
+    }
+    __syncthreads();
+    // slot i of the digit-ordered tile goes to its digit's output run
+    const uint32_t count = start[256];
+    for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
+        const uint64_t key = sk[i];
+        const uint32_t dg = (uint32_t)((key >> shift) & 255u);
+        const uint64_t pos = (uint64_t)offsets[(uint64_t)dg * tiles + blockIdx.x] + (i - start[dg]);
+        keys_out[pos] = key;
+        vals_out[pos] = sv[i];
     }
 }
 
@@ -195,12 +224,14 @@ cudaError_t radix_sort_pairs(uint64_t** keys, uint32_t** vals, uint64_t** tmp_ke
     const uint64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
     if (256 * tiles > (uint64_t)SCAN_TILE * SCAN_TILE) return cudaErrorInvalidValue;
     uint32_t* scan_scratch = hist + 256 * tiles;
+    cudaError_t ea = ensure_smem_limit((const void*)k_digit_scatter, (int)SCATTER_SMEM);
+    if (ea != cudaSuccess) return ea;
     for (int shift = 0; shift < bits && shift < 64; shift += 8) {
         k_digit_hist<<<(unsigned)tiles, SORT_THREADS, 0, st>>>(*keys, n, shift, hist, tiles);
         cudaError_t e = excl_scan(hist, 256 * tiles, scan_scratch, st);
         if (e != cudaSuccess) return e;
-        k_digit_scatter<<<(unsigned)tiles, SORT_THREADS, 0, st>>>(*keys, *vals, *tmp_keys, *tmp_vals, n,
-                                                                  shift, hist, tiles);
+        k_digit_scatter<<<(unsigned)tiles, SORT_THREADS, SCATTER_SMEM, st>>>(*keys, *vals, *tmp_keys, *tmp_vals,
+                                                                             n, shift, hist, tiles);
         uint64_t* tk = *keys; *keys = *tmp_keys; *tmp_keys = tk;
         uint32_t* tv = *vals; *vals = *tmp_vals; *tmp_vals = tv;
     }

@@ -132,17 +132,10 @@ __device__ __forceinline__ void consume_global(const QueryDev& q, const StageLay
             }
         }
     }
+    bool valid[ST_RPL];
 #pragma unroll
-    for (int j = 0; j < ST_RPL; ++j) {
-        int64_t tj[NS > 0 ? NS : 1];
-        I128 tmj[NS > 0 ? NS : 1];
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            if constexpr (FAST) tj[s] = t[s][j];
-            else tmj[s] = tm[s][j];
-        }
-        agg_warp_row<NS, FAST>(tab, q.err, q.n_sum, (pm >> j) & 1u, key[j], tj, tmj, claims);
-    }
+    for (int j = 0; j < ST_RPL; ++j) valid[j] = (pm >> j) & 1u;
+    agg_warp_rows<NS, FAST, ST_RPL>(tab, q.err, q.n_sum, valid, key, t, tm, claims);
 }
 
 template <int NS, bool FAST>

@@ -92,6 +92,7 @@ struct Lane {
     cudaStream_t compute = nullptr;
     cudaStream_t copy = nullptr;      // host -> device prefetch
     cudaStream_t spill = nullptr;     // device -> host spill copies (the other link direction)
+    cudaStream_t aux = nullptr;       // kernels that overlap the compute stream's (pipelined selection)
     uint64_t* host_words = nullptr;   // 4 KB pinned
 };
 
@@ -106,6 +107,7 @@ struct tp_engine {
     cudaStream_t compute = nullptr;
     cudaStream_t copy = nullptr;
     cudaStream_t spill = nullptr;
+    cudaStream_t aux = nullptr;
     bool own_compute = false;
     uint32_t copy_flags = 0;     // TP_COPY_* (tp_set_copy_options)
     std::mutex exec_mu;          // one execution at a time on the engine streams
@@ -126,6 +128,7 @@ struct tp_engine {
 
 struct tp_table {
     tp_engine* eng = nullptr;
+    uint64_t serial = 0;    // unique per table created in this process
     std::vector<int32_t> types;
     std::vector<int32_t> scales;
     std::vector<std::string> names;
@@ -284,7 +287,7 @@ int narrow_width_max(const tp_table* t, int c);
 constexpr uint64_t BATCH_BUILD_CHUNK = 65536;   // dimension rows per build task
 struct BatchPrep {
     uint64_t join_cap = 0, join_bytes = 0, acc_bytes = 0, out_bytes = 0, tile = 0, range = 0;
-    uint64_t build_items = 0, probe_items = 0;
+    uint64_t build_items = 0, probe_items = 0, final_items = 0;
     bool join = false, key64 = false, smem = false, fast = false, direct = false;
     tpk::TermBounds bounds[tpk::MAX_SUM] = {};
     int8_t mode[tpk::MAX_SUM] = {};
@@ -298,11 +301,14 @@ tp_status batch_check_plan(const tp_engine* e, const tp_plan* p, int i);
 // of shared memory.
 void batch_prep(const tp_engine* e, const tp_plan* p, float lf_tuned, uint32_t rows_per_warp, int agg, BatchPrep* x);
 // The device descriptor of p in a batch: its join table at join_slots (side
-// cell at side), accumulators at acc, outputs in out; shape id 0.
+// cell at side), accumulators at acc, outputs in out, its finalisation
+// ranges' words at final_done / final_end (both zeroed before every run);
+// shape id 0.
 void batch_query_desc(const tp_plan* p, const BatchPrep& x, void* join_slots, uint32_t* side, uint64_t* acc,
-                      uint32_t* err, const tpk::OutDev& out, tpk::BatchQuery* B);
+                      uint32_t* err, const tpk::OutDev& out, tpk::BatchQuery* B, unsigned* final_done = nullptr,
+                      unsigned long long* final_end = nullptr);
 // Appends query qi's tasks of one kind (BI_BUILD chunks, BI_PROBE tiles or
-// its BI_FINAL) to items.
+// its BI_FINAL group ranges) to items.
 void batch_items(const tp_plan* p, const BatchPrep& x, uint32_t qi, int kind, std::vector<tpk::BatchItem>* items);
 // The shape struct `name` of a batched query for the run-time compiled queue
 // kernel, and that kernel's source for shapes JS_0 .. JS_{n-1}.
