@@ -197,7 +197,6 @@ tp_status tp_init(const tp_config* cfg, tp_engine** out) {
     TP_TRY_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold));
     TP_TRY_CUDA(cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking));
     TP_TRY_CUDA(cudaStreamCreateWithFlags(&e->spill, cudaStreamNonBlocking));
-    TP_TRY_CUDA(cudaStreamCreateWithFlags(&e->aux, cudaStreamNonBlocking));
     if (cfg->compute_stream) {
         e->compute = (cudaStream_t)cfg->compute_stream;
     } else {
@@ -216,7 +215,6 @@ tp_status tp_init(const tp_config* cfg, tp_engine** out) {
             cudaFreeHost(e->host_words);
             cudaStreamDestroy(e->copy);
             cudaStreamDestroy(e->spill);
-            cudaStreamDestroy(e->aux);
             if (e->own_compute) cudaStreamDestroy(e->compute);
             return fail(TP_E_NOMEM, "page pool of %u x %llu bytes could not be pinned: %s", pp.n_pages,
                         (unsigned long long)pp.page_bytes, cudaGetErrorString(err));
@@ -228,7 +226,6 @@ tp_status tp_init(const tp_config* cfg, tp_engine** out) {
     e->lane0.compute = e->compute;
     e->lane0.copy = e->copy;
     e->lane0.spill = e->spill;
-    e->lane0.aux = e->aux;
     e->lane0.host_words = e->host_words;
     *out = e.release();
     return TP_OK;
@@ -240,12 +237,10 @@ void tp_shutdown(tp_engine* e) {
     cudaStreamSynchronize(e->compute);
     cudaStreamSynchronize(e->copy);
     cudaStreamSynchronize(e->spill);
-    cudaStreamSynchronize(e->aux);
     if (e->pool.base) cudaFreeHost(e->pool.base);
     if (e->host_words) cudaFreeHost(e->host_words);
     cudaStreamDestroy(e->copy);
     cudaStreamDestroy(e->spill);
-    cudaStreamDestroy(e->aux);
     if (e->own_compute) cudaStreamDestroy(e->compute);
     delete e;
 }

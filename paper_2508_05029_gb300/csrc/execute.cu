@@ -684,15 +684,6 @@ constexpr uint64_t DIRECT_AGG_MAX_SLOTS = 1ull << 27;
 constexpr double SELECT_MAX_SELECTIVITY = 0.25;
 constexpr uint64_t SEL_SLICE_ROWS = 1ull << 26;
 
-// Rows of one selection slice for a batch of `rows`: a batch of more than
-// 2^22 rows is cut into about four slices (multiples of 4096 rows, keeping
-// the filter column's 16-byte alignment), so that the gather of one slice
-// overlaps the selection of the next; two selection vectors alternate.
-uint64_t sel_slice(uint64_t rows) {
-    if (rows <= (1ull << 22)) return rows;
-    const uint64_t s = ((rows + 3) / 4 + 4095) / 4096 * 4096;
-    return std::min<uint64_t>(s, SEL_SLICE_ROWS);
-}
 constexpr uint64_t DIRECT_AGG_ALWAYS = 1ull << 20;
 
 // Lookahead filter: used automatically when the join table takes at least
@@ -1385,8 +1376,8 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         p->selectivity < SELECT_MAX_SELECTIVITY) {
         uint64_t max_rows = S.fact->placement == PL_PAGES ? 0 : S.fact->rows;
         for (auto& b : S.fact->batches) max_rows = std::max(max_rows, b.rows);
-        sel_rows = sel_slice(max_rows);
-        est += 2 * align256(sel_rows * 4);
+        sel_rows = std::min<uint64_t>(SEL_SLICE_ROWS, max_rows);
+        est += align256(sel_rows * 4);
     }
     uint64_t agg_cap = 0;
     bool gdirect = false;           // direct-addressed global table over [rmin, rmin + rspan)
@@ -1702,25 +1693,9 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
         const bool g_staged = !(e->cfg.flags & TP_FLAG_NO_STAGED);
         const bool gfast = g_staged && !(e->cfg.flags & TP_FLAG_EXACT_ONLY) && sums_fit_int64(p, S.fact);
         const bool stage_all = p->selectivity >= 0.25;
-        uint32_t* sel[2] = {nullptr, nullptr};
-        unsigned long long* sel_cursor = (unsigned long long*)((uint8_t*)misc + 1024);   // two words
-        if (sel_rows && ((s = sc.alloc((void**)&sel[0], align256(sel_rows * 4))) ||
-                         (s = sc.alloc((void**)&sel[1], align256(sel_rows * 4)))))
-            return s;
-        // selection slice k fills sel[k % 2] on the compute stream; its gather
-        // runs on the auxiliary stream while slice k + 1 is selected
-        cudaEvent_t sel_ev[2][2] = {};   // [buffer][0: selected, 1: gathered]
-        struct EvGuard {
-            cudaEvent_t (*ev)[2];
-            ~EvGuard() {
-                for (int b = 0; b < 2; ++b)
-                    for (int k = 0; k < 2; ++k)
-                        if (ev[b][k]) cudaEventDestroy(ev[b][k]);
-            }
-        } sel_ev_guard{sel_ev};
-        if (sel_rows)
-            for (int b = 0; b < 2; ++b)
-                for (int k = 0; k < 2; ++k) TP_TRY_CUDA(cudaEventCreateWithFlags(&sel_ev[b][k], cudaEventDisableTiming));
+        uint32_t* sel = nullptr;
+        unsigned long long* sel_cursor = (unsigned long long*)((uint8_t*)misc + 1024);
+        if (sel_rows && (s = sc.alloc((void**)&sel, align256(sel_rows * 4)))) return s;
         // key ranges still to aggregate, the next one at the back (ascending
         // keys come out in order); one range covering every key unless a
         // table had to be split
@@ -1854,35 +1829,24 @@ tp_status execute_locked(tp_plan* p, Lane* lane, DimCache* cache, tp_result** ou
             at.key_lo = kr.lo;
             at.key_hi = kr.lo + (kr.span - 1);
             auto global_core = [&](const tpk::QueryDev& q, uint64_t rows) -> tp_status {
-                if (sel[0] && tpk::select_usable(q, std::min(rows, sel_rows))) {
-                    // selective filter: select the passing rows, then aggregate
-                    // them; slice k's gather (auxiliary stream) overlaps slice
-                    // k + 1's selection (compute stream)
-                    cudaStream_t ax = lane->aux;
-                    return cuda_check(timer.run(st, rows, [&]() -> cudaError_t {
-                        cudaError_t ce = cudaSuccess;
-                        uint64_t k = 0;
-                        for (uint64_t off = 0; off < rows && ce == cudaSuccess; off += sel_rows, ++k) {
-                            const int b = (int)(k & 1);
-                            const uint64_t nr = std::min(sel_rows, rows - off);
-                            const tpk::QueryDev qs = off ? tpk::offset_rows(q, off) : q;
-                            // the buffer's previous gather must be done with it
-                            if (k >= 2) ce = cudaStreamWaitEvent(st, sel_ev[b][1], 0);
-                            if (ce == cudaSuccess) ce = cudaMemsetAsync(sel_cursor + b, 0, sizeof(unsigned long long), st);
-                            if (ce == cudaSuccess) ce = tpk::launch_select(qs, nr, sel[b], sel_cursor + b, e->num_sms, st);
-                            if (ce == cudaSuccess) ce = cudaEventRecord(sel_ev[b][0], st);
-                            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(ax, sel_ev[b][0], 0);
-                            if (ce == cudaSuccess)
-                                ce = tpk::launch_agg_selected(qs, sel[b], sel_cursor + b, nr, at, gfast, e->num_sms, ax);
-                            if (ce == cudaSuccess) ce = cudaEventRecord(sel_ev[b][1], ax);
-                            mark_launch(e);
-                            mark_launch(e);
-                        }
-                        // the compute stream goes on once every gather is done
-                        for (uint64_t j = 0; j < std::min<uint64_t>(k, 2) && ce == cudaSuccess; ++j)
-                            ce = cudaStreamWaitEvent(st, sel_ev[j][1], 0);
-                        return ce;
-                    }), "aggregate");
+                if (sel && tpk::select_usable(q, std::min(rows, sel_rows))) {
+                    // selective filter: select the passing rows, then aggregate them
+                    // (overlapping a slice's gather with the next selection on a
+                    // second stream was measured slower: both contend for DRAM)
+                    for (uint64_t off = 0; off < rows; off += sel_rows) {
+                        const uint64_t nr = std::min(sel_rows, rows - off);
+                        const tpk::QueryDev qs = off ? tpk::offset_rows(q, off) : q;
+                        TP_TRY_CUDA(cudaMemsetAsync(sel_cursor, 0, sizeof(unsigned long long), st));
+                        mark_launch(e);
+                        mark_launch(e);
+                        tp_status r = cuda_check(timer.run(st, nr, [&] {
+                            cudaError_t ce = tpk::launch_select(qs, nr, sel, sel_cursor, e->num_sms, st);
+                            if (ce != cudaSuccess) return ce;
+                            return tpk::launch_agg_selected(qs, sel, sel_cursor, nr, at, gfast, e->num_sms, st);
+                        }), "aggregate");
+                        if (r) return r;
+                    }
+                    return TP_OK;
                 }
                 mark_launch(e);
                 tpk::StageLayout L;

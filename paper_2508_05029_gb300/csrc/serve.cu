@@ -754,7 +754,6 @@ void server_free(tp_server* sv) {
         if (l.compute) cudaStreamSynchronize(l.compute);
         if (l.copy) cudaStreamSynchronize(l.copy);
         if (l.spill) cudaStreamSynchronize(l.spill);
-        if (l.aux) cudaStreamSynchronize(l.aux);
     }
     for (Slot& sl : sv->slots)
         if (sl.st) cudaStreamSynchronize(sl.st);
@@ -766,7 +765,6 @@ void server_free(tp_server* sv) {
         if (l.compute) cudaStreamDestroy(l.compute);
         if (l.copy) cudaStreamDestroy(l.copy);
         if (l.spill) cudaStreamDestroy(l.spill);
-        if (l.aux) cudaStreamDestroy(l.aux);
         if (l.host_words) cudaFreeHost(l.host_words);
     }
     for (Slot& sl : sv->slots) {
@@ -799,14 +797,12 @@ tp_status tp_server_start(tp_engine* e, int32_t workers, int32_t max_inflight, u
         TP_TRY_CUDA(cudaStreamCreateWithFlags(&l.compute, cudaStreamNonBlocking));
         TP_TRY_CUDA(cudaStreamCreateWithFlags(&l.copy, cudaStreamNonBlocking));
         TP_TRY_CUDA(cudaStreamCreateWithFlags(&l.spill, cudaStreamNonBlocking));
-        TP_TRY_CUDA(cudaStreamCreateWithFlags(&l.aux, cudaStreamNonBlocking));
         TP_TRY_CUDA(cudaHostAlloc((void**)&l.host_words, 4096, cudaHostAllocDefault));
     }
     if (sv->batch_on) {
         TP_TRY_CUDA(cudaStreamCreateWithFlags(&sv->dlane.compute, cudaStreamNonBlocking));
         TP_TRY_CUDA(cudaStreamCreateWithFlags(&sv->dlane.copy, cudaStreamNonBlocking));
         TP_TRY_CUDA(cudaStreamCreateWithFlags(&sv->dlane.spill, cudaStreamNonBlocking));
-        TP_TRY_CUDA(cudaStreamCreateWithFlags(&sv->dlane.aux, cudaStreamNonBlocking));
         TP_TRY_CUDA(cudaHostAlloc((void**)&sv->dlane.host_words, 4096, cudaHostAllocDefault));
         for (Slot& sl : sv->slots) {
             TP_TRY_CUDA(cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking));

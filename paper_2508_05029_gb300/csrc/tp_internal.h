@@ -92,7 +92,6 @@ struct Lane {
     cudaStream_t compute = nullptr;
     cudaStream_t copy = nullptr;      // host -> device prefetch
     cudaStream_t spill = nullptr;     // device -> host spill copies (the other link direction)
-    cudaStream_t aux = nullptr;       // kernels that overlap the compute stream's (pipelined selection)
     uint64_t* host_words = nullptr;   // 4 KB pinned
 };
 
@@ -107,7 +106,6 @@ struct tp_engine {
     cudaStream_t compute = nullptr;
     cudaStream_t copy = nullptr;
     cudaStream_t spill = nullptr;
-    cudaStream_t aux = nullptr;
     bool own_compute = false;
     uint32_t copy_flags = 0;     // TP_COPY_* (tp_set_copy_options)
     std::mutex exec_mu;          // one execution at a time on the engine streams
