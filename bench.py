@@ -65,6 +65,8 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample-rows", type=int, default=20_000_000)
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary queries")
+    ap.add_argument("--legs", default="config1,highcard,star,hashed",
+                    help="secondary device-resident legs to run (comma list of config1, highcard, star, hashed)")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="fact-size scale of the 256-query batched and served mixes (1.0 = the full ~394M rows)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window per served rate")
@@ -947,10 +949,15 @@ def main():
 
     extra = {}
     if not args.no_extra:
-        extra["star-1M-lowcard"] = config1_measure(T, W, torch, dev, stream, peak, args.cpu_sample_rows > 0)
-        extra.update(highcard_measure(T, W, torch, dev, stream, eng, ft, dt, fact, dim, n_fact, peak))
-        extra["star-60M-two-dims"] = star_measure(T, W, torch, dev, stream, eng, fact, dt, n_fact, peak)
-        extra["star-60M-lowcard-hashed"] = hashed_join_measure(T, W, torch, dev, stream, n_fact, n_dim, peak)
+        legs = set(args.legs.split(","))
+        if "config1" in legs:
+            extra["star-1M-lowcard"] = config1_measure(T, W, torch, dev, stream, peak, args.cpu_sample_rows > 0)
+        if "highcard" in legs:
+            extra.update(highcard_measure(T, W, torch, dev, stream, eng, ft, dt, fact, dim, n_fact, peak))
+        if "star" in legs:
+            extra["star-60M-two-dims"] = star_measure(T, W, torch, dev, stream, eng, fact, dt, n_fact, peak)
+        if "hashed" in legs:
+            extra["star-60M-lowcard-hashed"] = hashed_join_measure(T, W, torch, dev, stream, n_fact, n_dim, peak)
     plan.destroy()
     ft.destroy()
     dt.destroy()

@@ -453,16 +453,19 @@ __global__ void __launch_bounds__(256) k_compact_global(const __grid_constant__ 
     for (uint64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
         uint32_t occ = 0;
         uint64_t key[COMPACT_PER];
+        ulonglong2 kc[COMPACT_PER];   // {key, count} of each slot, all loads in flight at once
+#pragma unroll
+        for (int i = 0; i < COMPACT_PER; ++i) {
+            const uint64_t s = ch * per_chunk + (uint64_t)i * 256 + threadIdx.x;
+            kc[i] = s < cap_with_side ? __ldcs((const ulonglong2*)(t.slots + s * t.words)) : make_ulonglong2(0, 0);
+        }
 #pragma unroll
         for (int i = 0; i < COMPACT_PER; ++i) {
             const uint64_t s = ch * per_chunk + (uint64_t)i * 256 + threadIdx.x;
             key[i] = 0;
-            if (s < cap_with_side) {
-                const uint64_t* p = t.slots + s * t.words;
-                if (p[1] != 0) {
-                    occ |= 1u << i;
-                    key[i] = (s == cap_with_side - 1) ? EMPTY64 : p[0];
-                }
+            if (kc[i].y != 0) {
+                occ |= 1u << i;
+                key[i] = (s == cap_with_side - 1) ? EMPTY64 : kc[i].x;
             }
         }
         // block-wide exclusive scan of the occupied counts
