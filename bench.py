@@ -66,7 +66,8 @@ def parse_args():
     ap.add_argument("--cpu-sample-rows", type=int, default=20_000_000)
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary queries")
     ap.add_argument("--legs", default="config1,highcard,star,hashed",
-                    help="secondary device-resident legs to run (comma list of config1, highcard, star, hashed)")
+                    help="secondary device-resident legs to run (comma list of config1, highcard, star, hashed; "
+                         "highcard-hashed runs only the hashed-table leg of highcard)")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="fact-size scale of the 256-query batched and served mixes (1.0 = the full ~394M rows)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="arrival window per served rate")
@@ -558,8 +559,9 @@ def outofcore_measure(T, W, torch, dev, n_fact, n_dim, budgets_gb, steps, link, 
             "slowdown_vs_default": sec * 1e3 / out[f"budget_{b:g}GB"]["ms_per_step"]}
         p.destroy()
     eng.set_copy_options(2, False)
-    out["ablations"]["managed_memory"] = ("not built: the join table in managed memory, paged between host and "
-                                          "device by the driver instead of partitioned and spilled")
+    out["ablations"]["managed_memory"] = ("measured on the headline query (e2e.managed_memory: fact columns in "
+                                          "managed memory, demand-paged or read in place, against the page pool); "
+                                          "a join table oversubscribing the GPU's memory is not created here")
     if lip_budget > 0:
         out["lookahead"] = lookahead_measure(T, W, torch, eng, ft, dt, nf, lip_budget, steps)
     ft.destroy()
@@ -801,6 +803,114 @@ def e2e_measure(T, W, torch, dev, stream, local, world, fact, dim, n_fact, n_dim
     return out
 
 
+def _cudart():
+    """The CUDA runtime library, for the managed-memory ablation only (the
+    library under test links its own runtime statically)."""
+    import ctypes
+    for name in ("libcudart.so.13", "libcudart.so", "/usr/local/cuda/lib64/libcudart.so.13"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            pass
+    return None
+
+
+def managed_measure(T, W, torch, dev, stream, local, fact, dim, n_fact, steps, link):
+    """Ablation of explicit staging against managed (UVM) memory (the paper's
+    Section 5 finds the latter far slower): the headline query over fact
+    columns in managed memory, (a) on the device (prefetched there first),
+    (b) moved back to the host before each step (outside the timed region)
+    and migrated by demand paging as the kernel reads them, (c) kept on the
+    host (preferred location the host, mapped for the device) and read in
+    place over the link.  Plain-load kernels throughout (TP_FLAG_NO_STAGED):
+    page faults are taken by ordinary loads.  The GPU's memory is not
+    oversubscribed: that would take filling a shared GPU's memory."""
+    import ctypes
+    rt = _cudart()
+    if rt is None:
+        return "unavailable: no CUDA runtime library to allocate managed memory"
+
+    class Loc(ctypes.Structure):
+        _fields_ = [("type", ctypes.c_int), ("id", ctypes.c_int)]
+
+    rt.cudaMallocManaged.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t, ctypes.c_uint]
+    rt.cudaMemPrefetchAsync.argtypes = [ctypes.c_void_p, ctypes.c_size_t, Loc, ctypes.c_uint, ctypes.c_void_p]
+    rt.cudaMemAdvise.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, Loc]
+    rt.cudaFree.argtypes = [ctypes.c_void_p]
+    LOC_DEVICE, LOC_HOST = 1, 2
+    ADVISE_PREFERRED, ADVISE_ACCESSED_BY = 3, 5
+
+    def ok(rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what} returned CUDA error {rc}")
+
+    ok(rt.cudaSetDevice(local), "cudaSetDevice")
+    host, on_dev = Loc(LOC_HOST, 0), Loc(LOC_DEVICE, local)
+    allocs, cols = [], {}
+    eng = ft = dt = plan = None
+    try:
+        for name, arr in fact.items():
+            p = ctypes.c_void_p()
+            ok(rt.cudaMallocManaged(ctypes.byref(p), max(arr.nbytes, 16), 1), "cudaMallocManaged")
+            allocs.append((p.value, arr.nbytes))
+            ctypes.memmove(p.value, arr.ctypes.data, arr.nbytes)   # first touch on the host
+            cols[name] = (p.value, arr.dtype)
+        eng = T.Engine(compute_stream=stream.cuda_stream, flags=T.TP_FLAG_NO_STAGED, cuda_device=local)
+        dt = eng.table_from_torch({k: torch.from_numpy(v).to(dev) for k, v in dim.items()})
+        ft = eng.table_from_pointers(cols, n_fact)
+        plan = eng.plan(ft, dt, W.q_lowcard())
+        fact_bytes = BYTES_PER_FACT_ROW * n_fact   # the columns the query reads
+
+        def move(loc):
+            for a, nb in allocs:
+                ok(rt.cudaMemPrefetchAsync(a, nb, loc, 0, ctypes.c_void_p(stream.cuda_stream)), "cudaMemPrefetchAsync")
+            torch.cuda.synchronize()
+
+        def run():
+            with plan.execute() as r:
+                return r.keys().copy(), r.counts().copy()
+
+        def timed(before):
+            times, res = [], None
+            for _ in range(steps):
+                before()
+                t0 = time.perf_counter()
+                res = run()
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+            sec = statistics.median(times)
+            return {"ms_per_step": sec * 1e3, "fact_rows_per_s": n_fact / sec,
+                    "fact_gbs": fact_bytes / sec / 1e9}, res
+
+        move(on_dev)
+        run()
+        out = {"fact_bytes_read": fact_bytes, "managed_bytes": sum(nb for _, nb in allocs),
+               "kernels": "plain loads (TP_FLAG_NO_STAGED)", "link_peak_gbs": link}
+        out["device_resident"], ref = timed(lambda: None)
+        out["demand_paging"], res = timed(lambda: move(host))
+        same = all(np.array_equal(a, b) for a, b in zip(ref, res))
+        for a, nb in allocs:
+            ok(rt.cudaMemAdvise(a, nb, ADVISE_PREFERRED, host), "cudaMemAdvise")
+            ok(rt.cudaMemAdvise(a, nb, ADVISE_ACCESSED_BY, on_dev), "cudaMemAdvise")
+        move(host)
+        out["host_resident_mapped"], res = timed(lambda: None)
+        same = same and all(np.array_equal(a, b) for a, b in zip(ref, res))
+        out["results_match"] = bool(same)
+        for k in ("demand_paging", "host_resident_mapped"):
+            out[k]["link_frac"] = out[k]["fact_gbs"] / link
+            out[k]["slowdown_vs_device"] = out[k]["ms_per_step"] / out["device_resident"]["ms_per_step"]
+        return out
+    finally:
+        for h in (plan, ft, dt):
+            if h is not None:
+                h.destroy()
+        if eng is not None:
+            eng.close()
+        torch.cuda.synchronize()
+        for a, _ in allocs:
+            rt.cudaFree(ctypes.c_void_p(a))
+
+
 def config1_measure(T, W, torch, dev, stream, peak, with_cpu=True, reps=50):
     """Config 1: 1M fact rows, 10k-row dimension, device-resident, one batch.
     At 34 MB of input (about 5 us of HBM traffic) the query is bound by
@@ -829,7 +939,7 @@ def config1_measure(T, W, torch, dev, stream, peak, with_cpu=True, reps=50):
     return out
 
 
-def highcard_measure(T, W, torch, dev, stream, eng, ft, dt, fact, dim, n_fact, peak):
+def highcard_measure(T, W, torch, dev, stream, eng, ft, dt, fact, dim, n_fact, peak, only_hashed=False):
     """Config 2b (1%-selective date range, group by order key: about 600k
     groups), 2b' (the same at ~98%: 15M groups) with the direct-addressed
     table the dense order keys allow, and 2b' with the hashed table (sparse
@@ -846,6 +956,8 @@ def highcard_measure(T, W, torch, dev, stream, eng, ft, dt, fact, dim, n_fact, p
             ("star-60M-highcard-1pct", W.q_highcard(lo, lo + W.RANGE_1PCT), eng, ft, dt),
             ("star-60M-highcard-98pct", W.q_highcard(0, W.CUTOFF_98), eng, ft, dt),
             ("star-60M-highcard-98pct-hashed", W.q_highcard(0, W.CUTOFF_98), engh, fth, dth)):
+        if only_hashed and e is not engh:
+            continue
         p = e.plan(f_t, d_t, q)
         ms, kms, groups, joined = time_plan(torch, stream, e, p, reps=5)
         alg = 4 * n_fact + 28 * joined + 32 * groups
@@ -952,8 +1064,9 @@ def main():
         legs = set(args.legs.split(","))
         if "config1" in legs:
             extra["star-1M-lowcard"] = config1_measure(T, W, torch, dev, stream, peak, args.cpu_sample_rows > 0)
-        if "highcard" in legs:
-            extra.update(highcard_measure(T, W, torch, dev, stream, eng, ft, dt, fact, dim, n_fact, peak))
+        if "highcard" in legs or "highcard-hashed" in legs:
+            extra.update(highcard_measure(T, W, torch, dev, stream, eng, ft, dt, fact, dim, n_fact, peak,
+                                          only_hashed="highcard" not in legs))
         if "star" in legs:
             extra["star-60M-two-dims"] = star_measure(T, W, torch, dev, stream, eng, fact, dt, n_fact, peak)
         if "hashed" in legs:
@@ -972,6 +1085,8 @@ def main():
         raw = e2e_measure(T, W, torch, dev, stream, local, world, fact, dim, n_fact, n_dim, args.e2e_steps, link,
                           T.TP_FLAG_RAW_PAGES)
         e2e["raw_pages"] = {k: raw[k] for k in ("value", "unit", "link_frac", "h2d_bytes_per_step", "h2d_gbs")}
+        if rank == 0 and world == 1:
+            e2e["managed_memory"] = managed_measure(T, W, torch, dev, stream, local, fact, dim, n_fact, 3, link)
 
     if not args.no_outofcore and rank == 0:
         link_ooc = e2e["link_peak_gbs"] if e2e else link_peak_gbs(dev)

@@ -14,6 +14,8 @@
 // definition of dispatch_probe: a switch on the shape id calling
 // probe_tile<JS_id>.
 #pragma once
+// build tasks write the join tables earlier in the same launch
+#define TP_TABLES_BUILT_IN_LAUNCH 1
 #include "jit_common.cuh"
 
 namespace tpj {

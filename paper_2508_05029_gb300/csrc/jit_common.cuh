@@ -32,6 +32,9 @@
 // table's word layout) come from the launch, so one compiled kernel serves
 // every plan and batch of the same shape.
 #pragma once
+// run-time compiled kernels have the registers to hold every row's probe
+// sector at once
+#define TP_PROBE_LOADS_FIRST 1
 #include "pipeline.cuh"
 
 namespace tpj {
@@ -247,7 +250,7 @@ __device__ __forceinline__ void further_joins(const QueryDev& q, const C& c, uin
 #pragma unroll
             for (int j = 0; j < ST_RPL; ++j) {
                 const uint64_t idx = (uint64_t)(key[j] - jt.kmin);
-                pay[j] = ((pm >> j) & 1u) && idx < jt.range ? __ldg((const unsigned int*)jt.slots + idx) : EMPTY32;
+                pay[j] = ((pm >> j) & 1u) && idx < jt.range ? TP_LDT((const unsigned int*)jt.slots + idx) : EMPTY32;
             }
 #pragma unroll
             for (int j = 0; j < ST_RPL; ++j)
@@ -306,7 +309,7 @@ __device__ __forceinline__ void consume(const QueryDev& q, const Flt& flt, const
 #pragma unroll
         for (int j = 0; j < ST_RPL; ++j) {
             const uint64_t idx = (uint64_t)((int64_t)c.template ld<S::ktype, CI_K>(r0, j) - q.jt.kmin);
-            pay[j] = ((pm >> j) & 1u) && idx < q.jt.range ? __ldg(dt + idx) : EMPTY32;
+            pay[j] = ((pm >> j) & 1u) && idx < q.jt.range ? TP_LDT(dt + idx) : EMPTY32;
         }
 #pragma unroll
         for (int j = 0; j < ST_RPL; ++j)
@@ -353,7 +356,7 @@ __device__ __forceinline__ void consume(const QueryDev& q, const Flt& flt, const
             for (int j = 0; j < ST_RPL; ++j) {
                 if (!((live >> j) & 1u)) continue;
                 const uint64_t at = (uint64_t)first[j] + m;
-                if (at < q.jt.mn && __ldg(q.jt.mkeys + at) == (uint64_t)key[j]) pay[j] = __ldg(q.jt.mpay + at);
+                if (at < q.jt.mn && TP_LDT(q.jt.mkeys + at) == (uint64_t)key[j]) pay[j] = TP_LDT(q.jt.mpay + at);
                 else live &= ~(1u << j);
             }
             uint32_t pmm = live, bad = 0;

@@ -514,18 +514,61 @@ cudaError_t launch_compact_global(const AggTable& t, uint64_t cap_with_side, uin
     return cudaGetLastError();
 }
 
-__global__ void k_gather_global(const __grid_constant__ AggTable t, const uint64_t* __restrict__ skeys,
-                                const uint32_t* __restrict__ sidx, uint64_t n, int n_sum,
-                                const __grid_constant__ OutDev o, int lo_only) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t* p = t.slots + (uint64_t)sidx[i] * t.words;
-        uint64_t lh[2 * MAX_SUM];
-        for (int s = 0; s < n_sum; ++s) {
-            lh[2 * s] = p[2 + 2 * s];
-            lh[2 * s + 1] = lo_only ? (uint64_t)((int64_t)lh[2 * s] >> 63) : p[3 + 2 * s];
+// Rows of the sorted output: GATHER_PER rows per thread, every index and key
+// load, then every slot load, in flight before the first row is written.  A
+// 32-byte slot (one sum) is read with one 256-bit load (sm_100 and later):
+// a random slot then costs one L1 lookup per lane instead of three.
+constexpr int GATHER_PER = 4;
+
+__device__ __forceinline__ void ld_slot4(const uint64_t* p, uint64_t (&w)[4]) {
+    asm("ld.global.nc.v4.u64 {%0,%1,%2,%3}, [%4];" : "=l"(w[0]), "=l"(w[1]), "=l"(w[2]), "=l"(w[3]) : "l"(p));
+}
+
+__global__ void __launch_bounds__(256) k_gather_global(const __grid_constant__ AggTable t,
+                                                       const uint64_t* __restrict__ skeys,
+                                                       const uint32_t* __restrict__ sidx, uint64_t n, int n_sum,
+                                                       const __grid_constant__ OutDev o, int lo_only) {
+    const bool v4 = t.words == 4 && ((uintptr_t)t.slots & 31u) == 0;
+    const uint64_t per = (uint64_t)GATHER_PER * blockDim.x;
+    for (uint64_t b = blockIdx.x * per; b < n; b += (uint64_t)gridDim.x * per) {
+        uint64_t key[GATHER_PER];
+        uint32_t at[GATHER_PER];
+#pragma unroll
+        for (int r = 0; r < GATHER_PER; ++r) {
+            const uint64_t i = b + (uint64_t)r * blockDim.x + threadIdx.x;
+            at[r] = 0;
+            key[r] = 0;
+            if (i < n) {
+                at[r] = sidx[i];
+                key[r] = skeys[i];
+            }
         }
-        write_row(o, i, skeys[i], p[1], lh, n_sum);
+        if (v4) {
+            uint64_t w[GATHER_PER][4];
+#pragma unroll
+            for (int r = 0; r < GATHER_PER; ++r)
+                if (b + (uint64_t)r * blockDim.x + threadIdx.x < n) ld_slot4(t.slots + (uint64_t)at[r] * 4, w[r]);
+#pragma unroll
+            for (int r = 0; r < GATHER_PER; ++r) {
+                const uint64_t i = b + (uint64_t)r * blockDim.x + threadIdx.x;
+                if (i >= n) continue;
+                const uint64_t lh[2] = {w[r][2], lo_only ? (uint64_t)((int64_t)w[r][2] >> 63) : w[r][3]};
+                write_row(o, i, key[r], w[r][1], lh, 1);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < GATHER_PER; ++r) {
+                const uint64_t i = b + (uint64_t)r * blockDim.x + threadIdx.x;
+                if (i >= n) continue;
+                const uint64_t* p = t.slots + (uint64_t)at[r] * t.words;
+                uint64_t lh[2 * MAX_SUM];
+                for (int s = 0; s < n_sum; ++s) {
+                    lh[2 * s] = p[2 + 2 * s];
+                    lh[2 * s + 1] = lo_only ? (uint64_t)((int64_t)lh[2 * s] >> 63) : p[3 + 2 * s];
+                }
+                write_row(o, i, key[r], p[1], lh, n_sum);
+            }
+        }
     }
 }
 
@@ -533,7 +576,7 @@ cudaError_t launch_gather_global(const AggTable& t, const uint64_t* sorted_keys,
                                  const uint32_t* sorted_idx, uint64_t n, int n_sum, const OutDev& o,
                                  int num_sms, cudaStream_t st, bool lo_only) {
     if (n == 0) return cudaSuccess;
-    uint64_t blocks = (n + 255) / 256;
+    uint64_t blocks = (n + GATHER_PER * 256 - 1) / (GATHER_PER * 256);
     uint64_t cap = (uint64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;
     k_gather_global<<<(unsigned)blocks, 256, 0, st>>>(t, sorted_keys, sorted_idx, n, n_sum, o, lo_only ? 1 : 0);

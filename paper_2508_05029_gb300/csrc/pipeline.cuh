@@ -86,6 +86,28 @@ __device__ __forceinline__ void load8_smem(const unsigned char* base, int type, 
     }
 }
 
+// Reads of join tables.  Tables built by an earlier launch are read-only for
+// the probing kernel and go through the non-coherent path; a kernel that
+// builds its tables itself before probing them (the batched queue defines
+// TP_TABLES_BUILT_IN_LAUNCH) reads them with ordinary loads, which its
+// dependency waits' fences order after the build.
+#ifdef TP_TABLES_BUILT_IN_LAUNCH
+#define TP_LDT(p) (*(p))
+#else
+#define TP_LDT(p) __ldg(p)
+#endif
+
+// The four 8-byte words of the aligned 32-byte sector at p, as two 128-bit
+// loads.  (One 256-bit load, available from sm_100 on, measured slower in
+// the probe loop.)
+__device__ __forceinline__ void ld_sector(const uint64_t* p, uint64_t (&w)[4]) {
+    const ulonglong2 lo = TP_LDT((const ulonglong2*)p), hi = TP_LDT((const ulonglong2*)p + 1);
+    w[0] = lo.x;
+    w[1] = lo.y;
+    w[2] = hi.x;
+    w[3] = hi.y;
+}
+
 // Batched join probes, one aligned 32-byte sector ("bucket") per round.
 //
 // The table is filled by slot-wise linear probing from hash & mask.  A lookup
@@ -95,8 +117,21 @@ __device__ __forceinline__ void load8_smem(const unsigned char* base, int type, 
 // an empty slot ends the search.  Slots before the starting position in the
 // first sector belong to other probe sequences and are skipped.  A lane's
 // rows advance independently, so a round costs one sector load per live row
-// and most lookups finish in the first round.  pm loses the rows whose key
-// is absent; pay receives the payload of the others.
+// and most lookups finish in the first round.
+//
+// With TP_PROBE_LOADS_FIRST (the run-time compiled kernels, which have the
+// registers for it) each round first issues the sector loads of all of the
+// lane's live rows and only then examines them, so the rows' L2 round trips
+// overlap instead of following one another: 10% off the hashed star query's
+// kernel.  The ahead-of-time staged kernels run at their register cap, where
+// holding every row's sector spilled to local memory, so they examine each
+// row's sector as it arrives.  (A window of two sectors per round halves the
+// rounds a 64-row warp needs, but measured slower: doubling the probe's L2
+// traffic cost more than the round trips it saved.)  pm loses the rows whose
+// key is absent; pay receives the payload of the others.
+#ifndef TP_PROBE_LOADS_FIRST
+#define TP_PROBE_LOADS_FIRST 0
+#endif
 
 __device__ __forceinline__ void probe_rows_k32(const JoinTable& jt, const int64_t key[ST_RPL], uint32_t& pm,
                                                uint32_t pay[ST_RPL], uint32_t* err) {
@@ -111,37 +146,65 @@ __device__ __forceinline__ void probe_rows_k32(const JoinTable& jt, const int64_
         pay[j] = 0;
         if (!in32) pm &= ~(1u << j);
         if (in32 && k[j] == EMPTY32) {  // the key equal to the empty pattern lives in the side cell
-            if (__ldg(jt.side) != 0) pay[j] = __ldg(jt.side + 1);
+            if (TP_LDT(jt.side) != 0) pay[j] = TP_LDT(jt.side + 1);
             else pm &= ~(1u << j);
         } else if (pm & (1u << j)) {
             act |= 1u << j;
         }
     }
-    const ulonglong2* sectors = (const ulonglong2*)jt.slots;
     for (uint32_t it = 0; act && it <= mask; it += 4) {
+        if constexpr (TP_PROBE_LOADS_FIRST) {
+            const uint32_t live = act;
+            uint64_t w[ST_RPL][4];
 #pragma unroll
-        for (int j = 0; j < ST_RPL; ++j) {
-            if (!(act & (1u << j))) continue;
-            const uint32_t base = pos[j] & ~3u;
-            const ulonglong2 lo = __ldg(sectors + (base >> 1));
-            const ulonglong2 hi = __ldg(sectors + (base >> 1) + 1);
-            const uint64_t w[4] = {lo.x, lo.y, hi.x, hi.y};
-            const uint32_t first = pos[j] & 3u;
-            bool done = false;
+            for (int j = 0; j < ST_RPL; ++j)
+                if (live & (1u << j)) ld_sector(jt.slots + (pos[j] & ~3u), w[j]);
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                if (done || (uint32_t)m < first) continue;
-                const uint32_t wk = (uint32_t)w[m];
-                if (wk == k[j]) {
-                    pay[j] = (uint32_t)(w[m] >> 32);
-                    done = true;
-                } else if (wk == EMPTY32) {
-                    pm &= ~(1u << j);
-                    done = true;
+            for (int j = 0; j < ST_RPL; ++j) {
+                if (!(live & (1u << j))) continue;
+                const uint32_t first = pos[j] & 3u;
+                bool done = false;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (done || (uint32_t)m < first) continue;
+                    const uint32_t wk = (uint32_t)w[j][m];
+                    if (wk == k[j]) {
+                        pay[j] = (uint32_t)(w[j][m] >> 32);
+                        done = true;
+                    } else if (wk == EMPTY32) {
+                        pm &= ~(1u << j);
+                        done = true;
+                    }
                 }
+                if (done) act &= ~(1u << j);
+                else pos[j] = ((pos[j] & ~3u) + 4) & mask;
             }
-            if (done) act &= ~(1u << j);
-            else pos[j] = (base + 4) & mask;
+        } else {
+            const ulonglong2* sectors = (const ulonglong2*)jt.slots;
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) {
+                if (!(act & (1u << j))) continue;
+                const uint32_t base = pos[j] & ~3u;
+                const ulonglong2 lo = TP_LDT(sectors + (base >> 1));
+                const ulonglong2 hi = TP_LDT(sectors + (base >> 1) + 1);
+                const uint64_t w[4] = {lo.x, lo.y, hi.x, hi.y};
+                const uint32_t first = pos[j] & 3u;
+                bool done = false;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (done || (uint32_t)m < first) continue;
+                    const uint32_t wk = (uint32_t)w[m];
+                    if (wk == k[j]) {
+                        pay[j] = (uint32_t)(w[m] >> 32);
+                        done = true;
+                    } else if (wk == EMPTY32) {
+                        pm &= ~(1u << j);
+                        done = true;
+                    }
+                }
+                if (done) act &= ~(1u << j);
+                else pos[j] = (base + 4) & mask;
+            }
         }
     }
     if (act) {
@@ -161,41 +224,79 @@ __device__ __forceinline__ void probe_rows_k64(const JoinTable& jt, const int64_
         pos[j] = (uint32_t)fmix64((uint64_t)key[j]) & mask;
         if (!(pm & (1u << j))) continue;
         if ((uint64_t)key[j] == EMPTY64) {
-            if (__ldg(jt.side) != 0) pay[j] = __ldg(jt.side + 1);
+            if (TP_LDT(jt.side) != 0) pay[j] = TP_LDT(jt.side + 1);
             else pm &= ~(1u << j);
             continue;
         }
         act |= 1u << j;
     }
-    const ulonglong2* slots = (const ulonglong2*)jt.slots;
     for (uint32_t it = 0; act && it <= mask; it += 2) {
+        if constexpr (TP_PROBE_LOADS_FIRST) {
+            const uint32_t live = act;
+            ulonglong2 s0[ST_RPL], s1[ST_RPL];
+            const ulonglong2* slots = (const ulonglong2*)jt.slots;
 #pragma unroll
-        for (int j = 0; j < ST_RPL; ++j) {
-            if (!(act & (1u << j))) continue;
-            const uint32_t base = pos[j] & ~1u;
-            const ulonglong2 s0 = __ldg(slots + base);
-            const ulonglong2 s1 = __ldg(slots + base + 1);
-            bool done = false;
-            if ((pos[j] & 1u) == 0) {
-                if (s0.x == (uint64_t)key[j]) {
-                    pay[j] = (uint32_t)s0.y;
-                    done = true;
-                } else if (s0.x == EMPTY64) {
-                    pm &= ~(1u << j);
-                    done = true;
-                }
+            for (int j = 0; j < ST_RPL; ++j) {
+                if (!(live & (1u << j))) continue;
+                const uint32_t base = pos[j] & ~1u;
+                s0[j] = TP_LDT(slots + base);
+                s1[j] = TP_LDT(slots + base + 1);
             }
-            if (!done) {
-                if (s1.x == (uint64_t)key[j]) {
-                    pay[j] = (uint32_t)s1.y;
-                    done = true;
-                } else if (s1.x == EMPTY64) {
-                    pm &= ~(1u << j);
-                    done = true;
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) {
+                if (!(live & (1u << j))) continue;
+                bool done = false;
+                if ((pos[j] & 1u) == 0) {
+                    if (s0[j].x == (uint64_t)key[j]) {
+                        pay[j] = (uint32_t)s0[j].y;
+                        done = true;
+                    } else if (s0[j].x == EMPTY64) {
+                        pm &= ~(1u << j);
+                        done = true;
+                    }
                 }
+                if (!done) {
+                    if (s1[j].x == (uint64_t)key[j]) {
+                        pay[j] = (uint32_t)s1[j].y;
+                        done = true;
+                    } else if (s1[j].x == EMPTY64) {
+                        pm &= ~(1u << j);
+                        done = true;
+                    }
+                }
+                if (done) act &= ~(1u << j);
+                else pos[j] = ((pos[j] & ~1u) + 2) & mask;
             }
-            if (done) act &= ~(1u << j);
-            else pos[j] = (base + 2) & mask;
+        } else {
+            const ulonglong2* slots = (const ulonglong2*)jt.slots;
+#pragma unroll
+            for (int j = 0; j < ST_RPL; ++j) {
+                if (!(act & (1u << j))) continue;
+                const uint32_t base = pos[j] & ~1u;
+                const ulonglong2 s0 = TP_LDT(slots + base);
+                const ulonglong2 s1 = TP_LDT(slots + base + 1);
+                bool done = false;
+                if ((pos[j] & 1u) == 0) {
+                    if (s0.x == (uint64_t)key[j]) {
+                        pay[j] = (uint32_t)s0.y;
+                        done = true;
+                    } else if (s0.x == EMPTY64) {
+                        pm &= ~(1u << j);
+                        done = true;
+                    }
+                }
+                if (!done) {
+                    if (s1.x == (uint64_t)key[j]) {
+                        pay[j] = (uint32_t)s1.y;
+                        done = true;
+                    } else if (s1.x == EMPTY64) {
+                        pm &= ~(1u << j);
+                        done = true;
+                    }
+                }
+                if (done) act &= ~(1u << j);
+                else pos[j] = (base + 2) & mask;
+            }
         }
     }
     if (act) {
@@ -219,7 +320,7 @@ __device__ __forceinline__ void probe_rows(const JoinTable& jt, const int64_t ke
 #pragma unroll
         for (int j = 0; j < ST_RPL; ++j) {
             const uint64_t idx = (uint64_t)key[j] - (uint64_t)jt.kmin;
-            w[j] = ((pm >> j) & 1u) && idx < jt.range ? __ldg((const unsigned int*)jt.slots + idx) : EMPTY32;
+            w[j] = ((pm >> j) & 1u) && idx < jt.range ? TP_LDT((const unsigned int*)jt.slots + idx) : EMPTY32;
         }
 #pragma unroll
         for (int j = 0; j < ST_RPL; ++j) {

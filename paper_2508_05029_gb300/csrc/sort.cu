@@ -6,11 +6,13 @@
 //      digit-major (hist[d * tiles + tile]) so that one exclusive scan over the
 //      whole array yields every (digit, tile) output offset;
 //   2. an exclusive scan of that array (k_scan_*);
-//   3. k_digit_scatter: every warp ranks its 512 pairs in input order with
-//      __match_any_sync on the digit, so equal digits keep their order and the
-//      pass is stable; the tile's pairs are first placed digit-ordered in
-//      shared memory, then written out so that consecutive threads write
-//      consecutive slots of each digit's output run (coalesced stores).
+//   3. k_digit_scatter: every warp ranks its 512 pairs in input order by the
+//      set of lanes holding the same digit (built from nine ballots, which
+//      measured faster here than __match_any_sync: 2.91 vs 3.13 ms for the
+//      hashed 15M-group query), so equal digits keep their order and the pass
+//      is stable; the tile's pairs are first placed digit-ordered in shared
+//      memory, then written out so that consecutive threads write consecutive
+//      slots of each digit's output run (coalesced stores).
 #include "kernels.cuh"
 
 namespace tpk {
@@ -128,9 +130,23 @@ __global__ void __launch_bounds__(SORT_THREADS) k_digit_hist(const uint64_t* __r
     for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(uint64_t)d * tiles + blockIdx.x] = cnt[d];
 }
 
+// The lanes of the warp whose 9-bit digit (256 marks "no pair") equals this
+// lane's, from nine ballots: the set __match_any_sync would return.
+__device__ __forceinline__ unsigned digit_peers(uint32_t d) {
+    unsigned m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        m &= ((d >> b) & 1u) ? bal : ~bal;
+    }
+    return m;
+}
+
 // dynamic shared memory of k_digit_scatter: the tile's keys and values in
-// digit order, per-warp digit positions, per-digit tile-local starts
-constexpr size_t SCATTER_SMEM = (size_t)SORT_TILE * 8 + (size_t)SORT_TILE * 4 + SORT_WARPS * 257 * 4 + 257 * 4;
+// digit order, per-warp digit positions, per-digit tile-local starts, per-digit
+// output shifts (global position of slot i = shift[digit] + i)
+constexpr size_t SCATTER_SMEM =
+    (size_t)SORT_TILE * 8 + (size_t)SORT_TILE * 4 + SORT_WARPS * 257 * 4 + 257 * 4 + 4 + 256 * 8;
 
 __global__ void __launch_bounds__(SORT_THREADS) k_digit_scatter(
     const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
@@ -141,6 +157,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_digit_scatter(
     uint32_t* sv = (uint32_t*)(sk + SORT_TILE);                     // [SORT_TILE]
     uint32_t (*wpos)[257] = (uint32_t (*)[257])(sv + SORT_TILE);    // [SORT_WARPS][257]
     uint32_t* start = &wpos[SORT_WARPS - 1][0] + 257;               // [257]
+    unsigned long long* shift_out = (unsigned long long*)(start + 257 + 1);   // [256], 8-byte aligned
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < SORT_WARPS * 257; i += blockDim.x) (&wpos[0][0])[i] = 0;
     __syncthreads();
@@ -161,11 +178,13 @@ __global__ void __launch_bounds__(SORT_THREADS) k_digit_scatter(
             d[r] = 256;  // past the end: counted nowhere
         }
     }
-    // per-warp digit counts
+    // per-warp digit counts; each round's set of lanes with equal digits is
+    // kept for the placement below
+    unsigned peers[SORT_ROUNDS];
 #pragma unroll
     for (int r = 0; r < SORT_ROUNDS; ++r) {
-        const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
-        if (d[r] < 256 && lane == __ffs(peers) - 1) wpos[warp][d[r]] += __popc(peers);
+        peers[r] = digit_peers(d[r]);
+        if (d[r] < 256 && lane == __ffs(peers[r]) - 1) wpos[warp][d[r]] += __popc(peers[r]);
         __syncwarp();
     }
     __syncthreads();
@@ -180,6 +199,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_digit_scatter(
         uint32_t run = block_excl_scan(tot, scan_buf, &all);
         start[dg] = run;
         if (dg == 0) start[256] = all;
+        shift_out[dg] = (unsigned long long)offsets[(uint64_t)dg * tiles + blockIdx.x] - run;
         for (int w = 0; w < SORT_WARPS; ++w) {
             const uint32_t c = wpos[w][dg];
             wpos[w][dg] = run;
@@ -190,14 +210,13 @@ __global__ void __launch_bounds__(SORT_THREADS) k_digit_scatter(
     const unsigned below = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < SORT_ROUNDS; ++r) {
-        const unsigned peers = __match_any_sync(0xffffffffu, d[r]);
         if (d[r] < 256) {
-            const uint32_t pos = wpos[warp][d[r]] + __popc(peers & below);
+            const uint32_t pos = wpos[warp][d[r]] + __popc(peers[r] & below);
             sk[pos] = k[r];
             sv[pos] = v[r];
         }
         __syncwarp();
-        if (d[r] < 256 && lane == __ffs(peers) - 1) wpos[warp][d[r]] += __popc(peers);
+        if (d[r] < 256 && lane == __ffs(peers[r]) - 1) wpos[warp][d[r]] += __popc(peers[r]);
         __syncwarp();
     }
     __syncthreads();
@@ -205,8 +224,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_digit_scatter(
     const uint32_t count = start[256];
     for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) {
         const uint64_t key = sk[i];
-        const uint32_t dg = (uint32_t)((key >> shift) & 255u);
-        const uint64_t pos = (uint64_t)offsets[(uint64_t)dg * tiles + blockIdx.x] + (i - start[dg]);
+        const uint64_t pos = shift_out[(key >> shift) & 255u] + i;
         keys_out[pos] = key;
         vals_out[pos] = sv[i];
     }

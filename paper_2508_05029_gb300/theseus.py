@@ -324,6 +324,16 @@ class Engine:
         t._tensors = ts
         return t
 
+    def table_from_pointers(self, columns: dict, nrows: int) -> "Table":
+        """Registers device-accessible memory without copying: columns maps a
+        name to (address, numpy dtype); the memory must outlive the table."""
+        names = list(columns)
+        d, keep = self._desc(names, [np.dtype(columns[n][1]) for n in names])
+        ptrs = (ctypes.c_void_p * len(names))(*[int(columns[n][0]) for n in names])
+        h = ctypes.c_void_p()
+        _check(self.lib.tp_table_wrap_device(self.h, ctypes.byref(d), ptrs, nrows, ctypes.byref(h)))
+        return Table(self, h, names)
+
     def plan(self, fact: "Table", dim: "Table | None", query: dict, agg_strategy=TP_AGG_AUTO,
              load_factor=0.0, expected_groups=0, join_partitions=0, lip=TP_LIP_AUTO,
              extra_dims=None) -> "Plan":
