@@ -138,77 +138,6 @@ __device__ __forceinline__ void consume_global(const QueryDev& q, const StageLay
     agg_warp_rows<NS, FAST, ST_RPL>(tab, q.err, q.n_sum, valid, key, t, tm, claims);
 }
 
-// One stage's surviving rows of this lane whose table update was put off to
-// the next stage (FAST sums only): the home slots of their keys were
-// prefetched into L2 when they were read, so by the time they are updated a
-// stage's worth of work has covered the DRAM latency of a slot of a table
-// larger than L2.
-template <int NS>
-struct Deferred {
-    uint64_t key[ST_RPL];
-    int64_t t[NS > 0 ? NS : 1][ST_RPL];
-    uint32_t pm;
-};
-
-// The rows deferred from the previous stage update the table (every lane of
-// the warp calls it).
-template <int NS>
-__device__ __forceinline__ void flush_deferred(const QueryDev& q, const AggTable& tab, const Deferred<NS>& d,
-                                               uint32_t& claims) {
-    if (__ballot_sync(0xffffffffu, d.pm != 0) == 0) return;   // warp-uniform
-    bool valid[ST_RPL];
-#pragma unroll
-    for (int j = 0; j < ST_RPL; ++j) valid[j] = (d.pm >> j) & 1u;
-    I128 tm[NS > 0 ? NS : 1][ST_RPL];   // unused by 64-bit updates
-    int64_t t[NS > 0 ? NS : 1][ST_RPL];
-#pragma unroll
-    for (int s = 0; s < (NS > 0 ? NS : 1); ++s)
-#pragma unroll
-        for (int j = 0; j < ST_RPL; ++j) t[s][j] = d.t[s][j];
-    uint64_t key[ST_RPL];
-#pragma unroll
-    for (int j = 0; j < ST_RPL; ++j) key[j] = d.key[j];
-    agg_warp_rows<NS, true, ST_RPL>(tab, q.err, q.n_sum, valid, key, t, tm, claims);
-}
-
-// consume_global with the table update put off by one stage: this stage's
-// rows are evaluated, their home slots prefetched into L2 (hashed table) and
-// kept in registers, and the previous stage's rows update the table.
-template <int NS>
-__device__ __forceinline__ void consume_global_deferred(const QueryDev& q, const StageLayout& L, const AggTable& tab,
-                                                        const unsigned char* stage, uint64_t row0, uint32_t r0,
-                                                        Deferred<NS>& d, uint32_t& claims) {
-    uint64_t key[ST_RPL];
-    const uint32_t pm = eval_keys64(q, L, stage, row0, r0, key);
-    int64_t t[NS > 0 ? NS : 1][ST_RPL];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        if (s >= q.n_sum) break;
-        eval_terms64(q, L, s, stage, row0, r0, pm, t[s]);
-    }
-    if (!tab.direct) {
-#pragma unroll
-        for (int j = 0; j < ST_RPL; ++j)
-            if ((pm >> j) & 1u) {
-                const uint64_t* home = tab.slots + (fmix64(key[j]) & tab.mask) * tab.words;
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(home));
-            }
-    }
-    flush_deferred<NS>(q, tab, d, claims);
-#pragma unroll
-    for (int j = 0; j < ST_RPL; ++j) d.key[j] = key[j];
-#pragma unroll
-    for (int s = 0; s < NS; ++s)
-#pragma unroll
-        for (int j = 0; j < ST_RPL; ++j) d.t[s][j] = t[s][j];
-    d.pm = pm;
-}
-
-// Deferral is used for 64-bit sums of up to two sums per row, where the
-// deferred rows fit in a few registers.
-template <int NS, bool FAST>
-constexpr bool kDeferGlobal = FAST && NS <= 2;
-
 template <int NS, bool FAST>
 __global__ void __launch_bounds__(ST_THREADS, ST_CTAS)
     k_agg_global_staged(const __grid_constant__ QueryDev q, const __grid_constant__ StageLayout L, uint64_t n,
@@ -218,20 +147,9 @@ __global__ void __launch_bounds__(ST_THREADS, ST_CTAS)
     unsigned int* cta_claims = (unsigned int*)smem;
     if (threadIdx.x == 0) *cta_claims = 0;
     uint32_t claims = 0;
-    if constexpr (kDeferGlobal<NS, FAST>) {
-        Deferred<NS> d;
-        d.pm = 0;
-        run_pipeline(q, L, n, smem + GLOBAL_RING_OFFSET,
-                     [&](const unsigned char* stage, uint64_t row0, uint32_t r0) {
-                         consume_global_deferred<NS>(q, L, tab, stage, row0, r0, d, claims);
-                     });
-        if (threadIdx.x >= 32) flush_deferred<NS>(q, tab, d, claims);
-    } else {
-        run_pipeline(q, L, n, smem + GLOBAL_RING_OFFSET,
-                     [&](const unsigned char* stage, uint64_t row0, uint32_t r0) {
-                         consume_global<NS, FAST>(q, L, tab, stage, row0, r0, claims);
-                     });
-    }
+    run_pipeline(q, L, n, smem + GLOBAL_RING_OFFSET, [&](const unsigned char* stage, uint64_t row0, uint32_t r0) {
+        consume_global<NS, FAST>(q, L, tab, stage, row0, r0, claims);
+    });
     if (threadIdx.x >= 32) {
         const uint32_t w = __reduce_add_sync(0xffffffffu, claims);
         if ((threadIdx.x & 31) == 0 && w) atomicAdd(cta_claims, w);
