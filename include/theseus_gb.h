@@ -102,9 +102,10 @@ enum { TP_AGG_AUTO = 0, TP_AGG_SHARED = 1, TP_AGG_GLOBAL = 2 };
  *                         TP_FLAG_RAW_PAGES: store appended columns in pages
  *                         at their full width.  Without it every batch stores
  *                         each integer column as (value - the batch's minimum)
- *                         in the fewest bytes (1, 2 or 4) that hold the
- *                         batch's range, and the device widens it after the
- *                         copy: fewer bytes cross the host link.
+ *                         bit-packed in the fewest bits that hold the batch's
+ *                         range (up to 31; 8, 16 and 32 bits as plain bytes,
+ *                         words), and the device widens it after the copy:
+ *                         fewer bytes cross the host link.
  *                         TP_FLAG_NO_JIT: never compile plan-specialised
  *                         kernels at run time (NVRTC); the ahead-of-time
  *                         staged kernels run every shape.  Without the flag a

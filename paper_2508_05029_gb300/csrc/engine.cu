@@ -81,17 +81,23 @@ tp_status copy_batch_column(tp_engine* e, const tp_table* t, const Batch& b, int
     // narrow_width_max bytes per row)
     const uint64_t sz = b.narrow(c) ? (uint64_t)narrow_width_max(t, c) : type_size(t->types[c]);
     uint8_t* dst = (uint8_t*)(b.narrow(c) ? enc : full) + row_off * sz;
+    // a bit-packed column copies the bytes its values occupy, not the rest of
+    // its last word, so it stays inside its rows' share of the staging slot
+    uint64_t left = b.packed(c) ? (b.rows * b.enc_bits[c] + 7) / 8 : UINT64_MAX;
     for (const Extent& x : b.cols[c]) {
+        const uint64_t bytes = std::min<uint64_t>(x.bytes, left);
+        if (bytes == 0) break;
+        left -= bytes;
         const uint8_t* src = (const uint8_t*)tp_page_ptr(e, x.page) + x.offset;
         if (stage) {
-            memcpy(*stage, src, x.bytes);
+            memcpy(*stage, src, bytes);
             src = *stage;
-            *stage += x.bytes;
+            *stage += bytes;
         }
-        const cudaError_t err = cudaMemcpyAsync(dst, src, x.bytes, cudaMemcpyHostToDevice, st);
+        const cudaError_t err = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
         if (err != cudaSuccess) return fail(TP_E_CUDA, "batch copy: %s", cudaGetErrorString(err));
-        dst += x.bytes;
-        e->h2d_bytes += x.bytes;
+        dst += bytes;
+        e->h2d_bytes += bytes;
     }
     return TP_OK;
 }
@@ -116,6 +122,7 @@ tp_status widen_batch(tp_engine* e, const tp_table* t, const Batch& b, const std
         d.dst[d.n] = (uint8_t*)full[i] + row_off * sz;
         d.base[d.n] = b.enc_base[c];
         d.w[d.n] = b.enc_w[c];
+        d.bits[d.n] = b.packed(c) ? b.enc_bits[c] : 0;
         d.out[d.n] = (int32_t)sz;
         if (++d.n == tpk::MAX_DECODE) {
             tp_status s = flush();
@@ -123,6 +130,13 @@ tp_status widen_batch(tp_engine* e, const tp_table* t, const Batch& b, const std
         }
     }
     return flush();
+}
+
+int frame_bits(int64_t lo, int64_t hi) {
+    const uint64_t span = (uint64_t)hi - (uint64_t)lo;
+    int bits = 1;
+    while (bits < 64 && (span >> bits) != 0) ++bits;
+    return bits;
 }
 
 int frame_width(int64_t lo, int64_t hi, int full) {
@@ -355,6 +369,11 @@ static void free_batch_pages(tp_engine* e, Batch& b) {
 
 int tp::Batch::width(int c, int32_t type) const { return narrow(c) ? enc_w[c] : type_size(type); }
 
+uint64_t tp::Batch::stored_bytes(int c, int32_t type) const {
+    if (packed(c)) return 4 * ((rows * enc_bits[c] + 31) / 32);   // whole 32-bit words
+    return rows * (uint64_t)width(c, type);
+}
+
 namespace {
 
 int64_t value_at(const void* col, int32_t type, uint64_t i) {
@@ -381,9 +400,10 @@ tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) 
         Batch b;
         b.row0 = t->rows + r0;
         b.rows = rows;
-        if (narrow) {  // frame of reference per batch and column: the batch's minimum, the fewest bytes
+        if (narrow) {  // frame of reference per batch and column: the batch's minimum, the fewest bits
             b.enc_w.assign(nc, 0);
             b.enc_base.assign(nc, 0);
+            b.enc_bits.assign(nc, 0);
             for (int c = 0; c < nc; ++c) {
                 int64_t lo = INT64_MAX, hi = INT64_MIN;
                 for (uint64_t i = r0; i < r0 + rows; ++i) {
@@ -391,7 +411,14 @@ tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) 
                     lo = std::min(lo, v);
                     hi = std::max(hi, v);
                 }
-                b.enc_w[c] = (uint8_t)frame_width(lo, hi, type_size(t->types[c]));
+                const int bits = frame_bits(lo, hi);
+                const int full = type_size(t->types[c]);
+                if (bits < 32 && bits != 8 && bits != 16 && bits < 8 * full) {   // bit-packed
+                    b.enc_bits[c] = (uint8_t)bits;
+                    b.enc_w[c] = (uint8_t)((bits + 7) / 8);
+                } else {   // whole bytes (or full width)
+                    b.enc_w[c] = (uint8_t)frame_width(lo, hi, full);
+                }
                 b.enc_base[c] = lo;
             }
         }
@@ -401,7 +428,7 @@ tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) 
         for (int c = 0; c < nc; ++c) {
             total = (total + 255) & ~255ull;
             off[c] = total;
-            total += rows * b.width(c, t->types[c]);
+            total += b.stored_bytes(c, t->types[c]);
         }
         const uint64_t n_pages = (total + pb - 1) / pb;
         for (uint64_t i = 0; i < n_pages; ++i) {
@@ -417,11 +444,24 @@ tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) 
         }
         b.cols.resize(nc);
         std::vector<uint8_t> enc;
+        std::vector<uint32_t> words;
         for (int c = 0; c < nc; ++c) {
             const int sz = type_size(t->types[c]);
             const uint8_t* src = (const uint8_t*)cols[c] + r0 * sz;
             const int w = b.width(c, t->types[c]);
-            if (b.narrow(c)) {  // little-endian low bytes of (value - base)
+            if (b.packed(c)) {  // (value - base), LSB first, value i at bit i * bits of the word stream
+                const int bits = b.enc_bits[c];
+                words.assign(b.stored_bytes(c, t->types[c]) / 4, 0u);
+                for (uint64_t i = 0; i < rows; ++i) {
+                    const uint64_t d = (uint64_t)value_at(cols[c], t->types[c], r0 + i) - (uint64_t)b.enc_base[c];
+                    const uint64_t at = i * (uint64_t)bits;
+                    const uint64_t k = at >> 5;
+                    const int sh = (int)(at & 31);
+                    words[k] |= (uint32_t)(d << sh);
+                    if (sh + bits > 32) words[k + 1] |= (uint32_t)(d >> (32 - sh));
+                }
+                src = (const uint8_t*)words.data();
+            } else if (b.narrow(c)) {  // little-endian low bytes of (value - base)
                 enc.resize(rows * w);
                 for (uint64_t i = 0; i < rows; ++i) {
                     const uint64_t d = (uint64_t)value_at(cols[c], t->types[c], r0 + i) - (uint64_t)b.enc_base[c];
@@ -429,7 +469,7 @@ tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) 
                 }
                 src = enc.data();
             }
-            uint64_t pos = off[c], left = rows * w;
+            uint64_t pos = off[c], left = b.stored_bytes(c, t->types[c]);
             while (left) {
                 const uint64_t pi = pos / pb, po = pos % pb;
                 const uint64_t take = std::min<uint64_t>(left, pb - po);

@@ -37,6 +37,23 @@ int64_t paged_value(const tp_table* t, int c, uint64_t row) {
     auto it = std::upper_bound(t->batches.begin(), t->batches.end(), row,
                                [](uint64_t r, const Batch& b) { return r < b.row0; });
     const Batch& b = *(it - 1);
+    if (b.packed(c)) {   // the bytes holding the value's bits, gathered across extents
+        const int bits = b.enc_bits[c];
+        const uint64_t at = (row - b.row0) * (uint64_t)bits;
+        uint64_t d = 0;
+        for (uint64_t byte = at / 8, k = 0; byte <= (at + bits - 1) / 8; ++byte, ++k) {
+            uint64_t off = byte;
+            for (const Extent& x : b.cols[c]) {
+                if (off < x.bytes) {
+                    d |= (uint64_t)((const uint8_t*)tp_page_ptr(t->eng, x.page))[x.offset + off] << (8 * k);
+                    break;
+                }
+                off -= x.bytes;
+            }
+        }
+        d = (d >> (at % 8)) & ((1ull << bits) - 1);
+        return (int64_t)((uint64_t)b.enc_base[c] + d);
+    }
     const int sz = b.width(c, t->types[c]);
     uint64_t off = (row - b.row0) * sz;
     for (const Extent& x : b.cols[c]) {
@@ -232,7 +249,7 @@ tp_status for_each_dim_batch(ExecState& S, Scratch& sc, const tpk::BuildDev& pro
     for (size_t i = 0; i < bcols.size(); ++i) {
         tp_status s = sc.alloc(&stage[i], align256(max_rows * type_size(t->types[bcols[i]])));
         const int w = narrow ? narrow_width_max(t, bcols[i]) : 0;
-        if (!s && w) s = sc.alloc(&enc[i], align256(max_rows * (uint64_t)w));
+        if (!s && w) s = sc.alloc(&enc[i], align256(max_rows * (uint64_t)w + 16));   // + the decoder's word overrun
         if (s) return s;
     }
     for (auto& bt : t->batches) {
@@ -356,7 +373,7 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
         for (int c : S.used) {
             tp_status st = sc.alloc(&slot[s][c], align256(max_rows * type_size(t->types[c])));
             const int w = narrow ? narrow_width_max(t, c) : 0;
-            if (!st && w) st = sc.alloc(&enc[s][c], align256(max_rows * (uint64_t)w));
+            if (!st && w) st = sc.alloc(&enc[s][c], align256(max_rows * (uint64_t)w + 16));   // + the decoder's word overrun
             if (st) return st;
             full_used[s].push_back(slot[s][c]);
             enc_used[s].push_back(enc[s][c]);
@@ -431,12 +448,15 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
                 const Batch& b0 = t->batches[bi];
                 // batches lie at row offsets times the widest encoding: a run is
                 // contiguous when its narrow columns use exactly that width
-                bool packed = true;
-                for (int c : S.used) packed = packed && (!b0.narrow(c) || b0.enc_w[c] == narrow_width_max(t, c));
+                // (a bit-packed column's batches decode one at a time)
+                bool contiguous = true;
+                for (int c : S.used)
+                    contiguous = contiguous &&
+                                 (!b0.narrow(c) || (b0.enc_w[c] == narrow_width_max(t, c) && !b0.packed(c)));
                 size_t bj = bi + 1;
                 uint64_t rows = b0.rows;
-                while (packed && bj < groups[g].second && t->batches[bj].enc_w == b0.enc_w &&
-                       t->batches[bj].enc_base == b0.enc_base)
+                while (contiguous && bj < groups[g].second && t->batches[bj].enc_w == b0.enc_w &&
+                       t->batches[bj].enc_bits == b0.enc_bits && t->batches[bj].enc_base == b0.enc_base)
                     rows += t->batches[bj++].rows;
                 rc = widen_batch(e, t, b0, S.used, full_used[s], enc_used[s], row_off, S.lane->compute, rows);
                 row_off += rows;

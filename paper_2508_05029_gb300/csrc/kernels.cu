@@ -287,23 +287,46 @@ cudaError_t launch_final_dense(const uint64_t* gacc, uint32_t key_bits, int n_su
 // Occupied slots of the global table -> (key, slot index); also the max key.
 // ------------------------------------------------------------ narrow pages
 
+__device__ __forceinline__ void store_widened(void* dst, int out, uint64_t i, uint64_t v) {
+    if (out == 8) ((int64_t*)dst)[i] = (int64_t)v;
+    else if (out == 4) ((int32_t*)dst)[i] = (int32_t)(uint32_t)v;
+    else ((uint8_t*)dst)[i] = (uint8_t)v;
+}
+
 template <typename U>
 __device__ __forceinline__ void decode_col(const U* __restrict__ src, int64_t base, void* dst, int out,
                                            uint64_t rows) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    if (out == 8) {
-        int64_t* d = (int64_t*)dst;
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows; i += stride)
-            d[i] = (int64_t)((uint64_t)base + (uint64_t)__ldcs(src + i));
-    } else {
-        int32_t* d = (int32_t*)dst;
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows; i += stride)
-            d[i] = (int32_t)(uint32_t)((uint64_t)base + (uint64_t)__ldcs(src + i));
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows; i += stride)
+        store_widened(dst, out, i, (uint64_t)base + (uint64_t)__ldcs(src + i));
+}
+
+// Row i's value sits at bit bit0 + i * bits of the word stream starting at
+// the 4-byte-aligned address at or below src (bit0 = 8 * the misalignment);
+// the word after the value's first is read only when the value reaches into
+// it, so no word beyond the stream's last is touched.
+__device__ __forceinline__ void decode_bits(const uint8_t* src, int bits, int64_t base, void* dst, int out,
+                                            uint64_t rows) {
+    const uint32_t* w = (const uint32_t*)((uintptr_t)src & ~(uintptr_t)3);
+    const uint64_t bit0 = 8 * ((uintptr_t)src & 3);
+    const uint32_t mask = (1u << bits) - 1u;   // bits <= 31
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows; i += stride) {
+        const uint64_t at = bit0 + i * (uint64_t)bits;
+        const uint64_t k = at >> 5;
+        const uint32_t sh = (uint32_t)(at & 31);
+        uint32_t v = __ldg(w + k) >> sh;
+        if (sh + (uint32_t)bits > 32) v |= __ldg(w + k + 1) << (32 - sh);
+        store_widened(dst, out, i, (uint64_t)base + (uint64_t)(v & mask));
     }
 }
 
 __global__ void k_decode(const __grid_constant__ DecodeCols d, uint64_t rows) {
     for (int c = 0; c < d.n; ++c) {
+        if (d.bits[c]) {
+            decode_bits((const uint8_t*)d.src[c], d.bits[c], d.base[c], d.dst[c], d.out[c], rows);
+            continue;
+        }
         switch (d.w[c]) {
         case 1: decode_col((const uint8_t*)d.src[c], d.base[c], d.dst[c], d.out[c], rows); break;
         case 2: decode_col((const uint16_t*)d.src[c], d.base[c], d.dst[c], d.out[c], rows); break;

@@ -450,15 +450,18 @@ cudaError_t launch_gather_global(const AggTable& t, const uint64_t* sorted_keys,
                                  int num_sms, cudaStream_t st, bool lo_only = false);
 
 // Narrow columns of a host-page batch widened after their copy: column c
-// stores w[c] bytes per row (1, 2 or 4) of (value - base[c]) as an unsigned
-// little-endian integer; dst gets the out[c]-byte (4 or 8) value.
+// stores (value - base[c]) as an unsigned integer, either bits[c] bits per
+// row packed LSB first into little-endian 32-bit words (src need not be
+// word-aligned: the words are read from the aligned address below it) or
+// w[c] bytes per row (1, 2 or 4); dst gets the out[c]-byte (1, 4 or 8) value.
 constexpr int MAX_DECODE = 16;
 struct DecodeCols {
     const void* src[MAX_DECODE];
     void* dst[MAX_DECODE];
     int64_t base[MAX_DECODE];
-    int32_t w[MAX_DECODE];
-    int32_t out[MAX_DECODE];
+    int32_t w[MAX_DECODE];       // bytes per value (1, 2, 4) when bits is 0
+    int32_t bits[MAX_DECODE];    // bits per value of a bit-packed column (1..31), else 0
+    int32_t out[MAX_DECODE];     // bytes per widened value (1, 4, 8)
     int32_t n;
 };
 cudaError_t launch_decode(const DecodeCols& d, uint64_t rows, int num_sms, cudaStream_t st);

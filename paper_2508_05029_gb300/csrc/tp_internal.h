@@ -79,8 +79,15 @@ struct Batch {
     std::vector<uint32_t> pages;
     std::vector<uint8_t> enc_w;              // per column (empty: every column full width)
     std::vector<int64_t> enc_base;
-    int width(int c, int32_t type) const;    // bytes per row of column c as stored
+    // per column (empty: none): bits per value of a bit-packed column (value -
+    // enc_base, LSB first in little-endian 32-bit words), 0 for byte widths;
+    // a packed column's enc_w is ceil(bits / 8), the bytes per row it takes in
+    // a device staging slot
+    std::vector<uint8_t> enc_bits;
+    int width(int c, int32_t type) const;    // bytes per row of column c in a staging slot
+    uint64_t stored_bytes(int c, int32_t type) const;   // bytes of column c in the pages
     bool narrow(int c) const { return !enc_w.empty() && enc_w[c] != 0; }
+    bool packed(int c) const { return !enc_bits.empty() && enc_bits[c] != 0; }
 };
 
 enum Placement : int32_t { PL_PAGES = TP_HOST_PAGES, PL_DEVICE = TP_DEVICE, PL_WRAPPED = 3 };
@@ -273,6 +280,8 @@ tp_status widen_batch(tp_engine* e, const tp_table* t, const Batch& b, const std
 // Narrowest frame-of-reference width (1, 2 or 4 bytes) for values in [lo,
 // hi] of a column of full width `full`, or 0 when it saves nothing.
 int frame_width(int64_t lo, int64_t hi, int full);
+// Bits that hold hi - lo (at least 1).
+int frame_bits(int64_t lo, int64_t hi);
 // Whether any batch of t stores a narrow column.
 bool has_narrow(const tp_table* t);
 // The widest narrow encoding of column c over t's batches (0: never narrow).

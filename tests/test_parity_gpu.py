@@ -347,3 +347,55 @@ def test_narrow_pages_round_trip(flags):
         p.destroy(); ft.destroy(); dt.destroy()
     finally:
         e.close()
+
+
+@pytest.mark.parametrize("chunk", [3_001, 25_001])
+@pytest.mark.parametrize("prefetch", [0, 2])
+def test_bit_packed_pages_every_width(chunk, prefetch):
+    """Host-page columns bit-packed per batch at every width from 1 to 31 bits
+    (int64, int32 and uint8 columns; 8 and 16 bits stay byte widths) give the
+    oracle's result.  The table is appended in chunks: 3,001-row chunks make
+    one batch each, so several of them share a staging slot at row offsets that
+    leave a packed stream unaligned to its words; 25,001-row chunks make odd
+    batches of 9,999 rows with ragged last ones.  The filter, the join key and a
+    group key are packed columns too."""
+    n = 60_013
+    rng = np.random.default_rng(23)
+    fact = dict(
+        d=rng.integers(0, 2557, n).astype(np.int32),                 # 12 bits
+        fk=rng.integers(-40, 60, n).astype(np.int64),                 # 7 bits, negative
+        g=rng.integers(0, 3, n).astype(np.uint8),                     # 2 bits
+    )
+    names = []
+    for bits in range(1, 32):
+        lo = int(rng.integers(-(1 << 40), 1 << 40))
+        fact[f"q{bits}"] = rng.integers(0, 1 << bits, n).astype(np.int64) + lo
+        names.append(f"q{bits}")
+        if bits < 31:
+            lo32 = int(rng.integers(-(1 << 30), (1 << 30) - (1 << bits)))
+            fact[f"i{bits}"] = (rng.integers(0, 1 << bits, n) + lo32).astype(np.int32)
+            names.append(f"i{bits}")
+        if bits < 8:
+            fact[f"u{bits}"] = rng.integers(0, 1 << bits, n).astype(np.uint8)
+            names.append(f"u{bits}")
+    dim = dict(pk=np.arange(-40, 60, dtype=np.int64), attr=(np.arange(100) % 5).astype(np.int32))
+    e = T.Engine(page_bytes=1 << 20, n_pages=512, batch_rows=9_999, prefetch_depth=prefetch)
+    try:
+        dt = e.table_from_numpy(dim, placement=T.TP_HOST_PAGES)
+        for t0 in range(0, len(names), 28):   # a table holds at most 32 columns
+            part = {k: fact[k] for k in ("d", "fk", "g")}
+            part.update({k: fact[k] for k in names[t0:t0 + 28]})
+            ft = e.table_from_chunks({k: v[r:r + chunk] for k, v in part.items()} for r in range(0, n, chunk))
+            for k in range(t0, min(t0 + 28, len(names)), 6):   # six sums, a count and an average
+                cols = names[k:min(k + 6, t0 + 28)]
+                q = dict(filter=dict(col="d", lo=10, hi=2400), join=dict(fact_col="fk", dim_col="pk"),
+                         group=[("dim", "attr", 3), ("fact", "g", 2)],
+                         aggs=[("sum", c) for c in cols] + [("count",), ("avg", cols[0])])
+                p = e.plan(ft, dt, q)
+                with p.execute() as r:
+                    assert_matches_oracle(r, oracle.run_query(part, dim, q), q["aggs"])
+                p.destroy()
+            ft.destroy()
+        dt.destroy()
+    finally:
+        e.close()
