@@ -795,7 +795,7 @@ def e2e_measure(T, W, torch, dev, stream, local, world, fact, dim, n_fact, n_dim
            "d2h_bytes_per_step": (s1["d2h_bytes"] - s0["d2h_bytes"]) // steps,
            "h2d_gbs": h2d_gbs,
            "source": "pinned page pool, 64 MiB pages, prefetch depth 2" +
-                     (", full-width columns" if flags & T.TP_FLAG_RAW_PAGES else ", narrow (frame-of-reference) columns")}
+                     (", full-width columns" if flags & T.TP_FLAG_RAW_PAGES else ", bit-packed frame-of-reference columns")}
     p3.destroy()
     ft2.destroy()
     dt2.destroy()
