@@ -102,34 +102,83 @@ tp_status copy_batch_column(tp_engine* e, const tp_table* t, const Batch& b, int
     return TP_OK;
 }
 
+namespace {
+
+// Decode entries of one or more batches, launched whenever the descriptor is
+// full and once at the end.
+struct Widener {
+    tp_engine* e;
+    cudaStream_t st;
+    tpk::DecodeCols d{};
+    tp_status flush() {
+        if (d.n == 0) return TP_OK;
+        const cudaError_t err = tpk::launch_decode(d, e->num_sms, st);
+        if (err != cudaSuccess) return fail(TP_E_CUDA, "widening a batch: %s", cudaGetErrorString(err));
+        e->launches++;
+        d.n = 0;
+        std::fill(last.begin(), last.end(), -1);
+        return TP_OK;
+    }
+    std::vector<int> last;   // per column of cols: its entry in d, -1 if none
+    // batch b's narrow columns among cols, copied at row offset row_off of
+    // the staging slots enc (narrow) / full (widened); a byte-encoded column
+    // that continues the previous batch's entry (same encoding, rows at the
+    // slot's width) extends it
+    tp_status add(const tp_table* t, const Batch& b, const std::vector<int>& cols, const std::vector<void*>& full,
+                  const std::vector<void*>& enc, uint64_t row_off) {
+        if (last.size() != cols.size()) last.assign(cols.size(), -1);
+        for (size_t i = 0; i < cols.size(); ++i) {
+            const int c = cols[i];
+            if (!b.narrow(c)) {
+                last[i] = -1;
+                continue;
+            }
+            const uint64_t sz = type_size(t->types[c]);
+            const uint64_t wmax = (uint64_t)narrow_width_max(t, c);
+            const uint8_t* src = (const uint8_t*)enc[i] + row_off * wmax;
+            const int k = last[i];
+            if (k >= 0 && !b.packed(c) && d.bits[k] == 0 && d.w[k] == b.enc_w[c] && b.enc_w[c] == wmax &&
+                d.base[k] == b.enc_base[c] && (const uint8_t*)d.src[k] + d.rows[k] * wmax == src) {
+                d.rows[k] += b.rows;
+                continue;
+            }
+            last[i] = d.n;
+            d.src[d.n] = src;
+            d.dst[d.n] = (uint8_t*)full[i] + row_off * sz;
+            d.base[d.n] = b.enc_base[c];
+            d.rows[d.n] = b.rows;
+            d.w[d.n] = b.enc_w[c];
+            d.bits[d.n] = b.packed(c) ? b.enc_bits[c] : 0;
+            d.out[d.n] = (uint8_t)sz;
+            if (++d.n == tpk::MAX_DECODE) {
+                tp_status s = flush();
+                if (s) return s;
+            }
+        }
+        return TP_OK;
+    }
+};
+
+}  // namespace
+
 tp_status widen_batch(tp_engine* e, const tp_table* t, const Batch& b, const std::vector<int>& cols,
                       const std::vector<void*>& full, const std::vector<void*>& enc, uint64_t row_off,
-                      cudaStream_t st, uint64_t rows) {
-    if (rows == 0) rows = b.rows;
-    tpk::DecodeCols d{};
-    auto flush = [&]() -> tp_status {
-        const cudaError_t err = tpk::launch_decode(d, rows, e->num_sms, st);
-        if (err != cudaSuccess) return fail(TP_E_CUDA, "widening a batch: %s", cudaGetErrorString(err));
-        if (d.n) e->launches++;
-        d.n = 0;
-        return TP_OK;
-    };
-    for (size_t i = 0; i < cols.size(); ++i) {
-        const int c = cols[i];
-        if (!b.narrow(c)) continue;
-        const uint64_t sz = type_size(t->types[c]);
-        d.src[d.n] = (const uint8_t*)enc[i] + row_off * (uint64_t)narrow_width_max(t, c);
-        d.dst[d.n] = (uint8_t*)full[i] + row_off * sz;
-        d.base[d.n] = b.enc_base[c];
-        d.w[d.n] = b.enc_w[c];
-        d.bits[d.n] = b.packed(c) ? b.enc_bits[c] : 0;
-        d.out[d.n] = (int32_t)sz;
-        if (++d.n == tpk::MAX_DECODE) {
-            tp_status s = flush();
-            if (s) return s;
-        }
+                      cudaStream_t st) {
+    Widener w{e, st};
+    tp_status s = w.add(t, b, cols, full, enc, row_off);
+    return s ? s : w.flush();
+}
+
+tp_status widen_batches(tp_engine* e, const tp_table* t, size_t first, size_t last, const std::vector<int>& cols,
+                        const std::vector<void*>& full, const std::vector<void*>& enc, cudaStream_t st) {
+    Widener w{e, st};
+    uint64_t row_off = 0;
+    for (size_t bi = first; bi < last; ++bi) {
+        tp_status s = w.add(t, t->batches[bi], cols, full, enc, row_off);
+        if (s) return s;
+        row_off += t->batches[bi].rows;
     }
-    return flush();
+    return w.flush();
 }
 
 int frame_bits(int64_t lo, int64_t hi) {

@@ -442,26 +442,9 @@ tp_status for_each_batch(ExecState& S, Scratch& sc, F&& kernel) {
         uint64_t rows = 0;
         for (size_t bi = groups[g].first; bi < groups[g].second; ++bi) rows += t->batches[bi].rows;
         if (prefetch) cudaStreamWaitEvent(S.lane->compute, loaded[s], 0);
-        if (narrow) {  // widen the narrow columns; consecutive batches with one encoding in one launch
-            uint64_t row_off = 0;
-            for (size_t bi = groups[g].first; bi < groups[g].second && rc == TP_OK;) {
-                const Batch& b0 = t->batches[bi];
-                // batches lie at row offsets times the widest encoding: a run is
-                // contiguous when its narrow columns use exactly that width
-                // (a bit-packed column's batches decode one at a time)
-                bool contiguous = true;
-                for (int c : S.used)
-                    contiguous = contiguous &&
-                                 (!b0.narrow(c) || (b0.enc_w[c] == narrow_width_max(t, c) && !b0.packed(c)));
-                size_t bj = bi + 1;
-                uint64_t rows = b0.rows;
-                while (contiguous && bj < groups[g].second && t->batches[bj].enc_w == b0.enc_w &&
-                       t->batches[bj].enc_bits == b0.enc_bits && t->batches[bj].enc_base == b0.enc_base)
-                    rows += t->batches[bj++].rows;
-                rc = widen_batch(e, t, b0, S.used, full_used[s], enc_used[s], row_off, S.lane->compute, rows);
-                row_off += rows;
-                bi = bj;
-            }
+        if (narrow) {  // widen the narrow columns of every batch of the group, in as few launches as fit
+            rc = widen_batches(e, t, groups[g].first, groups[g].second, S.used, full_used[s], enc_used[s],
+                               S.lane->compute);
             if (rc) break;
         }
         for (int c : S.used) colptr[c] = gptr[s][c];

@@ -321,24 +321,26 @@ __device__ __forceinline__ void decode_bits(const uint8_t* src, int bits, int64_
     }
 }
 
-__global__ void k_decode(const __grid_constant__ DecodeCols d, uint64_t rows) {
+__global__ void k_decode(const __grid_constant__ DecodeCols d) {
     for (int c = 0; c < d.n; ++c) {
         if (d.bits[c]) {
-            decode_bits((const uint8_t*)d.src[c], d.bits[c], d.base[c], d.dst[c], d.out[c], rows);
+            decode_bits((const uint8_t*)d.src[c], d.bits[c], d.base[c], d.dst[c], d.out[c], d.rows[c]);
             continue;
         }
         switch (d.w[c]) {
-        case 1: decode_col((const uint8_t*)d.src[c], d.base[c], d.dst[c], d.out[c], rows); break;
-        case 2: decode_col((const uint16_t*)d.src[c], d.base[c], d.dst[c], d.out[c], rows); break;
-        default: decode_col((const uint32_t*)d.src[c], d.base[c], d.dst[c], d.out[c], rows); break;
+        case 1: decode_col((const uint8_t*)d.src[c], d.base[c], d.dst[c], d.out[c], d.rows[c]); break;
+        case 2: decode_col((const uint16_t*)d.src[c], d.base[c], d.dst[c], d.out[c], d.rows[c]); break;
+        default: decode_col((const uint32_t*)d.src[c], d.base[c], d.dst[c], d.out[c], d.rows[c]); break;
         }
     }
 }
 
-cudaError_t launch_decode(const DecodeCols& d, uint64_t rows, int num_sms, cudaStream_t st) {
-    if (rows == 0 || d.n == 0) return cudaSuccess;
+cudaError_t launch_decode(const DecodeCols& d, int num_sms, cudaStream_t st) {
+    uint64_t rows = 0;
+    for (int c = 0; c < d.n; ++c) rows = std::max<uint64_t>(rows, d.rows[c]);
+    if (rows == 0) return cudaSuccess;
     const uint64_t blocks = std::min<uint64_t>((rows + 255) / 256, (uint64_t)num_sms * 4);
-    k_decode<<<(unsigned)blocks, 256, 0, st>>>(d, rows);
+    k_decode<<<(unsigned)blocks, 256, 0, st>>>(d);
     return cudaGetLastError();
 }
 

@@ -449,22 +449,24 @@ cudaError_t launch_gather_global(const AggTable& t, const uint64_t* sorted_keys,
                                  const uint32_t* sorted_idx, uint64_t n, int n_sum, const OutDev& o,
                                  int num_sms, cudaStream_t st, bool lo_only = false);
 
-// Narrow columns of a host-page batch widened after their copy: column c
-// stores (value - base[c]) as an unsigned integer, either bits[c] bits per
-// row packed LSB first into little-endian 32-bit words (src need not be
-// word-aligned: the words are read from the aligned address below it) or
-// w[c] bytes per row (1, 2 or 4); dst gets the out[c]-byte (1, 4 or 8) value.
-constexpr int MAX_DECODE = 16;
+// Narrow columns of host-page batches widened after their copy: entry k holds
+// rows[k] values of (value - base[k]) as unsigned integers, either bits[k]
+// bits per row packed LSB first into little-endian 32-bit words (src need not
+// be word-aligned: the words are read from the aligned address below it) or
+// w[k] bytes per row (1, 2 or 4); dst gets the out[k]-byte (1, 4 or 8) values.
+// One launch widens every (batch, column) entry of a staging slot.
+constexpr int MAX_DECODE = 64;
 struct DecodeCols {
     const void* src[MAX_DECODE];
     void* dst[MAX_DECODE];
     int64_t base[MAX_DECODE];
-    int32_t w[MAX_DECODE];       // bytes per value (1, 2, 4) when bits is 0
-    int32_t bits[MAX_DECODE];    // bits per value of a bit-packed column (1..31), else 0
-    int32_t out[MAX_DECODE];     // bytes per widened value (1, 4, 8)
+    uint64_t rows[MAX_DECODE];
+    uint8_t w[MAX_DECODE];
+    uint8_t bits[MAX_DECODE];
+    uint8_t out[MAX_DECODE];
     int32_t n;
 };
-cudaError_t launch_decode(const DecodeCols& d, uint64_t rows, int num_sms, cudaStream_t st);
+cudaError_t launch_decode(const DecodeCols& d, int num_sms, cudaStream_t st);
 
 // Rows of the filter column that pass, among `samples` evenly spaced rows.
 cudaError_t launch_sample_filter(const QueryDev& q, uint64_t n, uint32_t samples,

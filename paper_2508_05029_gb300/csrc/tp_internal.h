@@ -272,11 +272,15 @@ std::string dense_shape(const tpk::QueryDev& q, const tpk::StageLayout& L, bool 
 tp_status copy_batch_column(tp_engine* e, const tp_table* t, const Batch& b, int c, void* full, void* enc,
                             uint64_t row_off, cudaStream_t st, uint8_t** stage = nullptr);
 // Widens batch b's narrow columns among cols (enc -> full, the offsets of
-// copy_batch_column) with one launch on st; rows (0: b.rows) lets one launch
-// cover consecutive batches that share b's encoding.
+// copy_batch_column at row_off) with one launch on st.
 tp_status widen_batch(tp_engine* e, const tp_table* t, const Batch& b, const std::vector<int>& cols,
                       const std::vector<void*>& full, const std::vector<void*>& enc, uint64_t row_off,
-                      cudaStream_t st, uint64_t rows = 0);
+                      cudaStream_t st);
+// The same for batches [first, last) of t copied one after another into the
+// same slots (each at the rows of the ones before it), in as few launches as
+// the decode descriptor allows.
+tp_status widen_batches(tp_engine* e, const tp_table* t, size_t first, size_t last, const std::vector<int>& cols,
+                        const std::vector<void*>& full, const std::vector<void*>& enc, cudaStream_t st);
 // Narrowest frame-of-reference width (1, 2 or 4 bytes) for values in [lo,
 // hi] of a column of full width `full`, or 0 when it saves nothing.
 int frame_width(int64_t lo, int64_t hi, int full);
