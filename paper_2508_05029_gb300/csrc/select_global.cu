@@ -13,10 +13,13 @@
 //    HBM rate and writes the batch-relative indices of the passing rows to a
 //    selection vector.  A chunk's passing rows get their output range from
 //    one atomic per CTA-chunk and stay in ascending row order inside it.
-//  * k_agg_selected gives every lane four selected rows, so all lanes issue
+//  * k_agg_selected gives every lane SEL_RPL selected rows, so all lanes issue
 //    their gathers, probes and table updates together; equal keys among a
 //    warp's rows (consecutive rows of one order key) are combined first
-//    (agg_warp.cuh), and hashed-table claims are counted once per warp.
+//    (agg_warp.cuh), and hashed-table claims are counted once per warp.  Two
+//    rows per lane at four CTAs per SM (64 registers) measured faster than
+//    four rows at two CTAs (128 registers): 0.128 against 0.140 ms at 600k
+//    selected rows; eight rows at one CTA 0.147 ms.
 #include <algorithm>
 #include <type_traits>
 
@@ -175,15 +178,16 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(const __grid_constant__ 
     }
 }
 
-// The selected rows' join, group key and terms, four rows per lane (entries
-// e0 + 32 j + lane of the selection vector), then warp-aggregated table
-// updates.  *count selected rows; the filter is not evaluated again.
+// The selected rows' join, group key and terms, SEL_RPL rows per lane
+// (entries e0 + 32 j + lane of the selection vector), then warp-aggregated
+// table updates.  *count selected rows; the filter is not evaluated again.
+constexpr int SEL_RPL = 2;
 template <int NS, bool FAST>
-__global__ void __launch_bounds__(256, 2) k_agg_selected(const __grid_constant__ QueryDev q,
+__global__ void __launch_bounds__(256, 4) k_agg_selected(const __grid_constant__ QueryDev q,
                                                       const uint32_t* __restrict__ sel,
                                                       const unsigned long long* count,
                                                       const __grid_constant__ AggTable tab) {
-    constexpr int R = 4;
+    constexpr int R = SEL_RPL;
     constexpr int NSX = NS > 0 ? NS : 1;
     const uint64_t cnt = *count;
     const int lane = threadIdx.x & 31;
@@ -205,8 +209,13 @@ __global__ void __launch_bounds__(256, 2) k_agg_selected(const __grid_constant__
         // fact-side group fields go straight to their bit positions of the
         // packed key (first field highest); dimension fields follow the probe
         int64_t fk[R], a[NSX][R], b[NSX][R];
-        uint64_t key[R] = {0, 0, 0, 0};
-        bool bad[R] = {false, false, false, false};
+        uint64_t key[R];
+        bool bad[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            key[j] = 0;
+            bad[j] = false;
+        }
 #pragma unroll
         for (int j = 0; j < R; ++j) fk[j] = (q.has_join && pass[j]) ? ld1(q.fk, row[j]) : 0;
         {
@@ -237,7 +246,9 @@ __global__ void __launch_bounds__(256, 2) k_agg_selected(const __grid_constant__
                 b[s][j] = (on && q.skind[s] == S_MUL_SUB) ? ld1(q.sb[s], row[j]) : 0;
             }
         }
-        uint32_t pay[R] = {0, 0, 0, 0};
+        uint32_t pay[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) pay[j] = 0;
         if (q.has_join) {
             probe4<true>(q.jt, fk, pass, pay, q.err);
 #pragma unroll
@@ -290,17 +301,36 @@ bool select_usable(const QueryDev& q, uint64_t n) {
            ((uintptr_t)q.fcol.ptr & 15u) == 0;
 }
 
+// CTAs of `fn` (block of `threads`, no dynamic shared memory) resident on
+// one SM at once; a grid of at most that many per SM runs in one wave, so no
+// CTA starts its fixed share of the chunks only after others finished theirs.
+static int resident_ctas(const void* fn, int threads) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n;
+}
+
+template <int T>
+static void select_t(const QueryDev& q, uint64_t n, uint32_t* sel, unsigned long long* cursor, uint64_t chunks,
+                     int num_sms, cudaStream_t st) {
+    static const int per_sm = resident_ctas((const void*)k_select<T>, SEL_THREADS);
+    const unsigned grid = (unsigned)std::min<uint64_t>(chunks, (uint64_t)num_sms * per_sm);
+    k_select<T><<<grid, SEL_THREADS, 0, st>>>(q.fcol, q.flo, q.fhi, n, sel, cursor);
+}
+
 cudaError_t launch_select(const QueryDev& q, uint64_t n, uint32_t* sel, unsigned long long* cursor, int num_sms,
                           cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     const int per = q.fcol.type == T_I32 ? 4 : (q.fcol.type == T_I64 ? 2 : 16);
     const uint64_t ch = (uint64_t)SEL_LOADS * SEL_THREADS * per;
     const uint64_t chunks = (n + ch - 1) / ch;
-    const unsigned grid = (unsigned)std::min<uint64_t>(chunks, (uint64_t)num_sms * 8);
     switch (q.fcol.type) {
-    case T_I32: k_select<T_I32><<<grid, SEL_THREADS, 0, st>>>(q.fcol, q.flo, q.fhi, n, sel, cursor); break;
-    case T_I64: k_select<T_I64><<<grid, SEL_THREADS, 0, st>>>(q.fcol, q.flo, q.fhi, n, sel, cursor); break;
-    default: k_select<T_U8><<<grid, SEL_THREADS, 0, st>>>(q.fcol, q.flo, q.fhi, n, sel, cursor); break;
+    case T_I32: select_t<T_I32>(q, n, sel, cursor, chunks, num_sms, st); break;
+    case T_I64: select_t<T_I64>(q, n, sel, cursor, chunks, num_sms, st); break;
+    default: select_t<T_U8>(q, n, sel, cursor, chunks, num_sms, st); break;
     }
     return cudaGetLastError();
 }
@@ -315,8 +345,8 @@ static cudaError_t launch_selected_t(const QueryDev& q, const uint32_t* sel, con
 cudaError_t launch_agg_selected(const QueryDev& q, const uint32_t* sel, const unsigned long long* count,
                                 uint64_t max_rows, const AggTable& t, bool fast, int num_sms, cudaStream_t st) {
     if (max_rows == 0) return cudaSuccess;
-    // one warp per 128 selected rows at most, at most 8 CTAs per SM
-    const uint64_t warps = (max_rows + 127) / 128;
+    // one warp per 32 * SEL_RPL selected rows at most, at most 8 CTAs per SM
+    const uint64_t warps = (max_rows + 32 * SEL_RPL - 1) / (32 * SEL_RPL);
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((warps + 7) / 8, (uint64_t)num_sms * 8));
     const int ns = q.n_sum;
     if (fast) {
