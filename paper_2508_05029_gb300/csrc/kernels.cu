@@ -532,8 +532,19 @@ __global__ void __launch_bounds__(256) k_compact_global(const __grid_constant__ 
 cudaError_t launch_compact_global(const AggTable& t, uint64_t cap_with_side, uint64_t* keys,
                                   uint32_t* idx, unsigned long long* count,
                                   unsigned long long* maxkey, int num_sms, cudaStream_t st) {
+    // as many CTAs as are resident at once: each takes a fixed share of the
+    // chunks, so a second, partial wave would leave SMs idle at the end
+    static const int per_sm = [] {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, (const void*)k_compact_global, 256, 0) != cudaSuccess ||
+            n < 1) {
+            cudaGetLastError();
+            n = 1;
+        }
+        return n;
+    }();
     uint64_t blocks = (cap_with_side + COMPACT_PER * 256 - 1) / (COMPACT_PER * 256);
-    uint64_t cap = (uint64_t)num_sms * 8;
+    const uint64_t cap = (uint64_t)num_sms * per_sm;
     if (blocks > cap) blocks = cap;
     k_compact_global<<<(unsigned)blocks, 256, 0, st>>>(t, cap_with_side, keys, idx, count, maxkey);
     return cudaGetLastError();
