@@ -16,10 +16,8 @@
 //  * k_agg_selected gives every lane SEL_RPL selected rows, so all lanes issue
 //    their gathers, probes and table updates together; equal keys among a
 //    warp's rows (consecutive rows of one order key) are combined first
-//    (agg_warp.cuh), and hashed-table claims are counted once per warp.  Two
-//    rows per lane at four CTAs per SM (64 registers) measured faster than
-//    four rows at two CTAs (128 registers): 0.128 against 0.140 ms at 600k
-//    selected rows; eight rows at one CTA 0.147 ms.
+//    (agg_warp.cuh), and hashed-table claims are counted once per warp.  The
+//    join probe (probe4) takes exactly four rows, so SEL_RPL is four.
 #include <algorithm>
 #include <type_traits>
 
@@ -181,13 +179,14 @@ __global__ void __launch_bounds__(SEL_THREADS) k_select(const __grid_constant__ 
 // The selected rows' join, group key and terms, SEL_RPL rows per lane
 // (entries e0 + 32 j + lane of the selection vector), then warp-aggregated
 // table updates.  *count selected rows; the filter is not evaluated again.
-constexpr int SEL_RPL = 2;
+constexpr int SEL_RPL = 4;
 template <int NS, bool FAST>
-__global__ void __launch_bounds__(256, 4) k_agg_selected(const __grid_constant__ QueryDev q,
+__global__ void __launch_bounds__(256, 2) k_agg_selected(const __grid_constant__ QueryDev q,
                                                       const uint32_t* __restrict__ sel,
                                                       const unsigned long long* count,
                                                       const __grid_constant__ AggTable tab) {
     constexpr int R = SEL_RPL;
+    static_assert(R == 4, "probe4 probes exactly four rows per lane");
     constexpr int NSX = NS > 0 ? NS : 1;
     const uint64_t cnt = *count;
     const int lane = threadIdx.x & 31;
