@@ -213,9 +213,13 @@ tp_status tp_table_create(tp_engine* eng, const tp_table_desc* desc, tp_table** 
  * per column, element type as declared) into pool pages.  Rows are cut into
  * batches of batch_rows; within a batch the columns lie back to back across
  * as many pages as they need, so one column may span pages, and the tail of
- * the batch's last page stays unused (Section 3.4).  The caller keeps its
- * arrays.  Errors: TP_E_POOL_EMPTY (pool exhausted: the append is undone),
- * TP_E_INVALID (table already on the device). */
+ * the batch's last page stays unused (Section 3.4).  Unless the engine has
+ * TP_FLAG_RAW_PAGES, each integer column of a batch is stored as (value -
+ * the batch's minimum) in the fewest bits that hold the batch's range:
+ * bit-packed, value i at bit i * bits of a little-endian 32-bit word stream,
+ * or as plain 1-, 2- or 4-byte integers when that is 8, 16 or 32 bits.  The
+ * caller keeps its arrays.  Errors: TP_E_POOL_EMPTY (pool exhausted: the
+ * append is undone), TP_E_INVALID (table already on the device). */
 tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows);
 
 /* Moves the table: TP_DEVICE copies every column into one contiguous device
