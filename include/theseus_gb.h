@@ -543,6 +543,14 @@ tp_status tp_stats_get(tp_engine* eng, tp_stats* out);
 /* Fault injection for tests: the next n host page allocations and device
  * reservations fail as if exhausted. */
 tp_status tp_debug_fail_next_alloc(tp_engine* eng, int32_t n);
+/* The page encoding of a bit-packed column, for tests (host only, no GPU):
+ * packs values[0..n) (each below 2^bits, 1 <= bits <= 31) into
+ * words[0..ceil(n * bits / 32)), value i at bits [i * bits, (i + 1) * bits)
+ * of the stream, least significant bit first, stream bit j being bit (j % 32)
+ * of words[j / 32].  The same function writes tp_table_append's pages.
+ * Errors: TP_E_INVALID (NULL pointers with n > 0, bits out of range, or a
+ * value that does not fit). */
+tp_status tp_debug_pack_bits(const uint64_t* values, uint64_t n, int32_t bits, uint32_t* words);
 
 /* ------------------------------------------------------ allocation-free call */
 

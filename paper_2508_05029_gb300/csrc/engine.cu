@@ -181,6 +181,16 @@ tp_status widen_batches(tp_engine* e, const tp_table* t, size_t first, size_t la
     return w.flush();
 }
 
+void pack_bits(const uint64_t* v, uint64_t n, int bits, uint32_t* words) {
+    for (uint64_t i = 0; i < n; ++i) {
+        const uint64_t at = i * (uint64_t)bits;
+        const uint64_t k = at >> 5;
+        const int sh = (int)(at & 31);
+        words[k] |= (uint32_t)(v[i] << sh);
+        if (sh + bits > 32) words[k + 1] |= (uint32_t)(v[i] >> (32 - sh));
+    }
+}
+
 int frame_bits(int64_t lo, int64_t hi) {
     const uint64_t span = (uint64_t)hi - (uint64_t)lo;
     int bits = 1;
@@ -494,21 +504,17 @@ tp_status tp_table_append(tp_table* t, const void* const* cols, uint64_t nrows) 
         b.cols.resize(nc);
         std::vector<uint8_t> enc;
         std::vector<uint32_t> words;
+        std::vector<uint64_t> deltas;
         for (int c = 0; c < nc; ++c) {
             const int sz = type_size(t->types[c]);
             const uint8_t* src = (const uint8_t*)cols[c] + r0 * sz;
             const int w = b.width(c, t->types[c]);
             if (b.packed(c)) {  // (value - base), LSB first, value i at bit i * bits of the word stream
-                const int bits = b.enc_bits[c];
+                deltas.resize(rows);
+                for (uint64_t i = 0; i < rows; ++i)
+                    deltas[i] = (uint64_t)value_at(cols[c], t->types[c], r0 + i) - (uint64_t)b.enc_base[c];
                 words.assign(b.stored_bytes(c, t->types[c]) / 4, 0u);
-                for (uint64_t i = 0; i < rows; ++i) {
-                    const uint64_t d = (uint64_t)value_at(cols[c], t->types[c], r0 + i) - (uint64_t)b.enc_base[c];
-                    const uint64_t at = i * (uint64_t)bits;
-                    const uint64_t k = at >> 5;
-                    const int sh = (int)(at & 31);
-                    words[k] |= (uint32_t)(d << sh);
-                    if (sh + bits > 32) words[k + 1] |= (uint32_t)(d >> (32 - sh));
-                }
+                pack_bits(deltas.data(), rows, b.enc_bits[c], words.data());
                 src = (const uint8_t*)words.data();
             } else if (b.narrow(c)) {  // little-endian low bytes of (value - base)
                 enc.resize(rows * w);
@@ -721,6 +727,18 @@ tp_status tp_stats_get(tp_engine* e, tp_stats* s) {
     std::lock_guard<std::mutex> lk(e->pool.mu);
     s->pages_total = e->pool.n_pages;
     s->pages_in_use = e->pool.n_pages - (uint32_t)e->pool.free_stack.size();
+    return TP_OK;
+}
+
+tp_status tp_debug_pack_bits(const uint64_t* values, uint64_t n, int32_t bits, uint32_t* words) {
+    clear_error();
+    if (bits < 1 || bits > 31 || (n && (!values || !words)))
+        return fail(TP_E_INVALID, "tp_debug_pack_bits: bad arguments");
+    for (uint64_t i = 0; i < n; ++i)
+        if (values[i] >> bits) return fail(TP_E_INVALID, "tp_debug_pack_bits: value %llu needs more than %d bits",
+                                           (unsigned long long)values[i], bits);
+    std::fill(words, words + (n * (uint64_t)bits + 31) / 32, 0u);
+    pack_bits(values, n, bits, words);
     return TP_OK;
 }
 

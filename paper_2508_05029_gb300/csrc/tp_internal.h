@@ -286,6 +286,10 @@ tp_status widen_batches(tp_engine* e, const tp_table* t, size_t first, size_t la
 int frame_width(int64_t lo, int64_t hi, int full);
 // Bits that hold hi - lo (at least 1).
 int frame_bits(int64_t lo, int64_t hi);
+// ORs v[0..n) (each below 2^bits) into the zeroed words: value i at stream
+// bits [i * bits, (i + 1) * bits), LSB first, stream bit j = bit j % 32 of
+// words[j / 32] (the bit-packed page layout).
+void pack_bits(const uint64_t* v, uint64_t n, int bits, uint32_t* words);
 // Whether any batch of t stores a narrow column.
 bool has_narrow(const tp_table* t);
 // The widest narrow encoding of column c over t's batches (0: never narrow).

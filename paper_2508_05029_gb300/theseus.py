@@ -154,6 +154,7 @@ SIGNATURES = {
     "tp_last_error": (ctypes.c_char_p, []),
     "tp_stats_get": (_i32, [_vp, ctypes.POINTER(tp_stats)]),
     "tp_debug_fail_next_alloc": (_i32, [_vp, _i32]),
+    "tp_debug_pack_bits": (_i32, [_vp, _u64, _i32, _vp]),
     "tp_batch_create": (_i32, [_vp, _PP, _i32, ctypes.c_char_p, _PP]),
     "tp_batch_execute": (_i32, [_vp, _PP]),
     "tp_batch_last_ms": (ctypes.c_double, [_vp]),
