@@ -293,12 +293,24 @@ __device__ __forceinline__ void store_widened(void* dst, int out, uint64_t i, ui
     else ((uint8_t*)dst)[i] = (uint8_t)v;
 }
 
+// Each thread widens DECODE_PER rows per round (rows i, i + T, ... for T
+// threads in the grid, so every load and store stays coalesced), with all of
+// their loads issued before the first store.
+constexpr int DECODE_PER = 4;
+
 template <typename U>
 __device__ __forceinline__ void decode_col(const U* __restrict__ src, int64_t base, void* dst, int out,
                                            uint64_t rows) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows; i += stride)
-        store_widened(dst, out, i, (uint64_t)base + (uint64_t)__ldcs(src + i));
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < rows; i0 += DECODE_PER * T) {
+        U v[DECODE_PER];
+#pragma unroll
+        for (int k = 0; k < DECODE_PER; ++k)
+            if (i0 + k * T < rows) v[k] = __ldcs(src + i0 + k * T);
+#pragma unroll
+        for (int k = 0; k < DECODE_PER; ++k)
+            if (i0 + k * T < rows) store_widened(dst, out, i0 + k * T, (uint64_t)base + (uint64_t)v[k]);
+    }
 }
 
 // Row i's value sits at bit bit0 + i * bits of the word stream starting at
@@ -310,14 +322,28 @@ __device__ __forceinline__ void decode_bits(const uint8_t* src, int bits, int64_
     const uint32_t* w = (const uint32_t*)((uintptr_t)src & ~(uintptr_t)3);
     const uint64_t bit0 = 8 * ((uintptr_t)src & 3);
     const uint32_t mask = (1u << bits) - 1u;   // bits <= 31
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < rows; i += stride) {
-        const uint64_t at = bit0 + i * (uint64_t)bits;
-        const uint64_t k = at >> 5;
-        const uint32_t sh = (uint32_t)(at & 31);
-        uint32_t v = __ldg(w + k) >> sh;
-        if (sh + (uint32_t)bits > 32) v |= __ldg(w + k + 1) << (32 - sh);
-        store_widened(dst, out, i, (uint64_t)base + (uint64_t)(v & mask));
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < rows; i0 += DECODE_PER * T) {
+        uint32_t lo[DECODE_PER], hi[DECODE_PER], sh[DECODE_PER];
+#pragma unroll
+        for (int r = 0; r < DECODE_PER; ++r) {
+            const uint64_t i = i0 + r * T;
+            lo[r] = hi[r] = sh[r] = 0;
+            if (i >= rows) continue;
+            const uint64_t at = bit0 + i * (uint64_t)bits;
+            const uint64_t k = at >> 5;
+            sh[r] = (uint32_t)(at & 31);
+            lo[r] = __ldg(w + k);
+            if (sh[r] + (uint32_t)bits > 32) hi[r] = __ldg(w + k + 1);
+        }
+#pragma unroll
+        for (int r = 0; r < DECODE_PER; ++r) {
+            const uint64_t i = i0 + r * T;
+            if (i >= rows) continue;
+            uint32_t v = lo[r] >> sh[r];
+            if (sh[r] + (uint32_t)bits > 32) v |= hi[r] << (32 - sh[r]);
+            store_widened(dst, out, i, (uint64_t)base + (uint64_t)(v & mask));
+        }
     }
 }
 
